@@ -1,0 +1,216 @@
+/*
+ * fstgpu.h -- C ABI of libfstgpu.so: Viterbi and forward-backward decoding
+ * with large, sparse, epsilon-free weighted finite-state transducers on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Argueta & Chiang, "Decoding with Finite-State Transducers on
+ * GPUs", EACL 2017.  An FST is M = (Q, Sigma, s, F, delta) with output
+ * labels on the arcs (Sec. 3); the weight of a string w = w_1..w_n is
+ * weight(w) = s^T (prod_t delta[w_t]) f (Eq. 1).  Viterbi evaluates Eq. 1 in
+ * the (max, *) pair semiring of Sec. 3 (best path and its arcs; Alg. 1,
+ * Sec. 5.1); forward-backward evaluates it in the (+, *) semiring and
+ * returns expected arc counts (Alg. 2, Sec. 5.2).  The only loop that is
+ * parallel is the one over the arcs of the slice delta[w_t] (Sec. 5).
+ *
+ * Conventions used by every entry point:
+ *   - Weights are natural-log weights theta = log p (weight_kind
+ *     FST_WEIGHT_LOG) or costs w = -log p (FST_WEIGHT_COST).  Scores and
+ *     log Z are always returned as log-weights (theta domain).  -inf (cost
+ *     +inf) means "absent"; NaN and theta = +inf are rejected.  A negative
+ *     zero weight is stored as +0.
+ *   - Arc ids are the caller's array order (0..num_arcs-1).
+ *   - Ties in Viterbi go to the lowest arc id into each state at each step,
+ *     and to the lowest state id at the final step (the paper's packed
+ *     atomicMax of Sec. 5.1 would pick the highest id; this library fixes
+ *     the lowest so that results are reproducible and checkable).
+ *   - Viterbi runs in float32 with one rounded addition per candidate, so
+ *     its score and path are bit-identical to a sequential float32 Viterbi.
+ *     Forward-backward relaxes in float32 in the log domain with a float64
+ *     running per-step normaliser folded into log Z.
+ *   - Status codes: 0 = FST_OK; every failure returns a nonzero code and
+ *     sets a thread-local message readable with fst_last_error().
+ *   - All entry points are host functions.  "Host" pointers are ordinary
+ *     CPU memory; "device" pointers are CUDA device memory of the device
+ *     that was current when the FST was created.
+ */
+#ifndef FSTGPU_H_
+#define FSTGPU_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FST_API __attribute__((visibility("default")))
+#else
+#define FST_API
+#endif
+
+#define FST_OK 0
+#define FST_ERR_INVALID_ARG 1  /* a size, id, label or weight out of range */
+#define FST_ERR_NO_PATH 2      /* the string has no accepting path */
+#define FST_ERR_OOM 3          /* device allocation failed */
+#define FST_ERR_CUDA 4         /* a CUDA runtime call failed */
+#define FST_ERR_TIMEOUT 5      /* a bounded device wait expired */
+#define FST_ERR_UNSUPPORTED 6  /* sizes beyond this library's limits */
+#define FST_ERR_STATE 7        /* call out of order (e.g. backward before forward) */
+
+#define FST_WEIGHT_LOG 0
+#define FST_WEIGHT_COST 1
+
+#define FST_FLAG_DEVICE_PTRS 1 /* fst_create / fst_set_weights: inputs are device pointers */
+
+typedef struct fst_s fst_t;
+typedef struct fst_plan_s fst_plan_t;
+
+/* Build an FST on the current CUDA device (Sec. 3 tuple; Sec. 4 and Fig. 2
+ * arc arrays S, T, O, P plus input labels; the start vector s and final
+ * vector f of Sec. 3, generalised to per-state log-weights).
+ *   num_states  Q >= 1.   num_arcs A >= 0 (A < 2^31).   num_isyms m >= 1.
+ *   src, dst    [A] states in [0, Q).      ilabel [A] in [0, m).
+ *   olabel      [A] any int32 (returned by Viterbi; may be NULL = all -1).
+ *   weight      [A] per weight_kind.
+ *   start_weight, final_weight  [Q] per weight_kind; "absent" = -inf
+ *               (FST_WEIGHT_LOG) or +inf (FST_WEIGHT_COST).
+ *   flags       FST_FLAG_DEVICE_PTRS if the arrays are device pointers.
+ * Every input is copied; the handle owns its device memory.  The arc store
+ * is re-sorted on the device into symbol-major, destination-segmented and
+ * source-segmented windows (the R offsets of Fig. 2 live on the device and
+ * the host).  Synchronous.  Errors: FST_ERR_INVALID_ARG (ranges, NaN,
+ * theta = +inf), FST_ERR_UNSUPPORTED (padded arc count >= 2^31),
+ * FST_ERR_OOM, FST_ERR_CUDA.  On error *out is NULL. */
+FST_API int fst_create(int32_t num_states, int64_t num_arcs, const int32_t* src, const int32_t* dst,
+               const int32_t* ilabel, const int32_t* olabel, const float* weight,
+               int32_t weight_kind, const float* start_weight, const float* final_weight,
+               int32_t num_isyms, int32_t flags, fst_t** out);
+
+/* Free an FST and everything it owns.  NULL is accepted.  Plans created on
+ * it must be destroyed first. */
+FST_API int fst_destroy(fst_t* fst);
+
+/* Sizes of a built FST (host outputs, any may be NULL): states, arcs, input
+ * symbols, padded arcs of the forward layout, windows of the forward
+ * layout, destination segments (sum over symbols of distinct destinations)
+ * and source segments. */
+FST_API int fst_info(const fst_t* fst, int32_t* num_states, int64_t* num_arcs, int32_t* num_isyms,
+             int64_t* padded_arcs, int64_t* num_windows, int64_t* dst_segments,
+             int64_t* src_segments);
+
+/* Per input symbol a (host arrays of length num_isyms, any may be NULL):
+ * |delta[a]| arcs (R[a+1]-R[a] of Fig. 2), distinct destinations D_a and
+ * distinct sources U_a.  Used for relaxation counts and the bytes model. */
+FST_API int fst_symbol_stats(const fst_t* fst, int64_t* arcs, int64_t* dsts, int64_t* srcs);
+
+/* Replace every arc weight (caller arc order, [num_arcs], per weight_kind;
+ * host or device per flags).  Same validation as fst_create; on error the
+ * FST keeps its old weights.  Used between training steps.  Synchronous
+ * with respect to the host; call it only when no plan on this FST is
+ * running. */
+FST_API int fst_set_weights(fst_t* fst, const float* weight, int32_t weight_kind, int32_t flags);
+
+/* Plain method, one string (the paper's design, Sec. 5: one kernel launch
+ * per input position over the arcs of delta[w_t], then the backtrace of
+ * Sec. 5.1 on the device).  Host pointers throughout; synchronous.
+ *   ids         [n] host, symbols in [0, m); n >= 0.
+ *   best_score  host float: log-weight of the best path including start and
+ *               final weights; -inf if there is none.
+ *   arc_path    [n] host (may be NULL if n == 0): arc id taken at each
+ *               position; -1 everywhere when there is no path.
+ *   olabels     [n] host or NULL: output label of each arc of the path.
+ * Returns FST_OK, FST_ERR_NO_PATH (outputs filled as above), or an error. */
+FST_API int fst_viterbi(fst_t* fst, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
+                int32_t* olabels);
+
+/* Plain method, one string: forward-backward (Alg. 2, Sec. 5.2).  Host
+ * pointers; synchronous.
+ *   log_z          host double: log of the total weight of the string (Eq. 1
+ *                  in the (+, *) semiring); -inf if no path.
+ *   arc_posteriors [num_arcs] host float or NULL: expected count of each
+ *                  arc, sum_t gamma_t(k) = d log Z / d theta_k; all zero if
+ *                  there is no path.
+ * Returns FST_OK, FST_ERR_NO_PATH or an error. */
+FST_API int fst_forward_backward(fst_t* fst, const int32_t* ids, int32_t n, double* log_z,
+                         float* arc_posteriors);
+
+/* Batched method: B strings decoded together, all on the device.
+ *   d_ids       device int32 [N], concatenated strings.
+ *   d_offsets   device int64 [B+1], d_offsets[0] = 0, non-decreasing;
+ *               string b is d_ids[d_offsets[b] .. d_offsets[b+1]).
+ *   d_scores    device float [B] best log-weights (-inf = no path).
+ *   d_paths     device int32 [N] arc ids, aligned with d_ids (-1 = no path).
+ *   d_olabels   device int32 [N] or NULL.
+ *   d_status    device int32 [B] or NULL: FST_OK or FST_ERR_NO_PATH per string.
+ *   stream      cudaStream_t to run on (NULL = legacy default stream).
+ * Allocates a plan internally (see fst_plan_create), runs it and frees it;
+ * returns after the work is queued and the plan's memory is released, which
+ * synchronises the stream.  The return code covers argument and launch
+ * errors; per-string outcomes go to d_status. */
+FST_API int fst_viterbi_batch(fst_t* fst, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
+                      float* d_scores, int32_t* d_paths, int32_t* d_olabels, int32_t* d_status,
+                      void* stream);
+
+/* Batched forward-backward.  Arguments as fst_viterbi_batch, plus
+ *   d_weights   device float [B] or NULL (all 1): per-string factor g_b;
+ *   d_logz      device double [B];
+ *   d_counts    device float [num_arcs] or NULL: sum_b g_b * count_b(k),
+ *               the gradient of sum_b g_b log Z_b with respect to theta. */
+FST_API int fst_forward_backward_batch(fst_t* fst, const int32_t* d_ids, const int64_t* d_offsets,
+                               int32_t B, const float* d_weights, double* d_logz,
+                               float* d_counts, int32_t* d_status, void* stream);
+
+/* A plan holds everything a batch needs on the device: the work lists (one
+ * entry per (step, symbol group, window)), the per-string frontiers and the
+ * per-step storage for backpointers and forward values.  Once created, the
+ * run calls below allocate nothing, so a sequence of them can be captured
+ * into a CUDA graph and replayed.
+ *   d_ids, d_offsets  as fst_viterbi_batch; they are read during
+ *               fst_plan_create only (the plan keeps its own copy).
+ *   mem_budget_bytes  cap on per-step storage; strings are processed in
+ *               waves that fit (0 = a default of 16 GiB).
+ *   flags       FST_PLAN_SINGLE_WAVE: fail with FST_ERR_OOM instead of
+ *               splitting into waves (needed by fst_plan_forward followed by
+ *               fst_plan_backward, which keep state between calls).
+ * Synchronises `stream`. */
+#define FST_PLAN_SINGLE_WAVE 1
+#define FST_PLAN_NO_VITERBI 2   /* do not allocate backpointer storage */
+#define FST_PLAN_NO_FB 4        /* do not allocate forward-backward storage */
+FST_API int fst_plan_create(fst_t* fst, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
+                    int64_t mem_budget_bytes, int32_t flags, void* stream, fst_plan_t** out);
+FST_API int fst_plan_destroy(fst_plan_t* plan);
+
+/* Plan statistics (host outputs, any may be NULL): strings, tokens (sum of
+ * lengths), waves, longest string, arc relaxations of one pass (sum over
+ * tokens of |delta[w_t]|), kernel launches of one Viterbi run and of one
+ * forward-backward run, and device bytes held by the plan. */
+FST_API int fst_plan_info(const fst_plan_t* plan, int32_t* num_strings, int64_t* num_tokens,
+                  int32_t* num_waves, int32_t* max_len, int64_t* relaxations,
+                  int64_t* viterbi_launches, int64_t* fb_launches, int64_t* device_bytes);
+
+/* Run Viterbi for every string of the plan (outputs as fst_viterbi_batch).
+ * Asynchronous on `stream`; allocates nothing. */
+FST_API int fst_plan_viterbi(fst_plan_t* plan, float* d_scores, int32_t* d_paths, int32_t* d_olabels,
+                     int32_t* d_status, void* stream);
+
+/* Forward pass only (log Z per string); keeps the forward values in the
+ * plan for fst_plan_backward.  Requires a single-wave plan. */
+FST_API int fst_plan_forward(fst_plan_t* plan, double* d_logz, int32_t* d_status, void* stream);
+
+/* Backward pass and expected counts after fst_plan_forward on the same plan:
+ * d_counts[k] = sum_b d_weights[b] * count_b(k) (d_weights NULL = all 1).
+ * Returns FST_ERR_STATE if no forward pass preceded it. */
+FST_API int fst_plan_backward(fst_plan_t* plan, const float* d_weights, float* d_counts, void* stream);
+
+/* Forward and backward for every wave of the plan (any number of waves). */
+FST_API int fst_plan_forward_backward(fst_plan_t* plan, const float* d_weights, double* d_logz,
+                              float* d_counts, int32_t* d_status, void* stream);
+
+/* Message of the last failing call on this host thread ("" if none). */
+FST_API const char* fst_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSTGPU_H_ */

@@ -1,0 +1,84 @@
+"""ctypes binding of libfstgpu.so (argument marshalling only).
+
+Every entry point of ``include/fstgpu.h`` is declared here with the same
+name.  Loading fails loudly when the library has not been built: there is
+no CPU fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+OK, INVALID_ARG, NO_PATH, OOM, CUDA, TIMEOUT, UNSUPPORTED, STATE = range(8)
+WEIGHT_LOG, WEIGHT_COST = 0, 1
+FLAG_DEVICE_PTRS = 1
+PLAN_SINGLE_WAVE, PLAN_NO_VITERBI, PLAN_NO_FB = 1, 2, 4
+
+_lock = threading.Lock()
+_lib = None
+
+vp = C.c_void_p
+i32, i64 = C.c_int32, C.c_int64
+
+# name -> argtypes (all return int, except fst_last_error)
+SIGNATURES = {
+    "fst_create": [i32, i64, vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(vp)],
+    "fst_destroy": [vp],
+    "fst_info": [vp, vp, vp, vp, vp, vp, vp, vp],
+    "fst_symbol_stats": [vp, vp, vp, vp],
+    "fst_set_weights": [vp, vp, i32, i32],
+    "fst_viterbi": [vp, vp, i32, vp, vp, vp],
+    "fst_forward_backward": [vp, vp, i32, vp, vp],
+    "fst_viterbi_batch": [vp, vp, vp, i32, vp, vp, vp, vp, vp],
+    "fst_forward_backward_batch": [vp, vp, vp, i32, vp, vp, vp, vp, vp],
+    "fst_plan_create": [vp, vp, vp, i32, i64, i32, vp, C.POINTER(vp)],
+    "fst_plan_destroy": [vp],
+    "fst_plan_info": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
+    "fst_plan_viterbi": [vp, vp, vp, vp, vp, vp],
+    "fst_plan_forward": [vp, vp, vp, vp],
+    "fst_plan_backward": [vp, vp, vp, vp],
+    "fst_plan_forward_backward": [vp, vp, vp, vp, vp, vp],
+}
+
+
+class FstError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed with code {code}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load libfstgpu.so; raises if it is missing (call build() first)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or lib_path()
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"{p} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = C.CDLL(p)
+        for name, args in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        lib.fst_last_error.argtypes = []
+        lib.fst_last_error.restype = C.c_char_p
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def check(rc: int, where: str, allow=(OK,)) -> int:
+    if rc not in allow:
+        msg = load().fst_last_error().decode(errors="replace")
+        raise FstError(rc, where, msg)
+    return rc

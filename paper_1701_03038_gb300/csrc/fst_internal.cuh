@@ -1,0 +1,151 @@
+// fst_internal.cuh -- shared definitions of the fstgpu CUDA library.
+//
+// Arc store (built once per FST on the device, Sec. 4 / Fig. 2 redesigned):
+// the arcs of every input symbol a (the slice delta[a], R[a]..R[a+1]-1 in
+// the paper) are sorted by (segment state, arc id) and cut into segments of
+// equal segment state.  Two layouts exist:
+//   forward  -- segments by destination (the column-major / CSC reading of
+//               Sec. 4: one reduction per destination state), arcs carry src;
+//   backward -- segments by source, arcs carry dst.
+// Segments are packed into windows of WIN = 128 arcs (one warp, 4 arcs per
+// lane, 16-byte vector loads).  A segment never straddles a window unless it
+// is longer than WIN ("long" segment): then it starts on a window boundary
+// and owns whole windows.  The tail of a window is padded with arcs of
+// weight -inf.  Each window has a 128-bit head mask (bit i set = arc i
+// starts a segment) and the index of its first segment.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "fstgpu.h"
+
+namespace fstgpu {
+
+constexpr int WARP = 32;
+constexpr int APL = 4;            // arcs per lane
+constexpr int WIN = WARP * APL;   // arcs per window
+constexpr int GMAX = 16;          // tokens per group (same symbol, same step)
+constexpr unsigned FULL = 0xffffffffu;
+
+// Window metadata, 32 bytes: two 16-byte loads.
+struct __align__(16) WinMeta {
+  int32_t seg;     // first segment starting in this window (or the long segment)
+  int32_t lseg;    // long windows: slice-local index of the long segment; -1 otherwise
+  int32_t lwin0;   // long windows: slice-local index of the segment's first long window
+  int32_t lcnt;    // long windows: number of windows of the segment
+  uint32_t mask[4];
+};
+
+struct Layout {
+  int64_t P = 0;         // padded arcs = nwin * WIN
+  int64_t nwin = 0;
+  int64_t nseg = 0;
+  int32_t* other = nullptr;   // [P] gathered state (src for forward, dst for backward); 0 on padding
+  float* theta = nullptr;     // [P] log-weight; -inf on padding
+  int32_t* arc_id = nullptr;  // [P] caller arc id; -1 on padding
+  double* theta64 = nullptr;  // [P] optional float64 weights (finite-difference variant)
+  WinMeta* win = nullptr;     // [nwin]
+  int32_t* seg_state = nullptr;  // [nseg] dst (forward) / src (backward)
+  int32_t* seg_pos = nullptr;    // [nseg] padded start position
+  int64_t* sym_win = nullptr;    // [m+1]
+  int64_t* sym_seg = nullptr;    // [m+1]
+  int64_t* sym_lseg = nullptr;   // [m+1] long segments
+  int64_t* sym_lwin = nullptr;   // [m+1] long windows
+  // host copies
+  int64_t* h_sym_win = nullptr;
+  int64_t* h_sym_seg = nullptr;
+  int64_t* h_sym_lseg = nullptr;
+  int64_t* h_sym_lwin = nullptr;
+};
+
+}  // namespace fstgpu
+
+struct fst_s {
+  int32_t Q = 0;
+  int64_t A = 0;
+  int32_t m = 0;
+  int device = 0;
+  int num_sms = 0;
+  fstgpu::Layout fwd, bwd;
+  float* theta_s = nullptr;    // [Q]
+  float* theta_f = nullptr;    // [Q]
+  int32_t* olabel = nullptr;   // [A] by caller arc id
+  int64_t* sym_arc = nullptr;  // [m+1] R offsets (device)
+  int64_t* h_sym_arc = nullptr;
+  int32_t max_seg_len = 0;
+  // per-handle state for the single-string calls
+  struct PlainWs* plain = nullptr;
+  uint32_t tag_epoch = 1;
+};
+
+namespace fstgpu {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+#define FST_CUDA(call)                                          \
+  do {                                                          \
+    cudaError_t e__ = (call);                                   \
+    if (e__ != cudaSuccess) return ::fstgpu::cuda_fail(e__, #call); \
+  } while (0)
+
+// ------------------------------------------------------------ device math
+// Order-preserving map float -> uint32 (total order, -0 < +0).
+__device__ __forceinline__ uint32_t fkey(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+constexpr uint32_t FKEY_NEG_INF = 0x007fffffu;  // fkey(-inf)
+
+// Tagged frontier entry: low word float bits, high word tag.
+__device__ __forceinline__ float tagged_value(unsigned long long e, uint32_t tag) {
+  return (uint32_t)(e >> 32) == tag ? __uint_as_float((uint32_t)e) : -__int_as_float(0x7f800000);
+}
+__device__ __forceinline__ unsigned long long tagged_make(float v, uint32_t tag) {
+  return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
+}
+
+// ------------------------------------------------------------ primitives
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the key.
+int radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s);
+// Exclusive scan of n int64 values (out may alias in); *total gets the sum (host).
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, cudaStream_t s);
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+
+// Device memory helpers (plain cudaMalloc; every buffer is owned by a handle).
+template <class T>
+int dalloc(T** p, int64_t n) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, (size_t)n * sizeof(T));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    set_error("cudaMalloc of %lld bytes failed: %s", (long long)((size_t)n * sizeof(T)),
+              cudaGetErrorString(e));
+    return FST_ERR_OOM;
+  }
+  return FST_OK;
+}
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// ------------------------------------------------------------ arc store
+int build_store(fst_s* f, const int32_t* d_src, const int32_t* d_dst, const int32_t* d_il,
+                const float* d_theta, cudaStream_t s);
+void free_layout(Layout& L);
+int set_layout_weights(fst_s* f, const float* d_theta_by_id, cudaStream_t s);
+int set_layout_weights64(fst_s* f, const double* d_theta_by_id, cudaStream_t s);
+
+int grid_for(int64_t work_warps, int block_threads, int num_sms, int max_blocks_per_sm);
+
+}  // namespace fstgpu

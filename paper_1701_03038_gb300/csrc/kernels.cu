@@ -1,0 +1,758 @@
+// kernels.cu -- the per-position relaxation kernels and their epilogues.
+//
+// For input position t the paper relaxes every arc of the slice
+// delta[w_t] with one thread per arc and resolves collisions on a state
+// with atomics: a packed 64-bit (probability | arc) atomicMax for Viterbi
+// (Sec. 5.1) and an atomic log-add-exp for forward and backward (Sec. 5.2,
+// Eq. 3).  Here one warp owns one 128-arc window of a segmented slice
+// (see store.cu): each lane loads 4 arcs with two 16-byte loads, gathers the
+// frontier, and the warp reduces every segment with a segmented shuffle
+// scan.  Only a segment longer than a window is combined across warps: with
+// the packed 64-bit atomicMax for Viterbi and with ordered per-window
+// partials for log-sum-exp; the last warp to arrive finalises it.
+//
+// Values: Viterbi keys are (order-preserving float32 bits << 32) | ~arc
+// position, so a 64-bit max picks the best score and, on ties, the lowest
+// position -- the lowest arc id, because arcs of a segment are sorted by id.
+// Forward and backward carry (max, scaled sum) pairs; each step's values are
+// shifted by that step's maximum, with the running shift kept in float64.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace fstgpu {
+namespace {
+
+constexpr int KT = 256;  // threads per block of the step kernels
+
+__device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
+
+struct MaxKey {
+  typedef unsigned long long T;
+  static __device__ __forceinline__ T identity() { return 0ull; }
+  static __device__ __forceinline__ T combine(T a, T b) { return a > b ? a : b; }
+  static __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(FULL, v, d); }
+};
+
+// log-sum-exp pairs (M, S): the value M + log(S).
+struct LogAdd {
+  typedef float2 T;
+  static __device__ __forceinline__ T identity() { return make_float2(__int_as_float(0xff800000), 0.f); }
+  static __device__ __forceinline__ T combine(T a, T b) {
+    if (a.x < b.x) { T c = a; a = b; b = c; }
+    if (b.x == __int_as_float(0xff800000)) return a;
+    return make_float2(a.x, a.y + b.y * expf(b.x - a.x));
+  }
+  static __device__ __forceinline__ T shfl_up(T v, int d) {
+    return make_float2(__shfl_up_sync(FULL, v.x, d), __shfl_up_sync(FULL, v.y, d));
+  }
+};
+
+// Segmented inclusive scan over lanes: each lane contributes the aggregate
+// of its last partial segment; `lane_head` = the lane contains a segment
+// start.  Returns the aggregate from the lane's last segment start (or the
+// window start) through this lane.
+template <class Op>
+__device__ __forceinline__ typename Op::T seg_scan_lanes(typename Op::T agg, bool lane_head, int lane) {
+  const uint32_t hm = __ballot_sync(FULL, lane_head);
+  const uint32_t le = hm & (0xffffffffu >> (31 - lane));
+  const int start = le ? 31 - __clz(le) : 0;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    typename Op::T o = Op::shfl_up(agg, d);
+    if (lane - d >= start) agg = Op::combine(o, agg);
+  }
+  return agg;
+}
+
+// Full segmented prefix at each of the lane's 4 arcs (bit j of h = arc j
+// starts a segment).  At a segment's last arc this is the segment total.
+template <class Op>
+__device__ __forceinline__ void window_scan(const typename Op::T (&e)[APL], uint32_t h, int lane,
+                                            typename Op::T (&full)[APL]) {
+  typename Op::T p[APL];
+  p[0] = e[0];
+#pragma unroll
+  for (int j = 1; j < APL; ++j) p[j] = ((h >> j) & 1u) ? e[j] : Op::combine(p[j - 1], e[j]);
+  const typename Op::T incl = seg_scan_lanes<Op>(p[APL - 1], h != 0u, lane);
+  typename Op::T carry = Op::shfl_up(incl, 1);
+  if (lane == 0) carry = Op::identity();
+  const int first = h ? __ffs(h) - 1 : APL;
+#pragma unroll
+  for (int j = 0; j < APL; ++j) full[j] = (j < first) ? Op::combine(carry, p[j]) : p[j];
+}
+
+struct ItemCtx {
+  int32_t g, sym, cnt;
+  int64_t wslice;
+};
+
+__device__ __forceinline__ ItemCtx resolve(const WorkView& W, int64_t item) {
+  ItemCtx c;
+  if (W.single) {
+    c.g = -1; c.sym = W.sym0; c.cnt = 1; c.wslice = item;
+    return c;
+  }
+  int lo = W.g0, hi = W.g1 - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (W.grp_item[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  c.g = lo;
+  c.sym = W.grp_sym[lo];
+  c.cnt = W.grp_cnt[lo];
+  c.wslice = item - W.grp_item[lo];
+  return c;
+}
+
+__device__ __forceinline__ int32_t token_of(const WorkView& W, const ItemCtx& c, int j) {
+  return W.single ? W.p0 : W.sorted_tok[W.grp_first[c.g] + j];
+}
+
+struct WinCtx {
+  int64_t w;
+  WinMeta meta;
+  uint32_t h;       // this lane's head bits
+  int32_t hb;       // heads of the window before this lane
+  int32_t segbase;  // first segment of the slice
+};
+
+__device__ __forceinline__ WinCtx load_win(const LayoutView& L, int32_t sym, int64_t wslice, int lane) {
+  WinCtx x;
+  x.w = L.sym_win[sym] + wslice;
+  x.meta = L.win[x.w];
+  const uint32_t word = x.meta.mask[lane >> 3];
+  const int sh = (lane & 7) * 4;
+  x.h = (word >> sh) & 0xFu;
+  int hb = __popc(word & ((1u << sh) - 1u));
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (k < (lane >> 3)) hb += __popc(x.meta.mask[k]);
+  x.hb = hb;
+  x.segbase = (int32_t)L.sym_seg[sym];
+  return x;
+}
+
+__device__ __forceinline__ int64_t warp_id_global() {
+  return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+__device__ __forceinline__ int64_t warps_total() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
+
+// ======================================================================
+// Viterbi step (Alg. 1 inner loop; Sec. 5.1)
+// ======================================================================
+__device__ __forceinline__ void vit_write(const LayoutView& L, const WaveState& S, int64_t cb, int32_t s,
+                                          int32_t sl, unsigned long long key, unsigned long long* aout,
+                                          uint32_t tag) {
+  S.bp[cb + sl] = key ? (int32_t)(~(uint32_t)key) : -1;
+  if (key) aout[L.seg_state[s]] = tagged_make(fkey_inv((uint32_t)(key >> 32)), tag);
+}
+
+__global__ void __launch_bounds__(KT) k_vit_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t tag_base = *S.epoch + S.tok0;
+  const int64_t nw = warps_total();
+  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
+    const ItemCtx c = resolve(W, item);
+    const WinCtx x = load_win(L, c.sym, c.wslice, lane);
+    const int64_t base = x.w * WIN + lane * APL;
+    const int4 s4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
+    const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
+    const int32_t src[APL] = {s4.x, s4.y, s4.z, s4.w};
+    const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
+    const bool is_long = x.meta.lseg >= 0;
+    const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
+    for (int j = 0; j < c.cnt; ++j) {
+      const int32_t p = token_of(W, c, j);
+      const int32_t b = T.b[p], t = T.t[p];
+      float a[APL];
+      if (t == 1) {
+#pragma unroll
+        for (int k = 0; k < APL; ++k) a[k] = __ldg(S.theta_s + src[k]);
+      } else {
+        const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+        const uint32_t tg = tag_base + (uint32_t)(p - 1);
+#pragma unroll
+        for (int k = 0; k < APL; ++k) a[k] = tagged_value(__ldg(ab + src[k]), tg);
+      }
+      unsigned long long key[APL];
+#pragma unroll
+      for (int k = 0; k < APL; ++k) {
+        const float cand = __fadd_rn(a[k], th[k]);
+        key[k] = (cand == neg_inf()) ? 0ull
+                                     : (((unsigned long long)fkey(cand) << 32) |
+                                        (unsigned long long)(~(uint32_t)(base + k)));
+      }
+      unsigned long long full[APL];
+      window_scan<MaxKey>(key, x.h, lane, full);
+      const int64_t cb = T.cbase[p];
+      unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
+      const uint32_t tag = tag_base + (uint32_t)p;
+      if (!is_long) {
+        int cum = x.hb;
+#pragma unroll
+        for (int k = 0; k < APL; ++k) {
+          cum += (x.h >> k) & 1u;
+          const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
+          if (tail) {
+            const int32_t s = x.meta.seg + cum - 1;
+            vit_write(L, S, cb, s, s - x.segbase, full[k], aout, tag);
+          }
+        }
+      } else if (lane == 31) {
+        // a destination segment that spans warps: packed 64-bit atomicMax
+        const int64_t slot = T.lbase[p] + x.meta.lseg;
+        atomicMax(S.skey + slot, full[APL - 1]);
+        __threadfence();
+        const uint32_t prev = atomicAdd(S.scnt + slot, 1u);
+        if (prev == (uint32_t)x.meta.lcnt - 1u) {
+          __threadfence();
+          const unsigned long long kf = atomicMax(S.skey + slot, 0ull);
+          const int32_t s = x.meta.seg;
+          vit_write(L, S, cb, s, s - x.segbase, kf, aout, tag);
+          S.skey[slot] = 0ull;
+          S.scnt[slot] = 0u;
+        }
+      }
+    }
+  }
+}
+
+// ======================================================================
+// Long-segment log-sum-exp: per-window partials, combined in window order
+// by the last warp to arrive.  Returns the segment total in every lane of
+// the finalising warp; `fin` tells whether this warp finalised.
+// ======================================================================
+__device__ __forceinline__ bool long_lse_arrive(const LayoutView& L, const WaveState& S, const WinCtx& x,
+                                                int64_t lslot, int64_t lwslot, float2 part, int lane,
+                                                float2& total) {
+  uint32_t prev = 0;
+  if (lane == 31) {
+    const int64_t w0 = L.seg_pos[x.meta.seg] / WIN;
+    S.spart[lwslot + x.meta.lwin0 + (x.w - w0)] = part;
+    __threadfence();
+    prev = atomicAdd(S.scnt + lslot + x.meta.lseg, 1u);
+  }
+  prev = __shfl_sync(FULL, prev, 31);
+  if (prev != (uint32_t)x.meta.lcnt - 1u) return false;
+  __threadfence();
+  float2 acc = LogAdd::identity();
+  const volatile float2* pp = S.spart + lwslot + x.meta.lwin0;
+  for (int j = lane; j < x.meta.lcnt; j += 32) {
+    float2 v;
+    v.x = pp[j].x;
+    v.y = pp[j].y;
+    acc = LogAdd::combine(acc, v);
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    float2 o = make_float2(__shfl_xor_sync(FULL, acc.x, d), __shfl_xor_sync(FULL, acc.y, d));
+    acc = (lane & d) ? LogAdd::combine(o, acc) : LogAdd::combine(acc, o);
+  }
+  if (lane == 0) S.scnt[lslot + x.meta.lseg] = 0u;
+  total = acc;
+  return true;
+}
+
+__device__ __forceinline__ float lse_value(float2 v) {
+  return v.x == neg_inf() ? neg_inf() : v.x + logf(v.y);
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, d));
+  return v;
+}
+
+__device__ __forceinline__ float decode_max(uint32_t k) { return k ? fkey_inv(k) : neg_inf(); }
+
+// ======================================================================
+// Forward step (Alg. 2 forward loop; Sec. 5.2)
+// ======================================================================
+__global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t tag_base = *S.epoch + S.tok0;
+  const int64_t nw = warps_total();
+  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
+    const ItemCtx c = resolve(W, item);
+    const WinCtx x = load_win(L, c.sym, c.wslice, lane);
+    const int64_t base = x.w * WIN + lane * APL;
+    const int4 s4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
+    const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
+    const int32_t src[APL] = {s4.x, s4.y, s4.z, s4.w};
+    const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
+    const bool is_long = x.meta.lseg >= 0;
+    const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
+    for (int j = 0; j < c.cnt; ++j) {
+      const int32_t p = token_of(W, c, j);
+      const int32_t b = T.b[p], t = T.t[p];
+      float a[APL];
+      if (t == 1) {
+#pragma unroll
+        for (int k = 0; k < APL; ++k) a[k] = __ldg(S.theta_s + src[k]);
+      } else {
+        const float mprev = decode_max(S.mkey[p - 1]);
+        const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+        const uint32_t tg = tag_base + (uint32_t)(p - 1);
+#pragma unroll
+        for (int k = 0; k < APL; ++k) {
+          const float r = tagged_value(__ldg(ab + src[k]), tg);
+          a[k] = (r == neg_inf() || mprev == neg_inf()) ? neg_inf() : r - mprev;
+        }
+      }
+      float2 e[APL];
+#pragma unroll
+      for (int k = 0; k < APL; ++k) {
+        const float v = a[k] + th[k];
+        e[k] = (v == neg_inf()) ? LogAdd::identity() : make_float2(v, 1.f);
+      }
+      float2 full[APL];
+      window_scan<LogAdd>(e, x.h, lane, full);
+      const int64_t cb = T.cbase[p];
+      unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
+      const uint32_t tag = tag_base + (uint32_t)p;
+      float rmax = neg_inf();
+      if (!is_long) {
+        int cum = x.hb;
+#pragma unroll
+        for (int k = 0; k < APL; ++k) {
+          cum += (x.h >> k) & 1u;
+          const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
+          if (tail) {
+            const int32_t s = x.meta.seg + cum - 1;
+            const float r = lse_value(full[k]);
+            S.rc[cb + (s - x.segbase)] = r;
+            if (r != neg_inf()) aout[L.seg_state[s]] = tagged_make(r, tag);
+            rmax = fmaxf(rmax, r);
+          }
+        }
+      } else {
+        float2 tot;
+        if (long_lse_arrive(L, S, x, T.lbase[p], T.lwbase[p], full[APL - 1], lane, tot)) {
+          const int32_t s = x.meta.seg;
+          const float r = lse_value(tot);
+          if (lane == 0) {
+            S.rc[cb + (s - x.segbase)] = r;
+            if (r != neg_inf()) aout[L.seg_state[s]] = tagged_make(r, tag);
+          }
+          rmax = r;
+        }
+      }
+      rmax = warp_max(rmax);
+      if (lane == 0 && rmax != neg_inf()) atomicMax(S.mkey + p, fkey(rmax));
+    }
+  }
+}
+
+// ======================================================================
+// Scatter the stored forward values of step t_s back into the dense
+// frontier (needed by the backward step t_s + 1 when step t_s + 2 has
+// overwritten that parity buffer).
+// ======================================================================
+__global__ void __launch_bounds__(KT) k_scatter_alpha(LayoutView L, TokenView T, WorkView W, WaveState S,
+                                                      int32_t t_bwd) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t tag_base = *S.epoch + S.tok0;
+  const int64_t nw = warps_total();
+  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
+    const ItemCtx c = resolve(W, item);
+    const WinCtx x = load_win(L, c.sym, c.wslice, lane);
+    if (!x.h) {
+      // nothing starts in this lane; the loop below is empty
+    }
+    for (int j = 0; j < c.cnt; ++j) {
+      const int32_t p = token_of(W, c, j);
+      const int32_t b = T.b[p], t = T.t[p];
+      if (S.bw_n[b] <= t_bwd) continue;  // this string's frontier was not overwritten
+      const int64_t cb = T.cbase[p];
+      unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
+      const uint32_t tag = tag_base + (uint32_t)p;
+      int cum = x.hb;
+#pragma unroll
+      for (int k = 0; k < APL; ++k) {
+        if ((x.h >> k) & 1u) {
+          const int32_t s = x.meta.seg + cum;
+          const float r = S.rc[cb + (s - x.segbase)];
+          if (r != neg_inf()) aout[L.seg_state[s]] = tagged_make(r, tag);
+          ++cum;
+        }
+      }
+    }
+  }
+}
+
+// ======================================================================
+// Backward step fused with the expected counts (Alg. 2 backward loop and
+// count loop; Sec. 5.2).  Segments are by source state.
+// ======================================================================
+__global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, WorkView W, WaveState S,
+                                                 CountView C) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t tag_base = *S.epoch + S.tok0;
+  const int64_t nw = warps_total();
+  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
+    const ItemCtx c = resolve(W, item);
+    const WinCtx x = load_win(L, c.sym, c.wslice, lane);
+    const int64_t base = x.w * WIN + lane * APL;
+    const int4 d4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
+    const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
+    const int32_t dst[APL] = {d4.x, d4.y, d4.z, d4.w};
+    const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
+    const bool is_long = x.meta.lseg >= 0;
+    const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
+    // segment (source state) of each arc
+    int32_t qs[APL];
+    {
+      int cum = x.hb;
+#pragma unroll
+      for (int k = 0; k < APL; ++k) {
+        cum += (x.h >> k) & 1u;
+        const int32_t s = is_long ? x.meta.seg : x.meta.seg + cum - 1;
+        qs[k] = (th[k] == neg_inf()) ? 0 : __ldg(L.seg_state + s);
+      }
+    }
+    double gacc[APL] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < c.cnt; ++j) {
+      const int32_t p = token_of(W, c, j);
+      const int32_t b = T.b[p], t = T.t[p];
+      const double lz = S.logz[b];
+      if (lz == -INFINITY) continue;
+      const int32_t n = S.bw_n[b];
+      // beta_t at the destinations
+      float bv[APL];
+      double Et;
+      if (t == n) {
+#pragma unroll
+        for (int k = 0; k < APL; ++k) bv[k] = __ldg(S.theta_f + dst[k]);
+        Et = 0.0;
+      } else {
+        const float et = decode_max(S.ekey[p]);
+        const unsigned long long* bb = S.beta + ((int64_t)b * 2 + (t & 1)) * S.Q;
+        const uint32_t tg = tag_base + (uint32_t)p;
+#pragma unroll
+        for (int k = 0; k < APL; ++k) {
+          const float u = tagged_value(__ldg(bb + dst[k]), tg);
+          bv[k] = (u == neg_inf() || et == neg_inf()) ? neg_inf() : u - et;
+        }
+        Et = S.esum[p + 1] + (double)et;
+      }
+      if (c.wslice == 0 && lane == 0) S.esum[p] = Et;
+      float v[APL];
+#pragma unroll
+      for (int k = 0; k < APL; ++k) v[k] = th[k] + bv[k];
+      // beta_{t-1} by source segment (not needed for t == 1)
+      if (t >= 2) {
+        float2 e[APL];
+#pragma unroll
+        for (int k = 0; k < APL; ++k) e[k] = (v[k] == neg_inf()) ? LogAdd::identity() : make_float2(v[k], 1.f);
+        float2 full[APL];
+        window_scan<LogAdd>(e, x.h, lane, full);
+        unsigned long long* bout = S.beta + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+        const uint32_t tag = tag_base + (uint32_t)(p - 1);
+        float umax = neg_inf();
+        if (!is_long) {
+          int cum = x.hb;
+#pragma unroll
+          for (int k = 0; k < APL; ++k) {
+            cum += (x.h >> k) & 1u;
+            const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
+            if (tail) {
+              const int32_t s = x.meta.seg + cum - 1;
+              const float u = lse_value(full[k]);
+              if (u != neg_inf()) bout[L.seg_state[s]] = tagged_make(u, tag);
+              umax = fmaxf(umax, u);
+            }
+          }
+        } else {
+          float2 tot;
+          if (long_lse_arrive(L, S, x, T.lbase_b[p], T.lwbase_b[p], full[APL - 1], lane, tot)) {
+            const float u = lse_value(tot);
+            if (lane == 0 && u != neg_inf()) bout[L.seg_state[x.meta.seg]] = tagged_make(u, tag);
+            umax = u;
+          }
+        }
+        umax = warp_max(umax);
+        if (lane == 0 && umax != neg_inf()) atomicMax(S.ekey + p - 1, fkey(umax));
+      }
+      // posteriors gamma_t(k) = exp(alpha_{t-1}[src] + theta_k + beta_t[dst] - log Z)
+      const double Ctm1 = (t == 1) ? 0.0 : S.csum[p - 1];
+      const float K = (float)(Ctm1 + Et - lz);
+      const float mprev = (t == 1) ? 0.f : decode_max(S.mkey[p - 1]);
+      const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+      const uint32_t tga = tag_base + (uint32_t)(p - 1);
+      const float gw = S.gweight ? S.gweight[b] : 1.f;
+#pragma unroll
+      for (int k = 0; k < APL; ++k) {
+        if (v[k] == neg_inf()) continue;
+        float ah;
+        if (t == 1) {
+          ah = __ldg(S.theta_s + qs[k]);
+        } else {
+          const float r = tagged_value(__ldg(ab + qs[k]), tga);
+          ah = (r == neg_inf() || mprev == neg_inf()) ? neg_inf() : r - mprev;
+        }
+        if (ah == neg_inf()) continue;
+        const float g = expf(ah + v[k] + K);
+        gacc[k] += (double)g * (double)gw;
+      }
+    }
+    // accumulate this item's counts
+#pragma unroll
+    for (int k = 0; k < APL; ++k) {
+      if (gacc[k] == 0.0) continue;
+      const int64_t pos = base + k;
+      if (C.batched) {
+        atomicAdd(C.cnt64 + pos, gacc[k]);
+      } else {
+        // compensated float32 summation (one string: no concurrent writer)
+        const float gv = (float)gacc[k];
+        const float s0 = C.cnt[pos], cmp = C.comp[pos];
+        const float y = __fsub_rn(gv, cmp);
+        const float s1 = __fadd_rn(s0, y);
+        C.comp[pos] = __fsub_rn(__fsub_rn(s1, s0), y);
+        C.cnt[pos] = s1;
+      }
+    }
+  }
+}
+
+// ======================================================================
+// Epilogues: final reduction (Alg. 1 return line; Alg. 2 Z), backtrace
+// (Sec. 5.1), and counts back to caller arc order.
+// ======================================================================
+__global__ void k_vit_final(LayoutView L, const int32_t* __restrict__ tok_sym, const int64_t* __restrict__ cbase,
+                            WaveState S, int32_t Bw, float* __restrict__ scores, int32_t* __restrict__ qfinal,
+                            int32_t* __restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t tag_base = *S.epoch + S.tok0;
+  const int64_t b = warp_id_global();
+  if (b >= Bw) return;
+  const int32_t n = S.bw_n[b];
+  unsigned long long best = 0ull;
+  if (n == 0) {
+    for (int32_t q = lane; q < S.Q; q += 32) {
+      const float cnd = __fadd_rn(S.theta_s[q], S.theta_f[q]);
+      if (cnd != neg_inf()) {
+        const unsigned long long k = ((unsigned long long)fkey(cnd) << 32) | (unsigned long long)(~(uint32_t)q);
+        best = k > best ? k : best;
+      }
+    }
+  } else {
+    const int64_t p = S.bw_off[b] + n - 1;
+    const int32_t sym = tok_sym[p];
+    const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + (n & 1)) * S.Q;
+    const uint32_t tg = tag_base + (uint32_t)p;
+    for (int64_t s = L.sym_seg[sym] + lane; s < L.sym_seg[sym + 1]; s += 32) {
+      const int32_t q = L.seg_state[s];
+      const float cnd = __fadd_rn(tagged_value(ab[q], tg), S.theta_f[q]);
+      if (cnd != neg_inf()) {
+        const unsigned long long k = ((unsigned long long)fkey(cnd) << 32) | (unsigned long long)(~(uint32_t)q);
+        best = k > best ? k : best;
+      }
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(FULL, best, d);
+    best = o > best ? o : best;
+  }
+  if (lane == 0) {
+    scores[b] = best ? fkey_inv((uint32_t)(best >> 32)) : neg_inf();
+    qfinal[b] = best ? (int32_t)(~(uint32_t)best) : -1;
+    if (status) status[b] = best ? FST_OK : FST_ERR_NO_PATH;
+  }
+}
+
+// One warp per string; a 32-way search finds the state's segment at each step.
+__global__ void k_backtrace(LayoutView L, const int32_t* __restrict__ tok_sym, const int64_t* __restrict__ cbase,
+                            WaveState S, const int32_t* __restrict__ olabel_by_id,
+                            const int32_t* __restrict__ arc_id, int32_t Bw, const int32_t* __restrict__ qfinal,
+                            int32_t* __restrict__ paths, int32_t* __restrict__ olabels) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = warp_id_global();
+  if (b >= Bw) return;
+  const int32_t n = S.bw_n[b];
+  const int64_t off = S.bw_off[b];
+  int32_t q = qfinal[b];
+  if (q < 0) {
+    for (int32_t t = lane; t < n; t += 32) {
+      paths[off + t] = -1;
+      if (olabels) olabels[off + t] = -1;
+    }
+    return;
+  }
+  for (int32_t t = n; t >= 1; --t) {
+    const int64_t p = off + t - 1;
+    const int32_t sym = tok_sym[p];
+    int64_t lo = L.sym_seg[sym], hi = L.sym_seg[sym + 1];
+    while (hi - lo > 32) {
+      const int64_t step = (hi - lo + 31) / 32;
+      const int64_t i = lo + (int64_t)lane * step;
+      const bool le = (i < hi) && (L.seg_state[i] <= q);
+      const uint32_t bal = __ballot_sync(FULL, le);
+      const int last = bal ? 31 - __clz(bal) : 0;
+      lo = lo + (int64_t)last * step;
+      hi = min(hi, lo + step);
+    }
+    const int64_t i = lo + lane;
+    const uint32_t bal = __ballot_sync(FULL, (i < hi) && (L.seg_state[i] == q));
+    int32_t pos = -1;
+    if (bal) {
+      const int64_t s = lo + (__ffs(bal) - 1);
+      pos = S.bp[cbase[p] + (s - L.sym_seg[sym])];
+    }
+    if (pos < 0) {  // cannot happen for a live state; leave a marker instead of faulting
+      if (lane == 0) paths[p] = -1;
+      break;
+    }
+    const int32_t k = arc_id[pos];
+    if (lane == 0) {
+      paths[p] = k;
+      if (olabels) olabels[p] = olabel_by_id[k];
+    }
+    q = L.other[pos];
+  }
+}
+
+__global__ void k_fb_final(LayoutView L, const int32_t* __restrict__ tok_sym, const int64_t* __restrict__ cbase,
+                           WaveState S, int32_t Bw, double* __restrict__ logz, int32_t* __restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = warp_id_global();
+  if (b >= Bw) return;
+  const int32_t n = S.bw_n[b];
+  const int64_t off = S.bw_off[b];
+  // running normaliser C_t = sum_{s<=t} m_s, float64
+  double Cprev = 0.0;
+  if (lane == 0) {
+    double Cs = 0.0;
+    for (int32_t t = 1; t <= n; ++t) {
+      const float m = decode_max(S.mkey[off + t - 1]);
+      Cs = (m == neg_inf()) ? -INFINITY : Cs + (double)m;
+      S.csum[off + t - 1] = Cs;
+      if (t == n - 1) Cprev = Cs;
+    }
+  }
+  Cprev = __shfl_sync(FULL, Cprev, 0);
+  double mx = -INFINITY;
+  // two passes over the final candidates: max, then sum of exp
+  if (n == 0) {
+    for (int32_t q = lane; q < S.Q; q += 32) mx = fmax(mx, (double)S.theta_s[q] + (double)S.theta_f[q]);
+  } else {
+    const int64_t p = off + n - 1;
+    const int32_t sym = tok_sym[p];
+    for (int64_t s = L.sym_seg[sym] + lane; s < L.sym_seg[sym + 1]; s += 32) {
+      const int32_t q = L.seg_state[s];
+      mx = fmax(mx, (double)S.rc[cbase[p] + (s - L.sym_seg[sym])] + (double)S.theta_f[q]);
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, d));
+  double sum = 0.0;
+  if (mx != -INFINITY) {
+    if (n == 0) {
+      for (int32_t q = lane; q < S.Q; q += 32) {
+        const double v = (double)S.theta_s[q] + (double)S.theta_f[q];
+        if (v != -INFINITY) sum += exp(v - mx);
+      }
+    } else {
+      const int64_t p = off + n - 1;
+      const int32_t sym = tok_sym[p];
+      for (int64_t s = L.sym_seg[sym] + lane; s < L.sym_seg[sym + 1]; s += 32) {
+        const int32_t q = L.seg_state[s];
+        const double v = (double)S.rc[cbase[p] + (s - L.sym_seg[sym])] + (double)S.theta_f[q];
+        if (v != -INFINITY) sum += exp(v - mx);
+      }
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) sum += __shfl_xor_sync(FULL, sum, d);
+  if (lane == 0) {
+    double lz = -INFINITY;
+    if (mx != -INFINITY && Cprev != -INFINITY) lz = Cprev + mx + log(sum);
+    logz[b] = lz;
+    if (status) status[b] = (lz == -INFINITY) ? FST_ERR_NO_PATH : FST_OK;
+  }
+}
+
+__global__ void k_counts_out(const int32_t* __restrict__ arc_id, int64_t P, CountView C, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const int32_t k = arc_id[i];
+  if (k < 0) return;
+  out[k] = C.batched ? (float)C.cnt64[i] : __fsub_rn(C.cnt[i], C.comp[i]);
+}
+
+inline int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return FST_OK;
+}
+
+inline unsigned grid_clamp(int64_t nitems, int grid) {
+  int64_t need = (nitems + (KT / 32) - 1) / (KT / 32);
+  if (need < 1) need = 1;
+  return (unsigned)(need < grid ? need : grid);
+}
+
+}  // namespace
+
+int launch_vit_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S, int grid,
+                    cudaStream_t s) {
+  if (W.nitems <= 0) return FST_OK;
+  k_vit_step<<<grid_clamp(W.nitems, grid), KT, 0, s>>>(L, T, W, S);
+  return check_launch("k_vit_step");
+}
+
+int launch_fwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S, int grid,
+                    cudaStream_t s) {
+  if (W.nitems <= 0) return FST_OK;
+  k_fwd_step<<<grid_clamp(W.nitems, grid), KT, 0, s>>>(L, T, W, S);
+  return check_launch("k_fwd_step");
+}
+
+int launch_bwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
+                    const CountView& C, int grid, cudaStream_t s) {
+  if (W.nitems <= 0) return FST_OK;
+  k_bwd_step<<<grid_clamp(W.nitems, grid), KT, 0, s>>>(L, T, W, S, C);
+  return check_launch("k_bwd_step");
+}
+
+int launch_scatter_alpha(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
+                         int32_t t_bwd, int grid, cudaStream_t s) {
+  if (W.nitems <= 0) return FST_OK;
+  k_scatter_alpha<<<grid_clamp(W.nitems, grid), KT, 0, s>>>(L, T, W, S, t_bwd);
+  return check_launch("k_scatter_alpha");
+}
+
+int launch_vit_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
+                     int32_t Bw, float* scores, int32_t* qfinal, int32_t* status, cudaStream_t s) {
+  if (Bw <= 0) return FST_OK;
+  k_vit_final<<<(unsigned)((Bw + 7) / 8), 256, 0, s>>>(Lf, tok_sym, cbase, S, Bw, scores, qfinal, status);
+  return check_launch("k_vit_final");
+}
+
+int launch_backtrace(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
+                     const int32_t* olabel_by_id, const int32_t* arc_id_fwd, int32_t Bw, const int32_t* qfinal,
+                     int32_t* paths, int32_t* olabels, cudaStream_t s) {
+  if (Bw <= 0) return FST_OK;
+  k_backtrace<<<(unsigned)((Bw + 3) / 4), 128, 0, s>>>(Lf, tok_sym, cbase, S, olabel_by_id, arc_id_fwd, Bw,
+                                                       qfinal, paths, olabels);
+  return check_launch("k_backtrace");
+}
+
+int launch_fb_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
+                    int32_t Bw, double* logz, int32_t* status, cudaStream_t s) {
+  if (Bw <= 0) return FST_OK;
+  k_fb_final<<<(unsigned)((Bw + 7) / 8), 256, 0, s>>>(Lf, tok_sym, cbase, S, Bw, logz, status);
+  return check_launch("k_fb_final");
+}
+
+int launch_counts_out(const int32_t* arc_id_bwd, int64_t P, const CountView& C, float* out, cudaStream_t s) {
+  if (P <= 0) return FST_OK;
+  k_counts_out<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(arc_id_bwd, P, C, out);
+  return check_launch("k_counts_out");
+}
+
+}  // namespace fstgpu

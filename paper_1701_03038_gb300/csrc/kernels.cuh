@@ -1,0 +1,100 @@
+// kernels.cuh -- launch arguments of the relaxation kernels (kernels.cu).
+#pragma once
+
+#include <stdint.h>
+
+#include "fst_internal.cuh"
+
+namespace fstgpu {
+
+// Device view of one arc layout.
+struct LayoutView {
+  const int32_t* other;
+  const float* theta;
+  const double* theta64;
+  const WinMeta* win;
+  const int32_t* seg_state;
+  const int32_t* seg_pos;
+  const int64_t* sym_win;
+  const int64_t* sym_seg;
+};
+
+inline LayoutView view_of(const Layout& L) {
+  return LayoutView{L.other, L.theta, L.theta64, L.win, L.seg_state, L.seg_pos, L.sym_win, L.sym_seg};
+}
+
+// Tokens of one wave: token p is position t (1-based) of wave-local string b.
+struct TokenView {
+  const int32_t* sym;
+  const int32_t* b;
+  const int32_t* t;
+  const int64_t* cbase;   // base of the token's per-segment storage (forward segments)
+  const int64_t* lbase;     // long-segment scratch slots (forward layout)
+  const int64_t* lbase_b;   // long-segment scratch slots (backward layout)
+  const int64_t* lwbase;    // long-window scratch slots (forward layout)
+  const int64_t* lwbase_b;  // long-window scratch slots (backward layout)
+};
+
+// Work list of one step: items are (group, window-of-slice) pairs; a group
+// is up to GMAX tokens of the same step with the same symbol.
+struct WorkView {
+  int single;        // 1: one token (p0, sym0); the group arrays are unused
+  int32_t p0, sym0;
+  int32_t g0, g1;    // group range of this step
+  int64_t nitems;
+  const int32_t* grp_first;
+  const int32_t* grp_cnt;
+  const int32_t* grp_sym;
+  const int64_t* grp_item;  // item offset of each group inside its step (this layout)
+  const int32_t* sorted_tok;
+};
+
+// Per-wave state shared by the passes.
+struct WaveState {
+  int32_t Q;
+  const uint32_t* epoch;             // device: tags of this run start at *epoch
+  uint32_t tok0;                     // first global token of the wave: token p writes *epoch + tok0 + p
+  unsigned long long* alpha;         // [Bw][2][Q] tagged frontier
+  unsigned long long* beta;          // [Bw][2][Q]
+  int32_t* bp;                       // compact backpointers (forward segments)
+  float* rc;                         // compact forward values r_t (forward segments)
+  uint32_t* mkey;                    // [N] forward step maxima (order keys)
+  uint32_t* ekey;                    // [N] backward step maxima
+  double* csum;                      // [N] C_t = sum_{s<=t} m_s
+  double* esum;                      // [N] E_t
+  unsigned long long* skey;          // long-segment max keys
+  uint32_t* scnt;                    // long-segment arrival counters
+  float2* spart;                     // long-window (max, sum) partials
+  const float* theta_s;
+  const float* theta_f;
+  const double* logz;                // [Bw] (wave-local view)
+  const float* gweight;              // [Bw] or null
+  int32_t* bw_n;                     // [Bw] string lengths
+  int64_t* bw_off;                   // [Bw] first token of each wave string
+};
+
+struct CountView {
+  int batched;        // 0: Kahan float pair per arc; 1: double atomics
+  float* cnt;         // [P_bwd]
+  float* comp;        // [P_bwd]
+  double* cnt64;      // [P_bwd]
+};
+
+int launch_vit_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
+                    int grid, cudaStream_t s);
+int launch_fwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
+                    int grid, cudaStream_t s);
+int launch_bwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
+                    const CountView& C, int grid, cudaStream_t s);
+int launch_scatter_alpha(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
+                         int32_t t_bwd, int grid, cudaStream_t s);
+int launch_vit_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
+                     int32_t Bw, float* scores, int32_t* qfinal, int32_t* status, cudaStream_t s);
+int launch_backtrace(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
+                     const int32_t* olabel_by_id, const int32_t* arc_id_fwd, int32_t Bw,
+                     const int32_t* qfinal, int32_t* paths, int32_t* olabels, cudaStream_t s);
+int launch_fb_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
+                    int32_t Bw, double* logz, int32_t* status, cudaStream_t s);
+int launch_counts_out(const int32_t* arc_id_bwd, int64_t P, const CountView& C, float* out, cudaStream_t s);
+
+}  // namespace fstgpu

@@ -1,0 +1,268 @@
+"""Python front end of libfstgpu: FST handles, single-string calls and batch
+plans.  Argument marshalling only -- every step runs in the CUDA library;
+PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+__all__ = ["Fst", "Plan"]
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def _hptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _dptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Fst:
+    """An epsilon-free weighted FST resident on one GPU.
+
+    Arrays are given in the caller's arc order; weights are costs
+    (``weight_kind="cost"``, w = -log p) or log-weights (``"log"``).  Host
+    numpy arrays or CUDA tensors are accepted (all of one kind).
+    """
+
+    def __init__(self, num_states, src, dst, ilabel, olabel, weight, start_weight, final_weight,
+                 num_isyms, weight_kind: str = "cost", device=None):
+        self._lib = _lib.load()
+        self._h = None
+        kind = {"cost": _lib.WEIGHT_COST, "log": _lib.WEIGHT_LOG}[weight_kind]
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        on_device = isinstance(src, torch.Tensor)
+        h = C.c_void_p()
+        with torch.cuda.device(dev):
+            if on_device:
+                arrs = [src, dst, ilabel, olabel, weight, start_weight, final_weight]
+                dts = [torch.int32] * 4 + [torch.float32] * 3
+                arrs = [a.to(device=dev, dtype=d).contiguous() for a, d in zip(arrs, dts)]
+                keep = arrs
+                ptrs = [_dptr(a) for a in arrs]
+                flags = _lib.FLAG_DEVICE_PTRS
+                na = int(arrs[0].numel())
+            else:
+                arrs = [_host(src, np.int32), _host(dst, np.int32), _host(ilabel, np.int32),
+                        _host(olabel, np.int32), _host(weight, np.float32),
+                        _host(start_weight, np.float32), _host(final_weight, np.float32)]
+                keep = arrs
+                ptrs = [_hptr(a) for a in arrs]
+                flags = 0
+                na = int(arrs[0].shape[0])
+            rc = self._lib.fst_create(int(num_states), na, ptrs[0], ptrs[1], ptrs[2], ptrs[3], ptrs[4],
+                                      kind, ptrs[5], ptrs[6], int(num_isyms), flags, C.byref(h))
+            del keep
+            check(rc, "fst_create")
+        self._h = h
+        self.num_states = int(num_states)
+        self.num_arcs = na
+        self.num_isyms = int(num_isyms)
+
+    @classmethod
+    def from_arrays(cls, fa, device=None) -> "Fst":
+        """Build from a ``synth.FstArrays`` (cost-domain weights)."""
+        return cls(fa.num_states, fa.src, fa.dst, fa.ilabel, fa.olabel, fa.weight, fa.start_weight,
+                   fa.final_weight, fa.num_isyms, weight_kind="cost", device=device)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            self._lib.fst_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ------------------------------------------------------------ queries
+    def info(self) -> dict:
+        q, m = C.c_int32(), C.c_int32()
+        a, p, w, ds, ss = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        check(self._lib.fst_info(self._h, C.byref(q), C.byref(a), C.byref(m), C.byref(p), C.byref(w),
+                                 C.byref(ds), C.byref(ss)), "fst_info")
+        return dict(num_states=q.value, num_arcs=a.value, num_isyms=m.value, padded_arcs=p.value,
+                    windows=w.value, dst_segments=ds.value, src_segments=ss.value)
+
+    def symbol_stats(self):
+        """(|delta[a]|, D_a distinct destinations, U_a distinct sources) per symbol."""
+        arcs = np.zeros(self.num_isyms, np.int64)
+        dsts = np.zeros(self.num_isyms, np.int64)
+        srcs = np.zeros(self.num_isyms, np.int64)
+        check(self._lib.fst_symbol_stats(self._h, _hptr(arcs), _hptr(dsts), _hptr(srcs)), "fst_symbol_stats")
+        return arcs, dsts, srcs
+
+    def set_weights(self, weight, weight_kind: str = "cost"):
+        kind = {"cost": _lib.WEIGHT_COST, "log": _lib.WEIGHT_LOG}[weight_kind]
+        if isinstance(weight, torch.Tensor):
+            w = weight.detach().to(device=self.device, dtype=torch.float32).contiguous()
+            with torch.cuda.device(self.device):
+                torch.cuda.current_stream().synchronize()
+                check(self._lib.fst_set_weights(self._h, _dptr(w), kind, _lib.FLAG_DEVICE_PTRS),
+                      "fst_set_weights")
+        else:
+            w = _host(weight, np.float32)
+            with torch.cuda.device(self.device):
+                check(self._lib.fst_set_weights(self._h, _hptr(w), kind, 0), "fst_set_weights")
+
+    # ------------------------------------------------- plain method (one string)
+    def viterbi(self, ids):
+        """Best path of one string: (score float32, arc ids int32[n], output
+        labels int32[n], status).  Status NO_PATH means no accepting path."""
+        x = _host(ids, np.int32)
+        n = int(x.shape[0])
+        best = np.zeros(1, np.float32)
+        path = np.zeros(max(n, 1), np.int32)
+        olab = np.zeros(max(n, 1), np.int32)
+        with torch.cuda.device(self.device):
+            rc = self._lib.fst_viterbi(self._h, _hptr(x), n, _hptr(best), _hptr(path), _hptr(olab))
+        check(rc, "fst_viterbi", allow=(_lib.OK, _lib.NO_PATH))
+        return best[0], path[:n], olab[:n], rc
+
+    def forward_backward(self, ids, posteriors: bool = True):
+        """(log Z float64, expected arc counts float32[A] or None, status)."""
+        x = _host(ids, np.int32)
+        n = int(x.shape[0])
+        lz = np.zeros(1, np.float64)
+        cnt = np.zeros(max(self.num_arcs, 1), np.float32) if posteriors else None
+        with torch.cuda.device(self.device):
+            rc = self._lib.fst_forward_backward(self._h, _hptr(x), n, _hptr(lz),
+                                                _hptr(cnt) if posteriors else None)
+        check(rc, "fst_forward_backward", allow=(_lib.OK, _lib.NO_PATH))
+        return float(lz[0]), (cnt[:self.num_arcs] if posteriors else None), rc
+
+    # ------------------------------------------------------ batched method
+    def plan(self, ids: torch.Tensor, offsets: torch.Tensor, mem_budget: int = 0, flags: int = 0,
+             stream=None) -> "Plan":
+        return Plan(self, ids, offsets, mem_budget=mem_budget, flags=flags, stream=stream)
+
+    def viterbi_batch(self, ids: torch.Tensor, offsets: torch.Tensor, stream=None):
+        _require_cuda(ids, torch.int32, "ids")
+        _require_cuda(offsets, torch.int64, "offsets")
+        B = int(offsets.numel()) - 1
+        scores = torch.empty(max(B, 1), dtype=torch.float32, device=ids.device)
+        paths = torch.empty(max(int(ids.numel()), 1), dtype=torch.int32, device=ids.device)
+        olab = torch.empty_like(paths)
+        status = torch.empty(max(B, 1), dtype=torch.int32, device=ids.device)
+        with torch.cuda.device(self.device):
+            check(self._lib.fst_viterbi_batch(self._h, _dptr(ids), _dptr(offsets), B, _dptr(scores),
+                                              _dptr(paths), _dptr(olab), _dptr(status), _stream(stream)),
+                  "fst_viterbi_batch")
+        n = int(ids.numel())
+        return dict(scores=scores[:B], paths=paths[:n], olabels=olab[:n], status=status[:B])
+
+    def forward_backward_batch(self, ids: torch.Tensor, offsets: torch.Tensor, weights=None,
+                               counts: bool = True, stream=None):
+        _require_cuda(ids, torch.int32, "ids")
+        _require_cuda(offsets, torch.int64, "offsets")
+        B = int(offsets.numel()) - 1
+        logz = torch.empty(max(B, 1), dtype=torch.float64, device=ids.device)
+        status = torch.empty(max(B, 1), dtype=torch.int32, device=ids.device)
+        cnt = torch.empty(max(self.num_arcs, 1), dtype=torch.float32, device=ids.device) if counts else None
+        if weights is not None:
+            _require_cuda(weights, torch.float32, "weights")
+        with torch.cuda.device(self.device):
+            check(self._lib.fst_forward_backward_batch(self._h, _dptr(ids), _dptr(offsets), B, _dptr(weights),
+                                                       _dptr(logz), _dptr(cnt), _dptr(status), _stream(stream)),
+                  "fst_forward_backward_batch")
+        return dict(logz=logz[:B], counts=None if cnt is None else cnt[:self.num_arcs], status=status[:B])
+
+
+class Plan:
+    """Device work lists and storage for one batch (see fst_plan_create).
+    Run calls allocate nothing and are safe to capture in a CUDA graph."""
+
+    def __init__(self, fst: Fst, ids: torch.Tensor, offsets: torch.Tensor, mem_budget: int = 0,
+                 flags: int = 0, stream=None):
+        _require_cuda(ids, torch.int32, "ids")
+        _require_cuda(offsets, torch.int64, "offsets")
+        self.fst = fst
+        self._lib = fst._lib
+        self._h = None
+        h = C.c_void_p()
+        self.B = int(offsets.numel()) - 1
+        self.N = int(ids.numel())
+        with torch.cuda.device(fst.device):
+            check(self._lib.fst_plan_create(fst.handle, _dptr(ids), _dptr(offsets), self.B, int(mem_budget),
+                                            int(flags), _stream(stream), C.byref(h)), "fst_plan_create")
+        self._h = h
+        dev = fst.device
+        self.scores = torch.empty(max(self.B, 1), dtype=torch.float32, device=dev)
+        self.paths = torch.empty(max(self.N, 1), dtype=torch.int32, device=dev)
+        self.olabels = torch.empty(max(self.N, 1), dtype=torch.int32, device=dev)
+        self.status = torch.empty(max(self.B, 1), dtype=torch.int32, device=dev)
+        self.logz = torch.empty(max(self.B, 1), dtype=torch.float64, device=dev)
+        self.counts = torch.empty(max(fst.num_arcs, 1), dtype=torch.float32, device=dev)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            self._lib.fst_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        b, w, ml = C.c_int32(), C.c_int32(), C.c_int32()
+        n, r, vl, fl, by = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        check(self._lib.fst_plan_info(self._h, C.byref(b), C.byref(n), C.byref(w), C.byref(ml), C.byref(r),
+                                      C.byref(vl), C.byref(fl), C.byref(by)), "fst_plan_info")
+        return dict(strings=b.value, tokens=n.value, waves=w.value, max_len=ml.value, relaxations=r.value,
+                    viterbi_launches=vl.value, fb_launches=fl.value, device_bytes=by.value)
+
+    def viterbi(self, stream=None):
+        """Queue Viterbi for every string; results land in self.scores /
+        self.paths / self.olabels / self.status."""
+        check(self._lib.fst_plan_viterbi(self._h, _dptr(self.scores), _dptr(self.paths), _dptr(self.olabels),
+                                         _dptr(self.status), _stream(stream)), "fst_plan_viterbi")
+
+    def forward(self, stream=None):
+        check(self._lib.fst_plan_forward(self._h, _dptr(self.logz), _dptr(self.status), _stream(stream)),
+              "fst_plan_forward")
+
+    def backward(self, weights: torch.Tensor | None = None, stream=None):
+        if weights is not None:
+            _require_cuda(weights, torch.float32, "weights")
+        check(self._lib.fst_plan_backward(self._h, _dptr(weights), _dptr(self.counts), _stream(stream)),
+              "fst_plan_backward")
+
+    def forward_backward(self, weights: torch.Tensor | None = None, counts: bool = True, stream=None):
+        if weights is not None:
+            _require_cuda(weights, torch.float32, "weights")
+        check(self._lib.fst_plan_forward_backward(self._h, _dptr(weights), _dptr(self.logz),
+                                                  _dptr(self.counts) if counts else None, _dptr(self.status),
+                                                  _stream(stream)), "fst_plan_forward_backward")

@@ -1,0 +1,65 @@
+"""The C-ABI library builds and exports every entry point of include/*.h
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import glob
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_1701_03038_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        names |= set(re.findall(r"FST_API\s+(?:const\s+)?\w+\s*\*?\s*(fst_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    return build.build()
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    assert {"fst_create", "fst_destroy", "fst_viterbi", "fst_forward_backward", "fst_viterbi_batch",
+            "fst_forward_backward_batch", "fst_last_error"} <= names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in sorted(declared_symbols()):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_binding_covers_every_declared_symbol():
+    names = declared_symbols()
+    bound = set(_lib.SIGNATURES) | {"fst_last_error"}
+    assert names <= bound, names - bound
+
+
+def test_library_does_not_link_libtorch(libpath):
+    data = open(libpath, "rb").read()
+    assert b"libtorch" not in data and b"libc10" not in data
+
+
+def test_last_error_callable_without_gpu(libpath):
+    lib = _lib.load()
+    assert lib.fst_last_error() is not None
+
+
+def test_invalid_args_rejected_without_gpu(libpath):
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    # Q = 0 is rejected before any CUDA call
+    rc = lib.fst_create(0, 0, None, None, None, None, None, 0, None, None, 1, 0, ctypes.byref(out))
+    assert rc == _lib.INVALID_ARG and not out.value
+    assert b"bad sizes" in lib.fst_last_error()

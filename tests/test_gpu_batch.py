@@ -1,0 +1,185 @@
+"""Batched method (plans: all strings advanced together) against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1701_03038_gb300 import synth
+
+from gpu_util import assert_counts_close, assert_logz_close, assert_viterbi_equal, ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _dev(strs):
+    import torch
+    return torch.from_numpy(strs.ids).cuda(), torch.from_numpy(strs.offsets).cuda()
+
+
+def check_batch_viterbi(o, strs, res):
+    sc = res["scores"].cpu().numpy()
+    pa = res["paths"].cpu().numpy()
+    ol = res["olabels"].cpu().numpy()
+    st = res["status"].cpu().numpy()
+    ob = o.viterbi_batch(strs.ids, strs.offsets, nthreads=8)
+    for b in range(strs.count):
+        lo, hi = strs.offsets[b], strs.offsets[b + 1]
+        ov = o.viterbi(strs.get(b))
+        assert_viterbi_equal(sc[b], pa[lo:hi], ol[lo:hi], st[b], ov)
+        assert sc[b] == ob["best"][b] or (math.isinf(sc[b]) and sc[b] == ob["best"][b])
+
+
+def check_batch_fb(o, strs, logz, counts, weights=None):
+    ob = o.fb_batch(strs.ids, strs.offsets, nthreads=8, weights=weights)
+    lz = logz.cpu().numpy()
+    for b in range(strs.count):
+        assert_logz_close(lz[b], ob["logz"][b])
+    if counts is not None:
+        assert_counts_close(counts.cpu().numpy(), ob["counts"], batch=True)
+
+
+@pytest.fixture(scope="module")
+def c2s():
+    from paper_1701_03038_gb300.fst import Fst
+    fa, strs = synth.make_config("c2", scale=0.02, strings=60)
+    return Fst.from_arrays(fa), oracle.Fst(fa), strs
+
+
+def test_viterbi_batch(c2s):
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    check_batch_viterbi(o, strs, f.viterbi_batch(ids, off))
+
+
+def test_forward_backward_batch(c2s):
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    r = f.forward_backward_batch(ids, off)
+    check_batch_fb(o, strs, r["logz"], r["counts"])
+
+
+def test_waves_match_single_wave(c2s):
+    import torch
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    p1 = f.plan(ids, off)
+    p2 = f.plan(ids, off, mem_budget=1 << 20)  # forces many waves
+    assert p1.info()["waves"] == 1 and p2.info()["waves"] > 2
+    for p in (p1, p2):
+        p.viterbi()
+        p.forward_backward()
+    torch.cuda.synchronize()
+    assert torch.equal(p1.scores, p2.scores) and torch.equal(p1.paths, p2.paths)
+    assert torch.allclose(p1.logz, p2.logz, rtol=1e-12, atol=0)
+    check_batch_viterbi(o, strs, dict(scores=p2.scores[:strs.count], paths=p2.paths[:len(strs.ids)],
+                                      olabels=p2.olabels[:len(strs.ids)], status=p2.status[:strs.count]))
+    check_batch_fb(o, strs, p2.logz[:strs.count], p2.counts[:o.A])
+
+
+def test_plain_equals_batched(c2s):
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    r = f.viterbi_batch(ids, off)
+    for b in range(0, strs.count, 7):
+        s, p, _, _ = f.viterbi(strs.get(b))
+        assert s == r["scores"][b].item()
+        assert np.array_equal(p, r["paths"][strs.offsets[b]:strs.offsets[b + 1]].cpu().numpy())
+
+
+def test_long_segments_batched():
+    from paper_1701_03038_gb300.fst import Fst
+    rng = np.random.default_rng(21)
+    A, m = 4000, 2
+    il = rng.integers(0, m, size=A).astype(np.int32)
+    w = (rng.random(A) * 3).astype(np.float32)
+    fa = synth.FstArrays(1, m, 3, np.zeros(A, np.int32), np.zeros(A, np.int32), il,
+                         rng.integers(0, 3, size=A).astype(np.int32), w,
+                         np.zeros(1, np.float32), np.zeros(1, np.float32))
+    strs = synth.make_strings(fa, 40, 1, 25, seed=4)  # many tokens share a symbol: groups of GMAX
+    f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+    ids, off = _dev(strs)
+    check_batch_viterbi(o, strs, f.viterbi_batch(ids, off))
+    r = f.forward_backward_batch(ids, off)
+    check_batch_fb(o, strs, r["logz"], r["counts"])
+
+
+def test_split_forward_backward_weighted(c2s):
+    import torch
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    p = f.plan(ids, off, flags=1)  # single wave
+    w = torch.linspace(-1.0, 2.0, strs.count, dtype=torch.float32, device="cuda")
+    p.forward()
+    p.backward(w)
+    torch.cuda.synchronize()
+    check_batch_fb(o, strs, p.logz[:strs.count], p.counts[:o.A], weights=w.double().cpu().numpy())
+
+
+def test_graph_capture_and_replay_after_weight_change(c2s):
+    import torch
+    from paper_1701_03038_gb300.fst import Fst
+    _, _, strs = c2s
+    fa, _ = synth.make_config("c2", scale=0.02, strings=1)
+    f = Fst.from_arrays(fa)
+    ids, off = _dev(strs)
+    p = f.plan(ids, off)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p.viterbi(stream=s)
+        p.forward_backward(stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        p.viterbi(stream=s)
+        p.forward_backward(stream=s)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    o = oracle.Fst(fa)
+    check_batch_viterbi(o, strs, dict(scores=p.scores[:strs.count], paths=p.paths[:len(strs.ids)],
+                                      olabels=p.olabels[:len(strs.ids)], status=p.status[:strs.count]))
+    check_batch_fb(o, strs, p.logz[:strs.count], p.counts[:o.A])
+    # new weights, same graph: fresh frontier tags every replay keep results exact
+    rng = np.random.default_rng(8)
+    fa.weight = (fa.weight * rng.uniform(0.5, 1.5, size=fa.num_arcs)).astype(np.float32)
+    f.set_weights(fa.weight)
+    g.replay()
+    torch.cuda.synchronize()
+    o = oracle.Fst(fa)
+    check_batch_viterbi(o, strs, dict(scores=p.scores[:strs.count], paths=p.paths[:len(strs.ids)],
+                                      olabels=p.olabels[:len(strs.ids)], status=p.status[:strs.count]))
+    check_batch_fb(o, strs, p.logz[:strs.count], p.counts[:o.A])
+
+
+def test_empty_and_zero_length_strings():
+    import torch
+    from paper_1701_03038_gb300.fst import Fst
+    fa = synth.fig1_fst()
+    f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+    strs = synth.Strings(np.array([0, 1, 2, 0, 1, 2], np.int32), np.array([0, 0, 3, 3, 6, 6], np.int64))
+    ids, off = _dev(strs)
+    check_batch_viterbi(o, strs, f.viterbi_batch(ids, off))
+    r = f.forward_backward_batch(ids, off)
+    check_batch_fb(o, strs, r["logz"], r["counts"])
+    empty = f.viterbi_batch(torch.zeros(0, dtype=torch.int32, device="cuda"),
+                            torch.zeros(1, dtype=torch.int64, device="cuda"))
+    assert empty["scores"].numel() == 0
+
+
+def test_iid_strings_no_path_status():
+    from paper_1701_03038_gb300.fst import Fst
+    fa, _ = synth.make_config("c1", scale=0.2, strings=1)
+    strs = synth.make_strings(fa, 30, 10, 30, seed=5, kind="iid")
+    f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+    ids, off = _dev(strs)
+    r = f.viterbi_batch(ids, off)
+    check_batch_viterbi(o, strs, r)
+    assert (r["status"].cpu().numpy() == 2).any()
+    rf = f.forward_backward_batch(ids, off)
+    check_batch_fb(o, strs, rf["logz"], rf["counts"])

@@ -1,0 +1,172 @@
+"""Plain method (one string, one launch per position) against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1701_03038_gb300 import synth
+
+from gpu_util import assert_counts_close, assert_logz_close, assert_viterbi_equal, ensure_built
+import pins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _fst(fa):
+    from paper_1701_03038_gb300.fst import Fst
+    return Fst.from_arrays(fa)
+
+
+def check_string(f, o, x, fb=True):
+    s, p, ol, rc = f.viterbi(x)
+    assert_viterbi_equal(s, p, ol, rc, o.viterbi(x))
+    if fb:
+        lz, cnt, rc2 = f.forward_backward(x)
+        ofb = o.forward_backward(x)
+        assert rc2 == ofb["status"]
+        assert_logz_close(lz, ofb["logz"])
+        assert_counts_close(cnt, ofb["counts"])
+
+
+def test_fig1_worked_example():
+    fa, x, exp, exp_out, post = pins.fig1_case()
+    f = _fst(fa)
+    s, p, ol, rc = f.viterbi(x)
+    assert rc == 0 and list(p) == exp["viterbi_arcs"] and list(ol) == exp_out
+    assert s == np.float32(math.log(exp["viterbi_probability"]))
+    lz, cnt, _ = f.forward_backward(x)
+    assert abs(lz - math.log(exp["total_weight_Z"])) < 1e-6
+    assert np.allclose(cnt, post, atol=1e-6)
+
+
+def test_tiny_random_fsts():
+    rng = np.random.default_rng(123)
+    for _ in range(150):
+        fa = synth.tiny_fst(rng)
+        f, o = _fst(fa), oracle.Fst(fa)
+        for _ in range(2):
+            x = rng.integers(0, fa.num_isyms, size=int(rng.integers(0, 7))).astype(np.int32)
+            check_string(f, o, x)
+
+
+def test_c1_full_size():
+    fa, strs = synth.make_config("c1", strings=6)
+    f, o = _fst(fa), oracle.Fst(fa)
+    for b in range(strs.count):
+        check_string(f, o, strs.get(b))
+
+
+def test_single_state_long_segments():
+    # one state: every slice is one segment, far longer than a 128-arc window
+    rng = np.random.default_rng(5)
+    A, m = 5000, 3
+    il = rng.integers(0, m, size=A).astype(np.int32)
+    w = (rng.random(A) * 4).astype(np.float32)
+    fa = synth.FstArrays(1, m, 4, np.zeros(A, np.int32), np.zeros(A, np.int32), il,
+                         rng.integers(0, 4, size=A).astype(np.int32), w,
+                         np.zeros(1, np.float32), np.zeros(1, np.float32))
+    f, o = _fst(fa), oracle.Fst(fa)
+    for n in (1, 2, 7, 30):
+        check_string(f, o, rng.integers(0, m, size=n).astype(np.int32))
+
+
+def test_hub_states_mix_long_and_short_segments():
+    rng = np.random.default_rng(9)
+    q, m, A = 300, 4, 20000
+    src = rng.integers(0, q, size=A).astype(np.int32)
+    dst = rng.integers(0, q, size=A).astype(np.int32)
+    hub = rng.random(A) < 0.3
+    dst[hub] = rng.integers(0, 3, size=int(hub.sum()))   # three hub destinations
+    src[rng.random(A) < 0.2] = 7                          # a hub source (long backward segments)
+    il = rng.integers(0, m, size=A).astype(np.int32)
+    w = (rng.random(A) * 5).astype(np.float32)
+    w[rng.random(A) < 0.05] = 1.0                         # exact ties
+    start = np.full(q, np.inf, np.float32); start[:3] = [0.0, 0.5, 1.0]
+    final = np.where(rng.random(q) < 0.2, 0.0, np.inf).astype(np.float32); final[0] = 0.25
+    fa = synth.FstArrays(q, m, 5, src, dst, il, rng.integers(0, 5, size=A).astype(np.int32), w, start, final)
+    f, o = _fst(fa), oracle.Fst(fa)
+    strs = synth.make_strings(fa, 5, 5, 40, seed=3)
+    for b in range(strs.count):
+        check_string(f, o, strs.get(b))
+
+
+def test_c2_scaled():
+    fa, strs = synth.make_config("c2", scale=0.02, strings=25)
+    f, o = _fst(fa), oracle.Fst(fa)
+    for b in range(strs.count):
+        check_string(f, o, strs.get(b))
+
+
+def test_no_path_and_empty_string():
+    fa, _ = synth.make_config("c1", scale=0.2, strings=1)
+    f, o = _fst(fa), oracle.Fst(fa)
+    iid = synth.make_strings(fa, 6, 20, 40, seed=77, kind="iid")
+    seen_nopath = False
+    for b in range(iid.count):
+        x = iid.get(b)
+        check_string(f, o, x)
+        seen_nopath |= o.viterbi(x)["status"] == oracle.NO_PATH
+    assert seen_nopath
+    check_string(f, o, np.zeros(0, np.int32))
+
+
+def test_symbol_without_arcs():
+    fa = synth.fig1_fst()
+    fa.num_isyms = 5  # symbols 3 and 4 have no arcs
+    f, o = _fst(fa), oracle.Fst(fa)
+    for x in ([0, 1, 2], [3], [0, 4, 2], []):
+        check_string(f, o, np.array(x, np.int32))
+
+
+def test_repeatable_bitwise():
+    fa, strs = synth.make_config("c2", scale=0.01, strings=3)
+    f = _fst(fa)
+    x = strs.get(0)
+    a = f.viterbi(x)
+    b = f.viterbi(x)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    la, ca, _ = f.forward_backward(x)
+    lb, cb, _ = f.forward_backward(x)
+    assert la == lb and np.array_equal(ca, cb)
+
+
+def test_invalid_inputs():
+    from paper_1701_03038_gb300._lib import FstError
+    from paper_1701_03038_gb300.fst import Fst
+    fa = synth.fig1_fst()
+    f = _fst(fa)
+    with pytest.raises(FstError):
+        f.viterbi(np.array([0, 9], np.int32))
+    bad = synth.fig1_fst()
+    bad.weight[1] = np.nan
+    with pytest.raises(FstError):
+        Fst.from_arrays(bad)
+    bad = synth.fig1_fst()
+    bad.dst[0] = 6
+    with pytest.raises(FstError):
+        Fst.from_arrays(bad)
+    bad = synth.fig1_fst()
+    bad.weight[0] = -np.inf  # cost -inf = theta +inf
+    with pytest.raises(FstError):
+        Fst.from_arrays(bad)
+
+
+def test_store_info_and_symbol_stats():
+    fa, _ = synth.make_config("c2", scale=0.01, strings=1)
+    f = _fst(fa)
+    info = f.info()
+    arcs, dsts, srcs = f.symbol_stats()
+    assert info["num_arcs"] == fa.num_arcs and arcs.sum() == fa.num_arcs
+    want_arcs = np.bincount(fa.ilabel, minlength=fa.num_isyms)
+    assert np.array_equal(arcs, want_arcs)
+    pairs_d = np.unique(fa.ilabel.astype(np.int64) * fa.num_states + fa.dst)
+    pairs_s = np.unique(fa.ilabel.astype(np.int64) * fa.num_states + fa.src)
+    assert np.array_equal(dsts, np.bincount(pairs_d // fa.num_states, minlength=fa.num_isyms))
+    assert np.array_equal(srcs, np.bincount(pairs_s // fa.num_states, minlength=fa.num_isyms))
+    assert info["padded_arcs"] % 128 == 0 and info["padded_arcs"] >= fa.num_arcs
