@@ -84,17 +84,20 @@ __global__ void k_check_ids(const int32_t* __restrict__ ids, int64_t n, int32_t 
   if (i < n && (ids[i] < 0 || ids[i] >= m)) atomicOr(err, 32u);
 }
 
-// Advance the run epoch: tags of a run are epoch + token.  When the 32-bit
-// range would run out, restart at 1 and ask for the frontiers to be cleared.
+// Run epochs: epoch[0] is the first tag of the current run and epoch[1]
+// the number of tags that run uses.  The next run starts past them; when the
+// 32-bit range would run out it restarts at 1 and the frontiers are cleared
+// (tag 0, left by the clear, is never a valid tag).
 __global__ void k_epoch_advance(uint32_t* epoch, uint32_t span, uint32_t* clear) {
-  const uint32_t e = *epoch;
-  if ((uint64_t)e + 2ull * span + 2ull >= 0xffffffffull) {
-    *epoch = 1u;
+  const uint64_t next = (uint64_t)epoch[0] + (uint64_t)epoch[1] + 1ull;
+  if (next + (uint64_t)span + 1ull >= 0xffffffffull) {
+    epoch[0] = 1u;
     *clear = 1u;
   } else {
-    *epoch = e + span + 1u;
+    epoch[0] = (uint32_t)next;
     *clear = 0u;
   }
+  epoch[1] = span;
 }
 
 __global__ void k_clear_if(const uint32_t* clear, unsigned long long* p, int64_t n) {
@@ -180,14 +183,14 @@ int plain_init(fst_s* f) {
       (rc = dalloc(&w->scnt, w->max_lseg)) || (rc = dalloc(&w->spart, w->max_lwin)) ||
       (rc = dalloc(&w->qfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
       (rc = dalloc(&w->logz, 1)) || (rc = dalloc(&w->bw_n, 1)) || (rc = dalloc(&w->bw_off, 1)) ||
-      (rc = dalloc(&w->epoch, 1)) || (rc = dalloc(&w->clear, 1)))
+      (rc = dalloc(&w->epoch, 2)) || (rc = dalloc(&w->clear, 1)))
     return rc;
   FST_CUDA(cudaMemset(w->alpha, 0, (size_t)2 * Q * sizeof(unsigned long long)));
   FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(unsigned long long)));
   FST_CUDA(cudaMemset(w->skey, 0, (size_t)std::max<int64_t>(1, w->max_lseg) * 8));
   FST_CUDA(cudaMemset(w->scnt, 0, (size_t)std::max<int64_t>(1, w->max_lseg) * 4));
   FST_CUDA(cudaMemset(w->bw_off, 0, sizeof(int64_t)));
-  FST_CUDA(cudaMemset(w->epoch, 0, sizeof(uint32_t)));
+  FST_CUDA(cudaMemset(w->epoch, 0, 2 * sizeof(uint32_t)));
   return FST_OK;
 }
 

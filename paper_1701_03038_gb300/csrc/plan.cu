@@ -145,15 +145,20 @@ __global__ void k_grp_item_local(const int32_t* __restrict__ grp_t, const int32_
   lb[g] = gib[g] - gib[g0];
 }
 
+// Run epochs: epoch[0] is the first tag of the current run and epoch[1]
+// the number of tags that run uses.  The next run starts past them; when the
+// 32-bit range would run out it restarts at 1 and the frontiers are cleared
+// (tag 0, left by the clear, is never a valid tag).
 __global__ void k_epoch_advance(uint32_t* epoch, uint32_t span, uint32_t* clear) {
-  const uint32_t e = *epoch;
-  if ((uint64_t)e + 2ull * span + 2ull >= 0xffffffffull) {
-    *epoch = 1u;
+  const uint64_t next = (uint64_t)epoch[0] + (uint64_t)epoch[1] + 1ull;
+  if (next + (uint64_t)span + 1ull >= 0xffffffffull) {
+    epoch[0] = 1u;
     *clear = 1u;
   } else {
-    *epoch = e + span + 1u;
+    epoch[0] = (uint32_t)next;
     *clear = 0u;
   }
+  epoch[1] = span;
 }
 
 __global__ void k_clear_if(const uint32_t* clear, unsigned long long* p, int64_t n) {
@@ -526,13 +531,13 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
         (rc = alloc_track(P, &P->csum, P->max_ntok)) || (rc = alloc_track(P, &P->esum, P->max_ntok)) ||
         (rc = alloc_track(P, &P->skey, P->max_lseg)) || (rc = alloc_track(P, &P->scnt, P->max_lseg)) ||
         (rc = alloc_track(P, &P->spart, P->max_lwin)) || (rc = alloc_track(P, &P->qfinal, P->max_bw)) ||
-        (rc = alloc_track(P, &P->logz, B)) || (rc = alloc_track(P, &P->epoch, 1)) ||
+        (rc = alloc_track(P, &P->logz, B)) || (rc = alloc_track(P, &P->epoch, 2)) ||
         (rc = alloc_track(P, &P->clear, 1)))
       break;
     if (want_fb && (rc = alloc_track(P, &P->cnt64, f->bwd.P))) break;
     FST_CUDA(cudaMemsetAsync(P->alpha, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
-    FST_CUDA(cudaMemsetAsync(P->epoch, 0, 4, s));
+    FST_CUDA(cudaMemsetAsync(P->epoch, 0, 8, s));
     FST_CUDA(cudaMemsetAsync(P->skey, 0, (size_t)std::max<int64_t>(1, P->max_lseg) * 8, s));
     FST_CUDA(cudaMemsetAsync(P->scnt, 0, (size_t)std::max<int64_t>(1, P->max_lseg) * 4, s));
     FST_CUDA(cudaStreamSynchronize(s));

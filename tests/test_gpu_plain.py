@@ -170,3 +170,12 @@ def test_store_info_and_symbol_stats():
     assert np.array_equal(dsts, np.bincount(pairs_d // fa.num_states, minlength=fa.num_isyms))
     assert np.array_equal(srcs, np.bincount(pairs_s // fa.num_states, minlength=fa.num_isyms))
     assert info["padded_arcs"] % 128 == 0 and info["padded_arcs"] >= fa.num_arcs
+
+
+def test_shorter_strings_after_longer_on_one_handle():
+    # frontier tags of one call must never be mistaken for those of the next
+    fa, _ = synth.make_config("c2", scale=0.01, strings=1)
+    f, o = _fst(fa), oracle.Fst(fa)
+    for n in (60, 45, 30, 12, 5, 2, 1, 33):
+        x = synth.make_strings(fa, 1, n, n, seed=100 + n).get(0)
+        check_string(f, o, x)
