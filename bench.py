@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: batched Viterbi + forward-backward on the 20M-arc workload.
+
+One step = one pass of the whole hot path over one batch: Viterbi (relax,
+final reduction, backtrace) and forward-backward (forward relax, log Z,
+backward relax fused with arc posteriors, counts back to arc order) for all
+4,096 strings of the 200,000-state, 20,000-symbol, 20,000,000-arc synthetic
+FST (lengths U[5, 200], random-walk strings, seeded).  Inputs are resident
+in HBM when the timed region starts and are larger than the L2 cache.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "arc-relaxations/s & sentences/s, batched vs plain, % of HBM roofline"
+UNIT = "arc-relaxations/s"
+WORKLOADS = {
+    "c3": "batched: 200,000 states, 20,000 input symbols, 20,000,000 arcs (Zipf arcs per symbol, lognormal "
+          "out-degree mean 100, Dirichlet(0.5) weights), 4,096 random-walk strings of length U[5,200]; "
+          "Viterbi + forward-backward with arc posteriors per step",
+    "c2": "plain-shaped: 50,000 states, 10,000 symbols, 5,000,000 arcs, 1,000 strings of length U[10,60]",
+    "c4": "100,000 states, 5,000 symbols, 2,000,000 arcs, 1,024 strings of length U[10,100]",
+    "c5": "1,000,000 states, 5,000 symbols, 100,000,000 arcs, 64 strings of length 1,000",
+    "c1": "1,000 states, 50 symbols, 20,000 arcs, one string of length 50",
+}
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--budget-gb", type=float, default=48.0, help="plan storage budget (waves)")
+    ap.add_argument("--plain-sample", type=int, default=48, help="strings timed on the plain path")
+    ap.add_argument("--cpu-sample", type=int, default=16, help="strings timed on the CPU oracle")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- models
+def bytes_model(stats, ids):
+    """Algorithmic bytes per pass (sum over tokens of the per-step figures):
+    Viterbi 12|A|+4U+8D, forward 12|A|+4U+4D, backward+posterior 20|A|+8U+4D."""
+    A, D, U = (s.astype(np.float64)[ids] for s in stats)
+    return {
+        "vit_step": float((12 * A + 4 * U + 8 * D).sum()),
+        "fwd_step": float((12 * A + 4 * U + 4 * D).sum()),
+        "bwd_step": float((20 * A + 8 * U + 4 * D).sum()),
+    }
+
+
+def load_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+def load_traffic(kernel: str, workload: str):
+    try:
+        with open(PROFILE_SUMMARY) as fh:
+            d = json.load(fh)
+        e = d.get(workload, {}).get(kernel)
+        if e and e.get("source_hash") == source_hash():
+            return e.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1701_03038_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+# ------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1701_03038_gb300 import synth
+    fa, strs = synth.make_config(args.workload)
+    o = oracle.Fst(fa)
+    cores = os.cpu_count() or 1
+    sample = max(1, min(args.cpu_sample, strs.count))
+    A = np.bincount(fa.ilabel, minlength=fa.num_isyms)
+    times = []
+    relax = 0
+    for k in range(args.warmup + args.steps):
+        b0 = (k * sample) % strs.count
+        sel = [(b0 + i) % strs.count for i in range(sample)]
+        ids = np.concatenate([strs.get(b) for b in sel]).astype(np.int32)
+        off = np.zeros(sample + 1, np.int64)
+        off[1:] = np.cumsum([len(strs.get(b)) for b in sel])
+        t0 = time.perf_counter()
+        o.viterbi_batch(ids, off, nthreads=cores)
+        o.fb_batch(ids, off, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            relax += 3 * int(A[ids].sum())
+    tot = sum(times)
+    value = relax / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ": " + WORKLOADS[args.workload],
+                   "reference": "CPU oracle (plain C; Viterbi float32, forward-backward float64)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} strings per step of the {args.workload} batch, "
+                                   f"Viterbi + forward-backward with counts, {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1701_03038_gb300 import build as gbuild
+    from paper_1701_03038_gb300 import synth
+    from paper_1701_03038_gb300.fst import Fst
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gbuild.build()
+    dev = torch.device("cuda", local)
+
+    fa, strs = synth.make_config(args.workload)
+    f = Fst.from_arrays(fa, device=dev)
+    stats = f.symbol_stats()
+    ids = torch.from_numpy(strs.ids).to(dev)
+    off = torch.from_numpy(strs.offsets).to(dev)
+    plan = f.plan(ids, off, mem_budget=int(args.budget_gb * (1 << 30)))
+    info = plan.info()
+    relax_pass = info["relaxations"]
+    relax_step = 3 * relax_pass  # Viterbi, forward and backward each relax every slice
+
+    def step():
+        plan.viterbi()
+        plan.forward_backward()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = relax_step * world / (ms / 1000.0)
+    sent_s = strs.count * world / (ms / 1000.0)
+
+    # per-kernel device time of one more step, with events around every launch
+    plan.profile(True)
+    step()
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile(False)
+    model = bytes_model(stats, strs.ids)
+    steps_ms = {k: prof[k][0] for k in ("vit_step", "fwd_step", "bwd_step")}
+    dom = max(steps_ms, key=steps_ms.get)
+    peak, peak_src = load_peak()
+    achieved = model[dom] / (prof[dom][0] / 1000.0) / 1e9
+    kernels = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items()}
+    for k in model:
+        kernels[k]["model_gbs"] = round(model[k] / (prof[k][0] / 1000.0) / 1e9, 1) if prof[k][0] > 0 else None
+    traffic = load_traffic(dom, args.workload)
+    kernel_names = {"vit_step": "k_vit_step", "fwd_step": "k_fwd_step", "bwd_step": "k_bwd_step"}
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kernel_names[dom],
+                "launches": prof[dom][1], "bytes_model": "Viterbi 12|A|+4U+8D, forward 12|A|+4U+4D, "
+                "backward+posterior 20|A|+8U+4D per token", "peak_source": peak_src}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload + ": " + WORKLOADS[args.workload], "strings": strs.count,
+                      "tokens": int(len(strs.ids)), "relaxations_per_pass": relax_pass, "waves": info["waves"],
+                      "plan_gb": round(info["device_bytes"] / 2**30, 2), "parallelism": "replicas" if world > 1 else "1 GPU",
+                      "l2": "no flush: inputs larger than L2 (arc store "
+                            f"{(fa.num_arcs * 24) / 2**30:.2f} GiB, frontiers and per-step storage "
+                            f"{info['device_bytes'] / 2**30:.1f} GiB)"},
+           "sentences_per_s": sent_s, "roofline": roofline, "kernels": kernels, "clocks": clk,
+           "gpu_launches": args.steps * (info["viterbi_launches"] + info["fb_launches"])}
+
+    # plain method (one string at a time, one launch per position) on a sample
+    if not args.no_plain and rank == 0:
+        n = min(args.plain_sample, strs.count)
+        for b in range(2):
+            f.viterbi(strs.get(b))
+            f.forward_backward(strs.get(b))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rx = 0
+        for b in range(n):
+            x = strs.get(b)
+            f.viterbi(x)
+            f.forward_backward(x)
+            rx += 3 * int(stats[0][x].sum())
+        dt = time.perf_counter() - t0
+        out["plain"] = {"value": rx / dt, "unit": UNIT, "sentences_per_s": n / dt,
+                        "sample": f"first {n} strings, host API (fst_viterbi + fst_forward_backward)"}
+        out["batched_over_plain_sentences"] = sent_s / world / (n / dt)
+
+    # end to end through the public batch API with host buffers
+    if not args.no_e2e:
+        h_ids = torch.from_numpy(strs.ids).pin_memory()
+        h_off = torch.from_numpy(strs.offsets).pin_memory()
+        h_scores = torch.empty(strs.count, dtype=torch.float32).pin_memory()
+        h_paths = torch.empty(len(strs.ids), dtype=torch.int32).pin_memory()
+        h_logz = torch.empty(strs.count, dtype=torch.float64).pin_memory()
+        h_counts = torch.empty(fa.num_arcs, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            d_ids = h_ids.to(dev, non_blocking=True)
+            d_off = h_off.to(dev, non_blocking=True)
+            v = f.viterbi_batch(d_ids, d_off)
+            r = f.forward_backward_batch(d_ids, d_off)
+            h_scores.copy_(v["scores"], non_blocking=True)
+            h_paths.copy_(v["paths"], non_blocking=True)
+            h_logz.copy_(r["logz"], non_blocking=True)
+            h_counts.copy_(r["counts"], non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        barrier()
+        h2d = strs.ids.nbytes + strs.offsets.nbytes
+        d2h = 4 * strs.count + 4 * len(strs.ids) + 8 * strs.count + 4 * fa.num_arcs
+        out["e2e"] = {"value": relax_step * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * dt,
+                      "api": "Fst.viterbi_batch + Fst.forward_backward_batch (plans built per call)"}
+
+    # CPU oracle on the host cores, bounded sample (rank 0, N = 1 only)
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle
+        o = oracle.Fst(fa)
+        cores = os.cpu_count() or 1
+        n = min(args.cpu_sample, strs.count)
+        sel_ids = np.concatenate([strs.get(b) for b in range(n)]).astype(np.int32)
+        sel_off = strs.offsets[:n + 1].copy()
+        t0 = time.perf_counter()
+        o.viterbi_batch(sel_ids, sel_off, nthreads=cores)
+        o.fb_batch(sel_ids, sel_off, nthreads=cores)
+        dt = time.perf_counter() - t0
+        rx = 3 * int(stats[0][sel_ids].sum())
+        out["cpu_baseline"] = {"value": rx / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"first {n} strings of the batch, Viterbi + forward-backward with "
+                                         f"counts, {cores} threads, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -206,6 +206,25 @@ FST_API int fst_plan_backward(fst_plan_t* plan, const float* d_weights, float* d
 FST_API int fst_plan_forward_backward(fst_plan_t* plan, const float* d_weights, double* d_logz,
                               float* d_counts, int32_t* d_status, void* stream);
 
+/* Per-launch timing of a plan's runs (the tracing subsystem).  With
+ * enable != 0, every kernel that a following fst_plan_* run queues is
+ * bracketed by two CUDA events on the run's stream; fst_plan_profile_read
+ * waits for the last of them and returns, per kernel kind, the summed
+ * device time in milliseconds and the number of launches since the last
+ * read (host arrays of FST_PROF_KINDS entries, either may be NULL), then
+ * starts a new accumulation.  Do not enable it while capturing a graph. */
+#define FST_PROF_VIT_STEP 0   /* Viterbi relaxation, one position */
+#define FST_PROF_VIT_FINAL 1  /* Viterbi final reduction */
+#define FST_PROF_BACKTRACE 2  /* Viterbi backtrace */
+#define FST_PROF_FWD_STEP 3   /* forward relaxation, one position */
+#define FST_PROF_FB_FINAL 4   /* log Z and the float64 normaliser prefix */
+#define FST_PROF_SCATTER 5    /* forward values restored for the backward pass */
+#define FST_PROF_BWD_STEP 6   /* backward relaxation fused with posteriors */
+#define FST_PROF_COUNTS 7     /* expected counts back to caller arc order */
+#define FST_PROF_KINDS 8
+FST_API int fst_plan_profile(fst_plan_t* plan, int32_t enable);
+FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t* launches_by_kind);
+
 /* Message of the last failing call on this host thread ("" if none). */
 FST_API const char* fst_last_error(void);
 

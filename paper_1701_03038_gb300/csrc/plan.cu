@@ -209,13 +209,45 @@ struct fst_plan_s {
   uint32_t *epoch = nullptr, *clear = nullptr;
   int64_t max_bw = 0, max_ntok = 0, max_store = 0, max_lseg = 0, max_lwin = 0;
   bool forward_done = false;
+  // optional per-launch CUDA events (fst_plan_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_kind;
+  size_t prof_used = 0;
   ~fst_plan_s() {
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (Wave& w : waves) w.release();
     dfree(ids); dfree(alpha); dfree(beta); dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum);
     dfree(esum); dfree(skey); dfree(scnt); dfree(spart); dfree(qfinal); dfree(cnt64); dfree(logz);
     dfree(epoch); dfree(clear);
   }
 };
+
+// Per-launch timing: an event before and after every kernel of a run.
+static long prof_begin(fst_plan_s* P, int kind, cudaStream_t s) {
+  if (!P->prof_on) return -1;
+  const size_t i = P->prof_used;
+  while (P->prof_ev.size() < 2 * (i + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    P->prof_ev.push_back(e);
+  }
+  if (P->prof_kind.size() < i + 1) P->prof_kind.resize(i + 1);
+  P->prof_kind[i] = kind;
+  cudaEventRecord(P->prof_ev[2 * i], s);
+  P->prof_used = i + 1;
+  return (long)i;
+}
+static void prof_end(fst_plan_s* P, long i, cudaStream_t s) {
+  if (i >= 0) cudaEventRecord(P->prof_ev[2 * i + 1], s);
+}
+#define PROF(kind, call)                              \
+  do {                                                \
+    const long pi__ = prof_begin(P, (kind), s);       \
+    const int rc__ = (call);                          \
+    prof_end(P, pi__, s);                             \
+    if (rc__) return rc__;                            \
+  } while (0)
 
 namespace {
 
@@ -403,9 +435,11 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   FST_CUDA(cudaMemsetAsync(P->ekey, 0, (size_t)std::max<int64_t>(1, W.ntok) * 4, s));
   for (int32_t t = 1; t <= W.tmax; ++t) {
     const WorkView V = wave_work(W, t, true);
-    if ((rc = launch_fwd_step(Lf, T, V, S, step_grid(f, V.nitems), s))) return rc;
+    PROF(FST_PROF_FWD_STEP, launch_fwd_step(Lf, T, V, S, step_grid(f, V.nitems), s));
   }
-  return launch_fb_final(Lf, W.tok_sym, W.cbase, S, W.Bw, P->logz + W.b0, d_status ? d_status + W.b0 : nullptr, s);
+  PROF(FST_PROF_FB_FINAL, launch_fb_final(Lf, W.tok_sym, W.cbase, S, W.Bw, P->logz + W.b0,
+                                           d_status ? d_status + W.b0 : nullptr, s));
+  return FST_OK;
 }
 
 int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cudaStream_t s) {
@@ -418,10 +452,10 @@ int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cuda
   for (int32_t t = W.tmax; t >= 1; --t) {
     if (t < W.tmax && t >= 2) {
       const WorkView V = wave_work(W, t - 1, true);
-      if ((rc = launch_scatter_alpha(Lf, T, V, S, t, step_grid(f, V.nitems), s))) return rc;
+      PROF(FST_PROF_SCATTER, launch_scatter_alpha(Lf, T, V, S, t, step_grid(f, V.nitems), s));
     }
     const WorkView V = wave_work(W, t, false);
-    if ((rc = launch_bwd_step(Lb, T, V, S, C, step_grid(f, V.nitems), s))) return rc;
+    PROF(FST_PROF_BWD_STEP, launch_bwd_step(Lb, T, V, S, C, step_grid(f, V.nitems), s));
   }
   return FST_OK;
 }
@@ -429,6 +463,8 @@ int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cuda
 inline cudaStream_t as_stream(void* p) { return (cudaStream_t)p; }
 
 }  // namespace
+
+
 
 extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                                int64_t mem_budget_bytes, int32_t flags, void* stream, fst_plan_t** out) {
@@ -598,14 +634,13 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
     const WaveState S = wave_state(P, W, nullptr);
     for (int32_t t = 1; t <= W.tmax; ++t) {
       const WorkView V = wave_work(W, t, true);
-      if ((rc = launch_vit_step(Lf, T, V, S, step_grid(f, V.nitems), s))) return rc;
+      PROF(FST_PROF_VIT_STEP, launch_vit_step(Lf, T, V, S, step_grid(f, V.nitems), s));
     }
-    if ((rc = launch_vit_final(Lf, W.tok_sym, W.cbase, S, W.Bw, d_scores + W.b0, P->qfinal,
-                               d_status ? d_status + W.b0 : nullptr, s)))
-      return rc;
-    if ((rc = launch_backtrace(Lf, W.tok_sym, W.cbase, S, f->olabel, f->fwd.arc_id, W.Bw, P->qfinal,
-                               d_paths + W.tok0, d_olabels ? d_olabels + W.tok0 : nullptr, s)))
-      return rc;
+    PROF(FST_PROF_VIT_FINAL, launch_vit_final(Lf, W.tok_sym, W.cbase, S, W.Bw, d_scores + W.b0, P->qfinal,
+                                              d_status ? d_status + W.b0 : nullptr, s));
+    PROF(FST_PROF_BACKTRACE, launch_backtrace(Lf, W.tok_sym, W.cbase, S, f->olabel, f->fwd.arc_id, W.Bw,
+                                              P->qfinal, d_paths + W.tok0, d_olabels ? d_olabels + W.tok0 : nullptr,
+                                              s));
   }
   return FST_OK;
 }
@@ -634,7 +669,8 @@ extern "C" int fst_plan_backward(fst_plan_t* P, const float* d_weights, float* d
   for (const Wave& W : P->waves)
     if ((rc = run_backward_wave(P, W, d_weights, s))) return rc;
   const CountView C{1, nullptr, nullptr, P->cnt64};
-  return launch_counts_out(f->bwd.arc_id, f->bwd.P, C, d_counts, s);
+  PROF(FST_PROF_COUNTS, launch_counts_out(f->bwd.arc_id, f->bwd.P, C, d_counts, s));
+  return FST_OK;
 }
 
 extern "C" int fst_plan_forward_backward(fst_plan_t* P, const float* d_weights, double* d_logz, float* d_counts,
@@ -653,7 +689,7 @@ extern "C" int fst_plan_forward_backward(fst_plan_t* P, const float* d_weights, 
   if (P->B > 0) FST_CUDA(cudaMemcpyAsync(d_logz, P->logz, (size_t)P->B * 8, cudaMemcpyDeviceToDevice, s));
   if (d_counts) {
     const CountView C{1, nullptr, nullptr, P->cnt64};
-    if ((rc = launch_counts_out(f->bwd.arc_id, f->bwd.P, C, d_counts, s))) return rc;
+    PROF(FST_PROF_COUNTS, launch_counts_out(f->bwd.arc_id, f->bwd.P, C, d_counts, s));
   }
   P->forward_done = P->waves.size() <= 1;
   return FST_OK;
@@ -683,4 +719,33 @@ extern "C" int fst_forward_backward_batch(fst_t* f, const int32_t* d_ids, const 
   if (!rc && e != cudaSuccess) rc = cuda_fail(e, "fst_forward_backward_batch");
   fst_plan_destroy(P);
   return rc;
+}
+
+extern "C" int fst_plan_profile(fst_plan_t* P, int32_t enable) {
+  if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
+  P->prof_on = enable != 0;
+  P->prof_used = 0;
+  return FST_OK;
+}
+
+extern "C" int fst_plan_profile_read(fst_plan_t* P, double* ms_by_kind, int64_t* launches_by_kind) {
+  if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
+  double ms[FST_PROF_KINDS] = {0};
+  int64_t cnt[FST_PROF_KINDS] = {0};
+  if (P->prof_used > 0) FST_CUDA(cudaEventSynchronize(P->prof_ev[2 * (P->prof_used - 1) + 1]));
+  for (size_t i = 0; i < P->prof_used; ++i) {
+    float t = 0.f;
+    FST_CUDA(cudaEventElapsedTime(&t, P->prof_ev[2 * i], P->prof_ev[2 * i + 1]));
+    const int k = P->prof_kind[i];
+    if (k >= 0 && k < FST_PROF_KINDS) {
+      ms[k] += t;
+      cnt[k] += 1;
+    }
+  }
+  P->prof_used = 0;
+  for (int k = 0; k < FST_PROF_KINDS; ++k) {
+    if (ms_by_kind) ms_by_kind[k] = ms[k];
+    if (launches_by_kind) launches_by_kind[k] = cnt[k];
+  }
+  return FST_OK;
 }

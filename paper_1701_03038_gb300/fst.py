@@ -244,6 +244,17 @@ class Plan:
         return dict(strings=b.value, tokens=n.value, waves=w.value, max_len=ml.value, relaxations=r.value,
                     viterbi_launches=vl.value, fb_launches=fl.value, device_bytes=by.value)
 
+    def profile(self, enable: bool = True):
+        """Bracket every kernel of the following runs with CUDA events."""
+        check(self._lib.fst_plan_profile(self._h, 1 if enable else 0), "fst_plan_profile")
+
+    def profile_read(self) -> dict:
+        """{kind: (milliseconds, launches)} accumulated since the last read."""
+        ms = np.zeros(len(_lib.PROF_KINDS), np.float64)
+        n = np.zeros(len(_lib.PROF_KINDS), np.int64)
+        check(self._lib.fst_plan_profile_read(self._h, _hptr(ms), _hptr(n)), "fst_plan_profile_read")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(_lib.PROF_KINDS)}
+
     def viterbi(self, stream=None):
         """Queue Viterbi for every string; results land in self.scores /
         self.paths / self.olabels / self.status."""
