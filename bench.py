@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--plain-sample", type=int, default=48, help="strings timed on the plain path")
     ap.add_argument("--cpu-sample", type=int, default=16, help="strings timed on the CPU oracle")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -223,6 +224,8 @@ def main():
     dev = torch.device("cuda", local)
 
     fa, strs = synth.make_config(args.workload)
+    if args.strings and args.strings < strs.count:
+        strs = synth.Strings(strs.ids[:strs.offsets[args.strings]].copy(), strs.offsets[:args.strings + 1].copy())
     f = Fst.from_arrays(fa, device=dev)
     stats = f.symbol_stats()
     ids = torch.from_numpy(strs.ids).to(dev)

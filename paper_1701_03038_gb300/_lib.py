@@ -55,7 +55,8 @@ class FstError(RuntimeError):
 
 
 def lib_path() -> str:
-    return _build.LIB_PATH
+    """The in-tree build, unless FSTGPU_LIB names another build of it."""
+    return os.environ.get("FSTGPU_LIB") or _build.LIB_PATH
 
 
 def load(path: str | None = None):

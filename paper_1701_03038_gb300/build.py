@@ -43,16 +43,21 @@ def up_to_date() -> bool:
     return os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= _newest_input()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every translation unit and link libfstgpu.so; returns its path."""
-    if not force and not extra_flags and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_path: str | None = None) -> str:
+    """Compile every translation unit and link libfstgpu.so; returns its path.
+    ``extra_flags`` (e.g. -D tuning macros) and ``out_path`` build a variant
+    elsewhere without touching the in-tree library."""
+    lib_path = out_path or LIB_PATH
+    if not force and not extra_flags and out_path is None and up_to_date():
         return LIB_PATH
-    os.makedirs(OUT_DIR, exist_ok=True)
+    obj_dir = OUT_DIR if out_path is None else os.path.dirname(os.path.abspath(out_path))
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+        tag = "" if out_path is None else "_" + os.path.splitext(os.path.basename(out_path))[0]
+        obj = os.path.join(obj_dir, os.path.splitext(src)[0] + tag + ".o")
         cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -65,13 +70,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-ldl", "-lpthread", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

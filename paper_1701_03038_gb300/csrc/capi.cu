@@ -294,7 +294,8 @@ WorkView single_work(int32_t p, int32_t sym, int64_t nitems) {
   return W;
 }
 
-int step_grid(const fst_s* f, int64_t nitems) { return grid_for(nitems, 256, f->num_sms, 8); }
+// the launchers size step grids from the SM count and the kernel's occupancy
+int step_grid(const fst_s* f, int64_t) { return f->num_sms; }
 
 struct DevGuard {
   int old = -1;

@@ -26,6 +26,12 @@ namespace fstgpu {
 namespace {
 
 constexpr int KT = 256;  // threads per block of the step kernels
+#ifndef KT_MIN_BLOCKS
+#define KT_MIN_BLOCKS 3
+#endif
+#ifndef KT_MIN_BLOCKS_BWD
+#define KT_MIN_BLOCKS_BWD 2
+#endif
 
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
@@ -43,7 +49,7 @@ struct LogAdd {
   static __device__ __forceinline__ T combine(T a, T b) {
     if (a.x < b.x) { T c = a; a = b; b = c; }
     if (b.x == __int_as_float(0xff800000)) return a;
-    return make_float2(a.x, a.y + b.y * expf(b.x - a.x));
+    return make_float2(a.x, a.y + b.y * __expf(b.x - a.x));
   }
   static __device__ __forceinline__ T shfl_up(T v, int d) {
     return make_float2(__shfl_up_sync(FULL, v.x, d), __shfl_up_sync(FULL, v.y, d));
@@ -84,54 +90,57 @@ __device__ __forceinline__ void window_scan(const typename Op::T (&e)[APL], uint
   for (int j = 0; j < APL; ++j) full[j] = (j < first) ? Op::combine(carry, p[j]) : p[j];
 }
 
-struct ItemCtx {
-  int32_t g, sym, cnt;
-  int64_t wslice;
+// Work-list resolution.  A warp walks items item0, item0 + nwarps, ...; the
+// group of the last item and, in lane j, the data of the group's j-th token
+// stay in registers until an item falls outside the group.
+struct Group {
+  int32_t g, sym, cnt, segbase;
+  int64_t lo, hi, wbase;
 };
 
-__device__ __forceinline__ ItemCtx resolve(const WorkView& W, int64_t item) {
-  ItemCtx c;
+__device__ __forceinline__ void find_group(const LayoutView& L, const WorkView& W, int64_t item, Group& G) {
   if (W.single) {
-    c.g = -1; c.sym = W.sym0; c.cnt = 1; c.wslice = item;
-    return c;
+    G.g = 0; G.lo = 0; G.hi = W.nitems; G.sym = W.sym0; G.cnt = 1;
+  } else {
+    int lo = G.g >= 0 ? G.g + 1 : W.g0;  // items only grow inside a warp's walk
+    int hi = W.g1 - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(W.grp_item + mid) <= item) lo = mid; else hi = mid - 1;
+    }
+    G.g = lo;
+    G.lo = __ldg(W.grp_item + lo);
+    G.hi = (lo + 1 < W.g1) ? __ldg(W.grp_item + lo + 1) : W.nitems;
+    G.sym = __ldg(W.grp_sym + lo);
+    G.cnt = __ldg(W.grp_cnt + lo);
   }
-  int lo = W.g0, hi = W.g1 - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (W.grp_item[mid] <= item) lo = mid; else hi = mid - 1;
-  }
-  c.g = lo;
-  c.sym = W.grp_sym[lo];
-  c.cnt = W.grp_cnt[lo];
-  c.wslice = item - W.grp_item[lo];
-  return c;
+  G.wbase = __ldg(L.sym_win + G.sym);
+  G.segbase = (int32_t)__ldg(L.sym_seg + G.sym);
 }
 
-__device__ __forceinline__ int32_t token_of(const WorkView& W, const ItemCtx& c, int j) {
-  return W.single ? W.p0 : W.sorted_tok[W.grp_first[c.g] + j];
+__device__ __forceinline__ int32_t group_token(const WorkView& W, const Group& G, int lane) {
+  return W.single ? W.p0 : __ldg(W.sorted_tok + __ldg(W.grp_first + G.g) + lane);
 }
 
-struct WinCtx {
+struct Win {
   int64_t w;
-  WinMeta meta;
-  uint32_t h;       // this lane's head bits
-  int32_t hb;       // heads of the window before this lane
-  int32_t segbase;  // first segment of the slice
+  int32_t seg, lseg, lwin0, lcnt;
+  uint32_t h;   // this lane's head bits
+  int32_t hb;   // heads of the window before this lane
 };
 
-__device__ __forceinline__ WinCtx load_win(const LayoutView& L, int32_t sym, int64_t wslice, int lane) {
-  WinCtx x;
-  x.w = L.sym_win[sym] + wslice;
-  x.meta = L.win[x.w];
-  const uint32_t word = x.meta.mask[lane >> 3];
+__device__ __forceinline__ Win load_win(const LayoutView& L, int64_t w, int lane) {
+  Win x;
+  x.w = w;
+  const int4 m0 = __ldg(reinterpret_cast<const int4*>(L.win + w));
+  const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(L.win + w) + 1);
+  x.seg = m0.x; x.lseg = m0.y; x.lwin0 = m0.z; x.lcnt = m0.w;
+  const int q = lane >> 3;
+  const uint32_t word = q == 0 ? m1.x : (q == 1 ? m1.y : (q == 2 ? m1.z : m1.w));
   const int sh = (lane & 7) * 4;
   x.h = (word >> sh) & 0xFu;
-  int hb = __popc(word & ((1u << sh) - 1u));
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    if (k < (lane >> 3)) hb += __popc(x.meta.mask[k]);
-  x.hb = hb;
-  x.segbase = (int32_t)L.sym_seg[sym];
+  x.hb = __popc(word & ((1u << sh) - 1u)) + (q > 0 ? __popc(m1.x) : 0) + (q > 1 ? __popc(m1.y) : 0) +
+         (q > 2 ? __popc(m1.z) : 0);
   return x;
 }
 
@@ -140,121 +149,11 @@ __device__ __forceinline__ int64_t warp_id_global() {
 }
 __device__ __forceinline__ int64_t warps_total() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
 
-// ======================================================================
-// Viterbi step (Alg. 1 inner loop; Sec. 5.1)
-// ======================================================================
-__device__ __forceinline__ void vit_write(const LayoutView& L, const WaveState& S, int64_t cb, int32_t s,
-                                          int32_t sl, unsigned long long key, unsigned long long* aout,
-                                          uint32_t tag) {
-  S.bp[cb + sl] = key ? (int32_t)(~(uint32_t)key) : -1;
-  if (key) aout[L.seg_state[s]] = tagged_make(fkey_inv((uint32_t)(key >> 32)), tag);
+__device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
+  return (int64_t)__shfl_sync(FULL, (long long)v, src);
 }
 
-__global__ void __launch_bounds__(KT) k_vit_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t tag_base = *S.epoch + S.tok0;
-  const int64_t nw = warps_total();
-  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
-    const ItemCtx c = resolve(W, item);
-    const WinCtx x = load_win(L, c.sym, c.wslice, lane);
-    const int64_t base = x.w * WIN + lane * APL;
-    const int4 s4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
-    const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
-    const int32_t src[APL] = {s4.x, s4.y, s4.z, s4.w};
-    const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
-    const bool is_long = x.meta.lseg >= 0;
-    const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
-    for (int j = 0; j < c.cnt; ++j) {
-      const int32_t p = token_of(W, c, j);
-      const int32_t b = T.b[p], t = T.t[p];
-      float a[APL];
-      if (t == 1) {
-#pragma unroll
-        for (int k = 0; k < APL; ++k) a[k] = __ldg(S.theta_s + src[k]);
-      } else {
-        const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
-        const uint32_t tg = tag_base + (uint32_t)(p - 1);
-#pragma unroll
-        for (int k = 0; k < APL; ++k) a[k] = tagged_value(__ldg(ab + src[k]), tg);
-      }
-      unsigned long long key[APL];
-#pragma unroll
-      for (int k = 0; k < APL; ++k) {
-        const float cand = __fadd_rn(a[k], th[k]);
-        key[k] = (cand == neg_inf()) ? 0ull
-                                     : (((unsigned long long)fkey(cand) << 32) |
-                                        (unsigned long long)(~(uint32_t)(base + k)));
-      }
-      unsigned long long full[APL];
-      window_scan<MaxKey>(key, x.h, lane, full);
-      const int64_t cb = T.cbase[p];
-      unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
-      const uint32_t tag = tag_base + (uint32_t)p;
-      if (!is_long) {
-        int cum = x.hb;
-#pragma unroll
-        for (int k = 0; k < APL; ++k) {
-          cum += (x.h >> k) & 1u;
-          const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
-          if (tail) {
-            const int32_t s = x.meta.seg + cum - 1;
-            vit_write(L, S, cb, s, s - x.segbase, full[k], aout, tag);
-          }
-        }
-      } else if (lane == 31) {
-        // a destination segment that spans warps: packed 64-bit atomicMax
-        const int64_t slot = T.lbase[p] + x.meta.lseg;
-        atomicMax(S.skey + slot, full[APL - 1]);
-        __threadfence();
-        const uint32_t prev = atomicAdd(S.scnt + slot, 1u);
-        if (prev == (uint32_t)x.meta.lcnt - 1u) {
-          __threadfence();
-          const unsigned long long kf = atomicMax(S.skey + slot, 0ull);
-          const int32_t s = x.meta.seg;
-          vit_write(L, S, cb, s, s - x.segbase, kf, aout, tag);
-          S.skey[slot] = 0ull;
-          S.scnt[slot] = 0u;
-        }
-      }
-    }
-  }
-}
-
-// ======================================================================
-// Long-segment log-sum-exp: per-window partials, combined in window order
-// by the last warp to arrive.  Returns the segment total in every lane of
-// the finalising warp; `fin` tells whether this warp finalised.
-// ======================================================================
-__device__ __forceinline__ bool long_lse_arrive(const LayoutView& L, const WaveState& S, const WinCtx& x,
-                                                int64_t lslot, int64_t lwslot, float2 part, int lane,
-                                                float2& total) {
-  uint32_t prev = 0;
-  if (lane == 31) {
-    const int64_t w0 = L.seg_pos[x.meta.seg] / WIN;
-    S.spart[lwslot + x.meta.lwin0 + (x.w - w0)] = part;
-    __threadfence();
-    prev = atomicAdd(S.scnt + lslot + x.meta.lseg, 1u);
-  }
-  prev = __shfl_sync(FULL, prev, 31);
-  if (prev != (uint32_t)x.meta.lcnt - 1u) return false;
-  __threadfence();
-  float2 acc = LogAdd::identity();
-  const volatile float2* pp = S.spart + lwslot + x.meta.lwin0;
-  for (int j = lane; j < x.meta.lcnt; j += 32) {
-    float2 v;
-    v.x = pp[j].x;
-    v.y = pp[j].y;
-    acc = LogAdd::combine(acc, v);
-  }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) {
-    float2 o = make_float2(__shfl_xor_sync(FULL, acc.x, d), __shfl_xor_sync(FULL, acc.y, d));
-    acc = (lane & d) ? LogAdd::combine(o, acc) : LogAdd::combine(acc, o);
-  }
-  if (lane == 0) S.scnt[lslot + x.meta.lseg] = 0u;
-  total = acc;
-  return true;
-}
+__device__ __forceinline__ float decode_max(uint32_t k) { return k ? fkey_inv(k) : neg_inf(); }
 
 __device__ __forceinline__ float lse_value(float2 v) {
   return v.x == neg_inf() ? neg_inf() : v.x + logf(v.y);
@@ -266,39 +165,206 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-__device__ __forceinline__ float decode_max(uint32_t k) { return k ? fkey_inv(k) : neg_inf(); }
+// Raw frontier entries of one token at the arcs' gather states; for the
+// first position the start weights are read instead (flag set).
+__device__ __forceinline__ void gather_raw(const unsigned long long* __restrict__ base,
+                                           const int32_t (&st)[APL], unsigned long long (&r)[APL]) {
+#pragma unroll
+  for (int k = 0; k < APL; ++k) r[k] = __ldg(base + st[k]);
+}
 
 // ======================================================================
-// Forward step (Alg. 2 forward loop; Sec. 5.2)
+// Viterbi step (Alg. 1 inner loop; Sec. 5.1)
 // ======================================================================
-__global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
+__device__ __forceinline__ void vit_write(const LayoutView& L, const WaveState& S, int64_t cb, int32_t s,
+                                          int32_t sl, unsigned long long key, unsigned long long* aout,
+                                          uint32_t tag) {
+  S.bp[cb + sl] = key ? (int32_t)(~(uint32_t)key) : -1;
+  if (key) aout[__ldg(L.seg_state + s)] = tagged_make(fkey_inv((uint32_t)(key >> 32)), tag);
+}
+
+__global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
   const int64_t nw = warps_total();
+  Group G;
+  G.g = -1; G.hi = -1; G.lo = 0;
+  int32_t tp = 0, tb = 0, tt = 0;
+  int64_t tcb = 0, tlb = 0;
   for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
-    const ItemCtx c = resolve(W, item);
-    const WinCtx x = load_win(L, c.sym, c.wslice, lane);
+    if (item >= G.hi) {
+      find_group(L, W, item, G);
+      if (lane < G.cnt) {
+        tp = group_token(W, G, lane);
+        tb = __ldg(T.b + tp); tt = __ldg(T.t + tp); tcb = __ldg(T.cbase + tp); tlb = __ldg(T.lbase + tp);
+      }
+    }
+    const Win x = load_win(L, G.wbase + (item - G.lo), lane);
     const int64_t base = x.w * WIN + lane * APL;
     const int4 s4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
     const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
     const int32_t src[APL] = {s4.x, s4.y, s4.z, s4.w};
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
-    const bool is_long = x.meta.lseg >= 0;
+    const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
-    for (int j = 0; j < c.cnt; ++j) {
-      const int32_t p = token_of(W, c, j);
-      const int32_t b = T.b[p], t = T.t[p];
+    unsigned long long rn[APL];
+    {
+      const int32_t b0 = __shfl_sync(FULL, tb, 0), t0 = __shfl_sync(FULL, tt, 0);
+      if (t0 > 1) gather_raw(S.alpha + ((int64_t)b0 * 2 + ((t0 - 1) & 1)) * S.Q, src, rn);
+    }
+    for (int j = 0; j < G.cnt; ++j) {
+      const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
+      unsigned long long rc[APL];
+#pragma unroll
+      for (int k = 0; k < APL; ++k) rc[k] = rn[k];
+      if (j + 1 < G.cnt) {  // prefetch the next token's frontier entries
+        const int32_t b1 = __shfl_sync(FULL, tb, j + 1), t1 = __shfl_sync(FULL, tt, j + 1);
+        if (t1 > 1) gather_raw(S.alpha + ((int64_t)b1 * 2 + ((t1 - 1) & 1)) * S.Q, src, rn);
+      }
       float a[APL];
       if (t == 1) {
 #pragma unroll
         for (int k = 0; k < APL; ++k) a[k] = __ldg(S.theta_s + src[k]);
       } else {
-        const float mprev = decode_max(S.mkey[p - 1]);
-        const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+        const uint32_t tg = tag_base + (uint32_t)(p - 1);
+#pragma unroll
+        for (int k = 0; k < APL; ++k) a[k] = tagged_value(rc[k], tg);
+      }
+      unsigned long long key[APL];
+#pragma unroll
+      for (int k = 0; k < APL; ++k) {
+        const float cand = __fadd_rn(a[k], th[k]);
+        key[k] = (cand == neg_inf()) ? 0ull
+                                     : (((unsigned long long)fkey(cand) << 32) |
+                                        (unsigned long long)(~(uint32_t)(base + k)));
+      }
+      unsigned long long full[APL];
+      window_scan<MaxKey>(key, x.h, lane, full);
+      const int64_t cb = shfl64(tcb, j);
+      unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
+      const uint32_t tag = tag_base + (uint32_t)p;
+      if (!is_long) {
+        int cum = x.hb;
+#pragma unroll
+        for (int k = 0; k < APL; ++k) {
+          cum += (x.h >> k) & 1u;
+          const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
+          if (tail) {
+            const int32_t s = x.seg + cum - 1;
+            vit_write(L, S, cb, s, s - G.segbase, full[k], aout, tag);
+          }
+        }
+      } else {
+        const int64_t lb = shfl64(tlb, j);
+        if (lane == 31) {
+          // a destination segment that spans warps: packed 64-bit atomicMax
+          const int64_t slot = lb + x.lseg;
+          atomicMax(S.skey + slot, full[APL - 1]);
+          __threadfence();
+          const uint32_t prev = atomicAdd(S.scnt + slot, 1u);
+          if (prev == (uint32_t)x.lcnt - 1u) {
+            __threadfence();
+            const unsigned long long kf = atomicMax(S.skey + slot, 0ull);
+            vit_write(L, S, cb, x.seg, x.seg - G.segbase, kf, aout, tag);
+            S.skey[slot] = 0ull;
+            S.scnt[slot] = 0u;
+          }
+        }
+      }
+    }
+  }
+}
+
+// ======================================================================
+// Long-segment log-sum-exp: per-window partials, combined in window order
+// by the last warp to arrive.  Returns the segment total in every lane of
+// the finalising warp; `fin` tells whether this warp finalised.
+// ======================================================================
+__device__ __forceinline__ bool long_lse_arrive(const LayoutView& L, const WaveState& S, const Win& x,
+                                                int64_t lslot, int64_t lwslot, float2 part, int lane,
+                                                float2& total) {
+  uint32_t prev = 0;
+  if (lane == 31) {
+    const int64_t w0 = __ldg(L.seg_pos + x.seg) / WIN;
+    S.spart[lwslot + x.lwin0 + (x.w - w0)] = part;
+    __threadfence();
+    prev = atomicAdd(S.scnt + lslot + x.lseg, 1u);
+  }
+  prev = __shfl_sync(FULL, prev, 31);
+  if (prev != (uint32_t)x.lcnt - 1u) return false;
+  __threadfence();
+  float2 acc = LogAdd::identity();
+  const volatile float2* pp = S.spart + lwslot + x.lwin0;
+  for (int j = lane; j < x.lcnt; j += 32) {
+    float2 v;
+    v.x = pp[j].x;
+    v.y = pp[j].y;
+    acc = LogAdd::combine(acc, v);
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    float2 o = make_float2(__shfl_xor_sync(FULL, acc.x, d), __shfl_xor_sync(FULL, acc.y, d));
+    acc = (lane & d) ? LogAdd::combine(o, acc) : LogAdd::combine(acc, o);
+  }
+  if (lane == 0) S.scnt[lslot + x.lseg] = 0u;
+  total = acc;
+  return true;
+}
+
+// ======================================================================
+// Forward step (Alg. 2 forward loop; Sec. 5.2)
+// ======================================================================
+__global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t tag_base = *S.epoch + S.tok0;
+  const int64_t nw = warps_total();
+  Group G;
+  G.g = -1; G.hi = -1; G.lo = 0;
+  int32_t tp = 0, tb = 0, tt = 0;
+  int64_t tcb = 0, tlb = 0, tlw = 0;
+  float tm = 0.f;
+  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
+    if (item >= G.hi) {
+      find_group(L, W, item, G);
+      if (lane < G.cnt) {
+        tp = group_token(W, G, lane);
+        tb = __ldg(T.b + tp); tt = __ldg(T.t + tp); tcb = __ldg(T.cbase + tp);
+        tlb = __ldg(T.lbase + tp); tlw = __ldg(T.lwbase + tp);
+        tm = tt > 1 ? decode_max(S.mkey[tp - 1]) : 0.f;
+      }
+    }
+    const Win x = load_win(L, G.wbase + (item - G.lo), lane);
+    const int64_t base = x.w * WIN + lane * APL;
+    const int4 s4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
+    const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
+    const int32_t src[APL] = {s4.x, s4.y, s4.z, s4.w};
+    const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
+    const bool is_long = x.lseg >= 0;
+    const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
+    unsigned long long rn[APL];
+    {
+      const int32_t b0 = __shfl_sync(FULL, tb, 0), t0 = __shfl_sync(FULL, tt, 0);
+      if (t0 > 1) gather_raw(S.alpha + ((int64_t)b0 * 2 + ((t0 - 1) & 1)) * S.Q, src, rn);
+    }
+    for (int j = 0; j < G.cnt; ++j) {
+      const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
+      const float mprev = __shfl_sync(FULL, tm, j);
+      unsigned long long rc[APL];
+#pragma unroll
+      for (int k = 0; k < APL; ++k) rc[k] = rn[k];
+      if (j + 1 < G.cnt) {
+        const int32_t b1 = __shfl_sync(FULL, tb, j + 1), t1 = __shfl_sync(FULL, tt, j + 1);
+        if (t1 > 1) gather_raw(S.alpha + ((int64_t)b1 * 2 + ((t1 - 1) & 1)) * S.Q, src, rn);
+      }
+      float a[APL];
+      if (t == 1) {
+#pragma unroll
+        for (int k = 0; k < APL; ++k) a[k] = __ldg(S.theta_s + src[k]);
+      } else {
         const uint32_t tg = tag_base + (uint32_t)(p - 1);
 #pragma unroll
         for (int k = 0; k < APL; ++k) {
-          const float r = tagged_value(__ldg(ab + src[k]), tg);
+          const float r = tagged_value(rc[k], tg);
           a[k] = (r == neg_inf() || mprev == neg_inf()) ? neg_inf() : r - mprev;
         }
       }
@@ -310,7 +376,7 @@ __global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, Work
       }
       float2 full[APL];
       window_scan<LogAdd>(e, x.h, lane, full);
-      const int64_t cb = T.cbase[p];
+      const int64_t cb = shfl64(tcb, j);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
       const uint32_t tag = tag_base + (uint32_t)p;
       float rmax = neg_inf();
@@ -321,21 +387,20 @@ __global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, Work
           cum += (x.h >> k) & 1u;
           const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
           if (tail) {
-            const int32_t s = x.meta.seg + cum - 1;
+            const int32_t s = x.seg + cum - 1;
             const float r = lse_value(full[k]);
-            S.rc[cb + (s - x.segbase)] = r;
-            if (r != neg_inf()) aout[L.seg_state[s]] = tagged_make(r, tag);
+            S.rc[cb + (s - G.segbase)] = r;
+            if (r != neg_inf()) aout[__ldg(L.seg_state + s)] = tagged_make(r, tag);
             rmax = fmaxf(rmax, r);
           }
         }
       } else {
         float2 tot;
-        if (long_lse_arrive(L, S, x, T.lbase[p], T.lwbase[p], full[APL - 1], lane, tot)) {
-          const int32_t s = x.meta.seg;
+        if (long_lse_arrive(L, S, x, shfl64(tlb, j), shfl64(tlw, j), full[APL - 1], lane, tot)) {
           const float r = lse_value(tot);
           if (lane == 0) {
-            S.rc[cb + (s - x.segbase)] = r;
-            if (r != neg_inf()) aout[L.seg_state[s]] = tagged_make(r, tag);
+            S.rc[cb + (x.seg - G.segbase)] = r;
+            if (r != neg_inf()) aout[__ldg(L.seg_state + x.seg)] = tagged_make(r, tag);
           }
           rmax = r;
         }
@@ -356,26 +421,33 @@ __global__ void __launch_bounds__(KT) k_scatter_alpha(LayoutView L, TokenView T,
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
   const int64_t nw = warps_total();
+  Group G;
+  G.g = -1; G.hi = -1; G.lo = 0;
+  int32_t tp = 0, tb = 0, tt = 0, tn = 0;
+  int64_t tcb = 0;
   for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
-    const ItemCtx c = resolve(W, item);
-    const WinCtx x = load_win(L, c.sym, c.wslice, lane);
-    if (!x.h) {
-      // nothing starts in this lane; the loop below is empty
+    if (item >= G.hi) {
+      find_group(L, W, item, G);
+      if (lane < G.cnt) {
+        tp = group_token(W, G, lane);
+        tb = __ldg(T.b + tp); tt = __ldg(T.t + tp); tcb = __ldg(T.cbase + tp); tn = S.bw_n[tb];
+      }
     }
-    for (int j = 0; j < c.cnt; ++j) {
-      const int32_t p = token_of(W, c, j);
-      const int32_t b = T.b[p], t = T.t[p];
-      if (S.bw_n[b] <= t_bwd) continue;  // this string's frontier was not overwritten
-      const int64_t cb = T.cbase[p];
+    const Win x = load_win(L, G.wbase + (item - G.lo), lane);
+    if (!__any_sync(FULL, x.h != 0u)) continue;
+    for (int j = 0; j < G.cnt; ++j) {
+      if (__shfl_sync(FULL, tn, j) <= t_bwd) continue;  // this string's frontier was not overwritten
+      const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
+      const int64_t cb = shfl64(tcb, j);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
       const uint32_t tag = tag_base + (uint32_t)p;
       int cum = x.hb;
 #pragma unroll
       for (int k = 0; k < APL; ++k) {
         if ((x.h >> k) & 1u) {
-          const int32_t s = x.meta.seg + cum;
-          const float r = S.rc[cb + (s - x.segbase)];
-          if (r != neg_inf()) aout[L.seg_state[s]] = tagged_make(r, tag);
+          const int32_t s = x.seg + cum;
+          const float r = S.rc[cb + (s - G.segbase)];
+          if (r != neg_inf()) aout[__ldg(L.seg_state + s)] = tagged_make(r, tag);
           ++cum;
         }
       }
@@ -387,20 +459,48 @@ __global__ void __launch_bounds__(KT) k_scatter_alpha(LayoutView L, TokenView T,
 // Backward step fused with the expected counts (Alg. 2 backward loop and
 // count loop; Sec. 5.2).  Segments are by source state.
 // ======================================================================
-__global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, WorkView W, WaveState S,
-                                                 CountView C) {
+__global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L, TokenView T, WorkView W,
+                                                                    WaveState S, CountView C) {
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
   const int64_t nw = warps_total();
+  Group G;
+  G.g = -1; G.hi = -1; G.lo = 0;
+  // lane j: token j of the group
+  int32_t tp = 0, tb = 0, tt = 0, tn = 0;
+  int64_t tlb = 0, tlw = 0;
+  float tK = 0.f, tm = 0.f, te = 0.f, tw = 0.f;
+  double tE = 0.0;
+  bool tlive = false;
   for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
-    const ItemCtx c = resolve(W, item);
-    const WinCtx x = load_win(L, c.sym, c.wslice, lane);
+    if (item >= G.hi) {
+      find_group(L, W, item, G);
+      if (lane < G.cnt) {
+        tp = group_token(W, G, lane);
+        tb = __ldg(T.b + tp); tt = __ldg(T.t + tp);
+        tlb = __ldg(T.lbase_b + tp); tlw = __ldg(T.lwbase_b + tp);
+        tn = S.bw_n[tb];
+        const double lz = S.logz[tb];
+        tlive = lz != -INFINITY;
+        te = (tt == tn) ? 0.f : decode_max(S.ekey[tp]);
+        tE = (tt == tn) ? 0.0 : S.esum[tp + 1] + (double)te;
+        const double Ctm1 = (tt == 1) ? 0.0 : S.csum[tp - 1];
+        tK = (float)(Ctm1 + tE - lz);
+        tm = (tt == 1) ? 0.f : decode_max(S.mkey[tp - 1]);
+        tw = S.gweight ? S.gweight[tb] : 1.f;
+      } else {
+        tlive = false;
+      }
+      // E_t for the next position's launch: written once per token
+      if (item == G.lo && lane < G.cnt && tlive) S.esum[tp] = tE;
+    }
+    const Win x = load_win(L, G.wbase + (item - G.lo), lane);
     const int64_t base = x.w * WIN + lane * APL;
     const int4 d4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
     const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
     const int32_t dst[APL] = {d4.x, d4.y, d4.z, d4.w};
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
-    const bool is_long = x.meta.lseg >= 0;
+    const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
     // segment (source state) of each arc
     int32_t qs[APL];
@@ -409,26 +509,22 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Work
 #pragma unroll
       for (int k = 0; k < APL; ++k) {
         cum += (x.h >> k) & 1u;
-        const int32_t s = is_long ? x.meta.seg : x.meta.seg + cum - 1;
-        qs[k] = (th[k] == neg_inf()) ? 0 : __ldg(L.seg_state + s);
+        const int32_t s = is_long ? x.seg : x.seg + cum - 1;
+        qs[k] = __ldg(L.seg_state + s);  // padding arcs belong to the window's last segment
       }
     }
     double gacc[APL] = {0.0, 0.0, 0.0, 0.0};
-    for (int j = 0; j < c.cnt; ++j) {
-      const int32_t p = token_of(W, c, j);
-      const int32_t b = T.b[p], t = T.t[p];
-      const double lz = S.logz[b];
-      if (lz == -INFINITY) continue;
-      const int32_t n = S.bw_n[b];
+    for (int j = 0; j < G.cnt; ++j) {
+      if (!__shfl_sync(FULL, tlive, j)) continue;
+      const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
+      const int32_t n = __shfl_sync(FULL, tn, j);
       // beta_t at the destinations
       float bv[APL];
-      double Et;
       if (t == n) {
 #pragma unroll
         for (int k = 0; k < APL; ++k) bv[k] = __ldg(S.theta_f + dst[k]);
-        Et = 0.0;
       } else {
-        const float et = decode_max(S.ekey[p]);
+        const float et = __shfl_sync(FULL, te, j);
         const unsigned long long* bb = S.beta + ((int64_t)b * 2 + (t & 1)) * S.Q;
         const uint32_t tg = tag_base + (uint32_t)p;
 #pragma unroll
@@ -436,9 +532,24 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Work
           const float u = tagged_value(__ldg(bb + dst[k]), tg);
           bv[k] = (u == neg_inf() || et == neg_inf()) ? neg_inf() : u - et;
         }
-        Et = S.esum[p + 1] + (double)et;
       }
-      if (c.wslice == 0 && lane == 0) S.esum[p] = Et;
+      // alpha_{t-1} at the sources (one state per segment: cached loads)
+      float ah[APL];
+      {
+        const float mprev = __shfl_sync(FULL, tm, j);
+        if (t == 1) {
+#pragma unroll
+          for (int k = 0; k < APL; ++k) ah[k] = __ldg(S.theta_s + qs[k]);
+        } else {
+          const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+          const uint32_t tga = tag_base + (uint32_t)(p - 1);
+#pragma unroll
+          for (int k = 0; k < APL; ++k) {
+            const float r = tagged_value(__ldg(ab + qs[k]), tga);
+            ah[k] = (r == neg_inf() || mprev == neg_inf()) ? neg_inf() : r - mprev;
+          }
+        }
+      }
       float v[APL];
 #pragma unroll
       for (int k = 0; k < APL; ++k) v[k] = th[k] + bv[k];
@@ -459,17 +570,16 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Work
             cum += (x.h >> k) & 1u;
             const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
             if (tail) {
-              const int32_t s = x.meta.seg + cum - 1;
               const float u = lse_value(full[k]);
-              if (u != neg_inf()) bout[L.seg_state[s]] = tagged_make(u, tag);
+              if (u != neg_inf()) bout[qs[k]] = tagged_make(u, tag);
               umax = fmaxf(umax, u);
             }
           }
         } else {
           float2 tot;
-          if (long_lse_arrive(L, S, x, T.lbase_b[p], T.lwbase_b[p], full[APL - 1], lane, tot)) {
+          if (long_lse_arrive(L, S, x, shfl64(tlb, j), shfl64(tlw, j), full[APL - 1], lane, tot)) {
             const float u = lse_value(tot);
-            if (lane == 0 && u != neg_inf()) bout[L.seg_state[x.meta.seg]] = tagged_make(u, tag);
+            if (lane == 0 && u != neg_inf()) bout[__ldg(L.seg_state + x.seg)] = tagged_make(u, tag);
             umax = u;
           }
         }
@@ -477,25 +587,12 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Work
         if (lane == 0 && umax != neg_inf()) atomicMax(S.ekey + p - 1, fkey(umax));
       }
       // posteriors gamma_t(k) = exp(alpha_{t-1}[src] + theta_k + beta_t[dst] - log Z)
-      const double Ctm1 = (t == 1) ? 0.0 : S.csum[p - 1];
-      const float K = (float)(Ctm1 + Et - lz);
-      const float mprev = (t == 1) ? 0.f : decode_max(S.mkey[p - 1]);
-      const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
-      const uint32_t tga = tag_base + (uint32_t)(p - 1);
-      const float gw = S.gweight ? S.gweight[b] : 1.f;
+      const float K = __shfl_sync(FULL, tK, j);
+      const float gw = __shfl_sync(FULL, tw, j);
 #pragma unroll
       for (int k = 0; k < APL; ++k) {
-        if (v[k] == neg_inf()) continue;
-        float ah;
-        if (t == 1) {
-          ah = __ldg(S.theta_s + qs[k]);
-        } else {
-          const float r = tagged_value(__ldg(ab + qs[k]), tga);
-          ah = (r == neg_inf() || mprev == neg_inf()) ? neg_inf() : r - mprev;
-        }
-        if (ah == neg_inf()) continue;
-        const float g = expf(ah + v[k] + K);
-        gacc[k] += (double)g * (double)gw;
+        if (v[k] == neg_inf() || ah[k] == neg_inf()) continue;
+        gacc[k] += (double)(__expf(ah[k] + v[k] + K) * gw);
       }
     }
     // accumulate this item's counts
@@ -690,39 +787,58 @@ inline int check_launch(const char* what) {
   return FST_OK;
 }
 
-inline unsigned grid_clamp(int64_t nitems, int grid) {
+// Step kernels are grid-stride loops: the grid is the number of blocks that
+// can be resident at once (all warps advance through the work list
+// together, which keeps the frontiers being gathered in L2).
+template <class K>
+inline int resident_blocks(K kernel, int* cache) {
+  if (*cache <= 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, KT, 0) != cudaSuccess || nb <= 0) {
+      (void)cudaGetLastError();
+      nb = 1;
+    }
+    *cache = nb;
+  }
+  return *cache;
+}
+
+inline unsigned grid_clamp(int64_t nitems, int num_sms, int per_sm) {
   int64_t need = (nitems + (KT / 32) - 1) / (KT / 32);
   if (need < 1) need = 1;
-  return (unsigned)(need < grid ? need : grid);
+  const int64_t cap = (int64_t)num_sms * per_sm;
+  return (unsigned)(need < cap ? need : cap);
 }
+
+int g_occ[4] = {0, 0, 0, 0};
 
 }  // namespace
 
 int launch_vit_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S, int grid,
                     cudaStream_t s) {
   if (W.nitems <= 0) return FST_OK;
-  k_vit_step<<<grid_clamp(W.nitems, grid), KT, 0, s>>>(L, T, W, S);
+  k_vit_step<<<grid_clamp(W.nitems, grid, resident_blocks(k_vit_step, &g_occ[0])), KT, 0, s>>>(L, T, W, S);
   return check_launch("k_vit_step");
 }
 
 int launch_fwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S, int grid,
                     cudaStream_t s) {
   if (W.nitems <= 0) return FST_OK;
-  k_fwd_step<<<grid_clamp(W.nitems, grid), KT, 0, s>>>(L, T, W, S);
+  k_fwd_step<<<grid_clamp(W.nitems, grid, resident_blocks(k_fwd_step, &g_occ[1])), KT, 0, s>>>(L, T, W, S);
   return check_launch("k_fwd_step");
 }
 
 int launch_bwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
                     const CountView& C, int grid, cudaStream_t s) {
   if (W.nitems <= 0) return FST_OK;
-  k_bwd_step<<<grid_clamp(W.nitems, grid), KT, 0, s>>>(L, T, W, S, C);
+  k_bwd_step<<<grid_clamp(W.nitems, grid, resident_blocks(k_bwd_step, &g_occ[2])), KT, 0, s>>>(L, T, W, S, C);
   return check_launch("k_bwd_step");
 }
 
 int launch_scatter_alpha(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
                          int32_t t_bwd, int grid, cudaStream_t s) {
   if (W.nitems <= 0) return FST_OK;
-  k_scatter_alpha<<<grid_clamp(W.nitems, grid), KT, 0, s>>>(L, T, W, S, t_bwd);
+  k_scatter_alpha<<<grid_clamp(W.nitems, grid, resident_blocks(k_scatter_alpha, &g_occ[3])), KT, 0, s>>>(L, T, W, S, t_bwd);
   return check_launch("k_scatter_alpha");
 }
 

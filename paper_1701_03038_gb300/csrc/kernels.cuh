@@ -80,6 +80,7 @@ struct CountView {
   double* cnt64;      // [P_bwd]
 };
 
+// `grid` of the step launchers is the device's SM count.
 int launch_vit_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
                     int grid, cudaStream_t s);
 int launch_fwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,

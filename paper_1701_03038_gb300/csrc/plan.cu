@@ -411,7 +411,8 @@ WorkView wave_work(const Wave& W, int32_t t, bool fwd) {
   return V;
 }
 
-int step_grid(const fst_s* f, int64_t nitems) { return grid_for(nitems, 256, f->num_sms, 8); }
+// the launchers size step grids from the SM count and the kernel's occupancy
+int step_grid(const fst_s* f, int64_t) { return f->num_sms; }
 
 int run_begin(fst_plan_s* P, cudaStream_t s, bool fb) {
   const uint32_t span = (uint32_t)std::min<int64_t>(P->N + 1, 0x7fffffff);
