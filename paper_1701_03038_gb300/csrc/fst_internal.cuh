@@ -27,7 +27,7 @@ namespace fstgpu {
 constexpr int WARP = 32;
 constexpr int APL = 4;            // arcs per lane
 constexpr int WIN = WARP * APL;   // arcs per window
-constexpr int GMAX = 16;          // tokens per group (same symbol, same step)
+constexpr int GMAX = 32;          // tokens per group (same symbol, same step): one per lane
 constexpr unsigned FULL = 0xffffffffu;
 
 // Window metadata, 32 bytes: two 16-byte loads.

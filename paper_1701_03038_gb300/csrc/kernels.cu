@@ -33,6 +33,7 @@ constexpr int KT = 256;  // threads per block of the step kernels
 #define KT_MIN_BLOCKS_BWD 2
 #endif
 
+
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
 struct MaxKey {
@@ -143,6 +144,7 @@ __device__ __forceinline__ Win load_win(const LayoutView& L, int64_t w, int lane
          (q > 2 ? __popc(m1.z) : 0);
   return x;
 }
+
 
 __device__ __forceinline__ int64_t warp_id_global() {
   return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

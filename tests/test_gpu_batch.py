@@ -75,8 +75,10 @@ def test_waves_match_single_wave(c2s):
         p.viterbi()
         p.forward_backward()
     torch.cuda.synchronize()
+    # Viterbi is exact whatever the grouping; forward-backward sums in a
+    # grouping-dependent order, so both splits are held to the oracle
     assert torch.equal(p1.scores, p2.scores) and torch.equal(p1.paths, p2.paths)
-    assert torch.allclose(p1.logz, p2.logz, rtol=1e-12, atol=0)
+    check_batch_fb(o, strs, p1.logz[:strs.count], p1.counts[:o.A])
     check_batch_viterbi(o, strs, dict(scores=p2.scores[:strs.count], paths=p2.paths[:len(strs.ids)],
                                       olabels=p2.olabels[:len(strs.ids)], status=p2.status[:strs.count]))
     check_batch_fb(o, strs, p2.logz[:strs.count], p2.counts[:o.A])
@@ -183,3 +185,17 @@ def test_iid_strings_no_path_status():
     assert (r["status"].cpu().numpy() == 2).any()
     rf = f.forward_backward_batch(ids, off)
     check_batch_fb(o, strs, rf["logz"], rf["counts"])
+
+
+def test_large_groups():
+    # few symbols and many strings: most positions have groups of 32 tokens
+    # with the same symbol (one window load serves up to 32 strings)
+    from paper_1701_03038_gb300.fst import Fst
+    fa = synth.random_fst(400, 3, 6, 30000, label_law="zipf", src_law="lognormal", mean_degree=75.0,
+                          dirichlet=0.5, seed=31)
+    strs = synth.make_strings(fa, 300, 5, 40, seed=32)
+    f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+    ids, off = _dev(strs)
+    check_batch_viterbi(o, strs, f.viterbi_batch(ids, off))
+    r = f.forward_backward_batch(ids, off)
+    check_batch_fb(o, strs, r["logz"], r["counts"])
