@@ -74,6 +74,18 @@ __global__ void k_convert_states(const float* __restrict__ w, int32_t Q, int kin
   out[q] = __fadd_rn(th, 0.0f);
 }
 
+// bit q of word q / 32 is set when w[q] is finite
+__global__ void k_finite_bitmap(const float* __restrict__ w, int32_t Q, uint32_t* __restrict__ bm, int32_t W) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= W) return;
+  uint32_t m = 0;
+  for (int k = 0; k < 32; ++k) {
+    const int64_t q = i * 32 + k;
+    if (q < Q && w[q] != -INFINITY) m |= 1u << k;
+  }
+  bm[i] = m;
+}
+
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -154,8 +166,10 @@ struct PlainWs {
   int32_t* bw_n = nullptr;
   int64_t* bw_off = nullptr;
   uint32_t *epoch = nullptr, *clear = nullptr;
+  uint32_t *abm = nullptr, *bbm = nullptr;  // [3][W] live-state bitmaps
   int64_t max_lseg = 0, max_lwin = 0;
   ~PlainWs() {
+    dfree(abm); dfree(bbm);
     dfree(alpha); dfree(beta); dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(zero64);
     dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(skey); dfree(scnt);
     dfree(spart); dfree(cnt); dfree(comp); dfree(counts_out); dfree(paths); dfree(olabels); dfree(qfinal);
@@ -183,7 +197,8 @@ int plain_init(fst_s* f) {
       (rc = dalloc(&w->scnt, w->max_lseg)) || (rc = dalloc(&w->spart, w->max_lwin)) ||
       (rc = dalloc(&w->qfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
       (rc = dalloc(&w->logz, 1)) || (rc = dalloc(&w->bw_n, 1)) || (rc = dalloc(&w->bw_off, 1)) ||
-      (rc = dalloc(&w->epoch, 2)) || (rc = dalloc(&w->clear, 1)))
+      (rc = dalloc(&w->epoch, 2)) || (rc = dalloc(&w->clear, 1)) || (rc = dalloc(&w->abm, 3 * (int64_t)f->W)) ||
+      (rc = dalloc(&w->bbm, 3 * (int64_t)f->W)))
     return rc;
   FST_CUDA(cudaMemset(w->alpha, 0, (size_t)2 * Q * sizeof(unsigned long long)));
   FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(unsigned long long)));
@@ -281,7 +296,19 @@ WaveState plain_state(fst_s* f) {
   S.gweight = nullptr;
   S.bw_n = w->bw_n;
   S.bw_off = w->bw_off;
+  S.abm = w->abm;
+  S.bbm = w->bbm;
+  S.bm_start = f->bm_start;
+  S.bm_final = f->bm_final;
+  S.W = f->W;
+  S.bm_rot = f->W;
   return S;
+}
+
+// Clear rotation r of a [3][W] bitmap set before the launch that fills it.
+int clear_rot(uint32_t* bm, int32_t r, int64_t words, cudaStream_t s) {
+  FST_CUDA(cudaMemsetAsync(bm + (int64_t)r * words, 0, (size_t)words * 4, s));
+  return FST_OK;
 }
 
 WorkView single_work(int32_t p, int32_t sym, int64_t nitems) {
@@ -377,6 +404,10 @@ extern "C" int fst_create(int32_t num_states, int64_t num_arcs, const int32_t* s
     } else if (A > 0) {
       k_fill_i32<<<nblk(A), TB, 0, s>>>(f->olabel, A, -1);
     }
+    f->W = (int32_t)((Q + 31) / 32);
+    if ((rc = dalloc(&f->bm_start, f->W)) || (rc = dalloc(&f->bm_final, f->W))) break;
+    k_finite_bitmap<<<nblk(f->W), TB, 0, s>>>(f->theta_s, f->Q, f->bm_start, f->W);
+    k_finite_bitmap<<<nblk(f->W), TB, 0, s>>>(f->theta_f, f->Q, f->bm_final, f->W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { rc = cuda_fail(e, "fst_create kernels"); break; }
     if ((rc = read_err_flag(d_err, "fst_create"))) break;
@@ -400,6 +431,8 @@ extern "C" int fst_destroy(fst_t* f) {
   free_layout(f->bwd);
   dfree(f->theta_s);
   dfree(f->theta_f);
+  dfree(f->bm_start);
+  dfree(f->bm_final);
   dfree(f->olabel);
   dfree(f->sym_arc);
   free(f->h_sym_arc);
@@ -481,6 +514,7 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
   for (int32_t t = 1; t <= n; ++t) {
     const int32_t a = ids[t - 1];
     const int64_t nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
+    if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
     if ((rc = launch_vit_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
   }
   if ((rc = launch_vit_final(Lf, w->tok_sym, w->cbase, S, 1, w->score, w->qfinal, w->status, s))) return rc;
@@ -526,6 +560,7 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   for (int32_t t = 1; t <= n; ++t) {
     const int32_t a = ids[t - 1];
     const int64_t nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
+    if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
     if ((rc = launch_fwd_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
   }
   if ((rc = launch_fb_final(Lf, w->tok_sym, w->cbase, S, 1, w->logz, w->status, s))) return rc;
@@ -541,6 +576,7 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
       }
       const int32_t a = ids[t - 1];
       const int64_t nitems = f->bwd.h_sym_win[a + 1] - f->bwd.h_sym_win[a];
+      if (t >= 2 && (rc = clear_rot(w->bbm, (t - 1) % 3, f->W, s))) return rc;
       if ((rc = launch_bwd_step(Lb, T, single_work(t - 1, a, nitems), S, C, step_grid(f, nitems), s))) return rc;
     }
     if ((rc = launch_counts_out(f->bwd.arc_id, f->bwd.P, C, w->counts_out, s))) return rc;

@@ -72,6 +72,9 @@ struct fst_s {
   fstgpu::Layout fwd, bwd;
   float* theta_s = nullptr;    // [Q]
   float* theta_f = nullptr;    // [Q]
+  int32_t W = 0;               // 32-bit words of a state bitmap, ceil(Q / 32)
+  uint32_t* bm_start = nullptr;  // [W] states with a finite start weight
+  uint32_t* bm_final = nullptr;  // [W] states with a finite final weight
   int32_t* olabel = nullptr;   // [A] by caller arc id
   int64_t* sym_arc = nullptr;  // [m+1] R offsets (device)
   int64_t* h_sym_arc = nullptr;

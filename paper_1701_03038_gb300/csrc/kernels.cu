@@ -167,22 +167,29 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Raw frontier entries of one token at the arcs' gather states; for the
-// first position the start weights are read instead (flag set).
-__device__ __forceinline__ void gather_raw(const unsigned long long* __restrict__ base,
-                                           const int32_t (&st)[APL], unsigned long long (&r)[APL]) {
+// Liveness of the arcs' gather states (bit k = arc k) in a frontier bitmap.
+__device__ __forceinline__ uint32_t live_bits(const uint32_t* __restrict__ bm, const int32_t (&st)[APL]) {
+  uint32_t m = 0;
 #pragma unroll
-  for (int k = 0; k < APL; ++k) r[k] = __ldg(base + st[k]);
+  for (int k = 0; k < APL; ++k) m |= ((__ldg(bm + (st[k] >> 5)) >> (st[k] & 31)) & 1u) << k;
+  return m;
 }
+
+__device__ __forceinline__ void set_live(uint32_t* bm, int32_t q) { atomicOr(bm + (q >> 5), 1u << (q & 31)); }
+
 
 // ======================================================================
 // Viterbi step (Alg. 1 inner loop; Sec. 5.1)
 // ======================================================================
 __device__ __forceinline__ void vit_write(const LayoutView& L, const WaveState& S, int64_t cb, int32_t s,
                                           int32_t sl, unsigned long long key, unsigned long long* aout,
-                                          uint32_t tag) {
+                                          uint32_t tag, uint32_t* bmout) {
   S.bp[cb + sl] = key ? (int32_t)(~(uint32_t)key) : -1;
-  if (key) aout[__ldg(L.seg_state + s)] = tagged_make(fkey_inv((uint32_t)(key >> 32)), tag);
+  if (key) {
+    const int32_t q = __ldg(L.seg_state + s);
+    aout[q] = tagged_make(fkey_inv((uint32_t)(key >> 32)), tag);
+    set_live(bmout, q);
+  }
 }
 
 __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
@@ -209,28 +216,22 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
     const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
-    unsigned long long rn[APL];
-    {
-      const int32_t b0 = __shfl_sync(FULL, tb, 0), t0 = __shfl_sync(FULL, tt, 0);
-      if (t0 > 1) gather_raw(S.alpha + ((int64_t)b0 * 2 + ((t0 - 1) & 1)) * S.Q, src, rn);
-    }
     for (int j = 0; j < G.cnt; ++j) {
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
-      unsigned long long rc[APL];
-#pragma unroll
-      for (int k = 0; k < APL; ++k) rc[k] = rn[k];
-      if (j + 1 < G.cnt) {  // prefetch the next token's frontier entries
-        const int32_t b1 = __shfl_sync(FULL, tb, j + 1), t1 = __shfl_sync(FULL, tt, j + 1);
-        if (t1 > 1) gather_raw(S.alpha + ((int64_t)b1 * 2 + ((t1 - 1) & 1)) * S.Q, src, rn);
-      }
+      // every arc is relaxed; a source whose bit is clear contributes -inf
+      // without reading its 8-byte frontier entry
+      const uint32_t lv = live_bits(t == 1 ? S.bm_start : S.abm + (int64_t)((t - 1) % 3) * S.bm_rot + (int64_t)b * S.W,
+                                    src);
+      if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no live source: every segment stays -inf
       float a[APL];
       if (t == 1) {
 #pragma unroll
-        for (int k = 0; k < APL; ++k) a[k] = __ldg(S.theta_s + src[k]);
+        for (int k = 0; k < APL; ++k) a[k] = ((lv >> k) & 1u) ? __ldg(S.theta_s + src[k]) : neg_inf();
       } else {
+        const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
         const uint32_t tg = tag_base + (uint32_t)(p - 1);
 #pragma unroll
-        for (int k = 0; k < APL; ++k) a[k] = tagged_value(rc[k], tg);
+        for (int k = 0; k < APL; ++k) a[k] = ((lv >> k) & 1u) ? tagged_value(__ldg(ab + src[k]), tg) : neg_inf();
       }
       unsigned long long key[APL];
 #pragma unroll
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
       window_scan<MaxKey>(key, x.h, lane, full);
       const int64_t cb = shfl64(tcb, j);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
+      uint32_t* bmout = S.abm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W;
       const uint32_t tag = tag_base + (uint32_t)p;
       if (!is_long) {
         int cum = x.hb;
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
           const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
           if (tail) {
             const int32_t s = x.seg + cum - 1;
-            vit_write(L, S, cb, s, s - G.segbase, full[k], aout, tag);
+            vit_write(L, S, cb, s, s - G.segbase, full[k], aout, tag, bmout);
           }
         }
       } else {
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
           if (prev == (uint32_t)x.lcnt - 1u) {
             __threadfence();
             const unsigned long long kf = atomicMax(S.skey + slot, 0ull);
-            vit_write(L, S, cb, x.seg, x.seg - G.segbase, kf, aout, tag);
+            vit_write(L, S, cb, x.seg, x.seg - G.segbase, kf, aout, tag, bmout);
             S.skey[slot] = 0ull;
             S.scnt[slot] = 0u;
           }
@@ -343,30 +345,33 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
     const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
-    unsigned long long rn[APL];
-    {
-      const int32_t b0 = __shfl_sync(FULL, tb, 0), t0 = __shfl_sync(FULL, tt, 0);
-      if (t0 > 1) gather_raw(S.alpha + ((int64_t)b0 * 2 + ((t0 - 1) & 1)) * S.Q, src, rn);
-    }
     for (int j = 0; j < G.cnt; ++j) {
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const float mprev = __shfl_sync(FULL, tm, j);
-      unsigned long long rc[APL];
+      const uint32_t lv = live_bits(t == 1 ? S.bm_start : S.abm + (int64_t)((t - 1) % 3) * S.bm_rot + (int64_t)b * S.W,
+                                    src);
+      if (!is_long && !__any_sync(FULL, lv != 0u)) {
+        // no live source: every segment of the window is -inf at this position
+        const int64_t cb = shfl64(tcb, j);
+        int cum = x.hb;
 #pragma unroll
-      for (int k = 0; k < APL; ++k) rc[k] = rn[k];
-      if (j + 1 < G.cnt) {
-        const int32_t b1 = __shfl_sync(FULL, tb, j + 1), t1 = __shfl_sync(FULL, tt, j + 1);
-        if (t1 > 1) gather_raw(S.alpha + ((int64_t)b1 * 2 + ((t1 - 1) & 1)) * S.Q, src, rn);
+        for (int k = 0; k < APL; ++k) {
+          cum += (x.h >> k) & 1u;
+          const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
+          if (tail) S.rc[cb + (x.seg + cum - 1 - G.segbase)] = neg_inf();
+        }
+        continue;
       }
       float a[APL];
       if (t == 1) {
 #pragma unroll
-        for (int k = 0; k < APL; ++k) a[k] = __ldg(S.theta_s + src[k]);
+        for (int k = 0; k < APL; ++k) a[k] = ((lv >> k) & 1u) ? __ldg(S.theta_s + src[k]) : neg_inf();
       } else {
+        const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
         const uint32_t tg = tag_base + (uint32_t)(p - 1);
 #pragma unroll
         for (int k = 0; k < APL; ++k) {
-          const float r = tagged_value(rc[k], tg);
+          const float r = ((lv >> k) & 1u) ? tagged_value(__ldg(ab + src[k]), tg) : neg_inf();
           a[k] = (r == neg_inf() || mprev == neg_inf()) ? neg_inf() : r - mprev;
         }
       }
@@ -380,6 +385,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
       window_scan<LogAdd>(e, x.h, lane, full);
       const int64_t cb = shfl64(tcb, j);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
+      uint32_t* bmout = S.abm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W;
       const uint32_t tag = tag_base + (uint32_t)p;
       float rmax = neg_inf();
       if (!is_long) {
@@ -392,7 +398,11 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
             const int32_t s = x.seg + cum - 1;
             const float r = lse_value(full[k]);
             S.rc[cb + (s - G.segbase)] = r;
-            if (r != neg_inf()) aout[__ldg(L.seg_state + s)] = tagged_make(r, tag);
+            if (r != neg_inf()) {
+              const int32_t q = __ldg(L.seg_state + s);
+              aout[q] = tagged_make(r, tag);
+              set_live(bmout, q);
+            }
             rmax = fmaxf(rmax, r);
           }
         }
@@ -402,7 +412,11 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
           const float r = lse_value(tot);
           if (lane == 0) {
             S.rc[cb + (x.seg - G.segbase)] = r;
-            if (r != neg_inf()) aout[__ldg(L.seg_state + x.seg)] = tagged_make(r, tag);
+            if (r != neg_inf()) {
+              const int32_t q = __ldg(L.seg_state + x.seg);
+              aout[q] = tagged_make(r, tag);
+              set_live(bmout, q);
+            }
           }
           rmax = r;
         }
@@ -520,18 +534,20 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
       if (!__shfl_sync(FULL, tlive, j)) continue;
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const int32_t n = __shfl_sync(FULL, tn, j);
-      // beta_t at the destinations
+      // beta_t at the destinations; a destination whose bit is clear is -inf
+      const uint32_t lv = live_bits(t == n ? S.bm_final : S.bbm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W, dst);
+      if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no arc reaches a live state: nothing to add
       float bv[APL];
       if (t == n) {
 #pragma unroll
-        for (int k = 0; k < APL; ++k) bv[k] = __ldg(S.theta_f + dst[k]);
+        for (int k = 0; k < APL; ++k) bv[k] = ((lv >> k) & 1u) ? __ldg(S.theta_f + dst[k]) : neg_inf();
       } else {
         const float et = __shfl_sync(FULL, te, j);
         const unsigned long long* bb = S.beta + ((int64_t)b * 2 + (t & 1)) * S.Q;
         const uint32_t tg = tag_base + (uint32_t)p;
 #pragma unroll
         for (int k = 0; k < APL; ++k) {
-          const float u = tagged_value(__ldg(bb + dst[k]), tg);
+          const float u = ((lv >> k) & 1u) ? tagged_value(__ldg(bb + dst[k]), tg) : neg_inf();
           bv[k] = (u == neg_inf() || et == neg_inf()) ? neg_inf() : u - et;
         }
       }
@@ -563,6 +579,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
         float2 full[APL];
         window_scan<LogAdd>(e, x.h, lane, full);
         unsigned long long* bout = S.beta + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+        uint32_t* bmout = S.bbm + (int64_t)((t - 1) % 3) * S.bm_rot + (int64_t)b * S.W;
         const uint32_t tag = tag_base + (uint32_t)(p - 1);
         float umax = neg_inf();
         if (!is_long) {
@@ -573,7 +590,10 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
             const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
             if (tail) {
               const float u = lse_value(full[k]);
-              if (u != neg_inf()) bout[qs[k]] = tagged_make(u, tag);
+              if (u != neg_inf()) {
+                bout[qs[k]] = tagged_make(u, tag);
+                set_live(bmout, qs[k]);
+              }
               umax = fmaxf(umax, u);
             }
           }
@@ -581,7 +601,11 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
           float2 tot;
           if (long_lse_arrive(L, S, x, shfl64(tlb, j), shfl64(tlw, j), full[APL - 1], lane, tot)) {
             const float u = lse_value(tot);
-            if (lane == 0 && u != neg_inf()) bout[__ldg(L.seg_state + x.seg)] = tagged_make(u, tag);
+            if (lane == 0 && u != neg_inf()) {
+              const int32_t q = __ldg(L.seg_state + x.seg);
+              bout[q] = tagged_make(u, tag);
+              set_live(bmout, q);
+            }
             umax = u;
           }
         }

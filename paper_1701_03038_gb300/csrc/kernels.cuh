@@ -71,6 +71,17 @@ struct WaveState {
   const float* gweight;              // [Bw] or null
   int32_t* bw_n;                     // [Bw] string lengths
   int64_t* bw_off;                   // [Bw] first token of each wave string
+  // Live-state bitmaps (bit q set = state q has a finite value): forward
+  // values at position t live in rotation t % 3 of abm, backward values at
+  // position t in rotation t % 3 of bbm; string b's bitmap of rotation r
+  // starts at r * bm_rot + b * W.  The driver clears a rotation before the
+  // launch that fills it.
+  uint32_t* abm;
+  uint32_t* bbm;
+  const uint32_t* bm_start;          // states with a finite start weight
+  const uint32_t* bm_final;          // states with a finite final weight
+  int32_t W;                         // 32-bit words per bitmap
+  int64_t bm_rot;
 };
 
 struct CountView {

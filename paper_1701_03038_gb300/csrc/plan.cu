@@ -207,6 +207,7 @@ struct fst_plan_s {
   double* cnt64 = nullptr;
   double* logz = nullptr;
   uint32_t *epoch = nullptr, *clear = nullptr;
+  uint32_t *abm = nullptr, *bbm = nullptr;  // [3][max_bw][W] live-state bitmaps
   int64_t max_bw = 0, max_ntok = 0, max_store = 0, max_lseg = 0, max_lwin = 0;
   bool forward_done = false;
   // optional per-launch CUDA events (fst_plan_profile)
@@ -219,7 +220,7 @@ struct fst_plan_s {
     for (Wave& w : waves) w.release();
     dfree(ids); dfree(alpha); dfree(beta); dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum);
     dfree(esum); dfree(skey); dfree(scnt); dfree(spart); dfree(qfinal); dfree(cnt64); dfree(logz);
-    dfree(epoch); dfree(clear);
+    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm);
   }
 };
 
@@ -389,7 +390,20 @@ WaveState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.gweight = gweight ? gweight + W.b0 : nullptr;
   S.bw_n = W.bw_n;
   S.bw_off = W.bw_off;
+  S.abm = P->abm;
+  S.bbm = P->bbm;
+  S.bm_start = f->bm_start;
+  S.bm_final = f->bm_final;
+  S.W = f->W;
+  S.bm_rot = P->max_bw * (int64_t)f->W;
   return S;
+}
+
+// Clear rotation r of a [3][max_bw][W] bitmap set before the launch that fills it.
+int clear_rot(fst_plan_s* P, uint32_t* bm, int32_t r, cudaStream_t s) {
+  const int64_t words = P->max_bw * (int64_t)P->fst->W;
+  FST_CUDA(cudaMemsetAsync(bm + (int64_t)r * words, 0, (size_t)std::max<int64_t>(words, 1) * 4, s));
+  return FST_OK;
 }
 
 TokenView wave_tokens(const Wave& W) {
@@ -436,6 +450,7 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   FST_CUDA(cudaMemsetAsync(P->ekey, 0, (size_t)std::max<int64_t>(1, W.ntok) * 4, s));
   for (int32_t t = 1; t <= W.tmax; ++t) {
     const WorkView V = wave_work(W, t, true);
+    if ((rc = clear_rot(P, P->abm, t % 3, s))) return rc;
     PROF(FST_PROF_FWD_STEP, launch_fwd_step(Lf, T, V, S, step_grid(f, V.nitems), s));
   }
   PROF(FST_PROF_FB_FINAL, launch_fb_final(Lf, W.tok_sym, W.cbase, S, W.Bw, P->logz + W.b0,
@@ -456,6 +471,7 @@ int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cuda
       PROF(FST_PROF_SCATTER, launch_scatter_alpha(Lf, T, V, S, t, step_grid(f, V.nitems), s));
     }
     const WorkView V = wave_work(W, t, false);
+    if (t >= 2 && (rc = clear_rot(P, P->bbm, (t - 1) % 3, s))) return rc;
     PROF(FST_PROF_BWD_STEP, launch_bwd_step(Lb, T, V, S, C, step_grid(f, V.nitems), s));
   }
   return FST_OK;
@@ -572,6 +588,8 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
         (rc = alloc_track(P, &P->clear, 1)))
       break;
     if (want_fb && (rc = alloc_track(P, &P->cnt64, f->bwd.P))) break;
+    if ((rc = alloc_track(P, &P->abm, 3 * P->max_bw * (int64_t)f->W))) break;
+    if (want_fb && (rc = alloc_track(P, &P->bbm, 3 * P->max_bw * (int64_t)f->W))) break;
     FST_CUDA(cudaMemsetAsync(P->alpha, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     FST_CUDA(cudaMemsetAsync(P->epoch, 0, 8, s));
@@ -635,6 +653,7 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
     const WaveState S = wave_state(P, W, nullptr);
     for (int32_t t = 1; t <= W.tmax; ++t) {
       const WorkView V = wave_work(W, t, true);
+      if ((rc = clear_rot(P, P->abm, t % 3, s))) return rc;
       PROF(FST_PROF_VIT_STEP, launch_vit_step(Lf, T, V, S, step_grid(f, V.nitems), s));
     }
     PROF(FST_PROF_VIT_FINAL, launch_vit_final(Lf, W.tok_sym, W.cbase, S, W.Bw, d_scores + W.b0, P->qfinal,
