@@ -225,6 +225,31 @@ FST_API int fst_plan_forward_backward(fst_plan_t* plan, const float* d_weights, 
 FST_API int fst_plan_profile(fst_plan_t* plan, int32_t enable);
 FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t* launches_by_kind);
 
+/* Plain-method Viterbi of one string that allocates no memory (the paper
+ * has no counterpart: this is a deployment variant of fst_viterbi).  For
+ * callers that cannot allocate device memory at decode time -- a host whose
+ * memory manager owns every allocation, a latency-critical loop that must
+ * not take the implicit synchronisation of cudaMalloc/cudaFree, a process
+ * under a hard device-memory cap.  Every piece of per-call working memory
+ * (frontier, live-state bitmaps, backpointers, token tables) comes from one
+ * fixed 32 MiB device array inside the library, resident on every device
+ * that loads it until the process exits.
+ *   ids        [n] host, symbols in [0, m); n >= 0.
+ *   d_score    device float [1]: best log-weight, -inf when no path.
+ *   d_path     device int32 [n]: arc ids of the best path (-1 when no path).
+ *   d_olabels  device int32 [n] or NULL.
+ *   stream     cudaStream_t; the call is asynchronous on it.
+ * Results are bit-identical to fst_viterbi.  Returns FST_ERR_UNSUPPORTED
+ * (nothing is launched) when the string needs more than the fixed array:
+ * about 16*Q + 4*(sum over positions of distinct destinations of the
+ * position's symbol) + 40*n bytes.  The first call on a device looks up
+ * the array's device address with that device current: make it before any
+ * stream capture.  All calls share the array and see the previous call's
+ * contents, which each call clears where needed; calls that overlap on the
+ * GPU race on it and must be serialised by the caller. */
+FST_API int fst_viterbi_noalloc(fst_t* fst, const int32_t* ids, int32_t n, float* d_score, int32_t* d_path,
+                                int32_t* d_olabels, void* stream);
+
 /* Message of the last failing call on this host thread ("" if none). */
 FST_API const char* fst_last_error(void);
 

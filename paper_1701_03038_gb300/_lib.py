@@ -43,6 +43,7 @@ SIGNATURES = {
     "fst_plan_forward_backward": [vp, vp, vp, vp, vp, vp],
     "fst_plan_profile": [vp, i32],
     "fst_plan_profile_read": [vp, vp, vp],
+    "fst_viterbi_noalloc": [vp, vp, i32, vp, vp, vp, vp],
 }
 
 PROF_KINDS = ["vit_step", "vit_final", "backtrace", "fwd_step", "fb_final", "scatter", "bwd_step", "counts"]
