@@ -206,6 +206,18 @@ FST_API int fst_plan_backward(fst_plan_t* plan, const float* d_weights, float* d
 FST_API int fst_plan_forward_backward(fst_plan_t* plan, const float* d_weights, double* d_logz,
                               float* d_counts, int32_t* d_status, void* stream);
 
+/* log Z of one string with every value and weight in float64 (the forward
+ * recursion of Alg. 2 in the log domain; plain method, one launch per
+ * position).  For finite-difference checks of d log Z / d theta, which a
+ * central difference of step 1e-6 can only resolve with log Z known to
+ * ~1e-12.  Host pointers; synchronous.
+ *   theta   [num_arcs] host float64 log-weights (caller arc order), or NULL
+ *           to reuse the float64 weights of the previous call
+ *           (FST_ERR_STATE if there were none).  The float32 weights used
+ *           by every other entry point are not touched.
+ *   ids     [n] host symbols.      log_z  host double (-inf = no path). */
+FST_API int fst_log_z_f64(fst_t* fst, const double* theta, const int32_t* ids, int32_t n, double* log_z);
+
 /* Per-launch timing of a plan's runs (the tracing subsystem).  With
  * enable != 0, every kernel that a following fst_plan_* run queues is
  * bracketed by two CUDA events on the run's stream; fst_plan_profile_read

@@ -44,6 +44,7 @@ SIGNATURES = {
     "fst_plan_profile": [vp, i32],
     "fst_plan_profile_read": [vp, vp, vp],
     "fst_viterbi_noalloc": [vp, vp, i32, vp, vp, vp, vp],
+    "fst_log_z_f64": [vp, vp, vp, i32, vp],
 }
 
 PROF_KINDS = ["vit_step", "vit_final", "backtrace", "fwd_step", "fb_final", "scatter", "bwd_step", "counts"]

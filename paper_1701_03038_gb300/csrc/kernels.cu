@@ -485,7 +485,8 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
   // lane j: token j of the group
   int32_t tp = 0, tb = 0, tt = 0, tn = 0;
   int64_t tlb = 0, tlw = 0;
-  float tK = 0.f, tm = 0.f, te = 0.f, tw = 0.f;
+  float tm = 0.f, te = 0.f, tw = 0.f;
+  double tK = 0.0;
   double tE = 0.0;
   bool tlive = false;
   for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
         te = (tt == tn) ? 0.f : decode_max(S.ekey[tp]);
         tE = (tt == tn) ? 0.0 : S.esum[tp + 1] + (double)te;
         const double Ctm1 = (tt == 1) ? 0.0 : S.csum[tp - 1];
-        tK = (float)(Ctm1 + tE - lz);
+        tK = Ctm1 + tE - lz;
         tm = (tt == 1) ? 0.f : decode_max(S.mkey[tp - 1]);
         tw = S.gweight ? S.gweight[tb] : 1.f;
       } else {
@@ -537,40 +538,34 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
       // beta_t at the destinations; a destination whose bit is clear is -inf
       const uint32_t lv = live_bits(t == n ? S.bm_final : S.bbm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W, dst);
       if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no arc reaches a live state: nothing to add
-      float bv[APL];
+      // raw values: ub = beta_t[dst] before its step shift (theta_f at the
+      // last position), ra = alpha_{t-1}[src] before its shift (theta_s at
+      // the first); -inf where the state is dead
+      const float et = (t == n) ? 0.f : __shfl_sync(FULL, te, j);
+      const float mprev = (t == 1) ? 0.f : __shfl_sync(FULL, tm, j);
+      float ub[APL], ra[APL];
       if (t == n) {
 #pragma unroll
-        for (int k = 0; k < APL; ++k) bv[k] = ((lv >> k) & 1u) ? __ldg(S.theta_f + dst[k]) : neg_inf();
+        for (int k = 0; k < APL; ++k) ub[k] = ((lv >> k) & 1u) ? __ldg(S.theta_f + dst[k]) : neg_inf();
       } else {
-        const float et = __shfl_sync(FULL, te, j);
         const unsigned long long* bb = S.beta + ((int64_t)b * 2 + (t & 1)) * S.Q;
         const uint32_t tg = tag_base + (uint32_t)p;
 #pragma unroll
-        for (int k = 0; k < APL; ++k) {
-          const float u = ((lv >> k) & 1u) ? tagged_value(__ldg(bb + dst[k]), tg) : neg_inf();
-          bv[k] = (u == neg_inf() || et == neg_inf()) ? neg_inf() : u - et;
-        }
+        for (int k = 0; k < APL; ++k) ub[k] = ((lv >> k) & 1u) ? tagged_value(__ldg(bb + dst[k]), tg) : neg_inf();
       }
-      // alpha_{t-1} at the sources (one state per segment: cached loads)
-      float ah[APL];
-      {
-        const float mprev = __shfl_sync(FULL, tm, j);
-        if (t == 1) {
+      if (t == 1) {
 #pragma unroll
-          for (int k = 0; k < APL; ++k) ah[k] = __ldg(S.theta_s + qs[k]);
-        } else {
-          const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
-          const uint32_t tga = tag_base + (uint32_t)(p - 1);
+        for (int k = 0; k < APL; ++k) ra[k] = __ldg(S.theta_s + qs[k]);
+      } else {
+        const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+        const uint32_t tga = tag_base + (uint32_t)(p - 1);
 #pragma unroll
-          for (int k = 0; k < APL; ++k) {
-            const float r = tagged_value(__ldg(ab + qs[k]), tga);
-            ah[k] = (r == neg_inf() || mprev == neg_inf()) ? neg_inf() : r - mprev;
-          }
-        }
+        for (int k = 0; k < APL; ++k) ra[k] = tagged_value(__ldg(ab + qs[k]), tga);
       }
+      const bool dead_shift = (et == neg_inf()) || (mprev == neg_inf());
       float v[APL];
 #pragma unroll
-      for (int k = 0; k < APL; ++k) v[k] = th[k] + bv[k];
+      for (int k = 0; k < APL; ++k) v[k] = (ub[k] == neg_inf() || dead_shift) ? neg_inf() : th[k] + (ub[k] - et);
       // beta_{t-1} by source segment (not needed for t == 1)
       if (t >= 2) {
         float2 e[APL];
@@ -612,13 +607,16 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
         umax = warp_max(umax);
         if (lane == 0 && umax != neg_inf()) atomicMax(S.ekey + p - 1, fkey(umax));
       }
-      // posteriors gamma_t(k) = exp(alpha_{t-1}[src] + theta_k + beta_t[dst] - log Z)
-      const float K = __shfl_sync(FULL, tK, j);
+      // posteriors gamma_t(k) = exp(alpha_{t-1}[src] + theta_k + beta_t[dst] - log Z);
+      // the exponent adds terms of either sign and tens in size that cancel to
+      // a small number, so it is formed in float64 (live arcs only)
+      const double K = __shfl_sync(FULL, tK, j);
       const float gw = __shfl_sync(FULL, tw, j);
 #pragma unroll
       for (int k = 0; k < APL; ++k) {
-        if (v[k] == neg_inf() || ah[k] == neg_inf()) continue;
-        gacc[k] += (double)(__expf(ah[k] + v[k] + K) * gw);
+        if (v[k] == neg_inf() || ra[k] == neg_inf()) continue;
+        const double ex = ((double)ra[k] - (double)mprev) + (double)th[k] + ((double)ub[k] - (double)et) + K;
+        gacc[k] += (double)(__expf((float)ex) * gw);
       }
     }
     // accumulate this item's counts

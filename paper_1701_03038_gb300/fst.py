@@ -162,6 +162,18 @@ class Fst:
         check(rc, "fst_forward_backward", allow=(_lib.OK, _lib.NO_PATH))
         return float(lz[0]), (cnt[:self.num_arcs] if posteriors else None), rc
 
+    def log_z_f64(self, ids, theta=None) -> float:
+        """log Z of one string in float64 (finite-difference checks).
+        ``theta``: float64 log-weights [A] in caller order, or None to reuse
+        the previous call's."""
+        x = _host(ids, np.int32)
+        lz = np.zeros(1, np.float64)
+        th = None if theta is None else _host(theta, np.float64)
+        with torch.cuda.device(self.device):
+            check(self._lib.fst_log_z_f64(self._h, None if th is None else _hptr(th), _hptr(x), int(x.shape[0]),
+                                          _hptr(lz)), "fst_log_z_f64")
+        return float(lz[0])
+
     # ------------------------------------------------------ batched method
     def plan(self, ids: torch.Tensor, offsets: torch.Tensor, mem_budget: int = 0, flags: int = 0,
              stream=None) -> "Plan":
