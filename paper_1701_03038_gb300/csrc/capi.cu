@@ -151,8 +151,10 @@ struct PlainWs {
   unsigned long long* alpha = nullptr;  // [2][Q]
   unsigned long long* beta = nullptr;
   int32_t *tok_sym = nullptr, *tok_b = nullptr, *tok_t = nullptr;
-  int64_t *cbase = nullptr, *zero64 = nullptr;
+  int64_t *cbase = nullptr, *zero64 = nullptr, *wbase = nullptr;
   int32_t* bp = nullptr;
+  uint8_t* wlive = nullptr;
+  int64_t cap_wlive = 0;
   float* rc = nullptr;
   uint32_t *mkey = nullptr, *ekey = nullptr;
   double *csum = nullptr, *esum = nullptr;
@@ -169,7 +171,7 @@ struct PlainWs {
   uint32_t *abm = nullptr, *bbm = nullptr;  // [3][W] live-state bitmaps
   int64_t max_lseg = 0, max_lwin = 0;
   ~PlainWs() {
-    dfree(abm); dfree(bbm);
+    dfree(abm); dfree(bbm); dfree(wbase); dfree(wlive);
     dfree(alpha); dfree(beta); dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(zero64);
     dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(skey); dfree(scnt);
     dfree(spart); dfree(cnt); dfree(comp); dfree(counts_out); dfree(paths); dfree(olabels); dfree(qfinal);
@@ -209,15 +211,23 @@ int plain_init(fst_s* f) {
   return FST_OK;
 }
 
-int plain_reserve(PlainWs* w, int64_t n, int64_t store) {
+int plain_reserve(PlainWs* w, int64_t n, int64_t store, int64_t nwins) {
   int rc;
+  if (nwins > w->cap_wlive) {
+    const int64_t c = std::max<int64_t>(nwins, 2 * w->cap_wlive);
+    dfree(w->wlive);
+    w->cap_wlive = 0;
+    if ((rc = dalloc(&w->wlive, c))) return rc;
+    w->cap_wlive = c;
+  }
   if (n > w->cap_n) {
     const int64_t c = std::max<int64_t>(n, 2 * w->cap_n);
-    dfree(w->tok_sym); dfree(w->tok_b); dfree(w->tok_t); dfree(w->cbase); dfree(w->zero64);
+    dfree(w->tok_sym); dfree(w->tok_b); dfree(w->tok_t); dfree(w->cbase); dfree(w->zero64); dfree(w->wbase);
     dfree(w->mkey); dfree(w->ekey); dfree(w->csum); dfree(w->esum); dfree(w->paths); dfree(w->olabels);
     w->cap_n = 0;
     if ((rc = dalloc(&w->tok_sym, c)) || (rc = dalloc(&w->tok_b, c)) || (rc = dalloc(&w->tok_t, c)) ||
-        (rc = dalloc(&w->cbase, c)) || (rc = dalloc(&w->zero64, c)) || (rc = dalloc(&w->mkey, c)) ||
+        (rc = dalloc(&w->cbase, c)) || (rc = dalloc(&w->zero64, c)) || (rc = dalloc(&w->wbase, c)) ||
+        (rc = dalloc(&w->mkey, c)) ||
         (rc = dalloc(&w->ekey, c)) || (rc = dalloc(&w->csum, c)) || (rc = dalloc(&w->esum, c)) ||
         (rc = dalloc(&w->paths, c)) || (rc = dalloc(&w->olabels, c)))
       return rc;
@@ -239,8 +249,8 @@ int plain_reserve(PlainWs* w, int64_t n, int64_t store) {
 int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
   PlainWs* w = f->plain;
   std::vector<int32_t> tt(std::max(n, 1));
-  std::vector<int64_t> cb(std::max(n, 1));
-  int64_t acc = 0;
+  std::vector<int64_t> cb(std::max(n, 1)), wb(std::max(n, 1));
+  int64_t acc = 0, wacc = 0;
   for (int32_t i = 0; i < n; ++i) {
     if (ids[i] < 0 || ids[i] >= f->m) {
       set_error("symbol %d at position %d is outside [0, %d)", ids[i], i, f->m);
@@ -248,14 +258,18 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
     }
     tt[i] = i + 1;
     cb[i] = acc;
+    wb[i] = wacc;
     acc += f->fwd.h_sym_seg[ids[i] + 1] - f->fwd.h_sym_seg[ids[i]];
+    wacc += f->fwd.h_sym_win[ids[i] + 1] - f->fwd.h_sym_win[ids[i]];
   }
-  int rc = plain_reserve(w, std::max(n, 1), std::max<int64_t>(acc, 1));
+  int rc = plain_reserve(w, std::max(n, 1), std::max<int64_t>(acc, 1), std::max<int64_t>(wacc, 1));
   if (rc) return rc;
   if (n > 0) {
     FST_CUDA(cudaMemcpyAsync(w->tok_sym, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     FST_CUDA(cudaMemcpyAsync(w->tok_t, tt.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
     FST_CUDA(cudaMemcpyAsync(w->cbase, cb.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    FST_CUDA(cudaMemcpyAsync(w->wbase, wb.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    FST_CUDA(cudaMemsetAsync(w->wlive, 0, (size_t)wacc, s));
   }
   FST_CUDA(cudaMemcpyAsync(w->bw_n, &n, 4, cudaMemcpyHostToDevice, s));
   // fresh tags for this string
@@ -269,7 +283,7 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
 }
 
 TokenView plain_tokview(PlainWs* w) {
-  return TokenView{w->tok_sym, w->tok_b, w->tok_t, w->cbase, w->zero64, w->zero64, w->zero64, w->zero64};
+  return TokenView{w->tok_sym, w->tok_b, w->tok_t, w->cbase, w->zero64, w->zero64, w->zero64, w->zero64, w->wbase};
 }
 
 WaveState plain_state(fst_s* f) {
@@ -302,6 +316,7 @@ WaveState plain_state(fst_s* f) {
   S.bm_final = f->bm_final;
   S.W = f->W;
   S.bm_rot = f->W;
+  S.wlive = w->wlive;
   return S;
 }
 

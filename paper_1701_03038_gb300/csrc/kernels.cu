@@ -93,15 +93,16 @@ __device__ __forceinline__ void window_scan(const typename Op::T (&e)[APL], uint
 
 // Work-list resolution.  A warp walks items item0, item0 + nwarps, ...; the
 // group of the last item and, in lane j, the data of the group's j-th token
-// stay in registers until an item falls outside the group.
+// stay in registers until an item falls outside the group.  Item, window and
+// arc indices fit in 32 bits (padded arcs < 2^31 is enforced at build).
 struct Group {
   int32_t g, sym, cnt, segbase;
-  int64_t lo, hi, wbase;
+  int32_t lo, hi, wbase;
 };
 
-__device__ __forceinline__ void find_group(const LayoutView& L, const WorkView& W, int64_t item, Group& G) {
+__device__ __forceinline__ void find_group(const LayoutView& L, const WorkView& W, int32_t item, Group& G) {
   if (W.single) {
-    G.g = 0; G.lo = 0; G.hi = W.nitems; G.sym = W.sym0; G.cnt = 1;
+    G.g = 0; G.lo = 0; G.hi = (int32_t)W.nitems; G.sym = W.sym0; G.cnt = 1;
   } else {
     int lo = G.g >= 0 ? G.g + 1 : W.g0;  // items only grow inside a warp's walk
     int hi = W.g1 - 1;
@@ -110,12 +111,12 @@ __device__ __forceinline__ void find_group(const LayoutView& L, const WorkView& 
       if (__ldg(W.grp_item + mid) <= item) lo = mid; else hi = mid - 1;
     }
     G.g = lo;
-    G.lo = __ldg(W.grp_item + lo);
-    G.hi = (lo + 1 < W.g1) ? __ldg(W.grp_item + lo + 1) : W.nitems;
+    G.lo = (int32_t)__ldg(W.grp_item + lo);
+    G.hi = (lo + 1 < W.g1) ? (int32_t)__ldg(W.grp_item + lo + 1) : (int32_t)W.nitems;
     G.sym = __ldg(W.grp_sym + lo);
     G.cnt = __ldg(W.grp_cnt + lo);
   }
-  G.wbase = __ldg(L.sym_win + G.sym);
+  G.wbase = (int32_t)__ldg(L.sym_win + G.sym);
   G.segbase = (int32_t)__ldg(L.sym_seg + G.sym);
 }
 
@@ -124,13 +125,13 @@ __device__ __forceinline__ int32_t group_token(const WorkView& W, const Group& G
 }
 
 struct Win {
-  int64_t w;
+  int32_t w;
   int32_t seg, lseg, lwin0, lcnt;
   uint32_t h;   // this lane's head bits
   int32_t hb;   // heads of the window before this lane
 };
 
-__device__ __forceinline__ Win load_win(const LayoutView& L, int64_t w, int lane) {
+__device__ __forceinline__ Win load_win(const LayoutView& L, int32_t w, int lane) {
   Win x;
   x.w = w;
   const int4 m0 = __ldg(reinterpret_cast<const int4*>(L.win + w));
@@ -145,11 +146,8 @@ __device__ __forceinline__ Win load_win(const LayoutView& L, int64_t w, int lane
   return x;
 }
 
-
-__device__ __forceinline__ int64_t warp_id_global() {
-  return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-}
-__device__ __forceinline__ int64_t warps_total() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
+__device__ __forceinline__ int32_t warp_id_global() { return (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+__device__ __forceinline__ int32_t warps_total() { return (int32_t)((gridDim.x * blockDim.x) >> 5); }
 
 __device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
   return (int64_t)__shfl_sync(FULL, (long long)v, src);
@@ -167,16 +165,21 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Liveness of the arcs' gather states (bit k = arc k) in a frontier bitmap.
-__device__ __forceinline__ uint32_t live_bits(const uint32_t* __restrict__ bm, const int32_t (&st)[APL]) {
+// Bitmap words of the arcs' gather states (issued early so that the loads
+// of the next token overlap the work of the current one).
+__device__ __forceinline__ void bitmap_words(const uint32_t* __restrict__ bm, const int32_t (&st)[APL],
+                                             uint32_t (&wd)[APL]) {
+#pragma unroll
+  for (int k = 0; k < APL; ++k) wd[k] = __ldg(bm + (st[k] >> 5));
+}
+__device__ __forceinline__ uint32_t live_of(const uint32_t (&wd)[APL], const int32_t (&st)[APL]) {
   uint32_t m = 0;
 #pragma unroll
-  for (int k = 0; k < APL; ++k) m |= ((__ldg(bm + (st[k] >> 5)) >> (st[k] & 31)) & 1u) << k;
+  for (int k = 0; k < APL; ++k) m |= ((wd[k] >> (st[k] & 31)) & 1u) << k;
   return m;
 }
 
 __device__ __forceinline__ void set_live(uint32_t* bm, int32_t q) { atomicOr(bm + (q >> 5), 1u << (q & 31)); }
-
 
 // ======================================================================
 // Viterbi step (Alg. 1 inner loop; Sec. 5.1)
@@ -192,36 +195,45 @@ __device__ __forceinline__ void vit_write(const LayoutView& L, const WaveState& 
   }
 }
 
+__device__ __forceinline__ const uint32_t* fwd_bitmap(const WaveState& S, int32_t b, int32_t t) {
+  // liveness of the forward values the position-t relaxation reads
+  return t == 1 ? S.bm_start : S.abm + (int64_t)((t - 1) % 3) * S.bm_rot + (int64_t)b * S.W;
+}
+
 __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
-  const int64_t nw = warps_total();
+  const int32_t nw = warps_total();
   Group G;
   G.g = -1; G.hi = -1; G.lo = 0;
   int32_t tp = 0, tb = 0, tt = 0;
-  int64_t tcb = 0, tlb = 0;
-  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
+  int64_t tcb = 0;
+  int32_t tlb = 0;
+  for (int32_t item = warp_id_global(); item < (int32_t)W.nitems; item += nw) {
     if (item >= G.hi) {
       find_group(L, W, item, G);
       if (lane < G.cnt) {
         tp = group_token(W, G, lane);
-        tb = __ldg(T.b + tp); tt = __ldg(T.t + tp); tcb = __ldg(T.cbase + tp); tlb = __ldg(T.lbase + tp);
+        tb = __ldg(T.b + tp); tt = __ldg(T.t + tp); tcb = __ldg(T.cbase + tp); tlb = (int32_t)__ldg(T.lbase + tp);
       }
     }
     const Win x = load_win(L, G.wbase + (item - G.lo), lane);
-    const int64_t base = x.w * WIN + lane * APL;
+    const int32_t base = x.w * WIN + lane * APL;
     const int4 s4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
     const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
     const int32_t src[APL] = {s4.x, s4.y, s4.z, s4.w};
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
     const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
+    uint32_t wn[APL];
+    bitmap_words(fwd_bitmap(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)), src, wn);
     for (int j = 0; j < G.cnt; ++j) {
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       // every arc is relaxed; a source whose bit is clear contributes -inf
       // without reading its 8-byte frontier entry
-      const uint32_t lv = live_bits(t == 1 ? S.bm_start : S.abm + (int64_t)((t - 1) % 3) * S.bm_rot + (int64_t)b * S.W,
-                                    src);
+      const uint32_t lv = live_of(wn, src);
+      if (j + 1 < G.cnt)
+        bitmap_words(fwd_bitmap(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1)), src, wn);
       if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no live source: every segment stays -inf
       float a[APL];
       if (t == 1) {
@@ -259,10 +271,10 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
           }
         }
       } else {
-        const int64_t lb = shfl64(tlb, j);
+        const int32_t lb = __shfl_sync(FULL, tlb, j);
         if (lane == 31) {
           // a destination segment that spans warps: packed 64-bit atomicMax
-          const int64_t slot = lb + x.lseg;
+          const int64_t slot = (int64_t)lb + x.lseg;
           atomicMax(S.skey + slot, full[APL - 1]);
           __threadfence();
           const uint32_t prev = atomicAdd(S.scnt + slot, 1u);
@@ -289,7 +301,7 @@ __device__ __forceinline__ bool long_lse_arrive(const LayoutView& L, const WaveS
                                                 float2& total) {
   uint32_t prev = 0;
   if (lane == 31) {
-    const int64_t w0 = __ldg(L.seg_pos + x.seg) / WIN;
+    const int32_t w0 = __ldg(L.seg_pos + x.seg) / WIN;
     S.spart[lwslot + x.lwin0 + (x.w - w0)] = part;
     __threadfence();
     prev = atomicAdd(S.scnt + lslot + x.lseg, 1u);
@@ -321,38 +333,42 @@ __device__ __forceinline__ bool long_lse_arrive(const LayoutView& L, const WaveS
 __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
-  const int64_t nw = warps_total();
+  const int32_t nw = warps_total();
   Group G;
   G.g = -1; G.hi = -1; G.lo = 0;
-  int32_t tp = 0, tb = 0, tt = 0;
-  int64_t tcb = 0, tlb = 0, tlw = 0;
+  int32_t tp = 0, tb = 0, tt = 0, tlb = 0, tlw = 0;
+  int64_t tcb = 0, twb = 0;
   float tm = 0.f;
-  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
+  for (int32_t item = warp_id_global(); item < (int32_t)W.nitems; item += nw) {
     if (item >= G.hi) {
       find_group(L, W, item, G);
       if (lane < G.cnt) {
         tp = group_token(W, G, lane);
         tb = __ldg(T.b + tp); tt = __ldg(T.t + tp); tcb = __ldg(T.cbase + tp);
-        tlb = __ldg(T.lbase + tp); tlw = __ldg(T.lwbase + tp);
+        tlb = (int32_t)__ldg(T.lbase + tp); tlw = (int32_t)__ldg(T.lwbase + tp); twb = __ldg(T.wbase + tp);
         tm = tt > 1 ? decode_max(S.mkey[tp - 1]) : 0.f;
       }
     }
-    const Win x = load_win(L, G.wbase + (item - G.lo), lane);
-    const int64_t base = x.w * WIN + lane * APL;
+    const int32_t wslice = item - G.lo;
+    const Win x = load_win(L, G.wbase + wslice, lane);
+    const int32_t base = x.w * WIN + lane * APL;
     const int4 s4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
     const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
     const int32_t src[APL] = {s4.x, s4.y, s4.z, s4.w};
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
     const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
+    uint32_t wn[APL];
+    bitmap_words(fwd_bitmap(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)), src, wn);
     for (int j = 0; j < G.cnt; ++j) {
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const float mprev = __shfl_sync(FULL, tm, j);
-      const uint32_t lv = live_bits(t == 1 ? S.bm_start : S.abm + (int64_t)((t - 1) % 3) * S.bm_rot + (int64_t)b * S.W,
-                                    src);
+      const uint32_t lv = live_of(wn, src);
+      if (j + 1 < G.cnt)
+        bitmap_words(fwd_bitmap(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1)), src, wn);
+      const int64_t cb = shfl64(tcb, j);
       if (!is_long && !__any_sync(FULL, lv != 0u)) {
         // no live source: every segment of the window is -inf at this position
-        const int64_t cb = shfl64(tcb, j);
         int cum = x.hb;
 #pragma unroll
         for (int k = 0; k < APL; ++k) {
@@ -383,7 +399,6 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
       }
       float2 full[APL];
       window_scan<LogAdd>(e, x.h, lane, full);
-      const int64_t cb = shfl64(tcb, j);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
       uint32_t* bmout = S.abm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W;
       const uint32_t tag = tag_base + (uint32_t)p;
@@ -406,9 +421,14 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
             rmax = fmaxf(rmax, r);
           }
         }
+        rmax = warp_max(rmax);
+        // the backward pass restores forward values only in windows marked live
+        const int64_t wbt = shfl64(twb, j);
+        if (lane == 0 && rmax != neg_inf()) S.wlive[wbt + wslice] = 1;
       } else {
         float2 tot;
-        if (long_lse_arrive(L, S, x, shfl64(tlb, j), shfl64(tlw, j), full[APL - 1], lane, tot)) {
+        const int64_t wbt = shfl64(twb, j);
+        if (long_lse_arrive(L, S, x, __shfl_sync(FULL, tlb, j), __shfl_sync(FULL, tlw, j), full[APL - 1], lane, tot)) {
           const float r = lse_value(tot);
           if (lane == 0) {
             S.rc[cb + (x.seg - G.segbase)] = r;
@@ -416,12 +436,13 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
               const int32_t q = __ldg(L.seg_state + x.seg);
               aout[q] = tagged_make(r, tag);
               set_live(bmout, q);
+              // the segment's first window carries its head
+              S.wlive[wbt + (__ldg(L.seg_pos + x.seg) / WIN - G.wbase)] = 1;
             }
           }
           rmax = r;
         }
       }
-      rmax = warp_max(rmax);
       if (lane == 0 && rmax != neg_inf()) atomicMax(S.mkey + p, fkey(rmax));
     }
   }
@@ -430,29 +451,36 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
 // ======================================================================
 // Scatter the stored forward values of step t_s back into the dense
 // frontier (needed by the backward step t_s + 1 when step t_s + 2 has
-// overwritten that parity buffer).
+// overwritten that parity buffer).  Only windows that the forward pass
+// marked live are read.
 // ======================================================================
 __global__ void __launch_bounds__(KT) k_scatter_alpha(LayoutView L, TokenView T, WorkView W, WaveState S,
                                                       int32_t t_bwd) {
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
-  const int64_t nw = warps_total();
+  const int32_t nw = warps_total();
   Group G;
   G.g = -1; G.hi = -1; G.lo = 0;
   int32_t tp = 0, tb = 0, tt = 0, tn = 0;
-  int64_t tcb = 0;
-  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
+  int64_t tcb = 0, twb = 0;
+  for (int32_t item = warp_id_global(); item < (int32_t)W.nitems; item += nw) {
     if (item >= G.hi) {
       find_group(L, W, item, G);
       if (lane < G.cnt) {
         tp = group_token(W, G, lane);
         tb = __ldg(T.b + tp); tt = __ldg(T.t + tp); tcb = __ldg(T.cbase + tp); tn = S.bw_n[tb];
+        twb = __ldg(T.wbase + tp);
       }
     }
-    const Win x = load_win(L, G.wbase + (item - G.lo), lane);
-    if (!__any_sync(FULL, x.h != 0u)) continue;
-    for (int j = 0; j < G.cnt; ++j) {
-      if (__shfl_sync(FULL, tn, j) <= t_bwd) continue;  // this string's frontier was not overwritten
+    const int32_t wslice = item - G.lo;
+    // lane j: is window `wslice` live for token j (and is its frontier needed)?
+    const bool need = lane < G.cnt && tn > t_bwd && S.wlive[twb + wslice] != 0;
+    uint32_t todo = __ballot_sync(FULL, need);
+    if (!todo) continue;
+    const Win x = load_win(L, G.wbase + wslice, lane);
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const int64_t cb = shfl64(tcb, j);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
@@ -475,75 +503,85 @@ __global__ void __launch_bounds__(KT) k_scatter_alpha(LayoutView L, TokenView T,
 // Backward step fused with the expected counts (Alg. 2 backward loop and
 // count loop; Sec. 5.2).  Segments are by source state.
 // ======================================================================
+__device__ __forceinline__ const uint32_t* bwd_bitmap(const WaveState& S, int32_t b, int32_t t, int32_t n) {
+  // liveness of the backward values the position-t relaxation reads
+  return t == n ? S.bm_final : S.bbm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W;
+}
+
 __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L, TokenView T, WorkView W,
                                                                     WaveState S, CountView C) {
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
-  const int64_t nw = warps_total();
+  const int32_t nw = warps_total();
   Group G;
   G.g = -1; G.hi = -1; G.lo = 0;
   // lane j: token j of the group
-  int32_t tp = 0, tb = 0, tt = 0, tn = 0;
-  int64_t tlb = 0, tlw = 0;
+  int32_t tp = 0, tb = 0, tt = 0, tn = 0, tlb = 0, tlw = 0;
   float tm = 0.f, te = 0.f, tw = 0.f;
   double tK = 0.0;
-  double tE = 0.0;
   bool tlive = false;
-  for (int64_t item = warp_id_global(); item < W.nitems; item += nw) {
+  for (int32_t item = warp_id_global(); item < (int32_t)W.nitems; item += nw) {
     if (item >= G.hi) {
       find_group(L, W, item, G);
       if (lane < G.cnt) {
         tp = group_token(W, G, lane);
         tb = __ldg(T.b + tp); tt = __ldg(T.t + tp);
-        tlb = __ldg(T.lbase_b + tp); tlw = __ldg(T.lwbase_b + tp);
+        tlb = (int32_t)__ldg(T.lbase_b + tp); tlw = (int32_t)__ldg(T.lwbase_b + tp);
         tn = S.bw_n[tb];
         const double lz = S.logz[tb];
         tlive = lz != -INFINITY;
         te = (tt == tn) ? 0.f : decode_max(S.ekey[tp]);
-        tE = (tt == tn) ? 0.0 : S.esum[tp + 1] + (double)te;
+        const double tE = (tt == tn) ? 0.0 : S.esum[tp + 1] + (double)te;
         const double Ctm1 = (tt == 1) ? 0.0 : S.csum[tp - 1];
         tK = Ctm1 + tE - lz;
         tm = (tt == 1) ? 0.f : decode_max(S.mkey[tp - 1]);
         tw = S.gweight ? S.gweight[tb] : 1.f;
+        // E_t for the next position's launch: written once per token
+        if (item == G.lo && tlive) S.esum[tp] = tE;
       } else {
         tlive = false;
       }
-      // E_t for the next position's launch: written once per token
-      if (item == G.lo && lane < G.cnt && tlive) S.esum[tp] = tE;
     }
     const Win x = load_win(L, G.wbase + (item - G.lo), lane);
-    const int64_t base = x.w * WIN + lane * APL;
+    const int32_t base = x.w * WIN + lane * APL;
     const int4 d4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
     const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
     const int32_t dst[APL] = {d4.x, d4.y, d4.z, d4.w};
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
     const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
-    // segment (source state) of each arc
+    // segment (source state) of each arc; padding arcs belong to the window's last segment
     int32_t qs[APL];
     {
       int cum = x.hb;
 #pragma unroll
       for (int k = 0; k < APL; ++k) {
         cum += (x.h >> k) & 1u;
-        const int32_t s = is_long ? x.seg : x.seg + cum - 1;
-        qs[k] = __ldg(L.seg_state + s);  // padding arcs belong to the window's last segment
+        qs[k] = __ldg(L.seg_state + (is_long ? x.seg : x.seg + cum - 1));
       }
     }
-    double gacc[APL] = {0.0, 0.0, 0.0, 0.0};
+    float gacc[APL] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t wn[APL];
+    bitmap_words(bwd_bitmap(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0), __shfl_sync(FULL, tn, 0)), dst,
+                 wn);
     for (int j = 0; j < G.cnt; ++j) {
-      if (!__shfl_sync(FULL, tlive, j)) continue;
+      const bool live_tok = __shfl_sync(FULL, tlive, j);
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const int32_t n = __shfl_sync(FULL, tn, j);
       // beta_t at the destinations; a destination whose bit is clear is -inf
-      const uint32_t lv = live_bits(t == n ? S.bm_final : S.bbm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W, dst);
+      const uint32_t lv = live_of(wn, dst);
+      if (j + 1 < G.cnt)
+        bitmap_words(bwd_bitmap(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1),
+                                __shfl_sync(FULL, tn, j + 1)),
+                     dst, wn);
+      if (!live_tok) continue;
       if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no arc reaches a live state: nothing to add
       // raw values: ub = beta_t[dst] before its step shift (theta_f at the
       // last position), ra = alpha_{t-1}[src] before its shift (theta_s at
       // the first); -inf where the state is dead
       const float et = (t == n) ? 0.f : __shfl_sync(FULL, te, j);
       const float mprev = (t == 1) ? 0.f : __shfl_sync(FULL, tm, j);
-      float ub[APL], ra[APL];
+      float ub[APL];
       if (t == n) {
 #pragma unroll
         for (int k = 0; k < APL; ++k) ub[k] = ((lv >> k) & 1u) ? __ldg(S.theta_f + dst[k]) : neg_inf();
@@ -552,15 +590,6 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
         const uint32_t tg = tag_base + (uint32_t)p;
 #pragma unroll
         for (int k = 0; k < APL; ++k) ub[k] = ((lv >> k) & 1u) ? tagged_value(__ldg(bb + dst[k]), tg) : neg_inf();
-      }
-      if (t == 1) {
-#pragma unroll
-        for (int k = 0; k < APL; ++k) ra[k] = __ldg(S.theta_s + qs[k]);
-      } else {
-        const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
-        const uint32_t tga = tag_base + (uint32_t)(p - 1);
-#pragma unroll
-        for (int k = 0; k < APL; ++k) ra[k] = tagged_value(__ldg(ab + qs[k]), tga);
       }
       const bool dead_shift = (et == neg_inf()) || (mprev == neg_inf());
       float v[APL];
@@ -594,7 +623,8 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
           }
         } else {
           float2 tot;
-          if (long_lse_arrive(L, S, x, shfl64(tlb, j), shfl64(tlw, j), full[APL - 1], lane, tot)) {
+          if (long_lse_arrive(L, S, x, __shfl_sync(FULL, tlb, j), __shfl_sync(FULL, tlw, j), full[APL - 1], lane,
+                              tot)) {
             const float u = lse_value(tot);
             if (lane == 0 && u != neg_inf()) {
               const int32_t q = __ldg(L.seg_state + x.seg);
@@ -612,23 +642,27 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
       // a small number, so it is formed in float64 (live arcs only)
       const double K = __shfl_sync(FULL, tK, j);
       const float gw = __shfl_sync(FULL, tw, j);
+      const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+      const uint32_t tga = tag_base + (uint32_t)(p - 1);
 #pragma unroll
       for (int k = 0; k < APL; ++k) {
-        if (v[k] == neg_inf() || ra[k] == neg_inf()) continue;
-        const double ex = ((double)ra[k] - (double)mprev) + (double)th[k] + ((double)ub[k] - (double)et) + K;
-        gacc[k] += (double)(__expf((float)ex) * gw);
+        if (v[k] == neg_inf()) continue;
+        const float ra = (t == 1) ? __ldg(S.theta_s + qs[k]) : tagged_value(__ldg(ab + qs[k]), tga);
+        if (ra == neg_inf()) continue;
+        const double ex = ((double)ra - (double)mprev) + (double)th[k] + ((double)ub[k] - (double)et) + K;
+        gacc[k] += __expf((float)ex) * gw;
       }
     }
     // accumulate this item's counts
 #pragma unroll
     for (int k = 0; k < APL; ++k) {
-      if (gacc[k] == 0.0) continue;
-      const int64_t pos = base + k;
+      if (gacc[k] == 0.f) continue;
+      const int32_t pos = base + k;
       if (C.batched) {
-        atomicAdd(C.cnt64 + pos, gacc[k]);
+        atomicAdd(C.cnt64 + pos, (double)gacc[k]);
       } else {
         // compensated float32 summation (one string: no concurrent writer)
-        const float gv = (float)gacc[k];
+        const float gv = gacc[k];
         const float s0 = C.cnt[pos], cmp = C.comp[pos];
         const float y = __fsub_rn(gv, cmp);
         const float s1 = __fadd_rn(s0, y);

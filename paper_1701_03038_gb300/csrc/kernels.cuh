@@ -33,6 +33,7 @@ struct TokenView {
   const int64_t* lbase_b;   // long-segment scratch slots (backward layout)
   const int64_t* lwbase;    // long-window scratch slots (forward layout)
   const int64_t* lwbase_b;  // long-window scratch slots (backward layout)
+  const int64_t* wbase;     // first window-liveness byte of the token (forward windows)
 };
 
 // Work list of one step: items are (group, window-of-slice) pairs; a group
@@ -82,6 +83,9 @@ struct WaveState {
   const uint32_t* bm_final;          // states with a finite final weight
   int32_t W;                         // 32-bit words per bitmap
   int64_t bm_rot;
+  // one byte per (token, forward window): 1 when the window wrote a finite
+  // forward value for that token (cleared before each forward pass)
+  uint8_t* wlive;
 };
 
 struct CountView {

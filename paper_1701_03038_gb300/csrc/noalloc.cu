@@ -168,7 +168,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.bm_final = f->bm_final;
   S.W = f->W;
   S.bm_rot = f->W;
-  const TokenView T{tok_sym, tok_b, tok_t, cbase, zero64, zero64, zero64, zero64};
+  const TokenView T{tok_sym, tok_b, tok_t, cbase, zero64, zero64, zero64, zero64, zero64};
   const LayoutView Lf = view_of(f->fwd);
   for (int32_t t = 1; t <= n; ++t) {
     const int32_t a = ids[t - 1];

@@ -60,8 +60,9 @@ __global__ void k_tok_info(const int32_t* __restrict__ ids, const int64_t* __res
 __global__ void k_tok_counts(const int32_t* __restrict__ sym, int64_t n, const int64_t* __restrict__ f_seg,
                              const int64_t* __restrict__ f_lseg, const int64_t* __restrict__ f_lwin,
                              const int64_t* __restrict__ b_lseg, const int64_t* __restrict__ b_lwin,
-                             int64_t* __restrict__ c0, int64_t* __restrict__ c1, int64_t* __restrict__ c2,
-                             int64_t* __restrict__ c3, int64_t* __restrict__ c4) {
+                             const int64_t* __restrict__ f_win, int64_t* __restrict__ c0,
+                             int64_t* __restrict__ c1, int64_t* __restrict__ c2, int64_t* __restrict__ c3,
+                             int64_t* __restrict__ c4, int64_t* __restrict__ c5) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t a = sym[i];
@@ -70,6 +71,7 @@ __global__ void k_tok_counts(const int32_t* __restrict__ sym, int64_t n, const i
   c2[i] = f_lwin[a + 1] - f_lwin[a];
   c3[i] = b_lseg[a + 1] - b_lseg[a];
   c4[i] = b_lwin[a + 1] - b_lwin[a];
+  c5[i] = f_win[a + 1] - f_win[a];
 }
 
 __global__ void k_tok_keys(const int32_t* __restrict__ sym, const int32_t* __restrict__ t, int64_t n, int sbits,
@@ -169,10 +171,11 @@ __global__ void k_clear_if(const uint32_t* clear, unsigned long long* p, int64_t
 
 struct Wave {
   int32_t b0 = 0, b1 = 0, Bw = 0, tmax = 0;
-  int64_t tok0 = 0, ntok = 0, store = 0, G = 0;
+  int64_t tok0 = 0, ntok = 0, store = 0, G = 0, nwins = 0;
   int64_t nlseg = 0, nlwin = 0;  // scratch slots needed (max of both layouts)
   int32_t *tok_sym = nullptr, *tok_b = nullptr, *tok_t = nullptr;
   int64_t *cbase = nullptr, *lbase_f = nullptr, *lwbase_f = nullptr, *lbase_b = nullptr, *lwbase_b = nullptr;
+  int64_t* wbase = nullptr;
   int32_t *sorted_tok = nullptr, *grp_first = nullptr, *grp_cnt = nullptr, *grp_sym = nullptr;
   int64_t *grp_item_f = nullptr, *grp_item_b = nullptr;
   int32_t* bw_n = nullptr;
@@ -181,6 +184,7 @@ struct Wave {
   std::vector<int64_t> items_f, items_b;  // [tmax + 1]
   void release() {
     dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(lbase_f); dfree(lwbase_f); dfree(lbase_b);
+    dfree(wbase);
     dfree(lwbase_b); dfree(sorted_tok); dfree(grp_first); dfree(grp_cnt); dfree(grp_sym); dfree(grp_item_f);
     dfree(grp_item_b); dfree(bw_n); dfree(bw_off);
   }
@@ -208,6 +212,8 @@ struct fst_plan_s {
   double* logz = nullptr;
   uint32_t *epoch = nullptr, *clear = nullptr;
   uint32_t *abm = nullptr, *bbm = nullptr;  // [3][max_bw][W] live-state bitmaps
+  uint8_t* wlive = nullptr;                 // per (token, forward window) liveness of the largest wave
+  int64_t max_nwins = 0;
   int64_t max_bw = 0, max_ntok = 0, max_store = 0, max_lseg = 0, max_lwin = 0;
   bool forward_done = false;
   // optional per-launch CUDA events (fst_plan_profile)
@@ -220,7 +226,7 @@ struct fst_plan_s {
     for (Wave& w : waves) w.release();
     dfree(ids); dfree(alpha); dfree(beta); dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum);
     dfree(esum); dfree(skey); dfree(scnt); dfree(spart); dfree(qfinal); dfree(cnt64); dfree(logz);
-    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm);
+    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(wlive);
   }
 };
 
@@ -279,6 +285,7 @@ int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, cudaSt
       (rc = alloc_track(P, &W.tok_t, n)) || (rc = alloc_track(P, &W.cbase, n + 1)) ||
       (rc = alloc_track(P, &W.lbase_f, n + 1)) || (rc = alloc_track(P, &W.lwbase_f, n + 1)) ||
       (rc = alloc_track(P, &W.lbase_b, n + 1)) || (rc = alloc_track(P, &W.lwbase_b, n + 1)) ||
+      (rc = alloc_track(P, &W.wbase, n + 1)) ||
       (rc = alloc_track(P, &W.sorted_tok, n)))
     return rc;
   FST_CUDA(cudaMemcpy(W.bw_off, boff.data(), (size_t)W.Bw * 8, cudaMemcpyHostToDevice));
@@ -287,18 +294,20 @@ int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, cudaSt
     k_tok_info<<<nblk((int64_t)W.Bw * 32), TB, 0, s>>>(P->ids + W.tok0, W.bw_off, W.bw_n, W.Bw, W.tok_sym, W.tok_b,
                                                        W.tok_t);
   // per-token storage and scratch bases
-  int64_t *c[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t *c[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   for (auto& p : c)
     if ((rc = dalloc(&p, n))) { for (auto& q : c) dfree(q); return rc; }
   if (W.ntok > 0)
     k_tok_counts<<<nblk(W.ntok), TB, 0, s>>>(W.tok_sym, W.ntok, f->fwd.sym_seg, f->fwd.sym_lseg, f->fwd.sym_lwin,
-                                             f->bwd.sym_lseg, f->bwd.sym_lwin, c[0], c[1], c[2], c[3], c[4]);
-  int64_t tot[5] = {0, 0, 0, 0, 0};
-  int64_t* outs[5] = {W.cbase, W.lbase_f, W.lwbase_f, W.lbase_b, W.lwbase_b};
-  for (int i = 0; i < 5 && !rc; ++i) rc = exclusive_scan_i64(c[i], outs[i], W.ntok, &tot[i], s);
+                                             f->bwd.sym_lseg, f->bwd.sym_lwin, f->fwd.sym_win, c[0], c[1], c[2], c[3],
+                                             c[4], c[5]);
+  int64_t tot[6] = {0, 0, 0, 0, 0, 0};
+  int64_t* outs[6] = {W.cbase, W.lbase_f, W.lwbase_f, W.lbase_b, W.lwbase_b, W.wbase};
+  for (int i = 0; i < 6 && !rc; ++i) rc = exclusive_scan_i64(c[i], outs[i], W.ntok, &tot[i], s);
   for (auto& q : c) dfree(q);
   if (rc) return rc;
   W.store = tot[0];
+  W.nwins = tot[5];
   W.nlseg = std::max(tot[1], tot[3]);
   W.nlwin = std::max(tot[2], tot[4]);
   // sort tokens by (position, symbol) and cut groups
@@ -396,6 +405,7 @@ WaveState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.bm_final = f->bm_final;
   S.W = f->W;
   S.bm_rot = P->max_bw * (int64_t)f->W;
+  S.wlive = P->wlive;
   return S;
 }
 
@@ -407,7 +417,7 @@ int clear_rot(fst_plan_s* P, uint32_t* bm, int32_t r, cudaStream_t s) {
 }
 
 TokenView wave_tokens(const Wave& W) {
-  return TokenView{W.tok_sym, W.tok_b, W.tok_t, W.cbase, W.lbase_f, W.lbase_b, W.lwbase_f, W.lwbase_b};
+  return TokenView{W.tok_sym, W.tok_b, W.tok_t, W.cbase, W.lbase_f, W.lbase_b, W.lwbase_f, W.lwbase_b, W.wbase};
 }
 
 WorkView wave_work(const Wave& W, int32_t t, bool fwd) {
@@ -448,6 +458,7 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   const WaveState S = wave_state(P, W, nullptr);
   FST_CUDA(cudaMemsetAsync(P->mkey, 0, (size_t)std::max<int64_t>(1, W.ntok) * 4, s));
   FST_CUDA(cudaMemsetAsync(P->ekey, 0, (size_t)std::max<int64_t>(1, W.ntok) * 4, s));
+  FST_CUDA(cudaMemsetAsync(P->wlive, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
   for (int32_t t = 1; t <= W.tmax; ++t) {
     const WorkView V = wave_work(W, t, true);
     if ((rc = clear_rot(P, P->abm, t % 3, s))) return rc;
@@ -573,6 +584,7 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
       P->max_lseg = std::max<int64_t>(P->max_lseg, w.nlseg);
       P->max_lwin = std::max<int64_t>(P->max_lwin, w.nlwin);
       P->max_len = std::max(P->max_len, w.tmax);
+      P->max_nwins = std::max(P->max_nwins, w.nwins);
     }
     if (rc) break;
     const int64_t na = P->max_bw * 2 * (int64_t)f->Q;
@@ -590,6 +602,7 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
     if (want_fb && (rc = alloc_track(P, &P->cnt64, f->bwd.P))) break;
     if ((rc = alloc_track(P, &P->abm, 3 * P->max_bw * (int64_t)f->W))) break;
     if (want_fb && (rc = alloc_track(P, &P->bbm, 3 * P->max_bw * (int64_t)f->W))) break;
+    if (want_fb && (rc = alloc_track(P, &P->wlive, P->max_nwins))) break;
     FST_CUDA(cudaMemsetAsync(P->alpha, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     FST_CUDA(cudaMemsetAsync(P->epoch, 0, 8, s));
