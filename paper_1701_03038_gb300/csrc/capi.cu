@@ -86,6 +86,18 @@ __global__ void k_finite_bitmap(const float* __restrict__ w, int32_t Q, uint32_t
   bm[i] = m;
 }
 
+// bit j of summary word i is set when bitmap word 32 i + j is nonzero
+__global__ void k_bitmap_summary(const uint32_t* __restrict__ bm, int32_t W, uint32_t* __restrict__ sum, int32_t Ws) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ws) return;
+  uint32_t m = 0;
+  for (int k = 0; k < 32; ++k) {
+    const int64_t w = i * 32 + k;
+    if (w < W && bm[w] != 0u) m |= 1u << k;
+  }
+  sum[i] = m;
+}
+
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -169,9 +181,10 @@ struct PlainWs {
   int64_t* bw_off = nullptr;
   uint32_t *epoch = nullptr, *clear = nullptr;
   uint32_t *abm = nullptr, *bbm = nullptr;  // [3][W] live-state bitmaps
+  uint32_t *asum = nullptr, *bsum = nullptr;  // [3][Ws] their summaries
   int64_t max_lseg = 0, max_lwin = 0;
   ~PlainWs() {
-    dfree(abm); dfree(bbm); dfree(wbase); dfree(wlive);
+    dfree(abm); dfree(bbm); dfree(asum); dfree(bsum); dfree(wbase); dfree(wlive);
     dfree(alpha); dfree(beta); dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(zero64);
     dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(skey); dfree(scnt);
     dfree(spart); dfree(cnt); dfree(comp); dfree(counts_out); dfree(paths); dfree(olabels); dfree(qfinal);
@@ -200,7 +213,8 @@ int plain_init(fst_s* f) {
       (rc = dalloc(&w->qfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
       (rc = dalloc(&w->logz, 1)) || (rc = dalloc(&w->bw_n, 1)) || (rc = dalloc(&w->bw_off, 1)) ||
       (rc = dalloc(&w->epoch, 2)) || (rc = dalloc(&w->clear, 1)) || (rc = dalloc(&w->abm, 3 * (int64_t)f->W)) ||
-      (rc = dalloc(&w->bbm, 3 * (int64_t)f->W)))
+      (rc = dalloc(&w->bbm, 3 * (int64_t)f->W)) || (rc = dalloc(&w->asum, 3 * (int64_t)f->Ws)) ||
+      (rc = dalloc(&w->bsum, 3 * (int64_t)f->Ws)))
     return rc;
   FST_CUDA(cudaMemset(w->alpha, 0, (size_t)2 * Q * sizeof(unsigned long long)));
   FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(unsigned long long)));
@@ -317,6 +331,12 @@ WaveState plain_state(fst_s* f) {
   S.W = f->W;
   S.bm_rot = f->W;
   S.wlive = w->wlive;
+  S.asum = w->asum;
+  S.bsum = w->bsum;
+  S.sum_start = f->sum_start;
+  S.sum_final = f->sum_final;
+  S.Ws = f->Ws;
+  S.sum_rot = f->Ws;
   return S;
 }
 
@@ -423,6 +443,10 @@ extern "C" int fst_create(int32_t num_states, int64_t num_arcs, const int32_t* s
     if ((rc = dalloc(&f->bm_start, f->W)) || (rc = dalloc(&f->bm_final, f->W))) break;
     k_finite_bitmap<<<nblk(f->W), TB, 0, s>>>(f->theta_s, f->Q, f->bm_start, f->W);
     k_finite_bitmap<<<nblk(f->W), TB, 0, s>>>(f->theta_f, f->Q, f->bm_final, f->W);
+    f->Ws = (f->W + 31) / 32;
+    if ((rc = dalloc(&f->sum_start, f->Ws)) || (rc = dalloc(&f->sum_final, f->Ws))) break;
+    k_bitmap_summary<<<nblk(f->Ws), TB, 0, s>>>(f->bm_start, f->W, f->sum_start, f->Ws);
+    k_bitmap_summary<<<nblk(f->Ws), TB, 0, s>>>(f->bm_final, f->W, f->sum_final, f->Ws);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { rc = cuda_fail(e, "fst_create kernels"); break; }
     if ((rc = read_err_flag(d_err, "fst_create"))) break;
@@ -448,6 +472,8 @@ extern "C" int fst_destroy(fst_t* f) {
   dfree(f->theta_f);
   dfree(f->bm_start);
   dfree(f->bm_final);
+  dfree(f->sum_start);
+  dfree(f->sum_final);
   dfree(f->olabel);
   dfree(f->sym_arc);
   free(f->h_sym_arc);
@@ -529,7 +555,7 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
   for (int32_t t = 1; t <= n; ++t) {
     const int32_t a = ids[t - 1];
     const int64_t nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
-    if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
+    if ((rc = clear_rot(w->abm, t % 3, f->W, s)) || (rc = clear_rot(w->asum, t % 3, f->Ws, s))) return rc;
     if ((rc = launch_vit_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
   }
   if ((rc = launch_vit_final(Lf, w->tok_sym, w->cbase, S, 1, w->score, w->qfinal, w->status, s))) return rc;
@@ -575,7 +601,7 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   for (int32_t t = 1; t <= n; ++t) {
     const int32_t a = ids[t - 1];
     const int64_t nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
-    if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
+    if ((rc = clear_rot(w->abm, t % 3, f->W, s)) || (rc = clear_rot(w->asum, t % 3, f->Ws, s))) return rc;
     if ((rc = launch_fwd_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
   }
   if ((rc = launch_fb_final(Lf, w->tok_sym, w->cbase, S, 1, w->logz, w->status, s))) return rc;
@@ -591,7 +617,8 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
       }
       const int32_t a = ids[t - 1];
       const int64_t nitems = f->bwd.h_sym_win[a + 1] - f->bwd.h_sym_win[a];
-      if (t >= 2 && (rc = clear_rot(w->bbm, (t - 1) % 3, f->W, s))) return rc;
+      if (t >= 2 && ((rc = clear_rot(w->bbm, (t - 1) % 3, f->W, s)) || (rc = clear_rot(w->bsum, (t - 1) % 3, f->Ws, s))))
+        return rc;
       if ((rc = launch_bwd_step(Lb, T, single_work(t - 1, a, nitems), S, C, step_grid(f, nitems), s))) return rc;
     }
     if ((rc = launch_counts_out(f->bwd.arc_id, f->bwd.P, C, w->counts_out, s))) return rc;

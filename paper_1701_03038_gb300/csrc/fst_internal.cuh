@@ -75,6 +75,9 @@ struct fst_s {
   int32_t W = 0;               // 32-bit words of a state bitmap, ceil(Q / 32)
   uint32_t* bm_start = nullptr;  // [W] states with a finite start weight
   uint32_t* bm_final = nullptr;  // [W] states with a finite final weight
+  int32_t Ws = 0;                // words of a bitmap summary, ceil(W / 32)
+  uint32_t* sum_start = nullptr; // [Ws] bit i = word i of bm_start is nonzero
+  uint32_t* sum_final = nullptr; // [Ws]
   int32_t* olabel = nullptr;   // [A] by caller arc id
   int64_t* sym_arc = nullptr;  // [m+1] R offsets (device)
   int64_t* h_sym_arc = nullptr;

@@ -165,39 +165,55 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Bitmap words of the arcs' gather states (issued early so that the loads
-// of the next token overlap the work of the current one).
-__device__ __forceinline__ void bitmap_words(const uint32_t* __restrict__ bm, const int32_t (&st)[APL],
-                                             uint32_t (&wd)[APL]) {
+// Two-level liveness of the arcs' gather states.  The summary word (one bit
+// per 32-state block) is read first -- it is small enough to stay in L1 --
+// and the state's own bitmap word only when its block holds a live state.
+// Summary words of the next token are issued early so their loads overlap
+// the current token's work.
+struct Live {
+  const uint32_t* fine;
+  const uint32_t* sum;
+};
+
+__device__ __forceinline__ void summary_words(const uint32_t* __restrict__ sum, const int32_t (&st)[APL],
+                                              uint32_t (&wd)[APL]) {
 #pragma unroll
-  for (int k = 0; k < APL; ++k) wd[k] = __ldg(bm + (st[k] >> 5));
+  for (int k = 0; k < APL; ++k) wd[k] = __ldg(sum + (st[k] >> 10));
 }
-__device__ __forceinline__ uint32_t live_of(const uint32_t (&wd)[APL], const int32_t (&st)[APL]) {
+
+__device__ __forceinline__ uint32_t live_of(const uint32_t* __restrict__ fine, const uint32_t (&sw)[APL],
+                                            const int32_t (&st)[APL]) {
   uint32_t m = 0;
 #pragma unroll
-  for (int k = 0; k < APL; ++k) m |= ((wd[k] >> (st[k] & 31)) & 1u) << k;
+  for (int k = 0; k < APL; ++k)
+    if ((sw[k] >> ((st[k] >> 5) & 31)) & 1u) m |= ((__ldg(fine + (st[k] >> 5)) >> (st[k] & 31)) & 1u) << k;
   return m;
 }
 
-__device__ __forceinline__ void set_live(uint32_t* bm, int32_t q) { atomicOr(bm + (q >> 5), 1u << (q & 31)); }
+__device__ __forceinline__ void set_live(uint32_t* fine, uint32_t* sum, int32_t q) {
+  atomicOr(fine + (q >> 5), 1u << (q & 31));
+  atomicOr(sum + (q >> 10), 1u << ((q >> 5) & 31));
+}
 
 // ======================================================================
 // Viterbi step (Alg. 1 inner loop; Sec. 5.1)
 // ======================================================================
 __device__ __forceinline__ void vit_write(const LayoutView& L, const WaveState& S, int64_t cb, int32_t s,
                                           int32_t sl, unsigned long long key, unsigned long long* aout,
-                                          uint32_t tag, uint32_t* bmout) {
+                                          uint32_t tag, uint32_t* bmout, uint32_t* smout) {
   S.bp[cb + sl] = key ? (int32_t)(~(uint32_t)key) : -1;
   if (key) {
     const int32_t q = __ldg(L.seg_state + s);
     aout[q] = tagged_make(fkey_inv((uint32_t)(key >> 32)), tag);
-    set_live(bmout, q);
+    set_live(bmout, smout, q);
   }
 }
 
-__device__ __forceinline__ const uint32_t* fwd_bitmap(const WaveState& S, int32_t b, int32_t t) {
+__device__ __forceinline__ Live fwd_live(const WaveState& S, int32_t b, int32_t t) {
   // liveness of the forward values the position-t relaxation reads
-  return t == 1 ? S.bm_start : S.abm + (int64_t)((t - 1) % 3) * S.bm_rot + (int64_t)b * S.W;
+  if (t == 1) return Live{S.bm_start, S.sum_start};
+  const int64_t r = (t - 1) % 3;
+  return Live{S.abm + r * S.bm_rot + (int64_t)b * S.W, S.asum + r * S.sum_rot + (int64_t)b * S.Ws};
 }
 
 __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
@@ -226,14 +242,14 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
     const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
     uint32_t wn[APL];
-    bitmap_words(fwd_bitmap(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)), src, wn);
+    summary_words(fwd_live(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)).sum, src, wn);
     for (int j = 0; j < G.cnt; ++j) {
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       // every arc is relaxed; a source whose bit is clear contributes -inf
       // without reading its 8-byte frontier entry
-      const uint32_t lv = live_of(wn, src);
+      const uint32_t lv = live_of(fwd_live(S, b, t).fine, wn, src);
       if (j + 1 < G.cnt)
-        bitmap_words(fwd_bitmap(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1)), src, wn);
+        summary_words(fwd_live(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1)).sum, src, wn);
       if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no live source: every segment stays -inf
       float a[APL];
       if (t == 1) {
@@ -258,6 +274,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
       const int64_t cb = shfl64(tcb, j);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
       uint32_t* bmout = S.abm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W;
+      uint32_t* smout = S.asum + (int64_t)(t % 3) * S.sum_rot + (int64_t)b * S.Ws;
       const uint32_t tag = tag_base + (uint32_t)p;
       if (!is_long) {
         int cum = x.hb;
@@ -267,7 +284,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
           const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
           if (tail) {
             const int32_t s = x.seg + cum - 1;
-            vit_write(L, S, cb, s, s - G.segbase, full[k], aout, tag, bmout);
+            vit_write(L, S, cb, s, s - G.segbase, full[k], aout, tag, bmout, smout);
           }
         }
       } else {
@@ -281,7 +298,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
           if (prev == (uint32_t)x.lcnt - 1u) {
             __threadfence();
             const unsigned long long kf = atomicMax(S.skey + slot, 0ull);
-            vit_write(L, S, cb, x.seg, x.seg - G.segbase, kf, aout, tag, bmout);
+            vit_write(L, S, cb, x.seg, x.seg - G.segbase, kf, aout, tag, bmout, smout);
             S.skey[slot] = 0ull;
             S.scnt[slot] = 0u;
           }
@@ -359,13 +376,13 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
     const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
     uint32_t wn[APL];
-    bitmap_words(fwd_bitmap(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)), src, wn);
+    summary_words(fwd_live(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)).sum, src, wn);
     for (int j = 0; j < G.cnt; ++j) {
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const float mprev = __shfl_sync(FULL, tm, j);
-      const uint32_t lv = live_of(wn, src);
+      const uint32_t lv = live_of(fwd_live(S, b, t).fine, wn, src);
       if (j + 1 < G.cnt)
-        bitmap_words(fwd_bitmap(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1)), src, wn);
+        summary_words(fwd_live(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1)).sum, src, wn);
       const int64_t cb = shfl64(tcb, j);
       if (!is_long && !__any_sync(FULL, lv != 0u)) {
         // no live source: every segment of the window is -inf at this position
@@ -401,6 +418,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
       window_scan<LogAdd>(e, x.h, lane, full);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
       uint32_t* bmout = S.abm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W;
+      uint32_t* smout = S.asum + (int64_t)(t % 3) * S.sum_rot + (int64_t)b * S.Ws;
       const uint32_t tag = tag_base + (uint32_t)p;
       float rmax = neg_inf();
       if (!is_long) {
@@ -416,7 +434,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
             if (r != neg_inf()) {
               const int32_t q = __ldg(L.seg_state + s);
               aout[q] = tagged_make(r, tag);
-              set_live(bmout, q);
+              set_live(bmout, smout, q);
             }
             rmax = fmaxf(rmax, r);
           }
@@ -435,7 +453,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
             if (r != neg_inf()) {
               const int32_t q = __ldg(L.seg_state + x.seg);
               aout[q] = tagged_make(r, tag);
-              set_live(bmout, q);
+              set_live(bmout, smout, q);
               // the segment's first window carries its head
               S.wlive[wbt + (__ldg(L.seg_pos + x.seg) / WIN - G.wbase)] = 1;
             }
@@ -503,9 +521,11 @@ __global__ void __launch_bounds__(KT) k_scatter_alpha(LayoutView L, TokenView T,
 // Backward step fused with the expected counts (Alg. 2 backward loop and
 // count loop; Sec. 5.2).  Segments are by source state.
 // ======================================================================
-__device__ __forceinline__ const uint32_t* bwd_bitmap(const WaveState& S, int32_t b, int32_t t, int32_t n) {
+__device__ __forceinline__ Live bwd_live(const WaveState& S, int32_t b, int32_t t, int32_t n) {
   // liveness of the backward values the position-t relaxation reads
-  return t == n ? S.bm_final : S.bbm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W;
+  if (t == n) return Live{S.bm_final, S.sum_final};
+  const int64_t r = t % 3;
+  return Live{S.bbm + r * S.bm_rot + (int64_t)b * S.W, S.bsum + r * S.sum_rot + (int64_t)b * S.Ws};
 }
 
 __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L, TokenView T, WorkView W,
@@ -562,18 +582,18 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
     }
     float gacc[APL] = {0.f, 0.f, 0.f, 0.f};
     uint32_t wn[APL];
-    bitmap_words(bwd_bitmap(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0), __shfl_sync(FULL, tn, 0)), dst,
-                 wn);
+    summary_words(bwd_live(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0), __shfl_sync(FULL, tn, 0)).sum, dst,
+                  wn);
     for (int j = 0; j < G.cnt; ++j) {
       const bool live_tok = __shfl_sync(FULL, tlive, j);
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const int32_t n = __shfl_sync(FULL, tn, j);
       // beta_t at the destinations; a destination whose bit is clear is -inf
-      const uint32_t lv = live_of(wn, dst);
+      const uint32_t lv = live_of(bwd_live(S, b, t, n).fine, wn, dst);
       if (j + 1 < G.cnt)
-        bitmap_words(bwd_bitmap(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1),
-                                __shfl_sync(FULL, tn, j + 1)),
-                     dst, wn);
+        summary_words(bwd_live(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1),
+                               __shfl_sync(FULL, tn, j + 1)).sum,
+                      dst, wn);
       if (!live_tok) continue;
       if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no arc reaches a live state: nothing to add
       // raw values: ub = beta_t[dst] before its step shift (theta_f at the
@@ -604,6 +624,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
         window_scan<LogAdd>(e, x.h, lane, full);
         unsigned long long* bout = S.beta + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
         uint32_t* bmout = S.bbm + (int64_t)((t - 1) % 3) * S.bm_rot + (int64_t)b * S.W;
+        uint32_t* smout = S.bsum + (int64_t)((t - 1) % 3) * S.sum_rot + (int64_t)b * S.Ws;
         const uint32_t tag = tag_base + (uint32_t)(p - 1);
         float umax = neg_inf();
         if (!is_long) {
@@ -616,7 +637,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
               const float u = lse_value(full[k]);
               if (u != neg_inf()) {
                 bout[qs[k]] = tagged_make(u, tag);
-                set_live(bmout, qs[k]);
+                set_live(bmout, smout, qs[k]);
               }
               umax = fmaxf(umax, u);
             }
@@ -629,7 +650,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
             if (lane == 0 && u != neg_inf()) {
               const int32_t q = __ldg(L.seg_state + x.seg);
               bout[q] = tagged_make(u, tag);
-              set_live(bmout, q);
+              set_live(bmout, smout, q);
             }
             umax = u;
           }

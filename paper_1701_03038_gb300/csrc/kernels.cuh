@@ -83,6 +83,14 @@ struct WaveState {
   const uint32_t* bm_final;          // states with a finite final weight
   int32_t W;                         // 32-bit words per bitmap
   int64_t bm_rot;
+  // Summaries of the bitmaps: bit i of a summary is set when word i of the
+  // bitmap is nonzero (one bit per 32 states), same rotation layout.
+  uint32_t* asum;
+  uint32_t* bsum;
+  const uint32_t* sum_start;
+  const uint32_t* sum_final;
+  int32_t Ws;                        // 32-bit words per summary
+  int64_t sum_rot;
   // one byte per (token, forward window): 1 when the window wrote a finite
   // forward value for that token (cleared before each forward pass)
   uint8_t* wlive;

@@ -109,7 +109,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
     max_lseg = std::max<int64_t>(max_lseg, f->fwd.h_sym_lseg[a + 1] - f->fwd.h_sym_lseg[a]);
   const int64_t Q = f->Q, W = f->W;
   auto rnd = [](int64_t bytes) { return ((bytes > 0 ? bytes : 1) + 255) & ~(int64_t)255; };
-  const int64_t need = rnd(2 * Q * 8) + rnd(3 * W * 4) + 3 * rnd((int64_t)n * 4) + 2 * rnd((int64_t)n * 8) +
+  const int64_t need = rnd(2 * Q * 8) + rnd(3 * W * 4) + rnd(3 * (int64_t)f->Ws * 4) + 3 * rnd((int64_t)n * 4) + 2 * rnd((int64_t)n * 8) +
                        rnd(store * 4) + rnd(max_lseg * 8) + rnd(max_lseg * 4) + 5 * rnd(8) + rnd(4) + rnd(8);
   if (need > (int64_t)NOALLOC_SCRATCH_BYTES) {
     set_error("fst_viterbi_noalloc: this string needs %lld bytes of working memory, beyond the fixed %llu bytes "
@@ -123,6 +123,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   Carver c{(unsigned char*)base};
   unsigned long long* alpha = c.take<unsigned long long>(2 * Q);
   uint32_t* abm = c.take<uint32_t>(3 * W);
+  uint32_t* asum = c.take<uint32_t>(3 * (int64_t)f->Ws);
   int32_t* tok_sym = c.take<int32_t>(n);
   int32_t* tok_b = c.take<int32_t>(n);
   int32_t* tok_t = c.take<int32_t>(n);
@@ -168,6 +169,10 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.bm_final = f->bm_final;
   S.W = f->W;
   S.bm_rot = f->W;
+  S.asum = asum;
+  S.sum_start = f->sum_start;
+  S.Ws = f->Ws;
+  S.sum_rot = f->Ws;
   const TokenView T{tok_sym, tok_b, tok_t, cbase, zero64, zero64, zero64, zero64, zero64};
   const LayoutView Lf = view_of(f->fwd);
   for (int32_t t = 1; t <= n; ++t) {
@@ -179,6 +184,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
     V.sym0 = a;
     V.nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
     FST_CUDA(cudaMemsetAsync(abm + (int64_t)(t % 3) * W, 0, (size_t)W * 4, s));
+    FST_CUDA(cudaMemsetAsync(asum + (int64_t)(t % 3) * f->Ws, 0, (size_t)f->Ws * 4, s));
     if ((rc = launch_vit_step(Lf, T, V, S, f->num_sms, s))) return rc;
   }
   if ((rc = launch_vit_final(Lf, tok_sym, cbase, S, 1, d_score, qfinal, status, s))) return rc;

@@ -212,6 +212,7 @@ struct fst_plan_s {
   double* logz = nullptr;
   uint32_t *epoch = nullptr, *clear = nullptr;
   uint32_t *abm = nullptr, *bbm = nullptr;  // [3][max_bw][W] live-state bitmaps
+  uint32_t *asum = nullptr, *bsum = nullptr;  // [3][max_bw][Ws] their summaries
   uint8_t* wlive = nullptr;                 // per (token, forward window) liveness of the largest wave
   int64_t max_nwins = 0;
   int64_t max_bw = 0, max_ntok = 0, max_store = 0, max_lseg = 0, max_lwin = 0;
@@ -226,7 +227,7 @@ struct fst_plan_s {
     for (Wave& w : waves) w.release();
     dfree(ids); dfree(alpha); dfree(beta); dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum);
     dfree(esum); dfree(skey); dfree(scnt); dfree(spart); dfree(qfinal); dfree(cnt64); dfree(logz);
-    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(wlive);
+    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(asum); dfree(bsum); dfree(wlive);
   }
 };
 
@@ -406,12 +407,19 @@ WaveState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.W = f->W;
   S.bm_rot = P->max_bw * (int64_t)f->W;
   S.wlive = P->wlive;
+  S.asum = P->asum;
+  S.bsum = P->bsum;
+  S.sum_start = f->sum_start;
+  S.sum_final = f->sum_final;
+  S.Ws = f->Ws;
+  S.sum_rot = P->max_bw * (int64_t)f->Ws;
   return S;
 }
 
-// Clear rotation r of a [3][max_bw][W] bitmap set before the launch that fills it.
-int clear_rot(fst_plan_s* P, uint32_t* bm, int32_t r, cudaStream_t s) {
-  const int64_t words = P->max_bw * (int64_t)P->fst->W;
+// Clear rotation r of a [3][max_bw][words] bitmap (or summary) set before the
+// launch that fills it.
+int clear_rot(fst_plan_s* P, uint32_t* bm, int32_t r, int32_t words_per_string, cudaStream_t s) {
+  const int64_t words = P->max_bw * (int64_t)words_per_string;
   FST_CUDA(cudaMemsetAsync(bm + (int64_t)r * words, 0, (size_t)std::max<int64_t>(words, 1) * 4, s));
   return FST_OK;
 }
@@ -461,7 +469,7 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   FST_CUDA(cudaMemsetAsync(P->wlive, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
   for (int32_t t = 1; t <= W.tmax; ++t) {
     const WorkView V = wave_work(W, t, true);
-    if ((rc = clear_rot(P, P->abm, t % 3, s))) return rc;
+    if ((rc = clear_rot(P, P->abm, t % 3, f->W, s)) || (rc = clear_rot(P, P->asum, t % 3, f->Ws, s))) return rc;
     PROF(FST_PROF_FWD_STEP, launch_fwd_step(Lf, T, V, S, step_grid(f, V.nitems), s));
   }
   PROF(FST_PROF_FB_FINAL, launch_fb_final(Lf, W.tok_sym, W.cbase, S, W.Bw, P->logz + W.b0,
@@ -482,7 +490,9 @@ int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cuda
       PROF(FST_PROF_SCATTER, launch_scatter_alpha(Lf, T, V, S, t, step_grid(f, V.nitems), s));
     }
     const WorkView V = wave_work(W, t, false);
-    if (t >= 2 && (rc = clear_rot(P, P->bbm, (t - 1) % 3, s))) return rc;
+    if (t >= 2 && ((rc = clear_rot(P, P->bbm, (t - 1) % 3, f->W, s)) ||
+                   (rc = clear_rot(P, P->bsum, (t - 1) % 3, f->Ws, s))))
+      return rc;
     PROF(FST_PROF_BWD_STEP, launch_bwd_step(Lb, T, V, S, C, step_grid(f, V.nitems), s));
   }
   return FST_OK;
@@ -601,7 +611,9 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
       break;
     if (want_fb && (rc = alloc_track(P, &P->cnt64, f->bwd.P))) break;
     if ((rc = alloc_track(P, &P->abm, 3 * P->max_bw * (int64_t)f->W))) break;
+    if ((rc = alloc_track(P, &P->asum, 3 * P->max_bw * (int64_t)f->Ws))) break;
     if (want_fb && (rc = alloc_track(P, &P->bbm, 3 * P->max_bw * (int64_t)f->W))) break;
+    if (want_fb && (rc = alloc_track(P, &P->bsum, 3 * P->max_bw * (int64_t)f->Ws))) break;
     if (want_fb && (rc = alloc_track(P, &P->wlive, P->max_nwins))) break;
     FST_CUDA(cudaMemsetAsync(P->alpha, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
@@ -666,7 +678,7 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
     const WaveState S = wave_state(P, W, nullptr);
     for (int32_t t = 1; t <= W.tmax; ++t) {
       const WorkView V = wave_work(W, t, true);
-      if ((rc = clear_rot(P, P->abm, t % 3, s))) return rc;
+      if ((rc = clear_rot(P, P->abm, t % 3, f->W, s)) || (rc = clear_rot(P, P->asum, t % 3, f->Ws, s))) return rc;
       PROF(FST_PROF_VIT_STEP, launch_vit_step(Lf, T, V, S, step_grid(f, V.nitems), s));
     }
     PROF(FST_PROF_VIT_FINAL, launch_vit_final(Lf, W.tok_sym, W.cbase, S, W.Bw, d_scores + W.b0, P->qfinal,
