@@ -181,10 +181,11 @@ struct PlainWs {
   int64_t* bw_off = nullptr;
   uint32_t *epoch = nullptr, *clear = nullptr;
   uint32_t *abm = nullptr, *bbm = nullptr;  // [3][W] live-state bitmaps
-  uint32_t *asum = nullptr, *bsum = nullptr;  // [3][Ws] their summaries
+  uint32_t *tsum = nullptr, *bsum = nullptr;  // per-token forward summaries [n][Ws]; backward [3][Ws]
+  int64_t cap_tsum = 0;
   int64_t max_lseg = 0, max_lwin = 0;
   ~PlainWs() {
-    dfree(abm); dfree(bbm); dfree(asum); dfree(bsum); dfree(wbase); dfree(wlive);
+    dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wbase); dfree(wlive);
     dfree(alpha); dfree(beta); dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(zero64);
     dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(skey); dfree(scnt);
     dfree(spart); dfree(cnt); dfree(comp); dfree(counts_out); dfree(paths); dfree(olabels); dfree(qfinal);
@@ -213,8 +214,7 @@ int plain_init(fst_s* f) {
       (rc = dalloc(&w->qfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
       (rc = dalloc(&w->logz, 1)) || (rc = dalloc(&w->bw_n, 1)) || (rc = dalloc(&w->bw_off, 1)) ||
       (rc = dalloc(&w->epoch, 2)) || (rc = dalloc(&w->clear, 1)) || (rc = dalloc(&w->abm, 3 * (int64_t)f->W)) ||
-      (rc = dalloc(&w->bbm, 3 * (int64_t)f->W)) || (rc = dalloc(&w->asum, 3 * (int64_t)f->Ws)) ||
-      (rc = dalloc(&w->bsum, 3 * (int64_t)f->Ws)))
+      (rc = dalloc(&w->bbm, 3 * (int64_t)f->W)) || (rc = dalloc(&w->bsum, 3 * (int64_t)f->Ws)))
     return rc;
   FST_CUDA(cudaMemset(w->alpha, 0, (size_t)2 * Q * sizeof(unsigned long long)));
   FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(unsigned long long)));
@@ -278,6 +278,14 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
   }
   int rc = plain_reserve(w, std::max(n, 1), std::max<int64_t>(acc, 1), std::max<int64_t>(wacc, 1));
   if (rc) return rc;
+  const int64_t ntsum = std::max<int64_t>((int64_t)n * f->Ws, 1);
+  if (ntsum > w->cap_tsum) {
+    dfree(w->tsum);
+    w->cap_tsum = 0;
+    if ((rc = dalloc(&w->tsum, std::max<int64_t>(ntsum, 2 * w->cap_tsum)))) return rc;
+    w->cap_tsum = ntsum;
+  }
+  FST_CUDA(cudaMemsetAsync(w->tsum, 0, (size_t)ntsum * 4, s));
   if (n > 0) {
     FST_CUDA(cudaMemcpyAsync(w->tok_sym, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     FST_CUDA(cudaMemcpyAsync(w->tok_t, tt.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
@@ -331,7 +339,7 @@ WaveState plain_state(fst_s* f) {
   S.W = f->W;
   S.bm_rot = f->W;
   S.wlive = w->wlive;
-  S.asum = w->asum;
+  S.tsum = w->tsum;
   S.bsum = w->bsum;
   S.sum_start = f->sum_start;
   S.sum_final = f->sum_final;
@@ -555,7 +563,7 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
   for (int32_t t = 1; t <= n; ++t) {
     const int32_t a = ids[t - 1];
     const int64_t nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
-    if ((rc = clear_rot(w->abm, t % 3, f->W, s)) || (rc = clear_rot(w->asum, t % 3, f->Ws, s))) return rc;
+    if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
     if ((rc = launch_vit_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
   }
   if ((rc = launch_vit_final(Lf, w->tok_sym, w->cbase, S, 1, w->score, w->qfinal, w->status, s))) return rc;
@@ -601,7 +609,7 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   for (int32_t t = 1; t <= n; ++t) {
     const int32_t a = ids[t - 1];
     const int64_t nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
-    if ((rc = clear_rot(w->abm, t % 3, f->W, s)) || (rc = clear_rot(w->asum, t % 3, f->Ws, s))) return rc;
+    if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
     if ((rc = launch_fwd_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
   }
   if ((rc = launch_fb_final(Lf, w->tok_sym, w->cbase, S, 1, w->logz, w->status, s))) return rc;

@@ -209,11 +209,10 @@ __device__ __forceinline__ void vit_write(const LayoutView& L, const WaveState& 
   }
 }
 
-__device__ __forceinline__ Live fwd_live(const WaveState& S, int32_t b, int32_t t) {
-  // liveness of the forward values the position-t relaxation reads
+__device__ __forceinline__ Live fwd_live(const WaveState& S, int32_t p, int32_t b, int32_t t) {
+  // liveness of the forward values the position-t relaxation of token p reads
   if (t == 1) return Live{S.bm_start, S.sum_start};
-  const int64_t r = (t - 1) % 3;
-  return Live{S.abm + r * S.bm_rot + (int64_t)b * S.W, S.asum + r * S.sum_rot + (int64_t)b * S.Ws};
+  return Live{S.abm + (int64_t)((t - 1) % 3) * S.bm_rot + (int64_t)b * S.W, S.tsum + (int64_t)(p - 1) * S.Ws};
 }
 
 __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, TokenView T, WorkView W, WaveState S) {
@@ -242,14 +241,17 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
     const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
     uint32_t wn[APL];
-    summary_words(fwd_live(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)).sum, src, wn);
+    summary_words(fwd_live(S, __shfl_sync(FULL, tp, 0), __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)).sum, src,
+                  wn);
     for (int j = 0; j < G.cnt; ++j) {
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       // every arc is relaxed; a source whose bit is clear contributes -inf
       // without reading its 8-byte frontier entry
-      const uint32_t lv = live_of(fwd_live(S, b, t).fine, wn, src);
+      const uint32_t lv = live_of(fwd_live(S, p, b, t).fine, wn, src);
       if (j + 1 < G.cnt)
-        summary_words(fwd_live(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1)).sum, src, wn);
+        summary_words(fwd_live(S, __shfl_sync(FULL, tp, j + 1), __shfl_sync(FULL, tb, j + 1),
+                               __shfl_sync(FULL, tt, j + 1)).sum,
+                      src, wn);
       if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no live source: every segment stays -inf
       float a[APL];
       if (t == 1) {
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
       const int64_t cb = shfl64(tcb, j);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
       uint32_t* bmout = S.abm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W;
-      uint32_t* smout = S.asum + (int64_t)(t % 3) * S.sum_rot + (int64_t)b * S.Ws;
+      uint32_t* smout = S.tsum + (int64_t)p * S.Ws;
       const uint32_t tag = tag_base + (uint32_t)p;
       if (!is_long) {
         int cum = x.hb;
@@ -376,13 +378,16 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
     const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
     uint32_t wn[APL];
-    summary_words(fwd_live(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)).sum, src, wn);
+    summary_words(fwd_live(S, __shfl_sync(FULL, tp, 0), __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)).sum, src,
+                  wn);
     for (int j = 0; j < G.cnt; ++j) {
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const float mprev = __shfl_sync(FULL, tm, j);
-      const uint32_t lv = live_of(fwd_live(S, b, t).fine, wn, src);
+      const uint32_t lv = live_of(fwd_live(S, p, b, t).fine, wn, src);
       if (j + 1 < G.cnt)
-        summary_words(fwd_live(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1)).sum, src, wn);
+        summary_words(fwd_live(S, __shfl_sync(FULL, tp, j + 1), __shfl_sync(FULL, tb, j + 1),
+                               __shfl_sync(FULL, tt, j + 1)).sum,
+                      src, wn);
       const int64_t cb = shfl64(tcb, j);
       if (!is_long && !__any_sync(FULL, lv != 0u)) {
         // no live source: every segment of the window is -inf at this position
@@ -418,7 +423,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
       window_scan<LogAdd>(e, x.h, lane, full);
       unsigned long long* aout = S.alpha + ((int64_t)b * 2 + (t & 1)) * S.Q;
       uint32_t* bmout = S.abm + (int64_t)(t % 3) * S.bm_rot + (int64_t)b * S.W;
-      uint32_t* smout = S.asum + (int64_t)(t % 3) * S.sum_rot + (int64_t)b * S.Ws;
+      uint32_t* smout = S.tsum + (int64_t)p * S.Ws;
       const uint32_t tag = tag_base + (uint32_t)p;
       float rmax = neg_inf();
       if (!is_long) {
@@ -589,13 +594,25 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const int32_t n = __shfl_sync(FULL, tn, j);
       // beta_t at the destinations; a destination whose bit is clear is -inf
-      const uint32_t lv = live_of(bwd_live(S, b, t, n).fine, wn, dst);
+      uint32_t lv = live_of(bwd_live(S, b, t, n).fine, wn, dst);
       if (j + 1 < G.cnt)
         summary_words(bwd_live(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1),
                                __shfl_sync(FULL, tn, j + 1)).sum,
                       dst, wn);
       if (!live_tok) continue;
-      if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no arc reaches a live state: nothing to add
+      // Only sources whose forward value alpha_{t-1} is finite matter: every
+      // posterior through a dead source is zero, and a finite-alpha state
+      // reaches only finite-alpha states, so its backward value is exact
+      // without the pruned terms.  Coarse test here; the source's own value
+      // is read below.
+      {
+        const uint32_t* asm_ = (t == 1) ? S.sum_start : S.tsum + (int64_t)(p - 1) * S.Ws;
+        uint32_t al = 0;
+#pragma unroll
+        for (int k = 0; k < APL; ++k) al |= ((__ldg(asm_ + (qs[k] >> 10)) >> ((qs[k] >> 5) & 31)) & 1u) << k;
+        lv &= al;
+      }
+      if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no arc joins a live source to a live state
       // raw values: ub = beta_t[dst] before its step shift (theta_f at the
       // last position), ra = alpha_{t-1}[src] before its shift (theta_s at
       // the first); -inf where the state is dead
@@ -611,10 +628,21 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
 #pragma unroll
         for (int k = 0; k < APL; ++k) ub[k] = ((lv >> k) & 1u) ? tagged_value(__ldg(bb + dst[k]), tg) : neg_inf();
       }
+      // alpha_{t-1} at the sources (one state per segment: cached loads)
+      float ra[APL];
+      {
+        const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
+        const uint32_t tga = tag_base + (uint32_t)(p - 1);
+#pragma unroll
+        for (int k = 0; k < APL; ++k)
+          ra[k] = !((lv >> k) & 1u) ? neg_inf()
+                                    : (t == 1 ? __ldg(S.theta_s + qs[k]) : tagged_value(__ldg(ab + qs[k]), tga));
+      }
       const bool dead_shift = (et == neg_inf()) || (mprev == neg_inf());
       float v[APL];
 #pragma unroll
-      for (int k = 0; k < APL; ++k) v[k] = (ub[k] == neg_inf() || dead_shift) ? neg_inf() : th[k] + (ub[k] - et);
+      for (int k = 0; k < APL; ++k)
+        v[k] = (ub[k] == neg_inf() || ra[k] == neg_inf() || dead_shift) ? neg_inf() : th[k] + (ub[k] - et);
       // beta_{t-1} by source segment (not needed for t == 1)
       if (t >= 2) {
         float2 e[APL];
@@ -663,14 +691,10 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
       // a small number, so it is formed in float64 (live arcs only)
       const double K = __shfl_sync(FULL, tK, j);
       const float gw = __shfl_sync(FULL, tw, j);
-      const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
-      const uint32_t tga = tag_base + (uint32_t)(p - 1);
 #pragma unroll
       for (int k = 0; k < APL; ++k) {
         if (v[k] == neg_inf()) continue;
-        const float ra = (t == 1) ? __ldg(S.theta_s + qs[k]) : tagged_value(__ldg(ab + qs[k]), tga);
-        if (ra == neg_inf()) continue;
-        const double ex = ((double)ra - (double)mprev) + (double)th[k] + ((double)ub[k] - (double)et) + K;
+        const double ex = ((double)ra[k] - (double)mprev) + (double)th[k] + ((double)ub[k] - (double)et) + K;
         gacc[k] += __expf((float)ex) * gw;
       }
     }

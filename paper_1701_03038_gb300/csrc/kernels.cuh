@@ -84,8 +84,11 @@ struct WaveState {
   int32_t W;                         // 32-bit words per bitmap
   int64_t bm_rot;
   // Summaries of the bitmaps: bit i of a summary is set when word i of the
-  // bitmap is nonzero (one bit per 32 states), same rotation layout.
-  uint32_t* asum;
+  // bitmap is nonzero (one bit per 32 states).  Forward summaries are kept
+  // per token for the whole pass (tsum + p * Ws): the backward pass prunes
+  // its relaxation to sources whose forward value is finite.  Backward
+  // summaries rotate like the bitmaps.
+  uint32_t* tsum;
   uint32_t* bsum;
   const uint32_t* sum_start;
   const uint32_t* sum_final;

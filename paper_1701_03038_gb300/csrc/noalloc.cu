@@ -109,7 +109,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
     max_lseg = std::max<int64_t>(max_lseg, f->fwd.h_sym_lseg[a + 1] - f->fwd.h_sym_lseg[a]);
   const int64_t Q = f->Q, W = f->W;
   auto rnd = [](int64_t bytes) { return ((bytes > 0 ? bytes : 1) + 255) & ~(int64_t)255; };
-  const int64_t need = rnd(2 * Q * 8) + rnd(3 * W * 4) + rnd(3 * (int64_t)f->Ws * 4) + 3 * rnd((int64_t)n * 4) + 2 * rnd((int64_t)n * 8) +
+  const int64_t need = rnd(2 * Q * 8) + rnd(3 * W * 4) + rnd((int64_t)n * f->Ws * 4) + 3 * rnd((int64_t)n * 4) + 2 * rnd((int64_t)n * 8) +
                        rnd(store * 4) + rnd(max_lseg * 8) + rnd(max_lseg * 4) + 5 * rnd(8) + rnd(4) + rnd(8);
   if (need > (int64_t)NOALLOC_SCRATCH_BYTES) {
     set_error("fst_viterbi_noalloc: this string needs %lld bytes of working memory, beyond the fixed %llu bytes "
@@ -123,7 +123,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   Carver c{(unsigned char*)base};
   unsigned long long* alpha = c.take<unsigned long long>(2 * Q);
   uint32_t* abm = c.take<uint32_t>(3 * W);
-  uint32_t* asum = c.take<uint32_t>(3 * (int64_t)f->Ws);
+  uint32_t* tsum = c.take<uint32_t>((int64_t)n * f->Ws);
   int32_t* tok_sym = c.take<int32_t>(n);
   int32_t* tok_b = c.take<int32_t>(n);
   int32_t* tok_t = c.take<int32_t>(n);
@@ -146,6 +146,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   FST_CUDA(cudaMemsetAsync(skey, 0, (size_t)std::max<int64_t>(max_lseg, 1) * 8, s));
   FST_CUDA(cudaMemsetAsync(scnt, 0, (size_t)std::max<int64_t>(max_lseg, 1) * 4, s));
   FST_CUDA(cudaMemsetAsync(bw_off, 0, 8, s));
+  FST_CUDA(cudaMemsetAsync(tsum, 0, (size_t)std::max<int64_t>((int64_t)n * f->Ws, 1) * 4, s));
   if (n > 0) FST_CUDA(cudaMemcpyAsync(tok_sym, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   FST_CUDA(cudaMemcpyAsync(bw_n, &n, 4, cudaMemcpyHostToDevice, s));
   k_noalloc_tokens<<<1, 1, 0, s>>>(tok_sym, n, f->fwd.sym_seg, tok_t, cbase, epoch);
@@ -169,7 +170,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.bm_final = f->bm_final;
   S.W = f->W;
   S.bm_rot = f->W;
-  S.asum = asum;
+  S.tsum = tsum;
   S.sum_start = f->sum_start;
   S.Ws = f->Ws;
   S.sum_rot = f->Ws;
@@ -184,7 +185,6 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
     V.sym0 = a;
     V.nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
     FST_CUDA(cudaMemsetAsync(abm + (int64_t)(t % 3) * W, 0, (size_t)W * 4, s));
-    FST_CUDA(cudaMemsetAsync(asum + (int64_t)(t % 3) * f->Ws, 0, (size_t)f->Ws * 4, s));
     if ((rc = launch_vit_step(Lf, T, V, S, f->num_sms, s))) return rc;
   }
   if ((rc = launch_vit_final(Lf, tok_sym, cbase, S, 1, d_score, qfinal, status, s))) return rc;

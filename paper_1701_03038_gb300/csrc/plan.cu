@@ -212,7 +212,7 @@ struct fst_plan_s {
   double* logz = nullptr;
   uint32_t *epoch = nullptr, *clear = nullptr;
   uint32_t *abm = nullptr, *bbm = nullptr;  // [3][max_bw][W] live-state bitmaps
-  uint32_t *asum = nullptr, *bsum = nullptr;  // [3][max_bw][Ws] their summaries
+  uint32_t *tsum = nullptr, *bsum = nullptr;  // forward summaries per token [max_ntok][Ws]; backward [3][max_bw][Ws]
   uint8_t* wlive = nullptr;                 // per (token, forward window) liveness of the largest wave
   int64_t max_nwins = 0;
   int64_t max_bw = 0, max_ntok = 0, max_store = 0, max_lseg = 0, max_lwin = 0;
@@ -227,7 +227,7 @@ struct fst_plan_s {
     for (Wave& w : waves) w.release();
     dfree(ids); dfree(alpha); dfree(beta); dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum);
     dfree(esum); dfree(skey); dfree(scnt); dfree(spart); dfree(qfinal); dfree(cnt64); dfree(logz);
-    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(asum); dfree(bsum); dfree(wlive);
+    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wlive);
   }
 };
 
@@ -407,7 +407,7 @@ WaveState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.W = f->W;
   S.bm_rot = P->max_bw * (int64_t)f->W;
   S.wlive = P->wlive;
-  S.asum = P->asum;
+  S.tsum = P->tsum;
   S.bsum = P->bsum;
   S.sum_start = f->sum_start;
   S.sum_final = f->sum_final;
@@ -467,9 +467,10 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   FST_CUDA(cudaMemsetAsync(P->mkey, 0, (size_t)std::max<int64_t>(1, W.ntok) * 4, s));
   FST_CUDA(cudaMemsetAsync(P->ekey, 0, (size_t)std::max<int64_t>(1, W.ntok) * 4, s));
   FST_CUDA(cudaMemsetAsync(P->wlive, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
+  FST_CUDA(cudaMemsetAsync(P->tsum, 0, (size_t)std::max<int64_t>(1, W.ntok * (int64_t)f->Ws) * 4, s));
   for (int32_t t = 1; t <= W.tmax; ++t) {
     const WorkView V = wave_work(W, t, true);
-    if ((rc = clear_rot(P, P->abm, t % 3, f->W, s)) || (rc = clear_rot(P, P->asum, t % 3, f->Ws, s))) return rc;
+    if ((rc = clear_rot(P, P->abm, t % 3, f->W, s))) return rc;
     PROF(FST_PROF_FWD_STEP, launch_fwd_step(Lf, T, V, S, step_grid(f, V.nitems), s));
   }
   PROF(FST_PROF_FB_FINAL, launch_fb_final(Lf, W.tok_sym, W.cbase, S, W.Bw, P->logz + W.b0,
@@ -611,7 +612,7 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
       break;
     if (want_fb && (rc = alloc_track(P, &P->cnt64, f->bwd.P))) break;
     if ((rc = alloc_track(P, &P->abm, 3 * P->max_bw * (int64_t)f->W))) break;
-    if ((rc = alloc_track(P, &P->asum, 3 * P->max_bw * (int64_t)f->Ws))) break;
+    if ((rc = alloc_track(P, &P->tsum, P->max_ntok * (int64_t)f->Ws))) break;
     if (want_fb && (rc = alloc_track(P, &P->bbm, 3 * P->max_bw * (int64_t)f->W))) break;
     if (want_fb && (rc = alloc_track(P, &P->bsum, 3 * P->max_bw * (int64_t)f->Ws))) break;
     if (want_fb && (rc = alloc_track(P, &P->wlive, P->max_nwins))) break;
@@ -676,9 +677,10 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
   for (const Wave& W : P->waves) {
     const TokenView T = wave_tokens(W);
     const WaveState S = wave_state(P, W, nullptr);
+    FST_CUDA(cudaMemsetAsync(P->tsum, 0, (size_t)std::max<int64_t>(1, W.ntok * (int64_t)f->Ws) * 4, s));
     for (int32_t t = 1; t <= W.tmax; ++t) {
       const WorkView V = wave_work(W, t, true);
-      if ((rc = clear_rot(P, P->abm, t % 3, f->W, s)) || (rc = clear_rot(P, P->asum, t % 3, f->Ws, s))) return rc;
+      if ((rc = clear_rot(P, P->abm, t % 3, f->W, s))) return rc;
       PROF(FST_PROF_VIT_STEP, launch_vit_step(Lf, T, V, S, step_grid(f, V.nitems), s));
     }
     PROF(FST_PROF_VIT_FINAL, launch_vit_final(Lf, W.tok_sym, W.cbase, S, W.Bw, d_scores + W.b0, P->qfinal,
