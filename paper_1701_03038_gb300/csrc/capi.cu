@@ -163,10 +163,10 @@ struct PlainWs {
   unsigned long long* alpha = nullptr;  // [2][Q]
   unsigned long long* beta = nullptr;
   int32_t *tok_sym = nullptr, *tok_b = nullptr, *tok_t = nullptr;
-  int64_t *cbase = nullptr, *zero64 = nullptr, *wbase = nullptr;
+  int64_t *cbase = nullptr, *zero64 = nullptr, *wbase = nullptr, *bwbase = nullptr;
   int32_t* bp = nullptr;
-  uint8_t* wlive = nullptr;
-  int64_t cap_wlive = 0;
+  uint8_t *wlive = nullptr, *fin = nullptr, *bin = nullptr;
+  int64_t cap_wlive = 0, cap_bin = 0;
   float* rc = nullptr;
   uint32_t *mkey = nullptr, *ekey = nullptr;
   double *csum = nullptr, *esum = nullptr;
@@ -185,7 +185,7 @@ struct PlainWs {
   int64_t cap_tsum = 0;
   int64_t max_lseg = 0, max_lwin = 0;
   ~PlainWs() {
-    dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wbase); dfree(wlive);
+    dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wbase); dfree(wlive); dfree(bwbase); dfree(fin); dfree(bin);
     dfree(alpha); dfree(beta); dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(zero64);
     dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(skey); dfree(scnt);
     dfree(spart); dfree(cnt); dfree(comp); dfree(counts_out); dfree(paths); dfree(olabels); dfree(qfinal);
@@ -225,22 +225,32 @@ int plain_init(fst_s* f) {
   return FST_OK;
 }
 
-int plain_reserve(PlainWs* w, int64_t n, int64_t store, int64_t nwins) {
+int plain_reserve(PlainWs* w, int64_t n, int64_t store, int64_t nwins, int64_t nwins_b) {
   int rc;
   if (nwins > w->cap_wlive) {
     const int64_t c = std::max<int64_t>(nwins, 2 * w->cap_wlive);
     dfree(w->wlive);
+    dfree(w->fin);
     w->cap_wlive = 0;
-    if ((rc = dalloc(&w->wlive, c))) return rc;
+    if ((rc = dalloc(&w->wlive, c)) || (rc = dalloc(&w->fin, c))) return rc;
     w->cap_wlive = c;
+  }
+  if (nwins_b > w->cap_bin) {
+    const int64_t c = std::max<int64_t>(nwins_b, 2 * w->cap_bin);
+    dfree(w->bin);
+    w->cap_bin = 0;
+    if ((rc = dalloc(&w->bin, c))) return rc;
+    w->cap_bin = c;
   }
   if (n > w->cap_n) {
     const int64_t c = std::max<int64_t>(n, 2 * w->cap_n);
     dfree(w->tok_sym); dfree(w->tok_b); dfree(w->tok_t); dfree(w->cbase); dfree(w->zero64); dfree(w->wbase);
+    dfree(w->bwbase);
     dfree(w->mkey); dfree(w->ekey); dfree(w->csum); dfree(w->esum); dfree(w->paths); dfree(w->olabels);
     w->cap_n = 0;
     if ((rc = dalloc(&w->tok_sym, c)) || (rc = dalloc(&w->tok_b, c)) || (rc = dalloc(&w->tok_t, c)) ||
         (rc = dalloc(&w->cbase, c)) || (rc = dalloc(&w->zero64, c)) || (rc = dalloc(&w->wbase, c)) ||
+        (rc = dalloc(&w->bwbase, c)) ||
         (rc = dalloc(&w->mkey, c)) ||
         (rc = dalloc(&w->ekey, c)) || (rc = dalloc(&w->csum, c)) || (rc = dalloc(&w->esum, c)) ||
         (rc = dalloc(&w->paths, c)) || (rc = dalloc(&w->olabels, c)))
@@ -263,8 +273,8 @@ int plain_reserve(PlainWs* w, int64_t n, int64_t store, int64_t nwins) {
 int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
   PlainWs* w = f->plain;
   std::vector<int32_t> tt(std::max(n, 1));
-  std::vector<int64_t> cb(std::max(n, 1)), wb(std::max(n, 1));
-  int64_t acc = 0, wacc = 0;
+  std::vector<int64_t> cb(std::max(n, 1)), wb(std::max(n, 1)), bwb(std::max(n, 1));
+  int64_t acc = 0, wacc = 0, bwacc = 0;
   for (int32_t i = 0; i < n; ++i) {
     if (ids[i] < 0 || ids[i] >= f->m) {
       set_error("symbol %d at position %d is outside [0, %d)", ids[i], i, f->m);
@@ -273,10 +283,13 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
     tt[i] = i + 1;
     cb[i] = acc;
     wb[i] = wacc;
+    bwb[i] = bwacc;
     acc += f->fwd.h_sym_seg[ids[i] + 1] - f->fwd.h_sym_seg[ids[i]];
     wacc += f->fwd.h_sym_win[ids[i] + 1] - f->fwd.h_sym_win[ids[i]];
+    bwacc += f->bwd.h_sym_win[ids[i] + 1] - f->bwd.h_sym_win[ids[i]];
   }
-  int rc = plain_reserve(w, std::max(n, 1), std::max<int64_t>(acc, 1), std::max<int64_t>(wacc, 1));
+  int rc = plain_reserve(w, std::max(n, 1), std::max<int64_t>(acc, 1), std::max<int64_t>(wacc, 1),
+                         std::max<int64_t>(bwacc, 1));
   if (rc) return rc;
   const int64_t ntsum = std::max<int64_t>((int64_t)n * f->Ws, 1);
   if (ntsum > w->cap_tsum) {
@@ -291,7 +304,10 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
     FST_CUDA(cudaMemcpyAsync(w->tok_t, tt.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
     FST_CUDA(cudaMemcpyAsync(w->cbase, cb.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
     FST_CUDA(cudaMemcpyAsync(w->wbase, wb.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    FST_CUDA(cudaMemcpyAsync(w->bwbase, bwb.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
     FST_CUDA(cudaMemsetAsync(w->wlive, 0, (size_t)wacc, s));
+    FST_CUDA(cudaMemsetAsync(w->fin, 0, (size_t)wacc, s));
+    FST_CUDA(cudaMemsetAsync(w->bin, 0, (size_t)bwacc, s));
   }
   FST_CUDA(cudaMemcpyAsync(w->bw_n, &n, 4, cudaMemcpyHostToDevice, s));
   // fresh tags for this string
@@ -305,7 +321,8 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
 }
 
 TokenView plain_tokview(PlainWs* w) {
-  return TokenView{w->tok_sym, w->tok_b, w->tok_t, w->cbase, w->zero64, w->zero64, w->zero64, w->zero64, w->wbase};
+  return TokenView{w->tok_sym, w->tok_b, w->tok_t, w->cbase, w->zero64, w->zero64, w->zero64, w->zero64, w->wbase,
+                   w->bwbase};
 }
 
 WaveState plain_state(fst_s* f) {
@@ -341,6 +358,15 @@ WaveState plain_state(fst_s* f) {
   S.wlive = w->wlive;
   S.tsum = w->tsum;
   S.bsum = w->bsum;
+  S.fin = w->fin;
+  S.bin = w->bin;
+  S.b_seg_state = f->bwd.seg_state;
+  S.b_seg_pos = f->bwd.seg_pos;
+  S.b_seg_len = f->bwd.seg_len;
+  S.b_sym_seg = f->bwd.sym_seg;
+  S.b_sym_win = f->bwd.sym_win;
+  S.b_fwin = f->bwd.fwin;
+  S.f_sym_win = f->fwd.sym_win;
   S.sum_start = f->sum_start;
   S.sum_final = f->sum_final;
   S.Ws = f->Ws;
@@ -612,7 +638,7 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
     if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
     if ((rc = launch_fwd_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
   }
-  if ((rc = launch_fb_final(Lf, w->tok_sym, w->cbase, S, 1, w->logz, w->status, s))) return rc;
+  if ((rc = launch_fb_final(Lf, w->tok_sym, w->cbase, w->wbase, S, 1, w->logz, w->status, s))) return rc;
   if (arc_posteriors) {
     CountView C{0, w->cnt, w->comp, nullptr};
     FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)f->bwd.P * 4, s));

@@ -50,6 +50,8 @@ struct Layout {
   WinMeta* win = nullptr;     // [nwin]
   int32_t* seg_state = nullptr;  // [nseg] dst (forward) / src (backward)
   int32_t* seg_pos = nullptr;    // [nseg] padded start position
+  int32_t* seg_len = nullptr;    // [nseg] arcs in the segment
+  int32_t* fwin = nullptr;       // backward layout only: [P] forward window of each arc (-1 on padding)
   int64_t* sym_win = nullptr;    // [m+1]
   int64_t* sym_seg = nullptr;    // [m+1]
   int64_t* sym_lseg = nullptr;   // [m+1] long segments

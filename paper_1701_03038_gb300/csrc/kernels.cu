@@ -195,17 +195,50 @@ __device__ __forceinline__ void set_live(uint32_t* fine, uint32_t* sum, int32_t 
   atomicOr(sum + (q >> 10), 1u << ((q >> 5) & 31));
 }
 
+// State q has a finite forward value for token p, which is not the last of
+// its string: mark, for token p + 1 (input symbol a), the backward window(s)
+// of the segment (a, q) and the forward windows of that segment's arcs.
+// Marks are plain byte stores (several writers store the same 1).
+__device__ __forceinline__ void mark_next(const WaveState& S, const TokenView& T, int32_t p, int32_t q) {
+  const int32_t pn = p + 1;
+  const int32_t a = __ldg(T.sym + pn);
+  int64_t lo = __ldg(S.b_sym_seg + a), hi = __ldg(S.b_sym_seg + a + 1);
+  const int64_t end = hi;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(S.b_seg_state + mid) < q) lo = mid + 1; else hi = mid;
+  }
+  if (lo >= end || __ldg(S.b_seg_state + lo) != q) return;  // q has no arc on symbol a
+  const int32_t pos0 = __ldg(S.b_seg_pos + lo), len = __ldg(S.b_seg_len + lo);
+  if (S.bin) {
+    const int64_t bb = __ldg(T.bwbase + pn) - __ldg(S.b_sym_win + a);
+    for (int32_t w = pos0 / WIN; w <= (pos0 + len - 1) / WIN; ++w) S.bin[bb + w] = 1;
+  }
+  const int64_t fb = __ldg(T.wbase + pn) - __ldg(S.f_sym_win + a);
+  for (int32_t i = 0; i < len; ++i) S.fin[fb + __ldg(S.b_fwin + pos0 + i)] = 1;
+}
+
+// Tokens of the group (bit j = token j) that visit this window: every token
+// at the first position; later, the tokens that marked it, and every token
+// on a long segment's window (its segment counts the arrivals of all of them).
+__device__ __forceinline__ uint32_t tokens_to_visit(const uint8_t* __restrict__ marks, int32_t cnt, int32_t t0,
+                                                    bool is_long, int64_t my_base, int32_t wslice, int lane) {
+  if (t0 == 1 || is_long) return cnt >= 32 ? FULL : ((1u << cnt) - 1u);
+  return __ballot_sync(FULL, lane < cnt && marks[my_base + wslice] != 0);
+}
+
 // ======================================================================
 // Viterbi step (Alg. 1 inner loop; Sec. 5.1)
 // ======================================================================
-__device__ __forceinline__ void vit_write(const LayoutView& L, const WaveState& S, int64_t cb, int32_t s,
-                                          int32_t sl, unsigned long long key, unsigned long long* aout,
-                                          uint32_t tag, uint32_t* bmout, uint32_t* smout) {
+__device__ __forceinline__ void vit_write(const LayoutView& L, const WaveState& S, const TokenView& T, int32_t p,
+                                          bool has_next, int64_t cb, int32_t s, int32_t sl, unsigned long long key,
+                                          unsigned long long* aout, uint32_t tag, uint32_t* bmout, uint32_t* smout) {
   S.bp[cb + sl] = key ? (int32_t)(~(uint32_t)key) : -1;
   if (key) {
     const int32_t q = __ldg(L.seg_state + s);
     aout[q] = tagged_make(fkey_inv((uint32_t)(key >> 32)), tag);
     set_live(bmout, smout, q);
+    if (has_next) mark_next(S, T, p, q);
   }
 }
 
@@ -221,8 +254,8 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
   const int32_t nw = warps_total();
   Group G;
   G.g = -1; G.hi = -1; G.lo = 0;
-  int32_t tp = 0, tb = 0, tt = 0;
-  int64_t tcb = 0;
+  int32_t tp = 0, tb = 0, tt = 0, tn = 0;
+  int64_t tcb = 0, twb = 0;
   int32_t tlb = 0;
   for (int32_t item = warp_id_global(); item < (int32_t)W.nitems; item += nw) {
     if (item >= G.hi) {
@@ -230,27 +263,35 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
       if (lane < G.cnt) {
         tp = group_token(W, G, lane);
         tb = __ldg(T.b + tp); tt = __ldg(T.t + tp); tcb = __ldg(T.cbase + tp); tlb = (int32_t)__ldg(T.lbase + tp);
+        tn = S.bw_n[tb];
+        twb = __ldg(T.wbase + tp);
       }
     }
-    const Win x = load_win(L, G.wbase + (item - G.lo), lane);
+    const int32_t wslice = item - G.lo;
+    const Win x = load_win(L, G.wbase + wslice, lane);
+    const bool is_long = x.lseg >= 0;
+    uint32_t todo = tokens_to_visit(S.fin, G.cnt, __shfl_sync(FULL, tt, 0), is_long, twb, wslice, lane);
+    if (!todo) continue;  // no token has a live source in this window
     const int32_t base = x.w * WIN + lane * APL;
     const int4 s4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
     const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
     const int32_t src[APL] = {s4.x, s4.y, s4.z, s4.w};
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
-    const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
     uint32_t wn[APL];
-    summary_words(fwd_live(S, __shfl_sync(FULL, tp, 0), __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)).sum, src,
-                  wn);
-    for (int j = 0; j < G.cnt; ++j) {
+    int jn = __ffs(todo) - 1;
+    summary_words(fwd_live(S, __shfl_sync(FULL, tp, jn), __shfl_sync(FULL, tb, jn), __shfl_sync(FULL, tt, jn)).sum,
+                  src, wn);
+    for (int j = jn; j >= 0; j = jn) {
+      todo &= todo - 1u;
+      jn = todo ? __ffs(todo) - 1 : -1;
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
+      const bool has_next = t < __shfl_sync(FULL, tn, j);
       // every arc is relaxed; a source whose bit is clear contributes -inf
       // without reading its 8-byte frontier entry
       const uint32_t lv = live_of(fwd_live(S, p, b, t).fine, wn, src);
-      if (j + 1 < G.cnt)
-        summary_words(fwd_live(S, __shfl_sync(FULL, tp, j + 1), __shfl_sync(FULL, tb, j + 1),
-                               __shfl_sync(FULL, tt, j + 1)).sum,
+      if (jn >= 0)
+        summary_words(fwd_live(S, __shfl_sync(FULL, tp, jn), __shfl_sync(FULL, tb, jn), __shfl_sync(FULL, tt, jn)).sum,
                       src, wn);
       if (!is_long && !__any_sync(FULL, lv != 0u)) continue;  // no live source: every segment stays -inf
       float a[APL];
@@ -286,7 +327,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
           const bool tail = (k < APL - 1) ? ((x.h >> (k + 1)) & 1u) : (lane == 31 || (hn & 1u));
           if (tail) {
             const int32_t s = x.seg + cum - 1;
-            vit_write(L, S, cb, s, s - G.segbase, full[k], aout, tag, bmout, smout);
+            vit_write(L, S, T, p, has_next, cb, s, s - G.segbase, full[k], aout, tag, bmout, smout);
           }
         }
       } else {
@@ -300,7 +341,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_vit_step(LayoutView L, To
           if (prev == (uint32_t)x.lcnt - 1u) {
             __threadfence();
             const unsigned long long kf = atomicMax(S.skey + slot, 0ull);
-            vit_write(L, S, cb, x.seg, x.seg - G.segbase, kf, aout, tag, bmout, smout);
+            vit_write(L, S, T, p, has_next, cb, x.seg, x.seg - G.segbase, kf, aout, tag, bmout, smout);
             S.skey[slot] = 0ull;
             S.scnt[slot] = 0u;
           }
@@ -355,7 +396,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
   const int32_t nw = warps_total();
   Group G;
   G.g = -1; G.hi = -1; G.lo = 0;
-  int32_t tp = 0, tb = 0, tt = 0, tlb = 0, tlw = 0;
+  int32_t tp = 0, tb = 0, tt = 0, tn = 0, tlb = 0, tlw = 0;
   int64_t tcb = 0, twb = 0;
   float tm = 0.f;
   for (int32_t item = warp_id_global(); item < (int32_t)W.nitems; item += nw) {
@@ -366,27 +407,35 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
         tb = __ldg(T.b + tp); tt = __ldg(T.t + tp); tcb = __ldg(T.cbase + tp);
         tlb = (int32_t)__ldg(T.lbase + tp); tlw = (int32_t)__ldg(T.lwbase + tp); twb = __ldg(T.wbase + tp);
         tm = tt > 1 ? decode_max(S.mkey[tp - 1]) : 0.f;
+        tn = S.bw_n[tb];
       }
     }
     const int32_t wslice = item - G.lo;
     const Win x = load_win(L, G.wbase + wslice, lane);
+    const bool is_long = x.lseg >= 0;
+    // unvisited (token, window) pairs write nothing: readers of the stored
+    // forward values consult the window-liveness bytes
+    uint32_t todo = tokens_to_visit(S.fin, G.cnt, __shfl_sync(FULL, tt, 0), is_long, twb, wslice, lane);
+    if (!todo) continue;
     const int32_t base = x.w * WIN + lane * APL;
     const int4 s4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
     const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
     const int32_t src[APL] = {s4.x, s4.y, s4.z, s4.w};
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
-    const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
     uint32_t wn[APL];
-    summary_words(fwd_live(S, __shfl_sync(FULL, tp, 0), __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0)).sum, src,
-                  wn);
-    for (int j = 0; j < G.cnt; ++j) {
+    int jn = __ffs(todo) - 1;
+    summary_words(fwd_live(S, __shfl_sync(FULL, tp, jn), __shfl_sync(FULL, tb, jn), __shfl_sync(FULL, tt, jn)).sum,
+                  src, wn);
+    for (int j = jn; j >= 0; j = jn) {
+      todo &= todo - 1u;
+      jn = todo ? __ffs(todo) - 1 : -1;
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const float mprev = __shfl_sync(FULL, tm, j);
+      const bool has_next = t < __shfl_sync(FULL, tn, j);
       const uint32_t lv = live_of(fwd_live(S, p, b, t).fine, wn, src);
-      if (j + 1 < G.cnt)
-        summary_words(fwd_live(S, __shfl_sync(FULL, tp, j + 1), __shfl_sync(FULL, tb, j + 1),
-                               __shfl_sync(FULL, tt, j + 1)).sum,
+      if (jn >= 0)
+        summary_words(fwd_live(S, __shfl_sync(FULL, tp, jn), __shfl_sync(FULL, tb, jn), __shfl_sync(FULL, tt, jn)).sum,
                       src, wn);
       const int64_t cb = shfl64(tcb, j);
       if (!is_long && !__any_sync(FULL, lv != 0u)) {
@@ -440,6 +489,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
               const int32_t q = __ldg(L.seg_state + s);
               aout[q] = tagged_make(r, tag);
               set_live(bmout, smout, q);
+              if (has_next) mark_next(S, T, p, q);
             }
             rmax = fmaxf(rmax, r);
           }
@@ -459,6 +509,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
               const int32_t q = __ldg(L.seg_state + x.seg);
               aout[q] = tagged_make(r, tag);
               set_live(bmout, smout, q);
+              if (has_next) mark_next(S, T, p, q);
               // the segment's first window carries its head
               S.wlive[wbt + (__ldg(L.seg_pos + x.seg) / WIN - G.wbase)] = 1;
             }
@@ -542,6 +593,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
   G.g = -1; G.hi = -1; G.lo = 0;
   // lane j: token j of the group
   int32_t tp = 0, tb = 0, tt = 0, tn = 0, tlb = 0, tlw = 0;
+  int64_t tbb = 0;
   float tm = 0.f, te = 0.f, tw = 0.f;
   double tK = 0.0;
   bool tlive = false;
@@ -552,6 +604,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
         tp = group_token(W, G, lane);
         tb = __ldg(T.b + tp); tt = __ldg(T.t + tp);
         tlb = (int32_t)__ldg(T.lbase_b + tp); tlw = (int32_t)__ldg(T.lwbase_b + tp);
+        tbb = __ldg(T.bwbase + tp);
         tn = S.bw_n[tb];
         const double lz = S.logz[tb];
         tlive = lz != -INFINITY;
@@ -567,13 +620,17 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
         tlive = false;
       }
     }
-    const Win x = load_win(L, G.wbase + (item - G.lo), lane);
+    const int32_t wslice = item - G.lo;
+    const Win x = load_win(L, G.wbase + wslice, lane);
+    const bool is_long = x.lseg >= 0;
+    uint32_t todo = tokens_to_visit(S.bin, G.cnt, __shfl_sync(FULL, tt, 0), is_long, tbb, wslice, lane) &
+                    __ballot_sync(FULL, tlive);
+    if (!todo) continue;  // no live token has a source with a finite forward value here
     const int32_t base = x.w * WIN + lane * APL;
     const int4 d4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
     const float4 t4 = __ldg(reinterpret_cast<const float4*>(L.theta + base));
     const int32_t dst[APL] = {d4.x, d4.y, d4.z, d4.w};
     const float th[APL] = {t4.x, t4.y, t4.z, t4.w};
-    const bool is_long = x.lseg >= 0;
     const uint32_t hn = __shfl_down_sync(FULL, x.h, 1);
     // segment (source state) of each arc; padding arcs belong to the window's last segment
     int32_t qs[APL];
@@ -587,19 +644,19 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
     }
     float gacc[APL] = {0.f, 0.f, 0.f, 0.f};
     uint32_t wn[APL];
-    summary_words(bwd_live(S, __shfl_sync(FULL, tb, 0), __shfl_sync(FULL, tt, 0), __shfl_sync(FULL, tn, 0)).sum, dst,
-                  wn);
-    for (int j = 0; j < G.cnt; ++j) {
-      const bool live_tok = __shfl_sync(FULL, tlive, j);
+    int jn = __ffs(todo) - 1;
+    summary_words(bwd_live(S, __shfl_sync(FULL, tb, jn), __shfl_sync(FULL, tt, jn), __shfl_sync(FULL, tn, jn)).sum,
+                  dst, wn);
+    for (int j = jn; j >= 0; j = jn) {
+      todo &= todo - 1u;
+      jn = todo ? __ffs(todo) - 1 : -1;
       const int32_t p = __shfl_sync(FULL, tp, j), b = __shfl_sync(FULL, tb, j), t = __shfl_sync(FULL, tt, j);
       const int32_t n = __shfl_sync(FULL, tn, j);
       // beta_t at the destinations; a destination whose bit is clear is -inf
       uint32_t lv = live_of(bwd_live(S, b, t, n).fine, wn, dst);
-      if (j + 1 < G.cnt)
-        summary_words(bwd_live(S, __shfl_sync(FULL, tb, j + 1), __shfl_sync(FULL, tt, j + 1),
-                               __shfl_sync(FULL, tn, j + 1)).sum,
+      if (jn >= 0)
+        summary_words(bwd_live(S, __shfl_sync(FULL, tb, jn), __shfl_sync(FULL, tt, jn), __shfl_sync(FULL, tn, jn)).sum,
                       dst, wn);
-      if (!live_tok) continue;
       // Only sources whose forward value alpha_{t-1} is finite matter: every
       // posterior through a dead source is zero, and a finite-alpha state
       // reaches only finite-alpha states, so its backward value is exact
@@ -816,8 +873,18 @@ __global__ void k_backtrace(LayoutView L, const int32_t* __restrict__ tok_sym, c
   }
 }
 
+// The stored forward values of the last position are valid only in windows
+// that the forward pass visited and marked live (others are -inf).
+__device__ __forceinline__ double final_value(const LayoutView& L, const WaveState& S, int64_t cb, int64_t wb,
+                                              int32_t sym, int64_t s) {
+  const int64_t wi = __ldg(L.seg_pos + s) / WIN - __ldg(L.sym_win + sym);
+  if (!S.wlive[wb + wi]) return -INFINITY;
+  return (double)S.rc[cb + (s - L.sym_seg[sym])] + (double)S.theta_f[L.seg_state[s]];
+}
+
 __global__ void k_fb_final(LayoutView L, const int32_t* __restrict__ tok_sym, const int64_t* __restrict__ cbase,
-                           WaveState S, int32_t Bw, double* __restrict__ logz, int32_t* __restrict__ status) {
+                           const int64_t* __restrict__ wbase, WaveState S, int32_t Bw, double* __restrict__ logz,
+                           int32_t* __restrict__ status) {
   const int lane = threadIdx.x & 31;
   const int64_t b = warp_id_global();
   if (b >= Bw) return;
@@ -842,10 +909,8 @@ __global__ void k_fb_final(LayoutView L, const int32_t* __restrict__ tok_sym, co
   } else {
     const int64_t p = off + n - 1;
     const int32_t sym = tok_sym[p];
-    for (int64_t s = L.sym_seg[sym] + lane; s < L.sym_seg[sym + 1]; s += 32) {
-      const int32_t q = L.seg_state[s];
-      mx = fmax(mx, (double)S.rc[cbase[p] + (s - L.sym_seg[sym])] + (double)S.theta_f[q]);
-    }
+    for (int64_t s = L.sym_seg[sym] + lane; s < L.sym_seg[sym + 1]; s += 32)
+      mx = fmax(mx, final_value(L, S, cbase[p], wbase[p], sym, s));
   }
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, d));
@@ -860,8 +925,7 @@ __global__ void k_fb_final(LayoutView L, const int32_t* __restrict__ tok_sym, co
       const int64_t p = off + n - 1;
       const int32_t sym = tok_sym[p];
       for (int64_t s = L.sym_seg[sym] + lane; s < L.sym_seg[sym + 1]; s += 32) {
-        const int32_t q = L.seg_state[s];
-        const double v = (double)S.rc[cbase[p] + (s - L.sym_seg[sym])] + (double)S.theta_f[q];
+        const double v = final_value(L, S, cbase[p], wbase[p], sym, s);
         if (v != -INFINITY) sum += exp(v - mx);
       }
     }
@@ -961,10 +1025,10 @@ int launch_backtrace(const LayoutView& Lf, const int32_t* tok_sym, const int64_t
   return check_launch("k_backtrace");
 }
 
-int launch_fb_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
-                    int32_t Bw, double* logz, int32_t* status, cudaStream_t s) {
+int launch_fb_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const int64_t* wbase,
+                    const WaveState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s) {
   if (Bw <= 0) return FST_OK;
-  k_fb_final<<<(unsigned)((Bw + 7) / 8), 256, 0, s>>>(Lf, tok_sym, cbase, S, Bw, logz, status);
+  k_fb_final<<<(unsigned)((Bw + 7) / 8), 256, 0, s>>>(Lf, tok_sym, cbase, wbase, S, Bw, logz, status);
   return check_launch("k_fb_final");
 }
 

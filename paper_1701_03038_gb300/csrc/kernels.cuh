@@ -34,6 +34,7 @@ struct TokenView {
   const int64_t* lwbase;    // long-window scratch slots (forward layout)
   const int64_t* lwbase_b;  // long-window scratch slots (backward layout)
   const int64_t* wbase;     // first window-liveness byte of the token (forward windows)
+  const int64_t* bwbase;    // first mark byte of the token in the backward windows
 };
 
 // Work list of one step: items are (group, window-of-slice) pairs; a group
@@ -97,6 +98,20 @@ struct WaveState {
   // one byte per (token, forward window): 1 when the window wrote a finite
   // forward value for that token (cleared before each forward pass)
   uint8_t* wlive;
+  // Window marks, one byte per (token, forward window) in fin and per
+  // (token, backward window) in bin: set when the window holds an arc out of
+  // a state whose forward value at the previous position is finite.  A pass
+  // visits only marked windows of tokens past the first position; every
+  // unmarked window holds arcs from dead sources only.  bin may be null.
+  uint8_t* fin;
+  uint8_t* bin;
+  const int32_t* b_seg_state;
+  const int32_t* b_seg_pos;
+  const int32_t* b_seg_len;
+  const int64_t* b_sym_seg;
+  const int64_t* b_sym_win;
+  const int32_t* b_fwin;
+  const int64_t* f_sym_win;
 };
 
 struct CountView {
@@ -120,8 +135,8 @@ int launch_vit_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t
 int launch_backtrace(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
                      const int32_t* olabel_by_id, const int32_t* arc_id_fwd, int32_t Bw,
                      const int32_t* qfinal, int32_t* paths, int32_t* olabels, cudaStream_t s);
-int launch_fb_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
-                    int32_t Bw, double* logz, int32_t* status, cudaStream_t s);
+int launch_fb_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const int64_t* wbase,
+                    const WaveState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s);
 int launch_counts_out(const int32_t* arc_id_bwd, int64_t P, const CountView& C, float* out, cudaStream_t s);
 
 }  // namespace fstgpu

@@ -75,13 +75,17 @@ struct Carver {
 // sum of destination segments per symbol).  One thread; n is at most a few
 // thousand here.
 __global__ void k_noalloc_tokens(const int32_t* __restrict__ ids, int32_t n, const int64_t* __restrict__ sym_seg,
-                                 int32_t* __restrict__ tok_t, int64_t* __restrict__ cbase, uint32_t* __restrict__ epoch) {
+                                 const int64_t* __restrict__ sym_win, int32_t* __restrict__ tok_t,
+                                 int64_t* __restrict__ cbase, int64_t* __restrict__ wbase,
+                                 uint32_t* __restrict__ epoch) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  int64_t acc = 0;
+  int64_t acc = 0, wacc = 0;
   for (int32_t i = 0; i < n; ++i) {
     tok_t[i] = i + 1;
     cbase[i] = acc;
+    wbase[i] = wacc;
     acc += sym_seg[ids[i] + 1] - sym_seg[ids[i]];
+    wacc += sym_win[ids[i] + 1] - sym_win[ids[i]];
   }
   epoch[0] = 1u;  // tags of this call are 1 + position; the cleared frontier holds tag 0
   epoch[1] = 0u;
@@ -97,19 +101,20 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   }
   cudaStream_t s = (cudaStream_t)stream;
   // sizes first, from host data only
-  int64_t store = 0, max_lseg = 0;
+  int64_t store = 0, max_lseg = 0, nwins = 0;
   for (int32_t i = 0; i < n; ++i) {
     if (ids[i] < 0 || ids[i] >= f->m) {
       set_error("fst_viterbi_noalloc: symbol %d at position %d is outside [0, %d)", ids[i], i, f->m);
       return FST_ERR_INVALID_ARG;
     }
     store += f->fwd.h_sym_seg[ids[i] + 1] - f->fwd.h_sym_seg[ids[i]];
+    nwins += f->fwd.h_sym_win[ids[i] + 1] - f->fwd.h_sym_win[ids[i]];
   }
   for (int32_t a = 0; a < f->m; ++a)
     max_lseg = std::max<int64_t>(max_lseg, f->fwd.h_sym_lseg[a + 1] - f->fwd.h_sym_lseg[a]);
   const int64_t Q = f->Q, W = f->W;
   auto rnd = [](int64_t bytes) { return ((bytes > 0 ? bytes : 1) + 255) & ~(int64_t)255; };
-  const int64_t need = rnd(2 * Q * 8) + rnd(3 * W * 4) + rnd((int64_t)n * f->Ws * 4) + 3 * rnd((int64_t)n * 4) + 2 * rnd((int64_t)n * 8) +
+  const int64_t need = rnd(2 * Q * 8) + rnd(3 * W * 4) + rnd((int64_t)n * f->Ws * 4) + rnd(nwins) + rnd((int64_t)n * 8) + 3 * rnd((int64_t)n * 4) + 2 * rnd((int64_t)n * 8) +
                        rnd(store * 4) + rnd(max_lseg * 8) + rnd(max_lseg * 4) + 5 * rnd(8) + rnd(4) + rnd(8);
   if (need > (int64_t)NOALLOC_SCRATCH_BYTES) {
     set_error("fst_viterbi_noalloc: this string needs %lld bytes of working memory, beyond the fixed %llu bytes "
@@ -129,6 +134,8 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   int32_t* tok_t = c.take<int32_t>(n);
   int64_t* cbase = c.take<int64_t>(n);
   int64_t* zero64 = c.take<int64_t>(n);
+  int64_t* wbase = c.take<int64_t>(n);
+  uint8_t* fin = c.take<uint8_t>(nwins);
   int32_t* bp = c.take<int32_t>(store);
   unsigned long long* skey = c.take<unsigned long long>(max_lseg);
   uint32_t* scnt = c.take<uint32_t>(max_lseg);
@@ -149,7 +156,8 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   FST_CUDA(cudaMemsetAsync(tsum, 0, (size_t)std::max<int64_t>((int64_t)n * f->Ws, 1) * 4, s));
   if (n > 0) FST_CUDA(cudaMemcpyAsync(tok_sym, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   FST_CUDA(cudaMemcpyAsync(bw_n, &n, 4, cudaMemcpyHostToDevice, s));
-  k_noalloc_tokens<<<1, 1, 0, s>>>(tok_sym, n, f->fwd.sym_seg, tok_t, cbase, epoch);
+  FST_CUDA(cudaMemsetAsync(fin, 0, (size_t)std::max<int64_t>(nwins, 1), s));
+  k_noalloc_tokens<<<1, 1, 0, s>>>(tok_sym, n, f->fwd.sym_seg, f->fwd.sym_win, tok_t, cbase, wbase, epoch);
   FST_CUDA(cudaGetLastError());
 
   WaveState S;
@@ -171,10 +179,19 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.W = f->W;
   S.bm_rot = f->W;
   S.tsum = tsum;
+  S.fin = fin;
+  S.bin = nullptr;
+  S.b_seg_state = f->bwd.seg_state;
+  S.b_seg_pos = f->bwd.seg_pos;
+  S.b_seg_len = f->bwd.seg_len;
+  S.b_sym_seg = f->bwd.sym_seg;
+  S.b_sym_win = f->bwd.sym_win;
+  S.b_fwin = f->bwd.fwin;
+  S.f_sym_win = f->fwd.sym_win;
   S.sum_start = f->sum_start;
   S.Ws = f->Ws;
   S.sum_rot = f->Ws;
-  const TokenView T{tok_sym, tok_b, tok_t, cbase, zero64, zero64, zero64, zero64, zero64};
+  const TokenView T{tok_sym, tok_b, tok_t, cbase, zero64, zero64, zero64, zero64, wbase, zero64};
   const LayoutView Lf = view_of(f->fwd);
   for (int32_t t = 1; t <= n; ++t) {
     const int32_t a = ids[t - 1];

@@ -62,7 +62,8 @@ __global__ void k_tok_counts(const int32_t* __restrict__ sym, int64_t n, const i
                              const int64_t* __restrict__ b_lseg, const int64_t* __restrict__ b_lwin,
                              const int64_t* __restrict__ f_win, int64_t* __restrict__ c0,
                              int64_t* __restrict__ c1, int64_t* __restrict__ c2, int64_t* __restrict__ c3,
-                             int64_t* __restrict__ c4, int64_t* __restrict__ c5) {
+                             int64_t* __restrict__ c4, int64_t* __restrict__ c5,
+                             const int64_t* __restrict__ b_win, int64_t* __restrict__ c6) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t a = sym[i];
@@ -72,6 +73,7 @@ __global__ void k_tok_counts(const int32_t* __restrict__ sym, int64_t n, const i
   c3[i] = b_lseg[a + 1] - b_lseg[a];
   c4[i] = b_lwin[a + 1] - b_lwin[a];
   c5[i] = f_win[a + 1] - f_win[a];
+  c6[i] = b_win[a + 1] - b_win[a];
 }
 
 __global__ void k_tok_keys(const int32_t* __restrict__ sym, const int32_t* __restrict__ t, int64_t n, int sbits,
@@ -171,11 +173,12 @@ __global__ void k_clear_if(const uint32_t* clear, unsigned long long* p, int64_t
 
 struct Wave {
   int32_t b0 = 0, b1 = 0, Bw = 0, tmax = 0;
-  int64_t tok0 = 0, ntok = 0, store = 0, G = 0, nwins = 0;
+  int64_t tok0 = 0, ntok = 0, store = 0, G = 0, nwins = 0, nwins_b = 0;
   int64_t nlseg = 0, nlwin = 0;  // scratch slots needed (max of both layouts)
   int32_t *tok_sym = nullptr, *tok_b = nullptr, *tok_t = nullptr;
   int64_t *cbase = nullptr, *lbase_f = nullptr, *lwbase_f = nullptr, *lbase_b = nullptr, *lwbase_b = nullptr;
   int64_t* wbase = nullptr;
+  int64_t* bwbase = nullptr;
   int32_t *sorted_tok = nullptr, *grp_first = nullptr, *grp_cnt = nullptr, *grp_sym = nullptr;
   int64_t *grp_item_f = nullptr, *grp_item_b = nullptr;
   int32_t* bw_n = nullptr;
@@ -184,7 +187,7 @@ struct Wave {
   std::vector<int64_t> items_f, items_b;  // [tmax + 1]
   void release() {
     dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(lbase_f); dfree(lwbase_f); dfree(lbase_b);
-    dfree(wbase);
+    dfree(wbase); dfree(bwbase);
     dfree(lwbase_b); dfree(sorted_tok); dfree(grp_first); dfree(grp_cnt); dfree(grp_sym); dfree(grp_item_f);
     dfree(grp_item_b); dfree(bw_n); dfree(bw_off);
   }
@@ -214,7 +217,8 @@ struct fst_plan_s {
   uint32_t *abm = nullptr, *bbm = nullptr;  // [3][max_bw][W] live-state bitmaps
   uint32_t *tsum = nullptr, *bsum = nullptr;  // forward summaries per token [max_ntok][Ws]; backward [3][max_bw][Ws]
   uint8_t* wlive = nullptr;                 // per (token, forward window) liveness of the largest wave
-  int64_t max_nwins = 0;
+  uint8_t *fin = nullptr, *bin = nullptr;   // window marks (forward / backward windows)
+  int64_t max_nwins = 0, max_nwins_b = 0;
   int64_t max_bw = 0, max_ntok = 0, max_store = 0, max_lseg = 0, max_lwin = 0;
   bool forward_done = false;
   // optional per-launch CUDA events (fst_plan_profile)
@@ -227,7 +231,7 @@ struct fst_plan_s {
     for (Wave& w : waves) w.release();
     dfree(ids); dfree(alpha); dfree(beta); dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum);
     dfree(esum); dfree(skey); dfree(scnt); dfree(spart); dfree(qfinal); dfree(cnt64); dfree(logz);
-    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wlive);
+    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wlive); dfree(fin); dfree(bin);
   }
 };
 
@@ -286,7 +290,7 @@ int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, cudaSt
       (rc = alloc_track(P, &W.tok_t, n)) || (rc = alloc_track(P, &W.cbase, n + 1)) ||
       (rc = alloc_track(P, &W.lbase_f, n + 1)) || (rc = alloc_track(P, &W.lwbase_f, n + 1)) ||
       (rc = alloc_track(P, &W.lbase_b, n + 1)) || (rc = alloc_track(P, &W.lwbase_b, n + 1)) ||
-      (rc = alloc_track(P, &W.wbase, n + 1)) ||
+      (rc = alloc_track(P, &W.wbase, n + 1)) || (rc = alloc_track(P, &W.bwbase, n + 1)) ||
       (rc = alloc_track(P, &W.sorted_tok, n)))
     return rc;
   FST_CUDA(cudaMemcpy(W.bw_off, boff.data(), (size_t)W.Bw * 8, cudaMemcpyHostToDevice));
@@ -295,20 +299,21 @@ int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, cudaSt
     k_tok_info<<<nblk((int64_t)W.Bw * 32), TB, 0, s>>>(P->ids + W.tok0, W.bw_off, W.bw_n, W.Bw, W.tok_sym, W.tok_b,
                                                        W.tok_t);
   // per-token storage and scratch bases
-  int64_t *c[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t *c[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   for (auto& p : c)
     if ((rc = dalloc(&p, n))) { for (auto& q : c) dfree(q); return rc; }
   if (W.ntok > 0)
     k_tok_counts<<<nblk(W.ntok), TB, 0, s>>>(W.tok_sym, W.ntok, f->fwd.sym_seg, f->fwd.sym_lseg, f->fwd.sym_lwin,
                                              f->bwd.sym_lseg, f->bwd.sym_lwin, f->fwd.sym_win, c[0], c[1], c[2], c[3],
-                                             c[4], c[5]);
-  int64_t tot[6] = {0, 0, 0, 0, 0, 0};
-  int64_t* outs[6] = {W.cbase, W.lbase_f, W.lwbase_f, W.lbase_b, W.lwbase_b, W.wbase};
-  for (int i = 0; i < 6 && !rc; ++i) rc = exclusive_scan_i64(c[i], outs[i], W.ntok, &tot[i], s);
+                                             c[4], c[5], f->bwd.sym_win, c[6]);
+  int64_t tot[7] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t* outs[7] = {W.cbase, W.lbase_f, W.lwbase_f, W.lbase_b, W.lwbase_b, W.wbase, W.bwbase};
+  for (int i = 0; i < 7 && !rc; ++i) rc = exclusive_scan_i64(c[i], outs[i], W.ntok, &tot[i], s);
   for (auto& q : c) dfree(q);
   if (rc) return rc;
   W.store = tot[0];
   W.nwins = tot[5];
+  W.nwins_b = tot[6];
   W.nlseg = std::max(tot[1], tot[3]);
   W.nlwin = std::max(tot[2], tot[4]);
   // sort tokens by (position, symbol) and cut groups
@@ -409,6 +414,15 @@ WaveState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.wlive = P->wlive;
   S.tsum = P->tsum;
   S.bsum = P->bsum;
+  S.fin = P->fin;
+  S.bin = P->bin;
+  S.b_seg_state = f->bwd.seg_state;
+  S.b_seg_pos = f->bwd.seg_pos;
+  S.b_seg_len = f->bwd.seg_len;
+  S.b_sym_seg = f->bwd.sym_seg;
+  S.b_sym_win = f->bwd.sym_win;
+  S.b_fwin = f->bwd.fwin;
+  S.f_sym_win = f->fwd.sym_win;
   S.sum_start = f->sum_start;
   S.sum_final = f->sum_final;
   S.Ws = f->Ws;
@@ -425,7 +439,8 @@ int clear_rot(fst_plan_s* P, uint32_t* bm, int32_t r, int32_t words_per_string, 
 }
 
 TokenView wave_tokens(const Wave& W) {
-  return TokenView{W.tok_sym, W.tok_b, W.tok_t, W.cbase, W.lbase_f, W.lbase_b, W.lwbase_f, W.lwbase_b, W.wbase};
+  return TokenView{W.tok_sym, W.tok_b, W.tok_t, W.cbase, W.lbase_f, W.lbase_b, W.lwbase_f, W.lwbase_b, W.wbase,
+                   W.bwbase};
 }
 
 WorkView wave_work(const Wave& W, int32_t t, bool fwd) {
@@ -468,12 +483,14 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   FST_CUDA(cudaMemsetAsync(P->ekey, 0, (size_t)std::max<int64_t>(1, W.ntok) * 4, s));
   FST_CUDA(cudaMemsetAsync(P->wlive, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
   FST_CUDA(cudaMemsetAsync(P->tsum, 0, (size_t)std::max<int64_t>(1, W.ntok * (int64_t)f->Ws) * 4, s));
+  FST_CUDA(cudaMemsetAsync(P->fin, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
+  FST_CUDA(cudaMemsetAsync(P->bin, 0, (size_t)std::max<int64_t>(1, W.nwins_b), s));
   for (int32_t t = 1; t <= W.tmax; ++t) {
     const WorkView V = wave_work(W, t, true);
     if ((rc = clear_rot(P, P->abm, t % 3, f->W, s))) return rc;
     PROF(FST_PROF_FWD_STEP, launch_fwd_step(Lf, T, V, S, step_grid(f, V.nitems), s));
   }
-  PROF(FST_PROF_FB_FINAL, launch_fb_final(Lf, W.tok_sym, W.cbase, S, W.Bw, P->logz + W.b0,
+  PROF(FST_PROF_FB_FINAL, launch_fb_final(Lf, W.tok_sym, W.cbase, W.wbase, S, W.Bw, P->logz + W.b0,
                                            d_status ? d_status + W.b0 : nullptr, s));
   return FST_OK;
 }
@@ -596,6 +613,7 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
       P->max_lwin = std::max<int64_t>(P->max_lwin, w.nlwin);
       P->max_len = std::max(P->max_len, w.tmax);
       P->max_nwins = std::max(P->max_nwins, w.nwins);
+      P->max_nwins_b = std::max(P->max_nwins_b, w.nwins_b);
     }
     if (rc) break;
     const int64_t na = P->max_bw * 2 * (int64_t)f->Q;
@@ -616,6 +634,8 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
     if (want_fb && (rc = alloc_track(P, &P->bbm, 3 * P->max_bw * (int64_t)f->W))) break;
     if (want_fb && (rc = alloc_track(P, &P->bsum, 3 * P->max_bw * (int64_t)f->Ws))) break;
     if (want_fb && (rc = alloc_track(P, &P->wlive, P->max_nwins))) break;
+    if ((rc = alloc_track(P, &P->fin, P->max_nwins))) break;
+    if (want_fb && (rc = alloc_track(P, &P->bin, P->max_nwins_b))) break;
     FST_CUDA(cudaMemsetAsync(P->alpha, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     FST_CUDA(cudaMemsetAsync(P->epoch, 0, 8, s));
@@ -678,6 +698,7 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
     const TokenView T = wave_tokens(W);
     const WaveState S = wave_state(P, W, nullptr);
     FST_CUDA(cudaMemsetAsync(P->tsum, 0, (size_t)std::max<int64_t>(1, W.ntok * (int64_t)f->Ws) * 4, s));
+    FST_CUDA(cudaMemsetAsync(P->fin, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
     for (int32_t t = 1; t <= W.tmax; ++t) {
       const WorkView V = wave_work(W, t, true);
       if ((rc = clear_rot(P, P->abm, t % 3, f->W, s))) return rc;

@@ -123,6 +123,26 @@ __global__ void k_seg_pos(const int32_t* __restrict__ seg_sym, const int64_t* __
   seg_pos[s] = (int32_t)(sym_win[seg_sym[s]] * WIN + seg_ppos[s]);
 }
 
+__global__ void k_seg_len(const int64_t* __restrict__ seg_first, int64_t nseg, int32_t* __restrict__ len) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nseg) len[s] = (int32_t)(seg_first[s + 1] - seg_first[s]);
+}
+
+// pos_by_id[id] = forward position of arc id
+__global__ void k_pos_by_id(const int32_t* __restrict__ arc_id, int64_t P, int32_t* __restrict__ pos_by_id) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P && arc_id[i] >= 0) pos_by_id[arc_id[i]] = (int32_t)i;
+}
+
+// fwin[i] = forward window of the arc at backward position i
+__global__ void k_fwin(const int32_t* __restrict__ arc_id_b, int64_t P, const int32_t* __restrict__ pos_by_id,
+                       int32_t* __restrict__ fwin) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const int32_t k = arc_id_b[i];
+  fwin[i] = k >= 0 ? pos_by_id[k] / WIN : -1;
+}
+
 __global__ void k_scatter_arcs(const uint32_t* __restrict__ perm, const int64_t* __restrict__ hd,
                                const int64_t* __restrict__ segx, const int64_t* __restrict__ seg_first,
                                const int32_t* __restrict__ seg_pos, const int32_t* __restrict__ oth_by_id,
@@ -292,8 +312,9 @@ int build_layout(fst_s* f, Layout& L, const int32_t* d_il, const int32_t* seg_st
     return FST_ERR_UNSUPPORTED;
   }
   if ((rc = dalloc(&L.other, L.P)) || (rc = dalloc(&L.theta, L.P)) || (rc = dalloc(&L.arc_id, L.P)) ||
-      (rc = dalloc(&L.seg_pos, nseg + 1)) || (rc = dalloc(&L.win, nwin)))
+      (rc = dalloc(&L.seg_pos, nseg + 1)) || (rc = dalloc(&L.win, nwin)) || (rc = dalloc(&L.seg_len, nseg + 1)))
     return rc;
+  if (nseg > 0) k_seg_len<<<blocks_for(nseg), TB, 0, s>>>(t.seg_first, nseg, L.seg_len);
   if (L.P > 0) k_fill_padding<<<blocks_for(L.P), TB, 0, s>>>(L.other, L.theta, L.arc_id, L.P);
   if (nseg > 0) k_seg_pos<<<blocks_for(nseg), TB, 0, s>>>(t.seg_sym, t.seg_ppos, L.sym_win, nseg, L.seg_pos);
   if (A > 0)
@@ -316,7 +337,7 @@ int build_layout(fst_s* f, Layout& L, const int32_t* d_il, const int32_t* seg_st
 
 void free_layout(Layout& L) {
   dfree(L.other); dfree(L.theta); dfree(L.arc_id); dfree(L.theta64); dfree(L.win);
-  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
+  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.seg_len); dfree(L.fwin); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
   dfree(L.sym_lwin);
   free(L.h_sym_win); free(L.h_sym_seg); free(L.h_sym_lseg); free(L.h_sym_lwin);
   L.h_sym_win = L.h_sym_seg = L.h_sym_lseg = L.h_sym_lwin = nullptr;
@@ -331,6 +352,15 @@ int build_store(fst_s* f, const int32_t* d_src, const int32_t* d_dst, const int3
   if ((rc = build_layout(f, f->fwd, d_il, d_dst, d_src, d_theta, &f->h_sym_arc, f->sym_arc, s))) return rc;
   // backward: segments by source, arcs carry their destination
   if ((rc = build_layout(f, f->bwd, d_il, d_src, d_dst, d_theta, nullptr, nullptr, s))) return rc;
+  // each backward arc knows its forward window (used to mark the windows a
+  // live source feeds at the next position)
+  int32_t* pos_by_id = nullptr;
+  if ((rc = dalloc(&pos_by_id, f->A)) || (rc = dalloc(&f->bwd.fwin, f->bwd.P))) { dfree(pos_by_id); return rc; }
+  if (f->fwd.P > 0) k_pos_by_id<<<blocks_for(f->fwd.P), TB, 0, s>>>(f->fwd.arc_id, f->fwd.P, pos_by_id);
+  if (f->bwd.P > 0) k_fwin<<<blocks_for(f->bwd.P), TB, 0, s>>>(f->bwd.arc_id, f->bwd.P, pos_by_id, f->bwd.fwin);
+  cudaError_t e = cudaStreamSynchronize(s);
+  dfree(pos_by_id);
+  if (e != cudaSuccess) return cuda_fail(e, "forward windows of backward arcs");
   return FST_OK;
 }
 
