@@ -165,7 +165,7 @@ struct PlainWs {
   int32_t *tok_sym = nullptr, *tok_b = nullptr, *tok_t = nullptr;
   int64_t *cbase = nullptr, *zero64 = nullptr, *wbase = nullptr, *bwbase = nullptr;
   int32_t* bp = nullptr;
-  uint8_t *wlive = nullptr, *fin = nullptr, *bin = nullptr;
+  uint8_t *wlive = nullptr, *fin = nullptr, *bin = nullptr, *bmk = nullptr;
   int64_t cap_wlive = 0, cap_bin = 0;
   float* rc = nullptr;
   uint32_t *mkey = nullptr, *ekey = nullptr;
@@ -185,7 +185,7 @@ struct PlainWs {
   int64_t cap_tsum = 0;
   int64_t max_lseg = 0, max_lwin = 0;
   ~PlainWs() {
-    dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wbase); dfree(wlive); dfree(bwbase); dfree(fin); dfree(bin);
+    dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wbase); dfree(wlive); dfree(bwbase); dfree(fin); dfree(bin); dfree(bmk);
     dfree(alpha); dfree(beta); dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(zero64);
     dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(skey); dfree(scnt);
     dfree(spart); dfree(cnt); dfree(comp); dfree(counts_out); dfree(paths); dfree(olabels); dfree(qfinal);
@@ -238,8 +238,9 @@ int plain_reserve(PlainWs* w, int64_t n, int64_t store, int64_t nwins, int64_t n
   if (nwins_b > w->cap_bin) {
     const int64_t c = std::max<int64_t>(nwins_b, 2 * w->cap_bin);
     dfree(w->bin);
+    dfree(w->bmk);
     w->cap_bin = 0;
-    if ((rc = dalloc(&w->bin, c))) return rc;
+    if ((rc = dalloc(&w->bin, c)) || (rc = dalloc(&w->bmk, c))) return rc;
     w->cap_bin = c;
   }
   if (n > w->cap_n) {
@@ -308,6 +309,7 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
     FST_CUDA(cudaMemsetAsync(w->wlive, 0, (size_t)wacc, s));
     FST_CUDA(cudaMemsetAsync(w->fin, 0, (size_t)wacc, s));
     FST_CUDA(cudaMemsetAsync(w->bin, 0, (size_t)bwacc, s));
+    FST_CUDA(cudaMemsetAsync(w->bmk, 0, (size_t)bwacc, s));
   }
   FST_CUDA(cudaMemcpyAsync(w->bw_n, &n, 4, cudaMemcpyHostToDevice, s));
   // fresh tags for this string
@@ -367,6 +369,12 @@ WaveState plain_state(fst_s* f) {
   S.b_sym_win = f->bwd.sym_win;
   S.b_fwin = f->bwd.fwin;
   S.f_sym_win = f->fwd.sym_win;
+  S.bmk = w->bmk;
+  S.f_seg_state = f->fwd.seg_state;
+  S.f_seg_pos = f->fwd.seg_pos;
+  S.f_seg_len = f->fwd.seg_len;
+  S.f_sym_seg = f->fwd.sym_seg;
+  S.f_bwin = f->fwd.bwin;
   S.sum_start = f->sum_start;
   S.sum_final = f->sum_final;
   S.Ws = f->Ws;

@@ -52,6 +52,7 @@ struct Layout {
   int32_t* seg_pos = nullptr;    // [nseg] padded start position
   int32_t* seg_len = nullptr;    // [nseg] arcs in the segment
   int32_t* fwin = nullptr;       // backward layout only: [P] forward window of each arc (-1 on padding)
+  int32_t* bwin = nullptr;       // forward layout only: [P] backward window of each arc (-1 on padding)
   int64_t* sym_win = nullptr;    // [m+1]
   int64_t* sym_seg = nullptr;    // [m+1]
   int64_t* sym_lseg = nullptr;   // [m+1] long segments

@@ -218,6 +218,24 @@ __device__ __forceinline__ void mark_next(const WaveState& S, const TokenView& T
   for (int32_t i = 0; i < len; ++i) S.fin[fb + __ldg(S.b_fwin + pos0 + i)] = 1;
 }
 
+// State q has a finite backward value at the position of token p (which is
+// not the first of its string): mark, for token p (input symbol a), the
+// backward windows that hold the arcs of the forward segment (a, q), i.e.
+// the arcs into q.
+__device__ __forceinline__ void mark_prev(const WaveState& S, const TokenView& T, int32_t p, int32_t q) {
+  const int32_t a = __ldg(T.sym + p);
+  int64_t lo = __ldg(S.f_sym_seg + a), hi = __ldg(S.f_sym_seg + a + 1);
+  const int64_t end = hi;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(S.f_seg_state + mid) < q) lo = mid + 1; else hi = mid;
+  }
+  if (lo >= end || __ldg(S.f_seg_state + lo) != q) return;  // no arc on symbol a enters q
+  const int32_t pos0 = __ldg(S.f_seg_pos + lo), len = __ldg(S.f_seg_len + lo);
+  const int64_t bb = __ldg(T.bwbase + p) - __ldg(S.b_sym_win + a);
+  for (int32_t i = 0; i < len; ++i) S.bmk[bb + __ldg(S.f_bwin + pos0 + i)] = 1;
+}
+
 // Tokens of the group (bit j = token j) that visit this window: every token
 // at the first position; later, the tokens that marked it, and every token
 // on a long segment's window (its segment counts the arrivals of all of them).
@@ -623,8 +641,24 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
     const int32_t wslice = item - G.lo;
     const Win x = load_win(L, G.wbase + wslice, lane);
     const bool is_long = x.lseg >= 0;
-    uint32_t todo = tokens_to_visit(S.bin, G.cnt, __shfl_sync(FULL, tt, 0), is_long, tbb, wslice, lane) &
-                    __ballot_sync(FULL, tlive);
+    bool visit = false;
+    if (lane < G.cnt && tlive) {
+      if (is_long) {
+        // every window of a long segment has the same source: all of them are
+        // visited, or none (their arrivals are counted); the forward marks
+        // cover every window of the segment of a live source
+        visit = (tt == 1) ? __ldg(S.theta_s + __ldg(L.seg_state + x.seg)) != neg_inf() : S.bin[tbb + wslice] != 0;
+      } else if (tt == 1 && tt == tn) {
+        visit = true;
+      } else if (tt == 1) {
+        visit = S.bmk[tbb + wslice] != 0;
+      } else if (tt == tn) {
+        visit = S.bin[tbb + wslice] != 0;
+      } else {
+        visit = S.bin[tbb + wslice] != 0 && S.bmk[tbb + wslice] != 0;
+      }
+    }
+    uint32_t todo = __ballot_sync(FULL, visit);
     if (!todo) continue;  // no live token has a source with a finite forward value here
     const int32_t base = x.w * WIN + lane * APL;
     const int4 d4 = __ldg(reinterpret_cast<const int4*>(L.other + base));
@@ -723,6 +757,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
               if (u != neg_inf()) {
                 bout[qs[k]] = tagged_make(u, tag);
                 set_live(bmout, smout, qs[k]);
+                mark_prev(S, T, p - 1, qs[k]);
               }
               umax = fmaxf(umax, u);
             }
@@ -736,6 +771,7 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
               const int32_t q = __ldg(L.seg_state + x.seg);
               bout[q] = tagged_make(u, tag);
               set_live(bmout, smout, q);
+              mark_prev(S, T, p - 1, q);
             }
             umax = u;
           }

@@ -112,6 +112,17 @@ struct WaveState {
   const int64_t* b_sym_win;
   const int32_t* b_fwin;
   const int64_t* f_sym_win;
+  // Backward marks, one byte per (token, backward window): set when the
+  // window holds an arc into a state whose backward value at that token's
+  // position is finite.  The backward pass visits a window of a token when
+  // its forward mark (bin) and backward mark (bmk) are set; at the first
+  // position only the backward mark, at the last only the forward mark.
+  uint8_t* bmk;
+  const int32_t* f_seg_state;
+  const int32_t* f_seg_pos;
+  const int32_t* f_seg_len;
+  const int64_t* f_sym_seg;
+  const int32_t* f_bwin;
 };
 
 struct CountView {

@@ -218,6 +218,7 @@ struct fst_plan_s {
   uint32_t *tsum = nullptr, *bsum = nullptr;  // forward summaries per token [max_ntok][Ws]; backward [3][max_bw][Ws]
   uint8_t* wlive = nullptr;                 // per (token, forward window) liveness of the largest wave
   uint8_t *fin = nullptr, *bin = nullptr;   // window marks (forward / backward windows)
+  uint8_t* bmk = nullptr;                   // backward marks (backward windows)
   int64_t max_nwins = 0, max_nwins_b = 0;
   int64_t max_bw = 0, max_ntok = 0, max_store = 0, max_lseg = 0, max_lwin = 0;
   bool forward_done = false;
@@ -231,7 +232,7 @@ struct fst_plan_s {
     for (Wave& w : waves) w.release();
     dfree(ids); dfree(alpha); dfree(beta); dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum);
     dfree(esum); dfree(skey); dfree(scnt); dfree(spart); dfree(qfinal); dfree(cnt64); dfree(logz);
-    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wlive); dfree(fin); dfree(bin);
+    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wlive); dfree(fin); dfree(bin); dfree(bmk);
   }
 };
 
@@ -423,6 +424,12 @@ WaveState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.b_sym_win = f->bwd.sym_win;
   S.b_fwin = f->bwd.fwin;
   S.f_sym_win = f->fwd.sym_win;
+  S.bmk = P->bmk;
+  S.f_seg_state = f->fwd.seg_state;
+  S.f_seg_pos = f->fwd.seg_pos;
+  S.f_seg_len = f->fwd.seg_len;
+  S.f_sym_seg = f->fwd.sym_seg;
+  S.f_bwin = f->fwd.bwin;
   S.sum_start = f->sum_start;
   S.sum_final = f->sum_final;
   S.Ws = f->Ws;
@@ -485,6 +492,7 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   FST_CUDA(cudaMemsetAsync(P->tsum, 0, (size_t)std::max<int64_t>(1, W.ntok * (int64_t)f->Ws) * 4, s));
   FST_CUDA(cudaMemsetAsync(P->fin, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
   FST_CUDA(cudaMemsetAsync(P->bin, 0, (size_t)std::max<int64_t>(1, W.nwins_b), s));
+  FST_CUDA(cudaMemsetAsync(P->bmk, 0, (size_t)std::max<int64_t>(1, W.nwins_b), s));
   for (int32_t t = 1; t <= W.tmax; ++t) {
     const WorkView V = wave_work(W, t, true);
     if ((rc = clear_rot(P, P->abm, t % 3, f->W, s))) return rc;
@@ -636,6 +644,7 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
     if (want_fb && (rc = alloc_track(P, &P->wlive, P->max_nwins))) break;
     if ((rc = alloc_track(P, &P->fin, P->max_nwins))) break;
     if (want_fb && (rc = alloc_track(P, &P->bin, P->max_nwins_b))) break;
+    if (want_fb && (rc = alloc_track(P, &P->bmk, P->max_nwins_b))) break;
     FST_CUDA(cudaMemsetAsync(P->alpha, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     FST_CUDA(cudaMemsetAsync(P->epoch, 0, 8, s));

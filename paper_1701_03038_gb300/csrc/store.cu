@@ -337,7 +337,7 @@ int build_layout(fst_s* f, Layout& L, const int32_t* d_il, const int32_t* seg_st
 
 void free_layout(Layout& L) {
   dfree(L.other); dfree(L.theta); dfree(L.arc_id); dfree(L.theta64); dfree(L.win);
-  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.seg_len); dfree(L.fwin); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
+  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.seg_len); dfree(L.fwin); dfree(L.bwin); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
   dfree(L.sym_lwin);
   free(L.h_sym_win); free(L.h_sym_seg); free(L.h_sym_lseg); free(L.h_sym_lwin);
   L.h_sym_win = L.h_sym_seg = L.h_sym_lseg = L.h_sym_lwin = nullptr;
@@ -355,9 +355,15 @@ int build_store(fst_s* f, const int32_t* d_src, const int32_t* d_dst, const int3
   // each backward arc knows its forward window (used to mark the windows a
   // live source feeds at the next position)
   int32_t* pos_by_id = nullptr;
-  if ((rc = dalloc(&pos_by_id, f->A)) || (rc = dalloc(&f->bwd.fwin, f->bwd.P))) { dfree(pos_by_id); return rc; }
+  if ((rc = dalloc(&pos_by_id, f->A)) || (rc = dalloc(&f->bwd.fwin, f->bwd.P)) || (rc = dalloc(&f->fwd.bwin, f->fwd.P))) {
+    dfree(pos_by_id);
+    return rc;
+  }
   if (f->fwd.P > 0) k_pos_by_id<<<blocks_for(f->fwd.P), TB, 0, s>>>(f->fwd.arc_id, f->fwd.P, pos_by_id);
   if (f->bwd.P > 0) k_fwin<<<blocks_for(f->bwd.P), TB, 0, s>>>(f->bwd.arc_id, f->bwd.P, pos_by_id, f->bwd.fwin);
+  // and each forward arc its backward window (marks of the backward pass)
+  if (f->bwd.P > 0) k_pos_by_id<<<blocks_for(f->bwd.P), TB, 0, s>>>(f->bwd.arc_id, f->bwd.P, pos_by_id);
+  if (f->fwd.P > 0) k_fwin<<<blocks_for(f->fwd.P), TB, 0, s>>>(f->fwd.arc_id, f->fwd.P, pos_by_id, f->fwd.bwin);
   cudaError_t e = cudaStreamSynchronize(s);
   dfree(pos_by_id);
   if (e != cudaSuccess) return cuda_fail(e, "forward windows of backward arcs");
