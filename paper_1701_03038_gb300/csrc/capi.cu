@@ -600,7 +600,7 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
     if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
     if ((rc = launch_vit_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
   }
-  if ((rc = launch_vit_final(Lf, w->tok_sym, w->cbase, S, 1, w->score, w->qfinal, w->status, s))) return rc;
+  if ((rc = launch_vit_final(S, 1, w->score, w->qfinal, w->status, s))) return rc;
   if ((rc = launch_backtrace(Lf, w->tok_sym, w->cbase, S, f->olabel, f->fwd.arc_id, 1, w->qfinal, w->paths,
                              w->olabels, s)))
     return rc;
@@ -646,7 +646,7 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
     if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
     if ((rc = launch_fwd_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
   }
-  if ((rc = launch_fb_final(Lf, w->tok_sym, w->cbase, w->wbase, S, 1, w->logz, w->status, s))) return rc;
+  if ((rc = launch_fb_final(S, 1, w->logz, w->status, s))) return rc;
   if (arc_posteriors) {
     CountView C{0, w->cnt, w->comp, nullptr};
     FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)f->bwd.P * 4, s));

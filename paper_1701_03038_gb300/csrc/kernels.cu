@@ -815,43 +815,78 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
 // Epilogues: final reduction (Alg. 1 return line; Alg. 2 Z), backtrace
 // (Sec. 5.1), and counts back to caller arc order.
 // ======================================================================
-__global__ void k_vit_final(LayoutView L, const int32_t* __restrict__ tok_sym, const int64_t* __restrict__ cbase,
-                            WaveState S, int32_t Bw, float* __restrict__ scores, int32_t* __restrict__ qfinal,
-                            int32_t* __restrict__ status) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t tag_base = *S.epoch + S.tok0;
-  const int64_t b = warp_id_global();
-  if (b >= Bw) return;
-  const int32_t n = S.bw_n[b];
-  unsigned long long best = 0ull;
-  if (n == 0) {
-    for (int32_t q = lane; q < S.Q; q += 32) {
-      const float cnd = __fadd_rn(S.theta_s[q], S.theta_f[q]);
-      if (cnd != neg_inf()) {
-        const unsigned long long k = ((unsigned long long)fkey(cnd) << 32) | (unsigned long long)(~(uint32_t)q);
-        best = k > best ? k : best;
-      }
-    }
-  } else {
-    const int64_t p = S.bw_off[b] + n - 1;
-    const int32_t sym = tok_sym[p];
-    const unsigned long long* ab = S.alpha + ((int64_t)b * 2 + (n & 1)) * S.Q;
-    const uint32_t tg = tag_base + (uint32_t)p;
-    for (int64_t s = L.sym_seg[sym] + lane; s < L.sym_seg[sym + 1]; s += 32) {
-      const int32_t q = L.seg_state[s];
-      const float cnd = __fadd_rn(tagged_value(ab[q], tg), S.theta_f[q]);
-      if (cnd != neg_inf()) {
-        const unsigned long long k = ((unsigned long long)fkey(cnd) << 32) | (unsigned long long)(~(uint32_t)q);
-        best = k > best ? k : best;
+// The states that can end a path at the last position lie in the 32-state
+// groups whose bit is set both in the position's forward summary (groups
+// holding a state written with a finite value) and in the summary of final
+// states.  A block per string: its warps stride over 32-word chunks of the
+// summaries, and for each marked group a warp reads its 32 states
+// (consecutive, one per lane) from the dense frontier, FV groups at a time.
+constexpr int FV = 4;
+constexpr int FT = 256;  // threads of the final-reduction blocks
+
+template <class F>
+__device__ __forceinline__ void for_final_groups(const uint32_t* __restrict__ live, const uint32_t* __restrict__ fin,
+                                                 int32_t Ws, F f) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int32_t c = warp * 32; c < Ws; c += (FT / 32) * 32) {
+    const int32_t wi = c + lane;
+    const uint32_t word = wi < Ws ? live[wi] & __ldg(fin + wi) : 0u;
+    uint32_t lanes = __ballot_sync(FULL, word != 0u);
+    while (lanes) {
+      const int l = __ffs(lanes) - 1;
+      lanes &= lanes - 1u;
+      uint32_t wd = __shfl_sync(FULL, word, l);  // warp-uniform
+      const int32_t g0 = (c + l) * 32;
+      while (wd) {
+        int32_t q[FV];
+#pragma unroll
+        for (int u = 0; u < FV; ++u) {
+          q[u] = wd ? (g0 + __ffs(wd) - 1) * 32 + lane : -1;
+          wd &= wd - 1u;
+        }
+        f(q);
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(FT) k_vit_final(WaveState S, float* __restrict__ scores,
+                                                  int32_t* __restrict__ qfinal, int32_t* __restrict__ status) {
+  __shared__ unsigned long long red[FT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t b = blockIdx.x;
+  const int32_t n = S.bw_n[b];
+  const int64_t p = S.bw_off[b] + n - 1;
+  const unsigned long long* ab = S.alpha + (b * 2 + (n & 1)) * S.Q;
+  const uint32_t tg = *S.epoch + S.tok0 + (uint32_t)p;
+  const int32_t Q = S.Q;
+  unsigned long long best = 0ull;
+  for_final_groups(n == 0 ? S.sum_start : S.tsum + p * S.Ws, S.sum_final, S.Ws, [&](const int32_t (&q)[FV]) {
+    float a[FV], fv[FV];
+#pragma unroll
+    for (int u = 0; u < FV; ++u) {
+      const bool ok = q[u] >= 0 && q[u] < Q;
+      a[u] = !ok ? neg_inf() : (n == 0 ? __ldg(S.theta_s + q[u]) : tagged_value(ab[q[u]], tg));
+      fv[u] = ok ? __ldg(S.theta_f + q[u]) : neg_inf();
+    }
+#pragma unroll
+    for (int u = 0; u < FV; ++u) {
+      const float cnd = __fadd_rn(a[u], fv[u]);
+      if (cnd != neg_inf()) {
+        const unsigned long long k = ((unsigned long long)fkey(cnd) << 32) | (unsigned long long)(~(uint32_t)q[u]);
+        best = k > best ? k : best;
+      }
+    }
+  });
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) {
     const unsigned long long o = __shfl_xor_sync(FULL, best, d);
     best = o > best ? o : best;
   }
-  if (lane == 0) {
+  if (lane == 0) red[warp] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < FT / 32; ++w) best = red[w] > best ? red[w] : best;
     scores[b] = best ? fkey_inv((uint32_t)(best >> 32)) : neg_inf();
     qfinal[b] = best ? (int32_t)(~(uint32_t)best) : -1;
     if (status) status[b] = best ? FST_OK : FST_ERR_NO_PATH;
@@ -909,68 +944,102 @@ __global__ void k_backtrace(LayoutView L, const int32_t* __restrict__ tok_sym, c
   }
 }
 
-// The stored forward values of the last position are valid only in windows
-// that the forward pass visited and marked live (others are -inf).
-__device__ __forceinline__ double final_value(const LayoutView& L, const WaveState& S, int64_t cb, int64_t wb,
-                                              int32_t sym, int64_t s) {
-  const int64_t wi = __ldg(L.seg_pos + s) / WIN - __ldg(L.sym_win + sym);
-  if (!S.wlive[wb + wi]) return -INFINITY;
-  return (double)S.rc[cb + (s - L.sym_seg[sym])] + (double)S.theta_f[L.seg_state[s]];
-}
-
-__global__ void k_fb_final(LayoutView L, const int32_t* __restrict__ tok_sym, const int64_t* __restrict__ cbase,
-                           const int64_t* __restrict__ wbase, WaveState S, int32_t Bw, double* __restrict__ logz,
-                           int32_t* __restrict__ status) {
-  const int lane = threadIdx.x & 31;
-  const int64_t b = warp_id_global();
-  if (b >= Bw) return;
+// log Z of one string (Alg. 2, Z): C_{n-1} + log sum_q exp(alpha_n[q] +
+// final[q]), alpha_n the shifted forward values of the last position.  Warp
+// 0 also writes the running normalisers C_t (a warp scan); the other
+// partial sums are online (max, sum) pairs per lane, exp in float32 as in
+// the step kernels, sums in float64, combined in a fixed order.
+__global__ void __launch_bounds__(FT) k_fb_final(WaveState S, double* __restrict__ logz,
+                                                 int32_t* __restrict__ status) {
+  __shared__ float red_m[FT / 32];
+  __shared__ double red_s[FT / 32];
+  __shared__ double c_prev;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t b = blockIdx.x;
   const int32_t n = S.bw_n[b];
   const int64_t off = S.bw_off[b];
-  // running normaliser C_t = sum_{s<=t} m_s, float64
-  double Cprev = 0.0;
-  if (lane == 0) {
-    double Cs = 0.0;
-    for (int32_t t = 1; t <= n; ++t) {
-      const float m = decode_max(S.mkey[off + t - 1]);
-      Cs = (m == neg_inf()) ? -INFINITY : Cs + (double)m;
-      S.csum[off + t - 1] = Cs;
-      if (t == n - 1) Cprev = Cs;
+  if (warp == 0) {
+    // C_t = sum_{s<=t} m_s in float64 (-inf once some position has no path)
+    if (lane == 0) c_prev = 0.0;
+    __syncwarp();
+    double carry = 0.0;
+    for (int32_t t0 = 0; t0 < n; t0 += 32) {
+      const int32_t t = t0 + lane;
+      double v = 0.0;
+      if (t < n) {
+        const float m = decode_max(S.mkey[off + t]);
+        v = (m == neg_inf()) ? -INFINITY : (double)m;
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const double o = __shfl_up_sync(FULL, v, d);
+        if (lane >= d) v += o;
+      }
+      v += carry;
+      if (t < n) S.csum[off + t] = v;
+      if (t == n - 2) c_prev = v;
+      carry = __shfl_sync(FULL, v, 31);
     }
   }
-  Cprev = __shfl_sync(FULL, Cprev, 0);
-  double mx = -INFINITY;
-  // two passes over the final candidates: max, then sum of exp
-  if (n == 0) {
-    for (int32_t q = lane; q < S.Q; q += 32) mx = fmax(mx, (double)S.theta_s[q] + (double)S.theta_f[q]);
-  } else {
-    const int64_t p = off + n - 1;
-    const int32_t sym = tok_sym[p];
-    for (int64_t s = L.sym_seg[sym] + lane; s < L.sym_seg[sym + 1]; s += 32)
-      mx = fmax(mx, final_value(L, S, cbase[p], wbase[p], sym, s));
-  }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, d));
+  const int64_t p = off + n - 1;
+  const unsigned long long* ab = S.alpha + (b * 2 + (n & 1)) * S.Q;
+  const uint32_t tg = *S.epoch + S.tok0 + (uint32_t)p;
+  const int32_t Q = S.Q;
+  float mx = neg_inf();
   double sum = 0.0;
-  if (mx != -INFINITY) {
-    if (n == 0) {
-      for (int32_t q = lane; q < S.Q; q += 32) {
-        const double v = (double)S.theta_s[q] + (double)S.theta_f[q];
-        if (v != -INFINITY) sum += exp(v - mx);
+  for_final_groups(n == 0 ? S.sum_start : S.tsum + p * S.Ws, S.sum_final, S.Ws, [&](const int32_t (&q)[FV]) {
+    float a[FV], fv[FV];
+#pragma unroll
+    for (int u = 0; u < FV; ++u) {
+      const bool ok = q[u] >= 0 && q[u] < Q;
+      a[u] = !ok ? neg_inf() : (n == 0 ? __ldg(S.theta_s + q[u]) : tagged_value(ab[q[u]], tg));
+      fv[u] = ok ? __ldg(S.theta_f + q[u]) : neg_inf();
+    }
+#pragma unroll
+    for (int u = 0; u < FV; ++u) {
+      const float v = __fadd_rn(a[u], fv[u]);
+      if (v == neg_inf()) continue;
+      if (v > mx) {
+        sum = (mx == neg_inf()) ? 1.0 : sum * (double)__expf(mx - v) + 1.0;
+        mx = v;
+      } else {
+        sum += (double)__expf(v - mx);
       }
-    } else {
-      const int64_t p = off + n - 1;
-      const int32_t sym = tok_sym[p];
-      for (int64_t s = L.sym_seg[sym] + lane; s < L.sym_seg[sym + 1]; s += 32) {
-        const double v = final_value(L, S, cbase[p], wbase[p], sym, s);
-        if (v != -INFINITY) sum += exp(v - mx);
+    }
+  });
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const float om = __shfl_xor_sync(FULL, mx, d);
+    const double os = __shfl_xor_sync(FULL, sum, d);
+    if (om != neg_inf()) {
+      if (om > mx) {
+        sum = (mx == neg_inf()) ? os : os + sum * (double)__expf(mx - om);
+        mx = om;
+      } else {
+        sum += os * (double)__expf(om - mx);
       }
     }
   }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) sum += __shfl_xor_sync(FULL, sum, d);
   if (lane == 0) {
+    red_m[warp] = mx;
+    red_s[warp] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < FT / 32; ++w) {
+      const float om = red_m[w];
+      const double os = red_s[w];
+      if (om == neg_inf()) continue;
+      if (om > mx) {
+        sum = (mx == neg_inf()) ? os : os + sum * (double)__expf(mx - om);
+        mx = om;
+      } else {
+        sum += os * (double)__expf(om - mx);
+      }
+    }
+    const double cp = c_prev;
     double lz = -INFINITY;
-    if (mx != -INFINITY && Cprev != -INFINITY) lz = Cprev + mx + log(sum);
+    if (mx != neg_inf() && cp != -INFINITY) lz = cp + (double)mx + log(sum);
     logz[b] = lz;
     if (status) status[b] = (lz == -INFINITY) ? FST_ERR_NO_PATH : FST_OK;
   }
@@ -1045,10 +1114,9 @@ int launch_scatter_alpha(const LayoutView& L, const TokenView& T, const WorkView
   return check_launch("k_scatter_alpha");
 }
 
-int launch_vit_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
-                     int32_t Bw, float* scores, int32_t* qfinal, int32_t* status, cudaStream_t s) {
+int launch_vit_final(const WaveState& S, int32_t Bw, float* scores, int32_t* qfinal, int32_t* status, cudaStream_t s) {
   if (Bw <= 0) return FST_OK;
-  k_vit_final<<<(unsigned)((Bw + 7) / 8), 256, 0, s>>>(Lf, tok_sym, cbase, S, Bw, scores, qfinal, status);
+  k_vit_final<<<(unsigned)Bw, FT, 0, s>>>(S, scores, qfinal, status);
   return check_launch("k_vit_final");
 }
 
@@ -1061,10 +1129,9 @@ int launch_backtrace(const LayoutView& Lf, const int32_t* tok_sym, const int64_t
   return check_launch("k_backtrace");
 }
 
-int launch_fb_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const int64_t* wbase,
-                    const WaveState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s) {
+int launch_fb_final(const WaveState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s) {
   if (Bw <= 0) return FST_OK;
-  k_fb_final<<<(unsigned)((Bw + 7) / 8), 256, 0, s>>>(Lf, tok_sym, cbase, wbase, S, Bw, logz, status);
+  k_fb_final<<<(unsigned)Bw, FT, 0, s>>>(S, logz, status);
   return check_launch("k_fb_final");
 }
 

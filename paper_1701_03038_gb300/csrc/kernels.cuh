@@ -141,13 +141,11 @@ int launch_bwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, 
                     const CountView& C, int grid, cudaStream_t s);
 int launch_scatter_alpha(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
                          int32_t t_bwd, int grid, cudaStream_t s);
-int launch_vit_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
-                     int32_t Bw, float* scores, int32_t* qfinal, int32_t* status, cudaStream_t s);
+int launch_vit_final(const WaveState& S, int32_t Bw, float* scores, int32_t* qfinal, int32_t* status, cudaStream_t s);
 int launch_backtrace(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
                      const int32_t* olabel_by_id, const int32_t* arc_id_fwd, int32_t Bw,
                      const int32_t* qfinal, int32_t* paths, int32_t* olabels, cudaStream_t s);
-int launch_fb_final(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const int64_t* wbase,
-                    const WaveState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s);
+int launch_fb_final(const WaveState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s);
 int launch_counts_out(const int32_t* arc_id_bwd, int64_t P, const CountView& C, float* out, cudaStream_t s);
 
 }  // namespace fstgpu

@@ -189,6 +189,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.b_fwin = f->bwd.fwin;
   S.f_sym_win = f->fwd.sym_win;
   S.sum_start = f->sum_start;
+  S.sum_final = f->sum_final;
   S.Ws = f->Ws;
   S.sum_rot = f->Ws;
   const TokenView T{tok_sym, tok_b, tok_t, cbase, zero64, zero64, zero64, zero64, wbase, zero64};
@@ -204,7 +205,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
     FST_CUDA(cudaMemsetAsync(abm + (int64_t)(t % 3) * W, 0, (size_t)W * 4, s));
     if ((rc = launch_vit_step(Lf, T, V, S, f->num_sms, s))) return rc;
   }
-  if ((rc = launch_vit_final(Lf, tok_sym, cbase, S, 1, d_score, qfinal, status, s))) return rc;
+  if ((rc = launch_vit_final(S, 1, d_score, qfinal, status, s))) return rc;
   if ((rc = launch_backtrace(Lf, tok_sym, cbase, S, f->olabel, f->fwd.arc_id, 1, qfinal, d_path, d_olabels, s)))
     return rc;
   return FST_OK;

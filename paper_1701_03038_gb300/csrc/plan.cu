@@ -498,7 +498,7 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
     if ((rc = clear_rot(P, P->abm, t % 3, f->W, s))) return rc;
     PROF(FST_PROF_FWD_STEP, launch_fwd_step(Lf, T, V, S, step_grid(f, V.nitems), s));
   }
-  PROF(FST_PROF_FB_FINAL, launch_fb_final(Lf, W.tok_sym, W.cbase, W.wbase, S, W.Bw, P->logz + W.b0,
+  PROF(FST_PROF_FB_FINAL, launch_fb_final(S, W.Bw, P->logz + W.b0,
                                            d_status ? d_status + W.b0 : nullptr, s));
   return FST_OK;
 }
@@ -713,7 +713,7 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
       if ((rc = clear_rot(P, P->abm, t % 3, f->W, s))) return rc;
       PROF(FST_PROF_VIT_STEP, launch_vit_step(Lf, T, V, S, step_grid(f, V.nitems), s));
     }
-    PROF(FST_PROF_VIT_FINAL, launch_vit_final(Lf, W.tok_sym, W.cbase, S, W.Bw, d_scores + W.b0, P->qfinal,
+    PROF(FST_PROF_VIT_FINAL, launch_vit_final(S, W.Bw, d_scores + W.b0, P->qfinal,
                                               d_status ? d_status + W.b0 : nullptr, s));
     PROF(FST_PROF_BACKTRACE, launch_backtrace(Lf, W.tok_sym, W.cbase, S, f->olabel, f->fwd.arc_id, W.Bw,
                                               P->qfinal, d_paths + W.tok0, d_olabels ? d_olabels + W.tok0 : nullptr,
