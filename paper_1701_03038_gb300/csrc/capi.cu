@@ -652,16 +652,19 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
     FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)f->bwd.P * 4, s));
     FST_CUDA(cudaMemsetAsync(w->comp, 0, (size_t)f->bwd.P * 4, s));
     for (int32_t t = n; t >= 1; --t) {
-      if (t < n && t >= 2) {
-        const int32_t a = ids[t - 2];
-        const int64_t ni = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
-        if ((rc = launch_scatter_alpha(Lf, T, single_work(t - 2, a, ni), S, t, step_grid(f, ni), s))) return rc;
+      // step t also restores alpha_{t-2} when the string is longer than t - 1
+      ScatterJob J{Lf, WorkView{}, t - 1};
+      if (t >= 3 && t - 1 < n) {
+        const int32_t a = ids[t - 3];
+        J.W = single_work(t - 3, a, f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a]);
       }
       const int32_t a = ids[t - 1];
       const int64_t nitems = f->bwd.h_sym_win[a + 1] - f->bwd.h_sym_win[a];
       if (t >= 2 && ((rc = clear_rot(w->bbm, (t - 1) % 3, f->W, s)) || (rc = clear_rot(w->bsum, (t - 1) % 3, f->Ws, s))))
         return rc;
-      if ((rc = launch_bwd_step(Lb, T, single_work(t - 1, a, nitems), S, C, step_grid(f, nitems), s))) return rc;
+      if ((rc = launch_bwd_step(Lb, T, single_work(t - 1, a, nitems), S, C, J,
+                                step_grid(f, std::max(nitems, J.W.nitems)), s)))
+        return rc;
     }
     if ((rc = launch_counts_out(f->bwd.arc_id, f->bwd.P, C, w->counts_out, s))) return rc;
     if (f->A > 0)

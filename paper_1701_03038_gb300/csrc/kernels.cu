@@ -541,13 +541,14 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS) k_fwd_step(LayoutView L, To
 }
 
 // ======================================================================
-// Scatter the stored forward values of step t_s back into the dense
-// frontier (needed by the backward step t_s + 1 when step t_s + 2 has
+// Scatter the stored forward values of one position t_s back into the
+// dense frontier (needed by the backward step t_s + 1 when step t_s + 2 has
 // overwritten that parity buffer).  Only windows that the forward pass
-// marked live are read.
+// marked live are read.  Runs inside the backward step t_s + 2, whose
+// frontier reads use the other parity buffer.
 // ======================================================================
-__global__ void __launch_bounds__(KT) k_scatter_alpha(LayoutView L, TokenView T, WorkView W, WaveState S,
-                                                      int32_t t_bwd) {
+__device__ __forceinline__ void scatter_alpha_items(const LayoutView& L, const TokenView& T, const WorkView& W,
+                                                    const WaveState& S, int32_t t_bwd) {
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
   const int32_t nw = warps_total();
@@ -603,7 +604,7 @@ __device__ __forceinline__ Live bwd_live(const WaveState& S, int32_t b, int32_t 
 }
 
 __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L, TokenView T, WorkView W,
-                                                                    WaveState S, CountView C) {
+                                                                    WaveState S, CountView C, ScatterJob J) {
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
   const int32_t nw = warps_total();
@@ -809,6 +810,9 @@ __global__ void __launch_bounds__(KT, KT_MIN_BLOCKS_BWD) k_bwd_step(LayoutView L
       }
     }
   }
+  // alpha_{t-2} for the next launch (backward step t - 1), into the parity
+  // buffer this step does not read
+  if (J.W.nitems > 0) scatter_alpha_items(J.L, T, J.W, S, J.t_bwd);
 }
 
 // ======================================================================
@@ -1101,17 +1105,11 @@ int launch_fwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, 
 }
 
 int launch_bwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
-                    const CountView& C, int grid, cudaStream_t s) {
-  if (W.nitems <= 0) return FST_OK;
-  k_bwd_step<<<grid_clamp(W.nitems, grid, resident_blocks(k_bwd_step, &g_occ[2])), KT, 0, s>>>(L, T, W, S, C);
+                    const CountView& C, const ScatterJob& J, int grid, cudaStream_t s) {
+  const int64_t items = W.nitems > J.W.nitems ? W.nitems : J.W.nitems;
+  if (items <= 0) return FST_OK;
+  k_bwd_step<<<grid_clamp(items, grid, resident_blocks(k_bwd_step, &g_occ[2])), KT, 0, s>>>(L, T, W, S, C, J);
   return check_launch("k_bwd_step");
-}
-
-int launch_scatter_alpha(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
-                         int32_t t_bwd, int grid, cudaStream_t s) {
-  if (W.nitems <= 0) return FST_OK;
-  k_scatter_alpha<<<grid_clamp(W.nitems, grid, resident_blocks(k_scatter_alpha, &g_occ[3])), KT, 0, s>>>(L, T, W, S, t_bwd);
-  return check_launch("k_scatter_alpha");
 }
 
 int launch_vit_final(const WaveState& S, int32_t Bw, float* scores, int32_t* qfinal, int32_t* status, cudaStream_t s) {

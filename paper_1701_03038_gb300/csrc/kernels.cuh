@@ -137,10 +137,18 @@ int launch_vit_step(const LayoutView& L, const TokenView& T, const WorkView& W, 
                     int grid, cudaStream_t s);
 int launch_fwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
                     int grid, cudaStream_t s);
+// Restoring the stored forward values of one position into the dense
+// frontier (the forward layout's work list of that position; only strings
+// longer than t_bwd).  It rides along with a backward step whose frontier
+// reads touch the other parity buffer; W.nitems == 0 means none.
+struct ScatterJob {
+  LayoutView L;
+  WorkView W;
+  int32_t t_bwd;
+};
+
 int launch_bwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
-                    const CountView& C, int grid, cudaStream_t s);
-int launch_scatter_alpha(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
-                         int32_t t_bwd, int grid, cudaStream_t s);
+                    const CountView& C, const ScatterJob& J, int grid, cudaStream_t s);
 int launch_vit_final(const WaveState& S, int32_t Bw, float* scores, int32_t* qfinal, int32_t* status, cudaStream_t s);
 int launch_backtrace(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
                      const int32_t* olabel_by_id, const int32_t* arc_id_fwd, int32_t Bw,

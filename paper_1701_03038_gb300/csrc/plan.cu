@@ -511,15 +511,15 @@ int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cuda
   const WaveState S = wave_state(P, W, d_weights);
   const CountView C{1, nullptr, nullptr, P->cnt64};
   for (int32_t t = W.tmax; t >= 1; --t) {
-    if (t < W.tmax && t >= 2) {
-      const WorkView V = wave_work(W, t - 1, true);
-      PROF(FST_PROF_SCATTER, launch_scatter_alpha(Lf, T, V, S, t, step_grid(f, V.nitems), s));
-    }
+    // step t also restores alpha_{t-2} of the strings longer than t - 1
+    // (their buffer of that parity now holds alpha_t)
+    ScatterJob J{Lf, WorkView{}, t - 1};
+    if (t >= 3) J.W = wave_work(W, t - 2, true);
     const WorkView V = wave_work(W, t, false);
     if (t >= 2 && ((rc = clear_rot(P, P->bbm, (t - 1) % 3, f->W, s)) ||
                    (rc = clear_rot(P, P->bsum, (t - 1) % 3, f->Ws, s))))
       return rc;
-    PROF(FST_PROF_BWD_STEP, launch_bwd_step(Lb, T, V, S, C, step_grid(f, V.nitems), s));
+    PROF(FST_PROF_BWD_STEP, launch_bwd_step(Lb, T, V, S, C, J, step_grid(f, std::max(V.nitems, J.W.nitems)), s));
   }
   return FST_OK;
 }
