@@ -225,15 +225,17 @@ FST_API int fst_log_z_f64(fst_t* fst, const double* theta, const int32_t* ids, i
  * device time in milliseconds and the number of launches since the last
  * read (host arrays of FST_PROF_KINDS entries, either may be NULL), then
  * starts a new accumulation.  Do not enable it while capturing a graph. */
-#define FST_PROF_VIT_STEP 0   /* Viterbi relaxation, one position */
-#define FST_PROF_VIT_FINAL 1  /* Viterbi final reduction */
-#define FST_PROF_BACKTRACE 2  /* Viterbi backtrace */
-#define FST_PROF_FWD_STEP 3   /* forward relaxation, one position */
-#define FST_PROF_FB_FINAL 4   /* log Z and the float64 normaliser prefix */
-#define FST_PROF_SCATTER 5    /* forward values restored for the backward pass */
-#define FST_PROF_BWD_STEP 6   /* backward relaxation fused with posteriors */
-#define FST_PROF_COUNTS 7     /* expected counts back to caller arc order */
-#define FST_PROF_KINDS 8
+#define FST_PROF_VIT_EXPAND 0  /* Viterbi: live states of t-1 stage the segments to reduce */
+#define FST_PROF_VIT_REDUCE 1  /* Viterbi: staged destination segments reduced (max, backpointer) */
+#define FST_PROF_VIT_FINAL 2   /* Viterbi final reduction */
+#define FST_PROF_BACKTRACE 3   /* Viterbi backtrace */
+#define FST_PROF_FWD_EXPAND 4  /* forward: live states of t-1 stage the segments to reduce */
+#define FST_PROF_FWD_REDUCE 5  /* forward: staged destination segments reduced (log-sum-exp) */
+#define FST_PROF_FB_FINAL 6    /* log Z and the float64 normaliser prefix */
+#define FST_PROF_BWD_EXPAND 7  /* backward: posteriors into the live states of t, sources staged */
+#define FST_PROF_BWD_REDUCE 8  /* backward: staged source segments reduced; forward values of t-2 restored */
+#define FST_PROF_COUNTS 9      /* expected counts back to caller arc order */
+#define FST_PROF_KINDS 10
 FST_API int fst_plan_profile(fst_plan_t* plan, int32_t enable);
 FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t* launches_by_kind);
 
@@ -243,7 +245,7 @@ FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t*
  * memory manager owns every allocation, a latency-critical loop that must
  * not take the implicit synchronisation of cudaMalloc/cudaFree, a process
  * under a hard device-memory cap.  Every piece of per-call working memory
- * (frontier, live-state bitmaps, backpointers, token tables) comes from one
+ * (frontier, touch bitmap, live states with backpointers, token tables) comes from one
  * fixed 32 MiB device array inside the library, resident on every device
  * that loads it until the process exits.
  *   ids        [n] host, symbols in [0, m); n >= 0.
@@ -253,10 +255,10 @@ FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t*
  *   stream     cudaStream_t; the call is asynchronous on it.
  * Results are bit-identical to fst_viterbi.  Returns FST_ERR_UNSUPPORTED
  * (nothing is launched) when the string needs more than the fixed array:
- * about 16*Q + 4*(sum over positions of distinct destinations of the
- * position's symbol) + 40*n bytes.  The first call on a device looks up
- * the array's device address with that device current: make it before any
- * stream capture.  All calls share the array and see the previous call's
+ * about 16*Q + Q/8 + 8*(sum over positions of the destination segments of
+ * the position's symbol) + 4*(the largest such count) + 40*n bytes.  The
+ * first call on a device looks up the array's device address with that
+ * device current: make it before any stream capture.  All calls share the array and see the previous call's
  * contents, which each call clears where needed; calls that overlap on the
  * GPU race on it and must be serialised by the caller. */
 FST_API int fst_viterbi_noalloc(fst_t* fst, const int32_t* ids, int32_t n, float* d_score, int32_t* d_path,

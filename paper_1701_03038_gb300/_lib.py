@@ -47,7 +47,8 @@ SIGNATURES = {
     "fst_log_z_f64": [vp, vp, vp, i32, vp],
 }
 
-PROF_KINDS = ["vit_step", "vit_final", "backtrace", "fwd_step", "fb_final", "scatter", "bwd_step", "counts"]
+PROF_KINDS = ["vit_expand", "vit_reduce", "vit_final", "backtrace", "fwd_expand", "fwd_reduce", "fb_final",
+              "bwd_expand", "bwd_reduce", "counts"]
 
 
 class FstError(RuntimeError):

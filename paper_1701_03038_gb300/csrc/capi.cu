@@ -74,38 +74,9 @@ __global__ void k_convert_states(const float* __restrict__ w, int32_t Q, int kin
   out[q] = __fadd_rn(th, 0.0f);
 }
 
-// bit q of word q / 32 is set when w[q] is finite
-__global__ void k_finite_bitmap(const float* __restrict__ w, int32_t Q, uint32_t* __restrict__ bm, int32_t W) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= W) return;
-  uint32_t m = 0;
-  for (int k = 0; k < 32; ++k) {
-    const int64_t q = i * 32 + k;
-    if (q < Q && w[q] != -INFINITY) m |= 1u << k;
-  }
-  bm[i] = m;
-}
-
-// bit j of summary word i is set when bitmap word 32 i + j is nonzero
-__global__ void k_bitmap_summary(const uint32_t* __restrict__ bm, int32_t W, uint32_t* __restrict__ sum, int32_t Ws) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Ws) return;
-  uint32_t m = 0;
-  for (int k = 0; k < 32; ++k) {
-    const int64_t w = i * 32 + k;
-    if (w < W && bm[w] != 0u) m |= 1u << k;
-  }
-  sum[i] = m;
-}
-
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
-}
-
-__global__ void k_check_ids(const int32_t* __restrict__ ids, int64_t n, int32_t m, unsigned int* __restrict__ err) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && (ids[i] < 0 || ids[i] >= m)) atomicOr(err, 32u);
 }
 
 // Run epochs: epoch[0] is the first tag of the current run and epoch[1]
@@ -158,48 +129,46 @@ struct DevBuf {
 }  // namespace
 
 // ======================================================== plain workspace
+// Working memory of the plain method (one string, one launch pair per
+// position), kept by the FST handle and grown on demand.
 struct PlainWs {
-  int64_t cap_n = 0, cap_store = 0;
   unsigned long long* alpha = nullptr;  // [2][Q]
-  unsigned long long* beta = nullptr;
-  int32_t *tok_sym = nullptr, *tok_b = nullptr, *tok_t = nullptr;
-  int64_t *cbase = nullptr, *zero64 = nullptr, *wbase = nullptr, *bwbase = nullptr;
-  int32_t* bp = nullptr;
-  uint8_t *wlive = nullptr, *fin = nullptr, *bin = nullptr, *bmk = nullptr;
-  int64_t cap_wlive = 0, cap_bin = 0;
-  float* rc = nullptr;
+  unsigned long long* beta = nullptr;   // [2][Q]
+  uint32_t* touch = nullptr;            // [W]
+  int32_t *tok_sym = nullptr, *tok_b = nullptr;
+  int32_t* iota = nullptr;              // step list: token t-1 is the only slot of position t
+  int64_t* zero64 = nullptr;            // staging offsets: one token per step
+  int64_t *slot_base = nullptr, *bslot_base = nullptr, *step_rng = nullptr, *bstep_rng = nullptr;
+  uint32_t *scnt_f = nullptr, *scnt_b = nullptr;
+  int64_t* pool_base = nullptr;
+  int32_t* pool_cnt = nullptr;
   uint32_t *mkey = nullptr, *ekey = nullptr;
   double *csum = nullptr, *esum = nullptr;
-  unsigned long long* skey = nullptr;
-  uint32_t* scnt = nullptr;
-  float2* spart = nullptr;
+  int32_t *paths = nullptr, *olabels = nullptr;
+  int64_t cap_n = 0;
+  int32_t* stage = nullptr;
+  int64_t cap_stage = 0;
+  int32_t *pool_q = nullptr, *pool_x = nullptr;
+  float* pool_v = nullptr;
+  int64_t cap_pool = 0;
   float *cnt = nullptr, *comp = nullptr, *counts_out = nullptr;
-  int32_t *paths = nullptr, *olabels = nullptr, *qfinal = nullptr, *status = nullptr;
+  int32_t *qfinal = nullptr, *status = nullptr, *bw_n = nullptr;
   float* score = nullptr;
   double* logz = nullptr;
-  int32_t* bw_n = nullptr;
   int64_t* bw_off = nullptr;
-  uint32_t *epoch = nullptr, *clear = nullptr;
-  uint32_t *abm = nullptr, *bbm = nullptr;  // [3][W] live-state bitmaps
-  uint32_t *tsum = nullptr, *bsum = nullptr;  // per-token forward summaries [n][Ws]; backward [3][Ws]
-  int64_t cap_tsum = 0;
-  int64_t max_lseg = 0, max_lwin = 0;
+  int64_t* pool_top = nullptr;
+  uint32_t *flags = nullptr, *epoch = nullptr, *clear = nullptr;
   ~PlainWs() {
-    dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wbase); dfree(wlive); dfree(bwbase); dfree(fin); dfree(bin); dfree(bmk);
-    dfree(alpha); dfree(beta); dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(zero64);
-    dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(skey); dfree(scnt);
-    dfree(spart); dfree(cnt); dfree(comp); dfree(counts_out); dfree(paths); dfree(olabels); dfree(qfinal);
-    dfree(status); dfree(score); dfree(logz); dfree(bw_n); dfree(bw_off); dfree(epoch); dfree(clear);
+    dfree(alpha); dfree(beta); dfree(touch); dfree(tok_sym); dfree(tok_b); dfree(iota); dfree(zero64);
+    dfree(slot_base); dfree(bslot_base); dfree(step_rng); dfree(bstep_rng); dfree(scnt_f);
+    dfree(scnt_b); dfree(pool_base); dfree(pool_cnt); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum);
+    dfree(paths); dfree(olabels); dfree(stage); dfree(pool_q); dfree(pool_x); dfree(pool_v); dfree(cnt);
+    dfree(comp); dfree(counts_out); dfree(qfinal); dfree(status); dfree(bw_n); dfree(score); dfree(logz);
+    dfree(bw_off); dfree(pool_top); dfree(flags); dfree(epoch); dfree(clear);
   }
 };
 
 namespace {
-
-int64_t max_diff(const int64_t* h, int32_t m) {
-  int64_t mx = 0;
-  for (int32_t a = 0; a < m; ++a) mx = std::max(mx, h[a + 1] - h[a]);
-  return mx;
-}
 
 int plain_init(fst_s* f) {
   if (f->plain) return FST_OK;
@@ -207,199 +176,160 @@ int plain_init(fst_s* f) {
   f->plain = w;
   const int64_t Q = f->Q;
   int rc;
-  w->max_lseg = std::max(max_diff(f->fwd.h_sym_lseg, f->m), max_diff(f->bwd.h_sym_lseg, f->m));
-  w->max_lwin = std::max(max_diff(f->fwd.h_sym_lwin, f->m), max_diff(f->bwd.h_sym_lwin, f->m));
-  if ((rc = dalloc(&w->alpha, 2 * Q)) || (rc = dalloc(&w->beta, 2 * Q)) || (rc = dalloc(&w->skey, w->max_lseg)) ||
-      (rc = dalloc(&w->scnt, w->max_lseg)) || (rc = dalloc(&w->spart, w->max_lwin)) ||
+  if ((rc = dalloc(&w->alpha, 2 * Q)) || (rc = dalloc(&w->beta, 2 * Q)) || (rc = dalloc(&w->touch, f->W)) ||
       (rc = dalloc(&w->qfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
       (rc = dalloc(&w->logz, 1)) || (rc = dalloc(&w->bw_n, 1)) || (rc = dalloc(&w->bw_off, 1)) ||
-      (rc = dalloc(&w->epoch, 2)) || (rc = dalloc(&w->clear, 1)) || (rc = dalloc(&w->abm, 3 * (int64_t)f->W)) ||
-      (rc = dalloc(&w->bbm, 3 * (int64_t)f->W)) || (rc = dalloc(&w->bsum, 3 * (int64_t)f->Ws)))
+      (rc = dalloc(&w->pool_top, 1)) || (rc = dalloc(&w->flags, 2)) || (rc = dalloc(&w->epoch, 2)) ||
+      (rc = dalloc(&w->clear, 1)))
     return rc;
   FST_CUDA(cudaMemset(w->alpha, 0, (size_t)2 * Q * sizeof(unsigned long long)));
   FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(unsigned long long)));
-  FST_CUDA(cudaMemset(w->skey, 0, (size_t)std::max<int64_t>(1, w->max_lseg) * 8));
-  FST_CUDA(cudaMemset(w->scnt, 0, (size_t)std::max<int64_t>(1, w->max_lseg) * 4));
+  FST_CUDA(cudaMemset(w->touch, 0, (size_t)f->W * 4));
   FST_CUDA(cudaMemset(w->bw_off, 0, sizeof(int64_t)));
   FST_CUDA(cudaMemset(w->epoch, 0, 2 * sizeof(uint32_t)));
   return FST_OK;
 }
 
-int plain_reserve(PlainWs* w, int64_t n, int64_t store, int64_t nwins, int64_t nwins_b) {
+// Grow the per-string buffers: n tokens, a staging buffer for the largest
+// slice, and a pool for every destination segment of the string (its exact
+// bound, so the plain method never runs out of pool).
+int plain_reserve(PlainWs* w, int64_t n, int64_t stage, int64_t pool) {
   int rc;
-  if (nwins > w->cap_wlive) {
-    const int64_t c = std::max<int64_t>(nwins, 2 * w->cap_wlive);
-    dfree(w->wlive);
-    dfree(w->fin);
-    w->cap_wlive = 0;
-    if ((rc = dalloc(&w->wlive, c)) || (rc = dalloc(&w->fin, c))) return rc;
-    w->cap_wlive = c;
-  }
-  if (nwins_b > w->cap_bin) {
-    const int64_t c = std::max<int64_t>(nwins_b, 2 * w->cap_bin);
-    dfree(w->bin);
-    dfree(w->bmk);
-    w->cap_bin = 0;
-    if ((rc = dalloc(&w->bin, c)) || (rc = dalloc(&w->bmk, c))) return rc;
-    w->cap_bin = c;
-  }
   if (n > w->cap_n) {
     const int64_t c = std::max<int64_t>(n, 2 * w->cap_n);
-    dfree(w->tok_sym); dfree(w->tok_b); dfree(w->tok_t); dfree(w->cbase); dfree(w->zero64); dfree(w->wbase);
-    dfree(w->bwbase);
-    dfree(w->mkey); dfree(w->ekey); dfree(w->csum); dfree(w->esum); dfree(w->paths); dfree(w->olabels);
+    dfree(w->tok_sym); dfree(w->tok_b); dfree(w->iota); dfree(w->zero64); dfree(w->slot_base); dfree(w->bslot_base);
+    dfree(w->step_rng); dfree(w->bstep_rng); dfree(w->scnt_f); dfree(w->scnt_b); dfree(w->pool_base);
+    dfree(w->pool_cnt); dfree(w->mkey); dfree(w->ekey); dfree(w->csum); dfree(w->esum); dfree(w->paths);
+    dfree(w->olabels);
     w->cap_n = 0;
-    if ((rc = dalloc(&w->tok_sym, c)) || (rc = dalloc(&w->tok_b, c)) || (rc = dalloc(&w->tok_t, c)) ||
-        (rc = dalloc(&w->cbase, c)) || (rc = dalloc(&w->zero64, c)) || (rc = dalloc(&w->wbase, c)) ||
-        (rc = dalloc(&w->bwbase, c)) ||
-        (rc = dalloc(&w->mkey, c)) ||
-        (rc = dalloc(&w->ekey, c)) || (rc = dalloc(&w->csum, c)) || (rc = dalloc(&w->esum, c)) ||
-        (rc = dalloc(&w->paths, c)) || (rc = dalloc(&w->olabels, c)))
+    if ((rc = dalloc(&w->iota, c)) || (rc = dalloc(&w->slot_base, c)) || (rc = dalloc(&w->bslot_base, c)) ||
+        (rc = dalloc(&w->step_rng, 2 * (c + 2))) || (rc = dalloc(&w->bstep_rng, 2 * (c + 2))))
+      return rc;
+    {
+      std::vector<int32_t> io(c);
+      for (int64_t i = 0; i < c; ++i) io[i] = (int32_t)i;
+      FST_CUDA(cudaMemcpy(w->iota, io.data(), (size_t)c * 4, cudaMemcpyHostToDevice));
+    }
+    if ((rc = dalloc(&w->tok_sym, c)) || (rc = dalloc(&w->tok_b, c)) || (rc = dalloc(&w->zero64, c)) ||
+        (rc = dalloc(&w->scnt_f, c)) || (rc = dalloc(&w->scnt_b, c)) || (rc = dalloc(&w->pool_base, c)) ||
+        (rc = dalloc(&w->pool_cnt, c)) || (rc = dalloc(&w->mkey, c)) || (rc = dalloc(&w->ekey, c)) ||
+        (rc = dalloc(&w->csum, c)) || (rc = dalloc(&w->esum, c)) || (rc = dalloc(&w->paths, c)) ||
+        (rc = dalloc(&w->olabels, c)))
       return rc;
     FST_CUDA(cudaMemset(w->tok_b, 0, (size_t)c * sizeof(int32_t)));
     FST_CUDA(cudaMemset(w->zero64, 0, (size_t)c * sizeof(int64_t)));
     w->cap_n = c;
   }
-  if (store > w->cap_store) {
-    const int64_t c = std::max<int64_t>(store, 2 * w->cap_store);
-    dfree(w->bp); dfree(w->rc);
-    w->cap_store = 0;
-    if ((rc = dalloc(&w->bp, c)) || (rc = dalloc(&w->rc, c))) return rc;
-    w->cap_store = c;
+  if (stage > w->cap_stage) {
+    const int64_t c = std::max<int64_t>(stage, 2 * w->cap_stage);
+    dfree(w->stage);
+    w->cap_stage = 0;
+    if ((rc = dalloc(&w->stage, c))) return rc;
+    w->cap_stage = c;
+  }
+  if (pool > w->cap_pool) {
+    const int64_t c = std::max<int64_t>(pool, 2 * w->cap_pool);
+    dfree(w->pool_q); dfree(w->pool_x); dfree(w->pool_v);
+    w->cap_pool = 0;
+    if ((rc = dalloc(&w->pool_q, c)) || (rc = dalloc(&w->pool_x, c)) || (rc = dalloc(&w->pool_v, c))) return rc;
+    w->cap_pool = c;
   }
   return FST_OK;
 }
 
-// Upload the tokens of one string: symbol, position, compact-storage base.
+// Upload the tokens of one string and start a run: fresh tags, zero counts.
 int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
   PlainWs* w = f->plain;
-  std::vector<int32_t> tt(std::max(n, 1));
-  std::vector<int64_t> cb(std::max(n, 1)), wb(std::max(n, 1)), bwb(std::max(n, 1));
-  int64_t acc = 0, wacc = 0, bwacc = 0;
+  int64_t stage = 1, pool = 1;
   for (int32_t i = 0; i < n; ++i) {
     if (ids[i] < 0 || ids[i] >= f->m) {
       set_error("symbol %d at position %d is outside [0, %d)", ids[i], i, f->m);
       return FST_ERR_INVALID_ARG;
     }
-    tt[i] = i + 1;
-    cb[i] = acc;
-    wb[i] = wacc;
-    bwb[i] = bwacc;
-    acc += f->fwd.h_sym_seg[ids[i] + 1] - f->fwd.h_sym_seg[ids[i]];
-    wacc += f->fwd.h_sym_win[ids[i] + 1] - f->fwd.h_sym_win[ids[i]];
-    bwacc += f->bwd.h_sym_win[ids[i] + 1] - f->bwd.h_sym_win[ids[i]];
+    const int64_t D = f->fwd.h_sym_seg[ids[i] + 1] - f->fwd.h_sym_seg[ids[i]];
+    const int64_t U = f->bwd.h_sym_seg[ids[i] + 1] - f->bwd.h_sym_seg[ids[i]];
+    stage = std::max(stage, std::max(D, U));
+    pool += D;
   }
-  int rc = plain_reserve(w, std::max(n, 1), std::max<int64_t>(acc, 1), std::max<int64_t>(wacc, 1),
-                         std::max<int64_t>(bwacc, 1));
+  int rc = plain_reserve(w, std::max(n, 1), stage, pool);
   if (rc) return rc;
-  const int64_t ntsum = std::max<int64_t>((int64_t)n * f->Ws, 1);
-  if (ntsum > w->cap_tsum) {
-    dfree(w->tsum);
-    w->cap_tsum = 0;
-    if ((rc = dalloc(&w->tsum, std::max<int64_t>(ntsum, 2 * w->cap_tsum)))) return rc;
-    w->cap_tsum = ntsum;
-  }
-  FST_CUDA(cudaMemsetAsync(w->tsum, 0, (size_t)ntsum * 4, s));
-  if (n > 0) {
-    FST_CUDA(cudaMemcpyAsync(w->tok_sym, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
-    FST_CUDA(cudaMemcpyAsync(w->tok_t, tt.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
-    FST_CUDA(cudaMemcpyAsync(w->cbase, cb.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
-    FST_CUDA(cudaMemcpyAsync(w->wbase, wb.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
-    FST_CUDA(cudaMemcpyAsync(w->bwbase, bwb.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
-    FST_CUDA(cudaMemsetAsync(w->wlive, 0, (size_t)wacc, s));
-    FST_CUDA(cudaMemsetAsync(w->fin, 0, (size_t)wacc, s));
-    FST_CUDA(cudaMemsetAsync(w->bin, 0, (size_t)bwacc, s));
-    FST_CUDA(cudaMemsetAsync(w->bmk, 0, (size_t)bwacc, s));
-  }
+  const size_t n4 = (size_t)std::max(n, 1) * 4;
+  if (n > 0) FST_CUDA(cudaMemcpyAsync(w->tok_sym, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   FST_CUDA(cudaMemcpyAsync(w->bw_n, &n, 4, cudaMemcpyHostToDevice, s));
+  FST_CUDA(cudaMemsetAsync(w->scnt_f, 0, n4, s));
+  FST_CUDA(cudaMemsetAsync(w->scnt_b, 0, n4, s));
+  FST_CUDA(cudaMemsetAsync(w->mkey, 0, n4, s));
+  FST_CUDA(cudaMemsetAsync(w->ekey, 0, n4, s));
+  FST_CUDA(cudaMemsetAsync(w->pool_top, 0, 8, s));
+  FST_CUDA(cudaMemsetAsync(w->flags, 0, 8, s));
+  FST_CUDA(cudaMemsetAsync(w->touch, 0, (size_t)f->W * 4, s));
   // fresh tags for this string
   k_epoch_advance<<<1, 1, 0, s>>>(w->epoch, (uint32_t)n + 1u, w->clear);
   k_clear_if<<<nblk(2 * (int64_t)f->Q), TB, 0, s>>>(w->clear, w->alpha, 2 * (int64_t)f->Q);
   k_clear_if<<<nblk(2 * (int64_t)f->Q), TB, 0, s>>>(w->clear, w->beta, 2 * (int64_t)f->Q);
-  FST_CUDA(cudaMemsetAsync(w->skey, 0, (size_t)std::max<int64_t>(1, w->max_lseg) * 8, s));
-  FST_CUDA(cudaMemsetAsync(w->scnt, 0, (size_t)std::max<int64_t>(1, w->max_lseg) * 4, s));
   FST_CUDA(cudaGetLastError());
   return FST_OK;
 }
 
-TokenView plain_tokview(PlainWs* w) {
-  return TokenView{w->tok_sym, w->tok_b, w->tok_t, w->cbase, w->zero64, w->zero64, w->zero64, w->zero64, w->wbase,
-                   w->bwbase};
-}
+TokenView plain_tokview(PlainWs* w) { return TokenView{w->iota, w->tok_sym, w->tok_b, w->zero64, w->zero64}; }
 
-WaveState plain_state(fst_s* f) {
+FrontierState plain_state(fst_s* f) {
   PlainWs* w = f->plain;
-  WaveState S;
+  FrontierState S;
   memset(&S, 0, sizeof(S));
   S.Q = f->Q;
+  S.W = f->W;
   S.epoch = w->epoch;
   S.tok0 = 0;
   S.alpha = w->alpha;
   S.beta = w->beta;
-  S.bp = w->bp;
-  S.rc = w->rc;
+  S.touch = w->touch;
+  S.stage = w->stage;
+  S.scnt_f = w->scnt_f;
+  S.scnt_b = w->scnt_b;
+  S.pool_q = w->pool_q;
+  S.pool_x = w->pool_x;
+  S.pool_v = w->pool_v;
+  S.pool_base = w->pool_base;
+  S.pool_cnt = w->pool_cnt;
+  S.slot_base = w->slot_base;
+  S.bslot_base = w->bslot_base;
+  S.step_rng = w->step_rng;
+  S.bstep_rng = w->bstep_rng;
+  S.pool_top = w->pool_top;
+  S.pool_cap = w->cap_pool;
+  S.flags = w->flags;
+  S.theta_s = f->theta_s;
+  S.theta_f = f->theta_f;
+  S.start_q = f->start_q;
+  S.nstart = f->nstart;
   S.mkey = w->mkey;
   S.ekey = w->ekey;
   S.csum = w->csum;
   S.esum = w->esum;
-  S.skey = w->skey;
-  S.scnt = w->scnt;
-  S.spart = w->spart;
-  S.theta_s = f->theta_s;
-  S.theta_f = f->theta_f;
   S.logz = w->logz;
   S.gweight = nullptr;
   S.bw_n = w->bw_n;
   S.bw_off = w->bw_off;
-  S.abm = w->abm;
-  S.bbm = w->bbm;
-  S.bm_start = f->bm_start;
-  S.bm_final = f->bm_final;
-  S.W = f->W;
-  S.bm_rot = f->W;
-  S.wlive = w->wlive;
-  S.tsum = w->tsum;
-  S.bsum = w->bsum;
-  S.fin = w->fin;
-  S.bin = w->bin;
-  S.b_seg_state = f->bwd.seg_state;
-  S.b_seg_pos = f->bwd.seg_pos;
-  S.b_seg_len = f->bwd.seg_len;
-  S.b_sym_seg = f->bwd.sym_seg;
-  S.b_sym_win = f->bwd.sym_win;
-  S.b_fwin = f->bwd.fwin;
-  S.f_sym_win = f->fwd.sym_win;
-  S.bmk = w->bmk;
-  S.f_seg_state = f->fwd.seg_state;
-  S.f_seg_pos = f->fwd.seg_pos;
-  S.f_seg_len = f->fwd.seg_len;
-  S.f_sym_seg = f->fwd.sym_seg;
-  S.f_bwin = f->fwd.bwin;
-  S.sum_start = f->sum_start;
-  S.sum_final = f->sum_final;
-  S.Ws = f->Ws;
-  S.sum_rot = f->Ws;
   return S;
 }
 
-// Clear rotation r of a [3][W] bitmap set before the launch that fills it.
-int clear_rot(uint32_t* bm, int32_t r, int64_t words, cudaStream_t s) {
-  FST_CUDA(cudaMemsetAsync(bm + (int64_t)r * words, 0, (size_t)words * 4, s));
-  return FST_OK;
+// The single token of position t (slot t-1); x_t names the other position
+// a kernel reads (the previous one for expand, t-2 for the backward reduce).
+// The grid covers the widest frontier the string's symbols allow, capped at
+// what is resident at once.
+StepView plain_step(const fst_s* f, int32_t n, int32_t t, int32_t x_t) {
+  StepView V;
+  V.t = t;
+  V.n = 1;
+  V.slot0 = t - 1;
+  const bool hasx = x_t >= 1 && x_t <= n;
+  V.x_t = hasx ? x_t : 0;
+  V.x_n = hasx ? 1 : 0;
+  V.x_slot0 = hasx ? x_t - 1 : 0;
+  V.blocks = f->num_sms * 4;
+  return V;
 }
-
-WorkView single_work(int32_t p, int32_t sym, int64_t nitems) {
-  WorkView W;
-  memset(&W, 0, sizeof(W));
-  W.single = 1;
-  W.p0 = p;
-  W.sym0 = sym;
-  W.nitems = nitems;
-  return W;
-}
-
-// the launchers size step grids from the SM count and the kernel's occupancy
-int step_grid(const fst_s* f, int64_t) { return f->num_sms; }
 
 struct DevGuard {
   int old = -1;
@@ -482,16 +412,20 @@ extern "C" int fst_create(int32_t num_states, int64_t num_arcs, const int32_t* s
       k_fill_i32<<<nblk(A), TB, 0, s>>>(f->olabel, A, -1);
     }
     f->W = (int32_t)((Q + 31) / 32);
-    if ((rc = dalloc(&f->bm_start, f->W)) || (rc = dalloc(&f->bm_final, f->W))) break;
-    k_finite_bitmap<<<nblk(f->W), TB, 0, s>>>(f->theta_s, f->Q, f->bm_start, f->W);
-    k_finite_bitmap<<<nblk(f->W), TB, 0, s>>>(f->theta_f, f->Q, f->bm_final, f->W);
-    f->Ws = (f->W + 31) / 32;
-    if ((rc = dalloc(&f->sum_start, f->Ws)) || (rc = dalloc(&f->sum_final, f->Ws))) break;
-    k_bitmap_summary<<<nblk(f->Ws), TB, 0, s>>>(f->bm_start, f->W, f->sum_start, f->Ws);
-    k_bitmap_summary<<<nblk(f->Ws), TB, 0, s>>>(f->bm_final, f->W, f->sum_final, f->Ws);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { rc = cuda_fail(e, "fst_create kernels"); break; }
     if ((rc = read_err_flag(d_err, "fst_create"))) break;
+    // the states with a finite start weight: the live states before the
+    // first position
+    {
+      std::vector<float> hs(Q);
+      FST_CUDA(cudaMemcpy(hs.data(), f->theta_s, (size_t)Q * 4, cudaMemcpyDeviceToHost));
+      std::vector<int32_t> sq;
+      for (int64_t q = 0; q < Q; ++q)
+        if (hs[q] != -INFINITY) sq.push_back((int32_t)q);
+      f->nstart = (int32_t)sq.size();
+      if ((rc = to_device(sq.data(), &f->start_q, (int64_t)sq.size()))) break;
+    }
     rc = build_store(f, d_src, d_dst, d_il, d_theta, s);
   } while (0);
   cleanup();
@@ -512,10 +446,7 @@ extern "C" int fst_destroy(fst_t* f) {
   free_layout(f->bwd);
   dfree(f->theta_s);
   dfree(f->theta_f);
-  dfree(f->bm_start);
-  dfree(f->bm_final);
-  dfree(f->sum_start);
-  dfree(f->sum_final);
+  dfree(f->start_q);
   dfree(f->olabel);
   dfree(f->sym_arc);
   free(f->h_sym_arc);
@@ -590,20 +521,16 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
   cudaStream_t s = 0;
   if ((rc = plain_tokens(f, ids, n, s))) return rc;
   PlainWs* w = f->plain;
-  const LayoutView Lf = view_of(f->fwd);
+  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
-  const WaveState S = plain_state(f);
-  // one launch per input position over the arcs of delta[w_t] (Sec. 5)
+  const FrontierState S = plain_state(f);
+  // one launch pair per input position (Sec. 5)
   for (int32_t t = 1; t <= n; ++t) {
-    const int32_t a = ids[t - 1];
-    const int64_t nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
-    if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
-    if ((rc = launch_vit_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
+    const StepView V = plain_step(f, n, t, t - 1);
+    if ((rc = launch_expand(Lb, T, V, S, s)) || (rc = launch_vit_reduce(Lf, T, V, S, s))) return rc;
   }
   if ((rc = launch_vit_final(S, 1, w->score, w->qfinal, w->status, s))) return rc;
-  if ((rc = launch_backtrace(Lf, w->tok_sym, w->cbase, S, f->olabel, f->fwd.arc_id, 1, w->qfinal, w->paths,
-                             w->olabels, s)))
-    return rc;
+  if ((rc = launch_backtrace(Lf, S, f->olabel, 1, w->qfinal, w->paths, w->olabels, s))) return rc;
   int32_t st = 0;
   FST_CUDA(cudaMemcpy(best_score, w->score, 4, cudaMemcpyDeviceToHost));
   FST_CUDA(cudaMemcpy(&st, w->status, 4, cudaMemcpyDeviceToHost));
@@ -630,43 +557,27 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   if ((rc = plain_tokens(f, ids, n, s))) return rc;
   PlainWs* w = f->plain;
   if (arc_posteriors && !w->cnt) {
-    if ((rc = dalloc(&w->cnt, f->bwd.P)) || (rc = dalloc(&w->comp, f->bwd.P)) || (rc = dalloc(&w->counts_out, f->A)))
+    if ((rc = dalloc(&w->cnt, f->fwd.P)) || (rc = dalloc(&w->comp, f->fwd.P)) || (rc = dalloc(&w->counts_out, f->A)))
       return rc;
   }
   const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
-  WaveState S = plain_state(f);
-  if (n > 0) {
-    FST_CUDA(cudaMemsetAsync(w->mkey, 0, (size_t)n * 4, s));
-    FST_CUDA(cudaMemsetAsync(w->ekey, 0, (size_t)n * 4, s));
-  }
+  const FrontierState S = plain_state(f);
   for (int32_t t = 1; t <= n; ++t) {
-    const int32_t a = ids[t - 1];
-    const int64_t nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
-    if ((rc = clear_rot(w->abm, t % 3, f->W, s))) return rc;
-    if ((rc = launch_fwd_step(Lf, T, single_work(t - 1, a, nitems), S, step_grid(f, nitems), s))) return rc;
+    const StepView V = plain_step(f, n, t, t - 1);
+    if ((rc = launch_expand(Lb, T, V, S, s)) || (rc = launch_fwd_reduce(Lf, T, V, S, s))) return rc;
   }
   if ((rc = launch_fb_final(S, 1, w->logz, w->status, s))) return rc;
   if (arc_posteriors) {
-    CountView C{0, w->cnt, w->comp, nullptr};
-    FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)f->bwd.P * 4, s));
-    FST_CUDA(cudaMemsetAsync(w->comp, 0, (size_t)f->bwd.P * 4, s));
+    const CountView C{0, w->cnt, w->comp, nullptr};
+    FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)f->fwd.P * 4, s));
+    FST_CUDA(cudaMemsetAsync(w->comp, 0, (size_t)f->fwd.P * 4, s));
     for (int32_t t = n; t >= 1; --t) {
-      // step t also restores alpha_{t-2} when the string is longer than t - 1
-      ScatterJob J{Lf, WorkView{}, t - 1};
-      if (t >= 3 && t - 1 < n) {
-        const int32_t a = ids[t - 3];
-        J.W = single_work(t - 3, a, f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a]);
-      }
-      const int32_t a = ids[t - 1];
-      const int64_t nitems = f->bwd.h_sym_win[a + 1] - f->bwd.h_sym_win[a];
-      if (t >= 2 && ((rc = clear_rot(w->bbm, (t - 1) % 3, f->W, s)) || (rc = clear_rot(w->bsum, (t - 1) % 3, f->Ws, s))))
-        return rc;
-      if ((rc = launch_bwd_step(Lb, T, single_work(t - 1, a, nitems), S, C, J,
-                                step_grid(f, std::max(nitems, J.W.nitems)), s)))
-        return rc;
+      const StepView V = plain_step(f, n, t, t - 2);
+      if ((rc = launch_bwd_expand(Lf, T, V, S, C, s))) return rc;
+      if (t >= 2 && (rc = launch_bwd_reduce(Lb, T, V, S, s))) return rc;
     }
-    if ((rc = launch_counts_out(f->bwd.arc_id, f->bwd.P, C, w->counts_out, s))) return rc;
+    if ((rc = launch_counts_out(f->fwd.arc_id, f->fwd.P, C, w->counts_out, s))) return rc;
     if (f->A > 0)
       FST_CUDA(cudaMemcpy(arc_posteriors, w->counts_out, (size_t)f->A * 4, cudaMemcpyDeviceToHost));
   }

@@ -27,7 +27,6 @@ namespace fstgpu {
 constexpr int WARP = 32;
 constexpr int APL = 4;            // arcs per lane
 constexpr int WIN = WARP * APL;   // arcs per window
-constexpr int GMAX = 32;          // tokens per group (same symbol, same step): one per lane
 constexpr unsigned FULL = 0xffffffffu;
 
 // Window metadata, 32 bytes: two 16-byte loads.
@@ -51,8 +50,7 @@ struct Layout {
   int32_t* seg_state = nullptr;  // [nseg] dst (forward) / src (backward)
   int32_t* seg_pos = nullptr;    // [nseg] padded start position
   int32_t* seg_len = nullptr;    // [nseg] arcs in the segment
-  int32_t* fwin = nullptr;       // backward layout only: [P] forward window of each arc (-1 on padding)
-  int32_t* bwin = nullptr;       // forward layout only: [P] backward window of each arc (-1 on padding)
+  int32_t* xseg = nullptr;       // [P] segment of the other layout holding the same arc (-1 on padding)
   int64_t* sym_win = nullptr;    // [m+1]
   int64_t* sym_seg = nullptr;    // [m+1]
   int64_t* sym_lseg = nullptr;   // [m+1] long segments
@@ -76,11 +74,8 @@ struct fst_s {
   float* theta_s = nullptr;    // [Q]
   float* theta_f = nullptr;    // [Q]
   int32_t W = 0;               // 32-bit words of a state bitmap, ceil(Q / 32)
-  uint32_t* bm_start = nullptr;  // [W] states with a finite start weight
-  uint32_t* bm_final = nullptr;  // [W] states with a finite final weight
-  int32_t Ws = 0;                // words of a bitmap summary, ceil(W / 32)
-  uint32_t* sum_start = nullptr; // [Ws] bit i = word i of bm_start is nonzero
-  uint32_t* sum_final = nullptr; // [Ws]
+  int32_t* start_q = nullptr;  // [nstart] states with a finite start weight
+  int32_t nstart = 0;
   int32_t* olabel = nullptr;   // [A] by caller arc id
   int64_t* sym_arc = nullptr;  // [m+1] R offsets (device)
   int64_t* h_sym_arc = nullptr;

@@ -1,4 +1,4 @@
-// kernels.cuh -- launch arguments of the relaxation kernels (kernels.cu).
+// kernels.cuh -- launch arguments of the frontier kernels (kernels.cu).
 #pragma once
 
 #include <stdint.h>
@@ -9,151 +9,124 @@ namespace fstgpu {
 
 // Device view of one arc layout.
 struct LayoutView {
-  const int32_t* other;
-  const float* theta;
-  const double* theta64;
-  const WinMeta* win;
-  const int32_t* seg_state;
-  const int32_t* seg_pos;
-  const int64_t* sym_win;
-  const int64_t* sym_seg;
+  const int32_t* other;      // [P] gathered state: source (forward layout) or destination (backward)
+  const float* theta;        // [P]
+  const int32_t* arc_id;     // [P] caller arc id, -1 on padding
+  const int32_t* seg_state;  // [nseg] destination (forward) or source (backward)
+  const int32_t* seg_pos;    // [nseg] first padded position
+  const int32_t* seg_len;    // [nseg] arcs
+  const int64_t* sym_seg;    // [m+1] segments of each input symbol
+  const int32_t* xseg;       // [P] segment of the other layout holding the same arc
 };
 
 inline LayoutView view_of(const Layout& L) {
-  return LayoutView{L.other, L.theta, L.theta64, L.win, L.seg_state, L.seg_pos, L.sym_win, L.sym_seg};
+  return LayoutView{L.other, L.theta, L.arc_id, L.seg_state, L.seg_pos, L.seg_len, L.sym_seg, L.xseg};
 }
 
-// Tokens of one wave: token p is position t (1-based) of wave-local string b.
+// The tokens of one input position t: slots slot0 .. slot0+n-1 of the
+// step list T.step_tok (tokens of a wave in step order).  Token p is
+// position t of wave-local string T.b[p]; the tokens of a string are
+// consecutive, so the previous position of token p is token p - 1.  The x_*
+// fields name another step whose pool entries the kernel also reads: the
+// previous position for the expand kernels, position t-2 for the backward
+// reduce (x_n = 0: none).
+struct StepView {
+  int32_t t;
+  int32_t n;
+  int32_t slot0;
+  int32_t x_t, x_n, x_slot0;
+  int32_t blocks;   // grid of the launch (work is a grid-stride loop)
+};
+
 struct TokenView {
+  const int32_t* step_tok;  // [N] token of each step slot
   const int32_t* sym;
   const int32_t* b;
-  const int32_t* t;
-  const int64_t* cbase;   // base of the token's per-segment storage (forward segments)
-  const int64_t* lbase;     // long-segment scratch slots (forward layout)
-  const int64_t* lbase_b;   // long-segment scratch slots (backward layout)
-  const int64_t* lwbase;    // long-window scratch slots (forward layout)
-  const int64_t* lwbase_b;  // long-window scratch slots (backward layout)
-  const int64_t* wbase;     // first window-liveness byte of the token (forward windows)
-  const int64_t* bwbase;    // first mark byte of the token in the backward windows
+  const int64_t* stf;   // forward staging offset of the token inside its step
+  const int64_t* stb;   // backward staging offset of the token inside its step
 };
 
-// Work list of one step: items are (group, window-of-slice) pairs; a group
-// is up to GMAX tokens of the same step with the same symbol.
-struct WorkView {
-  int single;        // 1: one token (p0, sym0); the group arrays are unused
-  int32_t p0, sym0;
-  int32_t g0, g1;    // group range of this step
-  int64_t nitems;
-  const int32_t* grp_first;
-  const int32_t* grp_cnt;
-  const int32_t* grp_sym;
-  const int64_t* grp_item;  // item offset of each group inside its step (this layout)
-  const int32_t* sorted_tok;
-};
-
-// Per-wave state shared by the passes.
-struct WaveState {
+// State of one wave (or of one plain-method string).
+//
+// Frontiers: dense per string, two parity buffers, entries tagged with the
+// token that wrote them (a mismatching tag reads as -inf), so nothing is
+// cleared between positions and a fresh run epoch invalidates everything.
+//
+// Live pool: for every token, the states with a finite forward (Viterbi)
+// value at its position, with the backpointer (Viterbi) or the forward
+// segment and stored value (forward).  The last block of a step's expand
+// kernel hands out the pool ranges: the step's tokens get consecutive ranges
+// in step order, so one position's entries are one flat range that the next
+// kernels split evenly over warps, whatever the tokens' frontier sizes.
+//
+// Staging: the segments a step has to reduce, per token, deduplicated with
+// a touch bitmap per string that the reduce kernel clears again.
+struct FrontierState {
   int32_t Q;
+  int32_t W;                         // 32-bit words of a touch bitmap
   const uint32_t* epoch;             // device: tags of this run start at *epoch
-  uint32_t tok0;                     // first global token of the wave: token p writes *epoch + tok0 + p
-  unsigned long long* alpha;         // [Bw][2][Q] tagged frontier
-  unsigned long long* beta;          // [Bw][2][Q]
-  int32_t* bp;                       // compact backpointers (forward segments)
-  float* rc;                         // compact forward values r_t (forward segments)
+  uint32_t tok0;                     // token p writes tag *epoch + tok0 + p
+  unsigned long long* alpha;         // [Bw][2][Q]
+  unsigned long long* beta;          // [Bw][2][Q] (null for Viterbi-only state)
+  uint32_t* touch;                   // [Bw][W], all zero between kernels
+  int32_t* stage;                    // staging of the current step
+  uint32_t* scnt_f;                  // [N] segments staged per token, forward direction
+  uint32_t* scnt_b;                  // [N] backward direction
+  int32_t* pool_q;                   // [cap] state (-1: the value turned out -inf)
+  int32_t* pool_x;                   // [cap] Viterbi: backpointer (forward position); forward: forward segment
+  float* pool_v;                     // [cap] forward value r_t (null for Viterbi)
+  int64_t* pool_base;                // [N] by token
+  int32_t* pool_cnt;                 // [N] by token
+  int64_t* slot_base;                // [N] by step slot: first pool entry of the slot's token
+  int64_t* bslot_base;               // [N] by step slot: first flat backward staging index
+  int64_t* step_rng;                 // [2 (T+2)]: pool entries [begin, end) of each position
+  int64_t* bstep_rng;                // [2 (T+2)]: flat backward staging indices [0, end) of each position
+  int64_t* pool_top;                 // [1] entries handed out in this run
+  int64_t pool_cap;
+  uint32_t* flags;                   // [2]: last-block counter, error bits (1 = pool full)
+  const float* theta_s;
+  const float* theta_f;
+  const int32_t* start_q;            // states with a finite start weight
+  int32_t nstart;
   uint32_t* mkey;                    // [N] forward step maxima (order keys)
   uint32_t* ekey;                    // [N] backward step maxima
   double* csum;                      // [N] C_t = sum_{s<=t} m_s
   double* esum;                      // [N] E_t
-  unsigned long long* skey;          // long-segment max keys
-  uint32_t* scnt;                    // long-segment arrival counters
-  float2* spart;                     // long-window (max, sum) partials
-  const float* theta_s;
-  const float* theta_f;
-  const double* logz;                // [Bw] (wave-local view)
+  const double* logz;                // [Bw]
   const float* gweight;              // [Bw] or null
-  int32_t* bw_n;                     // [Bw] string lengths
-  int64_t* bw_off;                   // [Bw] first token of each wave string
-  // Live-state bitmaps (bit q set = state q has a finite value): forward
-  // values at position t live in rotation t % 3 of abm, backward values at
-  // position t in rotation t % 3 of bbm; string b's bitmap of rotation r
-  // starts at r * bm_rot + b * W.  The driver clears a rotation before the
-  // launch that fills it.
-  uint32_t* abm;
-  uint32_t* bbm;
-  const uint32_t* bm_start;          // states with a finite start weight
-  const uint32_t* bm_final;          // states with a finite final weight
-  int32_t W;                         // 32-bit words per bitmap
-  int64_t bm_rot;
-  // Summaries of the bitmaps: bit i of a summary is set when word i of the
-  // bitmap is nonzero (one bit per 32 states).  Forward summaries are kept
-  // per token for the whole pass (tsum + p * Ws): the backward pass prunes
-  // its relaxation to sources whose forward value is finite.  Backward
-  // summaries rotate like the bitmaps.
-  uint32_t* tsum;
-  uint32_t* bsum;
-  const uint32_t* sum_start;
-  const uint32_t* sum_final;
-  int32_t Ws;                        // 32-bit words per summary
-  int64_t sum_rot;
-  // one byte per (token, forward window): 1 when the window wrote a finite
-  // forward value for that token (cleared before each forward pass)
-  uint8_t* wlive;
-  // Window marks, one byte per (token, forward window) in fin and per
-  // (token, backward window) in bin: set when the window holds an arc out of
-  // a state whose forward value at the previous position is finite.  A pass
-  // visits only marked windows of tokens past the first position; every
-  // unmarked window holds arcs from dead sources only.  bin may be null.
-  uint8_t* fin;
-  uint8_t* bin;
-  const int32_t* b_seg_state;
-  const int32_t* b_seg_pos;
-  const int32_t* b_seg_len;
-  const int64_t* b_sym_seg;
-  const int64_t* b_sym_win;
-  const int32_t* b_fwin;
-  const int64_t* f_sym_win;
-  // Backward marks, one byte per (token, backward window): set when the
-  // window holds an arc into a state whose backward value at that token's
-  // position is finite.  The backward pass visits a window of a token when
-  // its forward mark (bin) and backward mark (bmk) are set; at the first
-  // position only the backward mark, at the last only the forward mark.
-  uint8_t* bmk;
-  const int32_t* f_seg_state;
-  const int32_t* f_seg_pos;
-  const int32_t* f_seg_len;
-  const int64_t* f_sym_seg;
-  const int32_t* f_bwin;
+  const int32_t* bw_n;               // [Bw] string lengths
+  const int64_t* bw_off;             // [Bw] first token of each string
 };
 
+// Expected counts per forward padded arc position.
 struct CountView {
-  int batched;        // 0: Kahan float pair per arc; 1: double atomics
-  float* cnt;         // [P_bwd]
-  float* comp;        // [P_bwd]
-  double* cnt64;      // [P_bwd]
+  int batched;        // 0: Kahan float pair (one string); 1: double atomics
+  float* cnt;
+  float* comp;
+  double* cnt64;
 };
 
-// `grid` of the step launchers is the device's SM count.
-int launch_vit_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
-                    int grid, cudaStream_t s);
-int launch_fwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
-                    int grid, cudaStream_t s);
-// Restoring the stored forward values of one position into the dense
-// frontier (the forward layout's work list of that position; only strings
-// longer than t_bwd).  It rides along with a backward step whose frontier
-// reads touch the other parity buffer; W.nitems == 0 means none.
-struct ScatterJob {
-  LayoutView L;
-  WorkView W;
-  int32_t t_bwd;
-};
-
-int launch_bwd_step(const LayoutView& L, const TokenView& T, const WorkView& W, const WaveState& S,
-                    const CountView& C, const ScatterJob& J, int grid, cudaStream_t s);
-int launch_vit_final(const WaveState& S, int32_t Bw, float* scores, int32_t* qfinal, int32_t* status, cudaStream_t s);
-int launch_backtrace(const LayoutView& Lf, const int32_t* tok_sym, const int64_t* cbase, const WaveState& S,
-                     const int32_t* olabel_by_id, const int32_t* arc_id_fwd, int32_t Bw,
+// Expand (Viterbi and forward): every live state of the previous position
+// stages the forward segments its arcs on the step's symbol lead to.
+int launch_expand(const LayoutView& Lb, const TokenView& T, const StepView& V, const FrontierState& S, cudaStream_t s);
+// Reduce: each staged forward segment becomes one frontier entry.
+int launch_vit_reduce(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,
+                      cudaStream_t s);
+int launch_fwd_reduce(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,
+                      cudaStream_t s);
+// Backward expand: posteriors of the arcs into the live states of position
+// t and staging of the sources whose backward value at t-1 is needed.
+int launch_bwd_expand(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,
+                      const CountView& C, cudaStream_t s);
+// Backward reduce: backward values of the staged sources; also restores the
+// forward values of position t-2 for the next backward expand.
+int launch_bwd_reduce(const LayoutView& Lb, const TokenView& T, const StepView& V, const FrontierState& S,
+                      cudaStream_t s);
+int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t* qfinal, int32_t* status,
+                     cudaStream_t s);
+int launch_backtrace(const LayoutView& Lf, const FrontierState& S, const int32_t* olabel_by_id, int32_t Bw,
                      const int32_t* qfinal, int32_t* paths, int32_t* olabels, cudaStream_t s);
-int launch_fb_final(const WaveState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s);
-int launch_counts_out(const int32_t* arc_id_bwd, int64_t P, const CountView& C, float* out, cudaStream_t s);
+int launch_fb_final(const FrontierState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s);
+int launch_counts_out(const int32_t* arc_id_fwd, int64_t P, const CountView& C, float* out, cudaStream_t s);
 
 }  // namespace fstgpu

@@ -71,24 +71,15 @@ struct Carver {
   }
 };
 
-// Token tables of one string: position t, compact backpointer base (prefix
-// sum of destination segments per symbol).  One thread; n is at most a few
-// thousand here.
-__global__ void k_noalloc_tokens(const int32_t* __restrict__ ids, int32_t n, const int64_t* __restrict__ sym_seg,
-                                 const int64_t* __restrict__ sym_win, int32_t* __restrict__ tok_t,
-                                 int64_t* __restrict__ cbase, int64_t* __restrict__ wbase,
-                                 uint32_t* __restrict__ epoch) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  int64_t acc = 0, wacc = 0;
-  for (int32_t i = 0; i < n; ++i) {
-    tok_t[i] = i + 1;
-    cbase[i] = acc;
-    wbase[i] = wacc;
-    acc += sym_seg[ids[i] + 1] - sym_seg[ids[i]];
-    wacc += sym_win[ids[i] + 1] - sym_win[ids[i]];
+// Tags of this call are 1 + token (the cleared frontier holds tag 0); the
+// step list is the identity (token t-1 is the only slot of position t).
+__global__ void k_noalloc_epoch(uint32_t* __restrict__ epoch, int32_t* __restrict__ iota, int32_t n) {
+  const int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i == 0) {
+    epoch[0] = 1u;
+    epoch[1] = 0u;
   }
-  epoch[0] = 1u;  // tags of this call are 1 + position; the cleared frontier holds tag 0
-  epoch[1] = 0u;
+  if (i < n) iota[i] = i;
 }
 
 }  // namespace
@@ -101,21 +92,20 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   }
   cudaStream_t s = (cudaStream_t)stream;
   // sizes first, from host data only
-  int64_t store = 0, max_lseg = 0, nwins = 0;
+  int64_t pool = 0, dmax = 1;
   for (int32_t i = 0; i < n; ++i) {
     if (ids[i] < 0 || ids[i] >= f->m) {
       set_error("fst_viterbi_noalloc: symbol %d at position %d is outside [0, %d)", ids[i], i, f->m);
       return FST_ERR_INVALID_ARG;
     }
-    store += f->fwd.h_sym_seg[ids[i] + 1] - f->fwd.h_sym_seg[ids[i]];
-    nwins += f->fwd.h_sym_win[ids[i] + 1] - f->fwd.h_sym_win[ids[i]];
+    const int64_t D = f->fwd.h_sym_seg[ids[i] + 1] - f->fwd.h_sym_seg[ids[i]];
+    pool += D;
+    dmax = std::max(dmax, D);
   }
-  for (int32_t a = 0; a < f->m; ++a)
-    max_lseg = std::max<int64_t>(max_lseg, f->fwd.h_sym_lseg[a + 1] - f->fwd.h_sym_lseg[a]);
-  const int64_t Q = f->Q, W = f->W;
+  const int64_t Q = f->Q, W = f->W, nn = std::max(n, 1);
   auto rnd = [](int64_t bytes) { return ((bytes > 0 ? bytes : 1) + 255) & ~(int64_t)255; };
-  const int64_t need = rnd(2 * Q * 8) + rnd(3 * W * 4) + rnd((int64_t)n * f->Ws * 4) + rnd(nwins) + rnd((int64_t)n * 8) + 3 * rnd((int64_t)n * 4) + 2 * rnd((int64_t)n * 8) +
-                       rnd(store * 4) + rnd(max_lseg * 8) + rnd(max_lseg * 4) + 5 * rnd(8) + rnd(4) + rnd(8);
+  const int64_t need = rnd(2 * Q * 8) + rnd(W * 4) + 5 * rnd(nn * 4) + 3 * rnd(nn * 8) + rnd(dmax * 4) +
+                       2 * rnd(pool * 4) + rnd(2 * (nn + 2) * 8) + 6 * rnd(8);
   if (need > (int64_t)NOALLOC_SCRATCH_BYTES) {
     set_error("fst_viterbi_noalloc: this string needs %lld bytes of working memory, beyond the fixed %llu bytes "
               "(shorter strings or fewer states fit; fst_viterbi has no such limit)",
@@ -127,18 +117,21 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   if (rc) return rc;
   Carver c{(unsigned char*)base};
   unsigned long long* alpha = c.take<unsigned long long>(2 * Q);
-  uint32_t* abm = c.take<uint32_t>(3 * W);
-  uint32_t* tsum = c.take<uint32_t>((int64_t)n * f->Ws);
-  int32_t* tok_sym = c.take<int32_t>(n);
-  int32_t* tok_b = c.take<int32_t>(n);
-  int32_t* tok_t = c.take<int32_t>(n);
-  int64_t* cbase = c.take<int64_t>(n);
-  int64_t* zero64 = c.take<int64_t>(n);
-  int64_t* wbase = c.take<int64_t>(n);
-  uint8_t* fin = c.take<uint8_t>(nwins);
-  int32_t* bp = c.take<int32_t>(store);
-  unsigned long long* skey = c.take<unsigned long long>(max_lseg);
-  uint32_t* scnt = c.take<uint32_t>(max_lseg);
+  uint32_t* touch = c.take<uint32_t>(W);
+  int32_t* tok_sym = c.take<int32_t>(nn);
+  int32_t* tok_b = c.take<int32_t>(nn);
+  int32_t* iota = c.take<int32_t>(nn);
+  int64_t* slot_base = c.take<int64_t>(nn);
+  int64_t* step_rng = c.take<int64_t>(2 * (nn + 2));
+  uint32_t* scnt_f = c.take<uint32_t>(nn);
+  int32_t* pool_cnt = c.take<int32_t>(nn);
+  int64_t* zero64 = c.take<int64_t>(nn);
+  int64_t* pool_base = c.take<int64_t>(nn);
+  int32_t* stage = c.take<int32_t>(dmax);
+  int32_t* pool_q = c.take<int32_t>(pool);
+  int32_t* pool_x = c.take<int32_t>(pool);
+  int64_t* pool_top = c.take<int64_t>(1);
+  uint32_t* flags = c.take<uint32_t>(2);
   uint32_t* epoch = c.take<uint32_t>(2);
   int32_t* qfinal = c.take<int32_t>(1);
   int32_t* bw_n = c.take<int32_t>(1);
@@ -146,67 +139,60 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   int32_t* status = c.take<int32_t>(1);
 
   // what must start at zero: the tagged frontier (tag 0 is never valid), the
-  // string index and scratch bases of every token, the long-segment slots
+  // touch bits, string index and staging offsets of every token, staging
+  // counts, the pool counter and the error flags
   FST_CUDA(cudaMemsetAsync(alpha, 0, (size_t)(2 * Q * 8), s));
-  FST_CUDA(cudaMemsetAsync(tok_b, 0, (size_t)std::max(n, 1) * 4, s));
-  FST_CUDA(cudaMemsetAsync(zero64, 0, (size_t)std::max(n, 1) * 8, s));
-  FST_CUDA(cudaMemsetAsync(skey, 0, (size_t)std::max<int64_t>(max_lseg, 1) * 8, s));
-  FST_CUDA(cudaMemsetAsync(scnt, 0, (size_t)std::max<int64_t>(max_lseg, 1) * 4, s));
+  FST_CUDA(cudaMemsetAsync(touch, 0, (size_t)W * 4, s));
+  FST_CUDA(cudaMemsetAsync(tok_b, 0, (size_t)nn * 4, s));
+  FST_CUDA(cudaMemsetAsync(scnt_f, 0, (size_t)nn * 4, s));
+  FST_CUDA(cudaMemsetAsync(zero64, 0, (size_t)nn * 8, s));
+  FST_CUDA(cudaMemsetAsync(pool_top, 0, 8, s));
+  FST_CUDA(cudaMemsetAsync(flags, 0, 8, s));
   FST_CUDA(cudaMemsetAsync(bw_off, 0, 8, s));
-  FST_CUDA(cudaMemsetAsync(tsum, 0, (size_t)std::max<int64_t>((int64_t)n * f->Ws, 1) * 4, s));
   if (n > 0) FST_CUDA(cudaMemcpyAsync(tok_sym, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   FST_CUDA(cudaMemcpyAsync(bw_n, &n, 4, cudaMemcpyHostToDevice, s));
-  FST_CUDA(cudaMemsetAsync(fin, 0, (size_t)std::max<int64_t>(nwins, 1), s));
-  k_noalloc_tokens<<<1, 1, 0, s>>>(tok_sym, n, f->fwd.sym_seg, f->fwd.sym_win, tok_t, cbase, wbase, epoch);
+  k_noalloc_epoch<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(epoch, iota, n);
   FST_CUDA(cudaGetLastError());
 
-  WaveState S;
+  FrontierState S;
   memset(&S, 0, sizeof(S));
   S.Q = f->Q;
+  S.W = f->W;
   S.epoch = epoch;
   S.tok0 = 0;
   S.alpha = alpha;
-  S.bp = bp;
-  S.skey = skey;
-  S.scnt = scnt;
+  S.touch = touch;
+  S.stage = stage;
+  S.scnt_f = scnt_f;
+  S.pool_q = pool_q;
+  S.pool_x = pool_x;
+  S.pool_base = pool_base;
+  S.pool_cnt = pool_cnt;
+  S.slot_base = slot_base;
+  S.step_rng = step_rng;
+  S.pool_top = pool_top;
+  S.pool_cap = pool;
+  S.flags = flags;
   S.theta_s = f->theta_s;
   S.theta_f = f->theta_f;
+  S.start_q = f->start_q;
+  S.nstart = f->nstart;
   S.bw_n = bw_n;
   S.bw_off = bw_off;
-  S.abm = abm;
-  S.bm_start = f->bm_start;
-  S.bm_final = f->bm_final;
-  S.W = f->W;
-  S.bm_rot = f->W;
-  S.tsum = tsum;
-  S.fin = fin;
-  S.bin = nullptr;
-  S.b_seg_state = f->bwd.seg_state;
-  S.b_seg_pos = f->bwd.seg_pos;
-  S.b_seg_len = f->bwd.seg_len;
-  S.b_sym_seg = f->bwd.sym_seg;
-  S.b_sym_win = f->bwd.sym_win;
-  S.b_fwin = f->bwd.fwin;
-  S.f_sym_win = f->fwd.sym_win;
-  S.sum_start = f->sum_start;
-  S.sum_final = f->sum_final;
-  S.Ws = f->Ws;
-  S.sum_rot = f->Ws;
-  const TokenView T{tok_sym, tok_b, tok_t, cbase, zero64, zero64, zero64, zero64, wbase, zero64};
-  const LayoutView Lf = view_of(f->fwd);
+  const TokenView T{iota, tok_sym, tok_b, zero64, zero64};
+  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
   for (int32_t t = 1; t <= n; ++t) {
-    const int32_t a = ids[t - 1];
-    WorkView V;
-    memset(&V, 0, sizeof(V));
-    V.single = 1;
-    V.p0 = t - 1;
-    V.sym0 = a;
-    V.nitems = f->fwd.h_sym_win[a + 1] - f->fwd.h_sym_win[a];
-    FST_CUDA(cudaMemsetAsync(abm + (int64_t)(t % 3) * W, 0, (size_t)W * 4, s));
-    if ((rc = launch_vit_step(Lf, T, V, S, f->num_sms, s))) return rc;
+    StepView V;
+    V.t = t;
+    V.n = 1;
+    V.slot0 = t - 1;
+    V.x_t = t - 1;
+    V.x_n = t > 1 ? 1 : 0;
+    V.x_slot0 = t > 1 ? t - 2 : 0;
+    V.blocks = f->num_sms * 4;
+    if ((rc = launch_expand(Lb, T, V, S, s)) || (rc = launch_vit_reduce(Lf, T, V, S, s))) return rc;
   }
   if ((rc = launch_vit_final(S, 1, d_score, qfinal, status, s))) return rc;
-  if ((rc = launch_backtrace(Lf, tok_sym, cbase, S, f->olabel, f->fwd.arc_id, 1, qfinal, d_path, d_olabels, s)))
-    return rc;
+  if ((rc = launch_backtrace(Lf, S, f->olabel, 1, qfinal, d_path, d_olabels, s))) return rc;
   return FST_OK;
 }

@@ -2,12 +2,12 @@
 //
 // The paper decodes one string at a time and launches one kernel per input
 // position (Sec. 5; Sec. 7 times 100 sentences one after another).  A plan
-// instead advances every string of a wave by one position per launch.  The
-// work list of position t is built on the device once per plan: the tokens
-// of position t are sorted by symbol and cut into groups of up to GMAX
-// tokens with the same symbol, and every (group, window of the symbol's
-// slice) pair is one warp-sized work item; a warp loads the window's arcs
-// once and relaxes them for every token of its group.
+// instead advances every string of a wave by one position per launch pair
+// (expand, reduce; kernels.cu): the tokens of position t are all the
+// strings' t-th symbols, listed once per plan.  The plan also fixes, per
+// token, where its staged segments go inside the step's staging buffer, and
+// holds the dense frontiers, the live pool and the per-token scalars.
+// Strings are split into waves whose memory fits a budget.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -25,128 +25,16 @@ namespace {
 constexpr int TB = 256;
 inline unsigned nblk(int64_t n, int tb = TB) { return (unsigned)std::max<int64_t>(1, (n + tb - 1) / tb); }
 
-inline int bits_for(int64_t maxval) {
-  int b = 0;
-  while (b < 63 && ((int64_t)1 << b) <= maxval) ++b;
-  return b;
-}
+// live-pool entries reserved per token (the pool never exceeds the sum of
+// the tokens' destination-segment counts, its exact bound)
+constexpr int64_t POOL_PER_TOKEN = 256;
+// approximate device bytes per token of a wave (token tables, staging
+// counts, pool ranges, step maxima and running sums)
+constexpr int64_t TOKEN_BYTES = 80;
 
 __global__ void k_check_ids(const int32_t* __restrict__ ids, int64_t n, int32_t m, unsigned int* __restrict__ err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && (ids[i] < 0 || ids[i] >= m)) atomicOr(err, 1u);
-}
-
-__global__ void k_tok_nseg(const int32_t* __restrict__ ids, int64_t n, const int64_t* __restrict__ sym_seg,
-                           int64_t* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = sym_seg[ids[i] + 1] - sym_seg[ids[i]];
-}
-
-// one warp per string of the wave
-__global__ void k_tok_info(const int32_t* __restrict__ ids, const int64_t* __restrict__ bw_off,
-                           const int32_t* __restrict__ bw_n, int32_t Bw, int32_t* __restrict__ tok_sym,
-                           int32_t* __restrict__ tok_b, int32_t* __restrict__ tok_t) {
-  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (b >= Bw) return;
-  const int64_t off = bw_off[b];
-  for (int32_t i = lane; i < bw_n[b]; i += 32) {
-    tok_sym[off + i] = ids[off + i];
-    tok_b[off + i] = (int32_t)b;
-    tok_t[off + i] = i + 1;
-  }
-}
-
-__global__ void k_tok_counts(const int32_t* __restrict__ sym, int64_t n, const int64_t* __restrict__ f_seg,
-                             const int64_t* __restrict__ f_lseg, const int64_t* __restrict__ f_lwin,
-                             const int64_t* __restrict__ b_lseg, const int64_t* __restrict__ b_lwin,
-                             const int64_t* __restrict__ f_win, int64_t* __restrict__ c0,
-                             int64_t* __restrict__ c1, int64_t* __restrict__ c2, int64_t* __restrict__ c3,
-                             int64_t* __restrict__ c4, int64_t* __restrict__ c5,
-                             const int64_t* __restrict__ b_win, int64_t* __restrict__ c6) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int32_t a = sym[i];
-  c0[i] = f_seg[a + 1] - f_seg[a];
-  c1[i] = f_lseg[a + 1] - f_lseg[a];
-  c2[i] = f_lwin[a + 1] - f_lwin[a];
-  c3[i] = b_lseg[a + 1] - b_lseg[a];
-  c4[i] = b_lwin[a + 1] - b_lwin[a];
-  c5[i] = f_win[a + 1] - f_win[a];
-  c6[i] = b_win[a + 1] - b_win[a];
-}
-
-__global__ void k_tok_keys(const int32_t* __restrict__ sym, const int32_t* __restrict__ t, int64_t n, int sbits,
-                           uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  keys[i] = ((uint64_t)(uint32_t)t[i] << sbits) | (uint64_t)(uint32_t)sym[i];
-  vals[i] = (uint32_t)i;
-}
-
-__global__ void k_run_heads(const uint64_t* __restrict__ keys, int64_t n, int64_t* __restrict__ rh) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) rh[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
-}
-
-__global__ void k_run_first(const int64_t* __restrict__ rh, const int64_t* __restrict__ rx, int64_t n,
-                            int64_t* __restrict__ run_first) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && rh[i]) run_first[rx[i]] = i;
-}
-
-// group heads: run starts and every GMAX-th token inside a run
-__global__ void k_grp_heads(const int64_t* __restrict__ rh, const int64_t* __restrict__ rx,
-                            const int64_t* __restrict__ run_first, int64_t n, int gmax, int64_t* __restrict__ gh) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t r = rx[i] + rh[i] - 1;
-  gh[i] = ((i - run_first[r]) % gmax == 0) ? 1 : 0;
-}
-
-__global__ void k_grp_fill(const uint64_t* __restrict__ keys, const int64_t* __restrict__ gh,
-                           const int64_t* __restrict__ gx, int64_t n, int sbits, int32_t* __restrict__ grp_first,
-                           int32_t* __restrict__ grp_sym, int32_t* __restrict__ grp_t) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || !gh[i]) return;
-  const int64_t g = gx[i];
-  grp_first[g] = (int32_t)i;
-  grp_sym[g] = (int32_t)(keys[i] & (((uint64_t)1 << sbits) - 1));
-  grp_t[g] = (int32_t)(keys[i] >> sbits);
-}
-
-__global__ void k_grp_cnt_win(const int32_t* __restrict__ grp_first, const int32_t* __restrict__ grp_sym, int64_t G,
-                              int64_t n, const int64_t* __restrict__ fwin, const int64_t* __restrict__ bwin,
-                              int32_t* __restrict__ grp_cnt, int64_t* __restrict__ wf, int64_t* __restrict__ wb) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
-  const int64_t end = (g + 1 < G) ? grp_first[g + 1] : n;
-  grp_cnt[g] = (int32_t)(end - grp_first[g]);
-  const int32_t a = grp_sym[g];
-  wf[g] = fwin[a + 1] - fwin[a];
-  wb[g] = bwin[a + 1] - bwin[a];
-}
-
-// step_g0[t] = first group with position >= t, for t in [0, tmax+1]
-__global__ void k_step_g0(const int32_t* __restrict__ grp_t, int64_t G, int32_t tmax, int32_t* __restrict__ step_g0) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t > tmax + 1) return;
-  int64_t lo = 0, hi = G;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (grp_t[mid] < t) lo = mid + 1; else hi = mid;
-  }
-  step_g0[t] = (int32_t)lo;
-}
-
-__global__ void k_grp_item_local(const int32_t* __restrict__ grp_t, const int32_t* __restrict__ step_g0,
-                                 const int64_t* __restrict__ gif, const int64_t* __restrict__ gib, int64_t G,
-                                 int64_t* __restrict__ lf, int64_t* __restrict__ lb) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
-  const int32_t g0 = step_g0[grp_t[g]];
-  lf[g] = gif[g] - gif[g0];
-  lb[g] = gib[g] - gib[g0];
 }
 
 // Run epochs: epoch[0] is the first tag of the current run and epoch[1]
@@ -173,23 +61,16 @@ __global__ void k_clear_if(const uint32_t* clear, unsigned long long* p, int64_t
 
 struct Wave {
   int32_t b0 = 0, b1 = 0, Bw = 0, tmax = 0;
-  int64_t tok0 = 0, ntok = 0, store = 0, G = 0, nwins = 0, nwins_b = 0;
-  int64_t nlseg = 0, nlwin = 0;  // scratch slots needed (max of both layouts)
-  int32_t *tok_sym = nullptr, *tok_b = nullptr, *tok_t = nullptr;
-  int64_t *cbase = nullptr, *lbase_f = nullptr, *lwbase_f = nullptr, *lbase_b = nullptr, *lwbase_b = nullptr;
-  int64_t* wbase = nullptr;
-  int64_t* bwbase = nullptr;
-  int32_t *sorted_tok = nullptr, *grp_first = nullptr, *grp_cnt = nullptr, *grp_sym = nullptr;
-  int64_t *grp_item_f = nullptr, *grp_item_b = nullptr;
+  int64_t tok0 = 0, ntok = 0;
+  int64_t stage = 0;       // staging entries the largest step needs
+  int64_t pool_bound = 0;  // sum of the tokens' destination-segment counts
+  int32_t *tok_sym = nullptr, *tok_b = nullptr, *step_tok = nullptr;
+  int64_t *stf = nullptr, *stb = nullptr;
   int32_t* bw_n = nullptr;
   int64_t* bw_off = nullptr;
-  std::vector<int32_t> step_g0;        // [tmax + 2]
-  std::vector<int64_t> items_f, items_b;  // [tmax + 1]
+  std::vector<int32_t> step0;  // [tmax + 2]: tokens of position t are step_tok[step0[t] .. step0[t+1])
   void release() {
-    dfree(tok_sym); dfree(tok_b); dfree(tok_t); dfree(cbase); dfree(lbase_f); dfree(lwbase_f); dfree(lbase_b);
-    dfree(wbase); dfree(bwbase);
-    dfree(lwbase_b); dfree(sorted_tok); dfree(grp_first); dfree(grp_cnt); dfree(grp_sym); dfree(grp_item_f);
-    dfree(grp_item_b); dfree(bw_n); dfree(bw_off);
+    dfree(tok_sym); dfree(tok_b); dfree(step_tok); dfree(stf); dfree(stb); dfree(bw_n); dfree(bw_off);
   }
 };
 
@@ -200,27 +81,27 @@ struct fst_plan_s {
   int32_t B = 0, flags = 0, max_len = 0;
   int64_t N = 0, relax = 0, bytes = 0;
   std::vector<Wave> waves;
-  int32_t* ids = nullptr;
+  bool want_vit = true, want_fb = true;
   // shared per-wave buffers (sized for the largest wave)
   unsigned long long *alpha = nullptr, *beta = nullptr;
-  int32_t* bp = nullptr;
-  float* rc = nullptr;
+  uint32_t* touch = nullptr;
+  int32_t* stage = nullptr;
+  uint32_t *scnt_f = nullptr, *scnt_b = nullptr;
+  int32_t *pool_q = nullptr, *pool_x = nullptr;
+  float* pool_v = nullptr;
+  int64_t* pool_base = nullptr;
+  int32_t* pool_cnt = nullptr;
+  int64_t *slot_base = nullptr, *bslot_base = nullptr, *step_rng = nullptr, *bstep_rng = nullptr;
+  int64_t* pool_top = nullptr;
+  int64_t pool_cap = 0;
+  uint32_t* flags_d = nullptr;
   uint32_t *mkey = nullptr, *ekey = nullptr;
   double *csum = nullptr, *esum = nullptr;
-  unsigned long long* skey = nullptr;
-  uint32_t* scnt = nullptr;
-  float2* spart = nullptr;
   int32_t* qfinal = nullptr;
   double* cnt64 = nullptr;
   double* logz = nullptr;
   uint32_t *epoch = nullptr, *clear = nullptr;
-  uint32_t *abm = nullptr, *bbm = nullptr;  // [3][max_bw][W] live-state bitmaps
-  uint32_t *tsum = nullptr, *bsum = nullptr;  // forward summaries per token [max_ntok][Ws]; backward [3][max_bw][Ws]
-  uint8_t* wlive = nullptr;                 // per (token, forward window) liveness of the largest wave
-  uint8_t *fin = nullptr, *bin = nullptr;   // window marks (forward / backward windows)
-  uint8_t* bmk = nullptr;                   // backward marks (backward windows)
-  int64_t max_nwins = 0, max_nwins_b = 0;
-  int64_t max_bw = 0, max_ntok = 0, max_store = 0, max_lseg = 0, max_lwin = 0;
+  int64_t max_bw = 0, max_ntok = 0, max_stage = 0;
   bool forward_done = false;
   // optional per-launch CUDA events (fst_plan_profile)
   bool prof_on = false;
@@ -230,9 +111,11 @@ struct fst_plan_s {
   ~fst_plan_s() {
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (Wave& w : waves) w.release();
-    dfree(ids); dfree(alpha); dfree(beta); dfree(bp); dfree(rc); dfree(mkey); dfree(ekey); dfree(csum);
-    dfree(esum); dfree(skey); dfree(scnt); dfree(spart); dfree(qfinal); dfree(cnt64); dfree(logz);
-    dfree(epoch); dfree(clear); dfree(abm); dfree(bbm); dfree(tsum); dfree(bsum); dfree(wlive); dfree(fin); dfree(bin); dfree(bmk);
+    dfree(alpha); dfree(beta); dfree(touch); dfree(stage); dfree(scnt_f); dfree(scnt_b); dfree(pool_q);
+    dfree(pool_x); dfree(pool_v); dfree(pool_base); dfree(pool_cnt); dfree(pool_top); dfree(flags_d);
+    dfree(slot_base); dfree(bslot_base); dfree(step_rng); dfree(bstep_rng);
+    dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(qfinal); dfree(cnt64); dfree(logz); dfree(epoch);
+    dfree(clear);
   }
 };
 
@@ -271,202 +154,132 @@ int alloc_track(fst_plan_s* P, T** p, int64_t n) {
   return rc;
 }
 
-int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, cudaStream_t s) {
+template <class T>
+int upload(fst_plan_s* P, T** d, const std::vector<T>& h) {
+  int rc = alloc_track(P, d, (int64_t)h.size());
+  if (rc) return rc;
+  if (!h.empty()) FST_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FST_OK;
+}
+
+// Token tables of one wave, built on the host from the offsets and symbols.
+// Tokens of a string are consecutive (token p = position t of string b is
+// p = off_b + t - 1); the tokens of position t are listed string by string.
+int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, const std::vector<int32_t>& hid) {
   fst_s* f = P->fst;
   int rc;
   W.Bw = W.b1 - W.b0;
   W.tok0 = h_off[W.b0];
   W.ntok = h_off[W.b1] - W.tok0;
-  std::vector<int64_t> boff(std::max(W.Bw, 1));
-  std::vector<int32_t> bn(std::max(W.Bw, 1));
+  std::vector<int64_t> boff(W.Bw);
+  std::vector<int32_t> bn(W.Bw);
   W.tmax = 0;
   for (int32_t b = 0; b < W.Bw; ++b) {
     boff[b] = h_off[W.b0 + b] - W.tok0;
     bn[b] = (int32_t)(h_off[W.b0 + b + 1] - h_off[W.b0 + b]);
     W.tmax = std::max(W.tmax, bn[b]);
   }
-  const int64_t n = std::max<int64_t>(W.ntok, 1);
-  if ((rc = alloc_track(P, &W.bw_off, W.Bw)) || (rc = alloc_track(P, &W.bw_n, W.Bw)) ||
-      (rc = alloc_track(P, &W.tok_sym, n)) || (rc = alloc_track(P, &W.tok_b, n)) ||
-      (rc = alloc_track(P, &W.tok_t, n)) || (rc = alloc_track(P, &W.cbase, n + 1)) ||
-      (rc = alloc_track(P, &W.lbase_f, n + 1)) || (rc = alloc_track(P, &W.lwbase_f, n + 1)) ||
-      (rc = alloc_track(P, &W.lbase_b, n + 1)) || (rc = alloc_track(P, &W.lwbase_b, n + 1)) ||
-      (rc = alloc_track(P, &W.wbase, n + 1)) || (rc = alloc_track(P, &W.bwbase, n + 1)) ||
-      (rc = alloc_track(P, &W.sorted_tok, n)))
+  std::vector<int32_t> sym(W.ntok), tb(W.ntok), step_tok;
+  std::vector<int64_t> stf(W.ntok), stb(W.ntok);
+  step_tok.reserve(W.ntok);
+  for (int32_t b = 0; b < W.Bw; ++b)
+    for (int32_t i = 0; i < bn[b]; ++i) {
+      sym[boff[b] + i] = hid[W.tok0 + boff[b] + i];
+      tb[boff[b] + i] = b;
+    }
+  // strings sorted by length (descending) so that the tokens of position t
+  // are a prefix of that order: string b has a token at t iff n_b >= t
+  std::vector<int32_t> order(W.Bw);
+  for (int32_t b = 0; b < W.Bw; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return bn[x] > bn[y]; });
+  W.step0.assign(W.tmax + 2, 0);
+  W.stage = 0;
+  W.pool_bound = 0;
+  int32_t live = W.Bw;
+  for (int32_t t = 1; t <= W.tmax; ++t) {
+    while (live > 0 && bn[order[live - 1]] < t) --live;
+    W.step0[t] = (int32_t)step_tok.size();
+    int64_t accf = 0, accb = 0;
+    for (int32_t j = 0; j < live; ++j) {
+      const int64_t p = boff[order[j]] + t - 1;
+      const int32_t a = sym[p];
+      step_tok.push_back((int32_t)p);
+      stf[p] = accf;
+      stb[p] = accb;
+      const int64_t D = f->fwd.h_sym_seg[a + 1] - f->fwd.h_sym_seg[a];
+      accf += D;
+      accb += f->bwd.h_sym_seg[a + 1] - f->bwd.h_sym_seg[a];
+      W.pool_bound += D;
+    }
+    W.stage = std::max(W.stage, std::max(accf, accb));
+  }
+  W.step0[W.tmax + 1] = (int32_t)step_tok.size();
+  if ((rc = upload(P, &W.bw_off, boff)) || (rc = upload(P, &W.bw_n, bn)) || (rc = upload(P, &W.tok_sym, sym)) ||
+      (rc = upload(P, &W.tok_b, tb)) || (rc = upload(P, &W.step_tok, step_tok)) || (rc = upload(P, &W.stf, stf)) ||
+      (rc = upload(P, &W.stb, stb)))
     return rc;
-  FST_CUDA(cudaMemcpy(W.bw_off, boff.data(), (size_t)W.Bw * 8, cudaMemcpyHostToDevice));
-  FST_CUDA(cudaMemcpy(W.bw_n, bn.data(), (size_t)W.Bw * 4, cudaMemcpyHostToDevice));
-  if (W.Bw > 0)
-    k_tok_info<<<nblk((int64_t)W.Bw * 32), TB, 0, s>>>(P->ids + W.tok0, W.bw_off, W.bw_n, W.Bw, W.tok_sym, W.tok_b,
-                                                       W.tok_t);
-  // per-token storage and scratch bases
-  int64_t *c[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  for (auto& p : c)
-    if ((rc = dalloc(&p, n))) { for (auto& q : c) dfree(q); return rc; }
-  if (W.ntok > 0)
-    k_tok_counts<<<nblk(W.ntok), TB, 0, s>>>(W.tok_sym, W.ntok, f->fwd.sym_seg, f->fwd.sym_lseg, f->fwd.sym_lwin,
-                                             f->bwd.sym_lseg, f->bwd.sym_lwin, f->fwd.sym_win, c[0], c[1], c[2], c[3],
-                                             c[4], c[5], f->bwd.sym_win, c[6]);
-  int64_t tot[7] = {0, 0, 0, 0, 0, 0, 0};
-  int64_t* outs[7] = {W.cbase, W.lbase_f, W.lwbase_f, W.lbase_b, W.lwbase_b, W.wbase, W.bwbase};
-  for (int i = 0; i < 7 && !rc; ++i) rc = exclusive_scan_i64(c[i], outs[i], W.ntok, &tot[i], s);
-  for (auto& q : c) dfree(q);
-  if (rc) return rc;
-  W.store = tot[0];
-  W.nwins = tot[5];
-  W.nwins_b = tot[6];
-  W.nlseg = std::max(tot[1], tot[3]);
-  W.nlwin = std::max(tot[2], tot[4]);
-  // sort tokens by (position, symbol) and cut groups
-  uint64_t* keys = nullptr;
-  int64_t *rh = nullptr, *rx = nullptr, *rfirst = nullptr, *gh = nullptr, *gx = nullptr;
-  int32_t* grp_t = nullptr;
-  int64_t *wf = nullptr, *wb = nullptr, *gif = nullptr, *gib = nullptr;
-  int32_t* d_step_g0 = nullptr;
-  auto cleanup = [&]() {
-    dfree(keys); dfree(rh); dfree(rx); dfree(rfirst); dfree(gh); dfree(gx); dfree(grp_t); dfree(wf); dfree(wb);
-    dfree(gif); dfree(gib); dfree(d_step_g0);
-  };
-  do {
-    const int sbits = bits_for(f->m > 1 ? f->m - 1 : 1);
-    const int tbits = bits_for(W.tmax + 1);
-    if ((rc = dalloc(&keys, n)) || (rc = dalloc(&rh, n)) || (rc = dalloc(&rx, n + 1)) ||
-        (rc = dalloc(&rfirst, n + 1)) || (rc = dalloc(&gh, n)) || (rc = dalloc(&gx, n + 1)))
-      break;
-    if (W.ntok > 0) {
-      k_tok_keys<<<nblk(W.ntok), TB, 0, s>>>(W.tok_sym, W.tok_t, W.ntok, sbits, keys, (uint32_t*)W.sorted_tok);
-      if ((rc = radix_sort_pairs(keys, (uint32_t*)W.sorted_tok, W.ntok, sbits + tbits, s))) break;
-      k_run_heads<<<nblk(W.ntok), TB, 0, s>>>(keys, W.ntok, rh);
-    }
-    int64_t nruns = 0;
-    if ((rc = exclusive_scan_i64(rh, rx, W.ntok, &nruns, s))) break;
-    if (W.ntok > 0) {
-      k_run_first<<<nblk(W.ntok), TB, 0, s>>>(rh, rx, W.ntok, rfirst);
-      k_grp_heads<<<nblk(W.ntok), TB, 0, s>>>(rh, rx, rfirst, W.ntok, GMAX, gh);
-    }
-    int64_t G = 0;
-    if ((rc = exclusive_scan_i64(gh, gx, W.ntok, &G, s))) break;
-    W.G = G;
-    if ((rc = alloc_track(P, &W.grp_first, G)) || (rc = alloc_track(P, &W.grp_cnt, G)) ||
-        (rc = alloc_track(P, &W.grp_sym, G)) || (rc = alloc_track(P, &W.grp_item_f, G)) ||
-        (rc = alloc_track(P, &W.grp_item_b, G)) || (rc = dalloc(&grp_t, G)) || (rc = dalloc(&wf, G)) ||
-        (rc = dalloc(&wb, G)) || (rc = dalloc(&gif, G + 1)) || (rc = dalloc(&gib, G + 1)) ||
-        (rc = dalloc(&d_step_g0, (int64_t)W.tmax + 2)))
-      break;
-    if (W.ntok > 0) {
-      k_grp_fill<<<nblk(W.ntok), TB, 0, s>>>(keys, gh, gx, W.ntok, sbits, W.grp_first, W.grp_sym, grp_t);
-      k_grp_cnt_win<<<nblk(G), TB, 0, s>>>(W.grp_first, W.grp_sym, G, W.ntok, f->fwd.sym_win, f->bwd.sym_win,
-                                           W.grp_cnt, wf, wb);
-    }
-    int64_t totf = 0, totb = 0;
-    if ((rc = exclusive_scan_i64(wf, gif, G, &totf, s))) break;
-    if ((rc = exclusive_scan_i64(wb, gib, G, &totb, s))) break;
-    FST_CUDA(cudaMemcpy(gif + G, &totf, 8, cudaMemcpyHostToDevice));
-    FST_CUDA(cudaMemcpy(gib + G, &totb, 8, cudaMemcpyHostToDevice));
-    k_step_g0<<<nblk((int64_t)W.tmax + 2), TB, 0, s>>>(grp_t, G, W.tmax, d_step_g0);
-    if (G > 0) k_grp_item_local<<<nblk(G), TB, 0, s>>>(grp_t, d_step_g0, gif, gib, G, W.grp_item_f, W.grp_item_b);
-    FST_CUDA(cudaGetLastError());
-    W.step_g0.assign(W.tmax + 2, 0);
-    FST_CUDA(cudaMemcpy(W.step_g0.data(), d_step_g0, (size_t)(W.tmax + 2) * 4, cudaMemcpyDeviceToHost));
-    std::vector<int64_t> hf(G + 1), hb(G + 1);
-    FST_CUDA(cudaMemcpy(hf.data(), gif, (size_t)(G + 1) * 8, cudaMemcpyDeviceToHost));
-    FST_CUDA(cudaMemcpy(hb.data(), gib, (size_t)(G + 1) * 8, cudaMemcpyDeviceToHost));
-    W.items_f.assign(W.tmax + 1, 0);
-    W.items_b.assign(W.tmax + 1, 0);
-    for (int32_t t = 1; t <= W.tmax; ++t) {
-      W.items_f[t] = hf[W.step_g0[t + 1]] - hf[W.step_g0[t]];
-      W.items_b[t] = hb[W.step_g0[t + 1]] - hb[W.step_g0[t]];
-    }
-  } while (0);
-  cleanup();
-  return rc;
+  return FST_OK;
 }
 
-WaveState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
+FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   fst_s* f = P->fst;
-  WaveState S;
+  FrontierState S;
   memset(&S, 0, sizeof(S));
   S.Q = f->Q;
+  S.W = f->W;
   S.epoch = P->epoch;
   S.tok0 = (uint32_t)W.tok0;
   S.alpha = P->alpha;
   S.beta = P->beta;
-  S.bp = P->bp;
-  S.rc = P->rc;
+  S.touch = P->touch;
+  S.stage = P->stage;
+  S.scnt_f = P->scnt_f;
+  S.scnt_b = P->scnt_b;
+  S.pool_q = P->pool_q;
+  S.pool_x = P->pool_x;
+  S.pool_v = P->pool_v;
+  S.pool_base = P->pool_base;
+  S.pool_cnt = P->pool_cnt;
+  S.slot_base = P->slot_base;
+  S.bslot_base = P->bslot_base;
+  S.step_rng = P->step_rng;
+  S.bstep_rng = P->bstep_rng;
+  S.pool_top = P->pool_top;
+  S.pool_cap = P->pool_cap;
+  S.flags = P->flags_d;
+  S.theta_s = f->theta_s;
+  S.theta_f = f->theta_f;
+  S.start_q = f->start_q;
+  S.nstart = f->nstart;
   S.mkey = P->mkey;
   S.ekey = P->ekey;
   S.csum = P->csum;
   S.esum = P->esum;
-  S.skey = P->skey;
-  S.scnt = P->scnt;
-  S.spart = P->spart;
-  S.theta_s = f->theta_s;
-  S.theta_f = f->theta_f;
   S.logz = P->logz + W.b0;
   S.gweight = gweight ? gweight + W.b0 : nullptr;
   S.bw_n = W.bw_n;
   S.bw_off = W.bw_off;
-  S.abm = P->abm;
-  S.bbm = P->bbm;
-  S.bm_start = f->bm_start;
-  S.bm_final = f->bm_final;
-  S.W = f->W;
-  S.bm_rot = P->max_bw * (int64_t)f->W;
-  S.wlive = P->wlive;
-  S.tsum = P->tsum;
-  S.bsum = P->bsum;
-  S.fin = P->fin;
-  S.bin = P->bin;
-  S.b_seg_state = f->bwd.seg_state;
-  S.b_seg_pos = f->bwd.seg_pos;
-  S.b_seg_len = f->bwd.seg_len;
-  S.b_sym_seg = f->bwd.sym_seg;
-  S.b_sym_win = f->bwd.sym_win;
-  S.b_fwin = f->bwd.fwin;
-  S.f_sym_win = f->fwd.sym_win;
-  S.bmk = P->bmk;
-  S.f_seg_state = f->fwd.seg_state;
-  S.f_seg_pos = f->fwd.seg_pos;
-  S.f_seg_len = f->fwd.seg_len;
-  S.f_sym_seg = f->fwd.sym_seg;
-  S.f_bwin = f->fwd.bwin;
-  S.sum_start = f->sum_start;
-  S.sum_final = f->sum_final;
-  S.Ws = f->Ws;
-  S.sum_rot = P->max_bw * (int64_t)f->Ws;
   return S;
 }
 
-// Clear rotation r of a [3][max_bw][words] bitmap (or summary) set before the
-// launch that fills it.
-int clear_rot(fst_plan_s* P, uint32_t* bm, int32_t r, int32_t words_per_string, cudaStream_t s) {
-  const int64_t words = P->max_bw * (int64_t)words_per_string;
-  FST_CUDA(cudaMemsetAsync(bm + (int64_t)r * words, 0, (size_t)std::max<int64_t>(words, 1) * 4, s));
-  return FST_OK;
-}
+TokenView wave_tokens(const Wave& W) { return TokenView{W.step_tok, W.tok_sym, W.tok_b, W.stf, W.stb}; }
 
-TokenView wave_tokens(const Wave& W) {
-  return TokenView{W.tok_sym, W.tok_b, W.tok_t, W.cbase, W.lbase_f, W.lbase_b, W.lwbase_f, W.lwbase_b, W.wbase,
-                   W.bwbase};
-}
-
-WorkView wave_work(const Wave& W, int32_t t, bool fwd) {
-  WorkView V;
-  memset(&V, 0, sizeof(V));
-  V.single = 0;
-  V.g0 = W.step_g0[t];
-  V.g1 = W.step_g0[t + 1];
-  V.nitems = fwd ? W.items_f[t] : W.items_b[t];
-  V.grp_first = W.grp_first;
-  V.grp_cnt = W.grp_cnt;
-  V.grp_sym = W.grp_sym;
-  V.grp_item = fwd ? W.grp_item_f : W.grp_item_b;
-  V.sorted_tok = W.sorted_tok;
+// Position t of a wave; x names position x_t (previous position for the
+// expand kernels, t-2 for the backward reduce).  The grid assumes about 64
+// live states per token and is capped at what is resident at once.
+StepView wave_step(const fst_plan_s* P, const Wave& W, int32_t t, int32_t x_t) {
+  StepView V;
+  V.t = t;
+  V.slot0 = W.step0[t];
+  V.n = W.step0[t + 1] - W.step0[t];
+  const bool hasx = x_t >= 1 && x_t <= W.tmax;
+  V.x_t = hasx ? x_t : 0;
+  V.x_slot0 = hasx ? W.step0[x_t] : 0;
+  V.x_n = hasx ? W.step0[x_t + 1] - W.step0[x_t] : 0;
+  const int64_t est = (int64_t)std::max(V.n, V.x_n) * 64;
+  V.blocks = (int32_t)std::min<int64_t>((int64_t)P->fst->num_sms * 8, std::max<int64_t>(1, (est + 255) / 256));
   return V;
 }
-
-// the launchers size step grids from the SM count and the kernel's occupancy
-int step_grid(const fst_s* f, int64_t) { return f->num_sms; }
 
 int run_begin(fst_plan_s* P, cudaStream_t s, bool fb) {
   const uint32_t span = (uint32_t)std::min<int64_t>(P->N + 1, 0x7fffffff);
@@ -474,52 +287,73 @@ int run_begin(fst_plan_s* P, cudaStream_t s, bool fb) {
   const int64_t na = P->max_bw * 2 * (int64_t)P->fst->Q;
   if (P->alpha) k_clear_if<<<nblk(na), TB, 0, s>>>(P->clear, P->alpha, na);
   if (fb && P->beta) k_clear_if<<<nblk(na), TB, 0, s>>>(P->clear, P->beta, na);
-  FST_CUDA(cudaMemsetAsync(P->skey, 0, (size_t)std::max<int64_t>(1, P->max_lseg) * 8, s));
-  FST_CUDA(cudaMemsetAsync(P->scnt, 0, (size_t)std::max<int64_t>(1, P->max_lseg) * 4, s));
+  // touch bits are left clear by every reduce; cleared here as well so that
+  // an interrupted run cannot leak into the next
+  FST_CUDA(cudaMemsetAsync(P->touch, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)P->fst->W) * 4, s));
   FST_CUDA(cudaGetLastError());
+  return FST_OK;
+}
+
+// State that starts every pass of a wave at zero.
+int wave_begin(fst_plan_s* P, const Wave& W, cudaStream_t s, bool fb) {
+  const size_t n4 = (size_t)std::max<int64_t>(1, W.ntok) * 4;
+  FST_CUDA(cudaMemsetAsync(P->scnt_f, 0, n4, s));
+  FST_CUDA(cudaMemsetAsync(P->pool_top, 0, 8, s));
+  FST_CUDA(cudaMemsetAsync(P->flags_d, 0, 8, s));
+  if (fb) {
+    FST_CUDA(cudaMemsetAsync(P->scnt_b, 0, n4, s));
+    FST_CUDA(cudaMemsetAsync(P->mkey, 0, n4, s));
+    FST_CUDA(cudaMemsetAsync(P->ekey, 0, n4, s));
+  }
+  return FST_OK;
+}
+
+int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_paths, int32_t* d_olabels,
+                     int32_t* d_status, cudaStream_t s) {
+  fst_s* f = P->fst;
+  int rc;
+  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
+  const TokenView T = wave_tokens(W);
+  const FrontierState S = wave_state(P, W, nullptr);
+  if ((rc = wave_begin(P, W, s, false))) return rc;
+  for (int32_t t = 1; t <= W.tmax; ++t) {
+    const StepView V = wave_step(P, W, t, t - 1);
+    PROF(FST_PROF_VIT_EXPAND, launch_expand(Lb, T, V, S, s));
+    PROF(FST_PROF_VIT_REDUCE, launch_vit_reduce(Lf, T, V, S, s));
+  }
+  PROF(FST_PROF_VIT_FINAL,
+       launch_vit_final(S, W.Bw, d_scores + W.b0, P->qfinal, d_status ? d_status + W.b0 : nullptr, s));
+  PROF(FST_PROF_BACKTRACE, launch_backtrace(Lf, S, f->olabel, W.Bw, P->qfinal, d_paths + W.tok0,
+                                            d_olabels ? d_olabels + W.tok0 : nullptr, s));
   return FST_OK;
 }
 
 int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_status) {
   fst_s* f = P->fst;
   int rc;
-  const LayoutView Lf = view_of(f->fwd);
+  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
   const TokenView T = wave_tokens(W);
-  const WaveState S = wave_state(P, W, nullptr);
-  FST_CUDA(cudaMemsetAsync(P->mkey, 0, (size_t)std::max<int64_t>(1, W.ntok) * 4, s));
-  FST_CUDA(cudaMemsetAsync(P->ekey, 0, (size_t)std::max<int64_t>(1, W.ntok) * 4, s));
-  FST_CUDA(cudaMemsetAsync(P->wlive, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
-  FST_CUDA(cudaMemsetAsync(P->tsum, 0, (size_t)std::max<int64_t>(1, W.ntok * (int64_t)f->Ws) * 4, s));
-  FST_CUDA(cudaMemsetAsync(P->fin, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
-  FST_CUDA(cudaMemsetAsync(P->bin, 0, (size_t)std::max<int64_t>(1, W.nwins_b), s));
-  FST_CUDA(cudaMemsetAsync(P->bmk, 0, (size_t)std::max<int64_t>(1, W.nwins_b), s));
+  const FrontierState S = wave_state(P, W, nullptr);
+  if ((rc = wave_begin(P, W, s, true))) return rc;
   for (int32_t t = 1; t <= W.tmax; ++t) {
-    const WorkView V = wave_work(W, t, true);
-    if ((rc = clear_rot(P, P->abm, t % 3, f->W, s))) return rc;
-    PROF(FST_PROF_FWD_STEP, launch_fwd_step(Lf, T, V, S, step_grid(f, V.nitems), s));
+    const StepView V = wave_step(P, W, t, t - 1);
+    PROF(FST_PROF_FWD_EXPAND, launch_expand(Lb, T, V, S, s));
+    PROF(FST_PROF_FWD_REDUCE, launch_fwd_reduce(Lf, T, V, S, s));
   }
-  PROF(FST_PROF_FB_FINAL, launch_fb_final(S, W.Bw, P->logz + W.b0,
-                                           d_status ? d_status + W.b0 : nullptr, s));
+  PROF(FST_PROF_FB_FINAL, launch_fb_final(S, W.Bw, P->logz + W.b0, d_status ? d_status + W.b0 : nullptr, s));
   return FST_OK;
 }
 
 int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cudaStream_t s) {
   fst_s* f = P->fst;
-  int rc;
   const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
   const TokenView T = wave_tokens(W);
-  const WaveState S = wave_state(P, W, d_weights);
+  const FrontierState S = wave_state(P, W, d_weights);
   const CountView C{1, nullptr, nullptr, P->cnt64};
   for (int32_t t = W.tmax; t >= 1; --t) {
-    // step t also restores alpha_{t-2} of the strings longer than t - 1
-    // (their buffer of that parity now holds alpha_t)
-    ScatterJob J{Lf, WorkView{}, t - 1};
-    if (t >= 3) J.W = wave_work(W, t - 2, true);
-    const WorkView V = wave_work(W, t, false);
-    if (t >= 2 && ((rc = clear_rot(P, P->bbm, (t - 1) % 3, f->W, s)) ||
-                   (rc = clear_rot(P, P->bsum, (t - 1) % 3, f->Ws, s))))
-      return rc;
-    PROF(FST_PROF_BWD_STEP, launch_bwd_step(Lb, T, V, S, C, J, step_grid(f, std::max(V.nitems, J.W.nitems)), s));
+    const StepView V = wave_step(P, W, t, t - 2);
+    PROF(FST_PROF_BWD_EXPAND, launch_bwd_expand(Lf, T, V, S, C, s));
+    if (t >= 2) PROF(FST_PROF_BWD_REDUCE, launch_bwd_reduce(Lb, T, V, S, s));
   }
   return FST_OK;
 }
@@ -527,8 +361,6 @@ int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cuda
 inline cudaStream_t as_stream(void* p) { return (cudaStream_t)p; }
 
 }  // namespace
-
-
 
 extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                                int64_t mem_budget_bytes, int32_t flags, void* stream, fst_plan_t** out) {
@@ -550,16 +382,17 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
   P->B = B;
   P->N = N;
   P->flags = flags;
+  P->want_vit = !(flags & FST_PLAN_NO_VITERBI);
+  P->want_fb = !(flags & FST_PLAN_NO_FB);
   int rc = FST_OK;
-  int64_t* tok_nseg = nullptr;
-  int64_t* tok_cum = nullptr;
   unsigned int* d_err = nullptr;
+  int32_t* d_ids_copy = nullptr;
   do {
-    if ((rc = alloc_track(P, &P->ids, N))) break;
-    if (N > 0) FST_CUDA(cudaMemcpyAsync(P->ids, d_ids, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
-    if ((rc = dalloc(&d_err, 1))) break;
+    // symbols: checked on the device, then read back for the host tables
+    if ((rc = dalloc(&d_ids_copy, N)) || (rc = dalloc(&d_err, 1))) break;
+    if (N > 0) FST_CUDA(cudaMemcpyAsync(d_ids_copy, d_ids, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
     if (cudaMemsetAsync(d_err, 0, 4, s) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset"); break; }
-    if (N > 0) k_check_ids<<<nblk(N), TB, 0, s>>>(P->ids, N, f->m, d_err);
+    if (N > 0) k_check_ids<<<nblk(N), TB, 0, s>>>(d_ids_copy, N, f->m, d_err);
     unsigned int e = 0;
     if (cudaMemcpyAsync(&e, d_err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -567,33 +400,19 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
       break;
     }
     if (e) { set_error("a symbol id is outside [0, %d)", f->m); rc = FST_ERR_INVALID_ARG; break; }
-    // per-string storage (forward segments per token), for the wave split
-    if ((rc = dalloc(&tok_nseg, std::max<int64_t>(N, 1))) || (rc = dalloc(&tok_cum, N + 1))) break;
-    if (N > 0) k_tok_nseg<<<nblk(N), TB, 0, s>>>(P->ids, N, f->fwd.sym_seg, tok_nseg);
-    int64_t tot = 0;
-    if ((rc = exclusive_scan_i64(tok_nseg, tok_cum, N, &tot, s))) break;
-    std::vector<int64_t> cum(N + 1);
-    if (N > 0) FST_CUDA(cudaMemcpy(cum.data(), tok_cum, (size_t)N * 8, cudaMemcpyDeviceToHost));
-    cum[N] = tot;
-    // relaxations of one pass
+    std::vector<int32_t> hid(N);
+    if (N > 0) FST_CUDA(cudaMemcpy(hid.data(), d_ids_copy, (size_t)N * 4, cudaMemcpyDeviceToHost));
+    // relaxations of one pass (the paper's definition: every arc of every slice)
     P->relax = 0;
-    {
-      std::vector<int32_t> hid(std::max<int64_t>(N, 1));
-      if (N > 0) FST_CUDA(cudaMemcpy(hid.data(), P->ids, (size_t)N * 4, cudaMemcpyDeviceToHost));
-      for (int64_t i = 0; i < N; ++i) P->relax += f->h_sym_arc[hid[i] + 1] - f->h_sym_arc[hid[i]];
-    }
-    // waves: consecutive strings whose storage fits the budget
-    const bool want_vit = !(flags & FST_PLAN_NO_VITERBI);
-    const bool want_fb = !(flags & FST_PLAN_NO_FB);
+    for (int64_t i = 0; i < N; ++i) P->relax += f->h_sym_arc[hid[i] + 1] - f->h_sym_arc[hid[i]];
+    // waves: consecutive strings whose memory fits the budget
     const int64_t budget = mem_budget_bytes > 0 ? mem_budget_bytes : ((int64_t)16 << 30);
-    const int64_t per_seg = (want_vit ? 4 : 0) + (want_fb ? 4 : 0);
-    const int64_t per_string = (int64_t)f->Q * 16 * (want_fb ? 2 : 1);
+    const int64_t per_string = (int64_t)f->Q * 16 * (P->want_fb ? 2 : 1) + (int64_t)f->W * 4 + 64;
+    const int64_t per_token = TOKEN_BYTES + POOL_PER_TOKEN * (P->want_fb ? 12 : 8);
     int32_t b0 = 0;
     int64_t acc = 0;
     for (int32_t b = 0; b <= B; ++b) {
-      const int64_t need = (b < B) ? (cum[h_off[b + 1]] - cum[h_off[b]]) * per_seg + per_string +
-                                         (h_off[b + 1] - h_off[b]) * 64
-                                   : 0;
+      const int64_t need = (b < B) ? per_string + (h_off[b + 1] - h_off[b]) * per_token : 0;
       if (b == B || (b > b0 && acc + need > budget)) {
         if (b > b0 || (b == B && B == 0)) {
           Wave w;
@@ -607,53 +426,51 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
       acc += need;
     }
     if ((flags & FST_PLAN_SINGLE_WAVE) && P->waves.size() > 1) {
-      set_error("the batch needs %d waves under a budget of %lld bytes", (int)P->waves.size(),
-                (long long)budget);
+      set_error("the batch needs %d waves under a budget of %lld bytes", (int)P->waves.size(), (long long)budget);
       rc = FST_ERR_OOM;
       break;
     }
     for (Wave& w : P->waves) {
-      if ((rc = build_wave(P, w, h_off, s))) break;
+      if ((rc = build_wave(P, w, h_off, hid))) break;
       P->max_bw = std::max<int64_t>(P->max_bw, w.Bw);
       P->max_ntok = std::max<int64_t>(P->max_ntok, w.ntok);
-      P->max_store = std::max<int64_t>(P->max_store, w.store);
-      P->max_lseg = std::max<int64_t>(P->max_lseg, w.nlseg);
-      P->max_lwin = std::max<int64_t>(P->max_lwin, w.nlwin);
+      P->max_stage = std::max(P->max_stage, w.stage);
       P->max_len = std::max(P->max_len, w.tmax);
-      P->max_nwins = std::max(P->max_nwins, w.nwins);
-      P->max_nwins_b = std::max(P->max_nwins_b, w.nwins_b);
+      // live pool: its exact bound when that is small, else the largest of
+      // POOL_PER_TOKEN entries per token, a quarter of the budget and 256 MiB
+      const int64_t ebytes = P->want_fb ? 12 : 8;
+      const int64_t want = std::max(w.ntok * POOL_PER_TOKEN, std::max(budget / 4, (int64_t)256 << 20) / ebytes);
+      P->pool_cap = std::max(P->pool_cap, std::min(w.pool_bound, want));
     }
     if (rc) break;
     const int64_t na = P->max_bw * 2 * (int64_t)f->Q;
+    const int64_t nt = P->max_ntok;
     if ((rc = alloc_track(P, &P->alpha, na))) break;
-    if (want_fb && (rc = alloc_track(P, &P->beta, na))) break;
-    if (want_vit && (rc = alloc_track(P, &P->bp, P->max_store))) break;
-    if (want_fb && (rc = alloc_track(P, &P->rc, P->max_store))) break;
-    if ((rc = alloc_track(P, &P->mkey, P->max_ntok)) || (rc = alloc_track(P, &P->ekey, P->max_ntok)) ||
-        (rc = alloc_track(P, &P->csum, P->max_ntok)) || (rc = alloc_track(P, &P->esum, P->max_ntok)) ||
-        (rc = alloc_track(P, &P->skey, P->max_lseg)) || (rc = alloc_track(P, &P->scnt, P->max_lseg)) ||
-        (rc = alloc_track(P, &P->spart, P->max_lwin)) || (rc = alloc_track(P, &P->qfinal, P->max_bw)) ||
+    if (P->want_fb && (rc = alloc_track(P, &P->beta, na))) break;
+    if ((rc = alloc_track(P, &P->touch, P->max_bw * (int64_t)f->W)) ||
+        (rc = alloc_track(P, &P->stage, P->max_stage)) || (rc = alloc_track(P, &P->scnt_f, nt)) ||
+        (rc = alloc_track(P, &P->scnt_b, nt)) || (rc = alloc_track(P, &P->pool_q, P->pool_cap)) ||
+        (rc = alloc_track(P, &P->pool_x, P->pool_cap)) || (rc = alloc_track(P, &P->pool_base, nt)) ||
+        (rc = alloc_track(P, &P->pool_cnt, nt)) || (rc = alloc_track(P, &P->pool_top, 1)) ||
+        (rc = alloc_track(P, &P->slot_base, nt)) || (rc = alloc_track(P, &P->bslot_base, nt)) ||
+        (rc = alloc_track(P, &P->step_rng, 2 * ((int64_t)P->max_len + 2))) ||
+        (rc = alloc_track(P, &P->bstep_rng, 2 * ((int64_t)P->max_len + 2))) ||
+        (rc = alloc_track(P, &P->flags_d, 2)) || (rc = alloc_track(P, &P->mkey, nt)) ||
+        (rc = alloc_track(P, &P->ekey, nt)) || (rc = alloc_track(P, &P->csum, nt)) ||
+        (rc = alloc_track(P, &P->esum, nt)) || (rc = alloc_track(P, &P->qfinal, P->max_bw)) ||
         (rc = alloc_track(P, &P->logz, B)) || (rc = alloc_track(P, &P->epoch, 2)) ||
         (rc = alloc_track(P, &P->clear, 1)))
       break;
-    if (want_fb && (rc = alloc_track(P, &P->cnt64, f->bwd.P))) break;
-    if ((rc = alloc_track(P, &P->abm, 3 * P->max_bw * (int64_t)f->W))) break;
-    if ((rc = alloc_track(P, &P->tsum, P->max_ntok * (int64_t)f->Ws))) break;
-    if (want_fb && (rc = alloc_track(P, &P->bbm, 3 * P->max_bw * (int64_t)f->W))) break;
-    if (want_fb && (rc = alloc_track(P, &P->bsum, 3 * P->max_bw * (int64_t)f->Ws))) break;
-    if (want_fb && (rc = alloc_track(P, &P->wlive, P->max_nwins))) break;
-    if ((rc = alloc_track(P, &P->fin, P->max_nwins))) break;
-    if (want_fb && (rc = alloc_track(P, &P->bin, P->max_nwins_b))) break;
-    if (want_fb && (rc = alloc_track(P, &P->bmk, P->max_nwins_b))) break;
+    if (P->want_fb && ((rc = alloc_track(P, &P->pool_v, P->pool_cap)) || (rc = alloc_track(P, &P->cnt64, f->fwd.P))))
+      break;
     FST_CUDA(cudaMemsetAsync(P->alpha, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
+    FST_CUDA(cudaMemsetAsync(P->touch, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)f->W) * 4, s));
     FST_CUDA(cudaMemsetAsync(P->epoch, 0, 8, s));
-    FST_CUDA(cudaMemsetAsync(P->skey, 0, (size_t)std::max<int64_t>(1, P->max_lseg) * 8, s));
-    FST_CUDA(cudaMemsetAsync(P->scnt, 0, (size_t)std::max<int64_t>(1, P->max_lseg) * 4, s));
+    FST_CUDA(cudaMemsetAsync(P->flags_d, 0, 8, s));
     FST_CUDA(cudaStreamSynchronize(s));
   } while (0);
-  dfree(tok_nseg);
-  dfree(tok_cum);
+  dfree(d_ids_copy);
   dfree(d_err);
   if (rc) {
     delete P;
@@ -674,13 +491,8 @@ extern "C" int fst_plan_info(const fst_plan_t* P, int32_t* num_strings, int64_t*
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
   int64_t vl = 1, fl = 1;  // epoch kernel
   for (const Wave& w : P->waves) {
-    for (int32_t t = 1; t <= w.tmax; ++t) {
-      vl += w.items_f[t] > 0;
-      fl += (w.items_f[t] > 0) + (w.items_b[t] > 0);
-      if (t < w.tmax && t >= 2) fl += w.items_f[t - 1] > 0;
-    }
-    vl += 2;  // final + backtrace
-    fl += 1;  // final
+    vl += 2 * (int64_t)w.tmax + 2;  // expand + reduce per position, final, backtrace
+    fl += 2 * (int64_t)w.tmax + 1 + std::max<int64_t>(0, 2 * (int64_t)w.tmax - 1);  // forward, final, backward
   }
   fl += 1;  // counts out
   if (num_strings) *num_strings = P->B;
@@ -696,35 +508,24 @@ extern "C" int fst_plan_info(const fst_plan_t* P, int32_t* num_strings, int64_t*
 
 extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths, int32_t* d_olabels,
                                 int32_t* d_status, void* stream) {
-  if (!P || !d_scores || (P->N > 0 && !d_paths)) { set_error("fst_plan_viterbi: bad arguments"); return FST_ERR_INVALID_ARG; }
-  if (!P->bp) { set_error("plan was created without Viterbi storage"); return FST_ERR_STATE; }
-  fst_s* f = P->fst;
+  if (!P || !d_scores || (P->N > 0 && !d_paths)) {
+    set_error("fst_plan_viterbi: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  if (!P->want_vit) { set_error("plan was created without Viterbi storage"); return FST_ERR_STATE; }
   cudaStream_t s = as_stream(stream);
   int rc;
+  // the Viterbi run reuses the frontier and pool a pending backward pass needs
+  P->forward_done = false;
   if ((rc = run_begin(P, s, false))) return rc;
-  const LayoutView Lf = view_of(f->fwd);
-  for (const Wave& W : P->waves) {
-    const TokenView T = wave_tokens(W);
-    const WaveState S = wave_state(P, W, nullptr);
-    FST_CUDA(cudaMemsetAsync(P->tsum, 0, (size_t)std::max<int64_t>(1, W.ntok * (int64_t)f->Ws) * 4, s));
-    FST_CUDA(cudaMemsetAsync(P->fin, 0, (size_t)std::max<int64_t>(1, W.nwins), s));
-    for (int32_t t = 1; t <= W.tmax; ++t) {
-      const WorkView V = wave_work(W, t, true);
-      if ((rc = clear_rot(P, P->abm, t % 3, f->W, s))) return rc;
-      PROF(FST_PROF_VIT_STEP, launch_vit_step(Lf, T, V, S, step_grid(f, V.nitems), s));
-    }
-    PROF(FST_PROF_VIT_FINAL, launch_vit_final(S, W.Bw, d_scores + W.b0, P->qfinal,
-                                              d_status ? d_status + W.b0 : nullptr, s));
-    PROF(FST_PROF_BACKTRACE, launch_backtrace(Lf, W.tok_sym, W.cbase, S, f->olabel, f->fwd.arc_id, W.Bw,
-                                              P->qfinal, d_paths + W.tok0, d_olabels ? d_olabels + W.tok0 : nullptr,
-                                              s));
-  }
+  for (const Wave& W : P->waves)
+    if ((rc = run_viterbi_wave(P, W, d_scores, d_paths, d_olabels, d_status, s))) return rc;
   return FST_OK;
 }
 
 extern "C" int fst_plan_forward(fst_plan_t* P, double* d_logz, int32_t* d_status, void* stream) {
   if (!P || !d_logz) { set_error("fst_plan_forward: bad arguments"); return FST_ERR_INVALID_ARG; }
-  if (!P->rc) { set_error("plan was created without forward-backward storage"); return FST_ERR_STATE; }
+  if (!P->want_fb) { set_error("plan was created without forward-backward storage"); return FST_ERR_STATE; }
   if (P->waves.size() > 1) { set_error("fst_plan_forward needs a single-wave plan"); return FST_ERR_STATE; }
   cudaStream_t s = as_stream(stream);
   int rc;
@@ -738,27 +539,27 @@ extern "C" int fst_plan_forward(fst_plan_t* P, double* d_logz, int32_t* d_status
 
 extern "C" int fst_plan_backward(fst_plan_t* P, const float* d_weights, float* d_counts, void* stream) {
   if (!P || !d_counts) { set_error("fst_plan_backward: bad arguments"); return FST_ERR_INVALID_ARG; }
-  if (!P->forward_done) { set_error("fst_plan_backward before fst_plan_forward"); return FST_ERR_STATE; }
+  if (!P->forward_done) { set_error("fst_plan_backward needs a preceding fst_plan_forward"); return FST_ERR_STATE; }
   fst_s* f = P->fst;
   cudaStream_t s = as_stream(stream);
   int rc;
-  FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->bwd.P) * 8, s));
+  FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->fwd.P) * 8, s));
   for (const Wave& W : P->waves)
     if ((rc = run_backward_wave(P, W, d_weights, s))) return rc;
   const CountView C{1, nullptr, nullptr, P->cnt64};
-  PROF(FST_PROF_COUNTS, launch_counts_out(f->bwd.arc_id, f->bwd.P, C, d_counts, s));
+  PROF(FST_PROF_COUNTS, launch_counts_out(f->fwd.arc_id, f->fwd.P, C, d_counts, s));
   return FST_OK;
 }
 
 extern "C" int fst_plan_forward_backward(fst_plan_t* P, const float* d_weights, double* d_logz, float* d_counts,
                                          int32_t* d_status, void* stream) {
   if (!P || !d_logz) { set_error("fst_plan_forward_backward: bad arguments"); return FST_ERR_INVALID_ARG; }
-  if (!P->rc) { set_error("plan was created without forward-backward storage"); return FST_ERR_STATE; }
+  if (!P->want_fb) { set_error("plan was created without forward-backward storage"); return FST_ERR_STATE; }
   fst_s* f = P->fst;
   cudaStream_t s = as_stream(stream);
   int rc;
   if ((rc = run_begin(P, s, true))) return rc;
-  if (d_counts) FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->bwd.P) * 8, s));
+  if (d_counts) FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->fwd.P) * 8, s));
   for (const Wave& W : P->waves) {
     if ((rc = run_forward_wave(P, W, s, d_status))) return rc;
     if (d_counts && (rc = run_backward_wave(P, W, d_weights, s))) return rc;
@@ -766,7 +567,7 @@ extern "C" int fst_plan_forward_backward(fst_plan_t* P, const float* d_weights, 
   if (P->B > 0) FST_CUDA(cudaMemcpyAsync(d_logz, P->logz, (size_t)P->B * 8, cudaMemcpyDeviceToDevice, s));
   if (d_counts) {
     const CountView C{1, nullptr, nullptr, P->cnt64};
-    PROF(FST_PROF_COUNTS, launch_counts_out(f->bwd.arc_id, f->bwd.P, C, d_counts, s));
+    PROF(FST_PROF_COUNTS, launch_counts_out(f->fwd.arc_id, f->fwd.P, C, d_counts, s));
   }
   P->forward_done = P->waves.size() <= 1;
   return FST_OK;

@@ -134,13 +134,22 @@ __global__ void k_pos_by_id(const int32_t* __restrict__ arc_id, int64_t P, int32
   if (i < P && arc_id[i] >= 0) pos_by_id[arc_id[i]] = (int32_t)i;
 }
 
-// fwin[i] = forward window of the arc at backward position i
-__global__ void k_fwin(const int32_t* __restrict__ arc_id_b, int64_t P, const int32_t* __restrict__ pos_by_id,
-                       int32_t* __restrict__ fwin) {
+// segof[pos] = segment holding padded position pos (padding stays -1)
+__global__ void k_seg_of(const int32_t* __restrict__ seg_pos, const int32_t* __restrict__ seg_len, int64_t nseg,
+                         int32_t* __restrict__ segof) {
+  const int64_t sg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sg >= nseg) return;
+  const int32_t p0 = seg_pos[sg];
+  for (int32_t i = 0; i < seg_len[sg]; ++i) segof[p0 + i] = (int32_t)sg;
+}
+
+// xseg[i] = segment of the other layout that holds the arc at position i
+__global__ void k_xseg(const int32_t* __restrict__ arc_id, int64_t P, const int32_t* __restrict__ pos_by_id_other,
+                       const int32_t* __restrict__ segof_other, int32_t* __restrict__ xseg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
-  const int32_t k = arc_id_b[i];
-  fwin[i] = k >= 0 ? pos_by_id[k] / WIN : -1;
+  const int32_t k = arc_id[i];
+  xseg[i] = k >= 0 ? segof_other[pos_by_id_other[k]] : -1;
 }
 
 __global__ void k_scatter_arcs(const uint32_t* __restrict__ perm, const int64_t* __restrict__ hd,
@@ -337,7 +346,7 @@ int build_layout(fst_s* f, Layout& L, const int32_t* d_il, const int32_t* seg_st
 
 void free_layout(Layout& L) {
   dfree(L.other); dfree(L.theta); dfree(L.arc_id); dfree(L.theta64); dfree(L.win);
-  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.seg_len); dfree(L.fwin); dfree(L.bwin); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
+  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.seg_len); dfree(L.xseg); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
   dfree(L.sym_lwin);
   free(L.h_sym_win); free(L.h_sym_seg); free(L.h_sym_lseg); free(L.h_sym_lwin);
   L.h_sym_win = L.h_sym_seg = L.h_sym_lseg = L.h_sym_lwin = nullptr;
@@ -352,21 +361,32 @@ int build_store(fst_s* f, const int32_t* d_src, const int32_t* d_dst, const int3
   if ((rc = build_layout(f, f->fwd, d_il, d_dst, d_src, d_theta, &f->h_sym_arc, f->sym_arc, s))) return rc;
   // backward: segments by source, arcs carry their destination
   if ((rc = build_layout(f, f->bwd, d_il, d_src, d_dst, d_theta, nullptr, nullptr, s))) return rc;
-  // each backward arc knows its forward window (used to mark the windows a
-  // live source feeds at the next position)
-  int32_t* pos_by_id = nullptr;
-  if ((rc = dalloc(&pos_by_id, f->A)) || (rc = dalloc(&f->bwd.fwin, f->bwd.P)) || (rc = dalloc(&f->fwd.bwin, f->fwd.P))) {
-    dfree(pos_by_id);
+  // each arc knows the segment of the other layout that holds it: a live
+  // source's arcs (backward layout) lead to the destination segments to
+  // reduce (forward layout), and the other way round in the backward pass
+  int32_t *fpos = nullptr, *bpos = nullptr, *fsegof = nullptr, *bsegof = nullptr;
+  auto release = [&]() { dfree(fpos); dfree(bpos); dfree(fsegof); dfree(bsegof); };
+  if ((rc = dalloc(&fpos, f->A)) || (rc = dalloc(&bpos, f->A)) || (rc = dalloc(&fsegof, f->fwd.P)) ||
+      (rc = dalloc(&bsegof, f->bwd.P)) || (rc = dalloc(&f->fwd.xseg, f->fwd.P)) || (rc = dalloc(&f->bwd.xseg, f->bwd.P))) {
+    release();
     return rc;
   }
-  if (f->fwd.P > 0) k_pos_by_id<<<blocks_for(f->fwd.P), TB, 0, s>>>(f->fwd.arc_id, f->fwd.P, pos_by_id);
-  if (f->bwd.P > 0) k_fwin<<<blocks_for(f->bwd.P), TB, 0, s>>>(f->bwd.arc_id, f->bwd.P, pos_by_id, f->bwd.fwin);
-  // and each forward arc its backward window (marks of the backward pass)
-  if (f->bwd.P > 0) k_pos_by_id<<<blocks_for(f->bwd.P), TB, 0, s>>>(f->bwd.arc_id, f->bwd.P, pos_by_id);
-  if (f->fwd.P > 0) k_fwin<<<blocks_for(f->fwd.P), TB, 0, s>>>(f->fwd.arc_id, f->fwd.P, pos_by_id, f->fwd.bwin);
-  cudaError_t e = cudaStreamSynchronize(s);
-  dfree(pos_by_id);
-  if (e != cudaSuccess) return cuda_fail(e, "forward windows of backward arcs");
+  cudaError_t e = cudaSuccess;
+  if (f->fwd.P > 0) e = cudaMemsetAsync(fsegof, 0xff, (size_t)f->fwd.P * 4, s);
+  if (e == cudaSuccess && f->bwd.P > 0) e = cudaMemsetAsync(bsegof, 0xff, (size_t)f->bwd.P * 4, s);
+  if (e == cudaSuccess) {
+    if (f->fwd.P > 0) k_pos_by_id<<<blocks_for(f->fwd.P), TB, 0, s>>>(f->fwd.arc_id, f->fwd.P, fpos);
+    if (f->bwd.P > 0) k_pos_by_id<<<blocks_for(f->bwd.P), TB, 0, s>>>(f->bwd.arc_id, f->bwd.P, bpos);
+    if (f->fwd.nseg > 0)
+      k_seg_of<<<blocks_for(f->fwd.nseg), TB, 0, s>>>(f->fwd.seg_pos, f->fwd.seg_len, f->fwd.nseg, fsegof);
+    if (f->bwd.nseg > 0)
+      k_seg_of<<<blocks_for(f->bwd.nseg), TB, 0, s>>>(f->bwd.seg_pos, f->bwd.seg_len, f->bwd.nseg, bsegof);
+    if (f->fwd.P > 0) k_xseg<<<blocks_for(f->fwd.P), TB, 0, s>>>(f->fwd.arc_id, f->fwd.P, bpos, bsegof, f->fwd.xseg);
+    if (f->bwd.P > 0) k_xseg<<<blocks_for(f->bwd.P), TB, 0, s>>>(f->bwd.arc_id, f->bwd.P, fpos, fsegof, f->bwd.xseg);
+    e = cudaStreamSynchronize(s);
+  }
+  release();
+  if (e != cudaSuccess) return cuda_fail(e, "segments of the other layout");
   return FST_OK;
 }
 
