@@ -49,17 +49,6 @@ __device__ __forceinline__ int32_t warps_total() { return (int32_t)((gridDim.x *
 
 __device__ __forceinline__ float decode_max(uint32_t k) { return k ? fkey_inv(k) : neg_inf(); }
 
-// Running log-sum-exp as (max m, sum s of exp(v - m)): the value m + log s.
-__device__ __forceinline__ void lse_push(float& m, float& s, float v) {
-  if (v == neg_inf()) return;
-  if (v > m) {
-    s = s * __expf(m - v) + 1.f;  // exp(-inf) = 0 on the first term
-    m = v;
-  } else {
-    s += __expf(v - m);
-  }
-}
-__device__ __forceinline__ float lse_value(float m, float s) { return m == neg_inf() ? neg_inf() : m + logf(s); }
 
 // Owner of flat entry j among the n slots whose first entries base[0..n)
 // are nondecreasing with base[0] <= j: the last slot with base <= j.  A warp
@@ -108,50 +97,51 @@ __device__ __forceinline__ void untouch(uint32_t* tb, int32_t q) { atomicAnd(tb 
 // the end.  The tokens from the first whose range would pass `cap` on get
 // empty ranges (slot base INT64_MAX, so no flat index maps to them) and
 // raise error bit 1: every status of the run then reports FST_ERR_OOM.
+// Each thread scans a run of consecutive slots, then the block scans the
+// run totals (two warp levels).
 __device__ void ranges_last_block(const TokenView& T, const StepView& V, const FrontierState& S,
                                   const uint32_t* cnt, int64_t* top, int64_t cap, int64_t* slot_out,
                                   int64_t* base_out, int32_t* cnt_out, int64_t* rng_out) {
   __shared__ int last;
-  __shared__ long long sh[KT];
-  __shared__ long long carry, begin, first_bad;
+  __shared__ long long wsum[KT / 32];
+  __shared__ long long first_bad;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   __threadfence();
   if (threadIdx.x == 0) last = (atomicAdd(S.flags, 1u) == gridDim.x - 1u);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (threadIdx.x == 0) {
-    begin = top ? (long long)__ldcg(top) : 0ll;
-    carry = begin;
-    first_bad = (long long)INT64_MAX;
+  const long long begin = top ? (long long)__ldcg(top) : 0ll;
+  if (threadIdx.x == 0) first_bad = (long long)INT64_MAX;
+  const int32_t per = (V.n + KT - 1) / KT;
+  const int32_t k0 = (int32_t)threadIdx.x * per, k1 = min(V.n, k0 + per);
+  long long run = 0;
+  for (int32_t k = k0; k < k1; ++k) run += (long long)__ldcg(cnt + __ldg(T.step_tok + V.slot0 + k));
+  long long incl = run;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long o = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  long long wbase = 0;
+  for (int w = 0; w < warp; ++w) wbase += wsum[w];
+  long long base = begin + wbase + incl - run;
+  for (int32_t k = k0; k < k1; ++k) {
+    const int32_t p = __ldg(T.step_tok + V.slot0 + k);
+    const long long m = (long long)__ldcg(cnt + p);
+    const bool fit = base + m <= (long long)cap;
+    if (!fit) atomicMin(&first_bad, base);
+    slot_out[V.slot0 + k] = fit ? base : INT64_MAX;
+    if (base_out) base_out[p] = fit ? base : 0;
+    if (cnt_out) cnt_out[p] = fit ? (int32_t)m : 0;
+    base += m;
   }
   __syncthreads();
-  for (int32_t c = 0; c < V.n; c += KT) {
-    const int32_t k = c + (int32_t)threadIdx.x;
-    const int32_t p = k < V.n ? __ldg(T.step_tok + V.slot0 + k) : -1;
-    const long long m = p >= 0 ? (long long)__ldcg(cnt + p) : 0ll;
-    sh[threadIdx.x] = m;
-    __syncthreads();
-    for (int d = 1; d < KT; d <<= 1) {
-      const long long v = (int)threadIdx.x >= d ? sh[threadIdx.x - d] : 0ll;
-      __syncthreads();
-      sh[threadIdx.x] += v;
-      __syncthreads();
-    }
-    const long long base = carry + sh[threadIdx.x] - m;
-    if (p >= 0) {
-      const bool fit = base + m <= (long long)cap;
-      if (!fit) atomicMin(&first_bad, base);
-      slot_out[V.slot0 + k] = fit ? base : INT64_MAX;
-      if (base_out) base_out[p] = fit ? base : 0;
-      if (cnt_out) cnt_out[p] = fit ? (int32_t)m : 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == KT - 1) carry += sh[KT - 1];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const long long end = carry < first_bad ? carry : first_bad;
+  if (threadIdx.x == KT - 1) {
+    const long long end = base < first_bad ? base : first_bad;
     if (first_bad != (long long)INT64_MAX) atomicOr(S.flags + 1, 1u);
     rng_out[0] = begin;
     rng_out[1] = end;
@@ -159,6 +149,141 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
     S.flags[0] = 0u;
   }
 }
+
+// ======================================================================
+// Warp-flattened arc walks.  Lane i owns the arcs [e0_i, e0_i + len_i) of
+// one segment; the warp visits the arcs of all 32 lanes 32 at a time, in
+// lane order, so that a long segment (a hub state) spreads over the warp
+// instead of holding up one lane.
+// ======================================================================
+struct Flat {
+  int32_t excl;   // arcs of lower lanes
+  int32_t total;  // arcs of the warp
+};
+__device__ __forceinline__ Flat flat_prefix(int32_t len) {
+  const int lane = threadIdx.x & 31;
+  int32_t incl = len;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t o = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += o;
+  }
+  return Flat{incl - len, __shfl_sync(FULL, incl, 31)};
+}
+// Lane owning flat arc a: the last lane whose first flat arc is <= a.
+__device__ __forceinline__ int flat_owner(int32_t excl, int32_t a) {
+  int o = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const int32_t ex = __shfl_sync(FULL, excl, o + step);
+    if (ex <= a) o += step;
+  }
+  return o;
+}
+// Tail lane, in the round of flat arcs [r, r+32), of the run of this lane's
+// own segment; -1 when the segment has no arc in the round.
+__device__ __forceinline__ int flat_tail(const Flat& F, int32_t len, int32_t r) {
+  if (len <= 0 || F.excl >= r + 32 || F.excl + len <= r) return -1;
+  return min(F.excl + len, r + 32) - 1 - r;
+}
+// Inclusive segmented scan over lanes of `v` (runs of equal owner `o`).
+template <class Op>
+__device__ __forceinline__ typename Op::T run_scan(typename Op::T v, int o) {
+  const int lane = threadIdx.x & 31;
+  const int o_prev = __shfl_up_sync(FULL, o, 1);  // every lane shuffles: no short-circuit before it
+  const bool head = (lane == 0) || (o_prev != o);
+  const uint32_t hm = __ballot_sync(FULL, head) & (0xffffffffu >> (31 - lane));
+  const int start = 31 - __clz(hm);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const typename Op::T u = Op::shfl_up(v, d);
+    if (lane - d >= start) v = Op::combine(u, v);
+  }
+  return v;
+}
+
+struct MaxKey {
+  typedef unsigned long long T;
+  static __device__ __forceinline__ T identity() { return 0ull; }
+  static __device__ __forceinline__ T combine(T a, T b) { return a > b ? a : b; }
+  static __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(FULL, v, d); }
+  static __device__ __forceinline__ T shfl(T v, int l) { return __shfl_sync(FULL, v, l); }
+};
+struct MaxF {
+  typedef float T;
+  static __device__ __forceinline__ T identity() { return __int_as_float(0xff800000); }
+  static __device__ __forceinline__ T combine(T a, T b) { return fmaxf(a, b); }
+  static __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(FULL, v, d); }
+  static __device__ __forceinline__ T shfl(T v, int l) { return __shfl_sync(FULL, v, l); }
+};
+struct SumU {
+  typedef unsigned long long T;
+  static __device__ __forceinline__ T identity() { return 0ull; }
+  static __device__ __forceinline__ T combine(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(FULL, v, d); }
+  static __device__ __forceinline__ T shfl(T v, int l) { return __shfl_sync(FULL, v, l); }
+};
+
+// exp(v - m), v <= m, as a 2^-40 fixed-point integer: sums of these are exact
+// and so independent of the order in which the warp happens to add them
+constexpr double FIX_ONE = 1099511627776.0;  // 2^40
+__device__ __forceinline__ unsigned long long fix_exp(float v, float m) {
+  return v == __int_as_float(0xff800000) ? 0ull : __double2ull_rn((double)__expf(v - m) * FIX_ONE);
+}
+__device__ __forceinline__ float fix_log_sum(float m, unsigned long long s) {
+  return (m == __int_as_float(0xff800000) || s == 0ull) ? __int_as_float(0xff800000)
+                                                        : m + (float)log((double)s / FIX_ONE);
+}
+
+// Reduce the arcs of every lane's segment with Op; value(e, o) gives the
+// value of arc e owned by lane o (it must not use warp collectives: lane
+// data of the owner is fetched by the caller through `ctx` shuffles).
+template <class Op, class Ctx, class F>
+__device__ __forceinline__ typename Op::T flat_reduce(int32_t e0, int32_t len, const Ctx& mine, F value) {
+  const int lane = threadIdx.x & 31;
+  const Flat F0 = flat_prefix(len);
+  typename Op::T acc = Op::identity();
+  for (int32_t r = 0; r < F0.total; r += 32) {
+    const int32_t a = r + lane;
+    const bool act = a < F0.total;
+    const int o = flat_owner(F0.excl, act ? a : F0.total - 1);
+    const int32_t ex_o = __shfl_sync(FULL, F0.excl, o), e0_o = __shfl_sync(FULL, e0, o);
+    const Ctx c = mine.shfl(o);
+    typename Op::T v = act ? value(e0_o + (a - ex_o), c) : Op::identity();
+    v = run_scan<Op>(v, o);
+    const int tail = flat_tail(F0, len, r);
+    const typename Op::T run = Op::shfl(v, tail < 0 ? 0 : tail);
+    if (tail >= 0) acc = Op::combine(acc, run);
+    (void)lane;
+  }
+  return acc;
+}
+
+// Visit the arcs of every lane's segment: visit(e, o) per arc.
+template <class Ctx, class F>
+__device__ __forceinline__ void flat_visit(int32_t e0, int32_t len, const Ctx& mine, F visit) {
+  const int lane = threadIdx.x & 31;
+  const Flat F0 = flat_prefix(len);
+  for (int32_t r = 0; r < F0.total; r += 32) {
+    const int32_t a = r + lane;
+    const bool act = a < F0.total;
+    const int o = flat_owner(F0.excl, act ? a : F0.total - 1);
+    const int32_t ex_o = __shfl_sync(FULL, F0.excl, o), e0_o = __shfl_sync(FULL, e0, o);
+    const Ctx c = mine.shfl(o);
+    if (act) visit(e0_o + (a - ex_o), c);
+  }
+}
+
+// Per-lane context the arc walks need from the owner lane.
+struct TokCtx {
+  int32_t p, b;
+  float sh;  // a step shift (forward m_{t-1} or backward e_t), or unused
+  float m;   // the segment's maximum (second pass of a log-sum-exp)
+  __device__ __forceinline__ TokCtx shfl(int o) const {
+    return TokCtx{__shfl_sync(FULL, p, o), __shfl_sync(FULL, b, o), __shfl_sync(FULL, sh, o),
+                  __shfl_sync(FULL, m, o)};
+  }
+};
 
 // ======================================================================
 // Expand (Alg. 1 / Alg. 2 forward loops, restricted to live sources).
@@ -188,16 +313,22 @@ __global__ void __launch_bounds__(KT) k_expand(LayoutView Lb, TokenView T, StepV
         }
       }
     }
-    if (p < 0 || q < 0) continue;
-    const int64_t sg = find_seg(Lb, __ldg(T.sym + p), q);
-    if (sg < 0) continue;  // no arc out of q reads w_t
-    uint32_t* tb = S.touch + (int64_t)__ldg(T.b + p) * S.W;
-    int32_t* stg = S.stage + __ldg(T.stf + p);
-    const int32_t e0 = __ldg(Lb.seg_pos + sg), e1 = e0 + __ldg(Lb.seg_len + sg);
-    for (int32_t e = e0; e < e1; ++e) {
-      const int32_t d = __ldg(Lb.other + e);
-      if (touch_first(tb, d)) stg[atomicAdd(S.scnt_f + p, 1u)] = __ldg(Lb.xseg + e);
+    // the source's arcs on w_t: its segment of the source-segmented layout
+    int32_t e0 = 0, len = 0;
+    TokCtx me{p, 0, 0.f, 0.f};
+    if (p >= 0 && q >= 0) {
+      const int64_t sg = find_seg(Lb, __ldg(T.sym + p), q);
+      if (sg >= 0) {
+        e0 = __ldg(Lb.seg_pos + sg);
+        len = __ldg(Lb.seg_len + sg);
+        me.b = __ldg(T.b + p);
+      }
     }
+    flat_visit(e0, len, me, [&](int32_t e, const TokCtx& c) {
+      const int32_t d = __ldg(Lb.other + e);
+      if (touch_first(S.touch + (int64_t)c.b * S.W, d))
+        S.stage[__ldg(T.stf + c.p) + atomicAdd(S.scnt_f + c.p, 1u)] = __ldg(Lb.xseg + e);
+    });
   }
   ranges_last_block(T, V, S, S.scnt_f, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
                     S.step_rng + 2 * V.t);
@@ -226,27 +357,32 @@ __global__ void __launch_bounds__(KT) k_vit_reduce(LayoutView Lf, TokenView T, S
   for (int64_t c0 = R0 + (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
     const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
-    if (j >= R1) continue;
-    const Entry x = step_entry(T, V, S.slot_base, k0, j);
-    const int32_t b = __ldg(T.b + x.p);
-    const int32_t sg = S.stage[__ldg(T.stf + x.p) + x.i];
-    const int32_t d = __ldg(Lf.seg_state + sg);
-    untouch(S.touch + (int64_t)b * S.W, d);
-    const unsigned long long* ain = S.alpha + ((int64_t)b * 2 + ((V.t - 1) & 1)) * S.Q;
-    const uint32_t tin = tag_base + (uint32_t)(x.p - 1);
-    const int32_t e0 = __ldg(Lf.seg_pos + sg), e1 = e0 + __ldg(Lf.seg_len + sg);
-    unsigned long long best = 0ull;
-    for (int32_t e = e0; e < e1; ++e) {
-      const int32_t q = __ldg(Lf.other + e);
-      const float a = (V.t == 1) ? __ldg(S.theta_s + q) : tagged_value(__ldg(ain + q), tin);
-      const float c = __fadd_rn(a, __ldg(Lf.theta + e));
-      if (c != neg_inf()) {
-        const unsigned long long key = ((unsigned long long)fkey(c) << 32) | (unsigned long long)(~(uint32_t)e);
-        best = key > best ? key : best;
-      }
+    const bool act = j < R1;
+    int32_t d = 0, e0 = 0, len = 0;
+    TokCtx me{0, 0, 0.f, 0.f};
+    if (act) {
+      const Entry x = step_entry(T, V, S.slot_base, k0, j);
+      me.p = x.p;
+      me.b = __ldg(T.b + x.p);
+      const int32_t sg = S.stage[__ldg(T.stf + x.p) + x.i];
+      d = __ldg(Lf.seg_state + sg);
+      untouch(S.touch + (int64_t)me.b * S.W, d);
+      e0 = __ldg(Lf.seg_pos + sg);
+      len = __ldg(Lf.seg_len + sg);
     }
+    const unsigned long long best = flat_reduce<MaxKey>(e0, len, me, [&](int32_t e, const TokCtx& c) {
+      const int32_t q = __ldg(Lf.other + e);
+      const float a = (V.t == 1) ? __ldg(S.theta_s + q)
+                                 : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((V.t - 1) & 1)) * S.Q + q),
+                                                tag_base + (uint32_t)(c.p - 1));
+      const float cand = __fadd_rn(a, __ldg(Lf.theta + e));
+      return cand == neg_inf() ? 0ull
+                               : (((unsigned long long)fkey(cand) << 32) | (unsigned long long)(~(uint32_t)e));
+    });
+    if (!act) continue;
     if (best)
-      S.alpha[((int64_t)b * 2 + (V.t & 1)) * S.Q + d] = tagged_make(fkey_inv((uint32_t)(best >> 32)), tag_base + (uint32_t)x.p);
+      S.alpha[((int64_t)me.b * 2 + (V.t & 1)) * S.Q + d] =
+          tagged_make(fkey_inv((uint32_t)(best >> 32)), tag_base + (uint32_t)me.p);
     S.pool_q[j] = best ? d : -1;
     S.pool_x[j] = best ? (int32_t)(~(uint32_t)best) : -1;
   }
@@ -263,28 +399,39 @@ __global__ void __launch_bounds__(KT) k_fwd_reduce(LayoutView Lf, TokenView T, S
   for (int64_t c0 = R0 + (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
     const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
-    if (j >= R1) continue;
-    const Entry x = step_entry(T, V, S.slot_base, k0, j);
-    const int32_t b = __ldg(T.b + x.p);
-    const int32_t sg = S.stage[__ldg(T.stf + x.p) + x.i];
-    const int32_t d = __ldg(Lf.seg_state + sg);
-    untouch(S.touch + (int64_t)b * S.W, d);
-    const unsigned long long* ain = S.alpha + ((int64_t)b * 2 + ((V.t - 1) & 1)) * S.Q;
-    const uint32_t tin = tag_base + (uint32_t)(x.p - 1);
-    const float mprev = V.t > 1 ? decode_max(S.mkey[x.p - 1]) : 0.f;
-    const int32_t e0 = __ldg(Lf.seg_pos + sg), e1 = e0 + __ldg(Lf.seg_len + sg);
-    float m = neg_inf(), sum = 0.f;
-    if (mprev != neg_inf()) {
-      for (int32_t e = e0; e < e1; ++e) {
-        const int32_t q = __ldg(Lf.other + e);
-        const float a = (V.t == 1) ? __ldg(S.theta_s + q) : tagged_value(__ldg(ain + q), tin);
-        if (a != neg_inf()) lse_push(m, sum, (a - mprev) + __ldg(Lf.theta + e));
+    const bool act = j < R1;
+    int32_t d = 0, e0 = 0, len = 0, sg = 0;
+    TokCtx me{0, 0, 0.f, 0.f};
+    if (act) {
+      const Entry x = step_entry(T, V, S.slot_base, k0, j);
+      me.p = x.p;
+      me.b = __ldg(T.b + x.p);
+      me.sh = V.t > 1 ? decode_max(S.mkey[x.p - 1]) : 0.f;
+      sg = S.stage[__ldg(T.stf + x.p) + x.i];
+      d = __ldg(Lf.seg_state + sg);
+      untouch(S.touch + (int64_t)me.b * S.W, d);
+      if (me.sh != neg_inf()) {
+        e0 = __ldg(Lf.seg_pos + sg);
+        len = __ldg(Lf.seg_len + sg);
       }
     }
-    const float r = lse_value(m, sum);
+    auto value = [&](int32_t e, const TokCtx& c) {
+      const int32_t q = __ldg(Lf.other + e);
+      const float a = (V.t == 1) ? __ldg(S.theta_s + q)
+                                 : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((V.t - 1) & 1)) * S.Q + q),
+                                                tag_base + (uint32_t)(c.p - 1));
+      return a == neg_inf() ? neg_inf() : (a - c.sh) + __ldg(Lf.theta + e);
+    };
+    // log-sum-exp in two order-independent passes: max, then the
+    // fixed-point sum of exp(v - max)
+    me.m = flat_reduce<MaxF>(e0, len, me, value);
+    const unsigned long long su = flat_reduce<SumU>(
+        e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
+    if (!act) continue;
+    const float r = fix_log_sum(me.m, su);
     if (r != neg_inf()) {
-      S.alpha[((int64_t)b * 2 + (V.t & 1)) * S.Q + d] = tagged_make(r, tag_base + (uint32_t)x.p);
-      atomicMax(S.mkey + x.p, fkey(r));
+      S.alpha[((int64_t)me.b * 2 + (V.t & 1)) * S.Q + d] = tagged_make(r, tag_base + (uint32_t)me.p);
+      atomicMax(S.mkey + me.p, fkey(r));
     }
     S.pool_q[j] = r != neg_inf() ? d : -1;
     S.pool_x[j] = sg;
@@ -315,6 +462,18 @@ __device__ __forceinline__ void add_count(const CountView& C, int32_t e, float g
   }
 }
 
+// owner context of the backward expand: token, string, mprev, and the
+// float64 exponent offset (ub - e_t) + K of its destination
+struct BwdCtx {
+  int32_t p, b;
+  float mprev, gw;
+  double off;
+  __device__ __forceinline__ BwdCtx shfl(int o) const {
+    return BwdCtx{__shfl_sync(FULL, p, o), __shfl_sync(FULL, b, o), __shfl_sync(FULL, mprev, o),
+                  __shfl_sync(FULL, gw, o), __shfl_sync(FULL, off, o)};
+  }
+};
+
 __global__ void __launch_bounds__(KT) k_bwd_expand(LayoutView Lf, TokenView T, StepView V, FrontierState S,
                                                    CountView C) {
   const int lane = threadIdx.x & 31;
@@ -324,42 +483,46 @@ __global__ void __launch_bounds__(KT) k_bwd_expand(LayoutView Lf, TokenView T, S
   for (int64_t c0 = R0 + (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
     const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
-    if (j >= R1) continue;
-    const Entry x = step_entry(T, V, S.slot_base, k0, j);
-    const int32_t p = x.p, b = __ldg(T.b + p), n = S.bw_n[b];
-    const double lz = S.logz[b];
-    if (lz == -INFINITY) continue;  // no path: every posterior is zero
-    // shifts: e_t = this step's backward maximum, m_{t-1} the forward one;
-    // K = C_{t-1} + E_t - log Z collects the float64 running sums
-    const float et = (t == n) ? 0.f : decode_max(S.ekey[p]);
-    const double tE = (t == n) ? 0.0 : S.esum[p + 1] + (double)et;
-    if (x.i == 0) S.esum[p] = tE;  // E_t, read by the step at t-1
-    const double K = ((t == 1) ? 0.0 : S.csum[p - 1]) + tE - lz;
-    const float mprev = (t == 1) ? 0.f : decode_max(S.mkey[p - 1]);
-    const int32_t q = S.pool_q[j];
-    if (q < 0 || et == neg_inf() || mprev == neg_inf()) continue;
-    const float ub = (t == n) ? __ldg(S.theta_f + q)
-                              : tagged_value(__ldg(S.beta + ((int64_t)b * 2 + (t & 1)) * S.Q + q), tag_base + (uint32_t)p);
-    if (ub == neg_inf()) continue;
-    const double ubs = (double)ub - (double)et;
-    const float gw = S.gweight ? S.gweight[b] : 1.f;
-    const unsigned long long* ain = S.alpha + ((int64_t)b * 2 + ((t - 1) & 1)) * S.Q;
-    const uint32_t ta_tag = tag_base + (uint32_t)(p - 1);
-    uint32_t* tb = S.touch + (int64_t)b * S.W;
-    int32_t* stg = S.stage + __ldg(T.stb + p);
-    const int32_t sg = S.pool_x[j];
-    const int32_t e0 = __ldg(Lf.seg_pos + sg), e1 = e0 + __ldg(Lf.seg_len + sg);
-    for (int32_t e = e0; e < e1; ++e) {
+    int32_t e0 = 0, len = 0;
+    BwdCtx me{0, 0, 0.f, 0.f, 0.0};
+    if (j < R1) {
+      const Entry x = step_entry(T, V, S.slot_base, k0, j);
+      const int32_t p = x.p, b = __ldg(T.b + p), n = S.bw_n[b];
+      const double lz = S.logz[b];
+      // shifts: e_t = this step's backward maximum, m_{t-1} the forward one;
+      // K = C_{t-1} + E_t - log Z collects the float64 running sums
+      const float et = (t == n) ? 0.f : decode_max(S.ekey[p]);
+      const double tE = (t == n) ? 0.0 : S.esum[p + 1] + (double)et;
+      if (x.i == 0 && lz != -INFINITY) S.esum[p] = tE;  // E_t, read by the step at t-1
+      const double K = ((t == 1) ? 0.0 : S.csum[p - 1]) + tE - lz;
+      const float mprev = (t == 1) ? 0.f : decode_max(S.mkey[p - 1]);
+      const int32_t q = S.pool_q[j];
+      if (lz != -INFINITY && q >= 0 && et != neg_inf() && mprev != neg_inf()) {
+        const float ub = (t == n) ? __ldg(S.theta_f + q)
+                                  : tagged_value(__ldg(S.beta + ((int64_t)b * 2 + (t & 1)) * S.Q + q),
+                                                 tag_base + (uint32_t)p);
+        if (ub != neg_inf()) {
+          const int32_t sg = S.pool_x[j];
+          e0 = __ldg(Lf.seg_pos + sg);
+          len = __ldg(Lf.seg_len + sg);
+          me = BwdCtx{p, b, mprev, S.gweight ? S.gweight[b] : 1.f, ((double)ub - (double)et) + K};
+        }
+      }
+    }
+    flat_visit(e0, len, me, [&](int32_t e, const BwdCtx& c) {
       const int32_t src = __ldg(Lf.other + e);
-      const float ra = (t == 1) ? __ldg(S.theta_s + src) : tagged_value(__ldg(ain + src), ta_tag);
+      const float ra = (t == 1) ? __ldg(S.theta_s + src)
+                                : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((t - 1) & 1)) * S.Q + src),
+                                               tag_base + (uint32_t)(c.p - 1));
       const float th = __ldg(Lf.theta + e);
-      if (ra == neg_inf() || th == neg_inf()) continue;
+      if (ra == neg_inf() || th == neg_inf()) return;
       // the exponent adds terms of either sign and tens in size that cancel
       // to a small number: formed in float64
-      const double ex = ((double)ra - (double)mprev) + (double)th + ubs + K;
-      add_count(C, e, __expf((float)ex) * gw);
-      if (t >= 2 && touch_first(tb, src)) stg[atomicAdd(S.scnt_b + p, 1u)] = __ldg(Lf.xseg + e);
-    }
+      const double ex = ((double)ra - (double)c.mprev) + (double)th + c.off;
+      add_count(C, e, __expf((float)ex) * c.gw);
+      if (t >= 2 && touch_first(S.touch + (int64_t)c.b * S.W, src))
+        S.stage[__ldg(T.stb + c.p) + atomicAdd(S.scnt_b + c.p, 1u)] = __ldg(Lf.xseg + e);
+    });
   }
   if (t >= 2)
     ranges_last_block(T, V, S, S.scnt_b, nullptr, INT64_MAX, S.bslot_base, nullptr, nullptr, S.bstep_rng + 2 * t);
@@ -394,28 +557,39 @@ __global__ void __launch_bounds__(KT) k_bwd_reduce(LayoutView Lb, TokenView T, S
   for (int64_t c0 = (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
     const int32_t k0 = warp_owner(S.bslot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
-    if (j >= R1) continue;
-    const Entry x = step_entry(T, V, S.bslot_base, k0, j);
-    const int32_t p = x.p, b = __ldg(T.b + p), n = S.bw_n[b];
-    const int32_t sg = S.stage[__ldg(T.stb + p) + x.i];
-    const int32_t q = __ldg(Lb.seg_state + sg);
-    untouch(S.touch + (int64_t)b * S.W, q);
-    const float et = (t == n) ? 0.f : decode_max(S.ekey[p]);
-    const unsigned long long* bin = S.beta + ((int64_t)b * 2 + (t & 1)) * S.Q;
-    const uint32_t tin = tag_base + (uint32_t)p;
-    const int32_t e0 = __ldg(Lb.seg_pos + sg), e1 = e0 + __ldg(Lb.seg_len + sg);
-    float m = neg_inf(), sum = 0.f;
-    if (et != neg_inf()) {
-      for (int32_t e = e0; e < e1; ++e) {
-        const int32_t d = __ldg(Lb.other + e);
-        const float ub = (t == n) ? __ldg(S.theta_f + d) : tagged_value(__ldg(bin + d), tin);
-        if (ub != neg_inf()) lse_push(m, sum, __ldg(Lb.theta + e) + (ub - et));
+    const bool act = j < R1;
+    int32_t q = 0, e0 = 0, len = 0;
+    TokCtx me{0, 0, 0.f, 0.f};
+    int32_t n = 0;
+    if (act) {
+      const Entry x = step_entry(T, V, S.bslot_base, k0, j);
+      me.p = x.p;
+      me.b = __ldg(T.b + x.p);
+      n = S.bw_n[me.b];
+      me.sh = (t == n) ? 0.f : decode_max(S.ekey[x.p]);
+      const int32_t sg = S.stage[__ldg(T.stb + x.p) + x.i];
+      q = __ldg(Lb.seg_state + sg);
+      untouch(S.touch + (int64_t)me.b * S.W, q);
+      if (me.sh != neg_inf()) {
+        e0 = __ldg(Lb.seg_pos + sg);
+        len = __ldg(Lb.seg_len + sg);
       }
     }
-    const float u = lse_value(m, sum);
+    auto value = [&](int32_t e, const TokCtx& c) {
+      const int32_t d = __ldg(Lb.other + e);
+      const float ub = (t == S.bw_n[c.b]) ? __ldg(S.theta_f + d)
+                                          : tagged_value(__ldg(S.beta + ((int64_t)c.b * 2 + (t & 1)) * S.Q + d),
+                                                         tag_base + (uint32_t)c.p);
+      return ub == neg_inf() ? neg_inf() : __ldg(Lb.theta + e) + (ub - c.sh);
+    };
+    me.m = flat_reduce<MaxF>(e0, len, me, value);
+    const unsigned long long su = flat_reduce<SumU>(
+        e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
+    if (!act) continue;
+    const float u = fix_log_sum(me.m, su);
     if (u != neg_inf()) {
-      S.beta[((int64_t)b * 2 + ((t - 1) & 1)) * S.Q + q] = tagged_make(u, tag_base + (uint32_t)(p - 1));
-      atomicMax(S.ekey + p - 1, fkey(u));
+      S.beta[((int64_t)me.b * 2 + ((t - 1) & 1)) * S.Q + q] = tagged_make(u, tag_base + (uint32_t)(me.p - 1));
+      atomicMax(S.ekey + me.p - 1, fkey(u));
     }
   }
 }
