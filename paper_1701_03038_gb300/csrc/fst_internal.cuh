@@ -51,6 +51,10 @@ struct Layout {
   int32_t* seg_pos = nullptr;    // [nseg] padded start position
   int32_t* seg_len = nullptr;    // [nseg] arcs in the segment
   int32_t* xseg = nullptr;       // [P] segment of the other layout holding the same arc (-1 on padding)
+  // (symbol, state) -> segment, open addressing: slot = {key, segment};
+  // key = symbol << 32 | state, empty slots hold ~0
+  ulonglong2* seg_hash = nullptr;
+  int64_t hash_mask = 0;
   int64_t* sym_win = nullptr;    // [m+1]
   int64_t* sym_seg = nullptr;    // [m+1]
   int64_t* sym_lseg = nullptr;   // [m+1] long segments
@@ -122,6 +126,14 @@ int radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaSt
 // Exclusive scan of n int64 values (out may alias in); *total gets the sum (host).
 int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, cudaStream_t s);
 int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+
+// Slot of key k in a power-of-two table (Fibonacci hashing).
+__host__ __device__ __forceinline__ uint64_t seg_hash_slot(uint64_t k, int64_t mask) {
+  return (k * 0x9E3779B97F4A7C15ull >> 17) & (uint64_t)mask;
+}
+__host__ __device__ __forceinline__ uint64_t seg_hash_key(int32_t sym, int32_t state) {
+  return ((uint64_t)(uint32_t)sym << 32) | (uint64_t)(uint32_t)state;
+}
 
 // Device memory helpers (plain cudaMalloc; every buffer is owned by a handle).
 template <class T>

@@ -45,7 +45,6 @@ constexpr int FT = 256;  // threads per block of the final reductions
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
 __device__ __forceinline__ int32_t warp_id_global() { return (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
-__device__ __forceinline__ int32_t warps_total() { return (int32_t)((gridDim.x * blockDim.x) >> 5); }
 
 __device__ __forceinline__ float decode_max(uint32_t k) { return k ? fkey_inv(k) : neg_inf(); }
 
@@ -71,16 +70,19 @@ __device__ __forceinline__ int32_t lane_owner(const int64_t* __restrict__ base, 
   return k;
 }
 
-// Segment (a, q) of a layout: binary search over the symbol's segments,
-// which are sorted by segment state; -1 when q has no arc on a there.
+// Segment (a, q) of the source-segmented layout: a lookup in its
+// open-addressing table (load factor <= 1/2, one 16-byte probe on average);
+// -1 when q has no arc on a.
 __device__ __forceinline__ int64_t find_seg(const LayoutView& L, int32_t a, int32_t q) {
-  int64_t lo = __ldg(L.sym_seg + a), hi = __ldg(L.sym_seg + a + 1);
-  const int64_t end = hi;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (__ldg(L.seg_state + mid) < q) lo = mid + 1; else hi = mid;
+  const uint64_t k = seg_hash_key(a, q);
+  uint64_t h = seg_hash_slot(k, L.hash_mask);
+  for (int64_t probe = 0; probe <= L.hash_mask; ++probe) {
+    const ulonglong2 e = __ldg(L.seg_hash + h);
+    if (e.x == k) return (int64_t)e.y;
+    if (e.x == ~0ull) return -1;
+    h = (h + 1) & (uint64_t)L.hash_mask;
   }
-  return (lo < end && __ldg(L.seg_state + lo) == q) ? lo : -1;
+  return -1;
 }
 
 // Touch q in string bitmap tb: true for the first toucher only.
@@ -97,14 +99,17 @@ __device__ __forceinline__ void untouch(uint32_t* tb, int32_t q) { atomicAnd(tb 
 // the end.  The tokens from the first whose range would pass `cap` on get
 // empty ranges (slot base INT64_MAX, so no flat index maps to them) and
 // raise error bit 1: every status of the run then reports FST_ERR_OOM.
-// Each thread scans a run of consecutive slots, then the block scans the
-// run totals (two warp levels).
+// Each thread takes RPT consecutive slots (their loads issued together),
+// then the block scans the thread totals (two warp levels); RPT * KT slots
+// per round.
+constexpr int RPT = 16;
+
 __device__ void ranges_last_block(const TokenView& T, const StepView& V, const FrontierState& S,
                                   const uint32_t* cnt, int64_t* top, int64_t cap, int64_t* slot_out,
                                   int64_t* base_out, int32_t* cnt_out, int64_t* rng_out) {
   __shared__ int last;
   __shared__ long long wsum[KT / 32];
-  __shared__ long long first_bad;
+  __shared__ long long first_bad, carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   __threadfence();
@@ -113,35 +118,55 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
   if (!last) return;
   __threadfence();
   const long long begin = top ? (long long)__ldcg(top) : 0ll;
-  if (threadIdx.x == 0) first_bad = (long long)INT64_MAX;
-  const int32_t per = (V.n + KT - 1) / KT;
-  const int32_t k0 = (int32_t)threadIdx.x * per, k1 = min(V.n, k0 + per);
-  long long run = 0;
-  for (int32_t k = k0; k < k1; ++k) run += (long long)__ldcg(cnt + __ldg(T.step_tok + V.slot0 + k));
-  long long incl = run;
+  if (threadIdx.x == 0) {
+    first_bad = (long long)INT64_MAX;
+    carry = begin;
+  }
+  __syncthreads();
+  for (int32_t c = 0; c < V.n; c += KT * RPT) {
+    const int32_t k0 = c + (int32_t)threadIdx.x * RPT;
+    int32_t pv[RPT];
+    long long mv[RPT];
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const long long o = __shfl_up_sync(FULL, incl, d);
-    if (lane >= d) incl += o;
+    for (int i = 0; i < RPT; ++i) pv[i] = k0 + i < V.n ? __ldg(T.step_tok + V.slot0 + k0 + i) : -1;
+    long long run = 0;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      mv[i] = pv[i] >= 0 ? (long long)__ldcg(cnt + pv[i]) : 0ll;
+      run += mv[i];
+    }
+    long long incl = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long o = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += o;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    long long base = carry, round = 0;
+#pragma unroll
+    for (int w = 0; w < KT / 32; ++w) {
+      base += w < warp ? wsum[w] : 0ll;
+      round += wsum[w];
+    }
+    base += incl - run;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      if (pv[i] < 0) continue;
+      const long long m = mv[i];
+      const bool fit = base + m <= (long long)cap;
+      if (!fit) atomicMin(&first_bad, base);
+      slot_out[V.slot0 + k0 + i] = fit ? base : INT64_MAX;
+      if (base_out) base_out[pv[i]] = fit ? base : 0;
+      if (cnt_out) cnt_out[pv[i]] = fit ? (int32_t)m : 0;
+      base += m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += round;
+    __syncthreads();
   }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  long long wbase = 0;
-  for (int w = 0; w < warp; ++w) wbase += wsum[w];
-  long long base = begin + wbase + incl - run;
-  for (int32_t k = k0; k < k1; ++k) {
-    const int32_t p = __ldg(T.step_tok + V.slot0 + k);
-    const long long m = (long long)__ldcg(cnt + p);
-    const bool fit = base + m <= (long long)cap;
-    if (!fit) atomicMin(&first_bad, base);
-    slot_out[V.slot0 + k] = fit ? base : INT64_MAX;
-    if (base_out) base_out[p] = fit ? base : 0;
-    if (cnt_out) cnt_out[p] = fit ? (int32_t)m : 0;
-    base += m;
-  }
-  __syncthreads();
-  if (threadIdx.x == KT - 1) {
-    const long long end = base < first_bad ? base : first_bad;
+  if (threadIdx.x == 0) {
+    const long long end = carry < first_bad ? carry : first_bad;
     if (first_bad != (long long)INT64_MAX) atomicOr(S.flags + 1, 1u);
     rng_out[0] = begin;
     rng_out[1] = end;
@@ -151,81 +176,118 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
 }
 
 // ======================================================================
-// Warp-flattened arc walks.  Lane i owns the arcs [e0_i, e0_i + len_i) of
-// one segment; the warp visits the arcs of all 32 lanes 32 at a time, in
-// lane order, so that a long segment (a hub state) spreads over the warp
-// instead of holding up one lane.
+// Block-flattened arc walks.  Thread i of a block owns the arcs
+// [e0_i, e0_i + len_i) of one segment; the block visits the arcs of all its
+// threads 256 at a time, so a hub's segment (hundreds of arcs out of one
+// state on one symbol) spreads over the block instead of holding up one
+// thread.  Reductions go through shared-memory atomics on order-independent
+// operations (max, integer add), so their results do not depend on which
+// thread met which arc.
 // ======================================================================
-struct Flat {
-  int32_t excl;   // arcs of lower lanes
-  int32_t total;  // arcs of the warp
+template <class Ctx>
+struct BlockScratch {
+  int32_t excl[KT];   // first flat arc of each thread's segment
+  int32_t e0[KT];
+  int32_t wsum[KT / 32];
+  unsigned long long acc[KT];
+  Ctx ctx[KT];
 };
-__device__ __forceinline__ Flat flat_prefix(int32_t len) {
-  const int lane = threadIdx.x & 31;
+
+// Exclusive prefix of len over the block; *total gets the sum.
+__device__ __forceinline__ int32_t block_excl(int32_t len, int32_t* wsum, int32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t incl = len;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int32_t o = __shfl_up_sync(FULL, incl, d);
     if (lane >= d) incl += o;
   }
-  return Flat{incl - len, __shfl_sync(FULL, incl, 31)};
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  int32_t base = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < KT / 32; ++w) {
+    const int32_t x = wsum[w];
+    base += w < warp ? x : 0;
+    tot += x;
+  }
+  *total = tot;
+  return base + incl - len;
 }
-// Lane owning flat arc a: the last lane whose first flat arc is <= a.
-__device__ __forceinline__ int flat_owner(int32_t excl, int32_t a) {
+
+// Thread owning flat arc a: the last thread whose first flat arc is <= a.
+__device__ __forceinline__ int block_owner(const int32_t* excl, int32_t a) {
   int o = 0;
 #pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
-    const int32_t ex = __shfl_sync(FULL, excl, o + step);
-    if (ex <= a) o += step;
-  }
+  for (int step = KT / 2; step >= 1; step >>= 1)
+    if (excl[o + step] <= a) o += step;
   return o;
 }
-// Tail lane, in the round of flat arcs [r, r+32), of the run of this lane's
-// own segment; -1 when the segment has no arc in the round.
-__device__ __forceinline__ int flat_tail(const Flat& F, int32_t len, int32_t r) {
-  if (len <= 0 || F.excl >= r + 32 || F.excl + len <= r) return -1;
-  return min(F.excl + len, r + 32) - 1 - r;
-}
-// Inclusive segmented scan over lanes of `v` (runs of equal owner `o`).
-template <class Op>
-__device__ __forceinline__ typename Op::T run_scan(typename Op::T v, int o) {
-  const int lane = threadIdx.x & 31;
-  const int o_prev = __shfl_up_sync(FULL, o, 1);  // every lane shuffles: no short-circuit before it
-  const bool head = (lane == 0) || (o_prev != o);
-  const uint32_t hm = __ballot_sync(FULL, head) & (0xffffffffu >> (31 - lane));
-  const int start = 31 - __clz(hm);
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const typename Op::T u = Op::shfl_up(v, d);
-    if (lane - d >= start) v = Op::combine(u, v);
+
+// visit(e, ctx) for every arc of every thread's segment.
+template <class Ctx, class F>
+__device__ __forceinline__ void block_visit(BlockScratch<Ctx>& sh, int32_t e0, int32_t len, const Ctx& mine,
+                                            F visit) {
+  int32_t total;
+  const int32_t ex = block_excl(len, sh.wsum, &total);
+  sh.excl[threadIdx.x] = ex;
+  sh.e0[threadIdx.x] = e0;
+  sh.ctx[threadIdx.x] = mine;
+  __syncthreads();
+  for (int32_t a = threadIdx.x; a < total; a += KT) {
+    const int o = block_owner(sh.excl, a);
+    visit(sh.e0[o] + (a - sh.excl[o]), sh.ctx[o]);
   }
-  return v;
+  __syncthreads();
 }
 
-struct MaxKey {
+// Reductions over each thread's segment: Op maps a value to a 64-bit key,
+// combines keys atomically and maps the result back.
+struct RedKey {  // Viterbi: max of packed (score, ~position) keys
   typedef unsigned long long T;
-  static __device__ __forceinline__ T identity() { return 0ull; }
-  static __device__ __forceinline__ T combine(T a, T b) { return a > b ? a : b; }
-  static __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(FULL, v, d); }
-  static __device__ __forceinline__ T shfl(T v, int l) { return __shfl_sync(FULL, v, l); }
+  static __device__ __forceinline__ unsigned long long key(T v) { return v; }
+  static __device__ __forceinline__ T value(unsigned long long k) { return k; }
+  static __device__ __forceinline__ void atomic(unsigned long long* a, unsigned long long k) { if (k) atomicMax(a, k); }
 };
-struct MaxF {
+struct RedMax {  // max of floats through their order-preserving keys (0 = nothing)
   typedef float T;
-  static __device__ __forceinline__ T identity() { return __int_as_float(0xff800000); }
-  static __device__ __forceinline__ T combine(T a, T b) { return fmaxf(a, b); }
-  static __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(FULL, v, d); }
-  static __device__ __forceinline__ T shfl(T v, int l) { return __shfl_sync(FULL, v, l); }
+  static __device__ __forceinline__ unsigned long long key(T v) {
+    return v == __int_as_float(0xff800000) ? 0ull : (unsigned long long)fkey(v);
+  }
+  static __device__ __forceinline__ T value(unsigned long long k) {
+    return k ? fkey_inv((uint32_t)k) : __int_as_float(0xff800000);
+  }
+  static __device__ __forceinline__ void atomic(unsigned long long* a, unsigned long long k) { if (k) atomicMax(a, k); }
 };
-struct SumU {
+struct RedSum {  // exact integer sum
   typedef unsigned long long T;
-  static __device__ __forceinline__ T identity() { return 0ull; }
-  static __device__ __forceinline__ T combine(T a, T b) { return a + b; }
-  static __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(FULL, v, d); }
-  static __device__ __forceinline__ T shfl(T v, int l) { return __shfl_sync(FULL, v, l); }
+  static __device__ __forceinline__ unsigned long long key(T v) { return v; }
+  static __device__ __forceinline__ T value(unsigned long long k) { return k; }
+  static __device__ __forceinline__ void atomic(unsigned long long* a, unsigned long long k) { if (k) atomicAdd(a, k); }
 };
+
+template <class Op, class Ctx, class F>
+__device__ __forceinline__ typename Op::T block_reduce(BlockScratch<Ctx>& sh, int32_t e0, int32_t len,
+                                                       const Ctx& mine, F value) {
+  int32_t total;
+  const int32_t ex = block_excl(len, sh.wsum, &total);
+  sh.excl[threadIdx.x] = ex;
+  sh.e0[threadIdx.x] = e0;
+  sh.ctx[threadIdx.x] = mine;
+  sh.acc[threadIdx.x] = 0ull;
+  __syncthreads();
+  for (int32_t a = threadIdx.x; a < total; a += KT) {
+    const int o = block_owner(sh.excl, a);
+    Op::atomic(&sh.acc[o], Op::key(value(sh.e0[o] + (a - sh.excl[o]), sh.ctx[o])));
+  }
+  __syncthreads();
+  const typename Op::T r = Op::value(sh.acc[threadIdx.x]);
+  __syncthreads();
+  return r;
+}
 
 // exp(v - m), v <= m, as a 2^-40 fixed-point integer: sums of these are exact
-// and so independent of the order in which the warp happens to add them
+// and so independent of the order in which the block happens to add them
 constexpr double FIX_ONE = 1099511627776.0;  // 2^40
 __device__ __forceinline__ unsigned long long fix_exp(float v, float m) {
   return v == __int_as_float(0xff800000) ? 0ull : __double2ull_rn((double)__expf(v - m) * FIX_ONE);
@@ -235,54 +297,11 @@ __device__ __forceinline__ float fix_log_sum(float m, unsigned long long s) {
                                                         : m + (float)log((double)s / FIX_ONE);
 }
 
-// Reduce the arcs of every lane's segment with Op; value(e, o) gives the
-// value of arc e owned by lane o (it must not use warp collectives: lane
-// data of the owner is fetched by the caller through `ctx` shuffles).
-template <class Op, class Ctx, class F>
-__device__ __forceinline__ typename Op::T flat_reduce(int32_t e0, int32_t len, const Ctx& mine, F value) {
-  const int lane = threadIdx.x & 31;
-  const Flat F0 = flat_prefix(len);
-  typename Op::T acc = Op::identity();
-  for (int32_t r = 0; r < F0.total; r += 32) {
-    const int32_t a = r + lane;
-    const bool act = a < F0.total;
-    const int o = flat_owner(F0.excl, act ? a : F0.total - 1);
-    const int32_t ex_o = __shfl_sync(FULL, F0.excl, o), e0_o = __shfl_sync(FULL, e0, o);
-    const Ctx c = mine.shfl(o);
-    typename Op::T v = act ? value(e0_o + (a - ex_o), c) : Op::identity();
-    v = run_scan<Op>(v, o);
-    const int tail = flat_tail(F0, len, r);
-    const typename Op::T run = Op::shfl(v, tail < 0 ? 0 : tail);
-    if (tail >= 0) acc = Op::combine(acc, run);
-    (void)lane;
-  }
-  return acc;
-}
-
-// Visit the arcs of every lane's segment: visit(e, o) per arc.
-template <class Ctx, class F>
-__device__ __forceinline__ void flat_visit(int32_t e0, int32_t len, const Ctx& mine, F visit) {
-  const int lane = threadIdx.x & 31;
-  const Flat F0 = flat_prefix(len);
-  for (int32_t r = 0; r < F0.total; r += 32) {
-    const int32_t a = r + lane;
-    const bool act = a < F0.total;
-    const int o = flat_owner(F0.excl, act ? a : F0.total - 1);
-    const int32_t ex_o = __shfl_sync(FULL, F0.excl, o), e0_o = __shfl_sync(FULL, e0, o);
-    const Ctx c = mine.shfl(o);
-    if (act) visit(e0_o + (a - ex_o), c);
-  }
-}
-
-// Per-lane context the arc walks need from the owner lane.
+// Per-thread context the arc walks need from the owner thread.
 struct TokCtx {
   int32_t p, b;
   float sh;  // a step shift (forward m_{t-1} or backward e_t), or unused
   float m;   // the segment's maximum (second pass of a log-sum-exp)
-  __device__ __forceinline__ TokCtx shfl(int o) const {
-    return TokCtx{__shfl_sync(FULL, p, o), __shfl_sync(FULL, b, o), __shfl_sync(FULL, sh, o),
-                  __shfl_sync(FULL, m, o)};
-  }
 };
 
 // ======================================================================
@@ -291,10 +310,12 @@ struct TokCtx {
 // token that reads w_t), or every start state for every token at t = 1.
 // ======================================================================
 __global__ void __launch_bounds__(KT) k_expand(LayoutView Lb, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<TokCtx> sh;
   const int lane = threadIdx.x & 31;
   const int64_t R0 = V.t == 1 ? 0 : S.step_rng[2 * V.x_t];
   const int64_t R1 = V.t == 1 ? (int64_t)V.n * S.nstart : S.step_rng[2 * V.x_t + 1];
-  for (int64_t c0 = R0 + (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
+  for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
+    const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
     const int64_t j = c0 + lane;
     int32_t p = -1, q = -1;
     if (V.t == 1) {
@@ -324,7 +345,7 @@ __global__ void __launch_bounds__(KT) k_expand(LayoutView Lb, TokenView T, StepV
         me.b = __ldg(T.b + p);
       }
     }
-    flat_visit(e0, len, me, [&](int32_t e, const TokCtx& c) {
+    block_visit(sh, e0, len, me, [&](int32_t e, const TokCtx& c) {
       const int32_t d = __ldg(Lb.other + e);
       if (touch_first(S.touch + (int64_t)c.b * S.W, d))
         S.stage[__ldg(T.stf + c.p) + atomicAdd(S.scnt_f + c.p, 1u)] = __ldg(Lb.xseg + e);
@@ -351,10 +372,12 @@ __device__ __forceinline__ Entry step_entry(const TokenView& T, const StepView& 
 // Viterbi reduce (Alg. 1 inner max; Sec. 5.1): pool entry j of position t.
 // ======================================================================
 __global__ void __launch_bounds__(KT) k_vit_reduce(LayoutView Lf, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<TokCtx> sh;
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
   const int64_t R0 = S.step_rng[2 * V.t], R1 = S.step_rng[2 * V.t + 1];
-  for (int64_t c0 = R0 + (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
+  for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
+    const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
     const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
     const bool act = j < R1;
@@ -370,7 +393,7 @@ __global__ void __launch_bounds__(KT) k_vit_reduce(LayoutView Lf, TokenView T, S
       e0 = __ldg(Lf.seg_pos + sg);
       len = __ldg(Lf.seg_len + sg);
     }
-    const unsigned long long best = flat_reduce<MaxKey>(e0, len, me, [&](int32_t e, const TokCtx& c) {
+    const unsigned long long best = block_reduce<RedKey>(sh, e0, len, me, [&](int32_t e, const TokCtx& c) {
       const int32_t q = __ldg(Lf.other + e);
       const float a = (V.t == 1) ? __ldg(S.theta_s + q)
                                  : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((V.t - 1) & 1)) * S.Q + q),
@@ -393,10 +416,12 @@ __global__ void __launch_bounds__(KT) k_vit_reduce(LayoutView Lf, TokenView T, S
 // the previous step's maximum m_{t-1}; the stored value r_t is unshifted.
 // ======================================================================
 __global__ void __launch_bounds__(KT) k_fwd_reduce(LayoutView Lf, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<TokCtx> sh;
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
   const int64_t R0 = S.step_rng[2 * V.t], R1 = S.step_rng[2 * V.t + 1];
-  for (int64_t c0 = R0 + (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
+  for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
+    const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
     const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
     const bool act = j < R1;
@@ -424,9 +449,9 @@ __global__ void __launch_bounds__(KT) k_fwd_reduce(LayoutView Lf, TokenView T, S
     };
     // log-sum-exp in two order-independent passes: max, then the
     // fixed-point sum of exp(v - max)
-    me.m = flat_reduce<MaxF>(e0, len, me, value);
-    const unsigned long long su = flat_reduce<SumU>(
-        e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
+    me.m = block_reduce<RedMax>(sh, e0, len, me, value);
+    const unsigned long long su = block_reduce<RedSum>(
+        sh, e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
     if (!act) continue;
     const float r = fix_log_sum(me.m, su);
     if (r != neg_inf()) {
@@ -468,19 +493,17 @@ struct BwdCtx {
   int32_t p, b;
   float mprev, gw;
   double off;
-  __device__ __forceinline__ BwdCtx shfl(int o) const {
-    return BwdCtx{__shfl_sync(FULL, p, o), __shfl_sync(FULL, b, o), __shfl_sync(FULL, mprev, o),
-                  __shfl_sync(FULL, gw, o), __shfl_sync(FULL, off, o)};
-  }
 };
 
 __global__ void __launch_bounds__(KT) k_bwd_expand(LayoutView Lf, TokenView T, StepView V, FrontierState S,
                                                    CountView C) {
+  __shared__ BlockScratch<BwdCtx> sh;
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
   const int32_t t = V.t;
   const int64_t R0 = S.step_rng[2 * t], R1 = S.step_rng[2 * t + 1];
-  for (int64_t c0 = R0 + (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
+  for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
+    const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
     const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
     int32_t e0 = 0, len = 0;
@@ -509,7 +532,7 @@ __global__ void __launch_bounds__(KT) k_bwd_expand(LayoutView Lf, TokenView T, S
         }
       }
     }
-    flat_visit(e0, len, me, [&](int32_t e, const BwdCtx& c) {
+    block_visit(sh, e0, len, me, [&](int32_t e, const BwdCtx& c) {
       const int32_t src = __ldg(Lf.other + e);
       const float ra = (t == 1) ? __ldg(S.theta_s + src)
                                 : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((t - 1) & 1)) * S.Q + src),
@@ -536,12 +559,14 @@ __global__ void __launch_bounds__(KT) k_bwd_expand(LayoutView Lf, TokenView T, S
 // the next backward expand needs them.
 // ======================================================================
 __global__ void __launch_bounds__(KT) k_bwd_reduce(LayoutView Lb, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<TokCtx> sh;
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
   const int32_t t = V.t;
   if (V.x_n > 0) {
     const int64_t R0 = S.step_rng[2 * V.x_t], R1 = S.step_rng[2 * V.x_t + 1];
-    for (int64_t c0 = R0 + (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
+    for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
+      const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);
       const int64_t* base = S.slot_base + V.x_slot0;
       const int32_t k0 = warp_owner(base, V.x_n, c0);
       const int64_t j = c0 + lane;
@@ -554,7 +579,8 @@ __global__ void __launch_bounds__(KT) k_bwd_reduce(LayoutView Lb, TokenView T, S
     }
   }
   const int64_t R1 = S.bstep_rng[2 * t + 1];
-  for (int64_t c0 = (int64_t)warp_id_global() * 32; c0 < R1; c0 += (int64_t)warps_total() * 32) {
+  for (int64_t cb = (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
+    const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);
     const int32_t k0 = warp_owner(S.bslot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
     const bool act = j < R1;
@@ -582,9 +608,9 @@ __global__ void __launch_bounds__(KT) k_bwd_reduce(LayoutView Lb, TokenView T, S
                                                          tag_base + (uint32_t)c.p);
       return ub == neg_inf() ? neg_inf() : __ldg(Lb.theta + e) + (ub - c.sh);
     };
-    me.m = flat_reduce<MaxF>(e0, len, me, value);
-    const unsigned long long su = flat_reduce<SumU>(
-        e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
+    me.m = block_reduce<RedMax>(sh, e0, len, me, value);
+    const unsigned long long su = block_reduce<RedSum>(
+        sh, e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
     if (!act) continue;
     const float u = fix_log_sum(me.m, su);
     if (u != neg_inf()) {

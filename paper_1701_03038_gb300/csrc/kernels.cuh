@@ -17,10 +17,13 @@ struct LayoutView {
   const int32_t* seg_len;    // [nseg] arcs
   const int64_t* sym_seg;    // [m+1] segments of each input symbol
   const int32_t* xseg;       // [P] segment of the other layout holding the same arc
+  const ulonglong2* seg_hash;  // (symbol, state) -> segment (source-segmented layout only)
+  int64_t hash_mask;
 };
 
 inline LayoutView view_of(const Layout& L) {
-  return LayoutView{L.other, L.theta, L.arc_id, L.seg_state, L.seg_pos, L.seg_len, L.sym_seg, L.xseg};
+  return LayoutView{L.other, L.theta, L.arc_id, L.seg_state, L.seg_pos, L.seg_len, L.sym_seg, L.xseg,
+                    L.seg_hash, L.hash_mask};
 }
 
 // The tokens of one input position t: slots slot0 .. slot0+n-1 of the

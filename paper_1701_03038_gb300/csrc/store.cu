@@ -143,6 +143,29 @@ __global__ void k_seg_of(const int32_t* __restrict__ seg_pos, const int32_t* __r
   for (int32_t i = 0; i < seg_len[sg]; ++i) segof[p0 + i] = (int32_t)sg;
 }
 
+// Insert every segment (symbol, state) -> index into the open-addressing
+// table; one thread per symbol's segment range entry.
+__global__ void k_hash_insert(const int64_t* __restrict__ sym_seg, int32_t m, const int32_t* __restrict__ seg_state,
+                              int64_t nseg, ulonglong2* __restrict__ tab, int64_t mask) {
+  const int64_t sg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sg >= nseg) return;
+  int32_t lo = 0, hi = m;  // symbol of segment sg: last a with sym_seg[a] <= sg
+  while (hi - lo > 1) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (sym_seg[mid] <= sg) lo = mid; else hi = mid;
+  }
+  const uint64_t k = seg_hash_key(lo, seg_state[sg]);
+  uint64_t h = seg_hash_slot(k, mask);
+  for (int64_t probe = 0; probe <= mask; ++probe) {
+    const unsigned long long old = atomicCAS(&tab[h].x, ~0ull, (unsigned long long)k);
+    if (old == ~0ull || old == k) {
+      tab[h].y = (unsigned long long)sg;
+      return;
+    }
+    h = (h + 1) & (uint64_t)mask;
+  }
+}
+
 // xseg[i] = segment of the other layout that holds the arc at position i
 __global__ void k_xseg(const int32_t* __restrict__ arc_id, int64_t P, const int32_t* __restrict__ pos_by_id_other,
                        const int32_t* __restrict__ segof_other, int32_t* __restrict__ xseg) {
@@ -346,7 +369,7 @@ int build_layout(fst_s* f, Layout& L, const int32_t* d_il, const int32_t* seg_st
 
 void free_layout(Layout& L) {
   dfree(L.other); dfree(L.theta); dfree(L.arc_id); dfree(L.theta64); dfree(L.win);
-  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.seg_len); dfree(L.xseg); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
+  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.seg_len); dfree(L.xseg); dfree(L.seg_hash); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
   dfree(L.sym_lwin);
   free(L.h_sym_win); free(L.h_sym_seg); free(L.h_sym_lseg); free(L.h_sym_lwin);
   L.h_sym_win = L.h_sym_seg = L.h_sym_lseg = L.h_sym_lwin = nullptr;
@@ -387,6 +410,19 @@ int build_store(fst_s* f, const int32_t* d_src, const int32_t* d_dst, const int3
   }
   release();
   if (e != cudaSuccess) return cuda_fail(e, "segments of the other layout");
+  // (symbol, state) -> segment of the source-segmented layout: the expand
+  // kernels find a live state's arcs on a symbol with about one probe
+  {
+    Layout& L = f->bwd;
+    int64_t size = 2;
+    while (size < 2 * std::max<int64_t>(L.nseg, 1)) size <<= 1;
+    if ((rc = dalloc(&L.seg_hash, size))) return rc;
+    L.hash_mask = size - 1;
+    FST_CUDA(cudaMemsetAsync(L.seg_hash, 0xff, (size_t)size * sizeof(ulonglong2), s));
+    if (L.nseg > 0)
+      k_hash_insert<<<blocks_for(L.nseg), TB, 0, s>>>(L.sym_seg, f->m, L.seg_state, L.nseg, L.seg_hash, L.hash_mask);
+    FST_CUDA(cudaStreamSynchronize(s));
+  }
   return FST_OK;
 }
 
