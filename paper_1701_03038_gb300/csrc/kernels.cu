@@ -102,7 +102,7 @@ __device__ __forceinline__ void untouch(uint32_t* tb, int32_t q) { atomicAnd(tb 
 // Each thread takes RPT consecutive slots (their loads issued together),
 // then the block scans the thread totals (two warp levels); RPT * KT slots
 // per round.
-constexpr int RPT = 16;
+constexpr int RPT = 4;
 
 __device__ void ranges_last_block(const TokenView& T, const StepView& V, const FrontierState& S,
                                   const uint32_t* cnt, int64_t* top, int64_t cap, int64_t* slot_out,
