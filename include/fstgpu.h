@@ -225,12 +225,12 @@ FST_API int fst_log_z_f64(fst_t* fst, const double* theta, const int32_t* ids, i
  * device time in milliseconds and the number of launches since the last
  * read (host arrays of FST_PROF_KINDS entries, either may be NULL), then
  * starts a new accumulation.  Do not enable it while capturing a graph. */
-#define FST_PROF_VIT_EXPAND 0  /* Viterbi: live states of t-1 stage the segments to reduce */
-#define FST_PROF_VIT_REDUCE 1  /* Viterbi: staged destination segments reduced (max, backpointer) */
+#define FST_PROF_VIT_FIRST 0   /* Viterbi: start states stage the first position's segments */
+#define FST_PROF_VIT_STEP 1    /* Viterbi: one position reduced (max, backpointer) and expanded into the next */
 #define FST_PROF_VIT_FINAL 2   /* Viterbi final reduction */
 #define FST_PROF_BACKTRACE 3   /* Viterbi backtrace */
-#define FST_PROF_FWD_EXPAND 4  /* forward: live states of t-1 stage the segments to reduce */
-#define FST_PROF_FWD_REDUCE 5  /* forward: staged destination segments reduced (log-sum-exp) */
+#define FST_PROF_FWD_FIRST 4   /* forward: start states stage the first position's segments */
+#define FST_PROF_FWD_STEP 5    /* forward: one position reduced (log-sum-exp) and expanded into the next */
 #define FST_PROF_FB_FINAL 6    /* log Z and the float64 normaliser prefix */
 #define FST_PROF_BWD_EXPAND 7  /* backward: posteriors into the live states of t, sources staged */
 #define FST_PROF_BWD_REDUCE 8  /* backward: staged source segments reduced; forward values of t-2 restored */

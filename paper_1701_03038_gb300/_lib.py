@@ -47,7 +47,7 @@ SIGNATURES = {
     "fst_log_z_f64": [vp, vp, vp, i32, vp],
 }
 
-PROF_KINDS = ["vit_expand", "vit_reduce", "vit_final", "backtrace", "fwd_expand", "fwd_reduce", "fb_final",
+PROF_KINDS = ["vit_first", "vit_step", "vit_final", "backtrace", "fwd_first", "fwd_step", "fb_final",
               "bwd_expand", "bwd_reduce", "counts"]
 
 

@@ -135,6 +135,7 @@ struct PlainWs {
   unsigned long long* alpha = nullptr;  // [2][Q]
   unsigned long long* beta = nullptr;   // [2][Q]
   uint32_t* touch = nullptr;            // [W]
+  uint32_t* touch_b = nullptr;          // [W] second touch bitmap (odd positions, forward passes)
   int32_t *tok_sym = nullptr, *tok_b = nullptr;
   int32_t* iota = nullptr;              // step list: token t-1 is the only slot of position t
   int64_t* zero64 = nullptr;            // staging offsets: one token per step
@@ -146,7 +147,7 @@ struct PlainWs {
   double *csum = nullptr, *esum = nullptr;
   int32_t *paths = nullptr, *olabels = nullptr;
   int64_t cap_n = 0;
-  int32_t* stage = nullptr;
+  int32_t *stage = nullptr, *stage_b = nullptr;
   int64_t cap_stage = 0;
   int32_t *pool_q = nullptr, *pool_x = nullptr;
   float* pool_v = nullptr;
@@ -159,10 +160,10 @@ struct PlainWs {
   int64_t* pool_top = nullptr;
   uint32_t *flags = nullptr, *epoch = nullptr, *clear = nullptr;
   ~PlainWs() {
-    dfree(alpha); dfree(beta); dfree(touch); dfree(tok_sym); dfree(tok_b); dfree(iota); dfree(zero64);
+    dfree(alpha); dfree(beta); dfree(touch); dfree(touch_b); dfree(tok_sym); dfree(tok_b); dfree(iota); dfree(zero64);
     dfree(slot_base); dfree(bslot_base); dfree(step_rng); dfree(bstep_rng); dfree(scnt_f);
     dfree(scnt_b); dfree(pool_base); dfree(pool_cnt); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum);
-    dfree(paths); dfree(olabels); dfree(stage); dfree(pool_q); dfree(pool_x); dfree(pool_v); dfree(cnt);
+    dfree(paths); dfree(olabels); dfree(stage); dfree(stage_b); dfree(pool_q); dfree(pool_x); dfree(pool_v); dfree(cnt);
     dfree(comp); dfree(counts_out); dfree(qfinal); dfree(status); dfree(bw_n); dfree(score); dfree(logz);
     dfree(bw_off); dfree(pool_top); dfree(flags); dfree(epoch); dfree(clear);
   }
@@ -177,6 +178,7 @@ int plain_init(fst_s* f) {
   const int64_t Q = f->Q;
   int rc;
   if ((rc = dalloc(&w->alpha, 2 * Q)) || (rc = dalloc(&w->beta, 2 * Q)) || (rc = dalloc(&w->touch, f->W)) ||
+      (rc = dalloc(&w->touch_b, f->W)) ||
       (rc = dalloc(&w->qfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
       (rc = dalloc(&w->logz, 1)) || (rc = dalloc(&w->bw_n, 1)) || (rc = dalloc(&w->bw_off, 1)) ||
       (rc = dalloc(&w->pool_top, 1)) || (rc = dalloc(&w->flags, 2)) || (rc = dalloc(&w->epoch, 2)) ||
@@ -185,6 +187,7 @@ int plain_init(fst_s* f) {
   FST_CUDA(cudaMemset(w->alpha, 0, (size_t)2 * Q * sizeof(unsigned long long)));
   FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(unsigned long long)));
   FST_CUDA(cudaMemset(w->touch, 0, (size_t)f->W * 4));
+  FST_CUDA(cudaMemset(w->touch_b, 0, (size_t)f->W * 4));
   FST_CUDA(cudaMemset(w->bw_off, 0, sizeof(int64_t)));
   FST_CUDA(cudaMemset(w->epoch, 0, 2 * sizeof(uint32_t)));
   return FST_OK;
@@ -223,8 +226,9 @@ int plain_reserve(PlainWs* w, int64_t n, int64_t stage, int64_t pool) {
   if (stage > w->cap_stage) {
     const int64_t c = std::max<int64_t>(stage, 2 * w->cap_stage);
     dfree(w->stage);
+    dfree(w->stage_b);
     w->cap_stage = 0;
-    if ((rc = dalloc(&w->stage, c))) return rc;
+    if ((rc = dalloc(&w->stage, c)) || (rc = dalloc(&w->stage_b, c))) return rc;
     w->cap_stage = c;
   }
   if (pool > w->cap_pool) {
@@ -263,6 +267,7 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
   FST_CUDA(cudaMemsetAsync(w->pool_top, 0, 8, s));
   FST_CUDA(cudaMemsetAsync(w->flags, 0, 8, s));
   FST_CUDA(cudaMemsetAsync(w->touch, 0, (size_t)f->W * 4, s));
+  FST_CUDA(cudaMemsetAsync(w->touch_b, 0, (size_t)f->W * 4, s));
   // fresh tags for this string
   k_epoch_advance<<<1, 1, 0, s>>>(w->epoch, (uint32_t)n + 1u, w->clear);
   k_clear_if<<<nblk(2 * (int64_t)f->Q), TB, 0, s>>>(w->clear, w->alpha, 2 * (int64_t)f->Q);
@@ -284,7 +289,9 @@ FrontierState plain_state(fst_s* f) {
   S.alpha = w->alpha;
   S.beta = w->beta;
   S.touch = w->touch;
+  S.touch_b = w->touch_b;
   S.stage = w->stage;
+  S.stage_b = w->stage_b;
   S.scnt_f = w->scnt_f;
   S.scnt_b = w->scnt_b;
   S.pool_q = w->pool_q;
@@ -524,11 +531,10 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
   const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
   const FrontierState S = plain_state(f);
-  // one launch pair per input position (Sec. 5)
-  for (int32_t t = 1; t <= n; ++t) {
-    const StepView V = plain_step(f, n, t, t - 1);
-    if ((rc = launch_expand(Lb, T, V, S, s)) || (rc = launch_vit_reduce(Lf, T, V, S, s))) return rc;
-  }
+  // one launch per input position (Sec. 5), after the first position's expand
+  if (n >= 1 && (rc = launch_expand(Lb, T, plain_step(f, n, 1, 0), S, s))) return rc;
+  for (int32_t t = 1; t <= n; ++t)
+    if ((rc = launch_vit_step(Lf, Lb, T, plain_step(f, n, t, t + 1), S, s))) return rc;
   if ((rc = launch_vit_final(S, 1, w->score, w->qfinal, w->status, s))) return rc;
   if ((rc = launch_backtrace(Lf, S, f->olabel, 1, w->qfinal, w->paths, w->olabels, s))) return rc;
   int32_t st = 0;
@@ -563,10 +569,9 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
   const FrontierState S = plain_state(f);
-  for (int32_t t = 1; t <= n; ++t) {
-    const StepView V = plain_step(f, n, t, t - 1);
-    if ((rc = launch_expand(Lb, T, V, S, s)) || (rc = launch_fwd_reduce(Lf, T, V, S, s))) return rc;
-  }
+  if (n >= 1 && (rc = launch_expand(Lb, T, plain_step(f, n, 1, 0), S, s))) return rc;
+  for (int32_t t = 1; t <= n; ++t)
+    if ((rc = launch_fwd_step(Lf, Lb, T, plain_step(f, n, t, t + 1), S, s))) return rc;
   if ((rc = launch_fb_final(S, 1, w->logz, w->status, s))) return rc;
   if (arc_posteriors) {
     const CountView C{0, w->cnt, w->comp, nullptr};

@@ -85,6 +85,11 @@ __device__ __forceinline__ int64_t find_seg(const LayoutView& L, int32_t a, int3
   return -1;
 }
 
+// Staging buffer and touch bitmap of forward position t (two of each, by
+// parity: a step reads position t's while it fills position t+1's).
+__device__ __forceinline__ int32_t* fwd_stage(const FrontierState& S, int32_t t) { return (t & 1) ? S.stage_b : S.stage; }
+__device__ __forceinline__ uint32_t* fwd_touch(const FrontierState& S, int32_t t) { return (t & 1) ? S.touch_b : S.touch; }
+
 // Touch q in string bitmap tb: true for the first toucher only.
 __device__ __forceinline__ bool touch_first(uint32_t* tb, int32_t q) {
   const uint32_t bit = 1u << (q & 31);
@@ -347,8 +352,8 @@ __global__ void __launch_bounds__(KT) k_expand(LayoutView Lb, TokenView T, StepV
     }
     block_visit(sh, e0, len, me, [&](int32_t e, const TokCtx& c) {
       const int32_t d = __ldg(Lb.other + e);
-      if (touch_first(S.touch + (int64_t)c.b * S.W, d))
-        S.stage[__ldg(T.stf + c.p) + atomicAdd(S.scnt_f + c.p, 1u)] = __ldg(Lb.xseg + e);
+      if (touch_first(fwd_touch(S, V.t) + (int64_t)c.b * S.W, d))
+        fwd_stage(S, V.t)[__ldg(T.stf + c.p) + atomicAdd(S.scnt_f + c.p, 1u)] = __ldg(Lb.xseg + e);
     });
   }
   ranges_last_block(T, V, S, S.scnt_f, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
@@ -369,57 +374,33 @@ __device__ __forceinline__ Entry step_entry(const TokenView& T, const StepView& 
 }
 
 // ======================================================================
-// Viterbi reduce (Alg. 1 inner max; Sec. 5.1): pool entry j of position t.
+// One forward position, fused (Alg. 1 inner max, Sec. 5.1; Alg. 2 forward
+// loop, Sec. 5.2): reduce the staged destination segments of position t
+// into frontier entries, then expand every new live state into the
+// segments of position t+1 (the next token of its string) right away.
 // ======================================================================
-__global__ void __launch_bounds__(KT) k_vit_reduce(LayoutView Lf, TokenView T, StepView V, FrontierState S) {
-  __shared__ BlockScratch<TokCtx> sh;
-  const int lane = threadIdx.x & 31;
-  const uint32_t tag_base = *S.epoch + S.tok0;
-  const int64_t R0 = S.step_rng[2 * V.t], R1 = S.step_rng[2 * V.t + 1];
-  for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
-    const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
-    const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
-    const int64_t j = c0 + lane;
-    const bool act = j < R1;
-    int32_t d = 0, e0 = 0, len = 0;
-    TokCtx me{0, 0, 0.f, 0.f};
-    if (act) {
-      const Entry x = step_entry(T, V, S.slot_base, k0, j);
-      me.p = x.p;
-      me.b = __ldg(T.b + x.p);
-      const int32_t sg = S.stage[__ldg(T.stf + x.p) + x.i];
-      d = __ldg(Lf.seg_state + sg);
-      untouch(S.touch + (int64_t)me.b * S.W, d);
-      e0 = __ldg(Lf.seg_pos + sg);
-      len = __ldg(Lf.seg_len + sg);
-    }
-    const unsigned long long best = block_reduce<RedKey>(sh, e0, len, me, [&](int32_t e, const TokCtx& c) {
-      const int32_t q = __ldg(Lf.other + e);
-      const float a = (V.t == 1) ? __ldg(S.theta_s + q)
-                                 : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((V.t - 1) & 1)) * S.Q + q),
-                                                tag_base + (uint32_t)(c.p - 1));
-      const float cand = __fadd_rn(a, __ldg(Lf.theta + e));
-      return cand == neg_inf() ? 0ull
-                               : (((unsigned long long)fkey(cand) << 32) | (unsigned long long)(~(uint32_t)e));
-    });
-    if (!act) continue;
-    if (best)
-      S.alpha[((int64_t)me.b * 2 + (V.t & 1)) * S.Q + d] =
-          tagged_make(fkey_inv((uint32_t)(best >> 32)), tag_base + (uint32_t)me.p);
-    S.pool_q[j] = best ? d : -1;
-    S.pool_x[j] = best ? (int32_t)(~(uint32_t)best) : -1;
-  }
+// Expand live state q (just computed for token p at position t) into the
+// segments of position t+1: returns its arcs on w_{t+1}.
+__device__ __forceinline__ void next_arcs(const LayoutView& Lb, const TokenView& T, const FrontierState& S,
+                                          int32_t t, int32_t p, int32_t b, int32_t q, int32_t* e0, int32_t* len) {
+  *e0 = 0;
+  *len = 0;
+  if (q < 0 || S.bw_n[b] <= t) return;  // dead, or the string ends at t
+  const int64_t sg = find_seg(Lb, __ldg(T.sym + p + 1), q);
+  if (sg < 0) return;
+  *e0 = __ldg(Lb.seg_pos + sg);
+  *len = __ldg(Lb.seg_len + sg);
 }
 
-// ======================================================================
-// Forward reduce (Alg. 2 forward loop; Sec. 5.2).  Inputs are shifted by
-// the previous step's maximum m_{t-1}; the stored value r_t is unshifted.
-// ======================================================================
-__global__ void __launch_bounds__(KT) k_fwd_reduce(LayoutView Lf, TokenView T, StepView V, FrontierState S) {
-  __shared__ BlockScratch<TokCtx> sh;
+template <bool FWD>
+__device__ __forceinline__ void fwd_position(const LayoutView& Lf, const LayoutView& Lb, const TokenView& T,
+                                             const StepView& V, const FrontierState& S, BlockScratch<TokCtx>& sh) {
   const int lane = threadIdx.x & 31;
   const uint32_t tag_base = *S.epoch + S.tok0;
-  const int64_t R0 = S.step_rng[2 * V.t], R1 = S.step_rng[2 * V.t + 1];
+  const int32_t t = V.t;
+  const int64_t R0 = S.step_rng[2 * t], R1 = S.step_rng[2 * t + 1];
+  const int32_t* stg = fwd_stage(S, t);
+  uint32_t* tch = fwd_touch(S, t);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
     const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
     const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
@@ -431,37 +412,92 @@ __global__ void __launch_bounds__(KT) k_fwd_reduce(LayoutView Lf, TokenView T, S
       const Entry x = step_entry(T, V, S.slot_base, k0, j);
       me.p = x.p;
       me.b = __ldg(T.b + x.p);
-      me.sh = V.t > 1 ? decode_max(S.mkey[x.p - 1]) : 0.f;
-      sg = S.stage[__ldg(T.stf + x.p) + x.i];
+      me.sh = (FWD && t > 1) ? decode_max(S.mkey[x.p - 1]) : 0.f;
+      sg = stg[__ldg(T.stf + x.p) + x.i];
       d = __ldg(Lf.seg_state + sg);
-      untouch(S.touch + (int64_t)me.b * S.W, d);
+      untouch(tch + (int64_t)me.b * S.W, d);
       if (me.sh != neg_inf()) {
         e0 = __ldg(Lf.seg_pos + sg);
         len = __ldg(Lf.seg_len + sg);
       }
     }
-    auto value = [&](int32_t e, const TokCtx& c) {
+    // the value of source q on arc e, as the previous position left it
+    auto src_value = [&](int32_t e, const TokCtx& c) {
       const int32_t q = __ldg(Lf.other + e);
-      const float a = (V.t == 1) ? __ldg(S.theta_s + q)
-                                 : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((V.t - 1) & 1)) * S.Q + q),
-                                                tag_base + (uint32_t)(c.p - 1));
-      return a == neg_inf() ? neg_inf() : (a - c.sh) + __ldg(Lf.theta + e);
+      return (t == 1) ? __ldg(S.theta_s + q)
+                      : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((t - 1) & 1)) * S.Q + q),
+                                     tag_base + (uint32_t)(c.p - 1));
     };
-    // log-sum-exp in two order-independent passes: max, then the
-    // fixed-point sum of exp(v - max)
-    me.m = block_reduce<RedMax>(sh, e0, len, me, value);
-    const unsigned long long su = block_reduce<RedSum>(
-        sh, e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
-    if (!act) continue;
-    const float r = fix_log_sum(me.m, su);
-    if (r != neg_inf()) {
-      S.alpha[((int64_t)me.b * 2 + (V.t & 1)) * S.Q + d] = tagged_make(r, tag_base + (uint32_t)me.p);
-      atomicMax(S.mkey + me.p, fkey(r));
+    int32_t live = -1;  // the entry's state if its value is finite
+    if (!FWD) {
+      const unsigned long long best = block_reduce<RedKey>(sh, e0, len, me, [&](int32_t e, const TokCtx& c) {
+        const float cand = __fadd_rn(src_value(e, c), __ldg(Lf.theta + e));
+        return cand == neg_inf() ? 0ull
+                                 : (((unsigned long long)fkey(cand) << 32) | (unsigned long long)(~(uint32_t)e));
+      });
+      if (act) {
+        if (best)
+          S.alpha[((int64_t)me.b * 2 + (t & 1)) * S.Q + d] =
+              tagged_make(fkey_inv((uint32_t)(best >> 32)), tag_base + (uint32_t)me.p);
+        S.pool_q[j] = best ? d : -1;
+        S.pool_x[j] = best ? (int32_t)(~(uint32_t)best) : -1;
+        live = best ? d : -1;
+      }
+    } else {
+      auto value = [&](int32_t e, const TokCtx& c) {
+        const float a = src_value(e, c);
+        return a == neg_inf() ? neg_inf() : (a - c.sh) + __ldg(Lf.theta + e);
+      };
+      // log-sum-exp in two order-independent passes: max, then the
+      // fixed-point sum of exp(v - max)
+      me.m = block_reduce<RedMax>(sh, e0, len, me, value);
+      const unsigned long long su = block_reduce<RedSum>(
+          sh, e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
+      if (act) {
+        const float r = fix_log_sum(me.m, su);
+        if (r != neg_inf()) {
+          S.alpha[((int64_t)me.b * 2 + (t & 1)) * S.Q + d] = tagged_make(r, tag_base + (uint32_t)me.p);
+          atomicMax(S.mkey + me.p, fkey(r));
+        }
+        S.pool_q[j] = r != neg_inf() ? d : -1;
+        S.pool_x[j] = sg;
+        S.pool_v[j] = r;
+        live = r != neg_inf() ? d : -1;
+      }
     }
-    S.pool_q[j] = r != neg_inf() ? d : -1;
-    S.pool_x[j] = sg;
-    S.pool_v[j] = r;
+    // expand the new live state into position t+1
+    int32_t xe0 = 0, xlen = 0;
+    if (act && V.x_n > 0) next_arcs(Lb, T, S, t, me.p, me.b, live, &xe0, &xlen);
+    const TokCtx nx{me.p + 1, me.b, 0.f, 0.f};
+    int32_t* nstg = fwd_stage(S, t + 1);
+    uint32_t* ntch = fwd_touch(S, t + 1);
+    block_visit(sh, xe0, xlen, nx, [&](int32_t e, const TokCtx& c) {
+      const int32_t dn = __ldg(Lb.other + e);
+      if (touch_first(ntch + (int64_t)c.b * S.W, dn))
+        nstg[__ldg(T.stf + c.p) + atomicAdd(S.scnt_f + c.p, 1u)] = __ldg(Lb.xseg + e);
+    });
   }
+  // pool ranges of position t+1's tokens
+  if (V.x_n > 0) {
+    StepView Vn = V;
+    Vn.t = V.x_t;
+    Vn.n = V.x_n;
+    Vn.slot0 = V.x_slot0;
+    ranges_last_block(T, Vn, S, S.scnt_f, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
+                      S.step_rng + 2 * Vn.t);
+  }
+}
+
+__global__ void __launch_bounds__(KT) k_vit_step(LayoutView Lf, LayoutView Lb, TokenView T, StepView V,
+                                                 FrontierState S) {
+  __shared__ BlockScratch<TokCtx> sh;
+  fwd_position<false>(Lf, Lb, T, V, S, sh);
+}
+
+__global__ void __launch_bounds__(KT) k_fwd_step(LayoutView Lf, LayoutView Lb, TokenView T, StepView V,
+                                                 FrontierState S) {
+  __shared__ BlockScratch<TokCtx> sh;
+  fwd_position<true>(Lf, Lb, T, V, S, sh);
 }
 
 // ======================================================================
@@ -833,16 +869,16 @@ int launch_expand(const LayoutView& Lb, const TokenView& T, const StepView& V, c
   return check_launch("k_expand");
 }
 
-int launch_vit_reduce(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,
-                      cudaStream_t s) {
-  k_vit_reduce<<<step_grid(k_vit_reduce, &g_grid[1], V), KT, 0, s>>>(Lf, T, V, S);
-  return check_launch("k_vit_reduce");
+int launch_vit_step(const LayoutView& Lf, const LayoutView& Lb, const TokenView& T, const StepView& V,
+                    const FrontierState& S, cudaStream_t s) {
+  k_vit_step<<<step_grid(k_vit_step, &g_grid[1], V), KT, 0, s>>>(Lf, Lb, T, V, S);
+  return check_launch("k_vit_step");
 }
 
-int launch_fwd_reduce(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,
-                      cudaStream_t s) {
-  k_fwd_reduce<<<step_grid(k_fwd_reduce, &g_grid[2], V), KT, 0, s>>>(Lf, T, V, S);
-  return check_launch("k_fwd_reduce");
+int launch_fwd_step(const LayoutView& Lf, const LayoutView& Lb, const TokenView& T, const StepView& V,
+                    const FrontierState& S, cudaStream_t s) {
+  k_fwd_step<<<step_grid(k_fwd_step, &g_grid[2], V), KT, 0, s>>>(Lf, Lb, T, V, S);
+  return check_launch("k_fwd_step");
 }
 
 int launch_bwd_expand(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,

@@ -72,7 +72,9 @@ struct FrontierState {
   unsigned long long* alpha;         // [Bw][2][Q]
   unsigned long long* beta;          // [Bw][2][Q] (null for Viterbi-only state)
   uint32_t* touch;                   // [Bw][W], all zero between kernels
+  uint32_t* touch_b;                 // second touch bitmap: positions of odd parity in the forward passes
   int32_t* stage;                    // staging of the current step
+  int32_t* stage_b;                  // second staging buffer: positions of odd parity in the forward passes
   uint32_t* scnt_f;                  // [N] segments staged per token, forward direction
   uint32_t* scnt_b;                  // [N] backward direction
   int32_t* pool_q;                   // [cap] state (-1: the value turned out -inf)
@@ -109,14 +111,17 @@ struct CountView {
   double* cnt64;
 };
 
-// Expand (Viterbi and forward): every live state of the previous position
-// stages the forward segments its arcs on the step's symbol lead to.
+// Expand of the first position (Viterbi and forward): the start states
+// stage the forward segments their arcs on w_1 lead to.
 int launch_expand(const LayoutView& Lb, const TokenView& T, const StepView& V, const FrontierState& S, cudaStream_t s);
-// Reduce: each staged forward segment becomes one frontier entry.
-int launch_vit_reduce(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,
-                      cudaStream_t s);
-int launch_fwd_reduce(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,
-                      cudaStream_t s);
+// One position of the forward passes: each staged forward segment of
+// position t becomes a frontier entry (reduce), and each new live state
+// immediately stages the segments of position t+1 its arcs lead to
+// (expand).  V.x_* name position t+1 (x_n = 0 at a wave's last position).
+int launch_vit_step(const LayoutView& Lf, const LayoutView& Lb, const TokenView& T, const StepView& V,
+                    const FrontierState& S, cudaStream_t s);
+int launch_fwd_step(const LayoutView& Lf, const LayoutView& Lb, const TokenView& T, const StepView& V,
+                    const FrontierState& S, cudaStream_t s);
 // Backward expand: posteriors of the arcs into the live states of position
 // t and staging of the sources whose backward value at t-1 is needed.
 int launch_bwd_expand(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,

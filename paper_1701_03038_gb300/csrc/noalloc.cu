@@ -104,7 +104,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   }
   const int64_t Q = f->Q, W = f->W, nn = std::max(n, 1);
   auto rnd = [](int64_t bytes) { return ((bytes > 0 ? bytes : 1) + 255) & ~(int64_t)255; };
-  const int64_t need = rnd(2 * Q * 8) + rnd(W * 4) + 5 * rnd(nn * 4) + 3 * rnd(nn * 8) + rnd(dmax * 4) +
+  const int64_t need = rnd(2 * Q * 8) + 2 * rnd(W * 4) + 5 * rnd(nn * 4) + 3 * rnd(nn * 8) + 2 * rnd(dmax * 4) +
                        2 * rnd(pool * 4) + rnd(2 * (nn + 2) * 8) + 6 * rnd(8);
   if (need > (int64_t)NOALLOC_SCRATCH_BYTES) {
     set_error("fst_viterbi_noalloc: this string needs %lld bytes of working memory, beyond the fixed %llu bytes "
@@ -118,6 +118,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   Carver c{(unsigned char*)base};
   unsigned long long* alpha = c.take<unsigned long long>(2 * Q);
   uint32_t* touch = c.take<uint32_t>(W);
+  uint32_t* touch_b = c.take<uint32_t>(W);
   int32_t* tok_sym = c.take<int32_t>(nn);
   int32_t* tok_b = c.take<int32_t>(nn);
   int32_t* iota = c.take<int32_t>(nn);
@@ -128,6 +129,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   int64_t* zero64 = c.take<int64_t>(nn);
   int64_t* pool_base = c.take<int64_t>(nn);
   int32_t* stage = c.take<int32_t>(dmax);
+  int32_t* stage_b = c.take<int32_t>(dmax);
   int32_t* pool_q = c.take<int32_t>(pool);
   int32_t* pool_x = c.take<int32_t>(pool);
   int64_t* pool_top = c.take<int64_t>(1);
@@ -143,6 +145,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   // counts, the pool counter and the error flags
   FST_CUDA(cudaMemsetAsync(alpha, 0, (size_t)(2 * Q * 8), s));
   FST_CUDA(cudaMemsetAsync(touch, 0, (size_t)W * 4, s));
+  FST_CUDA(cudaMemsetAsync(touch_b, 0, (size_t)W * 4, s));
   FST_CUDA(cudaMemsetAsync(tok_b, 0, (size_t)nn * 4, s));
   FST_CUDA(cudaMemsetAsync(scnt_f, 0, (size_t)nn * 4, s));
   FST_CUDA(cudaMemsetAsync(zero64, 0, (size_t)nn * 8, s));
@@ -162,7 +165,9 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.tok0 = 0;
   S.alpha = alpha;
   S.touch = touch;
+  S.touch_b = touch_b;
   S.stage = stage;
+  S.stage_b = stage_b;
   S.scnt_f = scnt_f;
   S.pool_q = pool_q;
   S.pool_x = pool_x;
@@ -181,17 +186,21 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.bw_off = bw_off;
   const TokenView T{iota, tok_sym, tok_b, zero64, zero64};
   const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
-  for (int32_t t = 1; t <= n; ++t) {
+  auto step = [&](int32_t t, int32_t x_t) {
     StepView V;
     V.t = t;
     V.n = 1;
     V.slot0 = t - 1;
-    V.x_t = t - 1;
-    V.x_n = t > 1 ? 1 : 0;
-    V.x_slot0 = t > 1 ? t - 2 : 0;
+    const bool hasx = x_t >= 1 && x_t <= n;
+    V.x_t = hasx ? x_t : 0;
+    V.x_n = hasx ? 1 : 0;
+    V.x_slot0 = hasx ? x_t - 1 : 0;
     V.blocks = f->num_sms * 4;
-    if ((rc = launch_expand(Lb, T, V, S, s)) || (rc = launch_vit_reduce(Lf, T, V, S, s))) return rc;
-  }
+    return V;
+  };
+  if (n >= 1 && (rc = launch_expand(Lb, T, step(1, 0), S, s))) return rc;
+  for (int32_t t = 1; t <= n; ++t)
+    if ((rc = launch_vit_step(Lf, Lb, T, step(t, t + 1), S, s))) return rc;
   if ((rc = launch_vit_final(S, 1, d_score, qfinal, status, s))) return rc;
   if ((rc = launch_backtrace(Lf, S, f->olabel, 1, qfinal, d_path, d_olabels, s))) return rc;
   return FST_OK;

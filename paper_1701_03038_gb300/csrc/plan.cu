@@ -84,8 +84,8 @@ struct fst_plan_s {
   bool want_vit = true, want_fb = true;
   // shared per-wave buffers (sized for the largest wave)
   unsigned long long *alpha = nullptr, *beta = nullptr;
-  uint32_t* touch = nullptr;
-  int32_t* stage = nullptr;
+  uint32_t *touch = nullptr, *touch_b = nullptr;
+  int32_t *stage = nullptr, *stage_b = nullptr;
   uint32_t *scnt_f = nullptr, *scnt_b = nullptr;
   int32_t *pool_q = nullptr, *pool_x = nullptr;
   float* pool_v = nullptr;
@@ -111,7 +111,7 @@ struct fst_plan_s {
   ~fst_plan_s() {
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (Wave& w : waves) w.release();
-    dfree(alpha); dfree(beta); dfree(touch); dfree(stage); dfree(scnt_f); dfree(scnt_b); dfree(pool_q);
+    dfree(alpha); dfree(beta); dfree(touch); dfree(touch_b); dfree(stage); dfree(stage_b); dfree(scnt_f); dfree(scnt_b); dfree(pool_q);
     dfree(pool_x); dfree(pool_v); dfree(pool_base); dfree(pool_cnt); dfree(pool_top); dfree(flags_d);
     dfree(slot_base); dfree(bslot_base); dfree(step_rng); dfree(bstep_rng);
     dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(qfinal); dfree(cnt64); dfree(logz); dfree(epoch);
@@ -232,7 +232,9 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.alpha = P->alpha;
   S.beta = P->beta;
   S.touch = P->touch;
+  S.touch_b = P->touch_b;
   S.stage = P->stage;
+  S.stage_b = P->stage_b;
   S.scnt_f = P->scnt_f;
   S.scnt_b = P->scnt_b;
   S.pool_q = P->pool_q;
@@ -290,6 +292,7 @@ int run_begin(fst_plan_s* P, cudaStream_t s, bool fb) {
   // touch bits are left clear by every reduce; cleared here as well so that
   // an interrupted run cannot leak into the next
   FST_CUDA(cudaMemsetAsync(P->touch, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)P->fst->W) * 4, s));
+  FST_CUDA(cudaMemsetAsync(P->touch_b, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)P->fst->W) * 4, s));
   FST_CUDA(cudaGetLastError());
   return FST_OK;
 }
@@ -316,11 +319,9 @@ int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_p
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, nullptr);
   if ((rc = wave_begin(P, W, s, false))) return rc;
-  for (int32_t t = 1; t <= W.tmax; ++t) {
-    const StepView V = wave_step(P, W, t, t - 1);
-    PROF(FST_PROF_VIT_EXPAND, launch_expand(Lb, T, V, S, s));
-    PROF(FST_PROF_VIT_REDUCE, launch_vit_reduce(Lf, T, V, S, s));
-  }
+  if (W.tmax >= 1) PROF(FST_PROF_VIT_FIRST, launch_expand(Lb, T, wave_step(P, W, 1, 0), S, s));
+  for (int32_t t = 1; t <= W.tmax; ++t)
+    PROF(FST_PROF_VIT_STEP, launch_vit_step(Lf, Lb, T, wave_step(P, W, t, t + 1), S, s));
   PROF(FST_PROF_VIT_FINAL,
        launch_vit_final(S, W.Bw, d_scores + W.b0, P->qfinal, d_status ? d_status + W.b0 : nullptr, s));
   PROF(FST_PROF_BACKTRACE, launch_backtrace(Lf, S, f->olabel, W.Bw, P->qfinal, d_paths + W.tok0,
@@ -335,11 +336,9 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, nullptr);
   if ((rc = wave_begin(P, W, s, true))) return rc;
-  for (int32_t t = 1; t <= W.tmax; ++t) {
-    const StepView V = wave_step(P, W, t, t - 1);
-    PROF(FST_PROF_FWD_EXPAND, launch_expand(Lb, T, V, S, s));
-    PROF(FST_PROF_FWD_REDUCE, launch_fwd_reduce(Lf, T, V, S, s));
-  }
+  if (W.tmax >= 1) PROF(FST_PROF_FWD_FIRST, launch_expand(Lb, T, wave_step(P, W, 1, 0), S, s));
+  for (int32_t t = 1; t <= W.tmax; ++t)
+    PROF(FST_PROF_FWD_STEP, launch_fwd_step(Lf, Lb, T, wave_step(P, W, t, t + 1), S, s));
   PROF(FST_PROF_FB_FINAL, launch_fb_final(S, W.Bw, P->logz + W.b0, d_status ? d_status + W.b0 : nullptr, s));
   return FST_OK;
 }
@@ -448,7 +447,8 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
     if ((rc = alloc_track(P, &P->alpha, na))) break;
     if (P->want_fb && (rc = alloc_track(P, &P->beta, na))) break;
     if ((rc = alloc_track(P, &P->touch, P->max_bw * (int64_t)f->W)) ||
-        (rc = alloc_track(P, &P->stage, P->max_stage)) || (rc = alloc_track(P, &P->scnt_f, nt)) ||
+        (rc = alloc_track(P, &P->touch_b, P->max_bw * (int64_t)f->W)) ||
+        (rc = alloc_track(P, &P->stage, P->max_stage)) || (rc = alloc_track(P, &P->stage_b, P->max_stage)) || (rc = alloc_track(P, &P->scnt_f, nt)) ||
         (rc = alloc_track(P, &P->scnt_b, nt)) || (rc = alloc_track(P, &P->pool_q, P->pool_cap)) ||
         (rc = alloc_track(P, &P->pool_x, P->pool_cap)) || (rc = alloc_track(P, &P->pool_base, nt)) ||
         (rc = alloc_track(P, &P->pool_cnt, nt)) || (rc = alloc_track(P, &P->pool_top, 1)) ||
@@ -466,6 +466,7 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
     FST_CUDA(cudaMemsetAsync(P->alpha, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
     FST_CUDA(cudaMemsetAsync(P->touch, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)f->W) * 4, s));
+    FST_CUDA(cudaMemsetAsync(P->touch_b, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)f->W) * 4, s));
     FST_CUDA(cudaMemsetAsync(P->epoch, 0, 8, s));
     FST_CUDA(cudaMemsetAsync(P->flags_d, 0, 8, s));
     FST_CUDA(cudaStreamSynchronize(s));
@@ -491,8 +492,8 @@ extern "C" int fst_plan_info(const fst_plan_t* P, int32_t* num_strings, int64_t*
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
   int64_t vl = 1, fl = 1;  // epoch kernel
   for (const Wave& w : P->waves) {
-    vl += 2 * (int64_t)w.tmax + 2;  // expand + reduce per position, final, backtrace
-    fl += 2 * (int64_t)w.tmax + 1 + std::max<int64_t>(0, 2 * (int64_t)w.tmax - 1);  // forward, final, backward
+    vl += (int64_t)w.tmax + 3;  // first expand, one step per position, final, backtrace
+    fl += (int64_t)w.tmax + 2 + std::max<int64_t>(0, 2 * (int64_t)w.tmax - 1);  // forward, final, backward
   }
   fl += 1;  // counts out
   if (num_strings) *num_strings = P->B;
