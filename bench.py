@@ -142,13 +142,15 @@ def load_peak():
         return 6800.0, "fallback (6.8 TB/s)"
 
 
-def load_traffic(kernel: str, workload: str):
+def load_traffic(pass_name: str, workload: str):
+    """ncu DRAM bytes (read + write) of one whole pass, the same unit as the
+    model bytes behind `achieved`; None once the kernel sources changed."""
     try:
         with open(PROFILE_SUMMARY) as fh:
             d = json.load(fh)
-        e = d.get(workload, {}).get(kernel)
+        e = d.get(workload, {}).get(pass_name)
         if e and e.get("source_hash") == source_hash():
-            return e.get("dram_bytes_per_launch")
+            return e.get("dram_bytes_per_pass")
     except (OSError, ValueError):
         pass
     return None
@@ -293,7 +295,7 @@ def main():
     traffic = load_traffic(dom, args.workload)
     a, b = PASS_KERNELS[dom]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "frac": round(achieved / peak, 4), "traffic": traffic, "per": f"{dom} pass",
                 "kernel": f"{KERNEL_NAMES[a]} + {KERNEL_NAMES[b]}", "launches": prof[a][1] + prof[b][1],
                 "bytes_model": "per token: Viterbi 12|A|+4U+8D, forward 12|A|+4U+4D, "
                 "backward+posterior 20|A|+8U+4D (every arc of the slice, as the paper relaxes it)",
