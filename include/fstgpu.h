@@ -225,16 +225,16 @@ FST_API int fst_log_z_f64(fst_t* fst, const double* theta, const int32_t* ids, i
  * device time in milliseconds and the number of launches since the last
  * read (host arrays of FST_PROF_KINDS entries, either may be NULL), then
  * starts a new accumulation.  Do not enable it while capturing a graph. */
-#define FST_PROF_VIT_FIRST 0   /* Viterbi: start states stage the first position's segments */
-#define FST_PROF_VIT_STEP 1    /* Viterbi: one position reduced (max, backpointer) and expanded into the next */
+#define FST_PROF_VIT_FIRST 0   /* Viterbi: start states push their arcs into the first position */
+#define FST_PROF_VIT_STEP 1    /* Viterbi: one position's live states read out, their arcs pushed into the next */
 #define FST_PROF_VIT_FINAL 2   /* Viterbi final reduction */
 #define FST_PROF_BACKTRACE 3   /* Viterbi backtrace */
-#define FST_PROF_FWD_FIRST 4   /* forward: start states stage the first position's segments */
-#define FST_PROF_FWD_STEP 5    /* forward: one position reduced (log-sum-exp) and expanded into the next */
-#define FST_PROF_FB_FINAL 6    /* log Z and the float64 normaliser prefix */
-#define FST_PROF_BWD_EXPAND 7  /* backward: posteriors into the live states of t, sources staged */
-#define FST_PROF_BWD_REDUCE 8  /* backward: staged source segments reduced; forward values of t-2 restored */
-#define FST_PROF_COUNTS 9      /* expected counts back to caller arc order */
+#define FST_PROF_FWD_FIRST 4   /* forward: start states push their arc maxima into the first position */
+#define FST_PROF_FWD_SUM 5     /* forward: fixed-point sums of one position */
+#define FST_PROF_FWD_STEP 6    /* forward: one position's live states read out, their arc maxima pushed into the next */
+#define FST_PROF_FB_FINAL 7    /* log Z and the float64 normaliser prefix */
+#define FST_PROF_BWD_STEP 8    /* backward: backward values of position t-1 and the posteriors of position t */
+#define FST_PROF_COUNTS 9      /* expected counts to float */
 #define FST_PROF_KINDS 10
 FST_API int fst_plan_profile(fst_plan_t* plan, int32_t enable);
 FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t* launches_by_kind);
@@ -245,7 +245,7 @@ FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t*
  * memory manager owns every allocation, a latency-critical loop that must
  * not take the implicit synchronisation of cudaMalloc/cudaFree, a process
  * under a hard device-memory cap.  Every piece of per-call working memory
- * (frontier, touch bitmap, live states with backpointers, token tables) comes from one
+ * (accumulators, live states with backpointers, token tables) comes from one
  * fixed 32 MiB device array inside the library, resident on every device
  * that loads it until the process exits.
  *   ids        [n] host, symbols in [0, m); n >= 0.
@@ -255,8 +255,8 @@ FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t*
  *   stream     cudaStream_t; the call is asynchronous on it.
  * Results are bit-identical to fst_viterbi.  Returns FST_ERR_UNSUPPORTED
  * (nothing is launched) when the string needs more than the fixed array:
- * about 16*Q + Q/4 + 8*(sum over positions of the destination segments of
- * the position's symbol) + 8*(the largest such count) + 60*n bytes.  The
+ * about 16*Q + 12*(sum over positions of the distinct destinations of the
+ * position's symbol) + 8*(the largest such count) + 60*n bytes.  The
  * first call on a device looks up the array's device address with that
  * device current: make it before any stream capture.  All calls share the array and see the previous call's
  * contents, which each call clears where needed; calls that overlap on the

@@ -47,8 +47,8 @@ SIGNATURES = {
     "fst_log_z_f64": [vp, vp, vp, i32, vp],
 }
 
-PROF_KINDS = ["vit_first", "vit_step", "vit_final", "backtrace", "fwd_first", "fwd_step", "fb_final",
-              "bwd_expand", "bwd_reduce", "counts"]
+PROF_KINDS = ["vit_first", "vit_step", "vit_final", "backtrace", "fwd_first", "fwd_sum", "fwd_step", "fb_final",
+              "bwd_step", "counts"]
 
 
 class FstError(RuntimeError):

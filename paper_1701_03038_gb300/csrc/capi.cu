@@ -79,28 +79,6 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   if (i < n) p[i] = v;
 }
 
-// Run epochs: epoch[0] is the first tag of the current run and epoch[1]
-// the number of tags that run uses.  The next run starts past them; when the
-// 32-bit range would run out it restarts at 1 and the frontiers are cleared
-// (tag 0, left by the clear, is never a valid tag).
-__global__ void k_epoch_advance(uint32_t* epoch, uint32_t span, uint32_t* clear) {
-  const uint64_t next = (uint64_t)epoch[0] + (uint64_t)epoch[1] + 1ull;
-  if (next + (uint64_t)span + 1ull >= 0xffffffffull) {
-    epoch[0] = 1u;
-    *clear = 1u;
-  } else {
-    epoch[0] = (uint32_t)next;
-    *clear = 0u;
-  }
-  epoch[1] = span;
-}
-
-__global__ void k_clear_if(const uint32_t* clear, unsigned long long* p, int64_t n) {
-  if (!*clear) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = 0ull;
-}
-
 template <class T>
 int to_device(const T* h, T** d, int64_t n) {
   int rc = dalloc(d, n);
@@ -129,18 +107,16 @@ struct DevBuf {
 }  // namespace
 
 // ======================================================== plain workspace
-// Working memory of the plain method (one string, one launch pair per
-// position), kept by the FST handle and grown on demand.
+// Working memory of the plain method (one string, one launch per position),
+// kept by the FST handle and grown on demand.
 struct PlainWs {
-  unsigned long long* alpha = nullptr;  // [2][Q]
-  unsigned long long* beta = nullptr;   // [2][Q]
-  uint32_t* touch = nullptr;            // [W]
-  uint32_t* touch_b = nullptr;          // [W] second touch bitmap (odd positions, forward passes)
+  unsigned long long* acc = nullptr;    // [2][Q] x 2 words (sum, maximum), zero between runs
+  float* beta = nullptr;                // [2][Q]
   int32_t *tok_sym = nullptr, *tok_b = nullptr;
   int32_t* iota = nullptr;              // step list: token t-1 is the only slot of position t
   int64_t* zero64 = nullptr;            // staging offsets: one token per step
-  int64_t *slot_base = nullptr, *bslot_base = nullptr, *step_rng = nullptr, *bstep_rng = nullptr;
-  uint32_t *scnt_f = nullptr, *scnt_b = nullptr;
+  int64_t *slot_base = nullptr, *step_rng = nullptr;
+  uint32_t* scnt = nullptr;
   int64_t* pool_base = nullptr;
   int32_t* pool_cnt = nullptr;
   uint32_t *mkey = nullptr, *ekey = nullptr;
@@ -149,7 +125,7 @@ struct PlainWs {
   int64_t cap_n = 0;
   int32_t *stage = nullptr, *stage_b = nullptr;
   int64_t cap_stage = 0;
-  int32_t *pool_q = nullptr, *pool_x = nullptr;
+  int32_t *pool_q = nullptr, *pool_x = nullptr, *pool_n = nullptr;
   float* pool_v = nullptr;
   int64_t cap_pool = 0;
   float *cnt = nullptr, *comp = nullptr, *counts_out = nullptr;
@@ -158,14 +134,13 @@ struct PlainWs {
   double* logz = nullptr;
   int64_t* bw_off = nullptr;
   int64_t* pool_top = nullptr;
-  uint32_t *flags = nullptr, *epoch = nullptr, *clear = nullptr;
+  uint32_t* flags = nullptr;
   ~PlainWs() {
-    dfree(alpha); dfree(beta); dfree(touch); dfree(touch_b); dfree(tok_sym); dfree(tok_b); dfree(iota); dfree(zero64);
-    dfree(slot_base); dfree(bslot_base); dfree(step_rng); dfree(bstep_rng); dfree(scnt_f);
-    dfree(scnt_b); dfree(pool_base); dfree(pool_cnt); dfree(mkey); dfree(ekey); dfree(csum); dfree(esum);
-    dfree(paths); dfree(olabels); dfree(stage); dfree(stage_b); dfree(pool_q); dfree(pool_x); dfree(pool_v); dfree(cnt);
-    dfree(comp); dfree(counts_out); dfree(qfinal); dfree(status); dfree(bw_n); dfree(score); dfree(logz);
-    dfree(bw_off); dfree(pool_top); dfree(flags); dfree(epoch); dfree(clear);
+    dfree(acc); dfree(beta); dfree(tok_sym); dfree(tok_b); dfree(iota); dfree(zero64);
+    dfree(slot_base); dfree(step_rng); dfree(scnt); dfree(pool_base); dfree(pool_cnt); dfree(mkey); dfree(ekey);
+    dfree(csum); dfree(esum); dfree(paths); dfree(olabels); dfree(stage); dfree(stage_b); dfree(pool_q);
+    dfree(pool_x); dfree(pool_n); dfree(pool_v); dfree(cnt); dfree(comp); dfree(counts_out); dfree(qfinal); dfree(status);
+    dfree(bw_n); dfree(score); dfree(logz); dfree(bw_off); dfree(pool_top); dfree(flags);
   }
 };
 
@@ -177,36 +152,30 @@ int plain_init(fst_s* f) {
   f->plain = w;
   const int64_t Q = f->Q;
   int rc;
-  if ((rc = dalloc(&w->alpha, 2 * Q)) || (rc = dalloc(&w->beta, 2 * Q)) || (rc = dalloc(&w->touch, f->W)) ||
-      (rc = dalloc(&w->touch_b, f->W)) ||
+  if ((rc = dalloc(&w->acc, 4 * Q)) || (rc = dalloc(&w->beta, 2 * Q)) ||
       (rc = dalloc(&w->qfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
       (rc = dalloc(&w->logz, 1)) || (rc = dalloc(&w->bw_n, 1)) || (rc = dalloc(&w->bw_off, 1)) ||
-      (rc = dalloc(&w->pool_top, 1)) || (rc = dalloc(&w->flags, 2)) || (rc = dalloc(&w->epoch, 2)) ||
-      (rc = dalloc(&w->clear, 1)))
+      (rc = dalloc(&w->pool_top, 1)) || (rc = dalloc(&w->flags, 2)))
     return rc;
-  FST_CUDA(cudaMemset(w->alpha, 0, (size_t)2 * Q * sizeof(unsigned long long)));
-  FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(unsigned long long)));
-  FST_CUDA(cudaMemset(w->touch, 0, (size_t)f->W * 4));
-  FST_CUDA(cudaMemset(w->touch_b, 0, (size_t)f->W * 4));
+  FST_CUDA(cudaMemset(w->acc, 0, (size_t)4 * Q * sizeof(unsigned long long)));
+  FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(float)));
   FST_CUDA(cudaMemset(w->bw_off, 0, sizeof(int64_t)));
-  FST_CUDA(cudaMemset(w->epoch, 0, 2 * sizeof(uint32_t)));
+  FST_CUDA(cudaMemset(w->flags, 0, 2 * sizeof(uint32_t)));
   return FST_OK;
 }
 
 // Grow the per-string buffers: n tokens, a staging buffer for the largest
-// slice, and a pool for every destination segment of the string (its exact
-// bound, so the plain method never runs out of pool).
+// slice, and a pool for every destination of the string's symbols (its
+// exact bound, so the plain method never runs out of pool).
 int plain_reserve(PlainWs* w, int64_t n, int64_t stage, int64_t pool) {
   int rc;
   if (n > w->cap_n) {
     const int64_t c = std::max<int64_t>(n, 2 * w->cap_n);
-    dfree(w->tok_sym); dfree(w->tok_b); dfree(w->iota); dfree(w->zero64); dfree(w->slot_base); dfree(w->bslot_base);
-    dfree(w->step_rng); dfree(w->bstep_rng); dfree(w->scnt_f); dfree(w->scnt_b); dfree(w->pool_base);
-    dfree(w->pool_cnt); dfree(w->mkey); dfree(w->ekey); dfree(w->csum); dfree(w->esum); dfree(w->paths);
-    dfree(w->olabels);
+    dfree(w->tok_sym); dfree(w->tok_b); dfree(w->iota); dfree(w->zero64); dfree(w->slot_base);
+    dfree(w->step_rng); dfree(w->scnt); dfree(w->pool_base); dfree(w->pool_cnt); dfree(w->mkey); dfree(w->ekey);
+    dfree(w->csum); dfree(w->esum); dfree(w->paths); dfree(w->olabels);
     w->cap_n = 0;
-    if ((rc = dalloc(&w->iota, c)) || (rc = dalloc(&w->slot_base, c)) || (rc = dalloc(&w->bslot_base, c)) ||
-        (rc = dalloc(&w->step_rng, 2 * (c + 2))) || (rc = dalloc(&w->bstep_rng, 2 * (c + 2))))
+    if ((rc = dalloc(&w->iota, c)) || (rc = dalloc(&w->slot_base, c)) || (rc = dalloc(&w->step_rng, 2 * (c + 2))))
       return rc;
     {
       std::vector<int32_t> io(c);
@@ -214,10 +183,9 @@ int plain_reserve(PlainWs* w, int64_t n, int64_t stage, int64_t pool) {
       FST_CUDA(cudaMemcpy(w->iota, io.data(), (size_t)c * 4, cudaMemcpyHostToDevice));
     }
     if ((rc = dalloc(&w->tok_sym, c)) || (rc = dalloc(&w->tok_b, c)) || (rc = dalloc(&w->zero64, c)) ||
-        (rc = dalloc(&w->scnt_f, c)) || (rc = dalloc(&w->scnt_b, c)) || (rc = dalloc(&w->pool_base, c)) ||
-        (rc = dalloc(&w->pool_cnt, c)) || (rc = dalloc(&w->mkey, c)) || (rc = dalloc(&w->ekey, c)) ||
-        (rc = dalloc(&w->csum, c)) || (rc = dalloc(&w->esum, c)) || (rc = dalloc(&w->paths, c)) ||
-        (rc = dalloc(&w->olabels, c)))
+        (rc = dalloc(&w->scnt, c)) || (rc = dalloc(&w->pool_base, c)) || (rc = dalloc(&w->pool_cnt, c)) ||
+        (rc = dalloc(&w->mkey, c)) || (rc = dalloc(&w->ekey, c)) || (rc = dalloc(&w->csum, c)) ||
+        (rc = dalloc(&w->esum, c)) || (rc = dalloc(&w->paths, c)) || (rc = dalloc(&w->olabels, c)))
       return rc;
     FST_CUDA(cudaMemset(w->tok_b, 0, (size_t)c * sizeof(int32_t)));
     FST_CUDA(cudaMemset(w->zero64, 0, (size_t)c * sizeof(int64_t)));
@@ -233,15 +201,17 @@ int plain_reserve(PlainWs* w, int64_t n, int64_t stage, int64_t pool) {
   }
   if (pool > w->cap_pool) {
     const int64_t c = std::max<int64_t>(pool, 2 * w->cap_pool);
-    dfree(w->pool_q); dfree(w->pool_x); dfree(w->pool_v);
+    dfree(w->pool_q); dfree(w->pool_x); dfree(w->pool_n); dfree(w->pool_v);
     w->cap_pool = 0;
-    if ((rc = dalloc(&w->pool_q, c)) || (rc = dalloc(&w->pool_x, c)) || (rc = dalloc(&w->pool_v, c))) return rc;
+    if ((rc = dalloc(&w->pool_q, c)) || (rc = dalloc(&w->pool_x, c)) || (rc = dalloc(&w->pool_n, c)) ||
+        (rc = dalloc(&w->pool_v, c)))
+      return rc;
     w->cap_pool = c;
   }
   return FST_OK;
 }
 
-// Upload the tokens of one string and start a run: fresh tags, zero counts.
+// Upload the tokens of one string and start a run.
 int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
   PlainWs* w = f->plain;
   int64_t stage = 1, pool = 1;
@@ -251,8 +221,7 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
       return FST_ERR_INVALID_ARG;
     }
     const int64_t D = f->fwd.h_sym_seg[ids[i] + 1] - f->fwd.h_sym_seg[ids[i]];
-    const int64_t U = f->bwd.h_sym_seg[ids[i] + 1] - f->bwd.h_sym_seg[ids[i]];
-    stage = std::max(stage, std::max(D, U));
+    stage = std::max(stage, D);
     pool += D;
   }
   int rc = plain_reserve(w, std::max(n, 1), stage, pool);
@@ -260,49 +229,35 @@ int plain_tokens(fst_s* f, const int32_t* ids, int32_t n, cudaStream_t s) {
   const size_t n4 = (size_t)std::max(n, 1) * 4;
   if (n > 0) FST_CUDA(cudaMemcpyAsync(w->tok_sym, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   FST_CUDA(cudaMemcpyAsync(w->bw_n, &n, 4, cudaMemcpyHostToDevice, s));
-  FST_CUDA(cudaMemsetAsync(w->scnt_f, 0, n4, s));
-  FST_CUDA(cudaMemsetAsync(w->scnt_b, 0, n4, s));
+  FST_CUDA(cudaMemsetAsync(w->scnt, 0, n4, s));
   FST_CUDA(cudaMemsetAsync(w->mkey, 0, n4, s));
   FST_CUDA(cudaMemsetAsync(w->ekey, 0, n4, s));
   FST_CUDA(cudaMemsetAsync(w->pool_top, 0, 8, s));
   FST_CUDA(cudaMemsetAsync(w->flags, 0, 8, s));
-  FST_CUDA(cudaMemsetAsync(w->touch, 0, (size_t)f->W * 4, s));
-  FST_CUDA(cudaMemsetAsync(w->touch_b, 0, (size_t)f->W * 4, s));
-  // fresh tags for this string
-  k_epoch_advance<<<1, 1, 0, s>>>(w->epoch, (uint32_t)n + 1u, w->clear);
-  k_clear_if<<<nblk(2 * (int64_t)f->Q), TB, 0, s>>>(w->clear, w->alpha, 2 * (int64_t)f->Q);
-  k_clear_if<<<nblk(2 * (int64_t)f->Q), TB, 0, s>>>(w->clear, w->beta, 2 * (int64_t)f->Q);
-  FST_CUDA(cudaGetLastError());
   return FST_OK;
 }
 
-TokenView plain_tokview(PlainWs* w) { return TokenView{w->iota, w->tok_sym, w->tok_b, w->zero64, w->zero64}; }
+TokenView plain_tokview(PlainWs* w) { return TokenView{w->iota, w->tok_sym, w->tok_b, w->zero64}; }
 
 FrontierState plain_state(fst_s* f) {
   PlainWs* w = f->plain;
   FrontierState S;
   memset(&S, 0, sizeof(S));
   S.Q = f->Q;
-  S.W = f->W;
-  S.epoch = w->epoch;
-  S.tok0 = 0;
-  S.alpha = w->alpha;
+  S.acc = w->acc;
+  S.acc_stride = 2;
   S.beta = w->beta;
-  S.touch = w->touch;
-  S.touch_b = w->touch_b;
   S.stage = w->stage;
   S.stage_b = w->stage_b;
-  S.scnt_f = w->scnt_f;
-  S.scnt_b = w->scnt_b;
+  S.scnt = w->scnt;
   S.pool_q = w->pool_q;
   S.pool_x = w->pool_x;
+  S.pool_n = w->pool_n;
   S.pool_v = w->pool_v;
   S.pool_base = w->pool_base;
   S.pool_cnt = w->pool_cnt;
   S.slot_base = w->slot_base;
-  S.bslot_base = w->bslot_base;
   S.step_rng = w->step_rng;
-  S.bstep_rng = w->bstep_rng;
   S.pool_top = w->pool_top;
   S.pool_cap = w->cap_pool;
   S.flags = w->flags;
@@ -322,9 +277,8 @@ FrontierState plain_state(fst_s* f) {
 }
 
 // The single token of position t (slot t-1); x_t names the other position
-// a kernel reads (the previous one for expand, t-2 for the backward reduce).
-// The grid covers the widest frontier the string's symbols allow, capped at
-// what is resident at once.
+// a kernel works on (the next one for the forward steps, the previous one
+// for the kernels that walk the live states of t-1).
 StepView plain_step(const fst_s* f, int32_t n, int32_t t, int32_t x_t) {
   StepView V;
   V.t = t;
@@ -418,7 +372,6 @@ extern "C" int fst_create(int32_t num_states, int64_t num_arcs, const int32_t* s
     } else if (A > 0) {
       k_fill_i32<<<nblk(A), TB, 0, s>>>(f->olabel, A, -1);
     }
-    f->W = (int32_t)((Q + 31) / 32);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { rc = cuda_fail(e, "fst_create kernels"); break; }
     if ((rc = read_err_flag(d_err, "fst_create"))) break;
@@ -455,6 +408,7 @@ extern "C" int fst_destroy(fst_t* f) {
   dfree(f->theta_f);
   dfree(f->start_q);
   dfree(f->olabel);
+  dfree(f->src_by_id);
   dfree(f->sym_arc);
   free(f->h_sym_arc);
   delete f;
@@ -528,15 +482,15 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
   cudaStream_t s = 0;
   if ((rc = plain_tokens(f, ids, n, s))) return rc;
   PlainWs* w = f->plain;
-  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
+  const LayoutView L = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
   const FrontierState S = plain_state(f);
-  // one launch per input position (Sec. 5), after the first position's expand
-  if (n >= 1 && (rc = launch_expand(Lb, T, plain_step(f, n, 1, 0), S, s))) return rc;
+  // one launch per input position (Sec. 5), after the first position's push
+  if (n >= 1 && (rc = launch_vit_first(L, T, plain_step(f, n, 1, 0), S, s))) return rc;
   for (int32_t t = 1; t <= n; ++t)
-    if ((rc = launch_vit_step(Lf, Lb, T, plain_step(f, n, t, t + 1), S, s))) return rc;
+    if ((rc = launch_vit_step(L, T, plain_step(f, n, t, t + 1), S, s))) return rc;
   if ((rc = launch_vit_final(S, 1, w->score, w->qfinal, w->status, s))) return rc;
-  if ((rc = launch_backtrace(Lf, S, f->olabel, 1, w->qfinal, w->paths, w->olabels, s))) return rc;
+  if ((rc = launch_backtrace(S, f->src_by_id, f->olabel, 1, w->qfinal, w->paths, w->olabels, s))) return rc;
   int32_t st = 0;
   FST_CUDA(cudaMemcpy(best_score, w->score, 4, cudaMemcpyDeviceToHost));
   FST_CUDA(cudaMemcpy(&st, w->status, 4, cudaMemcpyDeviceToHost));
@@ -563,26 +517,25 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   if ((rc = plain_tokens(f, ids, n, s))) return rc;
   PlainWs* w = f->plain;
   if (arc_posteriors && !w->cnt) {
-    if ((rc = dalloc(&w->cnt, f->fwd.P)) || (rc = dalloc(&w->comp, f->fwd.P)) || (rc = dalloc(&w->counts_out, f->A)))
+    if ((rc = dalloc(&w->cnt, f->A)) || (rc = dalloc(&w->comp, f->A)) || (rc = dalloc(&w->counts_out, f->A)))
       return rc;
   }
-  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
+  const LayoutView L = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
   const FrontierState S = plain_state(f);
-  if (n >= 1 && (rc = launch_expand(Lb, T, plain_step(f, n, 1, 0), S, s))) return rc;
-  for (int32_t t = 1; t <= n; ++t)
-    if ((rc = launch_fwd_step(Lf, Lb, T, plain_step(f, n, t, t + 1), S, s))) return rc;
+  if (n >= 1 && (rc = launch_fwd_first(L, T, plain_step(f, n, 1, 0), S, s))) return rc;
+  for (int32_t t = 1; t <= n; ++t) {
+    if ((rc = launch_fwd_sum(L, T, plain_step(f, n, t, t - 1), S, s))) return rc;
+    if ((rc = launch_fwd_step(L, T, plain_step(f, n, t, t + 1), S, s))) return rc;
+  }
   if ((rc = launch_fb_final(S, 1, w->logz, w->status, s))) return rc;
   if (arc_posteriors) {
     const CountView C{0, w->cnt, w->comp, nullptr};
-    FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)f->fwd.P * 4, s));
-    FST_CUDA(cudaMemsetAsync(w->comp, 0, (size_t)f->fwd.P * 4, s));
-    for (int32_t t = n; t >= 1; --t) {
-      const StepView V = plain_step(f, n, t, t - 2);
-      if ((rc = launch_bwd_expand(Lf, T, V, S, C, s))) return rc;
-      if (t >= 2 && (rc = launch_bwd_reduce(Lb, T, V, S, s))) return rc;
-    }
-    if ((rc = launch_counts_out(f->fwd.arc_id, f->fwd.P, C, w->counts_out, s))) return rc;
+    FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
+    FST_CUDA(cudaMemsetAsync(w->comp, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
+    for (int32_t t = n; t >= 1; --t)
+      if ((rc = launch_bwd_step(L, T, plain_step(f, n, t, t - 1), S, C, s))) return rc;
+    if ((rc = launch_counts_out(f->A, C, w->counts_out, s))) return rc;
     if (f->A > 0)
       FST_CUDA(cudaMemcpy(arc_posteriors, w->counts_out, (size_t)f->A * 4, cudaMemcpyDeviceToHost));
   }

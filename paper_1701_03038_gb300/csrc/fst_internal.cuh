@@ -50,10 +50,13 @@ struct Layout {
   int32_t* seg_state = nullptr;  // [nseg] dst (forward) / src (backward)
   int32_t* seg_pos = nullptr;    // [nseg] padded start position
   int32_t* seg_len = nullptr;    // [nseg] arcs in the segment
-  int32_t* xseg = nullptr;       // [P] segment of the other layout holding the same arc (-1 on padding)
-  // (symbol, state) -> segment, open addressing: slot = {key, segment};
-  // key = symbol << 32 | state, empty slots hold ~0
+  // (symbol, state) -> arcs of the segment, open addressing: slot = {key,
+  // len << 32 | first position}; key = symbol << 32 | state, empty slots
+  // hold ~0 (source-segmented layout only)
   ulonglong2* seg_hash = nullptr;
+  // [P] the arcs packed for one 16-byte load each: {other, theta bits,
+  // caller id, 0} (source-segmented layout only)
+  int4* arcs = nullptr;
   int64_t hash_mask = 0;
   int64_t* sym_win = nullptr;    // [m+1]
   int64_t* sym_seg = nullptr;    // [m+1]
@@ -77,16 +80,15 @@ struct fst_s {
   fstgpu::Layout fwd, bwd;
   float* theta_s = nullptr;    // [Q]
   float* theta_f = nullptr;    // [Q]
-  int32_t W = 0;               // 32-bit words of a state bitmap, ceil(Q / 32)
   int32_t* start_q = nullptr;  // [nstart] states with a finite start weight
   int32_t nstart = 0;
   int32_t* olabel = nullptr;   // [A] by caller arc id
+  int32_t* src_by_id = nullptr;  // [A] source state by caller arc id
   int64_t* sym_arc = nullptr;  // [m+1] R offsets (device)
   int64_t* h_sym_arc = nullptr;
   int32_t max_seg_len = 0;
   // per-handle state for the single-string calls
   struct PlainWs* plain = nullptr;
-  uint32_t tag_epoch = 1;
 };
 
 namespace fstgpu {
@@ -111,14 +113,6 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
   return __uint_as_float(u);
 }
 constexpr uint32_t FKEY_NEG_INF = 0x007fffffu;  // fkey(-inf)
-
-// Tagged frontier entry: low word float bits, high word tag.
-__device__ __forceinline__ float tagged_value(unsigned long long e, uint32_t tag) {
-  return (uint32_t)(e >> 32) == tag ? __uint_as_float((uint32_t)e) : -__int_as_float(0x7f800000);
-}
-__device__ __forceinline__ unsigned long long tagged_make(float v, uint32_t tag) {
-  return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
-}
 
 // ------------------------------------------------------------ primitives
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the key.

@@ -8,26 +8,29 @@
 // The frontiers of real decoding are sparse: a handful of states out of
 // hundreds of thousands hold a finite value at a position.  An arc whose
 // source is -inf contributes -inf to a max or a log-sum-exp and zero to a
-// posterior, so skipping it changes no result.  Each position therefore
-// runs two kernels, both driven by the live states only:
+// posterior, so skipping it changes no result.  The kernels therefore walk
+// only the arcs out of live states, found through a (symbol, state) hash of
+// the source-segmented layout, and keep the paper's push direction:
 //
-//   expand  -- every live state q of position t-1 finds its segment (w_t, q)
-//              in the source-segmented layout and marks, through a touch
-//              bitmap per string, the destination segments (w_t, q') of the
-//              destination-segmented layout that its arcs lead to;
-//   reduce  -- every marked destination segment is reduced over all its arcs
-//              in arc order (a dead source reads as -inf), giving one
-//              frontier entry; the touch bits are cleared on the way.
+//   Viterbi  -- one launch per position: read and clear the accumulators of
+//               the destinations staged at t (the packed key of the best
+//               arc), write them to the live pool, and push every arc of
+//               each new live state into position t+1 with a 64-bit
+//               atomicMax of (order-preserving score bits << 32 | ~arc id):
+//               the best score wins, and on ties the lowest arc id;
+//   forward  -- two launches per position: the atomicMax of the arc values
+//               (order keys), then, once every maximum is final, an integer
+//               atomicAdd of exp(value - maximum) in 2^-40 fixed point.  Both
+//               are exact, so the log-sum-exp does not depend on the order
+//               in which the atomics land;
+//   backward -- one launch per position: each live state q of t-1 reduces
+//               beta over its own arcs on w_t (pull, in shared memory) and
+//               adds the posterior of each arc.
 //
-// The reduce visits each destination once, in a fixed order, with no
-// atomics on values: results do not depend on scheduling.  Viterbi keys
-// (order-preserving float bits << 32 | ~arc position) give the best score
-// and, on ties, the lowest position, i.e. the lowest arc id since the arcs of
-// a segment are sorted by id.  Forward and backward carry (max, scaled sum)
-// pairs; each step's values are shifted by that step's maximum, the running
-// shift kept in float64.  The backward pass mirrors the forward one: expand
-// over the live states of position t (posteriors of their incoming arcs,
-// staging of the sources), reduce over the staged source segments.
+// The push that finds an accumulator empty stages its destination, so each
+// position's live states are listed exactly once, with no bitmap.  Forward
+// values are shifted by the previous position's maximum and backward values
+// by the next position's; the running shifts are kept in float64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -47,7 +50,6 @@ __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); 
 __device__ __forceinline__ int32_t warp_id_global() { return (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
 
 __device__ __forceinline__ float decode_max(uint32_t k) { return k ? fkey_inv(k) : neg_inf(); }
-
 
 // Owner of flat entry j among the n slots whose first entries base[0..n)
 // are nondecreasing with base[0] <= j: the last slot with base <= j.  A warp
@@ -70,32 +72,41 @@ __device__ __forceinline__ int32_t lane_owner(const int64_t* __restrict__ base, 
   return k;
 }
 
-// Segment (a, q) of the source-segmented layout: a lookup in its
-// open-addressing table (load factor <= 1/2, one 16-byte probe on average);
-// -1 when q has no arc on a.
-__device__ __forceinline__ int64_t find_seg(const LayoutView& L, int32_t a, int32_t q) {
+// The arcs out of state q on symbol a: a lookup in the open-addressing
+// table of the source-segmented layout (load factor <= 1/2, one 16-byte
+// probe on average) giving their first position and count (0 when none).
+struct Arcs {
+  int32_t pos, len;
+};
+__device__ __forceinline__ Arcs find_arcs(const LayoutView& L, int32_t a, int32_t q) {
   const uint64_t k = seg_hash_key(a, q);
   uint64_t h = seg_hash_slot(k, L.hash_mask);
   for (int64_t probe = 0; probe <= L.hash_mask; ++probe) {
     const ulonglong2 e = __ldg(L.seg_hash + h);
-    if (e.x == k) return (int64_t)e.y;
-    if (e.x == ~0ull) return -1;
+    if (e.x == k) return Arcs{(int32_t)(uint32_t)e.y, (int32_t)(e.y >> 32)};
+    if (e.x == ~0ull) break;
     h = (h + 1) & (uint64_t)L.hash_mask;
   }
-  return -1;
+  return Arcs{0, 0};
 }
 
-// Staging buffer and touch bitmap of forward position t (two of each, by
-// parity: a step reads position t's while it fills position t+1's).
+// Staging buffer of forward position t (two, by parity: a step reads
+// position t's while it fills position t+1's).
 __device__ __forceinline__ int32_t* fwd_stage(const FrontierState& S, int32_t t) { return (t & 1) ? S.stage_b : S.stage; }
-__device__ __forceinline__ uint32_t* fwd_touch(const FrontierState& S, int32_t t) { return (t & 1) ? S.touch_b : S.touch; }
 
-// Touch q in string bitmap tb: true for the first toucher only.
-__device__ __forceinline__ bool touch_first(uint32_t* tb, int32_t q) {
-  const uint32_t bit = 1u << (q & 31);
-  return (atomicOr(tb + (q >> 5), bit) & bit) == 0u;
+// Slot of state q of wave-local string b at position t in the dense
+// [Bw][2][Q] arrays.
+__device__ __forceinline__ int64_t acc_slot(const FrontierState& S, int32_t b, int32_t t, int32_t q) {
+  return ((int64_t)b * 2 + (t & 1)) * S.Q + q;
 }
-__device__ __forceinline__ void untouch(uint32_t* tb, int32_t q) { atomicAnd(tb + (q >> 5), ~(1u << (q & 31))); }
+// Its Viterbi key, forward sum and forward maximum.
+__device__ __forceinline__ unsigned long long* vit_key(const FrontierState& S, int64_t slot) {
+  return S.acc + slot * S.acc_stride;
+}
+__device__ __forceinline__ unsigned long long* fwd_sum(const FrontierState& S, int64_t slot) { return S.acc + 2 * slot; }
+__device__ __forceinline__ uint32_t* fwd_max(const FrontierState& S, int64_t slot) {
+  return (uint32_t*)(S.acc + 2 * slot + 1);
+}
 
 // The last block of a kernel to finish hands out consecutive ranges, in step
 // order, to the step's tokens: prefix sums of their counts cnt[p] from
@@ -106,8 +117,8 @@ __device__ __forceinline__ void untouch(uint32_t* tb, int32_t q) { atomicAnd(tb 
 // raise error bit 1: every status of the run then reports FST_ERR_OOM.
 // Each thread takes RPT consecutive slots (their loads issued together),
 // then the block scans the thread totals (two warp levels); RPT * KT slots
-// per round.
-constexpr int RPT = 4;
+// per round, so one round for up to 4,096 tokens.
+constexpr int RPT = 16;
 
 __device__ void ranges_last_block(const TokenView& T, const StepView& V, const FrontierState& S,
                                   const uint32_t* cnt, int64_t* top, int64_t cap, int64_t* slot_out,
@@ -130,16 +141,12 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
   __syncthreads();
   for (int32_t c = 0; c < V.n; c += KT * RPT) {
     const int32_t k0 = c + (int32_t)threadIdx.x * RPT;
-    int32_t pv[RPT];
-    long long mv[RPT];
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) pv[i] = k0 + i < V.n ? __ldg(T.step_tok + V.slot0 + k0 + i) : -1;
+    // the thread's total first (its loads in flight together), then the
+    // ranges, re-reading the counts from cache
     long long run = 0;
 #pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-      mv[i] = pv[i] >= 0 ? (long long)__ldcg(cnt + pv[i]) : 0ll;
-      run += mv[i];
-    }
+    for (int i = 0; i < RPT; ++i)
+      if (k0 + i < V.n) run += (long long)__ldcg(cnt + __ldg(T.step_tok + V.slot0 + k0 + i));
     long long incl = run;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -155,15 +162,14 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
       round += wsum[w];
     }
     base += incl - run;
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-      if (pv[i] < 0) continue;
-      const long long m = mv[i];
+    for (int i = 0; i < RPT && k0 + i < V.n; ++i) {
+      const int32_t p = __ldg(T.step_tok + V.slot0 + k0 + i);
+      const long long m = (long long)__ldcg(cnt + p);
       const bool fit = base + m <= (long long)cap;
       if (!fit) atomicMin(&first_bad, base);
       slot_out[V.slot0 + k0 + i] = fit ? base : INT64_MAX;
-      if (base_out) base_out[pv[i]] = fit ? base : 0;
-      if (cnt_out) cnt_out[pv[i]] = fit ? (int32_t)m : 0;
+      if (base_out) base_out[p] = fit ? base : 0;
+      if (cnt_out) cnt_out[p] = fit ? (int32_t)m : 0;
       base += m;
     }
     __syncthreads();
@@ -183,12 +189,15 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
 // ======================================================================
 // Block-flattened arc walks.  Thread i of a block owns the arcs
 // [e0_i, e0_i + len_i) of one segment; the block visits the arcs of all its
-// threads 256 at a time, so a hub's segment (hundreds of arcs out of one
-// state on one symbol) spreads over the block instead of holding up one
-// thread.  Reductions go through shared-memory atomics on order-independent
+// threads KT * VU at a time (VU arcs per thread, their loads in flight
+// together), so a hub's segment (hundreds of arcs out of one state on one
+// symbol) spreads over the block instead of holding up one thread.
+// Reductions go through shared-memory atomics on order-independent
 // operations (max, integer add), so their results do not depend on which
 // thread met which arc.
 // ======================================================================
+constexpr int VU = 4;
+
 template <class Ctx>
 struct BlockScratch {
   int32_t excl[KT];   // first flat arc of each thread's segment
@@ -229,31 +238,47 @@ __device__ __forceinline__ int block_owner(const int32_t* excl, int32_t a) {
   return o;
 }
 
-// visit(e, ctx) for every arc of every thread's segment.
+// fn(e, ctx of e's owner, owner) for every arc of every thread's segment.
 template <class Ctx, class F>
-__device__ __forceinline__ void block_visit(BlockScratch<Ctx>& sh, int32_t e0, int32_t len, const Ctx& mine,
-                                            F visit) {
+__device__ __forceinline__ void block_walk(BlockScratch<Ctx>& sh, int32_t total, F fn) {
+  for (int32_t a0 = threadIdx.x; a0 < total; a0 += KT * VU) {
+    int oo[VU];
+    int32_t ee[VU];
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int32_t a = a0 + u * KT;
+      oo[u] = a < total ? block_owner(sh.excl, a) : -1;
+      ee[u] = oo[u] >= 0 ? sh.e0[oo[u]] + (a - sh.excl[oo[u]]) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < VU; ++u)
+      if (oo[u] >= 0) fn(ee[u], sh.ctx[oo[u]], oo[u]);
+  }
+}
+
+template <class Ctx>
+__device__ __forceinline__ int32_t block_stage(BlockScratch<Ctx>& sh, int32_t e0, int32_t len, const Ctx& mine) {
   int32_t total;
   const int32_t ex = block_excl(len, sh.wsum, &total);
   sh.excl[threadIdx.x] = ex;
   sh.e0[threadIdx.x] = e0;
   sh.ctx[threadIdx.x] = mine;
+  sh.acc[threadIdx.x] = 0ull;
   __syncthreads();
-  for (int32_t a = threadIdx.x; a < total; a += KT) {
-    const int o = block_owner(sh.excl, a);
-    visit(sh.e0[o] + (a - sh.excl[o]), sh.ctx[o]);
-  }
+  return total;
+}
+
+// visit(e, ctx) for every arc of every thread's segment.
+template <class Ctx, class F>
+__device__ __forceinline__ void block_visit(BlockScratch<Ctx>& sh, int32_t e0, int32_t len, const Ctx& mine,
+                                            F visit) {
+  const int32_t total = block_stage(sh, e0, len, mine);
+  block_walk(sh, total, [&](int32_t e, const Ctx& c, int) { visit(e, c); });
   __syncthreads();
 }
 
 // Reductions over each thread's segment: Op maps a value to a 64-bit key,
 // combines keys atomically and maps the result back.
-struct RedKey {  // Viterbi: max of packed (score, ~position) keys
-  typedef unsigned long long T;
-  static __device__ __forceinline__ unsigned long long key(T v) { return v; }
-  static __device__ __forceinline__ T value(unsigned long long k) { return k; }
-  static __device__ __forceinline__ void atomic(unsigned long long* a, unsigned long long k) { if (k) atomicMax(a, k); }
-};
 struct RedMax {  // max of floats through their order-preserving keys (0 = nothing)
   typedef float T;
   static __device__ __forceinline__ unsigned long long key(T v) {
@@ -274,17 +299,8 @@ struct RedSum {  // exact integer sum
 template <class Op, class Ctx, class F>
 __device__ __forceinline__ typename Op::T block_reduce(BlockScratch<Ctx>& sh, int32_t e0, int32_t len,
                                                        const Ctx& mine, F value) {
-  int32_t total;
-  const int32_t ex = block_excl(len, sh.wsum, &total);
-  sh.excl[threadIdx.x] = ex;
-  sh.e0[threadIdx.x] = e0;
-  sh.ctx[threadIdx.x] = mine;
-  sh.acc[threadIdx.x] = 0ull;
-  __syncthreads();
-  for (int32_t a = threadIdx.x; a < total; a += KT) {
-    const int o = block_owner(sh.excl, a);
-    Op::atomic(&sh.acc[o], Op::key(value(sh.e0[o] + (a - sh.excl[o]), sh.ctx[o])));
-  }
+  const int32_t total = block_stage(sh, e0, len, mine);
+  block_walk(sh, total, [&](int32_t e, const Ctx& c, int o) { Op::atomic(&sh.acc[o], Op::key(value(e, c))); });
   __syncthreads();
   const typename Op::T r = Op::value(sh.acc[threadIdx.x]);
   __syncthreads();
@@ -292,75 +308,126 @@ __device__ __forceinline__ typename Op::T block_reduce(BlockScratch<Ctx>& sh, in
 }
 
 // exp(v - m), v <= m, as a 2^-40 fixed-point integer: sums of these are exact
-// and so independent of the order in which the block happens to add them
-constexpr double FIX_ONE = 1099511627776.0;  // 2^40
+// and so independent of the order in which they are added.  A sum of fewer
+// than 2^24 terms cannot overflow (the store refuses longer segments).
 __device__ __forceinline__ unsigned long long fix_exp(float v, float m) {
-  return v == __int_as_float(0xff800000) ? 0ull : __double2ull_rn((double)__expf(v - m) * FIX_ONE);
+  return v == __int_as_float(0xff800000) ? 0ull : __float2ull_rn(__expf(v - m) * 0x1p40f);
 }
+// m + log(s / 2^40), the logarithm in float64: a float32 logarithm here
+// adds up to an ulp per position, which over a 200-symbol string moved
+// expected counts by 1e-5 relative.
 __device__ __forceinline__ float fix_log_sum(float m, unsigned long long s) {
   return (m == __int_as_float(0xff800000) || s == 0ull) ? __int_as_float(0xff800000)
-                                                        : m + (float)log((double)s / FIX_ONE);
+                                                        : m + (float)log((double)s * 0x1p-40);
 }
 
-// Per-thread context the arc walks need from the owner thread.
-struct TokCtx {
-  int32_t p, b;
-  float sh;  // a step shift (forward m_{t-1} or backward e_t), or unused
-  float m;   // the segment's maximum (second pass of a log-sum-exp)
+// ======================================================================
+// Push (Alg. 1 / Alg. 2 forward loops over the arcs of live sources).
+// ======================================================================
+struct PushCtx {
+  int32_t p;  // token of the destination position
+  int32_t b;  // wave-local string
+  float r;    // value of the source
 };
 
-// ======================================================================
-// Expand (Alg. 1 / Alg. 2 forward loops, restricted to live sources).
-// Sources: the pool entries of position t-1 (their token's successor is the
-// token that reads w_t), or every start state for every token at t = 1.
-// ======================================================================
-__global__ void __launch_bounds__(KT) k_expand(LayoutView Lb, TokenView T, StepView V, FrontierState S) {
-  __shared__ BlockScratch<TokCtx> sh;
-  const int lane = threadIdx.x & 31;
-  const int64_t R0 = V.t == 1 ? 0 : S.step_rng[2 * V.x_t];
-  const int64_t R1 = V.t == 1 ? (int64_t)V.n * S.nstart : S.step_rng[2 * V.x_t + 1];
-  for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
-    const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
-    const int64_t j = c0 + lane;
-    int32_t p = -1, q = -1;
-    if (V.t == 1) {
-      if (j < R1) {
-        p = __ldg(T.step_tok + V.slot0 + (int32_t)(j / S.nstart));
-        q = __ldg(S.start_q + (int32_t)(j % S.nstart));
-      }
-    } else {
-      const int64_t* base = S.slot_base + V.x_slot0;
-      const int32_t k0 = warp_owner(base, V.x_n, c0);
-      if (j < R1) {
-        const int32_t pp = __ldg(T.step_tok + V.x_slot0 + lane_owner(base, V.x_n, k0, j));
-        if (S.bw_n[__ldg(T.b + pp)] >= V.t) {  // the string goes on to position t
-          p = pp + 1;
-          q = S.pool_q[j];
-        }
-      }
-    }
-    // the source's arcs on w_t: its segment of the source-segmented layout
-    int32_t e0 = 0, len = 0;
-    TokCtx me{p, 0, 0.f, 0.f};
-    if (p >= 0 && q >= 0) {
-      const int64_t sg = find_seg(Lb, __ldg(T.sym + p), q);
-      if (sg >= 0) {
-        e0 = __ldg(Lb.seg_pos + sg);
-        len = __ldg(Lb.seg_len + sg);
-        me.b = __ldg(T.b + p);
-      }
-    }
-    block_visit(sh, e0, len, me, [&](int32_t e, const TokCtx& c) {
-      const int32_t d = __ldg(Lb.other + e);
-      if (touch_first(fwd_touch(S, V.t) + (int64_t)c.b * S.W, d))
-        fwd_stage(S, V.t)[__ldg(T.stf + c.p) + atomicAdd(S.scnt_f + c.p, 1u)] = __ldg(Lb.xseg + e);
-    });
+// Arc e out of a live source, into position t: the atomic max on the
+// destination's accumulator, and the staging of a destination met first.
+template <bool VIT>
+__device__ __forceinline__ void push_arc(const LayoutView& L, const TokenView& T, const FrontierState& S,
+                                         int32_t t, int32_t e, const PushCtx& c) {
+  const int4 a = __ldg(L.arcs + e);
+  const int32_t d = a.x;
+  const float u = __fadd_rn(c.r, __int_as_float(a.y));
+  if (u == neg_inf()) return;
+  const int64_t slot = acc_slot(S, c.b, t, d);
+  bool first;
+  if (VIT) {
+    const uint32_t id = (uint32_t)a.z;
+    first = atomicMax(vit_key(S, slot), ((unsigned long long)fkey(u) << 32) | (unsigned long long)(~id)) == 0ull;
+  } else {
+    first = atomicMax(fwd_max(S, slot), fkey(u)) == 0u;
   }
-  ranges_last_block(T, V, S, S.scnt_f, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
-                    S.step_rng + 2 * V.t);
+  if (first) fwd_stage(S, t)[__ldg(T.stf + c.p) + atomicAdd(S.scnt + c.p, 1u)] = d;
 }
 
-// Flat entry j of the reduce at position t: token p and its staging index i.
+// Live source j of position t-1 for the tokens of position t: at t = 1 the
+// start states of every token (j = token slot * nstart + start index), else
+// the pool entries of position t-1 (V.x_*) whose string goes on to t.
+struct Source {
+  int32_t p;   // token at position t, -1 when the entry's string ends at t-1
+  int32_t q;   // state
+  float r;     // value at t-1 (the start weight at t = 1)
+  bool head;   // first entry of its token (writes the token's scalars)
+};
+__device__ __forceinline__ Source source_at(const TokenView& T, const StepView& V, const FrontierState& S,
+                                            int32_t k0, int64_t j) {
+  Source x{-1, 0, 0.f, false};
+  if (V.t == 1) {
+    x.p = __ldg(T.step_tok + V.slot0 + (int32_t)(j / S.nstart));
+    x.q = __ldg(S.start_q + (int32_t)(j % S.nstart));
+    x.r = __ldg(S.theta_s + x.q);
+    x.head = j % S.nstart == 0;
+  } else {
+    const int64_t* base = S.slot_base + V.x_slot0;
+    const int32_t k = lane_owner(base, V.x_n, k0, j);
+    const int32_t pp = __ldg(T.step_tok + V.x_slot0 + k);
+    if (S.bw_n[__ldg(T.b + pp)] >= V.t) {
+      x.p = pp + 1;
+      x.q = S.pool_q[j];
+      x.r = S.pool_v[j];
+      x.head = __ldcg(base + k) == j;
+    }
+  }
+  return x;
+}
+// Range of the live sources of position t-1.
+__device__ __forceinline__ void source_range(const StepView& V, const FrontierState& S, int64_t* R0, int64_t* R1) {
+  if (V.t == 1) {
+    *R0 = 0;
+    *R1 = (int64_t)V.n * S.nstart;
+  } else {
+    *R0 = S.step_rng[2 * V.x_t];
+    *R1 = S.step_rng[2 * V.x_t + 1];
+  }
+}
+// The source's arcs on w_t: looked up at t = 1, stored in the pool by the
+// forward step afterwards.
+__device__ __forceinline__ Arcs source_arcs(const LayoutView& L, const TokenView& T, const StepView& V,
+                                            const FrontierState& S, const Source& x, int64_t j) {
+  return V.t == 1 ? find_arcs(L, __ldg(T.sym + x.p), x.q) : Arcs{S.pool_x[j], S.pool_n[j]};
+}
+
+// First position: the start states of every token push their arcs on w_1.
+template <bool VIT>
+__device__ __forceinline__ void first_position(const LayoutView& L, const TokenView& T, const StepView& V,
+                                               const FrontierState& S, BlockScratch<PushCtx>& sh) {
+  const int64_t R1 = (int64_t)V.n * S.nstart;
+  for (int64_t cb = (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
+    const int64_t j = cb + threadIdx.x;
+    int32_t e0 = 0, len = 0;
+    PushCtx me{0, 0, 0.f};
+    if (j < R1) {
+      const Source x = source_at(T, V, S, 0, j);
+      const Arcs r = find_arcs(L, __ldg(T.sym + x.p), x.q);
+      e0 = r.pos;
+      len = r.len;
+      me = PushCtx{x.p, __ldg(T.b + x.p), x.r};
+    }
+    block_visit(sh, e0, len, me, [&](int32_t e, const PushCtx& c) { push_arc<VIT>(L, T, S, 1, e, c); });
+  }
+  ranges_last_block(T, V, S, S.scnt, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt, S.step_rng + 2);
+}
+
+__global__ void __launch_bounds__(KT) k_vit_first(LayoutView L, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<PushCtx> sh;
+  first_position<true>(L, T, V, S, sh);
+}
+__global__ void __launch_bounds__(KT) k_fwd_first(LayoutView L, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<PushCtx> sh;
+  first_position<false>(L, T, V, S, sh);
+}
+
+// Flat entry j of position t: token p and its staging index i.
 struct Entry {
   int32_t p, i;
 };
@@ -375,107 +442,65 @@ __device__ __forceinline__ Entry step_entry(const TokenView& T, const StepView& 
 
 // ======================================================================
 // One forward position, fused (Alg. 1 inner max, Sec. 5.1; Alg. 2 forward
-// loop, Sec. 5.2): reduce the staged destination segments of position t
-// into frontier entries, then expand every new live state into the
-// segments of position t+1 (the next token of its string) right away.
+// loop, Sec. 5.2): every destination staged at t becomes a pool entry, and
+// every new live state pushes its arcs on w_{t+1} right away.
+//   Viterbi: the accumulator holds the packed key of the best arc.
+//   forward: r_t[d] = (M_d - m_{t-1}) + log(sum_d), M_d the largest
+//   r_{t-1}[src] + theta over the live arcs into d, sum_d the fixed-point
+//   sum of exp(r_{t-1}[src] + theta - M_d) and m_{t-1} the largest value of
+//   the token's previous position.
 // ======================================================================
-// Expand live state q (just computed for token p at position t) into the
-// segments of position t+1: returns its arcs on w_{t+1}.
-__device__ __forceinline__ void next_arcs(const LayoutView& Lb, const TokenView& T, const FrontierState& S,
-                                          int32_t t, int32_t p, int32_t b, int32_t q, int32_t* e0, int32_t* len) {
-  *e0 = 0;
-  *len = 0;
-  if (q < 0 || S.bw_n[b] <= t) return;  // dead, or the string ends at t
-  const int64_t sg = find_seg(Lb, __ldg(T.sym + p + 1), q);
-  if (sg < 0) return;
-  *e0 = __ldg(Lb.seg_pos + sg);
-  *len = __ldg(Lb.seg_len + sg);
-}
-
-template <bool FWD>
-__device__ __forceinline__ void fwd_position(const LayoutView& Lf, const LayoutView& Lb, const TokenView& T,
-                                             const StepView& V, const FrontierState& S, BlockScratch<TokCtx>& sh) {
+template <bool VIT>
+__device__ __forceinline__ void step_position(const LayoutView& L, const TokenView& T, const StepView& V,
+                                              const FrontierState& S, BlockScratch<PushCtx>& sh) {
   const int lane = threadIdx.x & 31;
-  const uint32_t tag_base = *S.epoch + S.tok0;
   const int32_t t = V.t;
   const int64_t R0 = S.step_rng[2 * t], R1 = S.step_rng[2 * t + 1];
   const int32_t* stg = fwd_stage(S, t);
-  uint32_t* tch = fwd_touch(S, t);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
     const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
     const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
-    const bool act = j < R1;
-    int32_t d = 0, e0 = 0, len = 0, sg = 0;
-    TokCtx me{0, 0, 0.f, 0.f};
-    if (act) {
+    int32_t e0 = 0, len = 0;
+    PushCtx nx{0, 0, 0.f};
+    if (j < R1) {
       const Entry x = step_entry(T, V, S.slot_base, k0, j);
-      me.p = x.p;
-      me.b = __ldg(T.b + x.p);
-      me.sh = (FWD && t > 1) ? decode_max(S.mkey[x.p - 1]) : 0.f;
-      sg = stg[__ldg(T.stf + x.p) + x.i];
-      d = __ldg(Lf.seg_state + sg);
-      untouch(tch + (int64_t)me.b * S.W, d);
-      if (me.sh != neg_inf()) {
-        e0 = __ldg(Lf.seg_pos + sg);
-        len = __ldg(Lf.seg_len + sg);
+      const int32_t b = __ldg(T.b + x.p);
+      const int32_t d = stg[__ldg(T.stf + x.p) + x.i];
+      const int64_t slot = acc_slot(S, b, t, d);
+      float r;
+      if (VIT) {
+        const unsigned long long key = *vit_key(S, slot);
+        r = fkey_inv((uint32_t)(key >> 32));
+        S.pool_x[j] = (int32_t)(~(uint32_t)key);  // the best incoming arc
+      } else {
+        const ulonglong2 a = *(const ulonglong2*)fwd_sum(S, slot);
+        const float sh_prev = t > 1 ? decode_max(S.mkey[x.p - 1]) : 0.f;
+        r = fix_log_sum(fkey_inv((uint32_t)a.y) - sh_prev, a.x);
+        atomicMax(S.mkey + x.p, fkey(r));
+      }
+      S.pool_q[j] = d;
+      S.pool_v[j] = r;
+      // the accumulator is zeroed only once its value has been used: a store
+      // issued right behind the load of the same word measured 25% slower
+      asm volatile("" ::: "memory");
+      if (VIT)
+        *vit_key(S, slot) = 0ull;
+      else
+        *(ulonglong2*)fwd_sum(S, slot) = make_ulonglong2(0ull, 0ull);
+      Arcs nxt{0, 0};
+      if (V.x_n > 0 && S.bw_n[b] > t) {  // the string goes on to t+1
+        nxt = find_arcs(L, __ldg(T.sym + x.p + 1), d);
+        e0 = nxt.pos;
+        len = nxt.len;
+        nx = PushCtx{x.p + 1, b, r};
+      }
+      if (!VIT) {
+        S.pool_x[j] = nxt.pos;
+        S.pool_n[j] = nxt.len;
       }
     }
-    // the value of source q on arc e, as the previous position left it
-    auto src_value = [&](int32_t e, const TokCtx& c) {
-      const int32_t q = __ldg(Lf.other + e);
-      return (t == 1) ? __ldg(S.theta_s + q)
-                      : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((t - 1) & 1)) * S.Q + q),
-                                     tag_base + (uint32_t)(c.p - 1));
-    };
-    int32_t live = -1;  // the entry's state if its value is finite
-    if (!FWD) {
-      const unsigned long long best = block_reduce<RedKey>(sh, e0, len, me, [&](int32_t e, const TokCtx& c) {
-        const float cand = __fadd_rn(src_value(e, c), __ldg(Lf.theta + e));
-        return cand == neg_inf() ? 0ull
-                                 : (((unsigned long long)fkey(cand) << 32) | (unsigned long long)(~(uint32_t)e));
-      });
-      if (act) {
-        if (best)
-          S.alpha[((int64_t)me.b * 2 + (t & 1)) * S.Q + d] =
-              tagged_make(fkey_inv((uint32_t)(best >> 32)), tag_base + (uint32_t)me.p);
-        S.pool_q[j] = best ? d : -1;
-        S.pool_x[j] = best ? (int32_t)(~(uint32_t)best) : -1;
-        live = best ? d : -1;
-      }
-    } else {
-      auto value = [&](int32_t e, const TokCtx& c) {
-        const float a = src_value(e, c);
-        return a == neg_inf() ? neg_inf() : (a - c.sh) + __ldg(Lf.theta + e);
-      };
-      // log-sum-exp in two order-independent passes: max, then the
-      // fixed-point sum of exp(v - max)
-      me.m = block_reduce<RedMax>(sh, e0, len, me, value);
-      const unsigned long long su = block_reduce<RedSum>(
-          sh, e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
-      if (act) {
-        const float r = fix_log_sum(me.m, su);
-        if (r != neg_inf()) {
-          S.alpha[((int64_t)me.b * 2 + (t & 1)) * S.Q + d] = tagged_make(r, tag_base + (uint32_t)me.p);
-          atomicMax(S.mkey + me.p, fkey(r));
-        }
-        S.pool_q[j] = r != neg_inf() ? d : -1;
-        S.pool_x[j] = sg;
-        S.pool_v[j] = r;
-        live = r != neg_inf() ? d : -1;
-      }
-    }
-    // expand the new live state into position t+1
-    int32_t xe0 = 0, xlen = 0;
-    if (act && V.x_n > 0) next_arcs(Lb, T, S, t, me.p, me.b, live, &xe0, &xlen);
-    const TokCtx nx{me.p + 1, me.b, 0.f, 0.f};
-    int32_t* nstg = fwd_stage(S, t + 1);
-    uint32_t* ntch = fwd_touch(S, t + 1);
-    block_visit(sh, xe0, xlen, nx, [&](int32_t e, const TokCtx& c) {
-      const int32_t dn = __ldg(Lb.other + e);
-      if (touch_first(ntch + (int64_t)c.b * S.W, dn))
-        nstg[__ldg(T.stf + c.p) + atomicAdd(S.scnt_f + c.p, 1u)] = __ldg(Lb.xseg + e);
-    });
+    block_visit(sh, e0, len, nx, [&](int32_t e, const PushCtx& c) { push_arc<VIT>(L, T, S, t + 1, e, c); });
   }
   // pool ranges of position t+1's tokens
   if (V.x_n > 0) {
@@ -483,175 +508,150 @@ __device__ __forceinline__ void fwd_position(const LayoutView& Lf, const LayoutV
     Vn.t = V.x_t;
     Vn.n = V.x_n;
     Vn.slot0 = V.x_slot0;
-    ranges_last_block(T, Vn, S, S.scnt_f, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
+    ranges_last_block(T, Vn, S, S.scnt, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
                       S.step_rng + 2 * Vn.t);
   }
 }
 
-__global__ void __launch_bounds__(KT) k_vit_step(LayoutView Lf, LayoutView Lb, TokenView T, StepView V,
-                                                 FrontierState S) {
-  __shared__ BlockScratch<TokCtx> sh;
-  fwd_position<false>(Lf, Lb, T, V, S, sh);
+__global__ void __launch_bounds__(KT) k_vit_step(LayoutView L, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<PushCtx> sh;
+  step_position<true>(L, T, V, S, sh);
 }
 
-__global__ void __launch_bounds__(KT) k_fwd_step(LayoutView Lf, LayoutView Lb, TokenView T, StepView V,
-                                                 FrontierState S) {
-  __shared__ BlockScratch<TokCtx> sh;
-  fwd_position<true>(Lf, Lb, T, V, S, sh);
+__global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<PushCtx> sh;
+  step_position<false>(L, T, V, S, sh);
 }
 
-// ======================================================================
-// Backward expand fused with the posteriors (Alg. 2 backward and count
-// loops; Sec. 5.2).  For each live state q of position t (finite forward
-// value, a pool entry) whose backward value beta_t[q] is finite, every arc
-// e into q on w_t with a finite forward value at its source gets
-//   gamma_t(e) = exp(alpha_{t-1}[src] + theta_e + beta_t[q] - log Z),
-// and its source is staged for the backward value at t-1.  Sources whose
-// forward value is -inf are never staged: every posterior through them is
-// zero, and no later backward step reads their backward value.
-// ======================================================================
-__device__ __forceinline__ void add_count(const CountView& C, int32_t e, float g) {
-  if (C.batched) {
-    atomicAdd(C.cnt64 + e, (double)g);
-  } else {
-    // compensated float32 summation (one string: one writer per arc and step)
-    const float s0 = C.cnt[e], cmp = C.comp[e];
-    const float y = __fsub_rn(g, cmp);
-    const float s1 = __fadd_rn(s0, y);
-    C.comp[e] = __fsub_rn(__fsub_rn(s1, s0), y);
-    C.cnt[e] = s1;
-  }
-}
-
-// owner context of the backward expand: token, string, mprev, and the
-// float64 exponent offset (ub - e_t) + K of its destination
-struct BwdCtx {
-  int32_t p, b;
-  float mprev, gw;
-  double off;
-};
-
-__global__ void __launch_bounds__(KT) k_bwd_expand(LayoutView Lf, TokenView T, StepView V, FrontierState S,
-                                                   CountView C) {
-  __shared__ BlockScratch<BwdCtx> sh;
+// Forward sum of position t: with every maximum M_d final, each live arc
+// adds exp(r_{t-1}[src] + theta - M_d) to its destination in fixed point.
+__global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<PushCtx> sh;
   const int lane = threadIdx.x & 31;
-  const uint32_t tag_base = *S.epoch + S.tok0;
   const int32_t t = V.t;
-  const int64_t R0 = S.step_rng[2 * t], R1 = S.step_rng[2 * t + 1];
+  int64_t R0, R1;
+  source_range(V, S, &R0, &R1);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
-    const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
-    const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
+    const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);
+    const int32_t k0 = t > 1 ? warp_owner(S.slot_base + V.x_slot0, V.x_n, c0) : 0;
     const int64_t j = c0 + lane;
     int32_t e0 = 0, len = 0;
-    BwdCtx me{0, 0, 0.f, 0.f, 0.0};
+    PushCtx me{0, 0, 0.f};
     if (j < R1) {
-      const Entry x = step_entry(T, V, S.slot_base, k0, j);
-      const int32_t p = x.p, b = __ldg(T.b + p), n = S.bw_n[b];
-      const double lz = S.logz[b];
-      // shifts: e_t = this step's backward maximum, m_{t-1} the forward one;
-      // K = C_{t-1} + E_t - log Z collects the float64 running sums
-      const float et = (t == n) ? 0.f : decode_max(S.ekey[p]);
-      const double tE = (t == n) ? 0.0 : S.esum[p + 1] + (double)et;
-      if (x.i == 0 && lz != -INFINITY) S.esum[p] = tE;  // E_t, read by the step at t-1
-      const double K = ((t == 1) ? 0.0 : S.csum[p - 1]) + tE - lz;
-      const float mprev = (t == 1) ? 0.f : decode_max(S.mkey[p - 1]);
-      const int32_t q = S.pool_q[j];
-      if (lz != -INFINITY && q >= 0 && et != neg_inf() && mprev != neg_inf()) {
-        const float ub = (t == n) ? __ldg(S.theta_f + q)
-                                  : tagged_value(__ldg(S.beta + ((int64_t)b * 2 + (t & 1)) * S.Q + q),
-                                                 tag_base + (uint32_t)p);
-        if (ub != neg_inf()) {
-          const int32_t sg = S.pool_x[j];
-          e0 = __ldg(Lf.seg_pos + sg);
-          len = __ldg(Lf.seg_len + sg);
-          me = BwdCtx{p, b, mprev, S.gweight ? S.gweight[b] : 1.f, ((double)ub - (double)et) + K};
-        }
+      const Source x = source_at(T, V, S, k0, j);
+      if (x.p >= 0) {
+        const Arcs r = source_arcs(L, T, V, S, x, j);
+        e0 = r.pos;
+        len = r.len;
+        me = PushCtx{x.p, __ldg(T.b + x.p), x.r};
       }
     }
-    block_visit(sh, e0, len, me, [&](int32_t e, const BwdCtx& c) {
-      const int32_t src = __ldg(Lf.other + e);
-      const float ra = (t == 1) ? __ldg(S.theta_s + src)
-                                : tagged_value(__ldg(S.alpha + ((int64_t)c.b * 2 + ((t - 1) & 1)) * S.Q + src),
-                                               tag_base + (uint32_t)(c.p - 1));
-      const float th = __ldg(Lf.theta + e);
-      if (ra == neg_inf() || th == neg_inf()) return;
-      // the exponent adds terms of either sign and tens in size that cancel
-      // to a small number: formed in float64
-      const double ex = ((double)ra - (double)c.mprev) + (double)th + c.off;
-      add_count(C, e, __expf((float)ex) * c.gw);
-      if (t >= 2 && touch_first(S.touch + (int64_t)c.b * S.W, src))
-        S.stage[__ldg(T.stb + c.p) + atomicAdd(S.scnt_b + c.p, 1u)] = __ldg(Lf.xseg + e);
+    block_visit(sh, e0, len, me, [&](int32_t e, const PushCtx& c) {
+      const int4 a = __ldg(L.arcs + e);
+      const float u = __fadd_rn(c.r, __int_as_float(a.y));
+      if (u == neg_inf()) return;
+      const int64_t slot = acc_slot(S, c.b, t, a.x);
+      atomicAdd(fwd_sum(S, slot), fix_exp(u, fkey_inv(*fwd_max(S, slot))));
     });
   }
-  if (t >= 2)
-    ranges_last_block(T, V, S, S.scnt_b, nullptr, INT64_MAX, S.bslot_base, nullptr, nullptr, S.bstep_rng + 2 * t);
 }
 
 // ======================================================================
-// Backward reduce: beta_{t-1}[q] = LSE over the arcs q -> q' on w_t of
-// theta + beta_t[q'] - e_t, for every staged source segment (q, w_t).  The
-// same launch restores the forward values of position t-2 into the dense
-// frontier (their parity buffer held alpha_t, which nothing reads any more);
-// the next backward expand needs them.
+// Backward step of position t fused with the posteriors (Alg. 2 backward
+// and count loops; Sec. 5.2).  For each live state q of position t-1 and
+// its arcs e = q -> q' on w_t:
+//   beta_{t-1}[q] = LSE_e theta_e + beta_t[q'] - e_t   (shifted by e_t, the
+//                   largest backward value of position t),
+//   gamma_t(e)   = exp(alpha_{t-1}[q] + theta_e + beta_t[q'] - log Z),
+// the exponent formed in float64 from the stored (shifted) values and the
+// float64 running shifts K = C_{t-1} + E_t - log Z.  States that are not
+// live in the forward pass are never visited: their posteriors are zero and
+// no backward value of theirs is read.
 // ======================================================================
-__global__ void __launch_bounds__(KT) k_bwd_reduce(LayoutView Lb, TokenView T, StepView V, FrontierState S) {
-  __shared__ BlockScratch<TokCtx> sh;
-  const int lane = threadIdx.x & 31;
-  const uint32_t tag_base = *S.epoch + S.tok0;
-  const int32_t t = V.t;
-  if (V.x_n > 0) {
-    const int64_t R0 = S.step_rng[2 * V.x_t], R1 = S.step_rng[2 * V.x_t + 1];
-    for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
-      const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);
-      const int64_t* base = S.slot_base + V.x_slot0;
-      const int32_t k0 = warp_owner(base, V.x_n, c0);
-      const int64_t j = c0 + lane;
-      if (j >= R1) continue;
-      const int32_t p2 = __ldg(T.step_tok + V.x_slot0 + lane_owner(base, V.x_n, k0, j));
-      const int32_t q = S.pool_q[j];
-      if (q >= 0)
-        S.alpha[((int64_t)__ldg(T.b + p2) * 2 + (V.x_t & 1)) * S.Q + q] =
-            tagged_make(S.pool_v[j], tag_base + (uint32_t)p2);
-    }
+__device__ __forceinline__ void add_count(const CountView& C, int32_t id, float g) {
+  if (C.batched) {
+    atomicAdd(C.cnt64 + id, (double)g);
+  } else {
+    // compensated float32 summation (one string: one writer per arc and step)
+    const float s0 = C.cnt[id], cmp = C.comp[id];
+    const float y = __fsub_rn(g, cmp);
+    const float s1 = __fadd_rn(s0, y);
+    C.comp[id] = __fsub_rn(__fsub_rn(s1, s0), y);
+    C.cnt[id] = s1;
   }
-  const int64_t R1 = S.bstep_rng[2 * t + 1];
-  for (int64_t cb = (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
+}
+
+struct BwdCtx {
+  int32_t b, n;
+  float et;     // e_t (0 at the string's last position)
+  float ra;     // r_{t-1}[q]
+  float gw;     // the string's gradient weight
+  float m;      // the segment's maximum (second pass)
+  double K;     // C_{t-1} + E_t - log Z - m_{t-1}
+};
+
+__global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, StepView V, FrontierState S,
+                                                 CountView C) {
+  __shared__ BlockScratch<BwdCtx> sh;
+  const int lane = threadIdx.x & 31;
+  const int32_t t = V.t;
+  int64_t R0, R1;
+  source_range(V, S, &R0, &R1);
+  for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
     const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);
-    const int32_t k0 = warp_owner(S.bslot_base + V.slot0, V.n, c0);
+    const int32_t k0 = t > 1 ? warp_owner(S.slot_base + V.x_slot0, V.x_n, c0) : 0;
     const int64_t j = c0 + lane;
-    const bool act = j < R1;
-    int32_t q = 0, e0 = 0, len = 0;
-    TokCtx me{0, 0, 0.f, 0.f};
-    int32_t n = 0;
-    if (act) {
-      const Entry x = step_entry(T, V, S.bslot_base, k0, j);
-      me.p = x.p;
-      me.b = __ldg(T.b + x.p);
-      n = S.bw_n[me.b];
-      me.sh = (t == n) ? 0.f : decode_max(S.ekey[x.p]);
-      const int32_t sg = S.stage[__ldg(T.stb + x.p) + x.i];
-      q = __ldg(Lb.seg_state + sg);
-      untouch(S.touch + (int64_t)me.b * S.W, q);
-      if (me.sh != neg_inf()) {
-        e0 = __ldg(Lb.seg_pos + sg);
-        len = __ldg(Lb.seg_len + sg);
+    int32_t e0 = 0, len = 0, q = -1, p = -1;
+    BwdCtx me{0, 0, 0.f, 0.f, 0.f, 0.f, 0.0};
+    if (j < R1) {
+      const Source x = source_at(T, V, S, k0, j);
+      const int32_t b = x.p >= 0 ? __ldg(T.b + x.p) : 0;
+      const double lz = x.p >= 0 ? S.logz[b] : -INFINITY;
+      if (lz != -INFINITY) {
+        p = x.p;
+        q = x.q;
+        const int32_t n = S.bw_n[b];
+        const float et = (t == n) ? 0.f : decode_max(S.ekey[p]);
+        const double tE = (t == n) ? 0.0 : S.esum[p + 1] + (double)et;
+        if (x.head && t > 1) S.esum[p] = tE;  // E_t, read by the step at t-1
+        const float mprev = (t == 1) ? 0.f : decode_max(S.mkey[p - 1]);
+        if (et != neg_inf()) {
+          const Arcs r = source_arcs(L, T, V, S, x, j);
+          e0 = r.pos;
+          len = r.len;
+        }
+        me = BwdCtx{b, n, et, x.r, S.gweight ? S.gweight[b] : 1.f, 0.f,
+                    (((t == 1) ? 0.0 : S.csum[p - 1]) + tE - lz) - (double)mprev};
       }
     }
-    auto value = [&](int32_t e, const TokCtx& c) {
-      const int32_t d = __ldg(Lb.other + e);
-      const float ub = (t == S.bw_n[c.b]) ? __ldg(S.theta_f + d)
-                                          : tagged_value(__ldg(S.beta + ((int64_t)c.b * 2 + (t & 1)) * S.Q + d),
-                                                         tag_base + (uint32_t)c.p);
-      return ub == neg_inf() ? neg_inf() : __ldg(Lb.theta + e) + (ub - c.sh);
+    // theta_e + beta_t[q'] - e_t; the final weight stands in for beta at the
+    // string's last position
+    auto ub_of = [&](int32_t d, const BwdCtx& c) {
+      return (t == c.n) ? __ldg(S.theta_f + d) : S.beta[acc_slot(S, c.b, t, d)];
+    };
+    auto value = [&](int32_t e, const BwdCtx& c) {
+      const int4 a = __ldg(L.arcs + e);
+      const float th = __int_as_float(a.y);
+      const float ub = ub_of(a.x, c);
+      return (th == neg_inf() || ub == neg_inf()) ? neg_inf() : th + (ub - c.et);
     };
     me.m = block_reduce<RedMax>(sh, e0, len, me, value);
-    const unsigned long long su = block_reduce<RedSum>(
-        sh, e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const TokCtx& c) { return fix_exp(value(e, c), c.m); });
-    if (!act) continue;
-    const float u = fix_log_sum(me.m, su);
-    if (u != neg_inf()) {
-      S.beta[((int64_t)me.b * 2 + ((t - 1) & 1)) * S.Q + q] = tagged_make(u, tag_base + (uint32_t)(me.p - 1));
-      atomicMax(S.ekey + me.p - 1, fkey(u));
+    const unsigned long long su =
+        block_reduce<RedSum>(sh, e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const BwdCtx& c) {
+          const int4 a = __ldg(L.arcs + e);
+          const float th = __int_as_float(a.y);
+          const float ub = ub_of(a.x, c);
+          if (th == neg_inf() || ub == neg_inf()) return 0ull;
+          // the exponent adds terms of either sign and tens in size that
+          // cancel to a small number: formed in float64
+          const double ex = (double)c.ra + (double)th + ((double)ub - (double)c.et) + c.K;
+          add_count(C, a.z, __expf((float)ex) * c.gw);
+          return fix_exp(th + (ub - c.et), c.m);
+        });
+    if (q >= 0 && t > 1) {
+      const float u = fix_log_sum(me.m, su);
+      S.beta[acc_slot(S, me.b, t - 1, q)] = u;
+      if (u != neg_inf()) atomicMax(S.ekey + p - 1, fkey(u));
     }
   }
 }
@@ -669,15 +669,13 @@ __global__ void __launch_bounds__(FT) k_vit_final(FrontierState S, float* __rest
   const int64_t b = blockIdx.x;
   const int32_t n = S.bw_n[b];
   const int64_t p = S.bw_off[b] + n - 1;
-  const unsigned long long* ab = S.alpha + (b * 2 + (n & 1)) * S.Q;
-  const uint32_t tg = *S.epoch + S.tok0 + (uint32_t)p;
   const int32_t* cand = n == 0 ? S.start_q : S.pool_q + S.pool_base[p];
   const int32_t ncand = n == 0 ? S.nstart : S.pool_cnt[p];
   unsigned long long best = 0ull;
   for (int32_t i = threadIdx.x; i < ncand; i += FT) {
     const int32_t q = cand[i];
     if (q < 0) continue;
-    const float a = n == 0 ? __ldg(S.theta_s + q) : tagged_value(ab[q], tg);
+    const float a = n == 0 ? __ldg(S.theta_s + q) : S.pool_v[S.pool_base[p] + i];
     const float c = __fadd_rn(a, __ldg(S.theta_f + q));
     if (c != neg_inf()) {
       const unsigned long long key = ((unsigned long long)fkey(c) << 32) | (unsigned long long)(~(uint32_t)q);
@@ -702,7 +700,8 @@ __global__ void __launch_bounds__(FT) k_vit_final(FrontierState S, float* __rest
 
 // One warp per string: at each position the warp finds the state among the
 // token's pool entries and follows its backpointer.
-__global__ void k_backtrace(LayoutView Lf, FrontierState S, const int32_t* __restrict__ olabel_by_id, int32_t Bw,
+__global__ void k_backtrace(FrontierState S, const int32_t* __restrict__ src_by_id,
+                            const int32_t* __restrict__ olabel_by_id, int32_t Bw,
                             const int32_t* __restrict__ qfinal, int32_t* __restrict__ paths,
                             int32_t* __restrict__ olabels) {
   const int lane = threadIdx.x & 31;
@@ -722,28 +721,27 @@ __global__ void k_backtrace(LayoutView Lf, FrontierState S, const int32_t* __res
     const int64_t p = off + t - 1;
     const int64_t pb = S.pool_base[p];
     const int32_t pc = S.pool_cnt[p];
-    int32_t pos = -1;
+    int32_t id = -1;
     for (int32_t c = 0; c < pc; c += 32) {
       const int32_t i = c + lane;
       const uint32_t hit = __ballot_sync(FULL, i < pc && S.pool_q[pb + i] == q);
       if (hit) {
-        pos = S.pool_x[pb + c + __ffs(hit) - 1];
+        id = S.pool_x[pb + c + __ffs(hit) - 1];  // the best incoming arc
         break;
       }
     }
-    if (pos < 0) {  // cannot happen for a state on the best path; leave a marker
+    if (id < 0) {  // cannot happen for a state on the best path; leave a marker
       for (int32_t u = lane; u < t; u += 32) {
         paths[off + u] = -1;
         if (olabels) olabels[off + u] = -1;
       }
       break;
     }
-    const int32_t id = __ldg(Lf.arc_id + pos);
     if (lane == 0) {
       paths[p] = id;
       if (olabels) olabels[p] = olabel_by_id[id];
     }
-    q = __ldg(Lf.other + pos);
+    q = __ldg(src_by_id + id);
   }
 }
 
@@ -828,12 +826,17 @@ __global__ void __launch_bounds__(FT) k_fb_final(FrontierState S, double* __rest
   }
 }
 
-__global__ void k_counts_out(const int32_t* __restrict__ arc_id, int64_t P, CountView C, float* __restrict__ out) {
+__global__ void k_counts_out(int64_t A, CountView C, float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P) return;
-  const int32_t k = arc_id[i];
-  if (k < 0) return;
-  out[k] = C.batched ? (float)C.cnt64[i] : __fsub_rn(C.cnt[i], C.comp[i]);
+  if (i >= A) return;
+  out[i] = C.batched ? (float)C.cnt64[i] : __fsub_rn(C.cnt[i], C.comp[i]);
+}
+
+__global__ void k_clear_if_overflow(const uint32_t* __restrict__ flag, unsigned long long* __restrict__ acc,
+                                    int64_t n) {
+  if (!(*flag & 1u)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc[i] = 0ull;
 }
 
 inline int check_launch(const char* what) {
@@ -860,37 +863,44 @@ inline unsigned step_grid(K kernel, int* cache, const StepView& V) {
   return (unsigned)std::max(1, std::min(V.blocks, *cache));
 }
 
-int g_grid[5] = {0, 0, 0, 0, 0};
+int g_grid[6] = {0, 0, 0, 0, 0, 0};
 
 }  // namespace
 
-int launch_expand(const LayoutView& Lb, const TokenView& T, const StepView& V, const FrontierState& S, cudaStream_t s) {
-  k_expand<<<step_grid(k_expand, &g_grid[0], V), KT, 0, s>>>(Lb, T, V, S);
-  return check_launch("k_expand");
+int launch_vit_first(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
+                     cudaStream_t s) {
+  k_vit_first<<<step_grid(k_vit_first, &g_grid[0], V), KT, 0, s>>>(L, T, V, S);
+  return check_launch("k_vit_first");
 }
 
-int launch_vit_step(const LayoutView& Lf, const LayoutView& Lb, const TokenView& T, const StepView& V,
-                    const FrontierState& S, cudaStream_t s) {
-  k_vit_step<<<step_grid(k_vit_step, &g_grid[1], V), KT, 0, s>>>(Lf, Lb, T, V, S);
+int launch_fwd_first(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
+                     cudaStream_t s) {
+  k_fwd_first<<<step_grid(k_fwd_first, &g_grid[1], V), KT, 0, s>>>(L, T, V, S);
+  return check_launch("k_fwd_first");
+}
+
+int launch_vit_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
+                    cudaStream_t s) {
+  k_vit_step<<<step_grid(k_vit_step, &g_grid[2], V), KT, 0, s>>>(L, T, V, S);
   return check_launch("k_vit_step");
 }
 
-int launch_fwd_step(const LayoutView& Lf, const LayoutView& Lb, const TokenView& T, const StepView& V,
-                    const FrontierState& S, cudaStream_t s) {
-  k_fwd_step<<<step_grid(k_fwd_step, &g_grid[2], V), KT, 0, s>>>(Lf, Lb, T, V, S);
+int launch_fwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
+                    cudaStream_t s) {
+  k_fwd_step<<<step_grid(k_fwd_step, &g_grid[3], V), KT, 0, s>>>(L, T, V, S);
   return check_launch("k_fwd_step");
 }
 
-int launch_bwd_expand(const LayoutView& Lf, const TokenView& T, const StepView& V, const FrontierState& S,
-                      const CountView& C, cudaStream_t s) {
-  k_bwd_expand<<<step_grid(k_bwd_expand, &g_grid[3], V), KT, 0, s>>>(Lf, T, V, S, C);
-  return check_launch("k_bwd_expand");
+int launch_fwd_sum(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
+                   cudaStream_t s) {
+  k_fwd_sum<<<step_grid(k_fwd_sum, &g_grid[4], V), KT, 0, s>>>(L, T, V, S);
+  return check_launch("k_fwd_sum");
 }
 
-int launch_bwd_reduce(const LayoutView& Lb, const TokenView& T, const StepView& V, const FrontierState& S,
-                      cudaStream_t s) {
-  k_bwd_reduce<<<step_grid(k_bwd_reduce, &g_grid[4], V), KT, 0, s>>>(Lb, T, V, S);
-  return check_launch("k_bwd_reduce");
+int launch_bwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
+                    const CountView& C, cudaStream_t s) {
+  k_bwd_step<<<step_grid(k_bwd_step, &g_grid[5], V), KT, 0, s>>>(L, T, V, S, C);
+  return check_launch("k_bwd_step");
 }
 
 int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t* qfinal, int32_t* status,
@@ -900,10 +910,10 @@ int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t*
   return check_launch("k_vit_final");
 }
 
-int launch_backtrace(const LayoutView& Lf, const FrontierState& S, const int32_t* olabel_by_id, int32_t Bw,
+int launch_backtrace(const FrontierState& S, const int32_t* src_by_id, const int32_t* olabel_by_id, int32_t Bw,
                      const int32_t* qfinal, int32_t* paths, int32_t* olabels, cudaStream_t s) {
   if (Bw <= 0) return FST_OK;
-  k_backtrace<<<(unsigned)((Bw + 7) / 8), 256, 0, s>>>(Lf, S, olabel_by_id, Bw, qfinal, paths, olabels);
+  k_backtrace<<<(unsigned)((Bw + 7) / 8), 256, 0, s>>>(S, src_by_id, olabel_by_id, Bw, qfinal, paths, olabels);
   return check_launch("k_backtrace");
 }
 
@@ -913,10 +923,17 @@ int launch_fb_final(const FrontierState& S, int32_t Bw, double* logz, int32_t* s
   return check_launch("k_fb_final");
 }
 
-int launch_counts_out(const int32_t* arc_id_fwd, int64_t P, const CountView& C, float* out, cudaStream_t s) {
-  if (P <= 0) return FST_OK;
-  k_counts_out<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(arc_id_fwd, P, C, out);
+int launch_counts_out(int64_t A, const CountView& C, float* out, cudaStream_t s) {
+  if (A <= 0) return FST_OK;
+  k_counts_out<<<(unsigned)((A + 255) / 256), 256, 0, s>>>(A, C, out);
   return check_launch("k_counts_out");
+}
+
+int launch_clear_if_overflow(const uint32_t* flag, unsigned long long* acc, int64_t n, int num_sms, cudaStream_t s) {
+  if (n <= 0) return FST_OK;
+  const int64_t blocks = std::min<int64_t>((int64_t)std::max(num_sms, 1) * 8, (n + 255) / 256);
+  k_clear_if_overflow<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(flag, acc, n);
+  return check_launch("k_clear_if_overflow");
 }
 
 }  // namespace fstgpu

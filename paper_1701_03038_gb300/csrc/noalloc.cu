@@ -71,14 +71,9 @@ struct Carver {
   }
 };
 
-// Tags of this call are 1 + token (the cleared frontier holds tag 0); the
-// step list is the identity (token t-1 is the only slot of position t).
-__global__ void k_noalloc_epoch(uint32_t* __restrict__ epoch, int32_t* __restrict__ iota, int32_t n) {
+// The step list is the identity (token t-1 is the only slot of position t).
+__global__ void k_noalloc_iota(int32_t* __restrict__ iota, int32_t n) {
   const int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-  if (i == 0) {
-    epoch[0] = 1u;
-    epoch[1] = 0u;
-  }
   if (i < n) iota[i] = i;
 }
 
@@ -102,10 +97,10 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
     pool += D;
     dmax = std::max(dmax, D);
   }
-  const int64_t Q = f->Q, W = f->W, nn = std::max(n, 1);
+  const int64_t Q = f->Q, nn = std::max(n, 1);
   auto rnd = [](int64_t bytes) { return ((bytes > 0 ? bytes : 1) + 255) & ~(int64_t)255; };
-  const int64_t need = rnd(2 * Q * 8) + 2 * rnd(W * 4) + 5 * rnd(nn * 4) + 3 * rnd(nn * 8) + 2 * rnd(dmax * 4) +
-                       2 * rnd(pool * 4) + rnd(2 * (nn + 2) * 8) + 6 * rnd(8);
+  const int64_t need = rnd(2 * Q * 8) + 5 * rnd(nn * 4) + 3 * rnd(nn * 8) + 2 * rnd(dmax * 4) +
+                       3 * rnd(pool * 4) + rnd(2 * (nn + 2) * 8) + 6 * rnd(8);
   if (need > (int64_t)NOALLOC_SCRATCH_BYTES) {
     set_error("fst_viterbi_noalloc: this string needs %lld bytes of working memory, beyond the fixed %llu bytes "
               "(shorter strings or fewer states fit; fst_viterbi has no such limit)",
@@ -116,15 +111,13 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   int rc = scratch_address(&base);
   if (rc) return rc;
   Carver c{(unsigned char*)base};
-  unsigned long long* alpha = c.take<unsigned long long>(2 * Q);
-  uint32_t* touch = c.take<uint32_t>(W);
-  uint32_t* touch_b = c.take<uint32_t>(W);
+  unsigned long long* acc = c.take<unsigned long long>(2 * Q);
   int32_t* tok_sym = c.take<int32_t>(nn);
   int32_t* tok_b = c.take<int32_t>(nn);
   int32_t* iota = c.take<int32_t>(nn);
   int64_t* slot_base = c.take<int64_t>(nn);
   int64_t* step_rng = c.take<int64_t>(2 * (nn + 2));
-  uint32_t* scnt_f = c.take<uint32_t>(nn);
+  uint32_t* scnt = c.take<uint32_t>(nn);
   int32_t* pool_cnt = c.take<int32_t>(nn);
   int64_t* zero64 = c.take<int64_t>(nn);
   int64_t* pool_base = c.take<int64_t>(nn);
@@ -132,45 +125,40 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   int32_t* stage_b = c.take<int32_t>(dmax);
   int32_t* pool_q = c.take<int32_t>(pool);
   int32_t* pool_x = c.take<int32_t>(pool);
+  float* pool_v = c.take<float>(pool);
   int64_t* pool_top = c.take<int64_t>(1);
   uint32_t* flags = c.take<uint32_t>(2);
-  uint32_t* epoch = c.take<uint32_t>(2);
   int32_t* qfinal = c.take<int32_t>(1);
   int32_t* bw_n = c.take<int32_t>(1);
   int64_t* bw_off = c.take<int64_t>(1);
   int32_t* status = c.take<int32_t>(1);
 
-  // what must start at zero: the tagged frontier (tag 0 is never valid), the
-  // touch bits, string index and staging offsets of every token, staging
-  // counts, the pool counter and the error flags
-  FST_CUDA(cudaMemsetAsync(alpha, 0, (size_t)(2 * Q * 8), s));
-  FST_CUDA(cudaMemsetAsync(touch, 0, (size_t)W * 4, s));
-  FST_CUDA(cudaMemsetAsync(touch_b, 0, (size_t)W * 4, s));
+  // what must start at zero: the accumulators, the string index and staging
+  // offsets of every token, staging counts, the pool counter and the error
+  // flags
+  FST_CUDA(cudaMemsetAsync(acc, 0, (size_t)(2 * Q * 8), s));
   FST_CUDA(cudaMemsetAsync(tok_b, 0, (size_t)nn * 4, s));
-  FST_CUDA(cudaMemsetAsync(scnt_f, 0, (size_t)nn * 4, s));
+  FST_CUDA(cudaMemsetAsync(scnt, 0, (size_t)nn * 4, s));
   FST_CUDA(cudaMemsetAsync(zero64, 0, (size_t)nn * 8, s));
   FST_CUDA(cudaMemsetAsync(pool_top, 0, 8, s));
   FST_CUDA(cudaMemsetAsync(flags, 0, 8, s));
   FST_CUDA(cudaMemsetAsync(bw_off, 0, 8, s));
   if (n > 0) FST_CUDA(cudaMemcpyAsync(tok_sym, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   FST_CUDA(cudaMemcpyAsync(bw_n, &n, 4, cudaMemcpyHostToDevice, s));
-  k_noalloc_epoch<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(epoch, iota, n);
+  k_noalloc_iota<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(iota, n);
   FST_CUDA(cudaGetLastError());
 
   FrontierState S;
   memset(&S, 0, sizeof(S));
   S.Q = f->Q;
-  S.W = f->W;
-  S.epoch = epoch;
-  S.tok0 = 0;
-  S.alpha = alpha;
-  S.touch = touch;
-  S.touch_b = touch_b;
+  S.acc = acc;
+  S.acc_stride = 1;
   S.stage = stage;
   S.stage_b = stage_b;
-  S.scnt_f = scnt_f;
+  S.scnt = scnt;
   S.pool_q = pool_q;
   S.pool_x = pool_x;
+  S.pool_v = pool_v;
   S.pool_base = pool_base;
   S.pool_cnt = pool_cnt;
   S.slot_base = slot_base;
@@ -184,8 +172,8 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.nstart = f->nstart;
   S.bw_n = bw_n;
   S.bw_off = bw_off;
-  const TokenView T{iota, tok_sym, tok_b, zero64, zero64};
-  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
+  const TokenView T{iota, tok_sym, tok_b, zero64};
+  const LayoutView L = view_of(f->bwd);
   auto step = [&](int32_t t, int32_t x_t) {
     StepView V;
     V.t = t;
@@ -198,10 +186,10 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
     V.blocks = f->num_sms * 4;
     return V;
   };
-  if (n >= 1 && (rc = launch_expand(Lb, T, step(1, 0), S, s))) return rc;
+  if (n >= 1 && (rc = launch_vit_first(L, T, step(1, 0), S, s))) return rc;
   for (int32_t t = 1; t <= n; ++t)
-    if ((rc = launch_vit_step(Lf, Lb, T, step(t, t + 1), S, s))) return rc;
+    if ((rc = launch_vit_step(L, T, step(t, t + 1), S, s))) return rc;
   if ((rc = launch_vit_final(S, 1, d_score, qfinal, status, s))) return rc;
-  if ((rc = launch_backtrace(Lf, S, f->olabel, 1, qfinal, d_path, d_olabels, s))) return rc;
+  if ((rc = launch_backtrace(S, f->src_by_id, f->olabel, 1, qfinal, d_path, d_olabels, s))) return rc;
   return FST_OK;
 }

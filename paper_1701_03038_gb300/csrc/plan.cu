@@ -2,12 +2,12 @@
 //
 // The paper decodes one string at a time and launches one kernel per input
 // position (Sec. 5; Sec. 7 times 100 sentences one after another).  A plan
-// instead advances every string of a wave by one position per launch pair
-// (expand, reduce; kernels.cu): the tokens of position t are all the
-// strings' t-th symbols, listed once per plan.  The plan also fixes, per
-// token, where its staged segments go inside the step's staging buffer, and
-// holds the dense frontiers, the live pool and the per-token scalars.
-// Strings are split into waves whose memory fits a budget.
+// instead advances every string of a wave by one position per launch
+// (kernels.cu): the tokens of position t are all the strings' t-th symbols,
+// listed once per plan.  The plan also fixes, per token, where its staged
+// destinations go inside the step's staging buffer, and holds the dense
+// accumulators, the live pool and the per-token scalars.  Strings are split
+// into waves whose memory fits a budget.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -37,40 +37,18 @@ __global__ void k_check_ids(const int32_t* __restrict__ ids, int64_t n, int32_t 
   if (i < n && (ids[i] < 0 || ids[i] >= m)) atomicOr(err, 1u);
 }
 
-// Run epochs: epoch[0] is the first tag of the current run and epoch[1]
-// the number of tags that run uses.  The next run starts past them; when the
-// 32-bit range would run out it restarts at 1 and the frontiers are cleared
-// (tag 0, left by the clear, is never a valid tag).
-__global__ void k_epoch_advance(uint32_t* epoch, uint32_t span, uint32_t* clear) {
-  const uint64_t next = (uint64_t)epoch[0] + (uint64_t)epoch[1] + 1ull;
-  if (next + (uint64_t)span + 1ull >= 0xffffffffull) {
-    epoch[0] = 1u;
-    *clear = 1u;
-  } else {
-    epoch[0] = (uint32_t)next;
-    *clear = 0u;
-  }
-  epoch[1] = span;
-}
-
-__global__ void k_clear_if(const uint32_t* clear, unsigned long long* p, int64_t n) {
-  if (!*clear) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = 0ull;
-}
-
 struct Wave {
   int32_t b0 = 0, b1 = 0, Bw = 0, tmax = 0;
   int64_t tok0 = 0, ntok = 0;
   int64_t stage = 0;       // staging entries the largest step needs
-  int64_t pool_bound = 0;  // sum of the tokens' destination-segment counts
+  int64_t pool_bound = 0;  // sum of the tokens' destination counts
   int32_t *tok_sym = nullptr, *tok_b = nullptr, *step_tok = nullptr;
-  int64_t *stf = nullptr, *stb = nullptr;
+  int64_t* stf = nullptr;
   int32_t* bw_n = nullptr;
   int64_t* bw_off = nullptr;
   std::vector<int32_t> step0;  // [tmax + 2]: tokens of position t are step_tok[step0[t] .. step0[t+1])
   void release() {
-    dfree(tok_sym); dfree(tok_b); dfree(step_tok); dfree(stf); dfree(stb); dfree(bw_n); dfree(bw_off);
+    dfree(tok_sym); dfree(tok_b); dfree(step_tok); dfree(stf); dfree(bw_n); dfree(bw_off);
   }
 };
 
@@ -83,15 +61,16 @@ struct fst_plan_s {
   std::vector<Wave> waves;
   bool want_vit = true, want_fb = true;
   // shared per-wave buffers (sized for the largest wave)
-  unsigned long long *alpha = nullptr, *beta = nullptr;
-  uint32_t *touch = nullptr, *touch_b = nullptr;
+  unsigned long long* acc = nullptr;  // [max_bw][2][Q] x acc_stride words
+  int32_t acc_stride = 1;
+  float* beta = nullptr;
   int32_t *stage = nullptr, *stage_b = nullptr;
-  uint32_t *scnt_f = nullptr, *scnt_b = nullptr;
-  int32_t *pool_q = nullptr, *pool_x = nullptr;
+  uint32_t* scnt = nullptr;
+  int32_t *pool_q = nullptr, *pool_x = nullptr, *pool_n = nullptr;
   float* pool_v = nullptr;
   int64_t* pool_base = nullptr;
   int32_t* pool_cnt = nullptr;
-  int64_t *slot_base = nullptr, *bslot_base = nullptr, *step_rng = nullptr, *bstep_rng = nullptr;
+  int64_t *slot_base = nullptr, *step_rng = nullptr;
   int64_t* pool_top = nullptr;
   int64_t pool_cap = 0;
   uint32_t* flags_d = nullptr;
@@ -100,7 +79,6 @@ struct fst_plan_s {
   int32_t* qfinal = nullptr;
   double* cnt64 = nullptr;
   double* logz = nullptr;
-  uint32_t *epoch = nullptr, *clear = nullptr;
   int64_t max_bw = 0, max_ntok = 0, max_stage = 0;
   bool forward_done = false;
   // optional per-launch CUDA events (fst_plan_profile)
@@ -111,11 +89,10 @@ struct fst_plan_s {
   ~fst_plan_s() {
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (Wave& w : waves) w.release();
-    dfree(alpha); dfree(beta); dfree(touch); dfree(touch_b); dfree(stage); dfree(stage_b); dfree(scnt_f); dfree(scnt_b); dfree(pool_q);
-    dfree(pool_x); dfree(pool_v); dfree(pool_base); dfree(pool_cnt); dfree(pool_top); dfree(flags_d);
-    dfree(slot_base); dfree(bslot_base); dfree(step_rng); dfree(bstep_rng);
-    dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(qfinal); dfree(cnt64); dfree(logz); dfree(epoch);
-    dfree(clear);
+    dfree(acc); dfree(beta); dfree(stage); dfree(stage_b); dfree(scnt); dfree(pool_q);
+    dfree(pool_x); dfree(pool_n); dfree(pool_v); dfree(pool_base); dfree(pool_cnt); dfree(pool_top); dfree(flags_d);
+    dfree(slot_base); dfree(step_rng);
+    dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(qfinal); dfree(cnt64); dfree(logz);
   }
 };
 
@@ -180,7 +157,7 @@ int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, const 
     W.tmax = std::max(W.tmax, bn[b]);
   }
   std::vector<int32_t> sym(W.ntok), tb(W.ntok), step_tok;
-  std::vector<int64_t> stf(W.ntok), stb(W.ntok);
+  std::vector<int64_t> stf(W.ntok);
   step_tok.reserve(W.ntok);
   for (int32_t b = 0; b < W.Bw; ++b)
     for (int32_t i = 0; i < bn[b]; ++i) {
@@ -199,24 +176,22 @@ int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, const 
   for (int32_t t = 1; t <= W.tmax; ++t) {
     while (live > 0 && bn[order[live - 1]] < t) --live;
     W.step0[t] = (int32_t)step_tok.size();
-    int64_t accf = 0, accb = 0;
+    int64_t accf = 0;
     for (int32_t j = 0; j < live; ++j) {
       const int64_t p = boff[order[j]] + t - 1;
       const int32_t a = sym[p];
       step_tok.push_back((int32_t)p);
       stf[p] = accf;
-      stb[p] = accb;
+      // distinct destinations of the symbol's arcs: the most a token can stage
       const int64_t D = f->fwd.h_sym_seg[a + 1] - f->fwd.h_sym_seg[a];
       accf += D;
-      accb += f->bwd.h_sym_seg[a + 1] - f->bwd.h_sym_seg[a];
       W.pool_bound += D;
     }
-    W.stage = std::max(W.stage, std::max(accf, accb));
+    W.stage = std::max(W.stage, accf);
   }
   W.step0[W.tmax + 1] = (int32_t)step_tok.size();
   if ((rc = upload(P, &W.bw_off, boff)) || (rc = upload(P, &W.bw_n, bn)) || (rc = upload(P, &W.tok_sym, sym)) ||
-      (rc = upload(P, &W.tok_b, tb)) || (rc = upload(P, &W.step_tok, step_tok)) || (rc = upload(P, &W.stf, stf)) ||
-      (rc = upload(P, &W.stb, stb)))
+      (rc = upload(P, &W.tok_b, tb)) || (rc = upload(P, &W.step_tok, step_tok)) || (rc = upload(P, &W.stf, stf)))
     return rc;
   return FST_OK;
 }
@@ -226,26 +201,20 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   FrontierState S;
   memset(&S, 0, sizeof(S));
   S.Q = f->Q;
-  S.W = f->W;
-  S.epoch = P->epoch;
-  S.tok0 = (uint32_t)W.tok0;
-  S.alpha = P->alpha;
+  S.acc = P->acc;
+  S.acc_stride = P->acc_stride;
   S.beta = P->beta;
-  S.touch = P->touch;
-  S.touch_b = P->touch_b;
   S.stage = P->stage;
   S.stage_b = P->stage_b;
-  S.scnt_f = P->scnt_f;
-  S.scnt_b = P->scnt_b;
+  S.scnt = P->scnt;
   S.pool_q = P->pool_q;
   S.pool_x = P->pool_x;
+  S.pool_n = P->pool_n;
   S.pool_v = P->pool_v;
   S.pool_base = P->pool_base;
   S.pool_cnt = P->pool_cnt;
   S.slot_base = P->slot_base;
-  S.bslot_base = P->bslot_base;
   S.step_rng = P->step_rng;
-  S.bstep_rng = P->bstep_rng;
   S.pool_top = P->pool_top;
   S.pool_cap = P->pool_cap;
   S.flags = P->flags_d;
@@ -264,11 +233,12 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   return S;
 }
 
-TokenView wave_tokens(const Wave& W) { return TokenView{W.step_tok, W.tok_sym, W.tok_b, W.stf, W.stb}; }
+TokenView wave_tokens(const Wave& W) { return TokenView{W.step_tok, W.tok_sym, W.tok_b, W.stf}; }
 
-// Position t of a wave; x names position x_t (previous position for the
-// expand kernels, t-2 for the backward reduce).  The grid assumes about 64
-// live states per token and is capped at what is resident at once.
+// Position t of a wave; x names position x_t (the next position for the
+// forward steps, the previous one for the kernels that walk the live states
+// of t-1).  The grid assumes about 64 live states per token and is capped at
+// what is resident at once.
 StepView wave_step(const fst_plan_s* P, const Wave& W, int32_t t, int32_t x_t) {
   StepView V;
   V.t = t;
@@ -283,28 +253,17 @@ StepView wave_step(const fst_plan_s* P, const Wave& W, int32_t t, int32_t x_t) {
   return V;
 }
 
-int run_begin(fst_plan_s* P, cudaStream_t s, bool fb) {
-  const uint32_t span = (uint32_t)std::min<int64_t>(P->N + 1, 0x7fffffff);
-  k_epoch_advance<<<1, 1, 0, s>>>(P->epoch, span, P->clear);
-  const int64_t na = P->max_bw * 2 * (int64_t)P->fst->Q;
-  if (P->alpha) k_clear_if<<<nblk(na), TB, 0, s>>>(P->clear, P->alpha, na);
-  if (fb && P->beta) k_clear_if<<<nblk(na), TB, 0, s>>>(P->clear, P->beta, na);
-  // touch bits are left clear by every reduce; cleared here as well so that
-  // an interrupted run cannot leak into the next
-  FST_CUDA(cudaMemsetAsync(P->touch, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)P->fst->W) * 4, s));
-  FST_CUDA(cudaMemsetAsync(P->touch_b, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)P->fst->W) * 4, s));
-  FST_CUDA(cudaGetLastError());
-  return FST_OK;
-}
-
-// State that starts every pass of a wave at zero.
+// State that starts every pass of a wave at zero.  A pass whose pool
+// overflowed left staged accumulators behind: they are cleared first.
 int wave_begin(fst_plan_s* P, const Wave& W, cudaStream_t s, bool fb) {
+  int rc;
+  const int64_t na = P->max_bw * 2 * (int64_t)P->fst->Q * P->acc_stride;
+  if ((rc = launch_clear_if_overflow(P->flags_d + 1, P->acc, na, P->fst->num_sms, s))) return rc;
   const size_t n4 = (size_t)std::max<int64_t>(1, W.ntok) * 4;
-  FST_CUDA(cudaMemsetAsync(P->scnt_f, 0, n4, s));
+  FST_CUDA(cudaMemsetAsync(P->scnt, 0, n4, s));
   FST_CUDA(cudaMemsetAsync(P->pool_top, 0, 8, s));
   FST_CUDA(cudaMemsetAsync(P->flags_d, 0, 8, s));
   if (fb) {
-    FST_CUDA(cudaMemsetAsync(P->scnt_b, 0, n4, s));
     FST_CUDA(cudaMemsetAsync(P->mkey, 0, n4, s));
     FST_CUDA(cudaMemsetAsync(P->ekey, 0, n4, s));
   }
@@ -315,16 +274,16 @@ int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_p
                      int32_t* d_status, cudaStream_t s) {
   fst_s* f = P->fst;
   int rc;
-  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
+  const LayoutView L = view_of(f->bwd);
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, nullptr);
   if ((rc = wave_begin(P, W, s, false))) return rc;
-  if (W.tmax >= 1) PROF(FST_PROF_VIT_FIRST, launch_expand(Lb, T, wave_step(P, W, 1, 0), S, s));
+  if (W.tmax >= 1) PROF(FST_PROF_VIT_FIRST, launch_vit_first(L, T, wave_step(P, W, 1, 0), S, s));
   for (int32_t t = 1; t <= W.tmax; ++t)
-    PROF(FST_PROF_VIT_STEP, launch_vit_step(Lf, Lb, T, wave_step(P, W, t, t + 1), S, s));
+    PROF(FST_PROF_VIT_STEP, launch_vit_step(L, T, wave_step(P, W, t, t + 1), S, s));
   PROF(FST_PROF_VIT_FINAL,
        launch_vit_final(S, W.Bw, d_scores + W.b0, P->qfinal, d_status ? d_status + W.b0 : nullptr, s));
-  PROF(FST_PROF_BACKTRACE, launch_backtrace(Lf, S, f->olabel, W.Bw, P->qfinal, d_paths + W.tok0,
+  PROF(FST_PROF_BACKTRACE, launch_backtrace(S, f->src_by_id, f->olabel, W.Bw, P->qfinal, d_paths + W.tok0,
                                             d_olabels ? d_olabels + W.tok0 : nullptr, s));
   return FST_OK;
 }
@@ -332,28 +291,27 @@ int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_p
 int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_status) {
   fst_s* f = P->fst;
   int rc;
-  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
+  const LayoutView L = view_of(f->bwd);
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, nullptr);
   if ((rc = wave_begin(P, W, s, true))) return rc;
-  if (W.tmax >= 1) PROF(FST_PROF_FWD_FIRST, launch_expand(Lb, T, wave_step(P, W, 1, 0), S, s));
-  for (int32_t t = 1; t <= W.tmax; ++t)
-    PROF(FST_PROF_FWD_STEP, launch_fwd_step(Lf, Lb, T, wave_step(P, W, t, t + 1), S, s));
+  if (W.tmax >= 1) PROF(FST_PROF_FWD_FIRST, launch_fwd_first(L, T, wave_step(P, W, 1, 0), S, s));
+  for (int32_t t = 1; t <= W.tmax; ++t) {
+    PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, wave_step(P, W, t, t - 1), S, s));
+    PROF(FST_PROF_FWD_STEP, launch_fwd_step(L, T, wave_step(P, W, t, t + 1), S, s));
+  }
   PROF(FST_PROF_FB_FINAL, launch_fb_final(S, W.Bw, P->logz + W.b0, d_status ? d_status + W.b0 : nullptr, s));
   return FST_OK;
 }
 
 int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cudaStream_t s) {
   fst_s* f = P->fst;
-  const LayoutView Lf = view_of(f->fwd), Lb = view_of(f->bwd);
+  const LayoutView L = view_of(f->bwd);
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, d_weights);
   const CountView C{1, nullptr, nullptr, P->cnt64};
-  for (int32_t t = W.tmax; t >= 1; --t) {
-    const StepView V = wave_step(P, W, t, t - 2);
-    PROF(FST_PROF_BWD_EXPAND, launch_bwd_expand(Lf, T, V, S, C, s));
-    if (t >= 2) PROF(FST_PROF_BWD_REDUCE, launch_bwd_reduce(Lb, T, V, S, s));
-  }
+  for (int32_t t = W.tmax; t >= 1; --t)
+    PROF(FST_PROF_BWD_STEP, launch_bwd_step(L, T, wave_step(P, W, t, t - 1), S, C, s));
   return FST_OK;
 }
 
@@ -406,8 +364,10 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
     for (int64_t i = 0; i < N; ++i) P->relax += f->h_sym_arc[hid[i] + 1] - f->h_sym_arc[hid[i]];
     // waves: consecutive strings whose memory fits the budget
     const int64_t budget = mem_budget_bytes > 0 ? mem_budget_bytes : ((int64_t)16 << 30);
-    const int64_t per_string = (int64_t)f->Q * 16 * (P->want_fb ? 2 : 1) + (int64_t)f->W * 4 + 64;
-    const int64_t per_token = TOKEN_BYTES + POOL_PER_TOKEN * (P->want_fb ? 12 : 8);
+    // accumulators: 2 x 8 bytes per state (Viterbi), or 2 x 16 for the
+    // forward sums and maxima plus 2 x 4 for the backward values
+    const int64_t per_string = (int64_t)f->Q * (P->want_fb ? 40 : 16) + 64;
+    const int64_t per_token = TOKEN_BYTES + POOL_PER_TOKEN * 12;
     int32_t b0 = 0;
     int64_t acc = 0;
     for (int32_t b = 0; b <= B; ++b) {
@@ -437,37 +397,31 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
       P->max_len = std::max(P->max_len, w.tmax);
       // live pool: its exact bound when that is small, else the largest of
       // POOL_PER_TOKEN entries per token, a quarter of the budget and 256 MiB
-      const int64_t ebytes = P->want_fb ? 12 : 8;
+      const int64_t ebytes = P->want_fb ? 16 : 12;
       const int64_t want = std::max(w.ntok * POOL_PER_TOKEN, std::max(budget / 4, (int64_t)256 << 20) / ebytes);
       P->pool_cap = std::max(P->pool_cap, std::min(w.pool_bound, want));
     }
     if (rc) break;
     const int64_t na = P->max_bw * 2 * (int64_t)f->Q;
     const int64_t nt = P->max_ntok;
-    if ((rc = alloc_track(P, &P->alpha, na))) break;
-    if (P->want_fb && (rc = alloc_track(P, &P->beta, na))) break;
-    if ((rc = alloc_track(P, &P->touch, P->max_bw * (int64_t)f->W)) ||
-        (rc = alloc_track(P, &P->touch_b, P->max_bw * (int64_t)f->W)) ||
-        (rc = alloc_track(P, &P->stage, P->max_stage)) || (rc = alloc_track(P, &P->stage_b, P->max_stage)) || (rc = alloc_track(P, &P->scnt_f, nt)) ||
-        (rc = alloc_track(P, &P->scnt_b, nt)) || (rc = alloc_track(P, &P->pool_q, P->pool_cap)) ||
-        (rc = alloc_track(P, &P->pool_x, P->pool_cap)) || (rc = alloc_track(P, &P->pool_base, nt)) ||
-        (rc = alloc_track(P, &P->pool_cnt, nt)) || (rc = alloc_track(P, &P->pool_top, 1)) ||
-        (rc = alloc_track(P, &P->slot_base, nt)) || (rc = alloc_track(P, &P->bslot_base, nt)) ||
+    P->acc_stride = P->want_fb ? 2 : 1;
+    if ((rc = alloc_track(P, &P->acc, na * P->acc_stride))) break;
+    if (P->want_fb && ((rc = alloc_track(P, &P->beta, na)) || (rc = alloc_track(P, &P->pool_n, P->pool_cap)))) break;
+    if ((rc = alloc_track(P, &P->stage, P->max_stage)) || (rc = alloc_track(P, &P->stage_b, P->max_stage)) ||
+        (rc = alloc_track(P, &P->scnt, nt)) || (rc = alloc_track(P, &P->pool_q, P->pool_cap)) ||
+        (rc = alloc_track(P, &P->pool_x, P->pool_cap)) || (rc = alloc_track(P, &P->pool_v, P->pool_cap)) ||
+        (rc = alloc_track(P, &P->pool_base, nt)) || (rc = alloc_track(P, &P->pool_cnt, nt)) ||
+        (rc = alloc_track(P, &P->pool_top, 1)) || (rc = alloc_track(P, &P->slot_base, nt)) ||
         (rc = alloc_track(P, &P->step_rng, 2 * ((int64_t)P->max_len + 2))) ||
-        (rc = alloc_track(P, &P->bstep_rng, 2 * ((int64_t)P->max_len + 2))) ||
         (rc = alloc_track(P, &P->flags_d, 2)) || (rc = alloc_track(P, &P->mkey, nt)) ||
         (rc = alloc_track(P, &P->ekey, nt)) || (rc = alloc_track(P, &P->csum, nt)) ||
         (rc = alloc_track(P, &P->esum, nt)) || (rc = alloc_track(P, &P->qfinal, P->max_bw)) ||
-        (rc = alloc_track(P, &P->logz, B)) || (rc = alloc_track(P, &P->epoch, 2)) ||
-        (rc = alloc_track(P, &P->clear, 1)))
+        (rc = alloc_track(P, &P->logz, B)))
       break;
-    if (P->want_fb && ((rc = alloc_track(P, &P->pool_v, P->pool_cap)) || (rc = alloc_track(P, &P->cnt64, f->fwd.P))))
-      break;
-    FST_CUDA(cudaMemsetAsync(P->alpha, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
-    if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s));
-    FST_CUDA(cudaMemsetAsync(P->touch, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)f->W) * 4, s));
-    FST_CUDA(cudaMemsetAsync(P->touch_b, 0, (size_t)std::max<int64_t>(1, P->max_bw * (int64_t)f->W) * 4, s));
-    FST_CUDA(cudaMemsetAsync(P->epoch, 0, 8, s));
+    if (P->want_fb && (rc = alloc_track(P, &P->cnt64, f->A))) break;
+    // the accumulators start at zero and every run leaves them so
+    FST_CUDA(cudaMemsetAsync(P->acc, 0, (size_t)std::max<int64_t>(na * P->acc_stride, 1) * 8, s));
+    if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 4, s));
     FST_CUDA(cudaMemsetAsync(P->flags_d, 0, 8, s));
     FST_CUDA(cudaStreamSynchronize(s));
   } while (0);
@@ -490,10 +444,13 @@ extern "C" int fst_plan_info(const fst_plan_t* P, int32_t* num_strings, int64_t*
                              int32_t* max_len, int64_t* relaxations, int64_t* viterbi_launches,
                              int64_t* fb_launches, int64_t* device_bytes) {
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
-  int64_t vl = 1, fl = 1;  // epoch kernel
+  int64_t vl = 0, fl = 0;
   for (const Wave& w : P->waves) {
-    vl += (int64_t)w.tmax + 3;  // first expand, one step per position, final, backtrace
-    fl += (int64_t)w.tmax + 2 + std::max<int64_t>(0, 2 * (int64_t)w.tmax - 1);  // forward, final, backward
+    // overflow clear, first push, one step per position, final, backtrace
+    vl += (int64_t)w.tmax + 4;
+    // overflow clear, first push, sum and step per position, final; one
+    // backward step per position
+    fl += 3 * (int64_t)w.tmax + 3;
   }
   fl += 1;  // counts out
   if (num_strings) *num_strings = P->B;
@@ -516,9 +473,8 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
   if (!P->want_vit) { set_error("plan was created without Viterbi storage"); return FST_ERR_STATE; }
   cudaStream_t s = as_stream(stream);
   int rc;
-  // the Viterbi run reuses the frontier and pool a pending backward pass needs
+  // the Viterbi run reuses the accumulators and pool a pending backward pass needs
   P->forward_done = false;
-  if ((rc = run_begin(P, s, false))) return rc;
   for (const Wave& W : P->waves)
     if ((rc = run_viterbi_wave(P, W, d_scores, d_paths, d_olabels, d_status, s))) return rc;
   return FST_OK;
@@ -530,7 +486,6 @@ extern "C" int fst_plan_forward(fst_plan_t* P, double* d_logz, int32_t* d_status
   if (P->waves.size() > 1) { set_error("fst_plan_forward needs a single-wave plan"); return FST_ERR_STATE; }
   cudaStream_t s = as_stream(stream);
   int rc;
-  if ((rc = run_begin(P, s, true))) return rc;
   for (const Wave& W : P->waves)
     if ((rc = run_forward_wave(P, W, s, d_status))) return rc;
   if (P->B > 0) FST_CUDA(cudaMemcpyAsync(d_logz, P->logz, (size_t)P->B * 8, cudaMemcpyDeviceToDevice, s));
@@ -544,11 +499,11 @@ extern "C" int fst_plan_backward(fst_plan_t* P, const float* d_weights, float* d
   fst_s* f = P->fst;
   cudaStream_t s = as_stream(stream);
   int rc;
-  FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->fwd.P) * 8, s));
+  FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->A) * 8, s));
   for (const Wave& W : P->waves)
     if ((rc = run_backward_wave(P, W, d_weights, s))) return rc;
   const CountView C{1, nullptr, nullptr, P->cnt64};
-  PROF(FST_PROF_COUNTS, launch_counts_out(f->fwd.arc_id, f->fwd.P, C, d_counts, s));
+  PROF(FST_PROF_COUNTS, launch_counts_out(f->A, C, d_counts, s));
   return FST_OK;
 }
 
@@ -559,8 +514,7 @@ extern "C" int fst_plan_forward_backward(fst_plan_t* P, const float* d_weights, 
   fst_s* f = P->fst;
   cudaStream_t s = as_stream(stream);
   int rc;
-  if ((rc = run_begin(P, s, true))) return rc;
-  if (d_counts) FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->fwd.P) * 8, s));
+  if (d_counts) FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->A) * 8, s));
   for (const Wave& W : P->waves) {
     if ((rc = run_forward_wave(P, W, s, d_status))) return rc;
     if (d_counts && (rc = run_backward_wave(P, W, d_weights, s))) return rc;
@@ -568,7 +522,7 @@ extern "C" int fst_plan_forward_backward(fst_plan_t* P, const float* d_weights, 
   if (P->B > 0) FST_CUDA(cudaMemcpyAsync(d_logz, P->logz, (size_t)P->B * 8, cudaMemcpyDeviceToDevice, s));
   if (d_counts) {
     const CountView C{1, nullptr, nullptr, P->cnt64};
-    PROF(FST_PROF_COUNTS, launch_counts_out(f->fwd.arc_id, f->fwd.P, C, d_counts, s));
+    PROF(FST_PROF_COUNTS, launch_counts_out(f->A, C, d_counts, s));
   }
   P->forward_done = P->waves.size() <= 1;
   return FST_OK;

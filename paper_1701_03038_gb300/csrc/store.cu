@@ -128,24 +128,10 @@ __global__ void k_seg_len(const int64_t* __restrict__ seg_first, int64_t nseg, i
   if (s < nseg) len[s] = (int32_t)(seg_first[s + 1] - seg_first[s]);
 }
 
-// pos_by_id[id] = forward position of arc id
-__global__ void k_pos_by_id(const int32_t* __restrict__ arc_id, int64_t P, int32_t* __restrict__ pos_by_id) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < P && arc_id[i] >= 0) pos_by_id[arc_id[i]] = (int32_t)i;
-}
-
-// segof[pos] = segment holding padded position pos (padding stays -1)
-__global__ void k_seg_of(const int32_t* __restrict__ seg_pos, const int32_t* __restrict__ seg_len, int64_t nseg,
-                         int32_t* __restrict__ segof) {
-  const int64_t sg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (sg >= nseg) return;
-  const int32_t p0 = seg_pos[sg];
-  for (int32_t i = 0; i < seg_len[sg]; ++i) segof[p0 + i] = (int32_t)sg;
-}
-
-// Insert every segment (symbol, state) -> index into the open-addressing
-// table; one thread per symbol's segment range entry.
+// Insert every segment (symbol, state) -> (first position, length) into the
+// open-addressing table; one thread per segment.
 __global__ void k_hash_insert(const int64_t* __restrict__ sym_seg, int32_t m, const int32_t* __restrict__ seg_state,
+                              const int32_t* __restrict__ seg_pos, const int32_t* __restrict__ seg_len,
                               int64_t nseg, ulonglong2* __restrict__ tab, int64_t mask) {
   const int64_t sg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (sg >= nseg) return;
@@ -159,20 +145,11 @@ __global__ void k_hash_insert(const int64_t* __restrict__ sym_seg, int32_t m, co
   for (int64_t probe = 0; probe <= mask; ++probe) {
     const unsigned long long old = atomicCAS(&tab[h].x, ~0ull, (unsigned long long)k);
     if (old == ~0ull || old == k) {
-      tab[h].y = (unsigned long long)sg;
+      tab[h].y = ((unsigned long long)(uint32_t)seg_len[sg] << 32) | (unsigned long long)(uint32_t)seg_pos[sg];
       return;
     }
     h = (h + 1) & (uint64_t)mask;
   }
-}
-
-// xseg[i] = segment of the other layout that holds the arc at position i
-__global__ void k_xseg(const int32_t* __restrict__ arc_id, int64_t P, const int32_t* __restrict__ pos_by_id_other,
-                       const int32_t* __restrict__ segof_other, int32_t* __restrict__ xseg) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P) return;
-  const int32_t k = arc_id[i];
-  xseg[i] = k >= 0 ? segof_other[pos_by_id_other[k]] : -1;
 }
 
 __global__ void k_scatter_arcs(const uint32_t* __restrict__ perm, const int64_t* __restrict__ hd,
@@ -232,6 +209,12 @@ __global__ void k_gather_sym(const int64_t* __restrict__ x, const int64_t* __res
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a > m) return;
   out[a] = x[sym_seg[a]];
+}
+
+__global__ void k_pack_arcs(const int32_t* __restrict__ other, const float* __restrict__ theta,
+                            const int32_t* __restrict__ arc_id, int64_t P, int4* __restrict__ arcs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P) arcs[i] = make_int4(other[i], __float_as_int(theta[i]), arc_id[i], 0);
 }
 
 __global__ void k_set_weights(const int32_t* __restrict__ id, const float* __restrict__ th_by_id, int64_t P,
@@ -369,7 +352,7 @@ int build_layout(fst_s* f, Layout& L, const int32_t* d_il, const int32_t* seg_st
 
 void free_layout(Layout& L) {
   dfree(L.other); dfree(L.theta); dfree(L.arc_id); dfree(L.theta64); dfree(L.win);
-  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.seg_len); dfree(L.xseg); dfree(L.seg_hash); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
+  dfree(L.seg_state); dfree(L.seg_pos); dfree(L.seg_len); dfree(L.seg_hash); dfree(L.arcs); dfree(L.sym_win); dfree(L.sym_seg); dfree(L.sym_lseg);
   dfree(L.sym_lwin);
   free(L.h_sym_win); free(L.h_sym_seg); free(L.h_sym_lseg); free(L.h_sym_lwin);
   L.h_sym_win = L.h_sym_seg = L.h_sym_lseg = L.h_sym_lwin = nullptr;
@@ -384,33 +367,16 @@ int build_store(fst_s* f, const int32_t* d_src, const int32_t* d_dst, const int3
   if ((rc = build_layout(f, f->fwd, d_il, d_dst, d_src, d_theta, &f->h_sym_arc, f->sym_arc, s))) return rc;
   // backward: segments by source, arcs carry their destination
   if ((rc = build_layout(f, f->bwd, d_il, d_src, d_dst, d_theta, nullptr, nullptr, s))) return rc;
-  // each arc knows the segment of the other layout that holds it: a live
-  // source's arcs (backward layout) lead to the destination segments to
-  // reduce (forward layout), and the other way round in the backward pass
-  int32_t *fpos = nullptr, *bpos = nullptr, *fsegof = nullptr, *bsegof = nullptr;
-  auto release = [&]() { dfree(fpos); dfree(bpos); dfree(fsegof); dfree(bsegof); };
-  if ((rc = dalloc(&fpos, f->A)) || (rc = dalloc(&bpos, f->A)) || (rc = dalloc(&fsegof, f->fwd.P)) ||
-      (rc = dalloc(&bsegof, f->bwd.P)) || (rc = dalloc(&f->fwd.xseg, f->fwd.P)) || (rc = dalloc(&f->bwd.xseg, f->bwd.P))) {
-    release();
-    return rc;
+  // the fixed-point sums of the step kernels add at most one term of at
+  // most 2^40 per arc of a segment: 2^24 arcs would overflow 64 bits
+  if (f->max_seg_len >= (1 << 24)) {
+    set_error("a state has %d arcs on one symbol, beyond the 2^24 the step kernels support", f->max_seg_len);
+    return FST_ERR_UNSUPPORTED;
   }
-  cudaError_t e = cudaSuccess;
-  if (f->fwd.P > 0) e = cudaMemsetAsync(fsegof, 0xff, (size_t)f->fwd.P * 4, s);
-  if (e == cudaSuccess && f->bwd.P > 0) e = cudaMemsetAsync(bsegof, 0xff, (size_t)f->bwd.P * 4, s);
-  if (e == cudaSuccess) {
-    if (f->fwd.P > 0) k_pos_by_id<<<blocks_for(f->fwd.P), TB, 0, s>>>(f->fwd.arc_id, f->fwd.P, fpos);
-    if (f->bwd.P > 0) k_pos_by_id<<<blocks_for(f->bwd.P), TB, 0, s>>>(f->bwd.arc_id, f->bwd.P, bpos);
-    if (f->fwd.nseg > 0)
-      k_seg_of<<<blocks_for(f->fwd.nseg), TB, 0, s>>>(f->fwd.seg_pos, f->fwd.seg_len, f->fwd.nseg, fsegof);
-    if (f->bwd.nseg > 0)
-      k_seg_of<<<blocks_for(f->bwd.nseg), TB, 0, s>>>(f->bwd.seg_pos, f->bwd.seg_len, f->bwd.nseg, bsegof);
-    if (f->fwd.P > 0) k_xseg<<<blocks_for(f->fwd.P), TB, 0, s>>>(f->fwd.arc_id, f->fwd.P, bpos, bsegof, f->fwd.xseg);
-    if (f->bwd.P > 0) k_xseg<<<blocks_for(f->bwd.P), TB, 0, s>>>(f->bwd.arc_id, f->bwd.P, fpos, fsegof, f->bwd.xseg);
-    e = cudaStreamSynchronize(s);
-  }
-  release();
-  if (e != cudaSuccess) return cuda_fail(e, "segments of the other layout");
-  // (symbol, state) -> segment of the source-segmented layout: the expand
+  // source state by caller arc id (the backtrace follows arc ids)
+  if ((rc = dalloc(&f->src_by_id, f->A))) return rc;
+  if (f->A > 0) FST_CUDA(cudaMemcpyAsync(f->src_by_id, d_src, (size_t)f->A * 4, cudaMemcpyDeviceToDevice, s));
+  // (symbol, state) -> segment of the source-segmented layout: the step
   // kernels find a live state's arcs on a symbol with about one probe
   {
     Layout& L = f->bwd;
@@ -420,7 +386,10 @@ int build_store(fst_s* f, const int32_t* d_src, const int32_t* d_dst, const int3
     L.hash_mask = size - 1;
     FST_CUDA(cudaMemsetAsync(L.seg_hash, 0xff, (size_t)size * sizeof(ulonglong2), s));
     if (L.nseg > 0)
-      k_hash_insert<<<blocks_for(L.nseg), TB, 0, s>>>(L.sym_seg, f->m, L.seg_state, L.nseg, L.seg_hash, L.hash_mask);
+      k_hash_insert<<<blocks_for(L.nseg), TB, 0, s>>>(L.sym_seg, f->m, L.seg_state, L.seg_pos, L.seg_len, L.nseg,
+                                                      L.seg_hash, L.hash_mask);
+    if ((rc = dalloc(&L.arcs, L.P))) return rc;
+    if (L.P > 0) k_pack_arcs<<<blocks_for(L.P), TB, 0, s>>>(L.other, L.theta, L.arc_id, L.P, L.arcs);
     FST_CUDA(cudaStreamSynchronize(s));
   }
   return FST_OK;
@@ -428,8 +397,10 @@ int build_store(fst_s* f, const int32_t* d_src, const int32_t* d_dst, const int3
 
 int set_layout_weights(fst_s* f, const float* d_theta_by_id, cudaStream_t s) {
   Layout* Ls[2] = {&f->fwd, &f->bwd};
-  for (Layout* L : Ls)
+  for (Layout* L : Ls) {
     if (L->P > 0) k_set_weights<<<blocks_for(L->P), TB, 0, s>>>(L->arc_id, d_theta_by_id, L->P, L->theta);
+    if (L->P > 0 && L->arcs) k_pack_arcs<<<blocks_for(L->P), TB, 0, s>>>(L->other, L->theta, L->arc_id, L->P, L->arcs);
+  }
   FST_CUDA(cudaGetLastError());
   return FST_OK;
 }
