@@ -52,9 +52,9 @@ __device__ __forceinline__ int32_t warp_id_global() { return (int32_t)((blockIdx
 __device__ __forceinline__ float decode_max(uint32_t k) { return k ? fkey_inv(k) : neg_inf(); }
 
 // Owner of flat entry j among the n slots whose first entries base[0..n)
-// are nondecreasing with base[0] <= j: the last slot with base <= j.  A warp
-// first finds the owner of its chunk start j0 (warp-uniform, 32-way search),
-// then each lane walks forward to its own entry (usually zero or one step).
+// are nondecreasing with base[0] <= j: the last slot with base <= j.  The
+// warp first finds the owner of its chunk start j0 (warp-uniform, 32-way
+// search); flat_owner then places each lane among the 32 slots that follow.
 __device__ __forceinline__ int32_t warp_owner(const int64_t* __restrict__ base, int32_t n, int64_t j0) {
   const int lane = threadIdx.x & 31;
   int32_t lo = 0, hi = n;
@@ -67,9 +67,41 @@ __device__ __forceinline__ int32_t warp_owner(const int64_t* __restrict__ base, 
   }
   return lo;
 }
-__device__ __forceinline__ int32_t lane_owner(const int64_t* __restrict__ base, int32_t n, int32_t k, int64_t j) {
-  while (k + 1 < n && __ldcg(base + k + 1) <= j) ++k;
-  return k;
+// An entry for lanes past the range end: the last entry, or c0 when the
+// warp lies wholly past it (the result is unused there).
+__device__ __forceinline__ int64_t clamp_entry(int64_t j, int64_t c0, int64_t R1) {
+  const int64_t last = R1 - 1 > c0 ? R1 - 1 : c0;
+  return j < last ? j : last;
+}
+
+struct Owner {
+  int32_t k;      // the owning slot
+  int64_t first;  // its first entry, base[k]
+};
+// Owner of this lane's entry j >= c0, c0 the warp's first entry (uniform).
+// All 32 lanes take part: the warp loads the 32 slot bases from the owner
+// of c0 on and each lane binary-searches them in registers (five shuffles);
+// an entry past them (a run of slots with no entries) is walked to.
+__device__ __forceinline__ Owner flat_owner(const int64_t* __restrict__ base, int32_t n, int64_t c0, int64_t j) {
+  const int lane = threadIdx.x & 31;
+  const int32_t k0 = warp_owner(base, n, c0);
+  const long long bv = k0 + lane < n ? (long long)__ldcg(base + k0 + lane) : (long long)INT64_MAX;
+  int idx = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const long long v = __shfl_sync(FULL, bv, idx + step);
+    if (v <= j) idx += step;
+  }
+  Owner o{k0 + idx, (int64_t)__shfl_sync(FULL, bv, idx)};
+  if (idx == 31) {
+    while (o.k + 1 < n) {
+      const int64_t nb = __ldcg(base + o.k + 1);
+      if (nb > j) break;
+      ++o.k;
+      o.first = nb;
+    }
+  }
+  return o;
 }
 
 // The arcs out of state q on symbol a: a lookup in the open-addressing
@@ -360,7 +392,7 @@ struct Source {
   bool head;   // first entry of its token (writes the token's scalars)
 };
 __device__ __forceinline__ Source source_at(const TokenView& T, const StepView& V, const FrontierState& S,
-                                            int32_t k0, int64_t j) {
+                                            const Owner& o, int64_t j) {
   Source x{-1, 0, 0.f, false};
   if (V.t == 1) {
     x.p = __ldg(T.step_tok + V.slot0 + (int32_t)(j / S.nstart));
@@ -368,14 +400,12 @@ __device__ __forceinline__ Source source_at(const TokenView& T, const StepView& 
     x.r = __ldg(S.theta_s + x.q);
     x.head = j % S.nstart == 0;
   } else {
-    const int64_t* base = S.slot_base + V.x_slot0;
-    const int32_t k = lane_owner(base, V.x_n, k0, j);
-    const int32_t pp = __ldg(T.step_tok + V.x_slot0 + k);
+    const int32_t pp = __ldg(T.step_tok + V.x_slot0 + o.k);
     if (S.bw_n[__ldg(T.b + pp)] >= V.t) {
       x.p = pp + 1;
       x.q = S.pool_q[j];
       x.r = S.pool_v[j];
-      x.head = __ldcg(base + k) == j;
+      x.head = o.first == j;
     }
   }
   return x;
@@ -407,7 +437,7 @@ __device__ __forceinline__ void first_position(const LayoutView& L, const TokenV
     int32_t e0 = 0, len = 0;
     PushCtx me{0, 0, 0.f};
     if (j < R1) {
-      const Source x = source_at(T, V, S, 0, j);
+      const Source x = source_at(T, V, S, Owner{0, 0}, j);
       const Arcs r = find_arcs(L, __ldg(T.sym + x.p), x.q);
       e0 = r.pos;
       len = r.len;
@@ -431,12 +461,10 @@ __global__ void __launch_bounds__(KT) k_fwd_first(LayoutView L, TokenView T, Ste
 struct Entry {
   int32_t p, i;
 };
-__device__ __forceinline__ Entry step_entry(const TokenView& T, const StepView& V, const int64_t* slot_base,
-                                            int32_t k0, int64_t j) {
-  const int32_t k = lane_owner(slot_base + V.slot0, V.n, k0, j);
+__device__ __forceinline__ Entry step_entry(const TokenView& T, const StepView& V, const Owner& o, int64_t j) {
   Entry x;
-  x.p = __ldg(T.step_tok + V.slot0 + k);
-  x.i = (int32_t)(j - __ldcg(slot_base + V.slot0 + k));
+  x.p = __ldg(T.step_tok + V.slot0 + o.k);
+  x.i = (int32_t)(j - o.first);
   return x;
 }
 
@@ -459,12 +487,12 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
   const int32_t* stg = fwd_stage(S, t);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
     const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
-    const int32_t k0 = warp_owner(S.slot_base + V.slot0, V.n, c0);
     const int64_t j = c0 + lane;
+    const Owner o = flat_owner(S.slot_base + V.slot0, V.n, c0, clamp_entry(j, c0, R1));
     int32_t e0 = 0, len = 0;
     PushCtx nx{0, 0, 0.f};
     if (j < R1) {
-      const Entry x = step_entry(T, V, S.slot_base, k0, j);
+      const Entry x = step_entry(T, V, o, j);
       const int32_t b = __ldg(T.b + x.p);
       const int32_t d = stg[__ldg(T.stf + x.p) + x.i];
       const int64_t slot = acc_slot(S, b, t, d);
@@ -533,12 +561,13 @@ __global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepV
   source_range(V, S, &R0, &R1);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
     const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);
-    const int32_t k0 = t > 1 ? warp_owner(S.slot_base + V.x_slot0, V.x_n, c0) : 0;
     const int64_t j = c0 + lane;
+    Owner o{0, 0};
+    if (t > 1) o = flat_owner(S.slot_base + V.x_slot0, V.x_n, c0, clamp_entry(j, c0, R1));  // t is uniform
     int32_t e0 = 0, len = 0;
     PushCtx me{0, 0, 0.f};
     if (j < R1) {
-      const Source x = source_at(T, V, S, k0, j);
+      const Source x = source_at(T, V, S, o, j);
       if (x.p >= 0) {
         const Arcs r = source_arcs(L, T, V, S, x, j);
         e0 = r.pos;
@@ -599,12 +628,13 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Step
   source_range(V, S, &R0, &R1);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
     const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);
-    const int32_t k0 = t > 1 ? warp_owner(S.slot_base + V.x_slot0, V.x_n, c0) : 0;
     const int64_t j = c0 + lane;
+    Owner o{0, 0};
+    if (t > 1) o = flat_owner(S.slot_base + V.x_slot0, V.x_n, c0, clamp_entry(j, c0, R1));  // t is uniform
     int32_t e0 = 0, len = 0, q = -1, p = -1;
     BwdCtx me{0, 0, 0.f, 0.f, 0.f, 0.f, 0.0};
     if (j < R1) {
-      const Source x = source_at(T, V, S, k0, j);
+      const Source x = source_at(T, V, S, o, j);
       const int32_t b = x.p >= 0 ? __ldg(T.b + x.p) : 0;
       const double lz = x.p >= 0 ? S.logz[b] : -INFINITY;
       if (lz != -INFINITY) {
