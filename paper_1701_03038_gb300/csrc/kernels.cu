@@ -147,10 +147,11 @@ __device__ __forceinline__ uint32_t* fwd_max(const FrontierState& S, int64_t slo
 // the end.  The tokens from the first whose range would pass `cap` on get
 // empty ranges (slot base INT64_MAX, so no flat index maps to them) and
 // raise error bit 1: every status of the run then reports FST_ERR_OOM.
-// Each thread takes RPT consecutive slots (their loads issued together),
-// then the block scans the thread totals (two warp levels); RPT * KT slots
-// per round, so one round for up to 4,096 tokens.
-constexpr int RPT = 16;
+// Each thread takes RPT consecutive slots: it sums their counts (loads
+// issued together), the block scans the thread totals (two warp levels),
+// and the thread reloads its slots to write their ranges.  RPT * KT slots
+// per round.
+constexpr int RPT = 8;
 
 __device__ void ranges_last_block(const TokenView& T, const StepView& V, const FrontierState& S,
                                   const uint32_t* cnt, int64_t* top, int64_t cap, int64_t* slot_out,
@@ -194,9 +195,17 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
       round += wsum[w];
     }
     base += incl - run;
-    for (int i = 0; i < RPT && k0 + i < V.n; ++i) {
-      const int32_t p = __ldg(T.step_tok + V.slot0 + k0 + i);
-      const long long m = (long long)__ldcg(cnt + p);
+    int32_t pv[RPT];
+    uint32_t mv[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) pv[i] = k0 + i < V.n ? __ldg(T.step_tok + V.slot0 + k0 + i) : -1;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) mv[i] = pv[i] >= 0 ? __ldcg(cnt + pv[i]) : 0u;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      if (pv[i] < 0) break;
+      const int32_t p = pv[i];
+      const long long m = (long long)mv[i];
       const bool fit = base + m <= (long long)cap;
       if (!fit) atomicMin(&first_bad, base);
       slot_out[V.slot0 + k0 + i] = fit ? base : INT64_MAX;
@@ -270,21 +279,22 @@ __device__ __forceinline__ int block_owner(const int32_t* excl, int32_t a) {
   return o;
 }
 
-// fn(e, ctx of e's owner, owner) for every arc of every thread's segment.
+// fn(e, ctx of e's owner, owner, valid) for every arc of every thread's
+// segment.  Every thread runs the same rounds and calls fn VU times per
+// round (valid = false past the end), so fn may use warp collectives.
 template <class Ctx, class F>
 __device__ __forceinline__ void block_walk(BlockScratch<Ctx>& sh, int32_t total, F fn) {
-  for (int32_t a0 = threadIdx.x; a0 < total; a0 += KT * VU) {
+  for (int32_t a0 = 0; a0 < total; a0 += KT * VU) {
     int oo[VU];
     int32_t ee[VU];
 #pragma unroll
     for (int u = 0; u < VU; ++u) {
-      const int32_t a = a0 + u * KT;
-      oo[u] = a < total ? block_owner(sh.excl, a) : -1;
-      ee[u] = oo[u] >= 0 ? sh.e0[oo[u]] + (a - sh.excl[oo[u]]) : 0;
+      const int32_t a = a0 + u * KT + (int32_t)threadIdx.x;
+      oo[u] = a < total ? block_owner(sh.excl, a) : 0;
+      ee[u] = a < total ? sh.e0[oo[u]] + (a - sh.excl[oo[u]]) : 0;
     }
 #pragma unroll
-    for (int u = 0; u < VU; ++u)
-      if (oo[u] >= 0) fn(ee[u], sh.ctx[oo[u]], oo[u]);
+    for (int u = 0; u < VU; ++u) fn(ee[u], sh.ctx[oo[u]], oo[u], a0 + u * KT + (int32_t)threadIdx.x < total);
   }
 }
 
@@ -300,12 +310,13 @@ __device__ __forceinline__ int32_t block_stage(BlockScratch<Ctx>& sh, int32_t e0
   return total;
 }
 
-// visit(e, ctx) for every arc of every thread's segment.
+// visit(e, ctx, valid) for every arc of every thread's segment, called by
+// all threads in the same rounds (valid = false past the end).
 template <class Ctx, class F>
 __device__ __forceinline__ void block_visit(BlockScratch<Ctx>& sh, int32_t e0, int32_t len, const Ctx& mine,
                                             F visit) {
   const int32_t total = block_stage(sh, e0, len, mine);
-  block_walk(sh, total, [&](int32_t e, const Ctx& c, int) { visit(e, c); });
+  block_walk(sh, total, [&](int32_t e, const Ctx& c, int, bool valid) { visit(e, c, valid); });
   __syncthreads();
 }
 
@@ -332,7 +343,9 @@ template <class Op, class Ctx, class F>
 __device__ __forceinline__ typename Op::T block_reduce(BlockScratch<Ctx>& sh, int32_t e0, int32_t len,
                                                        const Ctx& mine, F value) {
   const int32_t total = block_stage(sh, e0, len, mine);
-  block_walk(sh, total, [&](int32_t e, const Ctx& c, int o) { Op::atomic(&sh.acc[o], Op::key(value(e, c))); });
+  block_walk(sh, total, [&](int32_t e, const Ctx& c, int o, bool valid) {
+    if (valid) Op::atomic(&sh.acc[o], Op::key(value(e, c)));
+  });
   __syncthreads();
   const typename Op::T r = Op::value(sh.acc[threadIdx.x]);
   __syncthreads();
@@ -353,6 +366,37 @@ __device__ __forceinline__ float fix_log_sum(float m, unsigned long long s) {
                                                         : m + (float)log((double)s * 0x1p-40);
 }
 
+// Atomic max of key into a[p] for the lanes that hold one (p >= 0), with one
+// atomic per run of equal p: the lanes of a warp hold consecutive flat
+// entries, so equal tokens are adjacent and a segmented max over the warp
+// (five shuffle rounds) leaves each run's maximum on its last lane.  All 32
+// lanes call it.
+__device__ __forceinline__ void warp_max_by_token(uint32_t* a, int32_t p, uint32_t key) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t k2 = __shfl_up_sync(FULL, key, d);
+    const int32_t p2 = __shfl_up_sync(FULL, p, d);
+    if (lane >= d && p2 == p) key = k2 > key ? k2 : key;
+  }
+  const int32_t pn = __shfl_down_sync(FULL, p, 1);
+  if (p >= 0 && key != 0u && (lane == 31 || pn != p)) atomicMax(a + p, key);
+}
+
+// A slot in token p's staging list for every lane with want set: one
+// atomicAdd per group of lanes with the same token.  All 32 lanes call it;
+// returns the lane's index in the list (undefined when !want).
+__device__ __forceinline__ uint32_t warp_stage_index(uint32_t* cnt, int32_t p, bool want) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t wants = __ballot_sync(FULL, want);
+  const uint32_t peers = __match_any_sync(FULL, want ? p : -1) & wants;
+  const int head = peers ? __ffs(peers) - 1 : lane;
+  uint32_t base = 0u;
+  if (want && lane == head) base = atomicAdd(cnt + p, (uint32_t)__popc(peers));
+  base = __shfl_sync(FULL, base, head);
+  return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
 // ======================================================================
 // Push (Alg. 1 / Alg. 2 forward loops over the arcs of live sources).
 // ======================================================================
@@ -364,22 +408,28 @@ struct PushCtx {
 
 // Arc e out of a live source, into position t: the atomic max on the
 // destination's accumulator, and the staging of a destination met first.
+// All 32 lanes call it (valid = false: no arc).
 template <bool VIT>
 __device__ __forceinline__ void push_arc(const LayoutView& L, const TokenView& T, const FrontierState& S,
-                                         int32_t t, int32_t e, const PushCtx& c) {
-  const int4 a = __ldg(L.arcs + e);
-  const int32_t d = a.x;
-  const float u = __fadd_rn(c.r, __int_as_float(a.y));
-  if (u == neg_inf()) return;
-  const int64_t slot = acc_slot(S, c.b, t, d);
-  bool first;
-  if (VIT) {
-    const uint32_t id = (uint32_t)a.z;
-    first = atomicMax(vit_key(S, slot), ((unsigned long long)fkey(u) << 32) | (unsigned long long)(~id)) == 0ull;
-  } else {
-    first = atomicMax(fwd_max(S, slot), fkey(u)) == 0u;
+                                         int32_t t, int32_t e, const PushCtx& c, bool valid) {
+  bool first = false;
+  int32_t d = 0;
+  if (valid) {
+    const int4 a = __ldg(L.arcs + e);
+    d = a.x;
+    const float u = __fadd_rn(c.r, __int_as_float(a.y));
+    if (u != neg_inf()) {
+      const int64_t slot = acc_slot(S, c.b, t, d);
+      if (VIT) {
+        const uint32_t id = (uint32_t)a.z;
+        first = atomicMax(vit_key(S, slot), ((unsigned long long)fkey(u) << 32) | (unsigned long long)(~id)) == 0ull;
+      } else {
+        first = atomicMax(fwd_max(S, slot), fkey(u)) == 0u;
+      }
+    }
   }
-  if (first) fwd_stage(S, t)[__ldg(T.stf + c.p) + atomicAdd(S.scnt + c.p, 1u)] = d;
+  const uint32_t i = warp_stage_index(S.scnt, c.p, first);
+  if (first) fwd_stage(S, t)[__ldg(T.stf + c.p) + i] = d;
 }
 
 // Live source j of position t-1 for the tokens of position t: at t = 1 the
@@ -443,7 +493,7 @@ __device__ __forceinline__ void first_position(const LayoutView& L, const TokenV
       len = r.len;
       me = PushCtx{x.p, __ldg(T.b + x.p), x.r};
     }
-    block_visit(sh, e0, len, me, [&](int32_t e, const PushCtx& c) { push_arc<VIT>(L, T, S, 1, e, c); });
+    block_visit(sh, e0, len, me, [&](int32_t e, const PushCtx& c, bool ok) { push_arc<VIT>(L, T, S, 1, e, c, ok); });
   }
   ranges_last_block(T, V, S, S.scnt, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt, S.step_rng + 2);
 }
@@ -491,6 +541,8 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
     const Owner o = flat_owner(S.slot_base + V.slot0, V.n, c0, clamp_entry(j, c0, R1));
     int32_t e0 = 0, len = 0;
     PushCtx nx{0, 0, 0.f};
+    int32_t mk_p = -1;  // forward: the token and order key of this lane's value
+    uint32_t mk_key = 0u;
     if (j < R1) {
       const Entry x = step_entry(T, V, o, j);
       const int32_t b = __ldg(T.b + x.p);
@@ -505,7 +557,8 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
         const ulonglong2 a = *(const ulonglong2*)fwd_sum(S, slot);
         const float sh_prev = t > 1 ? decode_max(S.mkey[x.p - 1]) : 0.f;
         r = fix_log_sum(fkey_inv((uint32_t)a.y) - sh_prev, a.x);
-        atomicMax(S.mkey + x.p, fkey(r));
+        mk_p = x.p;
+        mk_key = fkey(r);
       }
       S.pool_q[j] = d;
       S.pool_v[j] = r;
@@ -528,7 +581,9 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
         S.pool_n[j] = nxt.len;
       }
     }
-    block_visit(sh, e0, len, nx, [&](int32_t e, const PushCtx& c) { push_arc<VIT>(L, T, S, t + 1, e, c); });
+    if (!VIT) warp_max_by_token(S.mkey, mk_p, mk_key);  // the step maximum m_t
+    block_visit(sh, e0, len, nx,
+                [&](int32_t e, const PushCtx& c, bool ok) { push_arc<VIT>(L, T, S, t + 1, e, c, ok); });
   }
   // pool ranges of position t+1's tokens
   if (V.x_n > 0) {
@@ -575,7 +630,8 @@ __global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepV
         me = PushCtx{x.p, __ldg(T.b + x.p), x.r};
       }
     }
-    block_visit(sh, e0, len, me, [&](int32_t e, const PushCtx& c) {
+    block_visit(sh, e0, len, me, [&](int32_t e, const PushCtx& c, bool ok) {
+      if (!ok) return;
       const int4 a = __ldg(L.arcs + e);
       const float u = __fadd_rn(c.r, __int_as_float(a.y));
       if (u == neg_inf()) return;
@@ -678,11 +734,17 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Step
           add_count(C, a.z, __expf((float)ex) * c.gw);
           return fix_exp(th + (ub - c.et), c.m);
         });
+    int32_t ek_p = -1;
+    uint32_t ek_key = 0u;
     if (q >= 0 && t > 1) {
       const float u = fix_log_sum(me.m, su);
       S.beta[acc_slot(S, me.b, t - 1, q)] = u;
-      if (u != neg_inf()) atomicMax(S.ekey + p - 1, fkey(u));
+      if (u != neg_inf()) {
+        ek_p = p - 1;
+        ek_key = fkey(u);
+      }
     }
+    warp_max_by_token(S.ekey, ek_p, ek_key);  // the step maximum e_{t-1}
   }
 }
 
