@@ -255,7 +255,7 @@ FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t*
  *   stream     cudaStream_t; the call is asynchronous on it.
  * Results are bit-identical to fst_viterbi.  Returns FST_ERR_UNSUPPORTED
  * (nothing is launched) when the string needs more than the fixed array:
- * about 16*Q + 12*(sum over positions of the distinct destinations of the
+ * about 24*Q + 16*(sum over positions of the distinct destinations of the
  * position's symbol) + 8*(the largest such count) + 60*n bytes.  The
  * first call on a device looks up the array's device address with that
  * device current: make it before any stream capture.  All calls share the array and see the previous call's

@@ -112,6 +112,7 @@ struct DevBuf {
 struct PlainWs {
   unsigned long long* acc = nullptr;    // [2][Q] x 2 words (sum, maximum), zero between runs
   float* beta = nullptr;                // [2][Q]
+  int32_t* vmap = nullptr;              // [2][Q]
   int32_t *tok_sym = nullptr, *tok_b = nullptr;
   int32_t* iota = nullptr;              // step list: token t-1 is the only slot of position t
   int64_t* zero64 = nullptr;            // staging offsets: one token per step
@@ -129,17 +130,17 @@ struct PlainWs {
   float* pool_v = nullptr;
   int64_t cap_pool = 0;
   float *cnt = nullptr, *comp = nullptr, *counts_out = nullptr;
-  int32_t *qfinal = nullptr, *status = nullptr, *bw_n = nullptr;
+  int32_t *jfinal = nullptr, *status = nullptr, *bw_n = nullptr;
   float* score = nullptr;
   double* logz = nullptr;
   int64_t* bw_off = nullptr;
   int64_t* pool_top = nullptr;
   uint32_t* flags = nullptr;
   ~PlainWs() {
-    dfree(acc); dfree(beta); dfree(tok_sym); dfree(tok_b); dfree(iota); dfree(zero64);
+    dfree(acc); dfree(beta); dfree(vmap); dfree(tok_sym); dfree(tok_b); dfree(iota); dfree(zero64);
     dfree(slot_base); dfree(step_rng); dfree(scnt); dfree(pool_base); dfree(pool_cnt); dfree(mkey); dfree(ekey);
     dfree(csum); dfree(esum); dfree(paths); dfree(olabels); dfree(stage); dfree(stage_b); dfree(pool_q);
-    dfree(pool_x); dfree(pool_n); dfree(pool_v); dfree(cnt); dfree(comp); dfree(counts_out); dfree(qfinal); dfree(status);
+    dfree(pool_x); dfree(pool_n); dfree(pool_v); dfree(cnt); dfree(comp); dfree(counts_out); dfree(jfinal); dfree(status);
     dfree(bw_n); dfree(score); dfree(logz); dfree(bw_off); dfree(pool_top); dfree(flags);
   }
 };
@@ -152,8 +153,8 @@ int plain_init(fst_s* f) {
   f->plain = w;
   const int64_t Q = f->Q;
   int rc;
-  if ((rc = dalloc(&w->acc, 4 * Q)) || (rc = dalloc(&w->beta, 2 * Q)) ||
-      (rc = dalloc(&w->qfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
+  if ((rc = dalloc(&w->acc, 4 * Q)) || (rc = dalloc(&w->beta, 2 * Q)) || (rc = dalloc(&w->vmap, 2 * Q)) ||
+      (rc = dalloc(&w->jfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
       (rc = dalloc(&w->logz, 1)) || (rc = dalloc(&w->bw_n, 1)) || (rc = dalloc(&w->bw_off, 1)) ||
       (rc = dalloc(&w->pool_top, 1)) || (rc = dalloc(&w->flags, 2)))
     return rc;
@@ -247,6 +248,8 @@ FrontierState plain_state(fst_s* f) {
   S.acc = w->acc;
   S.acc_stride = 2;
   S.beta = w->beta;
+  S.vmap = w->vmap;
+  S.src_by_id = f->src_by_id;
   S.stage = w->stage;
   S.stage_b = w->stage_b;
   S.scnt = w->scnt;
@@ -489,8 +492,8 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
   if (n >= 1 && (rc = launch_vit_first(L, T, plain_step(f, n, 1, 0), S, s))) return rc;
   for (int32_t t = 1; t <= n; ++t)
     if ((rc = launch_vit_step(L, T, plain_step(f, n, t, t + 1), S, s))) return rc;
-  if ((rc = launch_vit_final(S, 1, w->score, w->qfinal, w->status, s))) return rc;
-  if ((rc = launch_backtrace(S, f->src_by_id, f->olabel, 1, w->qfinal, w->paths, w->olabels, s))) return rc;
+  if ((rc = launch_vit_final(S, 1, w->score, w->jfinal, w->status, s))) return rc;
+  if ((rc = launch_backtrace(S, f->olabel, 1, w->jfinal, w->paths, w->olabels, s))) return rc;
   int32_t st = 0;
   FST_CUDA(cudaMemcpy(best_score, w->score, 4, cudaMemcpyDeviceToHost));
   FST_CUDA(cudaMemcpy(&st, w->status, 4, cudaMemcpyDeviceToHost));

@@ -552,7 +552,12 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
       if (VIT) {
         const unsigned long long key = *vit_key(S, slot);
         r = fkey_inv((uint32_t)(key >> 32));
-        S.pool_x[j] = (int32_t)(~(uint32_t)key);  // the best incoming arc
+        const int32_t id = (int32_t)(~(uint32_t)key);  // the best incoming arc
+        S.pool_x[j] = id;
+        // the predecessor entry: the source's entry at t-1, which the step
+        // before this one recorded in the state map of that position
+        S.pool_n[j] = t > 1 ? S.vmap[acc_slot(S, b, t - 1, __ldg(S.src_by_id + id))] : -1;
+        S.vmap[slot] = (int32_t)j;
       } else {
         const ulonglong2 a = *(const ulonglong2*)fwd_sum(S, slot);
         const float sh_prev = t > 1 ? decode_max(S.mkey[x.p - 1]) : 0.f;
@@ -755,19 +760,22 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Step
 // start states when it is empty.
 // ======================================================================
 __global__ void __launch_bounds__(FT) k_vit_final(FrontierState S, float* __restrict__ scores,
-                                                  int32_t* __restrict__ qfinal, int32_t* __restrict__ status) {
+                                                  int32_t* __restrict__ jfinal, int32_t* __restrict__ status) {
   __shared__ unsigned long long red[FT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t b = blockIdx.x;
   const int32_t n = S.bw_n[b];
   const int64_t p = S.bw_off[b] + n - 1;
-  const int32_t* cand = n == 0 ? S.start_q : S.pool_q + S.pool_base[p];
+  const int64_t base = n == 0 ? 0 : S.pool_base[p];
+  const int32_t* cand = n == 0 ? S.start_q : S.pool_q + base;
   const int32_t ncand = n == 0 ? S.nstart : S.pool_cnt[p];
+  // best (score, lowest state) key; the low word holds ~state, and for the
+  // pool entry the search below finds the index
   unsigned long long best = 0ull;
   for (int32_t i = threadIdx.x; i < ncand; i += FT) {
     const int32_t q = cand[i];
     if (q < 0) continue;
-    const float a = n == 0 ? __ldg(S.theta_s + q) : S.pool_v[S.pool_base[p] + i];
+    const float a = n == 0 ? __ldg(S.theta_s + q) : S.pool_v[base + i];
     const float c = __fadd_rn(a, __ldg(S.theta_f + q));
     if (c != neg_inf()) {
       const unsigned long long key = ((unsigned long long)fkey(c) << 32) | (unsigned long long)(~(uint32_t)q);
@@ -781,59 +789,42 @@ __global__ void __launch_bounds__(FT) k_vit_final(FrontierState S, float* __rest
   }
   if (lane == 0) red[warp] = best;
   __syncthreads();
+  best = red[0];
+  for (int w = 1; w < FT / 32; ++w) best = red[w] > best ? red[w] : best;
+  const bool oom = (S.flags[1] & 1u) != 0u;
+  const int32_t qbest = best ? (int32_t)(~(uint32_t)best) : -1;
   if (threadIdx.x == 0) {
-    for (int w = 1; w < FT / 32; ++w) best = red[w] > best ? red[w] : best;
-    const bool oom = (S.flags[1] & 1u) != 0u;
     scores[b] = (best && !oom) ? fkey_inv((uint32_t)(best >> 32)) : neg_inf();
-    qfinal[b] = (best && !oom) ? (int32_t)(~(uint32_t)best) : -1;
     if (status) status[b] = oom ? FST_ERR_OOM : (best ? FST_OK : FST_ERR_NO_PATH);
+    if (!best || oom || n == 0) jfinal[b] = -1;
   }
+  // the entry holding the best state (each state appears once per token)
+  if (best && !oom && n > 0)
+    for (int32_t i = threadIdx.x; i < ncand; i += FT)
+      if (cand[i] == qbest) jfinal[b] = (int32_t)(base + i);
 }
 
-// One warp per string: at each position the warp finds the state among the
-// token's pool entries and follows its backpointer.
-__global__ void k_backtrace(FrontierState S, const int32_t* __restrict__ src_by_id,
-                            const int32_t* __restrict__ olabel_by_id, int32_t Bw,
-                            const int32_t* __restrict__ qfinal, int32_t* __restrict__ paths,
+// One thread per string, from the last position back: each pool entry
+// names its best incoming arc and the entry of that arc's source, so the
+// path is a chain of loads with no search.
+__global__ void k_backtrace(FrontierState S, const int32_t* __restrict__ olabel_by_id, int32_t Bw,
+                            const int32_t* __restrict__ jfinal, int32_t* __restrict__ paths,
                             int32_t* __restrict__ olabels) {
-  const int lane = threadIdx.x & 31;
-  const int64_t b = warp_id_global();
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= Bw) return;
   const int32_t n = S.bw_n[b];
   const int64_t off = S.bw_off[b];
-  int32_t q = qfinal[b];
-  if (q < 0) {
-    for (int32_t t = lane; t < n; t += 32) {
-      paths[off + t] = -1;
-      if (olabels) olabels[off + t] = -1;
-    }
-    return;
+  int32_t j = jfinal[b];
+  int32_t t = n;
+  for (; t >= 1 && j >= 0; --t) {
+    const int32_t id = S.pool_x[j];
+    paths[off + t - 1] = id;
+    if (olabels) olabels[off + t - 1] = olabel_by_id[id];
+    j = S.pool_n[j];
   }
-  for (int32_t t = n; t >= 1; --t) {
-    const int64_t p = off + t - 1;
-    const int64_t pb = S.pool_base[p];
-    const int32_t pc = S.pool_cnt[p];
-    int32_t id = -1;
-    for (int32_t c = 0; c < pc; c += 32) {
-      const int32_t i = c + lane;
-      const uint32_t hit = __ballot_sync(FULL, i < pc && S.pool_q[pb + i] == q);
-      if (hit) {
-        id = S.pool_x[pb + c + __ffs(hit) - 1];  // the best incoming arc
-        break;
-      }
-    }
-    if (id < 0) {  // cannot happen for a state on the best path; leave a marker
-      for (int32_t u = lane; u < t; u += 32) {
-        paths[off + u] = -1;
-        if (olabels) olabels[off + u] = -1;
-      }
-      break;
-    }
-    if (lane == 0) {
-      paths[p] = id;
-      if (olabels) olabels[p] = olabel_by_id[id];
-    }
-    q = __ldg(src_by_id + id);
+  for (; t >= 1; --t) {  // no path (or an entry chain cut short): markers
+    paths[off + t - 1] = -1;
+    if (olabels) olabels[off + t - 1] = -1;
   }
 }
 
@@ -995,17 +986,17 @@ int launch_bwd_step(const LayoutView& L, const TokenView& T, const StepView& V, 
   return check_launch("k_bwd_step");
 }
 
-int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t* qfinal, int32_t* status,
+int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t* jfinal, int32_t* status,
                      cudaStream_t s) {
   if (Bw <= 0) return FST_OK;
-  k_vit_final<<<(unsigned)Bw, FT, 0, s>>>(S, scores, qfinal, status);
+  k_vit_final<<<(unsigned)Bw, FT, 0, s>>>(S, scores, jfinal, status);
   return check_launch("k_vit_final");
 }
 
-int launch_backtrace(const FrontierState& S, const int32_t* src_by_id, const int32_t* olabel_by_id, int32_t Bw,
-                     const int32_t* qfinal, int32_t* paths, int32_t* olabels, cudaStream_t s) {
+int launch_backtrace(const FrontierState& S, const int32_t* olabel_by_id, int32_t Bw, const int32_t* jfinal,
+                     int32_t* paths, int32_t* olabels, cudaStream_t s) {
   if (Bw <= 0) return FST_OK;
-  k_backtrace<<<(unsigned)((Bw + 7) / 8), 256, 0, s>>>(S, src_by_id, olabel_by_id, Bw, qfinal, paths, olabels);
+  k_backtrace<<<(unsigned)((Bw + 127) / 128), 128, 0, s>>>(S, olabel_by_id, Bw, jfinal, paths, olabels);
   return check_launch("k_backtrace");
 }
 

@@ -62,12 +62,15 @@ struct FrontierState {
   unsigned long long* acc;
   int32_t acc_stride;
   float* beta;                       // [Bw][2][Q] backward values (null for Viterbi-only state)
+  int32_t* vmap;                     // [Bw][2][Q] Viterbi: pool entry of each live state (null for forward-only state)
+  const int32_t* src_by_id;          // [A] source state of each arc
   int32_t* stage;                    // staged destinations of positions of even parity
   int32_t* stage_b;                  // of odd parity
   uint32_t* scnt;                    // [N] destinations staged per token
   int32_t* pool_q;                   // [cap] state
   int32_t* pool_x;                   // [cap] Viterbi: best incoming arc id; forward: first arc on the next symbol
-  int32_t* pool_n;                   // [cap] forward: arcs on the next symbol (null for Viterbi-only state)
+  int32_t* pool_n;                   // [cap] Viterbi: pool entry of the best arc's source (-1 at the first
+                                     // position); forward: arcs on the next symbol
   float* pool_v;                     // [cap] Viterbi score, or forward value r_t
   int64_t* pool_base;                // [N] by token
   int32_t* pool_cnt;                 // [N] by token
@@ -122,10 +125,12 @@ int launch_fwd_sum(const LayoutView& L, const TokenView& T, const StepView& V, c
 // those arcs.
 int launch_bwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                     const CountView& C, cudaStream_t s);
-int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t* qfinal, int32_t* status,
+// Best final state of each string; jfinal gets its pool entry (-1: no path).
+int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t* jfinal, int32_t* status,
                      cudaStream_t s);
-int launch_backtrace(const FrontierState& S, const int32_t* src_by_id, const int32_t* olabel_by_id, int32_t Bw,
-                     const int32_t* qfinal, int32_t* paths, int32_t* olabels, cudaStream_t s);
+// The best path of each string, following the pool entries' predecessors.
+int launch_backtrace(const FrontierState& S, const int32_t* olabel_by_id, int32_t Bw, const int32_t* jfinal,
+                     int32_t* paths, int32_t* olabels, cudaStream_t s);
 int launch_fb_final(const FrontierState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s);
 int launch_counts_out(int64_t A, const CountView& C, float* out, cudaStream_t s);
 // Zero n 64-bit words of accumulators if error bit 1 is set in *flag: a

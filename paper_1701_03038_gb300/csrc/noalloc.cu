@@ -99,8 +99,8 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   }
   const int64_t Q = f->Q, nn = std::max(n, 1);
   auto rnd = [](int64_t bytes) { return ((bytes > 0 ? bytes : 1) + 255) & ~(int64_t)255; };
-  const int64_t need = rnd(2 * Q * 8) + 5 * rnd(nn * 4) + 3 * rnd(nn * 8) + 2 * rnd(dmax * 4) +
-                       3 * rnd(pool * 4) + rnd(2 * (nn + 2) * 8) + 6 * rnd(8);
+  const int64_t need = rnd(2 * Q * 8) + rnd(2 * Q * 4) + 5 * rnd(nn * 4) + 3 * rnd(nn * 8) + 2 * rnd(dmax * 4) +
+                       4 * rnd(pool * 4) + rnd(2 * (nn + 2) * 8) + 6 * rnd(8);
   if (need > (int64_t)NOALLOC_SCRATCH_BYTES) {
     set_error("fst_viterbi_noalloc: this string needs %lld bytes of working memory, beyond the fixed %llu bytes "
               "(shorter strings or fewer states fit; fst_viterbi has no such limit)",
@@ -112,6 +112,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   if (rc) return rc;
   Carver c{(unsigned char*)base};
   unsigned long long* acc = c.take<unsigned long long>(2 * Q);
+  int32_t* vmap = c.take<int32_t>(2 * Q);
   int32_t* tok_sym = c.take<int32_t>(nn);
   int32_t* tok_b = c.take<int32_t>(nn);
   int32_t* iota = c.take<int32_t>(nn);
@@ -126,9 +127,10 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   int32_t* pool_q = c.take<int32_t>(pool);
   int32_t* pool_x = c.take<int32_t>(pool);
   float* pool_v = c.take<float>(pool);
+  int32_t* pool_n = c.take<int32_t>(pool);
   int64_t* pool_top = c.take<int64_t>(1);
   uint32_t* flags = c.take<uint32_t>(2);
-  int32_t* qfinal = c.take<int32_t>(1);
+  int32_t* jfinal = c.take<int32_t>(1);
   int32_t* bw_n = c.take<int32_t>(1);
   int64_t* bw_off = c.take<int64_t>(1);
   int32_t* status = c.take<int32_t>(1);
@@ -153,6 +155,9 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.Q = f->Q;
   S.acc = acc;
   S.acc_stride = 1;
+  S.vmap = vmap;
+  S.src_by_id = f->src_by_id;
+  S.pool_n = pool_n;
   S.stage = stage;
   S.stage_b = stage_b;
   S.scnt = scnt;
@@ -189,7 +194,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   if (n >= 1 && (rc = launch_vit_first(L, T, step(1, 0), S, s))) return rc;
   for (int32_t t = 1; t <= n; ++t)
     if ((rc = launch_vit_step(L, T, step(t, t + 1), S, s))) return rc;
-  if ((rc = launch_vit_final(S, 1, d_score, qfinal, status, s))) return rc;
-  if ((rc = launch_backtrace(S, f->src_by_id, f->olabel, 1, qfinal, d_path, d_olabels, s))) return rc;
+  if ((rc = launch_vit_final(S, 1, d_score, jfinal, status, s))) return rc;
+  if ((rc = launch_backtrace(S, f->olabel, 1, jfinal, d_path, d_olabels, s))) return rc;
   return FST_OK;
 }

@@ -64,6 +64,7 @@ struct fst_plan_s {
   unsigned long long* acc = nullptr;  // [max_bw][2][Q] x acc_stride words
   int32_t acc_stride = 1;
   float* beta = nullptr;
+  int32_t* vmap = nullptr;
   int32_t *stage = nullptr, *stage_b = nullptr;
   uint32_t* scnt = nullptr;
   int32_t *pool_q = nullptr, *pool_x = nullptr, *pool_n = nullptr;
@@ -76,7 +77,7 @@ struct fst_plan_s {
   uint32_t* flags_d = nullptr;
   uint32_t *mkey = nullptr, *ekey = nullptr;
   double *csum = nullptr, *esum = nullptr;
-  int32_t* qfinal = nullptr;
+  int32_t* jfinal = nullptr;
   double* cnt64 = nullptr;
   double* logz = nullptr;
   int64_t max_bw = 0, max_ntok = 0, max_stage = 0;
@@ -89,10 +90,10 @@ struct fst_plan_s {
   ~fst_plan_s() {
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (Wave& w : waves) w.release();
-    dfree(acc); dfree(beta); dfree(stage); dfree(stage_b); dfree(scnt); dfree(pool_q);
+    dfree(acc); dfree(beta); dfree(vmap); dfree(stage); dfree(stage_b); dfree(scnt); dfree(pool_q);
     dfree(pool_x); dfree(pool_n); dfree(pool_v); dfree(pool_base); dfree(pool_cnt); dfree(pool_top); dfree(flags_d);
     dfree(slot_base); dfree(step_rng);
-    dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(qfinal); dfree(cnt64); dfree(logz);
+    dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(jfinal); dfree(cnt64); dfree(logz);
   }
 };
 
@@ -204,6 +205,8 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.acc = P->acc;
   S.acc_stride = P->acc_stride;
   S.beta = P->beta;
+  S.vmap = P->vmap;
+  S.src_by_id = f->src_by_id;
   S.stage = P->stage;
   S.stage_b = P->stage_b;
   S.scnt = P->scnt;
@@ -282,8 +285,8 @@ int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_p
   for (int32_t t = 1; t <= W.tmax; ++t)
     PROF(FST_PROF_VIT_STEP, launch_vit_step(L, T, wave_step(P, W, t, t + 1), S, s));
   PROF(FST_PROF_VIT_FINAL,
-       launch_vit_final(S, W.Bw, d_scores + W.b0, P->qfinal, d_status ? d_status + W.b0 : nullptr, s));
-  PROF(FST_PROF_BACKTRACE, launch_backtrace(S, f->src_by_id, f->olabel, W.Bw, P->qfinal, d_paths + W.tok0,
+       launch_vit_final(S, W.Bw, d_scores + W.b0, P->jfinal, d_status ? d_status + W.b0 : nullptr, s));
+  PROF(FST_PROF_BACKTRACE, launch_backtrace(S, f->olabel, W.Bw, P->jfinal, d_paths + W.tok0,
                                             d_olabels ? d_olabels + W.tok0 : nullptr, s));
   return FST_OK;
 }
@@ -365,8 +368,9 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
     // waves: consecutive strings whose memory fits the budget
     const int64_t budget = mem_budget_bytes > 0 ? mem_budget_bytes : ((int64_t)16 << 30);
     // accumulators: 2 x 8 bytes per state (Viterbi), or 2 x 16 for the
-    // forward sums and maxima plus 2 x 4 for the backward values
-    const int64_t per_string = (int64_t)f->Q * (P->want_fb ? 40 : 16) + 64;
+    // forward sums and maxima plus 2 x 4 for the backward values; Viterbi
+    // also maps states to pool entries, 2 x 4 bytes
+    const int64_t per_string = (int64_t)f->Q * ((P->want_fb ? 40 : 16) + (P->want_vit ? 8 : 0)) + 64;
     const int64_t per_token = TOKEN_BYTES + POOL_PER_TOKEN * 12;
     int32_t b0 = 0;
     int64_t acc = 0;
@@ -397,16 +401,19 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
       P->max_len = std::max(P->max_len, w.tmax);
       // live pool: its exact bound when that is small, else the largest of
       // POOL_PER_TOKEN entries per token, a quarter of the budget and 256 MiB
-      const int64_t ebytes = P->want_fb ? 16 : 12;
+      const int64_t ebytes = 16;
       const int64_t want = std::max(w.ntok * POOL_PER_TOKEN, std::max(budget / 4, (int64_t)256 << 20) / ebytes);
-      P->pool_cap = std::max(P->pool_cap, std::min(w.pool_bound, want));
+      // pool entries are named by int32 indices
+      P->pool_cap = std::max(P->pool_cap, std::min(std::min(w.pool_bound, want), (int64_t)INT32_MAX));
     }
     if (rc) break;
     const int64_t na = P->max_bw * 2 * (int64_t)f->Q;
     const int64_t nt = P->max_ntok;
     P->acc_stride = P->want_fb ? 2 : 1;
     if ((rc = alloc_track(P, &P->acc, na * P->acc_stride))) break;
-    if (P->want_fb && ((rc = alloc_track(P, &P->beta, na)) || (rc = alloc_track(P, &P->pool_n, P->pool_cap)))) break;
+    if (P->want_fb && (rc = alloc_track(P, &P->beta, na))) break;
+    if (P->want_vit && (rc = alloc_track(P, &P->vmap, na))) break;
+    if ((rc = alloc_track(P, &P->pool_n, P->pool_cap))) break;
     if ((rc = alloc_track(P, &P->stage, P->max_stage)) || (rc = alloc_track(P, &P->stage_b, P->max_stage)) ||
         (rc = alloc_track(P, &P->scnt, nt)) || (rc = alloc_track(P, &P->pool_q, P->pool_cap)) ||
         (rc = alloc_track(P, &P->pool_x, P->pool_cap)) || (rc = alloc_track(P, &P->pool_v, P->pool_cap)) ||
@@ -415,7 +422,7 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
         (rc = alloc_track(P, &P->step_rng, 2 * ((int64_t)P->max_len + 2))) ||
         (rc = alloc_track(P, &P->flags_d, 2)) || (rc = alloc_track(P, &P->mkey, nt)) ||
         (rc = alloc_track(P, &P->ekey, nt)) || (rc = alloc_track(P, &P->csum, nt)) ||
-        (rc = alloc_track(P, &P->esum, nt)) || (rc = alloc_track(P, &P->qfinal, P->max_bw)) ||
+        (rc = alloc_track(P, &P->esum, nt)) || (rc = alloc_track(P, &P->jfinal, P->max_bw)) ||
         (rc = alloc_track(P, &P->logz, B)))
       break;
     if (P->want_fb && (rc = alloc_track(P, &P->cnt64, f->A))) break;
