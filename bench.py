@@ -409,7 +409,7 @@ def main():
         out["e2e"] = {"value": relax_step * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * dt,
                       "api": "Fst.viterbi_batch and Fst.forward_backward_batch from two host threads on two "
-                             "streams (plans built per call)"}
+                             "streams (plans built per call; device storage kept from the previous call of the same kind)"}
 
     # CPU oracle on the host cores, bounded sample (rank 0, N = 1 only)
     if not args.no_cpu and rank == 0 and world == 1:

@@ -328,6 +328,7 @@ extern "C" int fst_create(int32_t num_states, int64_t num_arcs, const int32_t* s
   }
   const bool dev = (flags & FST_FLAG_DEVICE_PTRS) != 0;
   fst_s* f = new fst_s();
+  f->batch_mu = new std::mutex();
   f->Q = num_states;
   f->A = num_arcs;
   f->m = num_isyms;
@@ -403,6 +404,12 @@ extern "C" int fst_create(int32_t num_states, int64_t num_arcs, const int32_t* s
 extern "C" int fst_destroy(fst_t* f) {
   if (!f) return FST_OK;
   DevGuard g(f->device);
+  for (int k = 0; k < 2; ++k) {
+    fst_plan_destroy(f->batch_plan[k]);
+    f->batch_plan[k] = nullptr;
+  }
+  delete f->batch_mu;
+  f->batch_mu = nullptr;
   delete f->plain;
   f->plain = nullptr;
   free_layout(f->fwd);

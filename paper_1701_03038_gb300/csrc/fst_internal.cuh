@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 
 #include "fstgpu.h"
@@ -89,6 +90,10 @@ struct fst_s {
   int32_t max_seg_len = 0;
   // per-handle state for the single-string calls
   struct PlainWs* plain = nullptr;
+  // the last plan of each batch call kind (Viterbi, forward-backward), whose
+  // storage the next call of that kind takes over
+  struct fst_plan_s* batch_plan[2] = {nullptr, nullptr};
+  std::mutex* batch_mu = nullptr;
 };
 
 namespace fstgpu {

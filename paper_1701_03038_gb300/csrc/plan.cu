@@ -13,6 +13,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "fst_internal.cuh"
@@ -54,6 +56,12 @@ struct Wave {
 
 }  // namespace
 
+// The device storage of a plan (everything but the per-wave token tables).
+#define PLAN_STORAGE(X)                                                                                          \
+  X(acc) X(beta) X(vmap) X(stage) X(stage_b) X(scnt) X(pool_q) X(pool_x) X(pool_n) X(pool_v) X(pool_base)          \
+  X(pool_cnt) X(slot_base) X(step_rng) X(pool_top) X(flags_d) X(mkey) X(ekey) X(csum) X(esum) X(jfinal) X(logz) \
+  X(cnt64)
+
 struct fst_plan_s {
   fst_t* fst = nullptr;
   int32_t B = 0, flags = 0, max_len = 0;
@@ -81,6 +89,9 @@ struct fst_plan_s {
   double* cnt64 = nullptr;
   double* logz = nullptr;
   int64_t max_bw = 0, max_ntok = 0, max_stage = 0;
+  // capacities of the device storage below: this plan's needs, or more when
+  // the storage was taken over from an earlier plan of the same handle
+  int64_t cap_bw = 0, cap_nt = 0, cap_stage = 0, cap_len = 0, cap_B = 0, store_bytes = 0;
   bool forward_done = false;
   // optional per-launch CUDA events (fst_plan_profile)
   bool prof_on = false;
@@ -90,10 +101,9 @@ struct fst_plan_s {
   ~fst_plan_s() {
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (Wave& w : waves) w.release();
-    dfree(acc); dfree(beta); dfree(vmap); dfree(stage); dfree(stage_b); dfree(scnt); dfree(pool_q);
-    dfree(pool_x); dfree(pool_n); dfree(pool_v); dfree(pool_base); dfree(pool_cnt); dfree(pool_top); dfree(flags_d);
-    dfree(slot_base); dfree(step_rng);
-    dfree(mkey); dfree(ekey); dfree(csum); dfree(esum); dfree(jfinal); dfree(cnt64); dfree(logz);
+#define PLAN_FREE(x) dfree(x);
+    PLAN_STORAGE(PLAN_FREE)
+#undef PLAN_FREE
   }
 };
 
@@ -129,6 +139,17 @@ template <class T>
 int alloc_track(fst_plan_s* P, T** p, int64_t n) {
   int rc = dalloc(p, n);
   if (!rc) P->bytes += std::max<int64_t>(n, 1) * (int64_t)sizeof(T);
+  return rc;
+}
+
+template <class T>
+int alloc_store(fst_plan_s* P, T** p, int64_t n) {
+  int rc = dalloc(p, n);
+  if (!rc) {
+    const int64_t by = std::max<int64_t>(n, 1) * (int64_t)sizeof(T);
+    P->bytes += by;
+    P->store_bytes += by;
+  }
   return rc;
 }
 
@@ -260,7 +281,7 @@ StepView wave_step(const fst_plan_s* P, const Wave& W, int32_t t, int32_t x_t) {
 // overflowed left staged accumulators behind: they are cleared first.
 int wave_begin(fst_plan_s* P, const Wave& W, cudaStream_t s, bool fb) {
   int rc;
-  const int64_t na = P->max_bw * 2 * (int64_t)P->fst->Q * P->acc_stride;
+  const int64_t na = P->cap_bw * 2 * (int64_t)P->fst->Q * P->acc_stride;
   if ((rc = launch_clear_if_overflow(P->flags_d + 1, P->acc, na, P->fst->num_sms, s))) return rc;
   const size_t n4 = (size_t)std::max<int64_t>(1, W.ntok) * 4;
   FST_CUDA(cudaMemsetAsync(P->scnt, 0, n4, s));
@@ -322,8 +343,12 @@ inline cudaStream_t as_stream(void* p) { return (cudaStream_t)p; }
 
 }  // namespace
 
-extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
-                               int64_t mem_budget_bytes, int32_t flags, void* stream, fst_plan_t** out) {
+// Plan creation.  `donor` (owned: always released here) is an earlier plan
+// of the same handle whose device storage is taken over when it is large
+// enough, so that repeated batch calls neither allocate nor clear it again.
+static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B, int64_t mem_budget_bytes,
+                       int32_t flags, void* stream, fst_plan_s* donor, fst_plan_t** out) {
+  std::unique_ptr<fst_plan_s> donor_owner(donor);
   if (!out) { set_error("out is NULL"); return FST_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!f || B < 0 || !d_offsets) { set_error("fst_plan_create: bad arguments"); return FST_ERR_INVALID_ARG; }
@@ -407,30 +432,56 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
       P->pool_cap = std::max(P->pool_cap, std::min(std::min(w.pool_bound, want), (int64_t)INT32_MAX));
     }
     if (rc) break;
+    P->acc_stride = P->want_fb ? 2 : 1;
+    fst_plan_s* d = donor_owner.get();
+    if (d && d->fst == f && d->want_fb == P->want_fb && d->want_vit == P->want_vit && d->cap_bw >= P->max_bw &&
+        d->cap_nt >= P->max_ntok && d->cap_stage >= P->max_stage && d->pool_cap >= P->pool_cap &&
+        d->cap_len >= P->max_len && d->cap_B >= B) {
+      // take the donor's storage: its accumulators are zero (or, after an
+      // overflow, cleared by the next pass through the moved error flag)
+#define PLAN_MOVE(x) P->x = d->x; d->x = nullptr;
+      PLAN_STORAGE(PLAN_MOVE)
+#undef PLAN_MOVE
+      P->cap_bw = d->cap_bw;
+      P->cap_nt = d->cap_nt;
+      P->cap_stage = d->cap_stage;
+      P->cap_len = d->cap_len;
+      P->cap_B = d->cap_B;
+      P->pool_cap = d->pool_cap;
+      P->store_bytes = d->store_bytes;
+      P->bytes += d->store_bytes;
+      break;
+    }
+    donor_owner.reset();  // too small (or none): release its memory first
+    P->cap_bw = P->max_bw;
+    P->cap_nt = P->max_ntok;
+    P->cap_stage = P->max_stage;
+    P->cap_len = P->max_len;
+    P->cap_B = B;
     const int64_t na = P->max_bw * 2 * (int64_t)f->Q;
     const int64_t nt = P->max_ntok;
-    P->acc_stride = P->want_fb ? 2 : 1;
-    if ((rc = alloc_track(P, &P->acc, na * P->acc_stride))) break;
-    if (P->want_fb && (rc = alloc_track(P, &P->beta, na))) break;
-    if (P->want_vit && (rc = alloc_track(P, &P->vmap, na))) break;
-    if ((rc = alloc_track(P, &P->pool_n, P->pool_cap))) break;
-    if ((rc = alloc_track(P, &P->stage, P->max_stage)) || (rc = alloc_track(P, &P->stage_b, P->max_stage)) ||
-        (rc = alloc_track(P, &P->scnt, nt)) || (rc = alloc_track(P, &P->pool_q, P->pool_cap)) ||
-        (rc = alloc_track(P, &P->pool_x, P->pool_cap)) || (rc = alloc_track(P, &P->pool_v, P->pool_cap)) ||
-        (rc = alloc_track(P, &P->pool_base, nt)) || (rc = alloc_track(P, &P->pool_cnt, nt)) ||
-        (rc = alloc_track(P, &P->pool_top, 1)) || (rc = alloc_track(P, &P->slot_base, nt)) ||
-        (rc = alloc_track(P, &P->step_rng, 2 * ((int64_t)P->max_len + 2))) ||
-        (rc = alloc_track(P, &P->flags_d, 2)) || (rc = alloc_track(P, &P->mkey, nt)) ||
-        (rc = alloc_track(P, &P->ekey, nt)) || (rc = alloc_track(P, &P->csum, nt)) ||
-        (rc = alloc_track(P, &P->esum, nt)) || (rc = alloc_track(P, &P->jfinal, P->max_bw)) ||
-        (rc = alloc_track(P, &P->logz, B)))
+    if ((rc = alloc_store(P, &P->acc, na * P->acc_stride))) break;
+    if (P->want_fb && (rc = alloc_store(P, &P->beta, na))) break;
+    if (P->want_vit && (rc = alloc_store(P, &P->vmap, na))) break;
+    if ((rc = alloc_store(P, &P->pool_n, P->pool_cap))) break;
+    if ((rc = alloc_store(P, &P->stage, P->max_stage)) || (rc = alloc_store(P, &P->stage_b, P->max_stage)) ||
+        (rc = alloc_store(P, &P->scnt, nt)) || (rc = alloc_store(P, &P->pool_q, P->pool_cap)) ||
+        (rc = alloc_store(P, &P->pool_x, P->pool_cap)) || (rc = alloc_store(P, &P->pool_v, P->pool_cap)) ||
+        (rc = alloc_store(P, &P->pool_base, nt)) || (rc = alloc_store(P, &P->pool_cnt, nt)) ||
+        (rc = alloc_store(P, &P->pool_top, 1)) || (rc = alloc_store(P, &P->slot_base, nt)) ||
+        (rc = alloc_store(P, &P->step_rng, 2 * ((int64_t)P->max_len + 2))) ||
+        (rc = alloc_store(P, &P->flags_d, 2)) || (rc = alloc_store(P, &P->mkey, nt)) ||
+        (rc = alloc_store(P, &P->ekey, nt)) || (rc = alloc_store(P, &P->csum, nt)) ||
+        (rc = alloc_store(P, &P->esum, nt)) || (rc = alloc_store(P, &P->jfinal, P->max_bw)) ||
+        (rc = alloc_store(P, &P->logz, B)))
       break;
-    if (P->want_fb && (rc = alloc_track(P, &P->cnt64, f->A))) break;
+    if (P->want_fb && (rc = alloc_store(P, &P->cnt64, f->A))) break;
     // the accumulators start at zero and every run leaves them so
-    FST_CUDA(cudaMemsetAsync(P->acc, 0, (size_t)std::max<int64_t>(na * P->acc_stride, 1) * 8, s));
-    if (P->beta) FST_CUDA(cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 4, s));
-    FST_CUDA(cudaMemsetAsync(P->flags_d, 0, 8, s));
-    FST_CUDA(cudaStreamSynchronize(s));
+    cudaError_t ce = cudaMemsetAsync(P->acc, 0, (size_t)std::max<int64_t>(na * P->acc_stride, 1) * 8, s);
+    if (ce == cudaSuccess && P->beta) ce = cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 4, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(P->flags_d, 0, 8, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "plan storage");
   } while (0);
   dfree(d_ids_copy);
   dfree(d_err);
@@ -440,6 +491,11 @@ extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_
   }
   *out = P;
   return FST_OK;
+}
+
+extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
+                               int64_t mem_budget_bytes, int32_t flags, void* stream, fst_plan_t** out) {
+  return plan_create(f, d_ids, d_offsets, B, mem_budget_bytes, flags, stream, nullptr, out);
 }
 
 extern "C" int fst_plan_destroy(fst_plan_t* P) {
@@ -535,29 +591,50 @@ extern "C" int fst_plan_forward_backward(fst_plan_t* P, const float* d_weights, 
   return FST_OK;
 }
 
+// The batch calls keep the storage of their last plan in the handle (one
+// slot per kind, taken out under a lock while a call runs), so that a
+// stream of batches of similar size allocates and clears it once.
+static fst_plan_s* take_cached(fst_t* f, int kind) {
+  std::lock_guard<std::mutex> lock(*f->batch_mu);
+  fst_plan_s* p = f->batch_plan[kind];
+  f->batch_plan[kind] = nullptr;
+  return p;
+}
+static void put_cached(fst_t* f, int kind, fst_plan_s* p) {
+  fst_plan_s* old = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(*f->batch_mu);
+    old = f->batch_plan[kind];
+    f->batch_plan[kind] = p;
+  }
+  delete old;
+}
+
 extern "C" int fst_viterbi_batch(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                                  float* d_scores, int32_t* d_paths, int32_t* d_olabels, int32_t* d_status,
                                  void* stream) {
+  if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
   fst_plan_t* P = nullptr;
-  int rc = fst_plan_create(f, d_ids, d_offsets, B, 0, FST_PLAN_NO_FB, stream, &P);
+  int rc = plan_create(f, d_ids, d_offsets, B, 0, FST_PLAN_NO_FB, stream, take_cached(f, 0), &P);
   if (rc) return rc;
   rc = fst_plan_viterbi(P, d_scores, d_paths, d_olabels, d_status, stream);
   cudaError_t e = cudaStreamSynchronize(as_stream(stream));
   if (!rc && e != cudaSuccess) rc = cuda_fail(e, "fst_viterbi_batch");
-  fst_plan_destroy(P);
+  if (rc) fst_plan_destroy(P); else put_cached(f, 0, P);
   return rc;
 }
 
 extern "C" int fst_forward_backward_batch(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                                           const float* d_weights, double* d_logz, float* d_counts,
                                           int32_t* d_status, void* stream) {
+  if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
   fst_plan_t* P = nullptr;
-  int rc = fst_plan_create(f, d_ids, d_offsets, B, 0, FST_PLAN_NO_VITERBI, stream, &P);
+  int rc = plan_create(f, d_ids, d_offsets, B, 0, FST_PLAN_NO_VITERBI, stream, take_cached(f, 1), &P);
   if (rc) return rc;
   rc = fst_plan_forward_backward(P, d_weights, d_logz, d_counts, d_status, stream);
   cudaError_t e = cudaStreamSynchronize(as_stream(stream));
   if (!rc && e != cudaSuccess) rc = cuda_fail(e, "fst_forward_backward_batch");
-  fst_plan_destroy(P);
+  if (rc) fst_plan_destroy(P); else put_cached(f, 1, P);
   return rc;
 }
 

@@ -64,6 +64,21 @@ def test_forward_backward_batch(c2s):
     check_batch_fb(o, strs, r["logz"], r["counts"])
 
 
+def test_repeated_batch_calls_reuse_storage(c2s):
+    # each batch call kind keeps its last plan's storage for the next call:
+    # a smaller batch reuses it, a larger one replaces it, and results stay
+    # those of the oracle either way (the accumulators stay zero between runs)
+    f, o, strs = c2s
+    subsets = [(0, 60), (10, 30), (0, 60), (25, 60)]
+    for b0, b1 in subsets:
+        sub = synth.Strings(strs.ids[strs.offsets[b0]:strs.offsets[b1]].copy(),
+                            (strs.offsets[b0:b1 + 1] - strs.offsets[b0]).copy())
+        ids, off = _dev(sub)
+        check_batch_viterbi(o, sub, f.viterbi_batch(ids, off))
+        r = f.forward_backward_batch(ids, off)
+        check_batch_fb(o, sub, r["logz"], r["counts"])
+
+
 def test_waves_match_single_wave(c2s):
     import torch
     f, o, strs = c2s
