@@ -143,10 +143,15 @@ FST_API int fst_forward_backward(fst_t* fst, const int32_t* ids, int32_t n, doub
  *   d_olabels   device int32 [N] or NULL.
  *   d_status    device int32 [B] or NULL: FST_OK or FST_ERR_NO_PATH per string.
  *   stream      cudaStream_t to run on (NULL = legacy default stream).
- * Allocates a plan internally (see fst_plan_create), runs it and frees it;
- * returns after the work is queued and the plan's memory is released, which
- * synchronises the stream.  The return code covers argument and launch
- * errors; per-string outcomes go to d_status. */
+ * Builds a plan internally (see fst_plan_create), runs it and synchronises
+ * the stream before returning.  The handle keeps that plan's device storage
+ * (one slot for Viterbi, one for forward-backward) and the next batch call
+ * of the same kind takes it over when it is large enough, instead of
+ * allocating and clearing its own; fst_destroy frees it.  Calls from
+ * several host threads on one handle are safe (each slot is taken under a
+ * lock; a call that finds it taken allocates its own).  The return code
+ * covers argument and launch errors; per-string outcomes go to d_status
+ * (FST_OK, FST_ERR_NO_PATH, or FST_ERR_OOM when the live pool overflowed). */
 FST_API int fst_viterbi_batch(fst_t* fst, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                       float* d_scores, int32_t* d_paths, int32_t* d_olabels, int32_t* d_status,
                       void* stream);
@@ -160,11 +165,13 @@ FST_API int fst_forward_backward_batch(fst_t* fst, const int32_t* d_ids, const i
                                int32_t B, const float* d_weights, double* d_logz,
                                float* d_counts, int32_t* d_status, void* stream);
 
-/* A plan holds everything a batch needs on the device: the work lists (one
- * entry per (step, symbol group, window)), the per-string frontiers and the
- * per-step storage for backpointers and forward values.  Once created, the
- * run calls below allocate nothing, so a sequence of them can be captured
- * into a CUDA graph and replayed.
+/* A plan holds everything a batch needs on the device: the token lists of
+ * every position (strings sorted by length), the per-string accumulators,
+ * the live pool of every position (states, values, backpointers or arcs)
+ * and the per-token scalars.  Once created, the run calls below allocate
+ * nothing, so a sequence of them can be captured into a CUDA graph and
+ * replayed.  A Viterbi-only plan and a forward-backward-only plan of the
+ * same batch share nothing and may run concurrently on two streams.
  *   d_ids, d_offsets  as fst_viterbi_batch; they are read during
  *               fst_plan_create only (the plan keeps its own copy).
  *   mem_budget_bytes  cap on per-step storage; strings are processed in
@@ -174,7 +181,7 @@ FST_API int fst_forward_backward_batch(fst_t* fst, const int32_t* d_ids, const i
  *               fst_plan_backward, which keep state between calls).
  * Synchronises `stream`. */
 #define FST_PLAN_SINGLE_WAVE 1
-#define FST_PLAN_NO_VITERBI 2   /* do not allocate backpointer storage */
+#define FST_PLAN_NO_VITERBI 2   /* do not allocate Viterbi storage (keys, state maps) */
 #define FST_PLAN_NO_FB 4        /* do not allocate forward-backward storage */
 FST_API int fst_plan_create(fst_t* fst, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                     int64_t mem_budget_bytes, int32_t flags, void* stream, fst_plan_t** out);
