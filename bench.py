@@ -114,6 +114,24 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------- replicas
+def max_over_ranks(x: float, device) -> float:
+    """The job's time: the slowest rank's (every rank runs the same work on
+    its own GPU, so the whole job ends when the slowest replica does)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job rate: the units all ranks processed over the job's time."""
+    return units_per_rank * world / seconds
+
+
 # ---------------------------------------------------------------- models
 PASS_KERNELS = {"vit": ("vit_first", "vit_step"), "fwd": ("fwd_first", "fwd_sum", "fwd_step"),
                 "bwd": ("bwd_step",)}
@@ -288,13 +306,9 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = relax_step * world / (ms / 1000.0)
-    sent_s = strs.count * world / (ms / 1000.0)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev)
+    value = job_throughput(relax_step, world, ms / 1000.0)
+    sent_s = job_throughput(strs.count, world, ms / 1000.0)
 
     # per-kernel device time of one more step, with events around every
     # launch; the passes run one after the other here so that each kernel's
@@ -402,11 +416,11 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             e2e_step()
-        dt = (time.perf_counter() - t0) / args.e2e_steps
+        dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dev)
         barrier()
         h2d = strs.ids.nbytes + strs.offsets.nbytes
         d2h = 4 * strs.count + 4 * len(strs.ids) + 8 * strs.count + 4 * fa.num_arcs
-        out["e2e"] = {"value": relax_step * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        out["e2e"] = {"value": job_throughput(relax_step, world, dt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * dt,
                       "api": "Fst.viterbi_batch and Fst.forward_backward_batch from two host threads on two "
                              "streams (plans built per call; device storage kept from the previous call of the same kind)"}
