@@ -174,11 +174,15 @@ def load_traffic(pass_name: str, workload: str):
     return None
 
 
+# the files that decide what the step kernels read and write
+KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "store.cu")
+
+
 def source_hash():
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1701_03038_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
