@@ -142,6 +142,38 @@ class Fst:
             out["beta"] = be
         return out
 
+    def state_posteriors(self, x):
+        """Expected start and final state of string x, the two ends of
+        Alg. 2: P(the path starts in q | x) = exp(alpha_0[q] + beta_0[q] -
+        log Z) and P(it ends in q | x) = exp(alpha_n[q] + beta_n[q] - log Z),
+        which are also d log Z / d (start log-weight of q) and d log Z /
+        d (final log-weight of q).  All zero when x has no path."""
+        x = np.ascontiguousarray(x, np.int32)
+        n = int(x.shape[0])
+        fb = self.forward_backward(x, tables=True)
+        lz = fb["logz"]
+        if lz == -np.inf:
+            z = np.zeros(self.Q, np.float64)
+            return dict(status=fb["status"], logz=lz, start=z, final=z.copy())
+        al, be = fb["alpha"], fb["beta"]
+        with np.errstate(invalid="ignore"):
+            start = np.exp(al[0] + be[0] - lz)
+            final = np.exp(al[n] + be[n] - lz)
+        return dict(status=fb["status"], logz=lz, start=np.nan_to_num(start), final=np.nan_to_num(final))
+
+    def state_posteriors_batch(self, ids, offsets, weights=None):
+        """Weighted sums over a batch of state_posteriors (weight 1 by
+        default): the gradients of sum_b g_b log Z_b."""
+        off = np.asarray(offsets, np.int64)
+        start = np.zeros(self.Q, np.float64)
+        final = np.zeros(self.Q, np.float64)
+        for b in range(int(off.shape[0] - 1)):
+            r = self.state_posteriors(np.asarray(ids)[off[b]:off[b + 1]])
+            g = 1.0 if weights is None else float(weights[b])
+            start += g * r["start"]
+            final += g * r["final"]
+        return dict(start=start, final=final)
+
     def viterbi_batch(self, ids, offsets, nthreads: int = 1):
         ids = np.ascontiguousarray(ids, np.int32)
         off = np.ascontiguousarray(offsets, np.int64)

@@ -391,5 +391,39 @@ def pin_deterministic(lib, cases=10, seed=13):
         assert np.allclose(fb["counts"], c, atol=1e-12)
 
 
+def pin_state_posteriors(lib, cases=120, seed=17):
+    """Start and final state posteriors against exhaustive path enumeration:
+    P(start in q) and P(end in q) summed over the accepting paths, and the
+    worked example of Figs. 1-2 (one start state, one final state)."""
+    fst, x, _, _, _ = fig1_case()
+    r = oracle.Fst(fst, lib).state_posteriors(x)
+    one0 = np.zeros(fst.num_states)
+    one0[0] = 1.0
+    assert np.allclose(r["start"], one0, atol=1e-12)
+    assert abs(r["final"].sum() - 1.0) < 1e-12 and r["final"].argmax() == 5
+    rng = np.random.default_rng(seed)
+    seen = 0
+    for _ in range(cases):
+        fst = synth.tiny_fst(rng)
+        ts = oracle.theta_of_cost(fst.start_weight)
+        n = int(rng.integers(0, 5))
+        x = rng.integers(0, fst.num_isyms, size=n).astype(np.int32)
+        paths = enumerate_paths(fst, x)
+        r = oracle.Fst(fst, lib).state_posteriors(x)
+        ws, wf = np.zeros(fst.num_states), np.zeros(fst.num_states)
+        if paths:
+            seen += 1
+            logz = _lse([p[2] for p in paths])
+            for seq, _, w64, qn in paths:
+                q0 = qn if not seq else int(fst.src[seq[0]])
+                ws[q0] += math.exp(w64 - logz)
+                wf[qn] += math.exp(w64 - logz)
+            assert abs(ws.sum() - 1.0) < 1e-9 and abs(wf.sum() - 1.0) < 1e-9
+            assert np.all(ws[ts == -np.inf] == 0)
+        assert np.allclose(r["start"], ws, atol=1e-12, rtol=1e-12), (r["start"], ws)
+        assert np.allclose(r["final"], wf, atol=1e-12, rtol=1e-12), (r["final"], wf)
+    assert seen > 20
+
+
 ALL_PINS = [pin_fig1, pin_bruteforce, pin_ties, pin_hmm, pin_single_state,
-            pin_unweighted_count, pin_invariants, pin_deterministic]
+            pin_unweighted_count, pin_invariants, pin_deterministic, pin_state_posteriors]
