@@ -110,6 +110,14 @@ FST_API int fst_symbol_stats(const fst_t* fst, int64_t* arcs, int64_t* dsts, int
  * running. */
 FST_API int fst_set_weights(fst_t* fst, const float* weight, int32_t weight_kind, int32_t flags);
 
+/* Replace the start and final weights of every state ([num_states] each,
+ * per weight_kind; host or device per flags; a NULL array keeps its old
+ * weights).  Same validation and rules as fst_set_weights.  The states with
+ * a finite start weight (the live states before the first position, Sec. 3)
+ * are listed again. */
+FST_API int fst_set_state_weights(fst_t* fst, const float* start_weight, const float* final_weight,
+                                  int32_t weight_kind, int32_t flags);
+
 /* Plain method, one string (the paper's design, Sec. 5: one kernel launch
  * per input position over the arcs of delta[w_t], then the backtrace of
  * Sec. 5.1 on the device).  Host pointers throughout; synchronous.
@@ -212,6 +220,21 @@ FST_API int fst_plan_backward(fst_plan_t* plan, const float* d_weights, float* d
 /* Forward and backward for every wave of the plan (any number of waves). */
 FST_API int fst_plan_forward_backward(fst_plan_t* plan, const float* d_weights, double* d_logz,
                               float* d_counts, int32_t* d_status, void* stream);
+
+/* As fst_plan_backward and fst_plan_forward_backward, with the expected
+ * start and final states as well (the two ends of Alg. 2's recursion):
+ *   d_start  device float [num_states] or NULL: sum_b g_b P_b(path starts in q)
+ *            = sum_b g_b exp(alpha_0[q] + beta_0[q] - log Z_b), the gradient
+ *            of sum_b g_b log Z_b with respect to the start log-weights;
+ *   d_final  device float [num_states] or NULL: likewise with
+ *            exp(alpha_n[q] + beta_n[q] - log Z_b), the final log-weights.
+ * d_counts may be NULL here; at least one output is required by
+ * fst_plan_backward_ex.  Strings without a path add nothing. */
+FST_API int fst_plan_backward_ex(fst_plan_t* plan, const float* d_weights, float* d_counts, float* d_start,
+                                 float* d_final, void* stream);
+FST_API int fst_plan_forward_backward_ex(fst_plan_t* plan, const float* d_weights, double* d_logz,
+                                         float* d_counts, float* d_start, float* d_final, int32_t* d_status,
+                                         void* stream);
 
 /* log Z of one string with every value and weight in float64 (the forward
  * recursion of Alg. 2 in the log domain; plain method, one launch per

@@ -30,6 +30,7 @@ SIGNATURES = {
     "fst_info": [vp, vp, vp, vp, vp, vp, vp, vp],
     "fst_symbol_stats": [vp, vp, vp, vp],
     "fst_set_weights": [vp, vp, i32, i32],
+    "fst_set_state_weights": [vp, vp, vp, i32, i32],
     "fst_viterbi": [vp, vp, i32, vp, vp, vp],
     "fst_forward_backward": [vp, vp, i32, vp, vp],
     "fst_viterbi_batch": [vp, vp, vp, i32, vp, vp, vp, vp, vp],
@@ -41,6 +42,8 @@ SIGNATURES = {
     "fst_plan_forward": [vp, vp, vp, vp],
     "fst_plan_backward": [vp, vp, vp, vp],
     "fst_plan_forward_backward": [vp, vp, vp, vp, vp, vp],
+    "fst_plan_backward_ex": [vp, vp, vp, vp, vp, vp],
+    "fst_plan_forward_backward_ex": [vp, vp, vp, vp, vp, vp, vp, vp],
     "fst_plan_profile": [vp, i32],
     "fst_plan_profile_read": [vp, vp, vp],
     "fst_viterbi_noalloc": [vp, vp, i32, vp, vp, vp, vp],

@@ -479,6 +479,63 @@ extern "C" int fst_set_weights(fst_t* f, const float* weight, int32_t weight_kin
   return rc;
 }
 
+extern "C" int fst_set_state_weights(fst_t* f, const float* start_weight, const float* final_weight,
+                                     int32_t weight_kind, int32_t flags) {
+  if (!f || (weight_kind != FST_WEIGHT_LOG && weight_kind != FST_WEIGHT_COST)) {
+    set_error("fst_set_state_weights: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  DevGuard g(f->device);
+  const int64_t Q = f->Q;
+  const bool dev = (flags & FST_FLAG_DEVICE_PTRS) != 0;
+  float *d_in = nullptr, *d_s = nullptr, *d_f = nullptr;
+  unsigned int* d_err = nullptr;
+  int rc = FST_OK;
+  do {
+    if ((rc = dalloc(&d_err, 1)) || (rc = dalloc(&d_s, Q)) || (rc = dalloc(&d_f, Q))) break;
+    if (cudaMemset(d_err, 0, 4) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset"); break; }
+    const float* src[2] = {start_weight, final_weight};
+    float* out[2] = {d_s, d_f};
+    for (int i = 0; i < 2 && !rc; ++i) {
+      if (!src[i]) continue;
+      const float* in = src[i];
+      if (!dev) {
+        dfree(d_in);
+        if ((rc = to_device(src[i], &d_in, Q))) break;
+        in = d_in;
+      }
+      k_convert_states<<<nblk(Q), TB>>>(in, f->Q, weight_kind, out[i], d_err);
+    }
+    if (rc) break;
+    if ((rc = read_err_flag(d_err, "fst_set_state_weights"))) break;
+    // validated: install the new weights and list the start states again
+    if (start_weight) {
+      std::vector<float> hs(Q);
+      if (cudaMemcpy(hs.data(), d_s, (size_t)Q * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "start weights");
+        break;
+      }
+      std::vector<int32_t> sq;
+      for (int64_t q = 0; q < Q; ++q)
+        if (hs[q] != -INFINITY) sq.push_back((int32_t)q);
+      int32_t* d_sq = nullptr;
+      if ((rc = to_device(sq.data(), &d_sq, (int64_t)sq.size()))) break;
+      dfree(f->start_q);
+      f->start_q = d_sq;
+      f->nstart = (int32_t)sq.size();
+      std::swap(f->theta_s, d_s);
+    }
+    if (final_weight) std::swap(f->theta_f, d_f);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = cuda_fail(e, "fst_set_state_weights");
+  } while (0);
+  dfree(d_in);
+  dfree(d_s);
+  dfree(d_f);
+  dfree(d_err);
+  return rc;
+}
+
 // ============================================================ plain method
 extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
                            int32_t* olabels) {

@@ -748,6 +748,11 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Step
         ek_p = p - 1;
         ek_key = fkey(u);
       }
+    } else if (q >= 0 && C.start64) {
+      // t = 1: the item is a start state q, log beta_0[q] = u + E_1 and its
+      // start posterior is exp(theta_s[q] + log beta_0[q] - log Z)
+      const float u = fix_log_sum(me.m, su);
+      if (u != neg_inf()) atomicAdd(C.start64 + q, exp((double)me.ra + (double)u + me.K) * (double)me.gw);
     }
     warp_max_by_token(S.ekey, ek_p, ek_key);  // the step maximum e_{t-1}
   }
@@ -909,6 +914,44 @@ __global__ void __launch_bounds__(FT) k_fb_final(FrontierState S, double* __rest
   }
 }
 
+// Final-state posteriors: exp(alpha_n[q] + theta_f[q] - log Z) for every
+// live state q of a string's last position, alpha_n = r_n + C_{n-1} (Alg. 2
+// at t = n); an empty string's path starts and ends in the same state.
+__global__ void __launch_bounds__(FT) k_final_post(FrontierState S, CountView C) {
+  const int64_t b = blockIdx.x;
+  const double lz = S.logz[b];
+  if (lz == -INFINITY) return;
+  const int32_t n = S.bw_n[b];
+  const double g = S.gweight ? (double)S.gweight[b] : 1.0;
+  if (n == 0) {
+    for (int32_t i = threadIdx.x; i < S.nstart; i += FT) {
+      const int32_t q = S.start_q[i];
+      const float v = __fadd_rn(__ldg(S.theta_s + q), __ldg(S.theta_f + q));
+      if (v == neg_inf()) continue;
+      const double post = exp((double)v - lz) * g;
+      if (C.final64) atomicAdd(C.final64 + q, post);
+      if (C.start64) atomicAdd(C.start64 + q, post);
+    }
+    return;
+  }
+  if (!C.final64) return;
+  const int64_t p = S.bw_off[b] + n - 1;
+  const double cprev = n >= 2 ? S.csum[p - 1] : 0.0;
+  const int64_t base = S.pool_base[p];
+  const int32_t cnt = S.pool_cnt[p];
+  for (int32_t i = threadIdx.x; i < cnt; i += FT) {
+    const int32_t q = S.pool_q[base + i];
+    const float tf = __ldg(S.theta_f + q);
+    if (tf == neg_inf()) continue;
+    atomicAdd(C.final64 + q, exp(((double)S.pool_v[base + i] + (double)tf) + cprev - lz) * g);
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ in, int64_t n, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
 __global__ void k_counts_out(int64_t A, CountView C, float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A) return;
@@ -1010,6 +1053,18 @@ int launch_counts_out(int64_t A, const CountView& C, float* out, cudaStream_t s)
   if (A <= 0) return FST_OK;
   k_counts_out<<<(unsigned)((A + 255) / 256), 256, 0, s>>>(A, C, out);
   return check_launch("k_counts_out");
+}
+
+int launch_final_posteriors(const FrontierState& S, int32_t Bw, const CountView& C, cudaStream_t s) {
+  if (Bw <= 0 || (!C.final64 && !C.start64)) return FST_OK;
+  k_final_post<<<(unsigned)Bw, FT, 0, s>>>(S, C);
+  return check_launch("k_final_post");
+}
+
+int launch_to_float(const double* in, int64_t n, float* out, cudaStream_t s) {
+  if (n <= 0) return FST_OK;
+  k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, n, out);
+  return check_launch("k_to_float");
 }
 
 int launch_clear_if_overflow(const uint32_t* flag, unsigned long long* acc, int64_t n, int num_sms, cudaStream_t s) {

@@ -99,6 +99,8 @@ struct CountView {
   float* cnt;
   float* comp;
   double* cnt64;
+  double* start64;    // [Q] expected start states, or null
+  double* final64;    // [Q] expected final states, or null
 };
 
 // First position (Viterbi and forward): the start states push their arcs
@@ -133,6 +135,12 @@ int launch_backtrace(const FrontierState& S, const int32_t* olabel_by_id, int32_
                      int32_t* paths, int32_t* olabels, cudaStream_t s);
 int launch_fb_final(const FrontierState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s);
 int launch_counts_out(int64_t A, const CountView& C, float* out, cudaStream_t s);
+// Expected final states of every string (and expected start states of the
+// empty strings, whose paths start where they end), added to C.final64 and
+// C.start64 with the strings' weights.  Needs the forward pass and log Z.
+int launch_final_posteriors(const FrontierState& S, int32_t Bw, const CountView& C, cudaStream_t s);
+// out[i] = (float)in[i], i < n.
+int launch_to_float(const double* in, int64_t n, float* out, cudaStream_t s);
 // Zero n 64-bit words of accumulators if error bit 1 is set in *flag: a
 // run whose pool overflowed leaves staged accumulators behind.
 int launch_clear_if_overflow(const uint32_t* flag, unsigned long long* acc, int64_t n, int num_sms, cudaStream_t s);

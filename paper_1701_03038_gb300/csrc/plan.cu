@@ -60,7 +60,7 @@ struct Wave {
 #define PLAN_STORAGE(X)                                                                                          \
   X(acc) X(beta) X(vmap) X(stage) X(stage_b) X(scnt) X(pool_q) X(pool_x) X(pool_n) X(pool_v) X(pool_base)          \
   X(pool_cnt) X(slot_base) X(step_rng) X(pool_top) X(flags_d) X(mkey) X(ekey) X(csum) X(esum) X(jfinal) X(logz) \
-  X(cnt64)
+  X(cnt64) X(start64) X(final64)
 
 struct fst_plan_s {
   fst_t* fst = nullptr;
@@ -87,6 +87,7 @@ struct fst_plan_s {
   double *csum = nullptr, *esum = nullptr;
   int32_t* jfinal = nullptr;
   double* cnt64 = nullptr;
+  double *start64 = nullptr, *final64 = nullptr;  // [Q] expected start and final states
   double* logz = nullptr;
   int64_t max_bw = 0, max_ntok = 0, max_stage = 0;
   // capacities of the device storage below: this plan's needs, or more when
@@ -328,14 +329,42 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   return FST_OK;
 }
 
-int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, cudaStream_t s) {
+// The backward pass of a wave; with `states`, also the expected start and
+// final states.
+int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, bool states, cudaStream_t s) {
   fst_s* f = P->fst;
   const LayoutView L = view_of(f->bwd);
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, d_weights);
-  const CountView C{1, nullptr, nullptr, P->cnt64};
+  const CountView C{1, nullptr, nullptr, P->cnt64, states ? P->start64 : nullptr, states ? P->final64 : nullptr};
   for (int32_t t = W.tmax; t >= 1; --t)
     PROF(FST_PROF_BWD_STEP, launch_bwd_step(L, T, wave_step(P, W, t, t - 1), S, C, s));
+  if (states) PROF(FST_PROF_COUNTS, launch_final_posteriors(S, W.Bw, C, s));
+  return FST_OK;
+}
+
+// Zero the count accumulators of a backward run.
+int counts_begin(fst_plan_s* P, bool states, cudaStream_t s) {
+  fst_s* f = P->fst;
+  FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->A) * 8, s));
+  if (states) {
+    FST_CUDA(cudaMemsetAsync(P->start64, 0, (size_t)f->Q * 8, s));
+    FST_CUDA(cudaMemsetAsync(P->final64, 0, (size_t)f->Q * 8, s));
+  }
+  return FST_OK;
+}
+
+// Counts (and state posteriors) from their float64 accumulators to the
+// caller's float arrays.
+int counts_end(fst_plan_s* P, float* d_counts, float* d_start, float* d_final, cudaStream_t s) {
+  fst_s* f = P->fst;
+  int rc;
+  if (d_counts) {
+    const CountView C{1, nullptr, nullptr, P->cnt64};
+    PROF(FST_PROF_COUNTS, launch_counts_out(f->A, C, d_counts, s));
+  }
+  if (d_start && (rc = launch_to_float(P->start64, f->Q, d_start, s))) return rc;
+  if (d_final && (rc = launch_to_float(P->final64, f->Q, d_final, s))) return rc;
   return FST_OK;
 }
 
@@ -475,7 +504,9 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
         (rc = alloc_store(P, &P->esum, nt)) || (rc = alloc_store(P, &P->jfinal, P->max_bw)) ||
         (rc = alloc_store(P, &P->logz, B)))
       break;
-    if (P->want_fb && (rc = alloc_store(P, &P->cnt64, f->A))) break;
+    if (P->want_fb && ((rc = alloc_store(P, &P->cnt64, f->A)) || (rc = alloc_store(P, &P->start64, f->Q)) ||
+                       (rc = alloc_store(P, &P->final64, f->Q))))
+      break;
     // the accumulators start at zero and every run leaves them so
     cudaError_t ce = cudaMemsetAsync(P->acc, 0, (size_t)std::max<int64_t>(na * P->acc_stride, 1) * 8, s);
     if (ce == cudaSuccess && P->beta) ce = cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 4, s);
@@ -556,39 +587,50 @@ extern "C" int fst_plan_forward(fst_plan_t* P, double* d_logz, int32_t* d_status
   return FST_OK;
 }
 
-extern "C" int fst_plan_backward(fst_plan_t* P, const float* d_weights, float* d_counts, void* stream) {
-  if (!P || !d_counts) { set_error("fst_plan_backward: bad arguments"); return FST_ERR_INVALID_ARG; }
+extern "C" int fst_plan_backward_ex(fst_plan_t* P, const float* d_weights, float* d_counts, float* d_start,
+                                    float* d_final, void* stream) {
+  if (!P || (!d_counts && !d_start && !d_final)) {
+    set_error("fst_plan_backward: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
   if (!P->forward_done) { set_error("fst_plan_backward needs a preceding fst_plan_forward"); return FST_ERR_STATE; }
-  fst_s* f = P->fst;
   cudaStream_t s = as_stream(stream);
+  const bool states = d_start || d_final;
   int rc;
-  FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->A) * 8, s));
+  if ((rc = counts_begin(P, states, s))) return rc;
   for (const Wave& W : P->waves)
-    if ((rc = run_backward_wave(P, W, d_weights, s))) return rc;
-  const CountView C{1, nullptr, nullptr, P->cnt64};
-  PROF(FST_PROF_COUNTS, launch_counts_out(f->A, C, d_counts, s));
+    if ((rc = run_backward_wave(P, W, d_weights, states, s))) return rc;
+  return counts_end(P, d_counts, d_start, d_final, s);
+}
+
+extern "C" int fst_plan_backward(fst_plan_t* P, const float* d_weights, float* d_counts, void* stream) {
+  if (!d_counts) { set_error("fst_plan_backward: bad arguments"); return FST_ERR_INVALID_ARG; }
+  return fst_plan_backward_ex(P, d_weights, d_counts, nullptr, nullptr, stream);
+}
+
+extern "C" int fst_plan_forward_backward_ex(fst_plan_t* P, const float* d_weights, double* d_logz,
+                                            float* d_counts, float* d_start, float* d_final, int32_t* d_status,
+                                            void* stream) {
+  if (!P || !d_logz) { set_error("fst_plan_forward_backward: bad arguments"); return FST_ERR_INVALID_ARG; }
+  if (!P->want_fb) { set_error("plan was created without forward-backward storage"); return FST_ERR_STATE; }
+  cudaStream_t s = as_stream(stream);
+  const bool states = d_start || d_final;
+  const bool bwd = d_counts || states;
+  int rc;
+  if (bwd && (rc = counts_begin(P, states, s))) return rc;
+  for (const Wave& W : P->waves) {
+    if ((rc = run_forward_wave(P, W, s, d_status))) return rc;
+    if (bwd && (rc = run_backward_wave(P, W, d_weights, states, s))) return rc;
+  }
+  if (P->B > 0) FST_CUDA(cudaMemcpyAsync(d_logz, P->logz, (size_t)P->B * 8, cudaMemcpyDeviceToDevice, s));
+  if (bwd && (rc = counts_end(P, d_counts, d_start, d_final, s))) return rc;
+  P->forward_done = P->waves.size() <= 1;
   return FST_OK;
 }
 
 extern "C" int fst_plan_forward_backward(fst_plan_t* P, const float* d_weights, double* d_logz, float* d_counts,
                                          int32_t* d_status, void* stream) {
-  if (!P || !d_logz) { set_error("fst_plan_forward_backward: bad arguments"); return FST_ERR_INVALID_ARG; }
-  if (!P->want_fb) { set_error("plan was created without forward-backward storage"); return FST_ERR_STATE; }
-  fst_s* f = P->fst;
-  cudaStream_t s = as_stream(stream);
-  int rc;
-  if (d_counts) FST_CUDA(cudaMemsetAsync(P->cnt64, 0, (size_t)std::max<int64_t>(1, f->A) * 8, s));
-  for (const Wave& W : P->waves) {
-    if ((rc = run_forward_wave(P, W, s, d_status))) return rc;
-    if (d_counts && (rc = run_backward_wave(P, W, d_weights, s))) return rc;
-  }
-  if (P->B > 0) FST_CUDA(cudaMemcpyAsync(d_logz, P->logz, (size_t)P->B * 8, cudaMemcpyDeviceToDevice, s));
-  if (d_counts) {
-    const CountView C{1, nullptr, nullptr, P->cnt64};
-    PROF(FST_PROF_COUNTS, launch_counts_out(f->A, C, d_counts, s));
-  }
-  P->forward_done = P->waves.size() <= 1;
-  return FST_OK;
+  return fst_plan_forward_backward_ex(P, d_weights, d_logz, d_counts, nullptr, nullptr, d_status, stream);
 }
 
 // The batch calls keep the storage of their last plan in the handle (one

@@ -136,6 +136,23 @@ class Fst:
             with torch.cuda.device(self.device):
                 check(self._lib.fst_set_weights(self._h, _hptr(w), kind, 0), "fst_set_weights")
 
+    def set_state_weights(self, start=None, final=None, weight_kind: str = "cost"):
+        """Replace the start and/or final weight of every state ([num_states]
+        each; None keeps the old ones)."""
+        kind = {"cost": _lib.WEIGHT_COST, "log": _lib.WEIGHT_LOG}[weight_kind]
+        if any(isinstance(v, torch.Tensor) for v in (start, final)):
+            vs = [None if v is None else torch.as_tensor(v).detach().to(device=self.device, dtype=torch.float32)
+                  .contiguous() for v in (start, final)]
+            with torch.cuda.device(self.device):
+                torch.cuda.current_stream().synchronize()
+                check(self._lib.fst_set_state_weights(self._h, _dptr(vs[0]), _dptr(vs[1]), kind,
+                                                      _lib.FLAG_DEVICE_PTRS), "fst_set_state_weights")
+        else:
+            vs = [None if v is None else _host(v, np.float32) for v in (start, final)]
+            with torch.cuda.device(self.device):
+                check(self._lib.fst_set_state_weights(self._h, *[None if v is None else _hptr(v) for v in vs], kind, 0),
+                      "fst_set_state_weights")
+
     # ------------------------------------------------- plain method (one string)
     def viterbi(self, ids):
         """Best path of one string: (score float32, arc ids int32[n], output
@@ -236,6 +253,9 @@ class Plan:
         self.status = torch.empty(max(self.B, 1), dtype=torch.int32, device=dev)
         self.logz = torch.empty(max(self.B, 1), dtype=torch.float64, device=dev)
         self.counts = torch.empty(max(fst.num_arcs, 1), dtype=torch.float32, device=dev)
+        # expected start and final states (forward_backward / backward with states=True)
+        self.start_counts = torch.empty(max(fst.num_states, 1), dtype=torch.float32, device=dev)
+        self.final_counts = torch.empty(max(fst.num_states, 1), dtype=torch.float32, device=dev)
 
     def close(self):
         if self._h is not None and self._h.value:
@@ -277,15 +297,30 @@ class Plan:
         check(self._lib.fst_plan_forward(self._h, _dptr(self.logz), _dptr(self.status), _stream(stream)),
               "fst_plan_forward")
 
-    def backward(self, weights: torch.Tensor | None = None, stream=None):
+    def backward(self, weights: torch.Tensor | None = None, stream=None, states: bool = False):
+        """Backward pass after forward(): arc counts into self.counts and,
+        with states=True, expected start and final states into
+        self.start_counts / self.final_counts."""
         if weights is not None:
             _require_cuda(weights, torch.float32, "weights")
-        check(self._lib.fst_plan_backward(self._h, _dptr(weights), _dptr(self.counts), _stream(stream)),
-              "fst_plan_backward")
+        if states:
+            check(self._lib.fst_plan_backward_ex(self._h, _dptr(weights), _dptr(self.counts),
+                                                 _dptr(self.start_counts), _dptr(self.final_counts),
+                                                 _stream(stream)), "fst_plan_backward_ex")
+        else:
+            check(self._lib.fst_plan_backward(self._h, _dptr(weights), _dptr(self.counts), _stream(stream)),
+                  "fst_plan_backward")
 
-    def forward_backward(self, weights: torch.Tensor | None = None, counts: bool = True, stream=None):
+    def forward_backward(self, weights: torch.Tensor | None = None, counts: bool = True, stream=None,
+                         states: bool = False):
         if weights is not None:
             _require_cuda(weights, torch.float32, "weights")
-        check(self._lib.fst_plan_forward_backward(self._h, _dptr(weights), _dptr(self.logz),
-                                                  _dptr(self.counts) if counts else None, _dptr(self.status),
-                                                  _stream(stream)), "fst_plan_forward_backward")
+        if states:
+            check(self._lib.fst_plan_forward_backward_ex(
+                self._h, _dptr(weights), _dptr(self.logz), _dptr(self.counts) if counts else None,
+                _dptr(self.start_counts), _dptr(self.final_counts), _dptr(self.status), _stream(stream)),
+                "fst_plan_forward_backward_ex")
+        else:
+            check(self._lib.fst_plan_forward_backward(self._h, _dptr(weights), _dptr(self.logz),
+                                                      _dptr(self.counts) if counts else None, _dptr(self.status),
+                                                      _stream(stream)), "fst_plan_forward_backward")

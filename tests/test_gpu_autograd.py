@@ -120,3 +120,73 @@ def test_weighted_gradient_and_training_loop():
         assert_counts_close(-model.theta.grad.double().cpu().numpy(), ob["counts"], batch=True)
         assert np.allclose(lz.detach().cpu().numpy(), ob["logz"], rtol=1e-5, atol=0)
         opt.step()
+
+
+def _multi_start_fst(seed=43):
+    # several start states and final states with unequal weights, so that
+    # the start and final posteriors are spread out
+    fa = sub_fst(seed)
+    rng = np.random.default_rng(seed)
+    sw = np.full(fa.num_states, np.inf, np.float32)
+    starts = rng.choice(fa.num_states, 6, replace=False)
+    sw[starts] = rng.uniform(0.0, 3.0, 6).astype(np.float32)
+    sw[0] = 0.0
+    fw = np.full(fa.num_states, np.inf, np.float32)
+    finals = rng.choice(fa.num_states, 25, replace=False)
+    fw[finals] = rng.uniform(0.0, 3.0, 25).astype(np.float32)
+    fa.start_weight, fa.final_weight = sw, fw
+    return fa
+
+
+def test_state_posteriors_match_oracle():
+    import torch
+    from paper_1701_03038_gb300.fst import Fst
+    fa = _multi_start_fst()
+    strs = synth.make_strings(fa, 12, 1, 30, seed=12)
+    # append an empty string: its path starts and ends in the same state
+    strs = synth.Strings(strs.ids, np.concatenate([strs.offsets, strs.offsets[-1:]]))
+    f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+    ids, off = _dev(strs)
+    w = np.linspace(0.5, 2.0, strs.count).astype(np.float32)
+    plan = f.plan(ids, off, flags=1 | 2)
+    plan.forward_backward(torch.from_numpy(w).cuda(), states=True)
+    torch.cuda.synchronize()
+    want = o.state_posteriors_batch(strs.ids, strs.offsets, weights=w)
+    assert_counts_close(plan.start_counts[:fa.num_states].cpu().numpy(), want["start"], batch=True)
+    assert_counts_close(plan.final_counts[:fa.num_states].cpu().numpy(), want["final"], batch=True)
+    assert want["start"].sum() == pytest.approx(float(w.sum()), rel=1e-9)
+    # forward then backward with states gives the same
+    plan.forward()
+    plan.backward(torch.from_numpy(w).cuda(), states=True)
+    torch.cuda.synchronize()
+    assert_counts_close(plan.final_counts[:fa.num_states].cpu().numpy(), want["final"], batch=True)
+
+
+def test_gradients_of_start_and_final_weights():
+    import torch
+    from paper_1701_03038_gb300.autograd import log_z
+    from paper_1701_03038_gb300.fst import Fst
+    fa = _multi_start_fst(47)
+    strs = synth.make_strings(fa, 8, 5, 25, seed=13)
+    f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+    ids, off = _dev(strs)
+    plan = f.plan(ids, off, flags=1 | 2)
+    theta = torch.tensor(o.theta, device="cuda", requires_grad=True)
+    ts = torch.tensor(oracle.theta_of_cost(fa.start_weight), device="cuda", dtype=torch.float32, requires_grad=True)
+    tf = torch.tensor(oracle.theta_of_cost(fa.final_weight), device="cuda", dtype=torch.float32, requires_grad=True)
+    lz = log_z(theta, f, plan, ts, tf)
+    lz.sum().backward()
+    want = o.state_posteriors_batch(strs.ids, strs.offsets)
+    assert_counts_close(ts.grad.double().cpu().numpy(), want["start"], batch=True)
+    assert_counts_close(tf.grad.double().cpu().numpy(), want["final"], batch=True)
+    ob = o.fb_batch(strs.ids, strs.offsets, nthreads=4)
+    assert_counts_close(theta.grad.double().cpu().numpy(), ob["counts"], batch=True)
+    # a changed final weight reaches log Z: one gradient step on theta_f
+    # raises sum log Z by about |grad|^2 * lr
+    with torch.no_grad():
+        tf2 = torch.where(torch.isfinite(tf), tf + 0.01 * tf.grad, tf)
+    lz2 = log_z(theta.detach(), f, plan, ts.detach(), tf2)
+    gain = float((lz2.sum() - lz.sum()).item())
+    g2 = float((tf.grad[torch.isfinite(tf)] ** 2).sum().item())
+    assert gain == pytest.approx(0.01 * g2, rel=0.05)
+
