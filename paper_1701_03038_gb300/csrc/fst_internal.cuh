@@ -7,12 +7,14 @@
 //   forward  -- segments by destination (the column-major / CSC reading of
 //               Sec. 4: one reduction per destination state), arcs carry src;
 //   backward -- segments by source, arcs carry dst.
-// Segments are packed into windows of WIN = 128 arcs (one warp, 4 arcs per
-// lane, 16-byte vector loads).  A segment never straddles a window unless it
-// is longer than WIN ("long" segment): then it starts on a window boundary
-// and owns whole windows.  The tail of a window is padded with arcs of
-// weight -inf.  Each window has a 128-bit head mask (bit i set = arc i
-// starts a segment) and the index of its first segment.
+// Segments are packed into windows of WIN = 128 arcs.  A segment never
+// straddles a window unless it is longer than WIN ("long" segment): then it
+// starts on a window boundary and owns whole windows.  The tail of a window
+// is padded with arcs of weight -inf.  Each window has a 128-bit head mask
+// (bit i set = arc i starts a segment) and the index of its first segment;
+// the windows serve the float64 check kernels (fd64.cu).  The step kernels
+// use the backward layout only, through its packed 16-byte arc records and
+// a (symbol, state) hash of its segments.
 #pragma once
 
 #include <cuda_runtime.h>
