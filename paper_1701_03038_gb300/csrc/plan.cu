@@ -404,7 +404,10 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
   do {
     // symbols: checked on the device, then read back for the host tables
     if ((rc = dalloc(&d_ids_copy, N)) || (rc = dalloc(&d_err, 1))) break;
-    if (N > 0) FST_CUDA(cudaMemcpyAsync(d_ids_copy, d_ids, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
+    if (N > 0 && cudaMemcpyAsync(d_ids_copy, d_ids, (size_t)N * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "ids copy");
+      break;
+    }
     if (cudaMemsetAsync(d_err, 0, 4, s) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset"); break; }
     if (N > 0) k_check_ids<<<nblk(N), TB, 0, s>>>(d_ids_copy, N, f->m, d_err);
     unsigned int e = 0;
@@ -415,7 +418,10 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
     }
     if (e) { set_error("a symbol id is outside [0, %d)", f->m); rc = FST_ERR_INVALID_ARG; break; }
     std::vector<int32_t> hid(N);
-    if (N > 0) FST_CUDA(cudaMemcpy(hid.data(), d_ids_copy, (size_t)N * 4, cudaMemcpyDeviceToHost));
+    if (N > 0 && cudaMemcpy(hid.data(), d_ids_copy, (size_t)N * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "ids read-back");
+      break;
+    }
     // relaxations of one pass (the paper's definition: every arc of every slice)
     P->relax = 0;
     for (int64_t i = 0; i < N; ++i) P->relax += f->h_sym_arc[hid[i] + 1] - f->h_sym_arc[hid[i]];
