@@ -150,6 +150,12 @@ def bytes_model(stats, ids):
     }
 
 
+# Dependent random 8-byte loads over buffers larger than L2 saturate near
+# this rate on a GB300 (measured with a pointer-chasing probe, 131,072
+# chains: 33-39 G/s for buffers of 1-32 GB).
+RANDOM_ACCESS_PEAK = 35.0
+
+
 def load_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -325,6 +331,7 @@ def main():
     prof = {k: (pv[k][0] + pf[k][0], pv[k][1] + pf[k][1]) for k in pv}
     plan_v.profile(False)
     plan_f.profile(False)
+    live = plan_f.live_work()
     model = bytes_model(stats, strs.ids)
     # a pass is its first-position push plus its kernels per position (Viterbi
     # one, forward two, backward one); the byte model is per pass, so the
@@ -345,6 +352,28 @@ def main():
                 "backward+posterior 20|A|+8U+4D (every arc of the slice, as the paper relaxes it)",
                 "peak_source": peak_src}
 
+    # the work the frontier-driven kernels actually do, against the bound
+    # that applies to it: random accesses (a pool entry or an arc each costs
+    # a few loads or atomics at unrelated addresses)
+    acc_model = {  # random accesses per live entry and per pushed arc
+        "vit": (5, 2),  # accumulator, hash probe, arc source, state map read and write; arc, atomicMax
+        "fwd": (2, 4),  # accumulator line, hash probe; arc and atomicMax, then arc and fixed-point add
+        "bwd": (1, 3),  # backward value; arc, backward value of the destination, count atomic
+    }
+    live_passes = {}
+    for k, (pe, pa) in acc_model.items():
+        acc = pe * live["entries"] + pa * max(live["arcs"], 0)
+        gps = acc / (pass_ms[k] / 1000.0) / 1e9 if pass_ms[k] > 0 else None
+        tr = load_traffic(k, args.workload)
+        live_passes[k] = {"accesses": acc, "g_accesses_per_s": round(gps, 2) if gps else None,
+                          "frac": round(gps / RANDOM_ACCESS_PEAK, 4) if gps else None,
+                          "dram_gbs": round(tr / (pass_ms[k] / 1000.0) / 1e9, 1) if tr and pass_ms[k] > 0 else None}
+    roofline_live = {"bound": "random DRAM accesses", "unit": "G accesses/s", "peak": RANDOM_ACCESS_PEAK,
+                     "peak_source": "pointer-chasing probe on a GB300 (profiles/launches_c3.md)",
+                     "live_entries_per_pass": live["entries"], "live_arcs_per_pass": live["arcs"],
+                     "model": "random accesses per live entry / per pushed arc: Viterbi 5/2, forward 2/4, "
+                              "backward 1/3", "passes": live_passes}
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -356,7 +385,7 @@ def main():
                       "l2": "no flush: inputs larger than L2 (arc store "
                             f"{(fa.num_arcs * 24) / 2**30:.2f} GiB, frontiers and per-step storage "
                             f"{info['device_bytes'] / 2**30:.1f} GiB)"},
-           "sentences_per_s": sent_s, "roofline": roofline, "passes": passes, "kernels": kernels, "clocks": clk,
+           "sentences_per_s": sent_s, "roofline": roofline, "roofline_live": roofline_live, "passes": passes, "kernels": kernels, "clocks": clk,
            "gpu_launches": args.steps * (info["viterbi_launches"] + info["fb_launches"])}
 
     # plain method (one string at a time, one launch per position) on a sample

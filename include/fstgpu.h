@@ -269,6 +269,13 @@ FST_API int fst_log_z_f64(fst_t* fst, const double* theta, const int32_t* ids, i
 FST_API int fst_plan_profile(fst_plan_t* plan, int32_t enable);
 FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t* launches_by_kind);
 
+/* The live work of the plan's last pass (its last wave), for measurement:
+ * *entries = live states over all positions (the pool entries handed out),
+ * *arcs = arcs out of those states on their next symbol (the pushes of the
+ * forward pass; -1 for a plan without forward-backward storage).  Waits for
+ * the plan's work on `stream`.  Either output may be NULL. */
+FST_API int fst_plan_live_work(fst_plan_t* plan, int64_t* entries, int64_t* arcs, void* stream);
+
 /* Plain-method Viterbi of one string that allocates no memory (the paper
  * has no counterpart: this is a deployment variant of fst_viterbi).  For
  * callers that cannot allocate device memory at decode time -- a host whose

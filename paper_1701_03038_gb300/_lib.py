@@ -43,6 +43,7 @@ SIGNATURES = {
     "fst_plan_backward": [vp, vp, vp, vp],
     "fst_plan_forward_backward": [vp, vp, vp, vp, vp, vp],
     "fst_plan_backward_ex": [vp, vp, vp, vp, vp, vp],
+    "fst_plan_live_work": [vp, vp, vp, vp],
     "fst_plan_forward_backward_ex": [vp, vp, vp, vp, vp, vp, vp, vp],
     "fst_plan_profile": [vp, i32],
     "fst_plan_profile_read": [vp, vp, vp],

@@ -34,6 +34,16 @@ constexpr int64_t POOL_PER_TOKEN = 256;
 // counts, pool ranges, step maxima and running sums)
 constexpr int64_t TOKEN_BYTES = 80;
 
+// *sum += the non-negative values of v[0..n).
+__global__ void k_sum_i32(const int32_t* __restrict__ v, int64_t n, unsigned long long* __restrict__ sum) {
+  unsigned long long acc = 0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (unsigned long long)(uint32_t)max(v[i], 0);
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sum, acc);
+}
+
 __global__ void k_check_ids(const int32_t* __restrict__ ids, int64_t n, int32_t m, unsigned int* __restrict__ err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && (ids[i] < 0 || ids[i] >= m)) atomicOr(err, 1u);
@@ -684,6 +694,37 @@ extern "C" int fst_forward_backward_batch(fst_t* f, const int32_t* d_ids, const 
   if (!rc && e != cudaSuccess) rc = cuda_fail(e, "fst_forward_backward_batch");
   if (rc) fst_plan_destroy(P); else put_cached(f, 1, P);
   return rc;
+}
+
+extern "C" int fst_plan_live_work(fst_plan_t* P, int64_t* entries, int64_t* arcs, void* stream) {
+  if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
+  cudaStream_t s = as_stream(stream);
+  int64_t top = 0;
+  FST_CUDA(cudaMemcpyAsync(&top, P->pool_top, 8, cudaMemcpyDeviceToHost, s));
+  FST_CUDA(cudaStreamSynchronize(s));
+  top = std::min(top, P->pool_cap);
+  if (entries) *entries = top;
+  if (arcs) {
+    *arcs = -1;
+    if (P->want_fb) {
+      unsigned long long* d_sum = nullptr;
+      int rc = dalloc(&d_sum, 1);
+      if (rc) return rc;
+      unsigned long long h = 0;
+      cudaError_t e = cudaMemsetAsync(d_sum, 0, 8, s);
+      if (e == cudaSuccess && top > 0) {
+        k_sum_i32<<<(unsigned)std::min<int64_t>(1024, (top + TB - 1) / TB), TB, 0, s>>>(P->pool_n, top, d_sum);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_sum, 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      dfree(d_sum);
+      if (rc) return rc;
+      if (e != cudaSuccess) return cuda_fail(e, "fst_plan_live_work");
+      *arcs = (int64_t)h;
+    }
+  }
+  return FST_OK;
 }
 
 extern "C" int fst_plan_profile(fst_plan_t* P, int32_t enable) {

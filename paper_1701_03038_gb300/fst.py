@@ -276,6 +276,12 @@ class Plan:
         return dict(strings=b.value, tokens=n.value, waves=w.value, max_len=ml.value, relaxations=r.value,
                     viterbi_launches=vl.value, fb_launches=fl.value, device_bytes=by.value)
 
+    def live_work(self, stream=None) -> dict:
+        """Live states and pushed arcs of the last pass (see fst_plan_live_work)."""
+        e, a = C.c_int64(), C.c_int64()
+        check(self._lib.fst_plan_live_work(self._h, C.byref(e), C.byref(a), _stream(stream)), "fst_plan_live_work")
+        return dict(entries=e.value, arcs=a.value)
+
     def profile(self, enable: bool = True):
         """Bracket every kernel of the following runs with CUDA events."""
         check(self._lib.fst_plan_profile(self._h, 1 if enable else 0), "fst_plan_profile")
