@@ -162,7 +162,7 @@ def test_graph_capture_and_replay_after_weight_change(c2s):
     check_batch_viterbi(o, strs, dict(scores=p.scores[:strs.count], paths=p.paths[:len(strs.ids)],
                                       olabels=p.olabels[:len(strs.ids)], status=p.status[:strs.count]))
     check_batch_fb(o, strs, p.logz[:strs.count], p.counts[:o.A])
-    # new weights, same graph: fresh frontier tags every replay keep results exact
+    # new weights, same graph: every run leaves its accumulators zero, so replays stay exact
     rng = np.random.default_rng(8)
     fa.weight = (fa.weight * rng.uniform(0.5, 1.5, size=fa.num_arcs)).astype(np.float32)
     f.set_weights(fa.weight)
