@@ -183,7 +183,8 @@ FST_API int fst_forward_backward_batch(fst_t* fst, const int32_t* d_ids, const i
  *   d_ids, d_offsets  as fst_viterbi_batch; they are read during
  *               fst_plan_create only (the plan keeps its own copy).
  *   mem_budget_bytes  cap on per-step storage; strings are processed in
- *               waves that fit (0 = a default of 16 GiB).
+ *               waves that fit (0 = half the free device memory at the
+ *               call, at least 16 GiB).
  *   flags       FST_PLAN_SINGLE_WAVE: fail with FST_ERR_OOM instead of
  *               splitting into waves (needed by fst_plan_forward followed by
  *               fst_plan_backward, which keep state between calls).

@@ -436,7 +436,17 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
     P->relax = 0;
     for (int64_t i = 0; i < N; ++i) P->relax += f->h_sym_arc[hid[i] + 1] - f->h_sym_arc[hid[i]];
     // waves: consecutive strings whose memory fits the budget
-    const int64_t budget = mem_budget_bytes > 0 ? mem_budget_bytes : ((int64_t)16 << 30);
+    // default: half the device memory free now, at least 16 GiB (a batch in
+    // fewer waves makes fewer, fuller launches)
+    int64_t budget = mem_budget_bytes;
+    if (budget <= 0) {
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_b = 0;
+      }
+      budget = std::max<int64_t>((int64_t)16 << 30, (int64_t)(free_b / 2));
+    }
     // accumulators: 2 x 8 bytes per state (Viterbi), or 2 x 16 for the
     // forward sums and maxima plus 2 x 4 for the backward values; Viterbi
     // also maps states to pool entries, 2 x 4 bytes
@@ -469,10 +479,12 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
       P->max_ntok = std::max<int64_t>(P->max_ntok, w.ntok);
       P->max_stage = std::max(P->max_stage, w.stage);
       P->max_len = std::max(P->max_len, w.tmax);
-      // live pool: its exact bound when that is small, else the largest of
-      // POOL_PER_TOKEN entries per token, a quarter of the budget and 256 MiB
+      // live pool: its exact bound when that is small, else the larger of
+      // POOL_PER_TOKEN entries per token and a quarter of the budget (at
+      // least 256 MiB, at most 4 GiB)
       const int64_t ebytes = 16;
-      const int64_t want = std::max(w.ntok * POOL_PER_TOKEN, std::max(budget / 4, (int64_t)256 << 20) / ebytes);
+      const int64_t want = std::max(w.ntok * POOL_PER_TOKEN,
+                                    std::min(std::max(budget / 4, (int64_t)256 << 20), (int64_t)4 << 30) / ebytes);
       // pool entries are named by int32 indices
       P->pool_cap = std::max(P->pool_cap, std::min(std::min(w.pool_bound, want), (int64_t)INT32_MAX));
     }
