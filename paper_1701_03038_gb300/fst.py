@@ -91,6 +91,13 @@ class Fst:
         return cls(fa.num_states, fa.src, fa.dst, fa.ilabel, fa.olabel, fa.weight, fa.start_weight,
                    fa.final_weight, fa.num_isyms, weight_kind="cost", device=device)
 
+    @classmethod
+    def from_att(cls, source, isyms=None, osyms=None, device=None, **kw) -> "Fst":
+        """Build from OpenFst / AT&T text (a path, text or file object; see
+        ``att.read_att`` for the symbol tables and options)."""
+        from . import att
+        return cls.from_arrays(att.read_att(source, isyms, osyms, **kw), device=device)
+
     def close(self):
         if self._h is not None and self._h.value:
             self._lib.fst_destroy(self._h)
