@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--budget-gb", type=float, default=48.0, help="plan storage budget (waves)")
     ap.add_argument("--plain-sample", type=int, default=48, help="strings timed on the plain path")
     ap.add_argument("--cpu-sample", type=int, default=16, help="strings timed on the CPU oracle")
+    ap.add_argument("--slice-sample", type=int, default=16,
+                    help="strings decoded with the paper's slice-wide relaxation for comparison")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
     ap.add_argument("--no-plain", action="store_true")
@@ -421,6 +423,24 @@ def main():
         out["plain"] = {"value": rx / dt, "unit": UNIT, "sentences_per_s": n / dt,
                         "sample": f"first {n} strings, host API (fst_viterbi + fst_forward_backward)"}
         out["batched_over_plain_sentences"] = sent_s / world / (n / dt)
+        # the paper's own relaxation (every arc of every slice, one thread
+        # per arc, packed atomicMax) against the frontier-driven plain path,
+        # Viterbi only, on the first strings
+        k = min(args.slice_sample, strs.count)
+        f.viterbi_slice(strs.get(0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b in range(k):
+            f.viterbi_slice(strs.get(b))
+        dt_slice = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for b in range(k):
+            f.viterbi(strs.get(b))
+        dt_ours = time.perf_counter() - t0
+        out["paper_design"] = {"sample": f"first {k} strings, Viterbi, one string at a time",
+                               "slice_relaxation_sentences_per_s": k / dt_slice,
+                               "frontier_plain_sentences_per_s": k / dt_ours,
+                               "speedup": dt_slice / dt_ours}
 
     # end to end through the public batch API with host buffers
     if not args.no_e2e:

@@ -131,6 +131,16 @@ FST_API int fst_set_state_weights(fst_t* fst, const float* start_weight, const f
 FST_API int fst_viterbi(fst_t* fst, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
                 int32_t* olabels);
 
+/* The paper's relaxation, kept for comparison (Sec. 5.1): Viterbi of one
+ * string where, at every position, each arc of the slice delta[w_t] is
+ * relaxed by its own thread whether or not its source is live, and
+ * collisions on a destination are resolved by a packed 64-bit atomicMax.
+ * Arguments, results and errors as fst_viterbi (bit-identical results),
+ * without output labels.  The handle keeps per-arc records of the slices
+ * and an (n+1) x num_states key array for the last string; fst_destroy
+ * frees them. */
+FST_API int fst_viterbi_slice(fst_t* fst, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path);
+
 /* Plain method, one string: forward-backward (Alg. 2, Sec. 5.2).  Host
  * pointers; synchronous.
  *   log_z          host double: log of the total weight of the string (Eq. 1

@@ -32,6 +32,7 @@ SIGNATURES = {
     "fst_set_weights": [vp, vp, i32, i32],
     "fst_set_state_weights": [vp, vp, vp, i32, i32],
     "fst_viterbi": [vp, vp, i32, vp, vp, vp],
+    "fst_viterbi_slice": [vp, vp, i32, vp, vp],
     "fst_forward_backward": [vp, vp, i32, vp, vp],
     "fst_viterbi_batch": [vp, vp, vp, i32, vp, vp, vp, vp, vp],
     "fst_forward_backward_batch": [vp, vp, vp, i32, vp, vp, vp, vp, vp],

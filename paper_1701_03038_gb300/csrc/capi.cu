@@ -410,6 +410,8 @@ extern "C" int fst_destroy(fst_t* f) {
   }
   delete f->batch_mu;
   f->batch_mu = nullptr;
+  dfree(f->slice_arcs);
+  dfree(f->slice_keys);
   delete f->plain;
   f->plain = nullptr;
   free_layout(f->fwd);

@@ -96,6 +96,12 @@ struct fst_s {
   // storage the next call of that kind takes over
   struct fst_plan_s* batch_plan[2] = {nullptr, nullptr};
   std::mutex* batch_mu = nullptr;
+  // the paper's slice-wide relaxation (fst_viterbi_slice): per-arc records
+  // {src, dst, id} in the destination-segmented layout's order, and the
+  // packed keys of every position of the last string
+  int4* slice_arcs = nullptr;
+  unsigned long long* slice_keys = nullptr;
+  int64_t slice_cap = 0;
 };
 
 namespace fstgpu {

@@ -174,6 +174,19 @@ class Fst:
         check(rc, "fst_viterbi", allow=(_lib.OK, _lib.NO_PATH))
         return best[0], path[:n], olab[:n], rc
 
+    def viterbi_slice(self, ids):
+        """The paper's relaxation (every arc of every slice, one thread per
+        arc), for comparison: (score float32, arc ids int32[n], status),
+        bit-identical to viterbi()."""
+        x = _host(ids, np.int32)
+        n = int(x.shape[0])
+        best = np.zeros(1, np.float32)
+        path = np.zeros(max(n, 1), np.int32)
+        with torch.cuda.device(self.device):
+            rc = self._lib.fst_viterbi_slice(self._h, _hptr(x), n, _hptr(best), _hptr(path))
+        check(rc, "fst_viterbi_slice", allow=(_lib.OK, _lib.NO_PATH))
+        return best[0], path[:n], rc
+
     def forward_backward(self, ids, posteriors: bool = True):
         """(log Z float64, expected arc counts float32[A] or None, status)."""
         x = _host(ids, np.int32)

@@ -179,3 +179,28 @@ def test_shorter_strings_after_longer_on_one_handle():
     for n in (60, 45, 30, 12, 5, 2, 1, 33):
         x = synth.make_strings(fa, 1, n, n, seed=100 + n).get(0)
         check_string(f, o, x)
+
+
+def test_slice_relaxation_is_bit_identical():
+    # the paper's relaxation (every arc of every slice, one thread per arc)
+    # against the oracle and the frontier-driven plain path
+    rng = np.random.default_rng(19)
+    cases = [(synth.fig1_fst(), [np.array([0, 1, 2], np.int32), np.array([2], np.int32), np.zeros(0, np.int32)])]
+    for _ in range(6):
+        fa = synth.tiny_fst(rng)
+        cases.append((fa, [rng.integers(0, fa.num_isyms, size=int(rng.integers(0, 7))).astype(np.int32)
+                           for _ in range(4)]))
+    fa, strs = synth.make_config("c2", scale=0.02, strings=6)
+    cases.append((fa, [strs.get(b) for b in range(strs.count)]))
+    for fa, xs in cases:
+        f, o = _fst(fa), oracle.Fst(fa)
+        for x in xs:
+            ov = o.viterbi(x)
+            s1, p1, st = f.viterbi_slice(x)
+            assert st == ov["status"]
+            assert s1 == ov["best"] or (np.isinf(ov["best"]) and s1 == ov["best"])
+            if ov["status"] == 0:
+                assert np.array_equal(p1, ov["path"])
+                s2, p2, _, _ = f.viterbi(x)
+                assert s1 == s2 and np.array_equal(p1, p2)
+
