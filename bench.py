@@ -260,7 +260,13 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    gbuild.build()
+    # one rank builds (when the in-tree library is stale) while the others
+    # wait, so that no two ranks write the same object files
+    if rank == 0:
+        gbuild.build()
+    if world > 1:
+        dist.barrier()
+        gbuild.build()
     dev = torch.device("cuda", local)
 
     fa, strs = synth.make_config(args.workload)
