@@ -5,8 +5,9 @@
 // slice by source and then target (Sec. 5).  Here each slice is instead
 // sorted by (segment state, arc id) on the device -- destination for the
 // forward layout, source for the backward layout -- and packed into
-// 128-arc windows whose head masks let one warp reduce whole segments
-// without atomics.
+// 128-arc windows (their head masks serve the float64 check kernels).  The
+// backward layout also gets packed 16-byte arc records and a (symbol,
+// state) hash of its segments, which the step kernels read.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
