@@ -1,22 +1,37 @@
 #!/usr/bin/env python
-"""Benchmark: batched Viterbi + forward-backward on the 20M-arc workload.
+"""Benchmark of the FST decoding hot path on the synthetic workloads.
 
-One step = one pass of the whole hot path over one batch: Viterbi (relax,
-final reduction, backtrace) and forward-backward (forward relax, log Z,
-backward relax fused with arc posteriors, counts back to arc order) for all
-4,096 strings of the 200,000-state, 20,000-symbol, 20,000,000-arc synthetic
-FST (lengths U[5, 200], random-walk strings, seeded).  Inputs are resident
-in HBM when the timed region starts and are larger than the L2 cache.
+Default workload (the 20M-arc batching workload): one step is one pass of
+the whole hot path over one batch -- Viterbi (relax, final reduction,
+backtrace) and forward-backward (forward relax, log Z, backward relax fused
+with arc posteriors, counts back to arc order) for all 4,096 strings of the
+200,000-state, 20,000-symbol, 20,000,000-arc FST (lengths U[5, 200],
+random-walk strings, seeded).  Inputs are resident in HBM when the timed
+region starts and are larger than the L2 cache.
+
+Other workloads (``--workload``):
+  c1  one 50-symbol string on a 1,000-state FST, plain method (latency);
+  c2  1,000 strings on a 5,000,000-arc FST, plain method, one string at a
+      time (one launch per position), the batched method timed beside it;
+  c4  a training step on a 2,000,000-arc FST: log Z of 1,024 strings
+      through autograd, loss.backward() (the fused backward pass) and an
+      SGD update of the arc weights;
+  c5  64 strings of length 1,000 on a 100,000,000-arc FST, batched.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 the host cores instead, on a bounded sample of the same workload.
+``--ingest-traffic CSV JSONLINE`` turns an ncu launch list (DRAM bytes per
+launch) of a small run into the per-pass traffic figures of
+profiles/traffic.json.
 """
 from __future__ import annotations
 
 import argparse
+import csv
+import hashlib
 import json
-import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -32,18 +47,31 @@ if ROOT not in sys.path:
 METRIC = "arc-relaxations/s & sentences/s, batched vs plain, % of HBM roofline"
 UNIT = "arc-relaxations/s"
 WORKLOADS = {
-    "c3": "batched: 200,000 states, 20,000 input symbols, 20,000,000 arcs (Zipf arcs per symbol, lognormal "
-          "out-degree mean 100, Dirichlet(0.5) weights), 4,096 random-walk strings of length U[5,200]; "
-          "Viterbi + forward-backward with arc posteriors per step",
-    "c2": "plain-shaped: 50,000 states, 10,000 symbols, 5,000,000 arcs, 1,000 strings of length U[10,60]",
-    "c4": "100,000 states, 5,000 symbols, 2,000,000 arcs, 1,024 strings of length U[10,100]",
-    "c5": "1,000,000 states, 5,000 symbols, 100,000,000 arcs, 64 strings of length 1,000",
-    "c1": "1,000 states, 50 symbols, 20,000 arcs, one string of length 50",
+    "c1": ("plain", "1,000 states, 50 input / 20 output symbols, 20,000 arcs (uniform laws, Dirichlet(1) "
+                    "weights), one string of length 50; plain method, Viterbi + forward-backward with posteriors"),
+    "c2": ("plain", "50,000 states, 10,000 symbols, 5,000,000 arcs (Zipf arcs per symbol, lognormal out-degree "
+                    "mean 100, Dirichlet(0.5)), 1,000 strings of length U[10,60]; plain method, one string at a "
+                    "time, Viterbi + forward-backward with posteriors"),
+    "c3": ("batch", "batched: 200,000 states, 20,000 input symbols, 20,000,000 arcs (Zipf arcs per symbol, "
+                    "lognormal out-degree mean 100, Dirichlet(0.5) weights), 4,096 random-walk strings of length "
+                    "U[5,200]; Viterbi + forward-backward with arc posteriors per step"),
+    "c4": ("train", "training: 100,000 states, 5,000 symbols, 2,000,000 arc weights with requires_grad, 1,024 "
+                    "strings of length U[10,100]; loss = sum log Z, backward = expected counts, SGD update"),
+    "c5": ("batch", "batched: 1,000,000 states, 5,000 symbols, 100,000,000 arcs (uniform laws, Dirichlet(1)), "
+                    "64 strings of length 1,000; Viterbi + forward-backward with arc posteriors per step"),
 }
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+# the files that decide what the step kernels read and write
+KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "store.cu", "plan.cu")
+PASS_KERNELS = {"vit": ("vit_first", "vit_step"), "fwd": ("fwd_first", "fwd_sum", "fwd_step"),
+                "bwd": ("bwd_step",)}
+KERNEL_NAMES = {"vit_first": "k_vit_first", "vit_step": "k_vit_step", "fwd_first": "k_fwd_first",
+                "fwd_sum": "k_fwd_sum", "fwd_step": "k_fwd_step", "bwd_step": "k_bwd_step",
+                "vit_final": "k_vit_final", "backtrace": "k_backtrace", "fb_final": "k_fb_final",
+                "counts": "k_counts_out"}
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -51,8 +79,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--budget-gb", type=float, default=48.0, help="plan storage budget (waves)")
-    ap.add_argument("--plain-sample", type=int, default=48, help="strings timed on the plain path")
-    ap.add_argument("--cpu-sample", type=int, default=16, help="strings timed on the CPU oracle")
+    ap.add_argument("--plain-sample", type=int, default=48, help="strings timed on the plain path (batch workloads)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--slice-sample", type=int, default=16,
                     help="strings decoded with the paper's slice-wide relaxation for comparison")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -61,7 +89,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps from the host, not a CUDA graph")
-    return ap.parse_args()
+    ap.add_argument("--ingest-traffic", nargs=2, metavar=("NCU_CSV", "BENCH_JSON"),
+                    help="write profiles/traffic.json from an ncu launch list of a small run and that run's line")
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------- clocks
@@ -135,28 +165,27 @@ def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
     return units_per_rank * world / seconds
 
 
-# ---------------------------------------------------------------- models
-PASS_KERNELS = {"vit": ("vit_first", "vit_step"), "fwd": ("fwd_first", "fwd_sum", "fwd_step"),
-                "bwd": ("bwd_step",)}
-KERNEL_NAMES = {"vit_first": "k_vit_first", "vit_step": "k_vit_step", "fwd_first": "k_fwd_first",
-                "fwd_sum": "k_fwd_sum", "fwd_step": "k_fwd_step", "bwd_step": "k_bwd_step"}
+# ------------------------------------------------------------ byte models
+def live_bytes(entries: int, arcs: int) -> dict:
+    """Algorithmic bytes of the work the kernels do in one pass, with the
+    per-step coefficients of the byte model (12 B per arc record, 4 B per
+    source or destination value, 8 B per count read-modify-write) applied to
+    the live work: each live state is a destination once and a source once,
+    and every arc out of a live state is relaxed once per pass.
+      Viterbi  12 P + 4 E (sources) + 8 E (value and backpointer)
+      forward  12 P + 4 E + 4 E
+      backward 20 P + 8 E + 4 E (arcs, counts, alpha and beta, beta out)"""
+    e, p = float(entries), float(max(arcs, 0))
+    return {"vit": 12 * p + 12 * e, "fwd": 12 * p + 8 * e, "bwd": 20 * p + 12 * e}
 
 
-def bytes_model(stats, ids):
-    """Algorithmic bytes per pass (sum over tokens of the per-step figures):
-    Viterbi 12|A|+4U+8D, forward 12|A|+4U+4D, backward+posterior 20|A|+8U+4D."""
+def slice_bytes(stats, ids) -> dict:
+    """The same model over every arc of every slice (the paper's relaxation,
+    which the frontier kernels do not perform): per token Viterbi
+    12|A|+4U+8D, forward 12|A|+4U+4D, backward 20|A|+8U+4D."""
     A, D, U = (s.astype(np.float64)[ids] for s in stats)
-    return {
-        "vit": float((12 * A + 4 * U + 8 * D).sum()),
-        "fwd": float((12 * A + 4 * U + 4 * D).sum()),
-        "bwd": float((20 * A + 8 * U + 4 * D).sum()),
-    }
-
-
-# Dependent random 8-byte loads over buffers larger than L2 saturate near
-# this rate on a GB300 (measured with a pointer-chasing probe, 131,072
-# chains: 33-39 G/s for buffers of 1-32 GB).
-RANDOM_ACCESS_PEAK = 35.0
+    return {"vit": float((12 * A + 4 * U + 8 * D).sum()), "fwd": float((12 * A + 4 * U + 4 * D).sum()),
+            "bwd": float((20 * A + 8 * U + 4 * D).sum())}
 
 
 def load_peak():
@@ -169,26 +198,7 @@ def load_peak():
         return 6800.0, "fallback (6.8 TB/s)"
 
 
-def load_traffic(pass_name: str, workload: str):
-    """ncu DRAM bytes (read + write) of one whole pass, the same unit as the
-    model bytes behind `achieved`; None once the kernel sources changed."""
-    try:
-        with open(PROFILE_SUMMARY) as fh:
-            d = json.load(fh)
-        e = d.get(workload, {}).get(pass_name)
-        if e and e.get("source_hash") == source_hash():
-            return e.get("dram_bytes_per_pass")
-    except (OSError, ValueError):
-        pass
-    return None
-
-
-# the files that decide what the step kernels read and write
-KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "store.cu")
-
-
 def source_hash():
-    import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1701_03038_gb300", "csrc")
     for f in KERNEL_SOURCES:
@@ -197,66 +207,201 @@ def source_hash():
     return h.hexdigest()[:12]
 
 
+def load_traffic():
+    """Per-pass DRAM bytes per algorithmic byte, measured by ncu on a small
+    run of the current kernels; None when the kernel sources changed since."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d
+
+
+def roofline(prof, live, peak, peak_src, traffic, stats=None, ids=None):
+    """Roofline of the dominant pass (the pass with the most kernel time)."""
+    pass_ms = {k: sum(prof[x][0] for x in ks) for k, ks in PASS_KERNELS.items()}
+    pass_ms = {k: v for k, v in pass_ms.items() if v > 0}
+    dom = max(pass_ms, key=pass_ms.get)
+    alg = live_bytes(live["entries"], live["arcs"])
+    sec = pass_ms[dom] / 1000.0
+    achieved = alg[dom] / sec / 1e9
+    tr = None
+    if traffic is not None and dom in traffic.get("passes", {}):
+        tr = traffic["passes"][dom]["dram_per_algorithmic_byte"] * alg[dom]
+    r = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+         "frac": round(achieved / peak, 5), "traffic": None if tr is None else int(tr),
+         "per": f"{dom} pass (all its launches)",
+         "kernel": " + ".join(KERNEL_NAMES[x] for x in PASS_KERNELS[dom]),
+         "launches": sum(prof[x][1] for x in PASS_KERNELS[dom]), "pass_ms": round(pass_ms[dom], 3),
+         "algorithmic_bytes": int(alg[dom]),
+         "bytes_model": "live work: Viterbi 12P+12E, forward 12P+8E, backward 20P+12E (P arcs out of live states, "
+                        "E live states), the per-step coefficients of the byte model",
+         "peak_source": peak_src}
+    if tr is not None:
+        r["dram_gbs"] = round(tr / sec / 1e9, 1)
+        r["dram_frac"] = round(tr / sec / 1e9 / peak, 4)
+        r["wasted_traffic_ratio"] = round(tr / alg[dom], 2)
+        r["traffic_source"] = traffic.get("note", "")
+    if stats is not None:
+        sl = slice_bytes(stats, ids)
+        r["slice_model_gbs"] = round(sl[dom] / sec / 1e9, 1)
+    passes = {}
+    for k, v in pass_ms.items():
+        passes[k] = {"ms": round(v, 3), "algorithmic_gbs": round(alg[k] / (v / 1000.0) / 1e9, 2)}
+        if traffic is not None and k in traffic.get("passes", {}):
+            t = traffic["passes"][k]["dram_per_algorithmic_byte"] * alg[k]
+            passes[k]["dram_gbs"] = round(t / (v / 1000.0) / 1e9, 1)
+    return r, passes
+
+
+# ---------------------------------------------------------- CPU oracle leg
+def host_mem_bytes() -> int:
+    try:
+        return int(os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE"))
+    except (ValueError, OSError, AttributeError):
+        return 16 << 30
+
+
+def oracle_threads(fa, strs, sel):
+    """Threads for the oracle's batch calls: every string in flight keeps
+    (n+1) x Q float64 forward and backward tables, and every thread a
+    float64 count per arc; use at most a third of the free host memory."""
+    cores = os.cpu_count() or 1
+    nmax = max(len(strs.get(b)) for b in sel) if len(sel) else 1
+    per = 16 * (nmax + 1) * fa.num_states + 8 * fa.num_arcs
+    return max(1, min(cores, len(sel), host_mem_bytes() // 3 // max(per, 1)))
+
+
+def cpu_oracle_run(fa, strs, sel, kind):
+    """One oracle pass over strings ``sel``: Viterbi + forward-backward with
+    counts (the step of the batch and plain workloads; the training step is
+    forward-backward with counts).  Returns (seconds, relaxations, threads)."""
+    import oracle
+    o = oracle.Fst(fa)
+    ids = np.concatenate([strs.get(b) for b in sel]).astype(np.int32)
+    off = np.zeros(len(sel) + 1, np.int64)
+    off[1:] = np.cumsum([len(strs.get(b)) for b in sel])
+    th = oracle_threads(fa, strs, sel)
+    A = np.bincount(fa.ilabel, minlength=fa.num_isyms)
+    t0 = time.perf_counter()
+    if kind != "train":
+        o.viterbi_batch(ids, off, nthreads=th)
+    o.fb_batch(ids, off, nthreads=th)
+    dt = time.perf_counter() - t0
+    passes = 2 if kind == "train" else 3
+    return dt, passes * int(A[ids].sum()), th
+
+
+def cpu_sample(fa, strs, kind, target_s):
+    """Strings of a bounded oracle sample: grow it until one pass takes about
+    target_s seconds (at least one string)."""
+    n = 1
+    dt, _, _ = cpu_oracle_run(fa, strs, [0], kind)
+    if dt > 0:
+        n = int(max(1, min(strs.count, target_s / dt * min(os.cpu_count() or 1, 8))))
+    return list(range(n))
+
+
 # ------------------------------------------------------------- reference arm
+def workload_config(name, fa, strs):
+    return {"workload": name + ": " + WORKLOADS[name][1], "strings": strs.count, "tokens": int(len(strs.ids)),
+            "states": int(fa.num_states), "arcs": int(fa.num_arcs)}
+
+
+def make_workload(args):
+    from paper_1701_03038_gb300 import synth
+    fa, strs = synth.make_config(args.workload)
+    if args.strings and args.strings < strs.count:
+        strs = synth.Strings(strs.ids[:strs.offsets[args.strings]].copy(), strs.offsets[:args.strings + 1].copy())
+    return fa, strs
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
-    import oracle
-    from paper_1701_03038_gb300 import synth
-    fa, strs = synth.make_config(args.workload)
-    o = oracle.Fst(fa)
-    cores = os.cpu_count() or 1
-    sample = max(1, min(args.cpu_sample, strs.count))
-    A = np.bincount(fa.ilabel, minlength=fa.num_isyms)
-    times = []
-    relax = 0
+    fa, strs = make_workload(args)
+    kind = WORKLOADS[args.workload][0]
+    sel = cpu_sample(fa, strs, kind, min(args.cpu_seconds, 3.0))
+    times, relax, th = [], 0, 1
     for k in range(args.warmup + args.steps):
-        b0 = (k * sample) % strs.count
-        sel = [(b0 + i) % strs.count for i in range(sample)]
-        ids = np.concatenate([strs.get(b) for b in sel]).astype(np.int32)
-        off = np.zeros(sample + 1, np.int64)
-        off[1:] = np.cumsum([len(strs.get(b)) for b in sel])
-        t0 = time.perf_counter()
-        o.viterbi_batch(ids, off, nthreads=cores)
-        o.fb_batch(ids, off, nthreads=cores)
-        dt = time.perf_counter() - t0
+        dt, rx, th = cpu_oracle_run(fa, strs, sel, kind)
         if k >= args.warmup:
             times.append(dt)
-            relax += 3 * int(A[ids].sum())
+            relax += rx
     tot = sum(times)
     value = relax / tot
+    sample = (f"{len(sel)} of {strs.count} strings per step ({args.workload}), "
+              f"{'forward-backward with counts' if kind == 'train' else 'Viterbi + forward-backward with counts'}, "
+              f"{th} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic",
-        "config": {"workload": args.workload + ": " + WORKLOADS[args.workload],
-                   "reference": "CPU oracle (plain C; Viterbi float32, forward-backward float64)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} strings per step of the {args.workload} batch, "
-                                   f"Viterbi + forward-backward with counts, {cores} threads"},
+        "data": "synthetic", "config": workload_config(args.workload, fa, strs),
+        "sentences_per_s": len(sel) * len(times) / tot,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------- traffic ingest
+def ingest_traffic(csv_path, line_path):
+    """profiles/traffic.json from an ncu launch list (per launch
+    dram__bytes_read.sum and dram__bytes_write.sum) of a small run, and that
+    run's bench line (its live work): DRAM bytes per algorithmic byte per
+    pass, which bench.py multiplies by the algorithmic bytes of the full
+    run.  DRAM traffic is taken to grow in proportion to the live work."""
+    by_kernel = {}
+    with open(csv_path) as fh:
+        rows = [r for r in csv.reader(fh) if r]
+    head = None
+    for r in rows:
+        if "Kernel Name" in r and "Metric Name" in r:
+            head = r
+            continue
+        if head is None or len(r) != len(head):
+            continue
+        d = dict(zip(head, r))
+        m = re.search(r"\b(k_[A-Za-z0-9_]+)", d["Kernel Name"])
+        if not m:
+            continue
+        name = m.group(1)
+        if d["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            v = float(d["Metric Value"].replace(",", ""))
+            unit = d.get("Metric Unit", "byte").lower()
+            v *= {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9}.get(unit, 1)
+            by_kernel[name] = by_kernel.get(name, 0.0) + v
+    with open(line_path) as fh:
+        line = json.loads([x for x in fh.read().splitlines() if x.startswith("{")][-1])
+    live = line["live_work"]
+    alg = live_bytes(live["entries"], live["arcs"])
+    passes = {}
+    for p, ks in PASS_KERNELS.items():
+        tot = sum(by_kernel.get(KERNEL_NAMES[k], 0.0) for k in ks)
+        if tot > 0:
+            passes[p] = {"dram_bytes": int(tot), "algorithmic_bytes": int(alg[p]),
+                         "dram_per_algorithmic_byte": tot / alg[p]}
+    out = {"source_hash": source_hash(), "workload": line["config"]["workload"][:60],
+           "strings": line["config"]["strings"], "live_work": live, "passes": passes,
+           "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over every launch of one step of a small run "
+                   "(--cache-control none), per algorithmic byte of its live work; scaled by the live work"}
+    with open(TRAFFIC_FILE, "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------ our arm
-def main():
-    args = parse_args()
+def init(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1701_03038_gb300 import build as gbuild
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank)
-        return
-    import torch
-    import torch.distributed as dist
-
-    from paper_1701_03038_gb300 import build as gbuild
-    from paper_1701_03038_gb300 import synth
-    from paper_1701_03038_gb300.fst import Fst
-    from paper_1701_03038_gb300._lib import PLAN_NO_FB, PLAN_NO_VITERBI
-
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -267,13 +412,48 @@ def main():
     if world > 1:
         dist.barrier()
         gbuild.build()
-    dev = torch.device("cuda", local)
+    return rank, world, local, torch.device("cuda", local)
 
-    fa, strs = synth.make_config(args.workload)
-    if args.strings and args.strings < strs.count:
-        strs = synth.Strings(strs.ids[:strs.offsets[args.strings]].copy(), strs.offsets[:args.strings + 1].copy())
-    f = Fst.from_arrays(fa, device=dev)
-    stats = f.symbol_stats()
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def timed(run_step, args, world, dev, clocks):
+    """W untimed steps, then K steps timed by CUDA events on the current
+    stream with a barrier and a synchronize on both sides; max over ranks."""
+    import torch
+    for _ in range(max(3, args.warmup)):
+        run_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        run_step()
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    return max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev), clk
+
+
+def base_line(args, world, fa, strs, ms, relax_step, clk, launches):
+    return {"metric": METRIC, "value": job_throughput(relax_step, world, ms / 1000.0), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args.workload, fa, strs),
+            "sentences_per_s": job_throughput(strs.count, world, ms / 1000.0), "clocks": clk,
+            "gpu_launches": launches}
+
+
+def bench_batch(args, rank, world, dev, fa, strs, f, stats):
+    import torch
+    from paper_1701_03038_gb300._lib import PLAN_NO_FB, PLAN_NO_VITERBI
     ids = torch.from_numpy(strs.ids).to(dev)
     off = torch.from_numpy(strs.offsets).to(dev)
     # the Viterbi pass and forward-backward are independent: one plan each,
@@ -282,10 +462,7 @@ def main():
     plan_v = f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB)
     plan_f = f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI)
     info_v, info_f = plan_v.info(), plan_f.info()
-    info = {"waves": max(info_v["waves"], info_f["waves"]), "device_bytes": info_v["device_bytes"] + info_f["device_bytes"],
-            "viterbi_launches": info_v["viterbi_launches"], "fb_launches": info_f["fb_launches"]}
     relax_pass = info_v["relaxations"]
-    relax_step = 3 * relax_pass  # Viterbi, forward and backward each relax every slice
     s_v, s_f = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
     def step():
@@ -301,18 +478,10 @@ def main():
             join.record(st)
             main.wait_event(join)
 
-    def step_serial():
-        plan_v.viterbi()
-        plan_f.forward_backward()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    # the step's ~800 launches replay as one CUDA graph (both streams)
+    # the step's launches replay as one CUDA graph (both streams)
     graph = None
     if not args.no_graph:
         s_c = torch.cuda.Stream(device=dev)
@@ -321,100 +490,45 @@ def main():
         with torch.cuda.graph(graph, stream=s_c):
             step()
         torch.cuda.synchronize()
-        for _ in range(max(3, args.warmup)):
-            graph.replay()
-        torch.cuda.synchronize()
     run_step = graph.replay if graph is not None else step
-
-    clocks = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(args.steps):
-        run_step()
-    ev1.record()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev)
-    value = job_throughput(relax_step, world, ms / 1000.0)
-    sent_s = job_throughput(strs.count, world, ms / 1000.0)
+    ms, clk = timed(run_step, args, world, dev, ClockSampler(int(str(dev).split(":")[-1])))
+    launches = info_v["viterbi_launches"] + info_f["fb_launches"]
+    out = base_line(args, world, fa, strs, ms, 3 * relax_pass, clk, args.steps * launches)
 
     # per-kernel device time of one more step, with events around every
     # launch; the passes run one after the other here so that each kernel's
     # time is its own
     plan_v.profile(True)
     plan_f.profile(True)
-    step_serial()
+    plan_v.viterbi()
+    plan_f.forward_backward()
     torch.cuda.synchronize()
     pv, pf = plan_v.profile_read(), plan_f.profile_read()
     prof = {k: (pv[k][0] + pf[k][0], pv[k][1] + pf[k][1]) for k in pv}
     plan_v.profile(False)
     plan_f.profile(False)
     live = plan_f.live_work()
-    model = bytes_model(stats, strs.ids)
-    # a pass is its first-position push plus its kernels per position (Viterbi
-    # one, forward two, backward one); the byte model is per pass, so the
-    # roofline is taken over the pass's kernels
-    pass_ms = {k: sum(prof[x][0] for x in ks) for k, ks in PASS_KERNELS.items()}
-    dom = max(pass_ms, key=pass_ms.get)
     peak, peak_src = load_peak()
-    achieved = model[dom] / (pass_ms[dom] / 1000.0) / 1e9
-    kernels = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items()}
-    passes = {k: {"ms": round(v, 3), "model_gbs": round(model[k] / (v / 1000.0) / 1e9, 1) if v > 0 else None}
-              for k, v in pass_ms.items()}
-    traffic = load_traffic(dom, args.workload)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "per": f"{dom} pass",
-                "kernel": " + ".join(KERNEL_NAMES[x] for x in PASS_KERNELS[dom]),
-                "launches": sum(prof[x][1] for x in PASS_KERNELS[dom]),
-                "bytes_model": "per token: Viterbi 12|A|+4U+8D, forward 12|A|+4U+4D, "
-                "backward+posterior 20|A|+8U+4D (every arc of the slice, as the paper relaxes it)",
-                "peak_source": peak_src}
-
-    # the work the frontier-driven kernels actually do, against the bound
-    # that applies to it: random accesses (a pool entry or an arc each costs
-    # a few loads or atomics at unrelated addresses)
-    acc_model = {  # random accesses per live entry and per pushed arc
-        "vit": (5, 2),  # accumulator, hash probe, arc source, state map read and write; arc, atomicMax
-        "fwd": (2, 4),  # accumulator line, hash probe; arc and atomicMax, then arc and fixed-point add
-        "bwd": (1, 3),  # backward value; arc, backward value of the destination, count atomic
-    }
-    live_passes = {}
-    for k, (pe, pa) in acc_model.items():
-        acc = pe * live["entries"] + pa * max(live["arcs"], 0)
-        gps = acc / (pass_ms[k] / 1000.0) / 1e9 if pass_ms[k] > 0 else None
-        tr = load_traffic(k, args.workload)
-        live_passes[k] = {"accesses": acc, "g_accesses_per_s": round(gps, 2) if gps else None,
-                          "frac": round(gps / RANDOM_ACCESS_PEAK, 4) if gps else None,
-                          "dram_gbs": round(tr / (pass_ms[k] / 1000.0) / 1e9, 1) if tr and pass_ms[k] > 0 else None}
-    roofline_live = {"bound": "random DRAM accesses", "unit": "G accesses/s", "peak": RANDOM_ACCESS_PEAK,
-                     "peak_source": "pointer-chasing probe on a GB300 (profiles/launches_c3.md)",
-                     "live_entries_per_pass": live["entries"], "live_arcs_per_pass": live["arcs"],
-                     "model": "random accesses per live entry / per pushed arc: Viterbi 5/2, forward 2/4, "
-                              "backward 1/3", "passes": live_passes}
-
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": args.workload + ": " + WORKLOADS[args.workload], "strings": strs.count,
-                      "tokens": int(len(strs.ids)), "relaxations_per_pass": relax_pass, "waves": info["waves"],
-                      "plan_gb": round(info["device_bytes"] / 2**30, 2), "parallelism": "replicas" if world > 1 else "1 GPU",
-                      "streams": "a Viterbi plan and a forward-backward plan on two CUDA streams; per-kernel "
-                                 "times from one more step run serially",
-                      "launch": "CUDA graph replay" if graph is not None else "host launches",
-                      "l2": "no flush: inputs larger than L2 (arc store "
-                            f"{(fa.num_arcs * 24) / 2**30:.2f} GiB, frontiers and per-step storage "
-                            f"{info['device_bytes'] / 2**30:.1f} GiB)"},
-           "sentences_per_s": sent_s, "roofline": roofline, "roofline_live": roofline_live, "passes": passes, "kernels": kernels, "clocks": clk,
-           "gpu_launches": args.steps * (info["viterbi_launches"] + info["fb_launches"])}
+    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(), stats, strs.ids)
+    performed = 3 * max(live["arcs"], 0)
+    out["config"].update({
+        "relaxations_per_pass": relax_pass, "waves": max(info_v["waves"], info_f["waves"]),
+        "plan_gb": round((info_v["device_bytes"] + info_f["device_bytes"]) / 2**30, 2),
+        "parallelism": "replicas" if world > 1 else "1 GPU",
+        "streams": "a Viterbi plan and a forward-backward plan on two CUDA streams; per-kernel times from one "
+                   "more step run serially",
+        "launch": "CUDA graph replay" if graph is not None else "host launches",
+        "l2": "no flush: inputs larger than L2 (arc store and hash "
+              f"{(fa.num_arcs * 24) / 2**30:.2f} GiB, plan storage "
+              f"{(info_v['device_bytes'] + info_f['device_bytes']) / 2**30:.1f} GiB)"})
+    out.update({"relaxations_performed_per_s": job_throughput(performed, world, ms / 1000.0),
+                "live_work": live, "roofline": rl, "passes": passes,
+                "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}})
 
     # plain method (one string at a time, one launch per position) on a sample
     if not args.no_plain and rank == 0:
         n = min(args.plain_sample, strs.count)
-        for b in range(2):
+        for b in range(min(2, strs.count)):
             f.viterbi(strs.get(b))
             f.forward_backward(strs.get(b))
         torch.cuda.synchronize()
@@ -428,7 +542,7 @@ def main():
         dt = time.perf_counter() - t0
         out["plain"] = {"value": rx / dt, "unit": UNIT, "sentences_per_s": n / dt,
                         "sample": f"first {n} strings, host API (fst_viterbi + fst_forward_backward)"}
-        out["batched_over_plain_sentences"] = sent_s / world / (n / dt)
+        out["batched_over_plain_sentences"] = out["sentences_per_s"] / world / (n / dt)
         # the paper's own relaxation (every arc of every slice, one thread
         # per arc, packed atomicMax) against the frontier-driven plain path,
         # Viterbi only, on the first strings
@@ -450,74 +564,229 @@ def main():
 
     # end to end through the public batch API with host buffers
     if not args.no_e2e:
-        h_ids = torch.from_numpy(strs.ids).pin_memory()
-        h_off = torch.from_numpy(strs.offsets).pin_memory()
-        h_scores = torch.empty(strs.count, dtype=torch.float32).pin_memory()
-        h_paths = torch.empty(len(strs.ids), dtype=torch.int32).pin_memory()
-        h_logz = torch.empty(strs.count, dtype=torch.float64).pin_memory()
-        h_counts = torch.empty(fa.num_arcs, dtype=torch.float32).pin_memory()
+        out["e2e"] = e2e_batch(args, world, dev, fa, strs, f, s_v, s_f, 3 * relax_pass)
+    return out
 
-        import threading
 
-        def e2e_vit(st):
-            with torch.cuda.stream(st):
-                d_ids = h_ids.to(dev, non_blocking=True)
-                d_off = h_off.to(dev, non_blocking=True)
-                v = f.viterbi_batch(d_ids, d_off, stream=st)
-                h_scores.copy_(v["scores"], non_blocking=True)
-                h_paths.copy_(v["paths"], non_blocking=True)
-                st.synchronize()
+def e2e_batch(args, world, dev, fa, strs, f, s_v, s_f, relax_step):
+    import threading
 
-        def e2e_fb(st):
-            with torch.cuda.stream(st):
-                d_ids = h_ids.to(dev, non_blocking=True)
-                d_off = h_off.to(dev, non_blocking=True)
-                r = f.forward_backward_batch(d_ids, d_off, stream=st)
-                h_logz.copy_(r["logz"], non_blocking=True)
-                h_counts.copy_(r["counts"], non_blocking=True)
-                st.synchronize()
+    import torch
+    h_ids = torch.from_numpy(strs.ids).pin_memory()
+    h_off = torch.from_numpy(strs.offsets).pin_memory()
+    h_scores = torch.empty(strs.count, dtype=torch.float32).pin_memory()
+    h_paths = torch.empty(len(strs.ids), dtype=torch.int32).pin_memory()
+    h_logz = torch.empty(strs.count, dtype=torch.float64).pin_memory()
+    h_counts = torch.empty(fa.num_arcs, dtype=torch.float32).pin_memory()
 
-        def e2e_step():
-            # the two batch calls from two host threads on two streams: their
-            # plan builds overlap on the host and their kernels on the GPU
-            th = threading.Thread(target=e2e_fb, args=(s_f,))
-            th.start()
-            e2e_vit(s_v)
-            th.join()
+    def e2e_vit(st):
+        with torch.cuda.stream(st):
+            d_ids = h_ids.to(dev, non_blocking=True)
+            d_off = h_off.to(dev, non_blocking=True)
+            v = f.viterbi_batch(d_ids, d_off, stream=st)
+            h_scores.copy_(v["scores"], non_blocking=True)
+            h_paths.copy_(v["paths"], non_blocking=True)
+            st.synchronize()
 
+    def e2e_fb(st):
+        with torch.cuda.stream(st):
+            d_ids = h_ids.to(dev, non_blocking=True)
+            d_off = h_off.to(dev, non_blocking=True)
+            r = f.forward_backward_batch(d_ids, d_off, stream=st)
+            h_logz.copy_(r["logz"], non_blocking=True)
+            h_counts.copy_(r["counts"], non_blocking=True)
+            st.synchronize()
+
+    def e2e_step():
+        # the two batch calls from two host threads on two streams: their
+        # plan builds overlap on the host and their kernels on the GPU
+        th = threading.Thread(target=e2e_fb, args=(s_f,))
+        th.start()
+        e2e_vit(s_v)
+        th.join()
+
+    e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
         e2e_step()
-        barrier()
+    dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dev)
+    barrier(world)
+    h2d = strs.ids.nbytes + strs.offsets.nbytes
+    d2h = 4 * strs.count + 4 * len(strs.ids) + 8 * strs.count + 4 * fa.num_arcs
+    return {"value": job_throughput(relax_step, world, dt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * dt,
+            "api": "Fst.viterbi_batch and Fst.forward_backward_batch from two host threads on two streams (plans "
+                   "built per call; device storage kept from the previous call of the same kind)"}
+
+
+def bench_plain(args, rank, world, dev, fa, strs, f, stats):
+    """The plain method: one string at a time through the host API
+    (fst_viterbi + fst_forward_backward with posteriors), one launch per
+    position; a step is every string of the workload.  The host API copies
+    each string in and its results out, so the step is end to end."""
+    import torch
+    relax_step = 3 * int(stats[0][strs.ids].sum())
+
+    def step():
+        for b in range(strs.count):
+            x = strs.get(b)
+            f.viterbi(x)
+            f.forward_backward(x)
+
+    ms, clk = timed(step, args, world, dev, ClockSampler(int(str(dev).split(":")[-1])))
+    # launches per string: Viterbi n+3, forward-backward 3n+3
+    lens = np.diff(strs.offsets)
+    launches = int((lens + 3).sum() + (3 * lens + 3).sum())
+    out = base_line(args, world, fa, strs, ms, relax_step, clk, args.steps * launches)
+    out["config"].update({"parallelism": "replicas" if world > 1 else "1 GPU",
+                          "launch": "host launches, one string at a time (fst_viterbi, fst_forward_backward)",
+                          "l2": "no flush: the step streams every string's slices; consecutive strings share "
+                                "L2-resident arcs, as a decoding loop would"})
+    h2d = strs.ids.nbytes
+    d2h = 4 * strs.count + 4 * len(strs.ids) * 2 + 8 * strs.count + 4 * fa.num_arcs * strs.count
+    out["e2e"] = {"value": out["value"], "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                  "ms_per_step": ms, "api": "fst_viterbi + fst_forward_backward (host buffers; copies inside)"}
+    out["us_per_sentence"] = 1000.0 * ms / strs.count
+    # per-kernel times and live work of one more step, with events
+    f.profile(True)
+    entries = arcs = 0
+    for b in range(strs.count):
+        x = strs.get(b)
+        f.viterbi(x)
+        f.forward_backward(x)
+        lw = f.live_work()
+        entries += lw["entries"]
+        arcs += max(lw["arcs"], 0)
+    prof = f.profile_read()
+    f.profile(False)
+    live = {"entries": entries, "arcs": arcs}
+    peak, peak_src = load_peak()
+    rl, passes = roofline(prof, live, peak, peak_src, None, stats, strs.ids)
+    out.update({"relaxations_performed_per_s": job_throughput(3 * arcs, world, ms / 1000.0), "live_work": live,
+                "roofline": rl, "passes": passes,
+                "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}})
+    # the batched method on the same strings, for comparison
+    if strs.count > 1 and rank == 0:
+        import torch
+        from paper_1701_03038_gb300._lib import PLAN_NO_FB, PLAN_NO_VITERBI
+        ids = torch.from_numpy(strs.ids).to(dev)
+        off = torch.from_numpy(strs.offsets).to(dev)
+        pv = f.plan(ids, off, flags=PLAN_NO_FB)
+        pf = f.plan(ids, off, flags=PLAN_NO_VITERBI)
+        for _ in range(3):
+            pv.viterbi()
+            pf.forward_backward()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(5):
+            pv.viterbi()
+            pf.forward_backward()
+        ev1.record()
+        torch.cuda.synchronize()
+        bms = ev0.elapsed_time(ev1) / 5
+        out["batched"] = {"ms_per_step": bms, "sentences_per_s": strs.count / (bms / 1000.0),
+                          "value": relax_step / (bms / 1000.0), "unit": UNIT,
+                          "how": "the same strings as one plan each for Viterbi and forward-backward, host launches"}
+        out["batched_over_plain_sentences"] = out["batched"]["sentences_per_s"] / (out["sentences_per_s"] / world)
+    # the paper's slice-wide relaxation on the same strings (Viterbi)
+    if rank == 0:
+        k = min(args.slice_sample, strs.count)
+        f.viterbi_slice(strs.get(0))
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dev)
-        barrier()
-        h2d = strs.ids.nbytes + strs.offsets.nbytes
-        d2h = 4 * strs.count + 4 * len(strs.ids) + 8 * strs.count + 4 * fa.num_arcs
-        out["e2e"] = {"value": job_throughput(relax_step, world, dt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * dt,
-                      "api": "Fst.viterbi_batch and Fst.forward_backward_batch from two host threads on two "
-                             "streams (plans built per call; device storage kept from the previous call of the same kind)"}
+        for b in range(k):
+            f.viterbi_slice(strs.get(b))
+        dt_slice = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for b in range(k):
+            f.viterbi(strs.get(b))
+        dt_ours = time.perf_counter() - t0
+        out["paper_design"] = {"sample": f"first {k} strings, Viterbi, one string at a time",
+                               "slice_relaxation_sentences_per_s": k / dt_slice,
+                               "frontier_plain_sentences_per_s": k / dt_ours, "speedup": dt_slice / dt_ours}
+    return out
+
+
+def bench_train(args, rank, world, dev, fa, strs, f, stats):
+    """A training step: log Z of every string through autograd (forward
+    pass), loss = -sum log Z / B, loss.backward() (the fused backward pass:
+    the gradient is minus the expected counts), and an SGD update of the
+    arc log-weights (written back to the FST by the next forward)."""
+    import torch
+    from paper_1701_03038_gb300._lib import PLAN_SINGLE_WAVE
+    from paper_1701_03038_gb300.autograd import LogZModule
+    ids = torch.from_numpy(strs.ids).to(dev)
+    off = torch.from_numpy(strs.offsets).to(dev)
+    plan = f.plan(ids, off, mem_budget=int(args.budget_gb * (1 << 30)), flags=PLAN_SINGLE_WAVE)
+    info = plan.info()
+    mod = LogZModule(f, -torch.from_numpy(fa.weight.astype(np.float32)))
+    opt = torch.optim.SGD(mod.parameters(), lr=1e-3)
+    B = strs.count
+
+    def step():
+        opt.zero_grad(set_to_none=False)
+        loss = -mod(plan).sum() / B
+        loss.backward()
+        opt.step()
+
+    ms, clk = timed(step, args, world, dev, ClockSampler(int(str(dev).split(":")[-1])))
+    relax_pass = info["relaxations"]
+    out = base_line(args, world, fa, strs, ms, 2 * relax_pass, clk, args.steps * info["fb_launches"])
+    out["config"].update({"relaxations_per_pass": relax_pass, "plan_gb": round(info["device_bytes"] / 2**30, 2),
+                          "parallelism": "replicas" if world > 1 else "1 GPU",
+                          "launch": "host launches (fst_set_weights between steps is synchronous)",
+                          "l2": "no flush: arc store, plan storage and the 2M-arc count vector exceed L2"})
+    plan.profile(True)
+    step()
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile(False)
+    live = plan.live_work()
+    peak, peak_src = load_peak()
+    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(), stats, strs.ids)
+    out.update({"relaxations_performed_per_s": job_throughput(2 * max(live["arcs"], 0), world, ms / 1000.0),
+                "live_work": live, "roofline": rl, "passes": passes,
+                "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}})
+    h2d = 0
+    d2h = 8  # the loss
+    out["e2e"] = {"value": out["value"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                  "ms_per_step": ms, "api": "LogZModule forward, loss.backward(), SGD step (weights resident)"}
+    return out
+
+
+def main():
+    args = parse_args()
+    if args.ingest_traffic:
+        ingest_traffic(*args.ingest_traffic)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    rank, world, local, dev = init(args)
+    from paper_1701_03038_gb300.fst import Fst
+    fa, strs = make_workload(args)
+    f = Fst.from_arrays(fa, device=dev)
+    stats = f.symbol_stats()
+    kind = WORKLOADS[args.workload][0]
+    fn = {"batch": bench_batch, "plain": bench_plain, "train": bench_train}[kind]
+    out = fn(args, rank, world, dev, fa, strs, f, stats)
 
     # CPU oracle on the host cores, bounded sample (rank 0, N = 1 only)
     if not args.no_cpu and rank == 0 and world == 1:
-        import oracle
-        o = oracle.Fst(fa)
-        cores = os.cpu_count() or 1
-        n = min(args.cpu_sample, strs.count)
-        sel_ids = np.concatenate([strs.get(b) for b in range(n)]).astype(np.int32)
-        sel_off = strs.offsets[:n + 1].copy()
-        t0 = time.perf_counter()
-        o.viterbi_batch(sel_ids, sel_off, nthreads=cores)
-        o.fb_batch(sel_ids, sel_off, nthreads=cores)
-        dt = time.perf_counter() - t0
-        rx = 3 * int(stats[0][sel_ids].sum())
-        out["cpu_baseline"] = {"value": rx / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"first {n} strings of the batch, Viterbi + forward-backward with "
-                                         f"counts, {cores} threads, {dt:.1f} s"}
+        sel = cpu_sample(fa, strs, kind, args.cpu_seconds)
+        dt, rx, th = cpu_oracle_run(fa, strs, sel, kind)
+        out["cpu_baseline"] = {"value": rx / dt, "unit": UNIT, "cores": th, "kind": "oracle",
+                               "sentences_per_s": len(sel) / dt,
+                               "sample": f"first {len(sel)} strings of the workload, "
+                                         f"{'forward-backward with counts' if kind == 'train' else 'Viterbi + forward-backward with counts'}, "
+                                         f"{th} threads, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
 
 

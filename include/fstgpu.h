@@ -280,12 +280,34 @@ FST_API int fst_log_z_f64(fst_t* fst, const double* theta, const int32_t* ids, i
 FST_API int fst_plan_profile(fst_plan_t* plan, int32_t enable);
 FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t* launches_by_kind);
 
+/* The same per-launch timing for the single-string calls of a handle
+ * (fst_viterbi, fst_forward_backward): kinds and semantics as
+ * fst_plan_profile / fst_plan_profile_read. */
+FST_API int fst_profile(fst_t* fst, int32_t enable);
+FST_API int fst_profile_read(fst_t* fst, double* ms_by_kind, int64_t* launches_by_kind);
+
+/* The live work of the handle's last single-string call, for measurement:
+ * *entries = live states over all positions, *arcs = arcs out of them on
+ * their next symbol (-1 unless the last call was fst_forward_backward).
+ * Synchronous.  Either output may be NULL. */
+FST_API int fst_live_work(fst_t* fst, int64_t* entries, int64_t* arcs);
+
 /* The live work of the plan's last pass (its last wave), for measurement:
  * *entries = live states over all positions (the pool entries handed out),
  * *arcs = arcs out of those states on their next symbol (the pushes of the
  * forward pass; -1 for a plan without forward-backward storage).  Waits for
  * the plan's work on `stream`.  Either output may be NULL. */
 FST_API int fst_plan_live_work(fst_plan_t* plan, int64_t* entries, int64_t* arcs, void* stream);
+
+/* Cap the live pool of the plan's following runs at `entries` live states
+ * (over all positions of a wave; 0 = the capacity the plan allocated, which
+ * larger values cannot exceed).  Allocates nothing.  A run whose live states
+ * do not fit stops handing out pool entries, reports FST_ERR_OOM in the
+ * status of every string of its wave (scores -inf, paths -1, log Z -inf,
+ * no counts) and leaves the plan usable: the next run clears what the
+ * overflowing one left behind.  For memory-capped deployments and for
+ * exercising that failure path. */
+FST_API int fst_plan_limit_pool(fst_plan_t* plan, int64_t entries);
 
 /* Plain-method Viterbi of one string that allocates no memory (the paper
  * has no counterpart: this is a deployment variant of fst_viterbi).  For
@@ -300,8 +322,13 @@ FST_API int fst_plan_live_work(fst_plan_t* plan, int64_t* entries, int64_t* arcs
  *   d_score    device float [1]: best log-weight, -inf when no path.
  *   d_path     device int32 [n]: arc ids of the best path (-1 when no path).
  *   d_olabels  device int32 [n] or NULL.
- *   stream     cudaStream_t; the call is asynchronous on it.
- * Results are bit-identical to fst_viterbi.  Returns FST_ERR_UNSUPPORTED
+ *   stream     cudaStream_t of the FST's device; the call is asynchronous
+ *              on it.  The FST's device must be the current device
+ *              (FST_ERR_INVALID_ARG otherwise, nothing launched).
+ * Score, path and output labels are bit-identical to fst_viterbi.  Being
+ * asynchronous, the call cannot return FST_ERR_NO_PATH: a string without an
+ * accepting path is reported only through the outputs (*d_score = -inf and
+ * d_path all -1), and the return code is FST_OK.  Returns FST_ERR_UNSUPPORTED
  * (nothing is launched) when the string needs more than the fixed array:
  * about 24*Q + 16*(sum over positions of the distinct destinations of the
  * position's symbol) + 8*(the largest such count) + 60*n bytes.  The

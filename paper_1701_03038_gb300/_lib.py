@@ -46,6 +46,10 @@ SIGNATURES = {
     "fst_plan_backward_ex": [vp, vp, vp, vp, vp, vp],
     "fst_plan_live_work": [vp, vp, vp, vp],
     "fst_plan_forward_backward_ex": [vp, vp, vp, vp, vp, vp, vp, vp],
+    "fst_plan_limit_pool": [vp, i64],
+    "fst_profile": [vp, i32],
+    "fst_profile_read": [vp, vp, vp],
+    "fst_live_work": [vp, vp, vp],
     "fst_plan_profile": [vp, i32],
     "fst_plan_profile_read": [vp, vp, vp],
     "fst_viterbi_noalloc": [vp, vp, i32, vp, vp, vp, vp],

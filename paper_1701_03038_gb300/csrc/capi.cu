@@ -39,6 +39,26 @@ int grid_for(int64_t work_warps, int block_threads, int num_sms, int max_blocks_
   if (need > cap) need = cap;
   return (int)(need < 1 ? 1 : need);
 }
+int LaunchProfile::read(double* ms_by_kind, int64_t* launches_by_kind) {
+  double ms[FST_PROF_KINDS] = {0};
+  int64_t cnt[FST_PROF_KINDS] = {0};
+  if (used > 0) FST_CUDA(cudaEventSynchronize(ev[2 * (used - 1) + 1]));
+  for (size_t i = 0; i < used; ++i) {
+    float t = 0.f;
+    FST_CUDA(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+    const int k = kind[i];
+    if (k >= 0 && k < FST_PROF_KINDS) {
+      ms[k] += t;
+      cnt[k] += 1;
+    }
+  }
+  used = 0;
+  for (int k = 0; k < FST_PROF_KINDS; ++k) {
+    if (ms_by_kind) ms_by_kind[k] = ms[k];
+    if (launches_by_kind) launches_by_kind[k] = cnt[k];
+  }
+  return FST_OK;
+}
 }  // namespace fstgpu
 
 extern "C" const char* fst_last_error(void) { return g_err; }
@@ -106,6 +126,15 @@ struct DevBuf {
 
 }  // namespace
 
+// Launch bracketed by the handle's profile events (fst_profile).
+#define PLAIN_PROF(kind, call)                        \
+  do {                                                \
+    const long pi__ = f->prof.begin((kind), s);       \
+    const int rc__ = (call);                          \
+    f->prof.end(pi__, s);                             \
+    if (rc__) return rc__;                            \
+  } while (0)
+
 // ======================================================== plain workspace
 // Working memory of the plain method (one string, one launch per position),
 // kept by the FST handle and grown on demand.
@@ -136,6 +165,7 @@ struct PlainWs {
   int64_t* bw_off = nullptr;
   int64_t* pool_top = nullptr;
   uint32_t* flags = nullptr;
+  bool last_fb = false;                 // the last call was forward-backward (pool_n holds arc counts)
   ~PlainWs() {
     dfree(acc); dfree(beta); dfree(vmap); dfree(tok_sym); dfree(tok_b); dfree(iota); dfree(zero64);
     dfree(slot_base); dfree(step_rng); dfree(scnt); dfree(pool_base); dfree(pool_cnt); dfree(mkey); dfree(ekey);
@@ -555,11 +585,12 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
   const TokenView T = plain_tokview(w);
   const FrontierState S = plain_state(f);
   // one launch per input position (Sec. 5), after the first position's push
-  if (n >= 1 && (rc = launch_vit_first(L, T, plain_step(f, n, 1, 0), S, s))) return rc;
+  if (n >= 1) PLAIN_PROF(FST_PROF_VIT_FIRST, launch_vit_first(L, T, plain_step(f, n, 1, 0), S, s));
   for (int32_t t = 1; t <= n; ++t)
-    if ((rc = launch_vit_step(L, T, plain_step(f, n, t, t + 1), S, s))) return rc;
-  if ((rc = launch_vit_final(S, 1, w->score, w->jfinal, w->status, s))) return rc;
-  if ((rc = launch_backtrace(S, f->olabel, 1, w->jfinal, w->paths, w->olabels, s))) return rc;
+    PLAIN_PROF(FST_PROF_VIT_STEP, launch_vit_step(L, T, plain_step(f, n, t, t + 1), S, s));
+  PLAIN_PROF(FST_PROF_VIT_FINAL, launch_vit_final(S, 1, w->score, w->jfinal, w->status, s));
+  PLAIN_PROF(FST_PROF_BACKTRACE, launch_backtrace(S, f->olabel, 1, w->jfinal, w->paths, w->olabels, s));
+  w->last_fb = false;
   int32_t st = 0;
   FST_CUDA(cudaMemcpy(best_score, w->score, 4, cudaMemcpyDeviceToHost));
   FST_CUDA(cudaMemcpy(&st, w->status, 4, cudaMemcpyDeviceToHost));
@@ -592,19 +623,20 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   const LayoutView L = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
   const FrontierState S = plain_state(f);
-  if (n >= 1 && (rc = launch_fwd_first(L, T, plain_step(f, n, 1, 0), S, s))) return rc;
+  if (n >= 1) PLAIN_PROF(FST_PROF_FWD_FIRST, launch_fwd_first(L, T, plain_step(f, n, 1, 0), S, s));
   for (int32_t t = 1; t <= n; ++t) {
-    if ((rc = launch_fwd_sum(L, T, plain_step(f, n, t, t - 1), S, s))) return rc;
-    if ((rc = launch_fwd_step(L, T, plain_step(f, n, t, t + 1), S, s))) return rc;
+    PLAIN_PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, plain_step(f, n, t, t - 1), S, s));
+    PLAIN_PROF(FST_PROF_FWD_STEP, launch_fwd_step(L, T, plain_step(f, n, t, t + 1), S, s));
   }
-  if ((rc = launch_fb_final(S, 1, w->logz, w->status, s))) return rc;
+  PLAIN_PROF(FST_PROF_FB_FINAL, launch_fb_final(S, 1, w->logz, w->status, s));
+  w->last_fb = true;
   if (arc_posteriors) {
     const CountView C{0, w->cnt, w->comp, nullptr};
     FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
     FST_CUDA(cudaMemsetAsync(w->comp, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
     for (int32_t t = n; t >= 1; --t)
-      if ((rc = launch_bwd_step(L, T, plain_step(f, n, t, t - 1), S, C, s))) return rc;
-    if ((rc = launch_counts_out(f->A, C, w->counts_out, s))) return rc;
+      PLAIN_PROF(FST_PROF_BWD_STEP, launch_bwd_step(L, T, plain_step(f, n, t, t - 1), S, C, s));
+    PLAIN_PROF(FST_PROF_COUNTS, launch_counts_out(f->A, C, w->counts_out, s));
     if (f->A > 0)
       FST_CUDA(cudaMemcpy(arc_posteriors, w->counts_out, (size_t)f->A * 4, cudaMemcpyDeviceToHost));
   }
@@ -614,6 +646,57 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   if (st != FST_OK) {
     set_error("no accepting path");
     return FST_ERR_NO_PATH;
+  }
+  return FST_OK;
+}
+
+// ============================================================ measurement
+extern "C" int fst_profile(fst_t* f, int32_t enable) {
+  if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
+  f->prof.on = enable != 0;
+  f->prof.used = 0;
+  return FST_OK;
+}
+
+extern "C" int fst_profile_read(fst_t* f, double* ms_by_kind, int64_t* launches_by_kind) {
+  if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
+  DevGuard g(f->device);
+  return f->prof.read(ms_by_kind, launches_by_kind);
+}
+
+namespace {
+// *sum += the non-negative values of v[0..n).
+__global__ void k_sum_nonneg(const int32_t* __restrict__ v, int64_t n, unsigned long long* __restrict__ sum) {
+  unsigned long long acc = 0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (unsigned long long)(uint32_t)max(v[i], 0);
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sum, acc);
+}
+}  // namespace
+
+extern "C" int fst_live_work(fst_t* f, int64_t* entries, int64_t* arcs) {
+  if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
+  DevGuard g(f->device);
+  PlainWs* w = f->plain;
+  if (entries) *entries = 0;
+  if (arcs) *arcs = w && w->last_fb ? 0 : -1;
+  if (!w) return FST_OK;
+  int64_t top = 0;
+  FST_CUDA(cudaMemcpy(&top, w->pool_top, 8, cudaMemcpyDeviceToHost));
+  top = std::min(top, w->cap_pool);
+  if (entries) *entries = top;
+  if (arcs && w->last_fb && top > 0) {
+    DevBuf sum;
+    FST_CUDA(cudaMalloc(&sum.p, 8));
+    FST_CUDA(cudaMemset(sum.p, 0, 8));
+    k_sum_nonneg<<<(unsigned)std::min<int64_t>(1024, (top + TB - 1) / TB), TB>>>(w->pool_n, top,
+                                                                              (unsigned long long*)sum.p);
+    FST_CUDA(cudaGetLastError());
+    unsigned long long h = 0;
+    FST_CUDA(cudaMemcpy(&h, sum.p, 8, cudaMemcpyDeviceToHost));
+    *arcs = (int64_t)h;
   }
   return FST_OK;
 }

@@ -22,6 +22,7 @@
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "fstgpu.h"
 
@@ -72,6 +73,39 @@ struct Layout {
   int64_t* h_sym_lwin = nullptr;
 };
 
+// Per-launch timing (the tracing subsystem): with `on`, every launch that a
+// run brackets with begin/end gets two CUDA events on its stream; read()
+// waits for the last one and sums device milliseconds and launches per
+// kernel kind (FST_PROF_*), then starts over.
+struct LaunchProfile {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  size_t used = 0;
+  ~LaunchProfile() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  long begin(int k, cudaStream_t s) {
+    if (!on) return -1;
+    const size_t i = used;
+    while (ev.size() < 2 * (i + 1)) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      ev.push_back(e);
+    }
+    if (kind.size() < i + 1) kind.resize(i + 1);
+    kind[i] = k;
+    cudaEventRecord(ev[2 * i], s);
+    used = i + 1;
+    return (long)i;
+  }
+  void end(long i, cudaStream_t s) {
+    if (i >= 0) cudaEventRecord(ev[2 * i + 1], s);
+  }
+  // ms_by_kind / launches_by_kind: FST_PROF_KINDS entries each, or NULL
+  int read(double* ms_by_kind, int64_t* launches_by_kind);
+};
+
 }  // namespace fstgpu
 
 struct fst_s {
@@ -92,6 +126,8 @@ struct fst_s {
   int32_t max_seg_len = 0;
   // per-handle state for the single-string calls
   struct PlainWs* plain = nullptr;
+  // launch timing of the single-string calls (fst_profile)
+  fstgpu::LaunchProfile prof;
   // the last plan of each batch call kind (Viterbi, forward-backward), whose
   // storage the next call of that kind takes over
   struct fst_plan_s* batch_plan[2] = {nullptr, nullptr};

@@ -85,6 +85,16 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
     set_error("fst_viterbi_noalloc: bad arguments");
     return FST_ERR_INVALID_ARG;
   }
+  // the FST's memory, the scratch array's address and the caller's stream
+  // all belong to the FST's device: a call made while another device is
+  // current is refused before anything is launched or looked up
+  int cur = -1;
+  FST_CUDA(cudaGetDevice(&cur));
+  if (cur != f->device) {
+    set_error("fst_viterbi_noalloc: device %d is current but the FST lives on device %d (make it current and "
+              "pass a stream of that device)", cur, f->device);
+    return FST_ERR_INVALID_ARG;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   // sizes first, from host data only
   int64_t pool = 0, dmax = 1;

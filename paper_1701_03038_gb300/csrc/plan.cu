@@ -92,6 +92,7 @@ struct fst_plan_s {
   int64_t *slot_base = nullptr, *step_rng = nullptr;
   int64_t* pool_top = nullptr;
   int64_t pool_cap = 0;
+  int64_t pool_limit = 0;  // fst_plan_limit_pool: entries a run may use (0 = pool_cap)
   uint32_t* flags_d = nullptr;
   uint32_t *mkey = nullptr, *ekey = nullptr;
   double *csum = nullptr, *esum = nullptr;
@@ -105,12 +106,8 @@ struct fst_plan_s {
   int64_t cap_bw = 0, cap_nt = 0, cap_stage = 0, cap_len = 0, cap_B = 0, store_bytes = 0;
   bool forward_done = false;
   // optional per-launch CUDA events (fst_plan_profile)
-  bool prof_on = false;
-  std::vector<cudaEvent_t> prof_ev;
-  std::vector<int> prof_kind;
-  size_t prof_used = 0;
+  LaunchProfile prof;
   ~fst_plan_s() {
-    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     for (Wave& w : waves) w.release();
 #define PLAN_FREE(x) dfree(x);
     PLAN_STORAGE(PLAN_FREE)
@@ -118,29 +115,11 @@ struct fst_plan_s {
   }
 };
 
-// Per-launch timing: an event before and after every kernel of a run.
-static long prof_begin(fst_plan_s* P, int kind, cudaStream_t s) {
-  if (!P->prof_on) return -1;
-  const size_t i = P->prof_used;
-  while (P->prof_ev.size() < 2 * (i + 1)) {
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) return -1;
-    P->prof_ev.push_back(e);
-  }
-  if (P->prof_kind.size() < i + 1) P->prof_kind.resize(i + 1);
-  P->prof_kind[i] = kind;
-  cudaEventRecord(P->prof_ev[2 * i], s);
-  P->prof_used = i + 1;
-  return (long)i;
-}
-static void prof_end(fst_plan_s* P, long i, cudaStream_t s) {
-  if (i >= 0) cudaEventRecord(P->prof_ev[2 * i + 1], s);
-}
 #define PROF(kind, call)                              \
   do {                                                \
-    const long pi__ = prof_begin(P, (kind), s);       \
+    const long pi__ = P->prof.begin((kind), s);       \
     const int rc__ = (call);                          \
-    prof_end(P, pi__, s);                             \
+    P->prof.end(pi__, s);                             \
     if (rc__) return rc__;                            \
   } while (0)
 
@@ -251,7 +230,7 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.slot_base = P->slot_base;
   S.step_rng = P->step_rng;
   S.pool_top = P->pool_top;
-  S.pool_cap = P->pool_cap;
+  S.pool_cap = P->pool_limit > 0 ? std::min(P->pool_limit, P->pool_cap) : P->pool_cap;
   S.flags = P->flags_d;
   S.theta_s = f->theta_s;
   S.theta_f = f->theta_f;
@@ -739,31 +718,20 @@ extern "C" int fst_plan_live_work(fst_plan_t* P, int64_t* entries, int64_t* arcs
   return FST_OK;
 }
 
+extern "C" int fst_plan_limit_pool(fst_plan_t* P, int64_t entries) {
+  if (!P || entries < 0) { set_error("fst_plan_limit_pool: bad arguments"); return FST_ERR_INVALID_ARG; }
+  P->pool_limit = entries;
+  return FST_OK;
+}
+
 extern "C" int fst_plan_profile(fst_plan_t* P, int32_t enable) {
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
-  P->prof_on = enable != 0;
-  P->prof_used = 0;
+  P->prof.on = enable != 0;
+  P->prof.used = 0;
   return FST_OK;
 }
 
 extern "C" int fst_plan_profile_read(fst_plan_t* P, double* ms_by_kind, int64_t* launches_by_kind) {
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
-  double ms[FST_PROF_KINDS] = {0};
-  int64_t cnt[FST_PROF_KINDS] = {0};
-  if (P->prof_used > 0) FST_CUDA(cudaEventSynchronize(P->prof_ev[2 * (P->prof_used - 1) + 1]));
-  for (size_t i = 0; i < P->prof_used; ++i) {
-    float t = 0.f;
-    FST_CUDA(cudaEventElapsedTime(&t, P->prof_ev[2 * i], P->prof_ev[2 * i + 1]));
-    const int k = P->prof_kind[i];
-    if (k >= 0 && k < FST_PROF_KINDS) {
-      ms[k] += t;
-      cnt[k] += 1;
-    }
-  }
-  P->prof_used = 0;
-  for (int k = 0; k < FST_PROF_KINDS; ++k) {
-    if (ms_by_kind) ms_by_kind[k] = ms[k];
-    if (launches_by_kind) launches_by_kind[k] = cnt[k];
-  }
-  return FST_OK;
+  return P->prof.read(ms_by_kind, launches_by_kind);
 }

@@ -211,6 +211,26 @@ class Fst:
                                           _hptr(lz)), "fst_log_z_f64")
         return float(lz[0])
 
+    # ------------------------------------------------------- measurement
+    def profile(self, enable: bool = True):
+        """Bracket every kernel of the following single-string calls with CUDA events."""
+        check(self._lib.fst_profile(self._h, 1 if enable else 0), "fst_profile")
+
+    def profile_read(self) -> dict:
+        """{kind: (milliseconds, launches)} of the single-string calls since the last read."""
+        ms = np.zeros(len(_lib.PROF_KINDS), np.float64)
+        n = np.zeros(len(_lib.PROF_KINDS), np.int64)
+        with torch.cuda.device(self.device):
+            check(self._lib.fst_profile_read(self._h, _hptr(ms), _hptr(n)), "fst_profile_read")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(_lib.PROF_KINDS)}
+
+    def live_work(self) -> dict:
+        """Live states and pushed arcs of the last single-string call (see fst_live_work)."""
+        e, a = C.c_int64(), C.c_int64()
+        with torch.cuda.device(self.device):
+            check(self._lib.fst_live_work(self._h, C.byref(e), C.byref(a)), "fst_live_work")
+        return dict(entries=e.value, arcs=a.value)
+
     # ------------------------------------------------------ batched method
     def plan(self, ids: torch.Tensor, offsets: torch.Tensor, mem_budget: int = 0, flags: int = 0,
              stream=None) -> "Plan":
@@ -301,6 +321,10 @@ class Plan:
         e, a = C.c_int64(), C.c_int64()
         check(self._lib.fst_plan_live_work(self._h, C.byref(e), C.byref(a), _stream(stream)), "fst_plan_live_work")
         return dict(entries=e.value, arcs=a.value)
+
+    def limit_pool(self, entries: int = 0):
+        """Cap the live pool of the following runs (0 = the full capacity)."""
+        check(self._lib.fst_plan_limit_pool(self._h, int(entries)), "fst_plan_limit_pool")
 
     def profile(self, enable: bool = True):
         """Bracket every kernel of the following runs with CUDA events."""

@@ -5,16 +5,20 @@ memory manager that owns every allocation, a latency-critical loop that must
 not synchronise on cudaMalloc/cudaFree, a hard memory cap): its working
 memory is a fixed device array inside the library.  These tests call it
 through the C ABI and compare it with fst_viterbi, the allocating entry
-point, on two calls in a row.  This file is collected last on purpose.
+point, on two calls in a row, and with the oracle, including a string with
+no accepting path and the empty string.  This file is collected last on
+purpose.
 """
 import ctypes
+import math
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1701_03038_gb300 import synth
 
-from gpu_util import ensure_built
+from gpu_util import assert_viterbi_equal, ensure_built
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +48,7 @@ def test_noalloc_matches_fst_viterbi_on_two_calls_in_a_row():
     lib = _lib.load()
     fa, strs = synth.make_config("c2", scale=0.02, strings=4)
     f = Fst.from_arrays(fa)
+    o = oracle.Fst(fa)
     # a longer string, then a shorter one: the second call starts from the
     # first call's leftovers in the shared array
     order = sorted(range(strs.count), key=lambda b: -len(strs.get(b)))[:2]
@@ -57,12 +62,51 @@ def test_noalloc_matches_fst_viterbi_on_two_calls_in_a_row():
         torch.cuda.synchronize()
         free_after = torch.cuda.mem_get_info()[0]
         assert rc == 0, lib.fst_last_error()
-        # Viterbi is compared bit for bit
+        # Viterbi is compared bit for bit, with fst_viterbi and with the oracle
         assert score.item() == ref_score, (call, score.item(), ref_score)
         assert np.array_equal(path.cpu().numpy(), ref_path), call
         assert np.array_equal(olab.cpu().numpy(), ref_olab), call
+        assert_viterbi_equal(score.item(), path.cpu().numpy(), olab.cpu().numpy(), oracle.OK, o.viterbi(x))
         if call == 1:  # the first call may load kernel code; the second must not change free memory
             assert free_after == free_before, (free_before, free_after)
+
+
+def test_noalloc_no_path_and_empty_string():
+    # i.i.d. strings mostly have no accepting path: the outputs say so (-inf
+    # score, -1 path) while the return code stays FST_OK (the call is
+    # asynchronous); the empty string scores the best start-and-final state
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    from paper_1701_03038_gb300.fst import Fst
+    lib = _lib.load()
+    fa, _ = synth.make_config("c1", scale=0.2, strings=1)
+    f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+    stream = torch.cuda.current_stream()
+    iid = synth.make_strings(fa, 6, 20, 40, seed=77, kind="iid")
+    seen_nopath = 0
+    for b in range(iid.count):
+        x = iid.get(b)
+        ov = o.viterbi(x)
+        rc, score, path, olab = _noalloc(lib, f, x, stream)
+        torch.cuda.synchronize()
+        assert rc == 0, lib.fst_last_error()
+        if ov["status"] == oracle.NO_PATH:
+            seen_nopath += 1
+            assert score.item() == -math.inf
+            assert (path.cpu().numpy() == -1).all() and (olab.cpu().numpy() == -1).all()
+        else:
+            assert_viterbi_equal(score.item(), path.cpu().numpy(), olab.cpu().numpy(), oracle.OK, ov)
+        s_ref, p_ref, _, _ = f.viterbi(x)
+        assert score.item() == s_ref and np.array_equal(path.cpu().numpy(), p_ref)
+    assert seen_nopath > 0
+    # n = 0: no path array is touched; the score is the best start state's
+    # start plus final weight (-inf here: state 0 is not final)
+    empty = np.zeros(0, np.int32)
+    rc, score, _, _ = _noalloc(lib, f, empty, stream)
+    torch.cuda.synchronize()
+    assert rc == 0, lib.fst_last_error()
+    ov = o.viterbi(empty)
+    assert np.float32(score.item()) == ov["best"] or (math.isinf(ov["best"]) and score.item() == ov["best"])
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
