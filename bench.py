@@ -60,6 +60,7 @@ WORKLOADS = {
     "c5": ("batch", "batched: 1,000,000 states, 5,000 symbols, 100,000,000 arcs (uniform laws, Dirichlet(1)), "
                     "64 strings of length 1,000; Viterbi + forward-backward with arc posteriors per step"),
 }
+PERSIST_NAMES = {"vit": "k_vit_persist", "fwd": "k_fwd_persist", "bwd": "k_bwd_persist"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 # the files that decide what the step kernels read and write
 KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "store.cu", "plan.cu")
@@ -89,6 +90,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps from the host, not a CUDA graph")
+    ap.add_argument("--driver", default="graph", choices=["graph", "persistent", "persistent-all", "autotune"],
+                    help="graph: one launch per position, the step replayed as a CUDA graph; persistent: the "
+                         "forward-backward plan as persistent passes (one cooperative launch each), the Viterbi "
+                         "plan beside it on its own stream; persistent-all: both plans persistent, one after the "
+                         "other; autotune: each plan's driver and grid chosen by fst_plan_autotune")
     ap.add_argument("--ingest-traffic", nargs=2, metavar=("NCU_CSV", "BENCH_JSON"),
                     help="write profiles/traffic.json from an ncu launch list of a small run and that run's line")
     return ap.parse_args(argv)
@@ -220,8 +226,9 @@ def load_traffic():
     return d
 
 
-def roofline(prof, live, peak, peak_src, traffic, stats=None, ids=None):
-    """Roofline of the dominant pass (the pass with the most kernel time)."""
+def roofline(prof, live, peak, peak_src, traffic, stats=None, ids=None, persistent=()):
+    """Roofline of the dominant pass (the pass with the most kernel time).
+    ``persistent``: the passes that ran as one persistent kernel each."""
     pass_ms = {k: sum(prof[x][0] for x in ks) for k, ks in PASS_KERNELS.items()}
     pass_ms = {k: v for k, v in pass_ms.items() if v > 0}
     dom = max(pass_ms, key=pass_ms.get)
@@ -234,7 +241,8 @@ def roofline(prof, live, peak, peak_src, traffic, stats=None, ids=None):
     r = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
          "frac": round(achieved / peak, 5), "traffic": None if tr is None else int(tr),
          "per": f"{dom} pass (all its launches)",
-         "kernel": " + ".join(KERNEL_NAMES[x] for x in PASS_KERNELS[dom]),
+         "kernel": (PERSIST_NAMES[dom] if dom in persistent
+                    else " + ".join(KERNEL_NAMES[x] for x in PASS_KERNELS[dom])),
          "launches": sum(prof[x][1] for x in PASS_KERNELS[dom]), "pass_ms": round(pass_ms[dom], 3),
          "algorithmic_bytes": int(alg[dom]),
          "bytes_model": "live work: Viterbi 12P+12E, forward 12P+8E, backward 20P+12E (P arcs out of live states, "
@@ -381,7 +389,7 @@ def ingest_traffic(csv_path, line_path):
     alg = live_bytes(live["entries"], live["arcs"])
     passes = {}
     for p, ks in PASS_KERNELS.items():
-        tot = sum(by_kernel.get(KERNEL_NAMES[k], 0.0) for k in ks)
+        tot = sum(by_kernel.get(KERNEL_NAMES[k], 0.0) for k in ks) + by_kernel.get(PERSIST_NAMES[p], 0.0)
         if tot > 0:
             passes[p] = {"dram_bytes": int(tot), "algorithmic_bytes": int(alg[p]),
                          "dram_per_algorithmic_byte": tot / alg[p]}
@@ -461,12 +469,26 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     budget = int(args.budget_gb * (1 << 30))
     plan_v = f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB)
     plan_f = f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI)
+    from paper_1701_03038_gb300 import _lib
+    tuned = {}
+    if args.driver in ("persistent", "persistent-all"):
+        plan_f.set_driver(_lib.DRIVER_PERSISTENT)
+    if args.driver == "persistent-all":
+        plan_v.set_driver(_lib.DRIVER_PERSISTENT)
+    if args.driver == "autotune":
+        tuned = {"viterbi": plan_v.autotune(), "forward_backward": plan_f.autotune()}
     info_v, info_f = plan_v.info(), plan_f.info()
     relax_pass = info_v["relaxations"]
     s_v, s_f = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    # two persistent (cooperative) passes never run at the same time
+    serial = plan_v.driver()[0] == _lib.DRIVER_PERSISTENT and plan_f.driver()[0] == _lib.DRIVER_PERSISTENT
 
     def step():
         main = torch.cuda.current_stream()
+        if serial:
+            plan_v.viterbi(stream=main)
+            plan_f.forward_backward(stream=main)
+            return
         fork = torch.cuda.Event()
         fork.record(main)
         s_v.wait_event(fork)
@@ -487,9 +509,14 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
         s_c = torch.cuda.Stream(device=dev)
         s_c.wait_stream(torch.cuda.current_stream())
         graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=s_c):
-            step()
-        torch.cuda.synchronize()
+        try:
+            with torch.cuda.graph(graph, stream=s_c):
+                step()
+            torch.cuda.synchronize()
+        except RuntimeError as e:  # a launch kind that cannot be captured: host launches
+            print(f"graph capture failed ({e}); timing host launches", file=sys.stderr)
+            graph = None
+            torch.cuda.synchronize()
     run_step = graph.replay if graph is not None else step
     ms, clk = timed(run_step, args, world, dev, ClockSampler(int(str(dev).split(":")[-1])))
     launches = info_v["viterbi_launches"] + info_f["fb_launches"]
@@ -509,7 +536,8 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     plan_f.profile(False)
     live = plan_f.live_work()
     peak, peak_src = load_peak()
-    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(), stats, strs.ids)
+    persistent = (("vit",) if plan_v.driver()[0] else ()) + (("fwd", "bwd") if plan_f.driver()[0] else ())
+    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(), stats, strs.ids, persistent)
     performed = 3 * max(live["arcs"], 0)
     out["config"].update({
         "relaxations_per_pass": relax_pass, "waves": max(info_v["waves"], info_f["waves"]),
@@ -518,6 +546,10 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
         "streams": "a Viterbi plan and a forward-backward plan on two CUDA streams; per-kernel times from one "
                    "more step run serially",
         "launch": "CUDA graph replay" if graph is not None else "host launches",
+        "driver": {"viterbi": "persistent" if plan_v.driver()[0] else "one launch per position",
+                   "forward_backward": "persistent" if plan_f.driver()[0] else "one launch per position",
+                   "grid": {"viterbi": plan_v.driver()[1], "forward_backward": plan_f.driver()[1]},
+                   "concurrent": not serial, "autotune": tuned or None},
         "l2": "no flush: inputs larger than L2 (arc store and hash "
               f"{(fa.num_arcs * 24) / 2**30:.2f} GiB, plan storage "
               f"{(info_v['device_bytes'] + info_f['device_bytes']) / 2**30:.1f} GiB)"})

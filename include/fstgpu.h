@@ -299,6 +299,59 @@ FST_API int fst_live_work(fst_t* fst, int64_t* entries, int64_t* arcs);
  * the plan's work on `stream`.  Either output may be NULL. */
 FST_API int fst_plan_live_work(fst_plan_t* plan, int64_t* entries, int64_t* arcs, void* stream);
 
+/* How a plan advances its positions (the batched driver).
+ *   FST_DRIVER_LAUNCH      one kernel launch per position and kernel kind
+ *                          (the default; a run can be captured into a CUDA
+ *                          graph and replayed).
+ *   FST_DRIVER_PERSISTENT  one cooperative launch per pass (Viterbi, forward,
+ *                          backward) of grid_blocks blocks (0 = the plan's
+ *                          estimate), all co-resident, that runs every
+ *                          position; positions are separated by a grid-wide
+ *                          barrier in device memory instead of kernel
+ *                          boundaries.  Each wait of that barrier gives up
+ *                          after barrier_timeout_us (0 = keep the current
+ *                          limit, 2 s by default); the run then ends early
+ *                          and reports FST_ERR_TIMEOUT in the status of every
+ *                          string of its wave, and the next run starts clean.
+ * Results are identical under both drivers.  FST_ERR_UNSUPPORTED when the
+ * device cannot launch cooperative kernels or grid_blocks cannot be
+ * co-resident.  Do not run a persistent plan concurrently with another
+ * persistent plan on the same device. */
+#define FST_DRIVER_LAUNCH 0
+#define FST_DRIVER_PERSISTENT 1
+FST_API int fst_plan_set_driver(fst_plan_t* plan, int32_t driver, int32_t grid_blocks, int64_t barrier_timeout_us);
+/* The plan's driver and, for the persistent one, the grid of its forward
+ * pass (host outputs, either may be NULL). */
+FST_API int fst_plan_get_driver(const fst_plan_t* plan, int32_t* driver, int32_t* grid_blocks);
+
+/* Autotuner of the batched driver: runs the plan's own passes (Viterbi and
+ * forward-backward with counts, those the plan has storage for) under each
+ * candidate configuration -- the launch driver with three grid densities
+ * (16, 64 or 256 live states assumed per token) and the persistent driver at
+ * whole multiples of the SM count up to the co-resident limit -- keeps the
+ * fastest (the best of two timed runs after a warm-up, CUDA events on
+ * `stream`), and sets it on the plan.  Results are cached per device name,
+ * FST shape (states, arcs, symbols) and batch shape (strings, tokens,
+ * longest string, waves, passes): a later plan with the same key takes the
+ * cached choice without timing (FST_TUNE_REFRESH times again).  When the
+ * environment variable FSTGPU_TUNE_CACHE names a file, the cache is read
+ * from and appended to it.  Allocates scratch outputs for the timing runs
+ * and synchronises `stream`; do not call it during graph capture.  Host
+ * outputs (any may be NULL): the chosen driver, its persistent grid (0 for
+ * the launch driver) and its time in milliseconds. */
+#define FST_TUNE_REFRESH 1
+FST_API int fst_plan_autotune(fst_plan_t* plan, void* stream, int32_t flags, int32_t* driver, int32_t* grid_blocks,
+                              double* best_ms);
+
+/* Fault injection for testing the failure paths (made on the host; nothing
+ * faults).  FST_FAULT_BARRIER_STALL: the grid barriers of the plan's
+ * persistent passes wait for `value` blocks (1..1024) beyond the grid, so
+ * that no wait can complete and every wait runs out (the FST_ERR_TIMEOUT
+ * path).  FST_FAULT_NONE (value ignored) turns injection off. */
+#define FST_FAULT_NONE 0
+#define FST_FAULT_BARRIER_STALL 1
+FST_API int fst_plan_fault_inject(fst_plan_t* plan, int32_t kind, int64_t value);
+
 /* Cap the live pool of the plan's following runs at `entries` live states
  * (over all positions of a wave; 0 = the capacity the plan allocated, which
  * larger values cannot exceed).  Allocates nothing.  A run whose live states

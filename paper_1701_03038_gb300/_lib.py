@@ -16,6 +16,9 @@ OK, INVALID_ARG, NO_PATH, OOM, CUDA, TIMEOUT, UNSUPPORTED, STATE = range(8)
 WEIGHT_LOG, WEIGHT_COST = 0, 1
 FLAG_DEVICE_PTRS = 1
 PLAN_SINGLE_WAVE, PLAN_NO_VITERBI, PLAN_NO_FB = 1, 2, 4
+DRIVER_LAUNCH, DRIVER_PERSISTENT = 0, 1
+FAULT_NONE, FAULT_BARRIER_STALL = 0, 1
+TUNE_REFRESH = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -47,6 +50,10 @@ SIGNATURES = {
     "fst_plan_live_work": [vp, vp, vp, vp],
     "fst_plan_forward_backward_ex": [vp, vp, vp, vp, vp, vp, vp, vp],
     "fst_plan_limit_pool": [vp, i64],
+    "fst_plan_set_driver": [vp, i32, i32, i64],
+    "fst_plan_get_driver": [vp, vp, vp],
+    "fst_plan_fault_inject": [vp, i32, i64],
+    "fst_plan_autotune": [vp, vp, i32, vp, vp, vp],
     "fst_profile": [vp, i32],
     "fst_profile_read": [vp, vp, vp],
     "fst_live_work": [vp, vp, vp],

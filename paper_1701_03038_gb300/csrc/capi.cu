@@ -140,7 +140,7 @@ struct DevBuf {
 // kept by the FST handle and grown on demand.
 struct PlainWs {
   unsigned long long* acc = nullptr;    // [2][Q] x 2 words (sum, maximum), zero between runs
-  float* beta = nullptr;                // [2][Q]
+  double* beta = nullptr;               // [2][Q] backward values
   int32_t* vmap = nullptr;              // [2][Q]
   int32_t *tok_sym = nullptr, *tok_b = nullptr;
   int32_t* iota = nullptr;              // step list: token t-1 is the only slot of position t
@@ -156,7 +156,7 @@ struct PlainWs {
   int32_t *stage = nullptr, *stage_b = nullptr;
   int64_t cap_stage = 0;
   int32_t *pool_q = nullptr, *pool_x = nullptr, *pool_n = nullptr;
-  float* pool_v = nullptr;
+  double* pool_v = nullptr;             // Viterbi scores (float32) or forward values (float64)
   int64_t cap_pool = 0;
   float *cnt = nullptr, *comp = nullptr, *counts_out = nullptr;
   int32_t *jfinal = nullptr, *status = nullptr, *bw_n = nullptr;
@@ -189,7 +189,7 @@ int plain_init(fst_s* f) {
       (rc = dalloc(&w->pool_top, 1)) || (rc = dalloc(&w->flags, 2)))
     return rc;
   FST_CUDA(cudaMemset(w->acc, 0, (size_t)4 * Q * sizeof(unsigned long long)));
-  FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(float)));
+  FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(double)));
   FST_CUDA(cudaMemset(w->bw_off, 0, sizeof(int64_t)));
   FST_CUDA(cudaMemset(w->flags, 0, 2 * sizeof(uint32_t)));
   return FST_OK;
@@ -286,7 +286,8 @@ FrontierState plain_state(fst_s* f) {
   S.pool_q = w->pool_q;
   S.pool_x = w->pool_x;
   S.pool_n = w->pool_n;
-  S.pool_v = w->pool_v;
+  S.pool_v = (float*)w->pool_v;
+  S.pool_d = w->pool_v;
   S.pool_base = w->pool_base;
   S.pool_cnt = w->pool_cnt;
   S.slot_base = w->slot_base;

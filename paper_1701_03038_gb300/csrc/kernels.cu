@@ -45,6 +45,14 @@ namespace {
 constexpr int KT = 256;  // threads per block of the step kernels
 constexpr int FT = 256;  // threads per block of the final reductions
 
+// Error bits of a run (FrontierState::flags[1]): the live pool overflowed,
+// or a grid barrier of a persistent pass gave up waiting.
+constexpr uint32_t ERR_POOL = 1u;
+constexpr uint32_t ERR_TIMEOUT = 2u;
+__device__ __forceinline__ int32_t run_error(uint32_t err) {
+  return (err & ERR_TIMEOUT) ? FST_ERR_TIMEOUT : FST_ERR_OOM;
+}
+
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
 __device__ __forceinline__ int32_t warp_id_global() { return (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
@@ -219,7 +227,7 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
   }
   if (threadIdx.x == 0) {
     const long long end = carry < first_bad ? carry : first_bad;
-    if (first_bad != (long long)INT64_MAX) atomicOr(S.flags + 1, 1u);
+    if (first_bad != (long long)INT64_MAX) atomicOr(S.flags + 1, ERR_POOL);
     rng_out[0] = begin;
     rng_out[1] = end;
     if (top) *top = end;
@@ -320,15 +328,33 @@ __device__ __forceinline__ void block_visit(BlockScratch<Ctx>& sh, int32_t e0, i
   __syncthreads();
 }
 
+// exp(v - m), v <= m, as a 2^-40 fixed-point integer: sums of these are exact
+// and so independent of the order in which they are added.  A sum of fewer
+// than 2^24 terms cannot overflow (the store refuses longer segments).  The
+// value and the reference are float64: the forward and backward values
+// carried from position to position are float64 (a float32 value rounds by
+// up to 2^-24 of its size at every position, and over a 200-position string
+// those roundings shift alpha + beta - log Z by ~1e-5, the whole posterior
+// tolerance), and so is the term, whose relative error would otherwise add
+// to the same drift.  v - m may exceed 0 by the rounding of m (a float32
+// order key): the term then exceeds 2^40 by that much.
+__device__ __forceinline__ unsigned long long fix_exp64(double v, double m) {
+  return v == -INFINITY ? 0ull : __double2ull_rn(exp(v - m) * 1099511627776.0);  // 2^40
+}
+// m + log(s / 2^40), in float64.
+__device__ __forceinline__ double fix_log_sum64(double m, unsigned long long s) {
+  return (m == -INFINITY || s == 0ull) ? -INFINITY : m + log((double)s * 0x1p-40);
+}
+// Order key of a float64 value rounded to float32 (0 = -inf, nothing).
+__device__ __forceinline__ uint32_t fkey64(double v) { return v == -INFINITY ? 0u : fkey((float)v); }
+
 // Reductions over each thread's segment: Op maps a value to a 64-bit key,
 // combines keys atomically and maps the result back.
-struct RedMax {  // max of floats through their order-preserving keys (0 = nothing)
-  typedef float T;
-  static __device__ __forceinline__ unsigned long long key(T v) {
-    return v == __int_as_float(0xff800000) ? 0ull : (unsigned long long)fkey(v);
-  }
+struct RedMaxD {  // max of float64 values through the order keys of their float32 roundings
+  typedef double T;
+  static __device__ __forceinline__ unsigned long long key(T v) { return (unsigned long long)fkey64(v); }
   static __device__ __forceinline__ T value(unsigned long long k) {
-    return k ? fkey_inv((uint32_t)k) : __int_as_float(0xff800000);
+    return k ? (double)fkey_inv((uint32_t)k) : -INFINITY;
   }
   static __device__ __forceinline__ void atomic(unsigned long long* a, unsigned long long k) { if (k) atomicMax(a, k); }
 };
@@ -352,19 +378,6 @@ __device__ __forceinline__ typename Op::T block_reduce(BlockScratch<Ctx>& sh, in
   return r;
 }
 
-// exp(v - m), v <= m, as a 2^-40 fixed-point integer: sums of these are exact
-// and so independent of the order in which they are added.  A sum of fewer
-// than 2^24 terms cannot overflow (the store refuses longer segments).
-__device__ __forceinline__ unsigned long long fix_exp(float v, float m) {
-  return v == __int_as_float(0xff800000) ? 0ull : __float2ull_rn(__expf(v - m) * 0x1p40f);
-}
-// m + log(s / 2^40), the logarithm in float64: a float32 logarithm here
-// adds up to an ulp per position, which over a 200-symbol string moved
-// expected counts by 1e-5 relative.
-__device__ __forceinline__ float fix_log_sum(float m, unsigned long long s) {
-  return (m == __int_as_float(0xff800000) || s == 0ull) ? __int_as_float(0xff800000)
-                                                        : m + (float)log((double)s * 0x1p-40);
-}
 
 // Atomic max of key into a[p] for the lanes that hold one (p >= 0), with one
 // atomic per run of equal p: the lanes of a warp hold consecutive flat
@@ -403,7 +416,7 @@ __device__ __forceinline__ uint32_t warp_stage_index(uint32_t* cnt, int32_t p, b
 struct PushCtx {
   int32_t p;  // token of the destination position
   int32_t b;  // wave-local string
-  float r;    // value of the source
+  double r;   // value of the source (Viterbi: a float32 score, held exactly)
 };
 
 // Arc e out of a live source, into position t: the atomic max on the
@@ -417,7 +430,9 @@ __device__ __forceinline__ void push_arc(const LayoutView& L, const TokenView& T
   if (valid) {
     const int4 a = __ldg(L.arcs + e);
     d = a.x;
-    const float u = __fadd_rn(c.r, __int_as_float(a.y));
+    // Viterbi: one rounded float32 addition; forward: the float32 rounding
+    // of the float64 value, an order key for the maximum only
+    const float u = VIT ? __fadd_rn((float)c.r, __int_as_float(a.y)) : (float)(c.r + (double)__int_as_float(a.y));
     if (u != neg_inf()) {
       const int64_t slot = acc_slot(S, c.b, t, d);
       if (VIT) {
@@ -438,23 +453,23 @@ __device__ __forceinline__ void push_arc(const LayoutView& L, const TokenView& T
 struct Source {
   int32_t p;   // token at position t, -1 when the entry's string ends at t-1
   int32_t q;   // state
-  float r;     // value at t-1 (the start weight at t = 1)
+  double r;    // value at t-1 (the start weight at t = 1)
   bool head;   // first entry of its token (writes the token's scalars)
 };
 __device__ __forceinline__ Source source_at(const TokenView& T, const StepView& V, const FrontierState& S,
                                             const Owner& o, int64_t j) {
-  Source x{-1, 0, 0.f, false};
+  Source x{-1, 0, 0.0, false};
   if (V.t == 1) {
     x.p = __ldg(T.step_tok + V.slot0 + (int32_t)(j / S.nstart));
     x.q = __ldg(S.start_q + (int32_t)(j % S.nstart));
-    x.r = __ldg(S.theta_s + x.q);
+    x.r = (double)__ldg(S.theta_s + x.q);
     x.head = j % S.nstart == 0;
   } else {
     const int32_t pp = __ldg(T.step_tok + V.x_slot0 + o.k);
     if (S.bw_n[__ldg(T.b + pp)] >= V.t) {
       x.p = pp + 1;
       x.q = S.pool_q[j];
-      x.r = S.pool_v[j];
+      x.r = S.pool_d[j];
       x.head = o.first == j;
     }
   }
@@ -485,7 +500,7 @@ __device__ __forceinline__ void first_position(const LayoutView& L, const TokenV
   for (int64_t cb = (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
     const int64_t j = cb + threadIdx.x;
     int32_t e0 = 0, len = 0;
-    PushCtx me{0, 0, 0.f};
+    PushCtx me{0, 0, 0.0};
     if (j < R1) {
       const Source x = source_at(T, V, S, Owner{0, 0}, j);
       const Arcs r = find_arcs(L, __ldg(T.sym + x.p), x.q);
@@ -540,7 +555,7 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
     const int64_t j = c0 + lane;
     const Owner o = flat_owner(S.slot_base + V.slot0, V.n, c0, clamp_entry(j, c0, R1));
     int32_t e0 = 0, len = 0;
-    PushCtx nx{0, 0, 0.f};
+    PushCtx nx{0, 0, 0.0};
     int32_t mk_p = -1;  // forward: the token and order key of this lane's value
     uint32_t mk_key = 0u;
     if (j < R1) {
@@ -548,10 +563,12 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
       const int32_t b = __ldg(T.b + x.p);
       const int32_t d = stg[__ldg(T.stf + x.p) + x.i];
       const int64_t slot = acc_slot(S, b, t, d);
-      float r;
+      double r;
       if (VIT) {
         const unsigned long long key = *vit_key(S, slot);
-        r = fkey_inv((uint32_t)(key >> 32));
+        const float rv = fkey_inv((uint32_t)(key >> 32));
+        r = rv;
+        S.pool_v[j] = rv;
         const int32_t id = (int32_t)(~(uint32_t)key);  // the best incoming arc
         S.pool_x[j] = id;
         // the predecessor entry: the source's entry at t-1, which the step
@@ -561,12 +578,12 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
       } else {
         const ulonglong2 a = *(const ulonglong2*)fwd_sum(S, slot);
         const float sh_prev = t > 1 ? decode_max(S.mkey[x.p - 1]) : 0.f;
-        r = fix_log_sum(fkey_inv((uint32_t)a.y) - sh_prev, a.x);
+        r = fix_log_sum64((double)fkey_inv((uint32_t)a.y) - (double)sh_prev, a.x);
+        S.pool_d[j] = r;
         mk_p = x.p;
-        mk_key = fkey(r);
+        mk_key = fkey64(r);
       }
       S.pool_q[j] = d;
-      S.pool_v[j] = r;
       // the accumulator is zeroed only once its value has been used: a store
       // issued right behind the load of the same word measured 25% slower
       asm volatile("" ::: "memory");
@@ -613,8 +630,8 @@ __global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, Step
 
 // Forward sum of position t: with every maximum M_d final, each live arc
 // adds exp(r_{t-1}[src] + theta - M_d) to its destination in fixed point.
-__global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepView V, FrontierState S) {
-  __shared__ BlockScratch<PushCtx> sh;
+__device__ __forceinline__ void sum_position(const LayoutView& L, const TokenView& T, const StepView& V,
+                                             const FrontierState& S, BlockScratch<PushCtx>& sh) {
   const int lane = threadIdx.x & 31;
   const int32_t t = V.t;
   int64_t R0, R1;
@@ -625,7 +642,7 @@ __global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepV
     Owner o{0, 0};
     if (t > 1) o = flat_owner(S.slot_base + V.x_slot0, V.x_n, c0, clamp_entry(j, c0, R1));  // t is uniform
     int32_t e0 = 0, len = 0;
-    PushCtx me{0, 0, 0.f};
+    PushCtx me{0, 0, 0.0};
     if (j < R1) {
       const Source x = source_at(T, V, S, o, j);
       if (x.p >= 0) {
@@ -638,12 +655,17 @@ __global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepV
     block_visit(sh, e0, len, me, [&](int32_t e, const PushCtx& c, bool ok) {
       if (!ok) return;
       const int4 a = __ldg(L.arcs + e);
-      const float u = __fadd_rn(c.r, __int_as_float(a.y));
-      if (u == neg_inf()) return;
+      const double v = c.r + (double)__int_as_float(a.y);
+      if (v == -INFINITY) return;
       const int64_t slot = acc_slot(S, c.b, t, a.x);
-      atomicAdd(fwd_sum(S, slot), fix_exp(u, fkey_inv(*fwd_max(S, slot))));
+      atomicAdd(fwd_sum(S, slot), fix_exp64(v, (double)fkey_inv(*fwd_max(S, slot))));
     });
   }
+}
+
+__global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepView V, FrontierState S) {
+  __shared__ BlockScratch<PushCtx> sh;
+  sum_position(L, T, V, S, sh);
 }
 
 // ======================================================================
@@ -674,15 +696,14 @@ __device__ __forceinline__ void add_count(const CountView& C, int32_t id, float 
 struct BwdCtx {
   int32_t b, n;
   float et;     // e_t (0 at the string's last position)
-  float ra;     // r_{t-1}[q]
   float gw;     // the string's gradient weight
-  float m;      // the segment's maximum (second pass)
+  double ra;    // r_{t-1}[q]
+  double m;     // the segment's maximum (second pass)
   double K;     // C_{t-1} + E_t - log Z - m_{t-1}
 };
 
-__global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, StepView V, FrontierState S,
-                                                 CountView C) {
-  __shared__ BlockScratch<BwdCtx> sh;
+__device__ __forceinline__ void bwd_position(const LayoutView& L, const TokenView& T, const StepView& V,
+                                             const FrontierState& S, const CountView& C, BlockScratch<BwdCtx>& sh) {
   const int lane = threadIdx.x & 31;
   const int32_t t = V.t;
   int64_t R0, R1;
@@ -693,7 +714,7 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Step
     Owner o{0, 0};
     if (t > 1) o = flat_owner(S.slot_base + V.x_slot0, V.x_n, c0, clamp_entry(j, c0, R1));  // t is uniform
     int32_t e0 = 0, len = 0, q = -1, p = -1;
-    BwdCtx me{0, 0, 0.f, 0.f, 0.f, 0.f, 0.0};
+    BwdCtx me{0, 0, 0.f, 0.f, 0.0, 0.0, 0.0};
     if (j < R1) {
       const Source x = source_at(T, V, S, o, j);
       const int32_t b = x.p >= 0 ? __ldg(T.b + x.p) : 0;
@@ -711,50 +732,157 @@ __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, Step
           e0 = r.pos;
           len = r.len;
         }
-        me = BwdCtx{b, n, et, x.r, S.gweight ? S.gweight[b] : 1.f, 0.f,
+        me = BwdCtx{b, n, et, S.gweight ? S.gweight[b] : 1.f, x.r, 0.0,
                     (((t == 1) ? 0.0 : S.csum[p - 1]) + tE - lz) - (double)mprev};
       }
     }
     // theta_e + beta_t[q'] - e_t; the final weight stands in for beta at the
     // string's last position
-    auto ub_of = [&](int32_t d, const BwdCtx& c) {
-      return (t == c.n) ? __ldg(S.theta_f + d) : S.beta[acc_slot(S, c.b, t, d)];
+    auto ub_of = [&](int32_t d, const BwdCtx& c) -> double {
+      return (t == c.n) ? (double)__ldg(S.theta_f + d) : S.beta[acc_slot(S, c.b, t, d)];
     };
-    auto value = [&](int32_t e, const BwdCtx& c) {
+    auto value = [&](int32_t e, const BwdCtx& c) -> double {
       const int4 a = __ldg(L.arcs + e);
       const float th = __int_as_float(a.y);
-      const float ub = ub_of(a.x, c);
-      return (th == neg_inf() || ub == neg_inf()) ? neg_inf() : th + (ub - c.et);
+      const double ub = ub_of(a.x, c);
+      return (th == neg_inf() || ub == -INFINITY) ? -INFINITY : (double)th + (ub - (double)c.et);
     };
-    me.m = block_reduce<RedMax>(sh, e0, len, me, value);
+    me.m = block_reduce<RedMaxD>(sh, e0, len, me, value);
     const unsigned long long su =
-        block_reduce<RedSum>(sh, e0, me.m == neg_inf() ? 0 : len, me, [&](int32_t e, const BwdCtx& c) {
+        block_reduce<RedSum>(sh, e0, me.m == -INFINITY ? 0 : len, me, [&](int32_t e, const BwdCtx& c) {
           const int4 a = __ldg(L.arcs + e);
           const float th = __int_as_float(a.y);
-          const float ub = ub_of(a.x, c);
-          if (th == neg_inf() || ub == neg_inf()) return 0ull;
+          const double ub = ub_of(a.x, c);
+          if (th == neg_inf() || ub == -INFINITY) return 0ull;
+          const double v = (double)th + (ub - (double)c.et);
           // the exponent adds terms of either sign and tens in size that
           // cancel to a small number: formed in float64
-          const double ex = (double)c.ra + (double)th + ((double)ub - (double)c.et) + c.K;
+          const double ex = c.ra + v + c.K;
           add_count(C, a.z, __expf((float)ex) * c.gw);
-          return fix_exp(th + (ub - c.et), c.m);
+          return fix_exp64(v, c.m);
         });
     int32_t ek_p = -1;
     uint32_t ek_key = 0u;
     if (q >= 0 && t > 1) {
-      const float u = fix_log_sum(me.m, su);
+      const double u = fix_log_sum64(me.m, su);
       S.beta[acc_slot(S, me.b, t - 1, q)] = u;
-      if (u != neg_inf()) {
+      if (u != -INFINITY) {
         ek_p = p - 1;
-        ek_key = fkey(u);
+        ek_key = fkey64(u);
       }
     } else if (q >= 0 && C.start64) {
       // t = 1: the item is a start state q, log beta_0[q] = u + E_1 and its
       // start posterior is exp(theta_s[q] + log beta_0[q] - log Z)
-      const float u = fix_log_sum(me.m, su);
-      if (u != neg_inf()) atomicAdd(C.start64 + q, exp((double)me.ra + (double)u + me.K) * (double)me.gw);
+      const double u = fix_log_sum64(me.m, su);
+      if (u != -INFINITY) atomicAdd(C.start64 + q, exp(me.ra + u + me.K) * (double)me.gw);
     }
     warp_max_by_token(S.ekey, ek_p, ek_key);  // the step maximum e_{t-1}
+  }
+}
+
+__global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, StepView V, FrontierState S,
+                                                 CountView C) {
+  __shared__ BlockScratch<BwdCtx> sh;
+  bwd_position(L, T, V, S, C, sh);
+}
+
+// ======================================================================
+// Persistent passes: one cooperative launch runs every position of a pass,
+// the positions separated by a grid-wide barrier instead of kernel
+// boundaries.  The step view of position t is rebuilt on the device from the
+// wave's step offsets.  Every wait of the barrier is bounded: past the limit
+// it raises ERR_TIMEOUT, every block leaves at its next barrier, and the
+// final kernels report FST_ERR_TIMEOUT for each string of the wave.
+// ======================================================================
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// All blocks of the grid (G.expected of them) meet; returns false when the
+// run was abandoned (this block's wait expired, or another block's did).
+// The fences follow the usual grid-synchronisation pattern: writes before
+// the barrier are visible to every block after it.
+__device__ __forceinline__ bool grid_sync(const GridSync& G, uint32_t* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* gen = G.bar + 1;
+    const uint32_t g0 = *gen;
+    int good = 1;
+    __threadfence();
+    const uint32_t arrived = atomicAdd(G.bar, 1u) + 1u;
+    if (arrived == G.expected) {
+      atomicExch(G.bar, 0u);
+      __threadfence();
+      atomicAdd(G.bar + 1, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      while (*gen == g0) {
+        if (*(volatile uint32_t*)err & ERR_TIMEOUT) { good = 0; break; }
+        if (global_ns() - t0 > G.limit_ns) {
+          atomicOr(err, ERR_TIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ StepView step_at(const WaveSteps& D, int32_t t, int32_t x_t) {
+  StepView V;
+  V.t = t;
+  V.slot0 = D.step0[t];
+  V.n = D.step0[t + 1] - V.slot0;
+  const bool hasx = x_t >= 1 && x_t <= D.tmax;
+  V.x_t = hasx ? x_t : 0;
+  V.x_slot0 = hasx ? D.step0[x_t] : 0;
+  V.x_n = hasx ? D.step0[x_t + 1] - V.x_slot0 : 0;
+  V.blocks = (int32_t)gridDim.x;
+  return V;
+}
+
+__global__ void __launch_bounds__(KT) k_vit_persist(LayoutView L, TokenView T, WaveSteps D, FrontierState S,
+                                                    GridSync G) {
+  __shared__ BlockScratch<PushCtx> sh;
+  if (D.tmax < 1) return;
+  first_position<true>(L, T, step_at(D, 1, 0), S, sh);
+  if (!grid_sync(G, S.flags + 1)) return;
+  for (int32_t t = 1; t <= D.tmax; ++t) {
+    step_position<true>(L, T, step_at(D, t, t + 1), S, sh);
+    if (!grid_sync(G, S.flags + 1)) return;
+  }
+}
+
+__global__ void __launch_bounds__(KT) k_fwd_persist(LayoutView L, TokenView T, WaveSteps D, FrontierState S,
+                                                    GridSync G) {
+  __shared__ BlockScratch<PushCtx> sh;
+  if (D.tmax < 1) return;
+  first_position<false>(L, T, step_at(D, 1, 0), S, sh);
+  if (!grid_sync(G, S.flags + 1)) return;
+  for (int32_t t = 1; t <= D.tmax; ++t) {
+    sum_position(L, T, step_at(D, t, t - 1), S, sh);
+    if (!grid_sync(G, S.flags + 1)) return;
+    step_position<false>(L, T, step_at(D, t, t + 1), S, sh);
+    if (!grid_sync(G, S.flags + 1)) return;
+  }
+}
+
+__global__ void __launch_bounds__(KT) k_bwd_persist(LayoutView L, TokenView T, WaveSteps D, FrontierState S,
+                                                    CountView C, GridSync G) {
+  __shared__ BlockScratch<BwdCtx> sh;
+  // a forward pass that gave up leaves nothing to walk back over
+  if (*(volatile uint32_t*)(S.flags + 1) & ERR_TIMEOUT) return;
+  for (int32_t t = D.tmax; t >= 1; --t) {
+    bwd_position(L, T, step_at(D, t, t - 1), S, C, sh);
+    if (!grid_sync(G, S.flags + 1)) return;
   }
 }
 
@@ -796,11 +924,12 @@ __global__ void __launch_bounds__(FT) k_vit_final(FrontierState S, float* __rest
   __syncthreads();
   best = red[0];
   for (int w = 1; w < FT / 32; ++w) best = red[w] > best ? red[w] : best;
-  const bool oom = (S.flags[1] & 1u) != 0u;
+  const uint32_t err = S.flags[1] & (ERR_POOL | ERR_TIMEOUT);
+  const bool oom = err != 0u;
   const int32_t qbest = best ? (int32_t)(~(uint32_t)best) : -1;
   if (threadIdx.x == 0) {
     scores[b] = (best && !oom) ? fkey_inv((uint32_t)(best >> 32)) : neg_inf();
-    if (status) status[b] = oom ? FST_ERR_OOM : (best ? FST_OK : FST_ERR_NO_PATH);
+    if (status) status[b] = err ? run_error(err) : (best ? FST_OK : FST_ERR_NO_PATH);
     if (!best || oom || n == 0) jfinal[b] = -1;
   }
   // the entry holding the best state (each state appears once per token)
@@ -837,7 +966,7 @@ __global__ void k_backtrace(FrontierState S, const int32_t* __restrict__ olabel_
 // Warp 0 first writes the running normalisers C_t (a warp scan, float64).
 __global__ void __launch_bounds__(FT) k_fb_final(FrontierState S, double* __restrict__ logz,
                                                  int32_t* __restrict__ status) {
-  __shared__ float red_m[FT / 32];
+  __shared__ double red_m[FT / 32];
   __shared__ unsigned long long red_lo[FT], red_hi[FT];
   __shared__ double c_prev;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -870,28 +999,28 @@ __global__ void __launch_bounds__(FT) k_fb_final(FrontierState S, double* __rest
   const int64_t p = off + n - 1;
   const int32_t* cand = n == 0 ? S.start_q : S.pool_q + S.pool_base[p];
   const int32_t ncand = n == 0 ? S.nstart : S.pool_cnt[p];
-  auto value = [&](int32_t i) -> float {
+  auto value = [&](int32_t i) -> double {
     const int32_t q = cand[i];
-    if (q < 0) return neg_inf();
-    const float a = n == 0 ? __ldg(S.theta_s + q) : S.pool_v[S.pool_base[p] + i];
-    return __fadd_rn(a, __ldg(S.theta_f + q));
+    if (q < 0) return -INFINITY;
+    const double a = n == 0 ? (double)__ldg(S.theta_s + q) : S.pool_d[S.pool_base[p] + i];
+    return a + (double)__ldg(S.theta_f + q);
   };
   // the candidates sit in the pool in scheduling order: the sum is made
   // order-independent (bitwise repeatable) by adding exp(v - max) as
   // integers, in units of 2^-62
-  float mx = neg_inf();
-  for (int32_t i = threadIdx.x; i < ncand; i += FT) mx = fmaxf(mx, value(i));
+  double mx = -INFINITY;
+  for (int32_t i = threadIdx.x; i < ncand; i += FT) mx = fmax(mx, value(i));
 #pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, d));
+  for (int d = 16; d >= 1; d >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, d));
   if (lane == 0) red_m[warp] = mx;
   __syncthreads();
-  for (int w = 0; w < FT / 32; ++w) mx = fmaxf(mx, red_m[w]);
+  for (int w = 0; w < FT / 32; ++w) mx = fmax(mx, red_m[w]);
   unsigned long long lo = 0ull, hi = 0ull;  // 128-bit accumulator
-  if (mx != neg_inf()) {
+  if (mx != -INFINITY) {
     for (int32_t i = threadIdx.x; i < ncand; i += FT) {
-      const float v = value(i);
-      if (v == neg_inf()) continue;
-      const unsigned long long u = __double2ull_rn((double)__expf(v - mx) * 4611686018427387904.0);  // 2^62
+      const double v = value(i);
+      if (v == -INFINITY) continue;
+      const unsigned long long u = __double2ull_rn(exp(v - mx) * 4611686018427387904.0);  // 2^62
       lo += u;
       hi += (lo < u) ? 1ull : 0ull;
     }
@@ -905,12 +1034,12 @@ __global__ void __launch_bounds__(FT) k_fb_final(FrontierState S, double* __rest
       hi += red_hi[i] + ((lo < red_lo[i]) ? 1ull : 0ull);
     }
     const double sum = ((double)hi * 18446744073709551616.0 + (double)lo) * 2.168404344971009e-19;  // 2^64, 2^-62
-    const bool oom = (S.flags[1] & 1u) != 0u;
+    const uint32_t err = S.flags[1] & (ERR_POOL | ERR_TIMEOUT);
     const double cp = c_prev;
     double lz = -INFINITY;
-    if (!oom && mx != neg_inf() && cp != -INFINITY) lz = cp + (double)mx + log(sum);
+    if (!err && mx != -INFINITY && cp != -INFINITY) lz = cp + mx + log(sum);
     logz[b] = lz;
-    if (status) status[b] = oom ? FST_ERR_OOM : ((lz == -INFINITY) ? FST_ERR_NO_PATH : FST_OK);
+    if (status) status[b] = err ? run_error(err) : ((lz == -INFINITY) ? FST_ERR_NO_PATH : FST_OK);
   }
 }
 
@@ -926,9 +1055,9 @@ __global__ void __launch_bounds__(FT) k_final_post(FrontierState S, CountView C)
   if (n == 0) {
     for (int32_t i = threadIdx.x; i < S.nstart; i += FT) {
       const int32_t q = S.start_q[i];
-      const float v = __fadd_rn(__ldg(S.theta_s + q), __ldg(S.theta_f + q));
-      if (v == neg_inf()) continue;
-      const double post = exp((double)v - lz) * g;
+      const double v = (double)__ldg(S.theta_s + q) + (double)__ldg(S.theta_f + q);
+      if (v == -INFINITY) continue;
+      const double post = exp(v - lz) * g;
       if (C.final64) atomicAdd(C.final64 + q, post);
       if (C.start64) atomicAdd(C.start64 + q, post);
     }
@@ -943,7 +1072,7 @@ __global__ void __launch_bounds__(FT) k_final_post(FrontierState S, CountView C)
     const int32_t q = S.pool_q[base + i];
     const float tf = __ldg(S.theta_f + q);
     if (tf == neg_inf()) continue;
-    atomicAdd(C.final64 + q, exp(((double)S.pool_v[base + i] + (double)tf) + cprev - lz) * g);
+    atomicAdd(C.final64 + q, exp((S.pool_d[base + i] + (double)tf) + cprev - lz) * g);
   }
 }
 
@@ -960,7 +1089,7 @@ __global__ void k_counts_out(int64_t A, CountView C, float* __restrict__ out) {
 
 __global__ void k_clear_if_overflow(const uint32_t* __restrict__ flag, unsigned long long* __restrict__ acc,
                                     int64_t n) {
-  if (!(*flag & 1u)) return;
+  if (!(*flag & (ERR_POOL | ERR_TIMEOUT))) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     acc[i] = 0ull;
 }
@@ -1027,6 +1156,64 @@ int launch_bwd_step(const LayoutView& L, const TokenView& T, const StepView& V, 
                     const CountView& C, cudaStream_t s) {
   k_bwd_step<<<step_grid(k_bwd_step, &g_grid[5], V), KT, 0, s>>>(L, T, V, S, C);
   return check_launch("k_bwd_step");
+}
+
+// Largest co-resident grid of a persistent kernel on this device.
+template <class K>
+int persist_capacity(K kernel, int* cache) {
+  if (*cache <= 0) {
+    int dev = 0, sms = 0, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, KT, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return 0;
+    }
+    *cache = sms * nb;
+  }
+  return *cache;
+}
+int g_persist_cap[3] = {0, 0, 0};
+
+template <class K, class... Args>
+int launch_persist(K kernel, int* cap_cache, int32_t grid, GridSync G, cudaStream_t s, const char* what,
+                   Args... args) {
+  const int cap = persist_capacity(kernel, cap_cache);
+  if (cap <= 0 || grid < 1 || grid > cap) {
+    set_error("%s: a grid of %d blocks cannot be co-resident (at most %d)", what, grid, cap);
+    return FST_ERR_UNSUPPORTED;
+  }
+  G.expected += (uint32_t)grid;
+  void* argv[sizeof...(Args) + 1];
+  int i = 0;
+  ((argv[i++] = (void*)&args), ...);
+  argv[i] = (void*)&G;
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)kernel, dim3((unsigned)grid), dim3(KT), argv, 0, s);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return FST_OK;
+}
+
+int persist_grid_limit(int which) {
+  switch (which) {
+    case 0: return persist_capacity(k_vit_persist, &g_persist_cap[0]);
+    case 1: return persist_capacity(k_fwd_persist, &g_persist_cap[1]);
+    default: return persist_capacity(k_bwd_persist, &g_persist_cap[2]);
+  }
+}
+
+int launch_vit_persist(const LayoutView& L, const TokenView& T, const WaveSteps& D, const FrontierState& S,
+                       int32_t grid, const GridSync& G, cudaStream_t s) {
+  return launch_persist(k_vit_persist, &g_persist_cap[0], grid, G, s, "k_vit_persist", L, T, D, S);
+}
+
+int launch_fwd_persist(const LayoutView& L, const TokenView& T, const WaveSteps& D, const FrontierState& S,
+                       int32_t grid, const GridSync& G, cudaStream_t s) {
+  return launch_persist(k_fwd_persist, &g_persist_cap[1], grid, G, s, "k_fwd_persist", L, T, D, S);
+}
+
+int launch_bwd_persist(const LayoutView& L, const TokenView& T, const WaveSteps& D, const FrontierState& S,
+                       const CountView& C, int32_t grid, const GridSync& G, cudaStream_t s) {
+  return launch_persist(k_bwd_persist, &g_persist_cap[2], grid, G, s, "k_bwd_persist", L, T, D, S, C);
 }
 
 int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t* jfinal, int32_t* status,

@@ -61,7 +61,7 @@ struct FrontierState {
   // order key in the low half}, so that both sit on one cache line
   unsigned long long* acc;
   int32_t acc_stride;
-  float* beta;                       // [Bw][2][Q] backward values (null for Viterbi-only state)
+  double* beta;                      // [Bw][2][Q] backward values, float64 (null for Viterbi-only state)
   int32_t* vmap;                     // [Bw][2][Q] Viterbi: pool entry of each live state (null for forward-only state)
   const int32_t* src_by_id;          // [A] source state of each arc
   int32_t* stage;                    // staged destinations of positions of even parity
@@ -71,7 +71,8 @@ struct FrontierState {
   int32_t* pool_x;                   // [cap] Viterbi: best incoming arc id; forward: first arc on the next symbol
   int32_t* pool_n;                   // [cap] Viterbi: pool entry of the best arc's source (-1 at the first
                                      // position); forward: arcs on the next symbol
-  float* pool_v;                     // [cap] Viterbi score, or forward value r_t
+  float* pool_v;                     // [cap] Viterbi score
+  double* pool_d;                    // [cap] forward value r_t, float64 (may share pool_v's storage)
   int64_t* pool_base;                // [N] by token
   int32_t* pool_cnt;                 // [N] by token
   int64_t* slot_base;                // [N] by step slot: first pool entry of the slot's token
@@ -91,6 +92,23 @@ struct FrontierState {
   const float* gweight;              // [Bw] or null
   const int32_t* bw_n;               // [Bw] string lengths
   const int64_t* bw_off;             // [Bw] first token of each string
+};
+
+// Step offsets of a wave on the device, for the persistent passes: the
+// tokens of position t are step slots step0[t] .. step0[t+1]-1.
+struct WaveSteps {
+  const int32_t* step0;  // [tmax + 2]
+  int32_t tmax;
+};
+
+// Grid barrier of a persistent pass: bar[0] counts arrivals, bar[1] is the
+// generation; a wait gives up after limit_ns.  `expected` is the number of
+// blocks that meet at each barrier beyond the grid (0 in normal use; a
+// fault-injection setting raises it so that the wait runs out).
+struct GridSync {
+  uint32_t* bar;
+  uint32_t expected;
+  uint64_t limit_ns;
 };
 
 // Expected counts by caller arc id.
@@ -127,6 +145,17 @@ int launch_fwd_sum(const LayoutView& L, const TokenView& T, const StepView& V, c
 // those arcs.
 int launch_bwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                     const CountView& C, cudaStream_t s);
+// Persistent passes (one cooperative launch of `grid` blocks runs every
+// position of the wave, separated by bounded grid barriers).  `grid` must be
+// co-resident: at most persist_grid_limit(0: Viterbi, 1: forward,
+// 2: backward); FST_ERR_UNSUPPORTED otherwise.  G.bar must be zero.
+int persist_grid_limit(int which);
+int launch_vit_persist(const LayoutView& L, const TokenView& T, const WaveSteps& D, const FrontierState& S,
+                       int32_t grid, const GridSync& G, cudaStream_t s);
+int launch_fwd_persist(const LayoutView& L, const TokenView& T, const WaveSteps& D, const FrontierState& S,
+                       int32_t grid, const GridSync& G, cudaStream_t s);
+int launch_bwd_persist(const LayoutView& L, const TokenView& T, const WaveSteps& D, const FrontierState& S,
+                       const CountView& C, int32_t grid, const GridSync& G, cudaStream_t s);
 // Best final state of each string; jfinal gets its pool entry (-1: no path).
 int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t* jfinal, int32_t* status,
                      cudaStream_t s);

@@ -13,8 +13,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "fst_internal.cuh"
@@ -59,8 +63,10 @@ struct Wave {
   int32_t* bw_n = nullptr;
   int64_t* bw_off = nullptr;
   std::vector<int32_t> step0;  // [tmax + 2]: tokens of position t are step_tok[step0[t] .. step0[t+1])
+  int32_t* d_step0 = nullptr;  // the same on the device (persistent passes)
+  int32_t grid_est = 1;        // blocks of the busiest position (about 64 live states per token)
   void release() {
-    dfree(tok_sym); dfree(tok_b); dfree(step_tok); dfree(stf); dfree(bw_n); dfree(bw_off);
+    dfree(tok_sym); dfree(tok_b); dfree(step_tok); dfree(stf); dfree(bw_n); dfree(bw_off); dfree(d_step0);
   }
 };
 
@@ -70,7 +76,7 @@ struct Wave {
 #define PLAN_STORAGE(X)                                                                                          \
   X(acc) X(beta) X(vmap) X(stage) X(stage_b) X(scnt) X(pool_q) X(pool_x) X(pool_n) X(pool_v) X(pool_base)          \
   X(pool_cnt) X(slot_base) X(step_rng) X(pool_top) X(flags_d) X(mkey) X(ekey) X(csum) X(esum) X(jfinal) X(logz) \
-  X(cnt64) X(start64) X(final64)
+  X(cnt64) X(start64) X(final64) X(gbar)
 
 struct fst_plan_s {
   fst_t* fst = nullptr;
@@ -81,12 +87,12 @@ struct fst_plan_s {
   // shared per-wave buffers (sized for the largest wave)
   unsigned long long* acc = nullptr;  // [max_bw][2][Q] x acc_stride words
   int32_t acc_stride = 1;
-  float* beta = nullptr;
+  double* beta = nullptr;
   int32_t* vmap = nullptr;
   int32_t *stage = nullptr, *stage_b = nullptr;
   uint32_t* scnt = nullptr;
   int32_t *pool_q = nullptr, *pool_x = nullptr, *pool_n = nullptr;
-  float* pool_v = nullptr;
+  double* pool_v = nullptr;  // Viterbi scores (float32) or forward values (float64)
   int64_t* pool_base = nullptr;
   int32_t* pool_cnt = nullptr;
   int64_t *slot_base = nullptr, *step_rng = nullptr;
@@ -107,6 +113,13 @@ struct fst_plan_s {
   bool forward_done = false;
   // optional per-launch CUDA events (fst_plan_profile)
   LaunchProfile prof;
+  // driver: one launch per position, or one persistent launch per pass
+  int32_t driver = FST_DRIVER_LAUNCH;
+  int32_t persist_grid = 0;          // 0: the plan's estimate, capped at what is co-resident
+  int32_t density = 64;              // launch driver: live states per token assumed when sizing a grid
+  uint64_t barrier_limit_ns = 2000000000ull;
+  uint32_t barrier_extra = 0;        // fault injection: blocks a barrier waits for beyond the grid
+  uint32_t* gbar = nullptr;          // [2] grid barrier (arrivals, generation)
   ~fst_plan_s() {
     for (Wave& w : waves) w.release();
 #define PLAN_FREE(x) dfree(x);
@@ -202,8 +215,12 @@ int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, const 
     W.stage = std::max(W.stage, accf);
   }
   W.step0[W.tmax + 1] = (int32_t)step_tok.size();
+  int64_t busiest = 1;
+  for (int32_t t = 1; t <= W.tmax; ++t) busiest = std::max<int64_t>(busiest, W.step0[t + 1] - W.step0[t]);
+  W.grid_est = (int32_t)std::min<int64_t>((int64_t)f->num_sms * 8, (busiest * 64 + 255) / 256);
   if ((rc = upload(P, &W.bw_off, boff)) || (rc = upload(P, &W.bw_n, bn)) || (rc = upload(P, &W.tok_sym, sym)) ||
-      (rc = upload(P, &W.tok_b, tb)) || (rc = upload(P, &W.step_tok, step_tok)) || (rc = upload(P, &W.stf, stf)))
+      (rc = upload(P, &W.tok_b, tb)) || (rc = upload(P, &W.step_tok, step_tok)) || (rc = upload(P, &W.stf, stf)) ||
+      (rc = upload(P, &W.d_step0, W.step0)))
     return rc;
   return FST_OK;
 }
@@ -224,7 +241,8 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.pool_q = P->pool_q;
   S.pool_x = P->pool_x;
   S.pool_n = P->pool_n;
-  S.pool_v = P->pool_v;
+  S.pool_v = (float*)P->pool_v;
+  S.pool_d = P->pool_v;
   S.pool_base = P->pool_base;
   S.pool_cnt = P->pool_cnt;
   S.slot_base = P->slot_base;
@@ -262,7 +280,7 @@ StepView wave_step(const fst_plan_s* P, const Wave& W, int32_t t, int32_t x_t) {
   V.x_t = hasx ? x_t : 0;
   V.x_slot0 = hasx ? W.step0[x_t] : 0;
   V.x_n = hasx ? W.step0[x_t + 1] - W.step0[x_t] : 0;
-  const int64_t est = (int64_t)std::max(V.n, V.x_n) * 64;
+  const int64_t est = (int64_t)std::max(V.n, V.x_n) * P->density;
   V.blocks = (int32_t)std::min<int64_t>((int64_t)P->fst->num_sms * 8, std::max<int64_t>(1, (est + 255) / 256));
   return V;
 }
@@ -277,12 +295,23 @@ int wave_begin(fst_plan_s* P, const Wave& W, cudaStream_t s, bool fb) {
   FST_CUDA(cudaMemsetAsync(P->scnt, 0, n4, s));
   FST_CUDA(cudaMemsetAsync(P->pool_top, 0, 8, s));
   FST_CUDA(cudaMemsetAsync(P->flags_d, 0, 8, s));
+  if (P->driver == FST_DRIVER_PERSISTENT) FST_CUDA(cudaMemsetAsync(P->gbar, 0, 8, s));
   if (fb) {
     FST_CUDA(cudaMemsetAsync(P->mkey, 0, n4, s));
     FST_CUDA(cudaMemsetAsync(P->ekey, 0, n4, s));
   }
   return FST_OK;
 }
+
+// The persistent grid of a pass: the plan's setting or its estimate, capped
+// at what can be co-resident.
+int32_t persist_grid(const fst_plan_s* P, const Wave& W, int which) {
+  const int cap = persist_grid_limit(which);
+  const int32_t want = P->persist_grid > 0 ? P->persist_grid : W.grid_est;
+  return std::max(1, std::min(want, cap));
+}
+GridSync grid_sync_of(const fst_plan_s* P) { return GridSync{P->gbar, P->barrier_extra, P->barrier_limit_ns}; }
+WaveSteps wave_steps(const Wave& W) { return WaveSteps{W.d_step0, W.tmax}; }
 
 int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_paths, int32_t* d_olabels,
                      int32_t* d_status, cudaStream_t s) {
@@ -292,9 +321,13 @@ int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_p
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, nullptr);
   if ((rc = wave_begin(P, W, s, false))) return rc;
-  if (W.tmax >= 1) PROF(FST_PROF_VIT_FIRST, launch_vit_first(L, T, wave_step(P, W, 1, 0), S, s));
-  for (int32_t t = 1; t <= W.tmax; ++t)
-    PROF(FST_PROF_VIT_STEP, launch_vit_step(L, T, wave_step(P, W, t, t + 1), S, s));
+  if (P->driver == FST_DRIVER_PERSISTENT) {
+    PROF(FST_PROF_VIT_STEP, launch_vit_persist(L, T, wave_steps(W), S, persist_grid(P, W, 0), grid_sync_of(P), s));
+  } else {
+    if (W.tmax >= 1) PROF(FST_PROF_VIT_FIRST, launch_vit_first(L, T, wave_step(P, W, 1, 0), S, s));
+    for (int32_t t = 1; t <= W.tmax; ++t)
+      PROF(FST_PROF_VIT_STEP, launch_vit_step(L, T, wave_step(P, W, t, t + 1), S, s));
+  }
   PROF(FST_PROF_VIT_FINAL,
        launch_vit_final(S, W.Bw, d_scores + W.b0, P->jfinal, d_status ? d_status + W.b0 : nullptr, s));
   PROF(FST_PROF_BACKTRACE, launch_backtrace(S, f->olabel, W.Bw, P->jfinal, d_paths + W.tok0,
@@ -309,10 +342,14 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, nullptr);
   if ((rc = wave_begin(P, W, s, true))) return rc;
-  if (W.tmax >= 1) PROF(FST_PROF_FWD_FIRST, launch_fwd_first(L, T, wave_step(P, W, 1, 0), S, s));
-  for (int32_t t = 1; t <= W.tmax; ++t) {
-    PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, wave_step(P, W, t, t - 1), S, s));
-    PROF(FST_PROF_FWD_STEP, launch_fwd_step(L, T, wave_step(P, W, t, t + 1), S, s));
+  if (P->driver == FST_DRIVER_PERSISTENT) {
+    PROF(FST_PROF_FWD_STEP, launch_fwd_persist(L, T, wave_steps(W), S, persist_grid(P, W, 1), grid_sync_of(P), s));
+  } else {
+    if (W.tmax >= 1) PROF(FST_PROF_FWD_FIRST, launch_fwd_first(L, T, wave_step(P, W, 1, 0), S, s));
+    for (int32_t t = 1; t <= W.tmax; ++t) {
+      PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, wave_step(P, W, t, t - 1), S, s));
+      PROF(FST_PROF_FWD_STEP, launch_fwd_step(L, T, wave_step(P, W, t, t + 1), S, s));
+    }
   }
   PROF(FST_PROF_FB_FINAL, launch_fb_final(S, W.Bw, P->logz + W.b0, d_status ? d_status + W.b0 : nullptr, s));
   return FST_OK;
@@ -326,8 +363,15 @@ int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, bool
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, d_weights);
   const CountView C{1, nullptr, nullptr, P->cnt64, states ? P->start64 : nullptr, states ? P->final64 : nullptr};
-  for (int32_t t = W.tmax; t >= 1; --t)
-    PROF(FST_PROF_BWD_STEP, launch_bwd_step(L, T, wave_step(P, W, t, t - 1), S, C, s));
+  if (P->driver == FST_DRIVER_PERSISTENT) {
+    if (P->gbar) FST_CUDA(cudaMemsetAsync(P->gbar, 0, 4, s));  // arrivals; a timed-out forward pass leaves them
+    if (W.tmax >= 1)
+      PROF(FST_PROF_BWD_STEP,
+           launch_bwd_persist(L, T, wave_steps(W), S, C, persist_grid(P, W, 2), grid_sync_of(P), s));
+  } else {
+    for (int32_t t = W.tmax; t >= 1; --t)
+      PROF(FST_PROF_BWD_STEP, launch_bwd_step(L, T, wave_step(P, W, t, t - 1), S, C, s));
+  }
   if (states) PROF(FST_PROF_COUNTS, launch_final_posteriors(S, W.Bw, C, s));
   return FST_OK;
 }
@@ -427,10 +471,10 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
       budget = std::max<int64_t>((int64_t)16 << 30, (int64_t)(free_b / 2));
     }
     // accumulators: 2 x 8 bytes per state (Viterbi), or 2 x 16 for the
-    // forward sums and maxima plus 2 x 4 for the backward values; Viterbi
+    // forward sums and maxima plus 2 x 8 for the backward values; Viterbi
     // also maps states to pool entries, 2 x 4 bytes
-    const int64_t per_string = (int64_t)f->Q * ((P->want_fb ? 40 : 16) + (P->want_vit ? 8 : 0)) + 64;
-    const int64_t per_token = TOKEN_BYTES + POOL_PER_TOKEN * 12;
+    const int64_t per_string = (int64_t)f->Q * ((P->want_fb ? 48 : 16) + (P->want_vit ? 8 : 0)) + 64;
+    const int64_t per_token = TOKEN_BYTES + POOL_PER_TOKEN * 20;
     int32_t b0 = 0;
     int64_t acc = 0;
     for (int32_t b = 0; b <= B; ++b) {
@@ -461,7 +505,7 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
       // live pool: its exact bound when that is small, else the larger of
       // POOL_PER_TOKEN entries per token and a quarter of the budget (at
       // least 256 MiB, at most 4 GiB)
-      const int64_t ebytes = 16;
+      const int64_t ebytes = 20;
       const int64_t want = std::max(w.ntok * POOL_PER_TOKEN,
                                     std::min(std::max(budget / 4, (int64_t)256 << 20), (int64_t)4 << 30) / ebytes);
       // pool entries are named by int32 indices
@@ -509,15 +553,16 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
         (rc = alloc_store(P, &P->flags_d, 2)) || (rc = alloc_store(P, &P->mkey, nt)) ||
         (rc = alloc_store(P, &P->ekey, nt)) || (rc = alloc_store(P, &P->csum, nt)) ||
         (rc = alloc_store(P, &P->esum, nt)) || (rc = alloc_store(P, &P->jfinal, P->max_bw)) ||
-        (rc = alloc_store(P, &P->logz, B)))
+        (rc = alloc_store(P, &P->logz, B)) || (rc = alloc_store(P, &P->gbar, 2)))
       break;
     if (P->want_fb && ((rc = alloc_store(P, &P->cnt64, f->A)) || (rc = alloc_store(P, &P->start64, f->Q)) ||
                        (rc = alloc_store(P, &P->final64, f->Q))))
       break;
     // the accumulators start at zero and every run leaves them so
     cudaError_t ce = cudaMemsetAsync(P->acc, 0, (size_t)std::max<int64_t>(na * P->acc_stride, 1) * 8, s);
-    if (ce == cudaSuccess && P->beta) ce = cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 4, s);
+    if (ce == cudaSuccess && P->beta) ce = cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(P->flags_d, 0, 8, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(P->gbar, 0, 8, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) rc = cuda_fail(ce, "plan storage");
   } while (0);
@@ -547,6 +592,13 @@ extern "C" int fst_plan_info(const fst_plan_t* P, int32_t* num_strings, int64_t*
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
   int64_t vl = 0, fl = 0;
   for (const Wave& w : P->waves) {
+    if (P->driver == FST_DRIVER_PERSISTENT) {
+      // overflow clear, the persistent pass, final, backtrace
+      vl += 4;
+      // overflow clear, forward pass, final, backward pass
+      fl += w.tmax >= 1 ? 4 : 3;
+      continue;
+    }
     // overflow clear, first push, one step per position, final, backtrace
     vl += (int64_t)w.tmax + 4;
     // overflow clear, first push, sum and step per position, final; one
@@ -721,6 +773,220 @@ extern "C" int fst_plan_live_work(fst_plan_t* P, int64_t* entries, int64_t* arcs
 extern "C" int fst_plan_limit_pool(fst_plan_t* P, int64_t entries) {
   if (!P || entries < 0) { set_error("fst_plan_limit_pool: bad arguments"); return FST_ERR_INVALID_ARG; }
   P->pool_limit = entries;
+  return FST_OK;
+}
+
+extern "C" int fst_plan_set_driver(fst_plan_t* P, int32_t driver, int32_t grid_blocks, int64_t barrier_timeout_us) {
+  if (!P || (driver != FST_DRIVER_LAUNCH && driver != FST_DRIVER_PERSISTENT) || grid_blocks < 0 ||
+      barrier_timeout_us < 0) {
+    set_error("fst_plan_set_driver: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  if (driver == FST_DRIVER_PERSISTENT) {
+    int dev = 0, coop = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    FST_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) { set_error("the device cannot launch cooperative kernels"); return FST_ERR_UNSUPPORTED; }
+    const int cap = std::min(persist_grid_limit(0), std::min(persist_grid_limit(1), persist_grid_limit(2)));
+    if (cap <= 0) { set_error("no co-resident grid for the persistent passes"); return FST_ERR_UNSUPPORTED; }
+    if (grid_blocks > cap) {
+      set_error("a grid of %d blocks cannot be co-resident (at most %d)", grid_blocks, cap);
+      return FST_ERR_UNSUPPORTED;
+    }
+  }
+  P->driver = driver;
+  P->persist_grid = grid_blocks;
+  if (barrier_timeout_us > 0) P->barrier_limit_ns = (uint64_t)barrier_timeout_us * 1000ull;
+  return FST_OK;
+}
+
+// ------------------------------------------------------------- autotuner
+// A configuration of a plan's driver: which driver, the persistent grid, and
+// the launch driver's grid density.  Results are cached per device name,
+// FST shape and batch shape, in this process and, when FSTGPU_TUNE_CACHE
+// names a file, across processes (one tab-separated line per key).
+namespace {
+struct TuneConf {
+  int32_t driver = FST_DRIVER_LAUNCH, grid = 0, density = 64;
+  double ms = 0.0;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneConf> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_file() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("FSTGPU_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fh = fopen(path, "r");
+  if (!fh) return;
+  char line[1024];
+  while (fgets(line, sizeof(line), fh)) {
+    char key[768];
+    TuneConf c;
+    if (sscanf(line, "%767[^\t]\t%d\t%d\t%d\t%lf", key, &c.driver, &c.grid, &c.density, &c.ms) == 5 &&
+        (c.driver == FST_DRIVER_LAUNCH || c.driver == FST_DRIVER_PERSISTENT) && c.grid >= 0 && c.density > 0)
+      g_tune[key] = c;
+  }
+  fclose(fh);
+}
+
+void tune_store_file(const std::string& key, const TuneConf& c) {
+  const char* path = getenv("FSTGPU_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fh = fopen(path, "a");
+  if (!fh) return;
+  fprintf(fh, "%s\t%d\t%d\t%d\t%.6f\n", key.c_str(), c.driver, c.grid, c.density, c.ms);
+  fclose(fh);
+}
+
+std::string tune_key(const fst_plan_s* P) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::string name = "gpu";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  else (void)cudaGetLastError();
+  for (char& ch : name)
+    if (ch == '\t' || ch == '\n') ch = ' ';
+  const fst_s* f = P->fst;
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s|Q=%d|A=%lld|m=%d|B=%d|N=%lld|T=%d|waves=%d|%s", name.c_str(), f->Q,
+           (long long)f->A, f->m, P->B, (long long)P->N, P->max_len, (int)P->waves.size(),
+           P->want_vit ? (P->want_fb ? "both" : "viterbi") : "forward-backward");
+  return buf;
+}
+}  // namespace
+
+// One run of the plan's own passes (Viterbi and/or forward-backward with
+// counts) into scratch outputs, timed with CUDA events on `s`.
+static int tune_time(fst_plan_s* P, cudaStream_t s, int reps, float* d_scores, int32_t* d_paths, int32_t* d_status,
+                     double* d_logz, float* d_counts, double* ms_out) {
+  cudaEvent_t e0, e1;
+  FST_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+  }
+  int rc = FST_OK;
+  float best = 1e30f;
+  for (int r = 0; r < reps + 1 && !rc; ++r) {
+    cudaEventRecord(e0, s);
+    if (P->want_vit) rc = fst_plan_viterbi(P, d_scores, d_paths, nullptr, d_status, s);
+    if (!rc && P->want_fb) rc = fst_plan_forward_backward(P, nullptr, d_logz, d_counts, d_status, s);
+    cudaEventRecord(e1, s);
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "autotune run"); break; }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (r > 0) best = std::min(best, t);  // the first run warms the caches
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = best;
+  return rc;
+}
+
+extern "C" int fst_plan_autotune(fst_plan_t* P, void* stream, int32_t flags, int32_t* driver, int32_t* grid_blocks,
+                                 double* best_ms) {
+  if (!P || (flags & ~FST_TUNE_REFRESH)) { set_error("fst_plan_autotune: bad arguments"); return FST_ERR_INVALID_ARG; }
+  cudaStream_t s = as_stream(stream);
+  const std::string key = tune_key(P);
+  TuneConf best;
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load_file();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end() && !(flags & FST_TUNE_REFRESH)) {
+      best = it->second;
+      have = true;
+    }
+  }
+  int rc = FST_OK;
+  if (!have) {
+    // scratch outputs of the candidate runs
+    fst_s* f = P->fst;
+    float *d_scores = nullptr, *d_counts = nullptr;
+    int32_t *d_paths = nullptr, *d_status = nullptr;
+    double* d_logz = nullptr;
+    const bool prof = P->prof.on;
+    P->prof.on = false;
+    const uint32_t extra = P->barrier_extra;
+    P->barrier_extra = 0;
+    const TuneConf saved{P->driver, P->persist_grid, P->density, 0.0};
+    do {
+      if ((rc = dalloc(&d_status, P->B)) || (rc = dalloc(&d_scores, P->B)) || (rc = dalloc(&d_paths, P->N)) ||
+          (rc = dalloc(&d_logz, P->B)) || (rc = dalloc(&d_counts, f->A)))
+        break;
+      std::vector<TuneConf> cands;
+      for (int32_t d : {16, 64, 256}) cands.push_back(TuneConf{FST_DRIVER_LAUNCH, 0, d, 0.0});
+      int dev = 0, coop = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop) {
+        const int cap = std::min(persist_grid_limit(0), std::min(persist_grid_limit(1), persist_grid_limit(2)));
+        std::vector<int32_t> grids;
+        for (int k = 1; k * f->num_sms <= cap; ++k) grids.push_back(k * f->num_sms);
+        if (cap > 0) grids.push_back(cap);
+        int32_t est = 1;
+        for (const Wave& w : P->waves) est = std::max(est, w.grid_est);
+        if (cap > 0) grids.push_back(std::min(est, cap));
+        std::sort(grids.begin(), grids.end());
+        grids.erase(std::unique(grids.begin(), grids.end()), grids.end());
+        for (int32_t g : grids) cands.push_back(TuneConf{FST_DRIVER_PERSISTENT, g, 64, 0.0});
+      } else {
+        (void)cudaGetLastError();
+      }
+      best.ms = 1e30;
+      for (TuneConf& c : cands) {
+        P->driver = c.driver;
+        P->persist_grid = c.grid;
+        P->density = c.density;
+        if ((rc = tune_time(P, s, 2, d_scores, d_paths, d_status, d_logz, d_counts, &c.ms))) break;
+        if (c.ms < best.ms) best = c;
+      }
+    } while (0);
+    dfree(d_scores); dfree(d_paths); dfree(d_status); dfree(d_logz); dfree(d_counts);
+    P->prof.on = prof;
+    P->barrier_extra = extra;
+    if (rc) {
+      P->driver = saved.driver;
+      P->persist_grid = saved.grid;
+      P->density = saved.density;
+      return rc;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = best;
+    tune_store_file(key, best);
+  }
+  P->driver = best.driver;
+  P->persist_grid = best.grid;
+  P->density = best.density;
+  if (driver) *driver = best.driver;
+  if (grid_blocks) *grid_blocks = best.driver == FST_DRIVER_PERSISTENT ? best.grid : 0;
+  if (best_ms) *best_ms = best.ms;
+  return FST_OK;
+}
+
+extern "C" int fst_plan_get_driver(const fst_plan_t* P, int32_t* driver, int32_t* grid_blocks) {
+  if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
+  if (driver) *driver = P->driver;
+  if (grid_blocks) {
+    int32_t g = 0;
+    if (P->driver == FST_DRIVER_PERSISTENT)
+      for (const Wave& w : P->waves) g = std::max(g, persist_grid(P, w, 1));
+    *grid_blocks = g;
+  }
+  return FST_OK;
+}
+
+extern "C" int fst_plan_fault_inject(fst_plan_t* P, int32_t kind, int64_t value) {
+  if (!P || kind < FST_FAULT_NONE || kind > FST_FAULT_BARRIER_STALL || value < 0 || value > 1024) {
+    set_error("fst_plan_fault_inject: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  P->barrier_extra = kind == FST_FAULT_BARRIER_STALL ? (uint32_t)value : 0u;
   return FST_OK;
 }
 

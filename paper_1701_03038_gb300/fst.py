@@ -322,6 +322,33 @@ class Plan:
         check(self._lib.fst_plan_live_work(self._h, C.byref(e), C.byref(a), _stream(stream)), "fst_plan_live_work")
         return dict(entries=e.value, arcs=a.value)
 
+    def set_driver(self, driver: int, grid_blocks: int = 0, barrier_timeout_us: int = 0):
+        """Driver of the following runs: _lib.DRIVER_LAUNCH (one launch per
+        position) or _lib.DRIVER_PERSISTENT (one cooperative launch per pass)."""
+        with torch.cuda.device(self.fst.device):
+            check(self._lib.fst_plan_set_driver(self._h, int(driver), int(grid_blocks), int(barrier_timeout_us)),
+                  "fst_plan_set_driver")
+
+    def autotune(self, refresh: bool = False, stream=None) -> dict:
+        """Time the plan's pass under each driver configuration and keep the
+        fastest (see fst_plan_autotune); returns the choice."""
+        d, g, ms = C.c_int32(), C.c_int32(), C.c_double()
+        with torch.cuda.device(self.fst.device):
+            check(self._lib.fst_plan_autotune(self._h, _stream(stream), _lib.TUNE_REFRESH if refresh else 0,
+                                              C.byref(d), C.byref(g), C.byref(ms)), "fst_plan_autotune")
+        return dict(driver="persistent" if d.value == _lib.DRIVER_PERSISTENT else "launch", grid=g.value,
+                    ms=ms.value)
+
+    def driver(self) -> tuple[int, int]:
+        d, g = C.c_int32(), C.c_int32()
+        check(self._lib.fst_plan_get_driver(self._h, C.byref(d), C.byref(g)), "fst_plan_get_driver")
+        return d.value, g.value
+
+    def fault_inject(self, kind: int, value: int = 0):
+        """Testing hook: _lib.FAULT_BARRIER_STALL makes the persistent passes'
+        barriers wait for `value` blocks that do not exist (their waits time out)."""
+        check(self._lib.fst_plan_fault_inject(self._h, int(kind), int(value)), "fst_plan_fault_inject")
+
     def limit_pool(self, entries: int = 0):
         """Cap the live pool of the following runs (0 = the full capacity)."""
         check(self._lib.fst_plan_limit_pool(self._h, int(entries)), "fst_plan_limit_pool")

@@ -214,3 +214,68 @@ def test_large_groups():
     check_batch_viterbi(o, strs, f.viterbi_batch(ids, off))
     r = f.forward_backward_batch(ids, off)
     check_batch_fb(o, strs, r["logz"], r["counts"])
+
+
+@pytest.mark.parametrize("grid", [0, 1, 7, -1])
+def test_persistent_driver_matches_launch_driver(c2s, grid):
+    # one cooperative launch per pass with grid barriers between positions:
+    # Viterbi bit-identical to the per-position launches, forward-backward
+    # held to the oracle; grid 0 = the plan's estimate, -1 = every block that
+    # can be co-resident; also over several waves and the split
+    # forward / backward calls
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    ref = f.plan(ids, off)
+    ref.viterbi()
+    torch.cuda.synchronize()
+    for budget, flags in ((0, 0), (1 << 20, 0), (0, _lib.PLAN_SINGLE_WAVE)):
+        p = f.plan(ids, off, mem_budget=budget, flags=flags)
+        g = grid
+        if g < 0:
+            p.set_driver(_lib.DRIVER_PERSISTENT, 1)
+            g = 1
+            while True:  # the largest co-resident grid
+                try:
+                    p.set_driver(_lib.DRIVER_PERSISTENT, g * 2)
+                    g *= 2
+                except _lib.FstError:
+                    break
+        p.set_driver(_lib.DRIVER_PERSISTENT, g)
+        assert p.driver()[0] == _lib.DRIVER_PERSISTENT
+        p.viterbi()
+        if flags & _lib.PLAN_SINGLE_WAVE:
+            p.forward()
+            p.backward()
+        else:
+            p.forward_backward()
+        torch.cuda.synchronize()
+        assert torch.equal(p.scores, ref.scores) and torch.equal(p.paths, ref.paths)
+        assert torch.equal(p.olabels, ref.olabels) and torch.equal(p.status, ref.status)
+        check_batch_fb(o, strs, p.logz[:strs.count], p.counts[:o.A])
+        info = p.info()
+        assert info["viterbi_launches"] == 4 * info["waves"]
+
+
+def test_autotune_keeps_results_and_caches(c2s, tmp_path, monkeypatch):
+    # the autotuner times the plan under every driver configuration and
+    # keeps the fastest; results are those of the oracle whatever it picks,
+    # and a second plan of the same shapes takes the cached choice
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    p = f.plan(ids, off)
+    choice = p.autotune(refresh=True)
+    assert choice["driver"] in ("launch", "persistent") and choice["ms"] > 0
+    assert (p.driver()[0] == _lib.DRIVER_PERSISTENT) == (choice["driver"] == "persistent")
+    p.viterbi()
+    p.forward_backward()
+    torch.cuda.synchronize()
+    check_batch_viterbi(o, strs, dict(scores=p.scores[:strs.count], paths=p.paths[:len(strs.ids)],
+                                      olabels=p.olabels[:len(strs.ids)], status=p.status[:strs.count]))
+    check_batch_fb(o, strs, p.logz[:strs.count], p.counts[:o.A])
+    q = f.plan(ids, off)
+    again = q.autotune()
+    assert again == choice  # cached: same configuration, same recorded time

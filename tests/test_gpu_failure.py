@@ -8,6 +8,7 @@ exact again.  The overflow is forced by capping the pool
 bounds.
 """
 import math
+import time
 
 import numpy as np
 import pytest
@@ -83,3 +84,68 @@ def test_pool_limit_rejects_negative():
     p = f.plan(torch.from_numpy(strs.ids).cuda(), torch.from_numpy(strs.offsets).cuda())
     with pytest.raises(FstError):
         p.limit_pool(-1)
+
+
+def test_persistent_barrier_timeout_reports_and_recovers():
+    # the persistent passes' grid barriers are told to wait for one block
+    # that does not exist: every wait runs out after its limit (0.2 s here),
+    # the run ends early with FST_ERR_TIMEOUT for every string, the GPU keeps
+    # answering, and the next run on the same plans is exact
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    from paper_1701_03038_gb300._lib import PLAN_NO_FB, PLAN_NO_VITERBI
+    from paper_1701_03038_gb300.fst import Fst
+    fa, strs = synth.make_config("c2", scale=0.02, strings=16)
+    f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+    ids = torch.from_numpy(strs.ids).cuda()
+    off = torch.from_numpy(strs.offsets).cuda()
+    pv = f.plan(ids, off, flags=PLAN_NO_FB)
+    pf = f.plan(ids, off, flags=PLAN_NO_VITERBI)
+    for p in (pv, pf):
+        p.set_driver(_lib.DRIVER_PERSISTENT, 0, 200_000)
+    B = strs.count
+    ov = [o.viterbi(strs.get(b)) for b in range(B)]
+    ofb = o.fb_batch(strs.ids, strs.offsets, nthreads=8)
+    for p in (pv, pf):
+        p.fault_inject(_lib.FAULT_BARRIER_STALL, 1)
+    t0 = time.perf_counter()
+    pv.viterbi()
+    torch.cuda.synchronize()
+    pf.forward_backward()
+    torch.cuda.synchronize()
+    waited = time.perf_counter() - t0
+    assert waited < 30.0
+    assert (pv.status[:B].cpu().numpy() == _lib.TIMEOUT).all()
+    assert (pf.status[:B].cpu().numpy() == _lib.TIMEOUT).all()
+    assert np.isneginf(pv.scores[:B].cpu().numpy()).all()
+    assert np.isneginf(pf.logz[:B].cpu().numpy()).all()
+    assert (pf.counts.cpu().numpy() == 0).all()
+    # the context is still usable: the same plans, injection off, are exact
+    for p in (pv, pf):
+        p.fault_inject(_lib.FAULT_NONE)
+    pv.viterbi()
+    pf.forward_backward()
+    torch.cuda.synchronize()
+    sc, pa, ol, st = pv.scores.cpu().numpy(), pv.paths.cpu().numpy(), pv.olabels.cpu().numpy(), pv.status.cpu().numpy()
+    for b in range(B):
+        lo, hi = strs.offsets[b], strs.offsets[b + 1]
+        assert_viterbi_equal(sc[b], pa[lo:hi], ol[lo:hi], st[b], ov[b])
+        assert_logz_close(pf.logz[b].item(), ofb["logz"][b])
+    assert_counts_close(pf.counts.cpu().numpy(), ofb["counts"], batch=True)
+
+
+def test_fault_inject_rejects_bad_arguments():
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    from paper_1701_03038_gb300._lib import FstError
+    from paper_1701_03038_gb300.fst import Fst
+    fa, strs = synth.make_config("c1", scale=0.2, strings=2)
+    f = Fst.from_arrays(fa)
+    p = f.plan(torch.from_numpy(strs.ids).cuda(), torch.from_numpy(strs.offsets).cuda())
+    for kind, value in ((7, 0), (_lib.FAULT_BARRIER_STALL, -1), (_lib.FAULT_BARRIER_STALL, 5000)):
+        with pytest.raises(FstError):
+            p.fault_inject(kind, value)
+    with pytest.raises(FstError):
+        p.set_driver(5)
+    with pytest.raises(FstError):
+        p.set_driver(_lib.DRIVER_PERSISTENT, 10 ** 7)  # far more blocks than can be co-resident
