@@ -468,8 +468,8 @@ __device__ __forceinline__ Source source_at(const TokenView& T, const StepView& 
     const int32_t pp = __ldg(T.step_tok + V.x_slot0 + o.k);
     if (S.bw_n[__ldg(T.b + pp)] >= V.t) {
       x.p = pp + 1;
-      x.q = S.pool_q[j];
-      x.r = S.pool_d[j];
+      x.q = __ldcg(S.pool_q + j);
+      x.r = __ldcg(S.pool_d + j);
       x.head = o.first == j;
     }
   }
@@ -481,15 +481,15 @@ __device__ __forceinline__ void source_range(const StepView& V, const FrontierSt
     *R0 = 0;
     *R1 = (int64_t)V.n * S.nstart;
   } else {
-    *R0 = S.step_rng[2 * V.x_t];
-    *R1 = S.step_rng[2 * V.x_t + 1];
+    *R0 = __ldcg(S.step_rng + 2 * V.x_t);
+    *R1 = __ldcg(S.step_rng + 2 * V.x_t + 1);
   }
 }
 // The source's arcs on w_t: looked up at t = 1, stored in the pool by the
 // forward step afterwards.
 __device__ __forceinline__ Arcs source_arcs(const LayoutView& L, const TokenView& T, const StepView& V,
                                             const FrontierState& S, const Source& x, int64_t j) {
-  return V.t == 1 ? find_arcs(L, __ldg(T.sym + x.p), x.q) : Arcs{S.pool_x[j], S.pool_n[j]};
+  return V.t == 1 ? find_arcs(L, __ldg(T.sym + x.p), x.q) : Arcs{__ldcg(S.pool_x + j), __ldcg(S.pool_n + j)};
 }
 
 // First position: the start states of every token push their arcs on w_1.
@@ -548,7 +548,7 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
                                               const FrontierState& S, BlockScratch<PushCtx>& sh) {
   const int lane = threadIdx.x & 31;
   const int32_t t = V.t;
-  const int64_t R0 = S.step_rng[2 * t], R1 = S.step_rng[2 * t + 1];
+  const int64_t R0 = __ldcg(S.step_rng + 2 * t), R1 = __ldcg(S.step_rng + 2 * t + 1);
   const int32_t* stg = fwd_stage(S, t);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
     const int64_t c0 = cb + (int64_t)(threadIdx.x & ~31);  // this warp's 32 entries (block-uniform loop)
@@ -561,11 +561,11 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
     if (j < R1) {
       const Entry x = step_entry(T, V, o, j);
       const int32_t b = __ldg(T.b + x.p);
-      const int32_t d = stg[__ldg(T.stf + x.p) + x.i];
+      const int32_t d = __ldcg(stg + __ldg(T.stf + x.p) + x.i);
       const int64_t slot = acc_slot(S, b, t, d);
       double r;
       if (VIT) {
-        const unsigned long long key = *vit_key(S, slot);
+        const unsigned long long key = __ldcg(vit_key(S, slot));
         const float rv = fkey_inv((uint32_t)(key >> 32));
         r = rv;
         S.pool_v[j] = rv;
@@ -573,11 +573,11 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
         S.pool_x[j] = id;
         // the predecessor entry: the source's entry at t-1, which the step
         // before this one recorded in the state map of that position
-        S.pool_n[j] = t > 1 ? S.vmap[acc_slot(S, b, t - 1, __ldg(S.src_by_id + id))] : -1;
+        S.pool_n[j] = t > 1 ? __ldcg(S.vmap + acc_slot(S, b, t - 1, __ldg(S.src_by_id + id))) : -1;
         S.vmap[slot] = (int32_t)j;
       } else {
-        const ulonglong2 a = *(const ulonglong2*)fwd_sum(S, slot);
-        const float sh_prev = t > 1 ? decode_max(S.mkey[x.p - 1]) : 0.f;
+        const ulonglong2 a = __ldcg((const ulonglong2*)fwd_sum(S, slot));
+        const float sh_prev = t > 1 ? decode_max(__ldcg(S.mkey + x.p - 1)) : 0.f;
         r = fix_log_sum64((double)fkey_inv((uint32_t)a.y) - (double)sh_prev, a.x);
         S.pool_d[j] = r;
         mk_p = x.p;
@@ -658,7 +658,7 @@ __device__ __forceinline__ void sum_position(const LayoutView& L, const TokenVie
       const double v = c.r + (double)__int_as_float(a.y);
       if (v == -INFINITY) return;
       const int64_t slot = acc_slot(S, c.b, t, a.x);
-      atomicAdd(fwd_sum(S, slot), fix_exp64(v, (double)fkey_inv(*fwd_max(S, slot))));
+      atomicAdd(fwd_sum(S, slot), fix_exp64(v, (double)fkey_inv(__ldcg(fwd_max(S, slot)))));
     });
   }
 }
@@ -718,28 +718,28 @@ __device__ __forceinline__ void bwd_position(const LayoutView& L, const TokenVie
     if (j < R1) {
       const Source x = source_at(T, V, S, o, j);
       const int32_t b = x.p >= 0 ? __ldg(T.b + x.p) : 0;
-      const double lz = x.p >= 0 ? S.logz[b] : -INFINITY;
+      const double lz = x.p >= 0 ? __ldcg(S.logz + b) : -INFINITY;
       if (lz != -INFINITY) {
         p = x.p;
         q = x.q;
         const int32_t n = S.bw_n[b];
-        const float et = (t == n) ? 0.f : decode_max(S.ekey[p]);
-        const double tE = (t == n) ? 0.0 : S.esum[p + 1] + (double)et;
+        const float et = (t == n) ? 0.f : decode_max(__ldcg(S.ekey + p));
+        const double tE = (t == n) ? 0.0 : __ldcg(S.esum + p + 1) + (double)et;
         if (x.head && t > 1) S.esum[p] = tE;  // E_t, read by the step at t-1
-        const float mprev = (t == 1) ? 0.f : decode_max(S.mkey[p - 1]);
+        const float mprev = (t == 1) ? 0.f : decode_max(__ldcg(S.mkey + p - 1));
         if (et != neg_inf()) {
           const Arcs r = source_arcs(L, T, V, S, x, j);
           e0 = r.pos;
           len = r.len;
         }
         me = BwdCtx{b, n, et, S.gweight ? S.gweight[b] : 1.f, x.r, 0.0,
-                    (((t == 1) ? 0.0 : S.csum[p - 1]) + tE - lz) - (double)mprev};
+                    (((t == 1) ? 0.0 : __ldcg(S.csum + p - 1)) + tE - lz) - (double)mprev};
       }
     }
     // theta_e + beta_t[q'] - e_t; the final weight stands in for beta at the
     // string's last position
     auto ub_of = [&](int32_t d, const BwdCtx& c) -> double {
-      return (t == c.n) ? (double)__ldg(S.theta_f + d) : S.beta[acc_slot(S, c.b, t, d)];
+      return (t == c.n) ? (double)__ldg(S.theta_f + d) : __ldcg(S.beta + acc_slot(S, c.b, t, d));
     };
     auto value = [&](int32_t e, const BwdCtx& c) -> double {
       const int4 a = __ldg(L.arcs + e);
