@@ -594,8 +594,10 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
                                "frontier_plain_sentences_per_s": k / dt_ours,
                                "speedup": dt_slice / dt_ours}
 
-    # end to end through the public batch API with host buffers
+    # end to end through the public batch API with host buffers (the batch
+    # calls' plans get the same storage budget as the timed plans)
     if not args.no_e2e:
+        f.set_batch_budget(budget)
         out["e2e"] = e2e_batch(args, world, dev, fa, strs, f, s_v, s_f, 3 * relax_pass)
     return out
 
@@ -752,6 +754,12 @@ def bench_train(args, rank, world, dev, fa, strs, f, stats):
     ids = torch.from_numpy(strs.ids).to(dev)
     off = torch.from_numpy(strs.offsets).to(dev)
     plan = f.plan(ids, off, mem_budget=int(args.budget_gb * (1 << 30)), flags=PLAN_SINGLE_WAVE)
+    from paper_1701_03038_gb300 import _lib
+    tuned = None
+    if args.driver in ("persistent", "persistent-all"):
+        plan.set_driver(_lib.DRIVER_PERSISTENT)
+    elif args.driver == "autotune":
+        tuned = plan.autotune()
     info = plan.info()
     mod = LogZModule(f, -torch.from_numpy(fa.weight.astype(np.float32)))
     opt = torch.optim.SGD(mod.parameters(), lr=1e-3)
@@ -769,6 +777,8 @@ def bench_train(args, rank, world, dev, fa, strs, f, stats):
     out["config"].update({"relaxations_per_pass": relax_pass, "plan_gb": round(info["device_bytes"] / 2**30, 2),
                           "parallelism": "replicas" if world > 1 else "1 GPU",
                           "launch": "host launches (fst_set_weights between steps is synchronous)",
+                          "driver": {"forward_backward": "persistent" if plan.driver()[0] else "one launch per position",
+                                     "grid": plan.driver()[1], "autotune": tuned},
                           "l2": "no flush: arc store, plan storage and the 2M-arc count vector exceed L2"})
     plan.profile(True)
     step()
@@ -777,7 +787,8 @@ def bench_train(args, rank, world, dev, fa, strs, f, stats):
     plan.profile(False)
     live = plan.live_work()
     peak, peak_src = load_peak()
-    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(), stats, strs.ids)
+    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(), stats, strs.ids,
+                          ("fwd", "bwd") if plan.driver()[0] else ())
     out.update({"relaxations_performed_per_s": job_throughput(2 * max(live["arcs"], 0), world, ms / 1000.0),
                 "live_work": live, "roofline": rl, "passes": passes,
                 "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}})

@@ -183,6 +183,11 @@ FST_API int fst_forward_backward_batch(fst_t* fst, const int32_t* d_ids, const i
                                int32_t B, const float* d_weights, double* d_logz,
                                float* d_counts, int32_t* d_status, void* stream);
 
+/* Storage budget of the plans that fst_viterbi_batch and
+ * fst_forward_backward_batch build (0 = the fst_plan_create default).  A
+ * batch whose per-string storage exceeds it runs in several waves. */
+FST_API int fst_set_batch_budget(fst_t* fst, int64_t mem_budget_bytes);
+
 /* A plan holds everything a batch needs on the device: the token lists of
  * every position (strings sorted by length), the per-string accumulators,
  * the live pool of every position (states, values, backpointers or arcs)
@@ -193,8 +198,8 @@ FST_API int fst_forward_backward_batch(fst_t* fst, const int32_t* d_ids, const i
  *   d_ids, d_offsets  as fst_viterbi_batch; they are read during
  *               fst_plan_create only (the plan keeps its own copy).
  *   mem_budget_bytes  cap on per-step storage; strings are processed in
- *               waves that fit (0 = half the free device memory at the
- *               call, at least 16 GiB).
+ *               waves that fit (0 = a quarter of the free device memory at
+ *               the call, at most 32 GiB and at least 256 MiB).
  *   flags       FST_PLAN_SINGLE_WAVE: fail with FST_ERR_OOM instead of
  *               splitting into waves (needed by fst_plan_forward followed by
  *               fst_plan_backward, which keep state between calls).

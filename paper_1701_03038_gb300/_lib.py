@@ -50,6 +50,7 @@ SIGNATURES = {
     "fst_plan_live_work": [vp, vp, vp, vp],
     "fst_plan_forward_backward_ex": [vp, vp, vp, vp, vp, vp, vp, vp],
     "fst_plan_limit_pool": [vp, i64],
+    "fst_set_batch_budget": [vp, i64],
     "fst_plan_set_driver": [vp, i32, i32, i64],
     "fst_plan_get_driver": [vp, vp, vp],
     "fst_plan_fault_inject": [vp, i32, i64],

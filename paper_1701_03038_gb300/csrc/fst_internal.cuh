@@ -131,6 +131,7 @@ struct fst_s {
   // the last plan of each batch call kind (Viterbi, forward-backward), whose
   // storage the next call of that kind takes over
   struct fst_plan_s* batch_plan[2] = {nullptr, nullptr};
+  int64_t batch_budget = 0;  // plan storage budget of the batch calls (0 = the plan default)
   std::mutex* batch_mu = nullptr;
   // the paper's slice-wide relaxation (fst_viterbi_slice): per-arc records
   // {src, dst, id} in the destination-segmented layout's order, and the

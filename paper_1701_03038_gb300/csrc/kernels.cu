@@ -144,8 +144,8 @@ __device__ __forceinline__ unsigned long long* vit_key(const FrontierState& S, i
   return S.acc + slot * S.acc_stride;
 }
 __device__ __forceinline__ unsigned long long* fwd_sum(const FrontierState& S, int64_t slot) { return S.acc + 2 * slot; }
-__device__ __forceinline__ uint32_t* fwd_max(const FrontierState& S, int64_t slot) {
-  return (uint32_t*)(S.acc + 2 * slot + 1);
+__device__ __forceinline__ unsigned long long* fwd_max(const FrontierState& S, int64_t slot) {
+  return S.acc + 2 * slot + 1;
 }
 
 // The last block of a kernel to finish hands out consecutive ranges, in step
@@ -328,18 +328,32 @@ __device__ __forceinline__ void block_visit(BlockScratch<Ctx>& sh, int32_t e0, i
   __syncthreads();
 }
 
+// Order-preserving map float64 -> uint64 (as fkey for float32); no finite
+// value or -inf maps to 0, which therefore means "nothing yet".
+__device__ __forceinline__ unsigned long long dkey(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+  const unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)u);
+}
+
 // exp(v - m), v <= m, as a 2^-40 fixed-point integer: sums of these are exact
 // and so independent of the order in which they are added.  A sum of fewer
 // than 2^24 terms cannot overflow (the store refuses longer segments).  The
-// value and the reference are float64: the forward and backward values
+// value and the maximum m are float64: the forward and backward values
 // carried from position to position are float64 (a float32 value rounds by
 // up to 2^-24 of its size at every position, and over a 200-position string
 // those roundings shift alpha + beta - log Z by ~1e-5, the whole posterior
 // tolerance), and so is the term, whose relative error would otherwise add
-// to the same drift.  v - m may exceed 0 by the rounding of m (a float32
-// order key): the term then exceeds 2^40 by that much.
+// to the same drift.  The maximal term is exactly 2^40 and costs no
+// exponential (most destinations of a sparse frontier have one live arc;
+// float64 arithmetic is scarce on this GPU).
 __device__ __forceinline__ unsigned long long fix_exp64(double v, double m) {
-  return v == -INFINITY ? 0ull : __double2ull_rn(exp(v - m) * 1099511627776.0);  // 2^40
+  if (v == -INFINITY) return 0ull;
+  if (v == m) return 1099511627776ull;  // 2^40
+  return __double2ull_rn(exp(v - m) * 1099511627776.0);
 }
 // m + log(s / 2^40), in float64.
 __device__ __forceinline__ double fix_log_sum64(double m, unsigned long long s) {
@@ -350,12 +364,10 @@ __device__ __forceinline__ uint32_t fkey64(double v) { return v == -INFINITY ? 0
 
 // Reductions over each thread's segment: Op maps a value to a 64-bit key,
 // combines keys atomically and maps the result back.
-struct RedMaxD {  // max of float64 values through the order keys of their float32 roundings
+struct RedMaxD {  // exact max of float64 values through their order keys (0 = nothing)
   typedef double T;
-  static __device__ __forceinline__ unsigned long long key(T v) { return (unsigned long long)fkey64(v); }
-  static __device__ __forceinline__ T value(unsigned long long k) {
-    return k ? (double)fkey_inv((uint32_t)k) : -INFINITY;
-  }
+  static __device__ __forceinline__ unsigned long long key(T v) { return v == -INFINITY ? 0ull : dkey(v); }
+  static __device__ __forceinline__ T value(unsigned long long k) { return k ? dkey_inv(k) : -INFINITY; }
   static __device__ __forceinline__ void atomic(unsigned long long* a, unsigned long long k) { if (k) atomicMax(a, k); }
 };
 struct RedSum {  // exact integer sum
@@ -430,17 +442,18 @@ __device__ __forceinline__ void push_arc(const LayoutView& L, const TokenView& T
   if (valid) {
     const int4 a = __ldg(L.arcs + e);
     d = a.x;
-    // Viterbi: one rounded float32 addition; forward: the float32 rounding
-    // of the float64 value, an order key for the maximum only
-    const float u = VIT ? __fadd_rn((float)c.r, __int_as_float(a.y)) : (float)(c.r + (double)__int_as_float(a.y));
-    if (u != neg_inf()) {
-      const int64_t slot = acc_slot(S, c.b, t, d);
-      if (VIT) {
+    if (VIT) {
+      // one rounded float32 addition per candidate
+      const float u = __fadd_rn((float)c.r, __int_as_float(a.y));
+      if (u != neg_inf()) {
         const uint32_t id = (uint32_t)a.z;
-        first = atomicMax(vit_key(S, slot), ((unsigned long long)fkey(u) << 32) | (unsigned long long)(~id)) == 0ull;
-      } else {
-        first = atomicMax(fwd_max(S, slot), fkey(u)) == 0u;
+        first = atomicMax(vit_key(S, acc_slot(S, c.b, t, d)),
+                          ((unsigned long long)fkey(u) << 32) | (unsigned long long)(~id)) == 0ull;
       }
+    } else {
+      // the exact float64 maximum (its term in the sum is then exactly 1)
+      const double v = c.r + (double)__int_as_float(a.y);
+      if (v != -INFINITY) first = atomicMax(fwd_max(S, acc_slot(S, c.b, t, d)), dkey(v)) == 0ull;
     }
   }
   const uint32_t i = warp_stage_index(S.scnt, c.p, first);
@@ -578,7 +591,7 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
       } else {
         const ulonglong2 a = __ldcg((const ulonglong2*)fwd_sum(S, slot));
         const float sh_prev = t > 1 ? decode_max(__ldcg(S.mkey + x.p - 1)) : 0.f;
-        r = fix_log_sum64((double)fkey_inv((uint32_t)a.y) - (double)sh_prev, a.x);
+        r = fix_log_sum64(dkey_inv(a.y) - (double)sh_prev, a.x);
         S.pool_d[j] = r;
         mk_p = x.p;
         mk_key = fkey64(r);
@@ -658,7 +671,7 @@ __device__ __forceinline__ void sum_position(const LayoutView& L, const TokenVie
       const double v = c.r + (double)__int_as_float(a.y);
       if (v == -INFINITY) return;
       const int64_t slot = acc_slot(S, c.b, t, a.x);
-      atomicAdd(fwd_sum(S, slot), fix_exp64(v, (double)fkey_inv(__ldcg(fwd_max(S, slot)))));
+      atomicAdd(fwd_sum(S, slot), fix_exp64(v, dkey_inv(__ldcg(fwd_max(S, slot)))));
     });
   }
 }
@@ -899,9 +912,12 @@ __global__ void __launch_bounds__(FT) k_vit_final(FrontierState S, float* __rest
   const int64_t b = blockIdx.x;
   const int32_t n = S.bw_n[b];
   const int64_t p = S.bw_off[b] + n - 1;
-  const int64_t base = n == 0 ? 0 : S.pool_base[p];
+  // a run that stopped early (pool overflow, barrier timeout) may not have
+  // handed out the last position's pool range: read no candidates then
+  const uint32_t err = S.flags[1] & (ERR_POOL | ERR_TIMEOUT);
+  const int64_t base = (n == 0 || err) ? 0 : S.pool_base[p];
   const int32_t* cand = n == 0 ? S.start_q : S.pool_q + base;
-  const int32_t ncand = n == 0 ? S.nstart : S.pool_cnt[p];
+  const int32_t ncand = err ? 0 : (n == 0 ? S.nstart : S.pool_cnt[p]);
   // best (score, lowest state) key; the low word holds ~state, and for the
   // pool entry the search below finds the index
   unsigned long long best = 0ull;
@@ -924,7 +940,6 @@ __global__ void __launch_bounds__(FT) k_vit_final(FrontierState S, float* __rest
   __syncthreads();
   best = red[0];
   for (int w = 1; w < FT / 32; ++w) best = red[w] > best ? red[w] : best;
-  const uint32_t err = S.flags[1] & (ERR_POOL | ERR_TIMEOUT);
   const bool oom = err != 0u;
   const int32_t qbest = best ? (int32_t)(~(uint32_t)best) : -1;
   if (threadIdx.x == 0) {
@@ -997,12 +1012,16 @@ __global__ void __launch_bounds__(FT) k_fb_final(FrontierState S, double* __rest
     }
   }
   const int64_t p = off + n - 1;
-  const int32_t* cand = n == 0 ? S.start_q : S.pool_q + S.pool_base[p];
-  const int32_t ncand = n == 0 ? S.nstart : S.pool_cnt[p];
+  // a run that stopped early may not have handed out the last position's
+  // pool range: read no candidates then
+  const uint32_t err = S.flags[1] & (ERR_POOL | ERR_TIMEOUT);
+  const int64_t base = (n == 0 || err) ? 0 : S.pool_base[p];
+  const int32_t* cand = n == 0 ? S.start_q : S.pool_q + base;
+  const int32_t ncand = err ? 0 : (n == 0 ? S.nstart : S.pool_cnt[p]);
   auto value = [&](int32_t i) -> double {
     const int32_t q = cand[i];
     if (q < 0) return -INFINITY;
-    const double a = n == 0 ? (double)__ldg(S.theta_s + q) : S.pool_d[S.pool_base[p] + i];
+    const double a = n == 0 ? (double)__ldg(S.theta_s + q) : S.pool_d[base + i];
     return a + (double)__ldg(S.theta_f + q);
   };
   // the candidates sit in the pool in scheduling order: the sum is made
@@ -1034,7 +1053,6 @@ __global__ void __launch_bounds__(FT) k_fb_final(FrontierState S, double* __rest
       hi += red_hi[i] + ((lo < red_lo[i]) ? 1ull : 0ull);
     }
     const double sum = ((double)hi * 18446744073709551616.0 + (double)lo) * 2.168404344971009e-19;  // 2^64, 2^-62
-    const uint32_t err = S.flags[1] & (ERR_POOL | ERR_TIMEOUT);
     const double cp = c_prev;
     double lz = -INFINITY;
     if (!err && mx != -INFINITY && cp != -INFINITY) lz = cp + mx + log(sum);

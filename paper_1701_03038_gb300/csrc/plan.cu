@@ -458,9 +458,9 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
     // relaxations of one pass (the paper's definition: every arc of every slice)
     P->relax = 0;
     for (int64_t i = 0; i < N; ++i) P->relax += f->h_sym_arc[hid[i] + 1] - f->h_sym_arc[hid[i]];
-    // waves: consecutive strings whose memory fits the budget
-    // default: half the device memory free now, at least 16 GiB (a batch in
-    // fewer waves makes fewer, fuller launches)
+    // waves: consecutive strings whose memory fits the budget.  Default: a
+    // quarter of the device memory free now, at most 32 GiB and at least
+    // 256 MiB (the GPU may be shared; fst_set_batch_budget raises it)
     int64_t budget = mem_budget_bytes;
     if (budget <= 0) {
       size_t free_b = 0, total_b = 0;
@@ -468,7 +468,7 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
         (void)cudaGetLastError();
         free_b = 0;
       }
-      budget = std::max<int64_t>((int64_t)16 << 30, (int64_t)(free_b / 2));
+      budget = std::max<int64_t>((int64_t)256 << 20, std::min<int64_t>((int64_t)32 << 30, (int64_t)(free_b / 4)));
     }
     // accumulators: 2 x 8 bytes per state (Viterbi), or 2 x 16 for the
     // forward sums and maxima plus 2 x 8 for the backward values; Viterbi
@@ -563,6 +563,10 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
     if (ce == cudaSuccess && P->beta) ce = cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(P->flags_d, 0, 8, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(P->gbar, 0, 8, s);
+    // per-token pool ranges start empty: a run that stops early leaves the
+    // later positions' ranges as the previous run (or this clear) left them
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(P->pool_base, 0, (size_t)std::max<int64_t>(nt, 1) * 8, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(P->pool_cnt, 0, (size_t)std::max<int64_t>(nt, 1) * 4, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) rc = cuda_fail(ce, "plan storage");
   } while (0);
@@ -716,7 +720,7 @@ extern "C" int fst_viterbi_batch(fst_t* f, const int32_t* d_ids, const int64_t* 
                                  void* stream) {
   if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
   fst_plan_t* P = nullptr;
-  int rc = plan_create(f, d_ids, d_offsets, B, 0, FST_PLAN_NO_FB, stream, take_cached(f, 0), &P);
+  int rc = plan_create(f, d_ids, d_offsets, B, f->batch_budget, FST_PLAN_NO_FB, stream, take_cached(f, 0), &P);
   if (rc) return rc;
   rc = fst_plan_viterbi(P, d_scores, d_paths, d_olabels, d_status, stream);
   cudaError_t e = cudaStreamSynchronize(as_stream(stream));
@@ -730,7 +734,7 @@ extern "C" int fst_forward_backward_batch(fst_t* f, const int32_t* d_ids, const 
                                           int32_t* d_status, void* stream) {
   if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
   fst_plan_t* P = nullptr;
-  int rc = plan_create(f, d_ids, d_offsets, B, 0, FST_PLAN_NO_VITERBI, stream, take_cached(f, 1), &P);
+  int rc = plan_create(f, d_ids, d_offsets, B, f->batch_budget, FST_PLAN_NO_VITERBI, stream, take_cached(f, 1), &P);
   if (rc) return rc;
   rc = fst_plan_forward_backward(P, d_weights, d_logz, d_counts, d_status, stream);
   cudaError_t e = cudaStreamSynchronize(as_stream(stream));
@@ -1000,4 +1004,10 @@ extern "C" int fst_plan_profile(fst_plan_t* P, int32_t enable) {
 extern "C" int fst_plan_profile_read(fst_plan_t* P, double* ms_by_kind, int64_t* launches_by_kind) {
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
   return P->prof.read(ms_by_kind, launches_by_kind);
+}
+
+extern "C" int fst_set_batch_budget(fst_t* f, int64_t mem_budget_bytes) {
+  if (!f || mem_budget_bytes < 0) { set_error("fst_set_batch_budget: bad arguments"); return FST_ERR_INVALID_ARG; }
+  f->batch_budget = mem_budget_bytes;
+  return FST_OK;
 }

@@ -232,6 +232,11 @@ class Fst:
         return dict(entries=e.value, arcs=a.value)
 
     # ------------------------------------------------------ batched method
+    def set_batch_budget(self, nbytes: int):
+        """Storage budget of the plans built by viterbi_batch and
+        forward_backward_batch (0 = the library default)."""
+        check(self._lib.fst_set_batch_budget(self._h, int(nbytes)), "fst_set_batch_budget")
+
     def plan(self, ids: torch.Tensor, offsets: torch.Tensor, mem_budget: int = 0, flags: int = 0,
              stream=None) -> "Plan":
         return Plan(self, ids, offsets, mem_budget=mem_budget, flags=flags, stream=stream)
