@@ -4,7 +4,12 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never does.
 
 The arithmetic lives in ``oracle.c`` (plain C, compiled on first use into
-``oracle/_build/liboracle.so``); this module only marshals numpy arrays.
+``oracle/_build/liboracle.so``); this module only marshals numpy arrays,
+except for ``Fst.clamped``, which writes down the output-clamped problem of
+a pair (x, y) by its definition (the arcs read the pair of their input and
+output labels) so that ``forward_backward_clamped`` is the pinned
+forward-backward of that problem.  Pins: brute-force enumeration of the paths
+of x that write y, and sum_y Z(x, y) = Z(x).
 Inputs are FSTs in the cost domain (w = -log p), as produced by
 ``paper_1701_03038_gb300.synth``; they are turned into natural-log weights
 theta = -w here, with -0.0 stored as +0.0 and +inf costs as -inf.
@@ -55,8 +60,9 @@ def _declare(lib):
     lib.oracle_forward_backward.argtypes = fst + [i32p, C.c_int32, f64p, vp, vp, vp]
     lib.oracle_viterbi_batch.argtypes = fst + [i32p, i64p, C.c_int32, C.c_int32, f32p, i32p, i32p]
     lib.oracle_fb_batch.argtypes = fst + [i32p, i64p, C.c_int32, C.c_int32, vp, f64p, vp, i32p]
+    lib.oracle_em_update.argtypes = [C.c_int32, C.c_int64, i32p, f64p, f32p, C.c_double, f64p]
     for f in (lib.oracle_viterbi, lib.oracle_forward_backward, lib.oracle_viterbi_batch,
-              lib.oracle_fb_batch):
+              lib.oracle_fb_batch, lib.oracle_em_update):
         f.restype = C.c_int
     return lib
 
@@ -199,3 +205,46 @@ class Fst:
         if rc:
             raise RuntimeError(f"oracle_fb_batch failed: {rc}")
         return dict(logz=logz[:B], counts=None if cs is None else cs[:self.A], status=status[:B])
+
+    # ------------------------------------------------------------ training
+    def em_update(self, counts, alpha: float = 0.0) -> np.ndarray:
+        """EM re-estimation (see oracle_em_update in oracle.c): float64 log-weights
+        theta'_k = log((count_k + alpha) / sum over the arcs of src_k of
+        (count + alpha)); states with a zero total keep their old weights."""
+        c = np.ascontiguousarray(counts, np.float64)
+        out = np.zeros(max(self.A, 1), np.float64)
+        rc = self.lib.oracle_em_update(self.Q, self.A, self.src, c, self.theta, float(alpha), out)
+        if rc:
+            raise RuntimeError(f"oracle_em_update failed: {rc}")
+        return out[:self.A]
+
+    def clamped(self, x, y):
+        """The output-clamped problem of (x, y): the paths that read x and
+        write y are the paths of the FST whose arc k reads the pair
+        (ilabel_k, olabel_k), run on the string of pairs (x_t, y_t).  Returns
+        (an Fst view of that FST, the pair string); a pair no arc carries maps
+        to a symbol without arcs.  Arc ids, weights and states are unchanged,
+        so counts stay per original arc."""
+        x = np.asarray(x, np.int64)
+        y = np.asarray(y, np.int64)
+        if x.shape != y.shape:
+            raise ValueError("x and y differ in length")
+        pairs = {}
+        lab = np.zeros(self.A, np.int32)
+        for k in range(self.A):
+            key = (int(self.ilabel[k]), int(self.olabel[k]))
+            lab[k] = pairs.setdefault(key, len(pairs))
+        absent = len(pairs)
+        xs = np.array([pairs.get((int(a), int(b)), absent) for a, b in zip(x, y)], np.int32)
+        v = Fst.__new__(Fst)
+        v.Q, v.A, v.m = self.Q, self.A, absent + 1
+        v.src, v.dst, v.ilabel, v.olabel = self.src, self.dst, lab, self.olabel
+        v.theta, v.theta_s, v.theta_f, v.lib = self.theta, self.theta_s, self.theta_f, self.lib
+        return v, xs
+
+    def forward_backward_clamped(self, x, y):
+        """log Z(x, y) (the total weight of the paths reading x and writing
+        y) and the arc posteriors given both: forward-backward of the
+        output-clamped problem."""
+        v, xs = self.clamped(x, y)
+        return v.forward_backward(xs)

@@ -31,9 +31,14 @@
  *     would produce NaN from -inf - -inf);
  *   - the delta[w] in the count update of Alg. 2 is delta[w_{t+1}].
  *
+ * Training (Sec. 4: the expected counts serve EM): oracle_em_update sets
+ * each state's outgoing arc weights to its normalised expected counts.
+ *
  * Parity status: every function below is pinned by the non-GPU tests
  * (worked example of Figs. 1-2, brute-force path enumeration, a dense HMM,
- * single-state and unweighted closed forms, and the alpha-beta invariants).
+ * single-state and unweighted closed forms, the alpha-beta invariants; for
+ * the EM update the worked example's counts, per-state normalisation, the
+ * pseudo-count closed form and the monotone likelihood of EM).
  *
  * Build: gcc -O2 -ffp-contract=off -std=c11 -shared -fPIC (no FMA
  * contraction, so each float32 candidate is one rounded addition).
@@ -396,4 +401,33 @@ int oracle_fb_batch(FST_ARGS, const int32_t *ids, const int64_t *off, int32_t B,
     }
     free_index(&ix);
     return rc;
+}
+
+/*
+ * EM re-estimation of the arc weights from expected counts (the use the
+ * paper gives the counts of Alg. 2: training by expectation-maximisation,
+ * Sec. 4).  Each state's outgoing arcs form one categorical distribution, so
+ * the M-step sets
+ *
+ *     p'_k = (count_k + alpha) / sum_{j: src_j = src_k} (count_j + alpha)
+ *
+ * (alpha >= 0 a pseudo-count added to every arc) and returns theta'_k =
+ * log p'_k in float64.  A state whose arcs have a zero total (never used and
+ * alpha = 0) keeps its arcs' old log-weights.
+ */
+int oracle_em_update(int32_t Q, int64_t A, const int32_t *src, const double *counts, const float *theta,
+                     double alpha, double *theta_out)
+{
+    if (Q < 1 || A < 0 || !(alpha >= 0.0)) return OR_INVALID;
+    for (int64_t k = 0; k < A; ++k)
+        if (src[k] < 0 || src[k] >= Q || !(counts[k] >= 0.0)) return OR_INVALID;
+    double *total = (double *)calloc((size_t)Q, sizeof(double));
+    if (!total) return OR_OOM;
+    for (int64_t k = 0; k < A; ++k) total[src[k]] += counts[k] + alpha;
+    for (int64_t k = 0; k < A; ++k) {
+        const double t = total[src[k]];
+        theta_out[k] = t > 0.0 ? log((counts[k] + alpha) / t) : (double)theta[k];
+    }
+    free(total);
+    return OR_OK;
 }

@@ -425,5 +425,140 @@ def pin_state_posteriors(lib, cases=120, seed=17):
     assert seen > 20
 
 
+# --------------------------------------------------------------------------
+# Output-clamped log Z (the numerator of a conditional / CRF likelihood)
+# --------------------------------------------------------------------------
+def pin_clamped_bruteforce(lib, cases=150, seed=19):
+    """log Z(x, y) and the arc posteriors given x and y against the accepting
+    paths of x whose output labels spell y, enumerated; y is the output of
+    a random accepting path half of the time, else random."""
+    rng = np.random.default_rng(seed)
+    seen = 0
+    for _ in range(cases):
+        fst = synth.tiny_fst(rng)
+        n = int(rng.integers(0, 5))
+        x = rng.integers(0, fst.num_isyms, size=n).astype(np.int32)
+        paths = enumerate_paths(fst, x)
+        if paths and rng.random() < 0.5:
+            seq = paths[int(rng.integers(0, len(paths)))][0]
+            y = np.array([fst.olabel[k] for k in seq], np.int32)
+        else:
+            y = rng.integers(0, 4, size=n).astype(np.int32)
+        keep = [p for p in paths if tuple(int(fst.olabel[k]) for k in p[0]) == tuple(int(v) for v in y)]
+        r = oracle.Fst(fst, lib).forward_backward_clamped(x, y)
+        if not keep:
+            assert r["logz"] == -math.inf and np.all(r["counts"] == 0)
+            continue
+        seen += 1
+        logz = _lse([p[2] for p in keep])
+        assert abs(r["logz"] - logz) <= 1e-12 * max(1.0, abs(logz))
+        cnt = np.zeros(fst.num_arcs)
+        for seq, _, w64, _ in keep:
+            for k in seq:
+                cnt[k] += math.exp(w64 - logz)
+        assert np.allclose(r["counts"], cnt, atol=1e-12, rtol=1e-12)
+    assert seen > 30
+
+
+def pin_clamped_marginal(lib, cases=40, seed=23):
+    """Summing Z(x, y) over every output string y of length n gives Z(x):
+    each path writes exactly one y."""
+    rng = np.random.default_rng(seed)
+    for _ in range(cases):
+        fst = synth.tiny_fst(rng)
+        n = int(rng.integers(0, 4))
+        x = rng.integers(0, fst.num_isyms, size=n).astype(np.int32)
+        o = oracle.Fst(fst, lib)
+        want = o.forward_backward(x)["logz"]
+        got = _lse([o.forward_backward_clamped(x, np.array(y, np.int32))["logz"]
+                    for y in itertools.product(range(4), repeat=n)])
+        if want == -math.inf:
+            assert got == -math.inf
+        else:
+            assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
+
+
+# --------------------------------------------------------------------------
+# EM re-estimation from expected counts (Sec. 4: the counts serve EM)
+# --------------------------------------------------------------------------
+def pin_em_fig1(lib):
+    """Worked example: the counts of "le chat </s>" are 6/7, 1/7 on the two
+    arcs out of state 0 and the same on the single arcs of states 1-4, so
+    the M-step gives log 6/7, log 1/7 and log 1 = 0 elsewhere; with a
+    pseudo-count of 1, state 0 gets (6/7 + 1) / 3 = 13/21 and 8/21."""
+    fst, x, _, _, post = fig1_case()
+    o = oracle.Fst(fst, lib)
+    c = o.forward_backward(x)["counts"]
+    assert np.allclose(c, post, atol=1e-6)
+    exact = np.array(post, np.float64)
+    th = o.em_update(exact)
+    want = np.log([6 / 7, 1 / 7, 1.0, 1.0, 1.0, 1.0])
+    assert np.allclose(th, want, atol=1e-14, rtol=0)
+    th1 = o.em_update(exact, alpha=1.0)
+    want1 = np.log([13 / 21, 8 / 21, 1.0, 1.0, 1.0, 1.0])
+    assert np.allclose(th1, want1, atol=1e-14, rtol=0)
+
+
+def pin_em_invariants(lib, cases=60, seed=29):
+    """On random FSTs: each used state's new arc probabilities sum to one,
+    unused states keep their weights, the pseudo-count closed form holds,
+    and an EM step from normalised weights never lowers the likelihood
+    sum_b log Z(x_b) (the M-step maximises the expected complete
+    log-likelihood over per-state distributions)."""
+    rng = np.random.default_rng(seed)
+    rises = 0
+    for _ in range(cases):
+        fst = synth.tiny_fst(rng, max_states=5, max_arcs=12)
+        o = oracle.Fst(fst, lib)
+        # normalised starting weights: each state's arcs as a distribution
+        p0 = np.exp(o.theta.astype(np.float64))
+        tot = np.bincount(fst.src, weights=p0, minlength=fst.num_states)
+        th0 = np.log(p0 / tot[fst.src])
+        fa = synth.FstArrays(fst.num_states, fst.num_isyms, fst.num_osyms, fst.src, fst.dst, fst.ilabel,
+                             fst.olabel, (-th0).astype(np.float32), fst.start_weight, fst.final_weight)
+        o = oracle.Fst(fa, lib)
+        xs = [rng.integers(0, fst.num_isyms, size=int(rng.integers(1, 5))).astype(np.int32) for _ in range(4)]
+        fbs = [o.forward_backward(x) for x in xs]
+        if all(r["logz"] == -math.inf for r in fbs):
+            continue
+        L0 = sum(r["logz"] for r in fbs if r["logz"] > -math.inf)
+        counts = sum(r["counts"] for r in fbs)
+        th1 = o.em_update(counts)
+        used = np.bincount(fst.src, weights=counts, minlength=fst.num_states) > 0
+        for q in range(fst.num_states):
+            arcs = np.flatnonzero(fst.src == q)
+            if arcs.size and used[q]:
+                assert abs(np.exp(th1[arcs]).sum() - 1.0) < 1e-12
+            elif arcs.size:
+                assert np.array_equal(th1[arcs], o.theta[arcs].astype(np.float64))
+        a = 0.5
+        th2 = o.em_update(counts, alpha=a)
+        den = np.bincount(fst.src, weights=counts + a, minlength=fst.num_states)
+        assert np.allclose(th2, np.log((counts + a) / den[fst.src]), atol=1e-12, rtol=0)
+        # the likelihood in float64 weights (float32 storage would blur a tiny rise)
+        L1 = sum(_lse([p[2] for p in _enum64(fa, th1, x)]) for x, r in zip(xs, fbs) if r["logz"] > -math.inf)
+        L0e = sum(_lse([p[2] for p in _enum64(fa, th0, x)]) for x, r in zip(xs, fbs) if r["logz"] > -math.inf)
+        assert abs(L0e - L0) < 1e-5 * max(1.0, abs(L0))
+        assert L1 >= L0e - 1e-9, (L1, L0e)
+        rises += L1 > L0e + 1e-9
+    assert rises > 10
+
+
+def _enum64(fst, theta64, x):
+    """Accepting paths of x with float64 arc log-weights theta64."""
+    ts = oracle.theta_of_cost(fst.start_weight).astype(np.float64)
+    tf = oracle.theta_of_cost(fst.final_weight).astype(np.float64)
+    cand = [np.flatnonzero(fst.ilabel == a) for a in x]
+    out = []
+    for seq in itertools.product(*cand):
+        if ts[fst.src[seq[0]]] == -np.inf or tf[fst.dst[seq[-1]]] == -np.inf:
+            continue
+        if not all(fst.dst[seq[i]] == fst.src[seq[i + 1]] for i in range(len(seq) - 1)):
+            continue
+        out.append((seq, None, ts[fst.src[seq[0]]] + sum(theta64[k] for k in seq) + tf[fst.dst[seq[-1]]]))
+    return out
+
+
 ALL_PINS = [pin_fig1, pin_bruteforce, pin_ties, pin_hmm, pin_single_state,
-            pin_unweighted_count, pin_invariants, pin_deterministic, pin_state_posteriors]
+            pin_unweighted_count, pin_invariants, pin_deterministic, pin_state_posteriors,
+            pin_clamped_bruteforce, pin_clamped_marginal, pin_em_fig1, pin_em_invariants]

@@ -24,6 +24,9 @@ MUTANTS = {
     "fb_backward_not_reversed": ("const int32_t *from = reverse ? f->dst : f->src;", "const int32_t *from = f->src;"),
     "counts_drop_beta": ("+ be[(size_t)t * Q + f->dst[k]] - logz;", "- logz;"),
     "counts_alpha_off_by_one": ("const double e = al[(size_t)(t - 1) * Q + f->src[k]]", "const double e = al[(size_t)t * Q + f->src[k]]"),
+    "em_reads_one_states_total": ("const double t = total[src[k]];", "const double t = total[0];"),
+    "em_drops_pseudo_count_in_total": ("total[src[k]] += counts[k] + alpha;", "total[src[k]] += counts[k];"),
+    "em_unused_states_get_minus_inf": (": (double)theta[k];", ": -INFINITY;"),
     "logz_drops_final_weight": ("s += exp(al[(size_t)n * Q + q] + (double)f->theta_f[q] - m);", "s += exp(al[(size_t)n * Q + q] - m);"),
 }
 
