@@ -252,6 +252,43 @@ FST_API int fst_plan_forward_backward_ex(fst_plan_t* plan, const float* d_weight
                                          float* d_counts, float* d_start, float* d_final, int32_t* d_status,
                                          void* stream);
 
+/* EM re-estimation of the arc weights from expected counts (the M-step of
+ * the training by expectation-maximisation that the counts of Alg. 2 serve,
+ * Sec. 4).  Each state's outgoing arcs (over all symbols) are one
+ * categorical distribution:
+ *     theta'_k = log((count_k + pseudo_count) / sum_{j: src_j = src_k} (count_j + pseudo_count)),
+ * computed in float64 and rounded to float32; a state whose arcs' total is
+ * zero keeps their current log-weights.
+ *   counts       [num_arcs] float expected counts (e.g. the d_counts of
+ *                fst_plan_backward), caller arc order, >= 0.
+ *   pseudo_count >= 0, added to every arc.
+ *   theta_out    [num_arcs] float: the new log-weights (caller-owned).
+ *   flags        FST_FLAG_DEVICE_PTRS: counts and theta_out are device
+ *                pointers (else host); FST_EM_APPLY: also install them as the
+ *                FST's weights (as fst_set_weights with FST_WEIGHT_LOG).
+ * Synchronous.  FST_ERR_INVALID_ARG for a negative, NaN or infinite count. */
+#define FST_EM_APPLY 2
+FST_API int fst_em_update(fst_t* fst, const float* counts, float pseudo_count, float* theta_out, int32_t flags);
+
+/* The output-clamped FST of `fst`, for the numerator log Z(x, y) of a
+ * conditional (CRF-style) likelihood: the weight of the paths that read x
+ * and write y (Eq. 1 restricted to the arcs whose output label is y_t at
+ * position t).  Its arc k is fst's arc k (same id, states and weight) with
+ * the input label replaced by the pair (ilabel_k, olabel_k); the pairs are
+ * numbered 0..*num_pairs-1 in (input, output) order and symbol *num_pairs
+ * has no arcs.  So log Z(x, y) and the arc posteriors given x and y are
+ * fst_forward_backward (or a plan) of the clamped FST on the pair string
+ * that fst_clamp_labels makes.  The handle is an ordinary FST (free it with
+ * fst_destroy); fst_set_weights takes the same weight vector as fst's. */
+FST_API int fst_create_clamped(const fst_t* fst, fst_t** out, int32_t* num_pairs);
+
+/* Pair string of (ids, olabels) for an FST made by fst_create_clamped: host
+ * arrays of length n; pair_ids[t] is the symbol of (ids[t], olabels[t]), or
+ * num_pairs (no arcs) when no arc carries that pair.  FST_ERR_STATE for a
+ * handle that is not a clamped FST. */
+FST_API int fst_clamp_labels(const fst_t* clamped, const int32_t* ids, const int32_t* olabels, int64_t n,
+                             int32_t* pair_ids);
+
 /* log Z of one string with every value and weight in float64 (the forward
  * recursion of Alg. 2 in the log domain; plain method, one launch per
  * position).  For finite-difference checks of d log Z / d theta, which a

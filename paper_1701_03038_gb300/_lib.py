@@ -19,6 +19,7 @@ PLAN_SINGLE_WAVE, PLAN_NO_VITERBI, PLAN_NO_FB = 1, 2, 4
 DRIVER_LAUNCH, DRIVER_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_BARRIER_STALL = 0, 1
 TUNE_REFRESH = 1
+EM_APPLY = 2
 
 _lock = threading.Lock()
 _lib = None
@@ -62,6 +63,9 @@ SIGNATURES = {
     "fst_plan_profile_read": [vp, vp, vp],
     "fst_viterbi_noalloc": [vp, vp, i32, vp, vp, vp, vp],
     "fst_log_z_f64": [vp, vp, vp, i32, vp],
+    "fst_em_update": [vp, vp, C.c_float, vp, i32],
+    "fst_create_clamped": [vp, C.POINTER(vp), vp],
+    "fst_clamp_labels": [vp, vp, vp, i64, vp],
 }
 
 PROF_KINDS = ["vit_first", "vit_step", "vit_final", "backtrace", "fwd_first", "fwd_sum", "fwd_step", "fb_final",

@@ -15,7 +15,7 @@ import torch
 
 from .fst import Fst, Plan
 
-__all__ = ["FstLogZ", "log_z", "LogZModule"]
+__all__ = ["FstLogZ", "log_z", "LogZModule", "crf_nll", "CrfModule"]
 
 
 class FstLogZ(torch.autograd.Function):
@@ -75,3 +75,30 @@ class LogZModule(torch.nn.Module):
 
     def forward(self, plan: Plan) -> torch.Tensor:
         return FstLogZ.apply(self.theta, self.fst, plan, self.theta_s, self.theta_f)
+
+
+def crf_nll(theta: torch.Tensor, fst: Fst, plan_x: Plan, clamped: Fst, plan_xy: Plan) -> torch.Tensor:
+    """Conditional negative log-likelihood -log p(y_b | x_b) = log Z(x_b) -
+    log Z(x_b, y_b) of every string pair, differentiable in the arc
+    log-weights: its gradient is the expected counts given x minus the
+    expected counts given x and y.  ``plan_x`` is a single-wave plan of
+    ``fst`` on the inputs x_b; ``plan_xy`` one of ``clamped``
+    (``fst.clamped()``) on the pair strings ``clamped.clamp(x_b, y_b)``, in
+    the same string order."""
+    return FstLogZ.apply(theta, fst, plan_x, None, None) - FstLogZ.apply(theta, clamped, plan_xy, None, None)
+
+
+class CrfModule(torch.nn.Module):
+    """Arc log-weights as a parameter of a conditional (CRF-style) model of
+    output strings given input strings; forward(plan_x, plan_xy) returns
+    -log p(y_b | x_b) per string (see crf_nll).  The clamped FST shares the
+    weights (it is rebuilt from the FST's arcs once)."""
+
+    def __init__(self, fst: Fst, theta0: torch.Tensor):
+        super().__init__()
+        self.fst = fst
+        self.clamped = fst.clamped()
+        self.theta = torch.nn.Parameter(theta0.detach().to(device=fst.device, dtype=torch.float32).clone())
+
+    def forward(self, plan_x: Plan, plan_xy: Plan) -> torch.Tensor:
+        return crf_nll(self.theta, self.fst, plan_x, self.clamped, plan_xy)

@@ -441,6 +441,8 @@ extern "C" int fst_destroy(fst_t* f) {
   }
   delete f->batch_mu;
   f->batch_mu = nullptr;
+  delete f->pair_keys;
+  f->pair_keys = nullptr;
   dfree(f->slice_arcs);
   dfree(f->slice_keys);
   delete f->plain;

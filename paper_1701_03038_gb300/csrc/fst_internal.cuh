@@ -132,6 +132,9 @@ struct fst_s {
   // storage the next call of that kind takes over
   struct fst_plan_s* batch_plan[2] = {nullptr, nullptr};
   int64_t batch_budget = 0;  // plan storage budget of the batch calls (0 = the plan default)
+  // an output-clamped FST (fst_create_clamped): the (input, output) label
+  // pair of each of its input symbols, ((uint64)ilabel << 32 | olabel), sorted
+  std::vector<uint64_t>* pair_keys = nullptr;
   std::mutex* batch_mu = nullptr;
   // the paper's slice-wide relaxation (fst_viterbi_slice): per-arc records
   // {src, dst, id} in the destination-segmented layout's order, and the

@@ -86,6 +86,16 @@ class Fst:
         self.num_isyms = int(num_isyms)
 
     @classmethod
+    def _wrap(cls, handle, num_states: int, num_arcs: int, num_isyms: int, device) -> "Fst":
+        """An Fst object around a handle the library made (e.g. fst_create_clamped)."""
+        f = cls.__new__(cls)
+        f._lib = _lib.load()
+        f._h = handle
+        f.device = device
+        f.num_states, f.num_arcs, f.num_isyms = int(num_states), int(num_arcs), int(num_isyms)
+        return f
+
+    @classmethod
     def from_arrays(cls, fa, device=None) -> "Fst":
         """Build from a ``synth.FstArrays`` (cost-domain weights)."""
         return cls(fa.num_states, fa.src, fa.dst, fa.ilabel, fa.olabel, fa.weight, fa.start_weight,
@@ -210,6 +220,52 @@ class Fst:
             check(self._lib.fst_log_z_f64(self._h, None if th is None else _hptr(th), _hptr(x), int(x.shape[0]),
                                           _hptr(lz)), "fst_log_z_f64")
         return float(lz[0])
+
+    # ------------------------------------------------------------ training
+    def em_update(self, counts, pseudo_count: float = 0.0, apply: bool = False):
+        """EM M-step (fst_em_update): new log-weights, each state's outgoing
+        arcs renormalised from their expected counts.  ``counts``: a CUDA
+        float32 tensor (returns a CUDA tensor) or a host array (returns
+        numpy).  ``apply`` also installs them as the FST's weights."""
+        flags = _lib.EM_APPLY if apply else 0
+        if isinstance(counts, torch.Tensor):
+            c = counts.detach().to(device=self.device, dtype=torch.float32).contiguous()
+            out = torch.empty(max(self.num_arcs, 1), dtype=torch.float32, device=self.device)
+            with torch.cuda.device(self.device):
+                torch.cuda.current_stream().synchronize()
+                check(self._lib.fst_em_update(self._h, _dptr(c), float(pseudo_count), _dptr(out),
+                                              flags | _lib.FLAG_DEVICE_PTRS), "fst_em_update")
+            return out[:self.num_arcs]
+        c = _host(counts, np.float32)
+        out = np.zeros(max(self.num_arcs, 1), np.float32)
+        with torch.cuda.device(self.device):
+            check(self._lib.fst_em_update(self._h, _hptr(c), float(pseudo_count), _hptr(out), flags),
+                  "fst_em_update")
+        return out[:self.num_arcs]
+
+    def clamped(self) -> "Fst":
+        """The output-clamped FST (fst_create_clamped): same arcs and ids, input
+        symbols = (input, output) label pairs; log Z(x, y) is its log Z on
+        the pair string clamp(x, y)."""
+        h = C.c_void_p()
+        npairs = C.c_int32()
+        with torch.cuda.device(self.device):
+            check(self._lib.fst_create_clamped(self._h, C.byref(h), C.byref(npairs)), "fst_create_clamped")
+        f = Fst._wrap(h, self.num_states, self.num_arcs, npairs.value + 1, self.device)
+        f.num_pairs = npairs.value
+        return f
+
+    def clamp(self, ids, olabels) -> np.ndarray:
+        """Pair string of an input string and an output string of the same
+        length (for a clamped FST; see fst_clamp_labels)."""
+        x = _host(ids, np.int32)
+        y = _host(olabels, np.int32)
+        if x.shape != y.shape:
+            raise ValueError("ids and olabels differ in length")
+        out = np.zeros(max(x.shape[0], 1), np.int32)
+        check(self._lib.fst_clamp_labels(self._h, _hptr(x), _hptr(y), int(x.shape[0]), _hptr(out)),
+              "fst_clamp_labels")
+        return out[:x.shape[0]]
 
     # ------------------------------------------------------- measurement
     def profile(self, enable: bool = True):
