@@ -141,6 +141,27 @@ FST_API int fst_viterbi(fst_t* fst, const int32_t* ids, int32_t n, float* best_s
  * frees them. */
 FST_API int fst_viterbi_slice(fst_t* fst, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path);
 
+/* The paper's forward-backward, kept for comparison (Sec. 5.2, Eq. 3): at
+ * every position each arc of the slice adds its value into its
+ * destination's forward value (backward: its source's backward value) with
+ * an atomic log-add-exp -- a compare-and-swap loop over
+ * log(e^a + e^b) = b + log1p(e^(a-b)), a <= b, with -inf + a = a -- on
+ * float32 log-probabilities kept for every position ((n+1) x num_states
+ * each, held by the handle), then log Z (float64 sum) and the per-arc
+ * posteriors of Alg. 2.  Arguments, results and errors as
+ * fst_forward_backward.  Its float32 values are not rescaled, so its
+ * posteriors drift with the string's length (see the tests). */
+FST_API int fst_forward_backward_slice(fst_t* fst, const int32_t* ids, int32_t n, double* log_z,
+                                       float* arc_posteriors);
+
+/* Order of the arcs within a slice for fst_viterbi_slice and
+ * fst_forward_backward_slice (the layout study of Sec. 4):
+ * FST_SLICE_BY_DESTINATION (column-major / CSC, the default) or
+ * FST_SLICE_BY_SOURCE (row-major / CSR, the paper's own order). */
+#define FST_SLICE_BY_DESTINATION 0
+#define FST_SLICE_BY_SOURCE 1
+FST_API int fst_set_slice_order(fst_t* fst, int32_t order);
+
 /* Plain method, one string: forward-backward (Alg. 2, Sec. 5.2).  Host
  * pointers; synchronous.
  *   log_z          host double: log of the total weight of the string (Eq. 1

@@ -20,6 +20,7 @@ DRIVER_LAUNCH, DRIVER_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_BARRIER_STALL = 0, 1
 TUNE_REFRESH = 1
 EM_APPLY = 2
+SLICE_BY_DESTINATION, SLICE_BY_SOURCE = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -37,6 +38,8 @@ SIGNATURES = {
     "fst_set_state_weights": [vp, vp, vp, i32, i32],
     "fst_viterbi": [vp, vp, i32, vp, vp, vp],
     "fst_viterbi_slice": [vp, vp, i32, vp, vp],
+    "fst_forward_backward_slice": [vp, vp, i32, vp, vp],
+    "fst_set_slice_order": [vp, i32],
     "fst_forward_backward": [vp, vp, i32, vp, vp],
     "fst_viterbi_batch": [vp, vp, vp, i32, vp, vp, vp, vp, vp],
     "fst_forward_backward_batch": [vp, vp, vp, i32, vp, vp, vp, vp, vp],

@@ -444,7 +444,9 @@ extern "C" int fst_destroy(fst_t* f) {
   delete f->pair_keys;
   f->pair_keys = nullptr;
   dfree(f->slice_arcs);
+  dfree(f->slice_arcs_src);
   dfree(f->slice_keys);
+  dfree(f->slice_fb);
   delete f->plain;
   f->plain = nullptr;
   free_layout(f->fwd);

@@ -139,9 +139,13 @@ struct fst_s {
   // the paper's slice-wide relaxation (fst_viterbi_slice): per-arc records
   // {src, dst, id} in the destination-segmented layout's order, and the
   // packed keys of every position of the last string
-  int4* slice_arcs = nullptr;
+  int4* slice_arcs = nullptr;      // in the destination-segmented (column-major) order
+  int4* slice_arcs_src = nullptr;  // in the source-segmented (row-major) order
+  int32_t slice_order = 0;         // FST_SLICE_BY_DESTINATION or FST_SLICE_BY_SOURCE
   unsigned long long* slice_keys = nullptr;
   int64_t slice_cap = 0;
+  float* slice_fb = nullptr;       // forward and backward tables of fst_forward_backward_slice
+  int64_t slice_fb_cap = 0;
 };
 
 namespace fstgpu {

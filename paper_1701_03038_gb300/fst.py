@@ -197,6 +197,24 @@ class Fst:
         check(rc, "fst_viterbi_slice", allow=(_lib.OK, _lib.NO_PATH))
         return best[0], path[:n], rc
 
+    def forward_backward_slice(self, ids, posteriors: bool = True):
+        """The paper's forward-backward (every arc of every slice, atomic
+        log-add-exp in float32), for comparison: (log Z, counts, status)."""
+        x = _host(ids, np.int32)
+        n = int(x.shape[0])
+        lz = np.zeros(1, np.float64)
+        cnt = np.zeros(max(self.num_arcs, 1), np.float32) if posteriors else None
+        with torch.cuda.device(self.device):
+            rc = self._lib.fst_forward_backward_slice(self._h, _hptr(x), n, _hptr(lz),
+                                                      _hptr(cnt) if posteriors else None)
+        check(rc, "fst_forward_backward_slice", allow=(_lib.OK, _lib.NO_PATH))
+        return float(lz[0]), (cnt[:self.num_arcs] if posteriors else None), rc
+
+    def set_slice_order(self, order: int):
+        """Arc order within a slice for the paper-design calls:
+        _lib.SLICE_BY_DESTINATION (column-major) or _lib.SLICE_BY_SOURCE (row-major)."""
+        check(self._lib.fst_set_slice_order(self._h, int(order)), "fst_set_slice_order")
+
     def forward_backward(self, ids, posteriors: bool = True):
         """(log Z float64, expected arc counts float32[A] or None, status)."""
         x = _host(ids, np.int32)

@@ -204,3 +204,44 @@ def test_slice_relaxation_is_bit_identical():
                 s2, p2, _, _ = f.viterbi(x)
                 assert s1 == s2 and np.array_equal(p1, p2)
 
+
+
+def test_slice_orders_and_paper_forward_backward():
+    # the paper's design, both arc orders within a slice (by destination /
+    # column-major, by source / row-major): Viterbi bit-identical to the
+    # oracle; the float32 atomic log-add forward-backward (Eq. 3) within
+    # 1e-5 of log Z, its posteriors within the looser bound that float32
+    # values without rescaling can keep over these lengths
+    from paper_1701_03038_gb300 import _lib
+    rng = np.random.default_rng(23)
+    cases = [(synth.fig1_fst(), [np.array([0, 1, 2], np.int32), np.zeros(0, np.int32)])]
+    for _ in range(6):
+        fa = synth.tiny_fst(rng)
+        cases.append((fa, [rng.integers(0, fa.num_isyms, size=int(rng.integers(0, 7))).astype(np.int32)
+                           for _ in range(4)]))
+    fa, strs = synth.make_config("c1", scale=1.0, strings=2)
+    cases.append((fa, [strs.get(b) for b in range(strs.count)]))
+    fa, strs = synth.make_config("c2", scale=0.02, strings=4)
+    cases.append((fa, [strs.get(b) for b in range(strs.count)]))
+    worst = 0.0
+    for fa, xs in cases:
+        f, o = _fst(fa), oracle.Fst(fa)
+        for order in (_lib.SLICE_BY_DESTINATION, _lib.SLICE_BY_SOURCE):
+            f.set_slice_order(order)
+            for x in xs:
+                ov = o.viterbi(x)
+                s1, p1, st = f.viterbi_slice(x)
+                assert st == ov["status"]
+                assert s1 == ov["best"] or (np.isinf(ov["best"]) and s1 == ov["best"])
+                if st == 0:
+                    assert np.array_equal(p1, ov["path"])
+                ofb = o.forward_backward(x)
+                lz, cnt, st2 = f.forward_backward_slice(x)
+                assert st2 == ofb["status"]
+                assert_logz_close(lz, ofb["logz"])
+                err = float(np.abs(cnt.astype(np.float64) - ofb["counts"]).max()) if fa.num_arcs else 0.0
+                worst = max(worst, err)
+                assert err <= 5e-4, (order, err)
+    print(f"paper forward-backward: largest posterior error {worst:.2e}")
+    with pytest.raises(_lib.FstError):
+        f.set_slice_order(2)
