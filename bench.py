@@ -575,30 +575,45 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
         out["plain"] = {"value": rx / dt, "unit": UNIT, "sentences_per_s": n / dt,
                         "sample": f"first {n} strings, host API (fst_viterbi + fst_forward_backward)"}
         out["batched_over_plain_sentences"] = out["sentences_per_s"] / world / (n / dt)
-        # the paper's own relaxation (every arc of every slice, one thread
-        # per arc, packed atomicMax) against the frontier-driven plain path,
-        # Viterbi only, on the first strings
-        k = min(args.slice_sample, strs.count)
-        f.viterbi_slice(strs.get(0))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for b in range(k):
-            f.viterbi_slice(strs.get(b))
-        dt_slice = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        for b in range(k):
-            f.viterbi(strs.get(b))
-        dt_ours = time.perf_counter() - t0
-        out["paper_design"] = {"sample": f"first {k} strings, Viterbi, one string at a time",
-                               "slice_relaxation_sentences_per_s": k / dt_slice,
-                               "frontier_plain_sentences_per_s": k / dt_ours,
-                               "speedup": dt_slice / dt_ours}
+        out["paper_design"] = paper_design(f, strs, args.slice_sample)
 
     # end to end through the public batch API with host buffers (the batch
     # calls' plans get the same storage budget as the timed plans)
     if not args.no_e2e:
         f.set_batch_budget(budget)
         out["e2e"] = e2e_batch(args, world, dev, fa, strs, f, s_v, s_f, 3 * relax_pass)
+    return out
+
+
+def paper_design(f, strs, k):
+    """The paper's slice-wide relaxation (every arc of every slice, one thread
+    per arc; Viterbi by packed atomicMax, forward-backward by float32 atomic
+    log-add-exp) in both arc orders within a slice, against the frontier
+    plain path, one string at a time on the first k strings (sentences/s)."""
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    xs = [strs.get(b) for b in range(min(k, strs.count))]
+
+    def rate(fn):
+        fn(xs[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for x in xs:
+            fn(x)
+        return len(xs) / (time.perf_counter() - t0)
+
+    out = {"sample": f"first {len(xs)} strings, one string at a time (host API)",
+           "frontier": {"viterbi_sentences_per_s": rate(f.viterbi),
+                        "fb_sentences_per_s": rate(f.forward_backward)}}
+    for name, order in (("by_destination", _lib.SLICE_BY_DESTINATION), ("by_source", _lib.SLICE_BY_SOURCE)):
+        f.set_slice_order(order)
+        out["slice_" + name] = {"viterbi_sentences_per_s": rate(f.viterbi_slice),
+                                "fb_sentences_per_s": rate(f.forward_backward_slice)}
+    f.set_slice_order(_lib.SLICE_BY_DESTINATION)
+    out["viterbi_frontier_over_slice"] = (out["frontier"]["viterbi_sentences_per_s"]
+                                          / out["slice_by_destination"]["viterbi_sentences_per_s"])
+    out["fb_frontier_over_slice"] = (out["frontier"]["fb_sentences_per_s"]
+                                     / out["slice_by_destination"]["fb_sentences_per_s"])
     return out
 
 
@@ -724,22 +739,9 @@ def bench_plain(args, rank, world, dev, fa, strs, f, stats):
                           "value": relax_step / (bms / 1000.0), "unit": UNIT,
                           "how": "the same strings as one plan each for Viterbi and forward-backward, host launches"}
         out["batched_over_plain_sentences"] = out["batched"]["sentences_per_s"] / (out["sentences_per_s"] / world)
-    # the paper's slice-wide relaxation on the same strings (Viterbi)
+    # the paper's slice-wide relaxation on the same strings
     if rank == 0:
-        k = min(args.slice_sample, strs.count)
-        f.viterbi_slice(strs.get(0))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for b in range(k):
-            f.viterbi_slice(strs.get(b))
-        dt_slice = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        for b in range(k):
-            f.viterbi(strs.get(b))
-        dt_ours = time.perf_counter() - t0
-        out["paper_design"] = {"sample": f"first {k} strings, Viterbi, one string at a time",
-                               "slice_relaxation_sentences_per_s": k / dt_slice,
-                               "frontier_plain_sentences_per_s": k / dt_ours, "speedup": dt_slice / dt_ours}
+        out["paper_design"] = paper_design(f, strs, args.slice_sample)
     return out
 
 
