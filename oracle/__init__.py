@@ -9,7 +9,11 @@ except for ``Fst.clamped``, which writes down the output-clamped problem of
 a pair (x, y) by its definition (the arcs read the pair of their input and
 output labels) so that ``forward_backward_clamped`` is the pinned
 forward-backward of that problem.  Pins: brute-force enumeration of the paths
-of x that write y, and sum_y Z(x, y) = Z(x).
+of x that write y, and sum_y Z(x, y) = Z(x).  ``lattice_viterbi`` and
+``lattice_forward_backward`` (an acyclic input lattice composed with the
+FST, Sec. 6.1) are plain loops over the edges in node order, pinned by the
+linear lattice of a string (which must decode exactly as the string) and by
+brute force over every (lattice path, FST path) pair.
 Inputs are FSTs in the cost domain (w = -log p), as produced by
 ``paper_1701_03038_gb300.synth``; they are turned into natural-log weights
 theta = -w here, with -0.0 stored as +0.0 and +inf costs as -inf.
@@ -248,3 +252,129 @@ class Fst:
         output-clamped problem."""
         v, xs = self.clamped(x, y)
         return v.forward_backward(xs)
+
+
+# ---------------------------------------------------------------- lattices
+class Lattice:
+    """An acyclic input lattice: nodes 0..num_nodes-1, node 0 the start and
+    node num_nodes-1 the end; edge e goes from frm[e] to to[e] > frm[e],
+    reads symbol label[e] and carries log-weight weight[e] (float32)."""
+
+    def __init__(self, num_nodes, frm, to, label, weight):
+        self.N = int(num_nodes)
+        self.frm = np.asarray(frm, np.int64)
+        self.to = np.asarray(to, np.int64)
+        self.label = np.asarray(label, np.int64)
+        self.weight = np.asarray(weight, np.float32)
+        self.E = int(self.frm.shape[0])
+        if self.N < 1 or np.any(self.frm >= self.to) or np.any(self.frm < 0) or np.any(self.to >= self.N):
+            raise ValueError("edges must go from a lower to a higher node id within [0, num_nodes)")
+
+    @classmethod
+    def from_string(cls, x):
+        """The linear lattice of a string: edge t reads x_t, weight 0."""
+        n = len(x)
+        return cls(n + 1, np.arange(n), np.arange(1, n + 1), np.asarray(x), np.zeros(n, np.float32))
+
+
+def lattice_viterbi(o: Fst, lat: Lattice):
+    """Viterbi over an input lattice composed with the FST, node by node in
+    id order (a topological order), float32 as the string case: a candidate
+    through edge e = (u -> v) and arc k is fl(fl(V[u][src_k] + theta_k) +
+    w_e); the best wins, ties to the lowest arc id, then the lowest edge id.
+    At the end node the best state adds its final weight (lowest state on
+    ties).  Returns dict(status, best, edges[L], arcs[L]) along the best
+    path (L = its number of edges)."""
+    Q, N = o.Q, lat.N
+    NEG = np.float32(-np.inf)
+    V = np.full((N, Q), NEG, np.float32)
+    V[0] = o.theta_s
+    bk = np.full((N, Q), -1, np.int64)  # best arc
+    be = np.full((N, Q), -1, np.int64)  # its edge
+    by_label = {}
+    for k in range(o.A):
+        by_label.setdefault(int(o.ilabel[k]), []).append(k)
+    order = np.lexsort((np.arange(lat.E), lat.to))  # by destination node, then edge id
+    for e in order:
+        u, v, w = int(lat.frm[e]), int(lat.to[e]), np.float32(lat.weight[e])
+        for k in by_label.get(int(lat.label[e]), []):
+            s, d = int(o.src[k]), int(o.dst[k])
+            if V[u][s] == NEG:
+                continue
+            c = np.float32(np.float32(V[u][s] + o.theta[k]) + w)
+            if c == NEG:
+                continue
+            if c > V[v][d] or (c == V[v][d] and k < bk[v][d]):
+                V[v][d], bk[v][d], be[v][d] = c, k, e
+    best, qb = NEG, -1
+    for q in range(Q):
+        c = np.float32(V[N - 1][q] + o.theta_f[q])
+        if c > best:
+            best, qb = c, q
+    if qb < 0:
+        return dict(status=NO_PATH, best=NEG, edges=np.zeros(0, np.int32), arcs=np.zeros(0, np.int32))
+    edges, arcs = [], []
+    v, q = N - 1, qb
+    while v != 0 or bk[v][q] >= 0:
+        k, e = int(bk[v][q]), int(be[v][q])
+        if k < 0:
+            break
+        edges.append(e)
+        arcs.append(k)
+        v, q = int(lat.frm[e]), int(o.src[k])
+    return dict(status=OK, best=best, edges=np.array(edges[::-1], np.int32), arcs=np.array(arcs[::-1], np.int32))
+
+
+def _lse(v):
+    v = np.asarray(v, np.float64)
+    if v.size == 0:
+        return -np.inf
+    m = v.max()
+    if m == -np.inf:
+        return -np.inf
+    return float(m + np.log(np.exp(v - m).sum()))
+
+
+def lattice_forward_backward(o: Fst, lat: Lattice):
+    """Forward-backward over an input lattice composed with the FST, float64:
+    alpha[v][q'] = LSE over edges e = (u -> v) and arcs k = (q -> q') on the
+    edge's symbol of alpha[u][q] + w_e + theta_k (alpha[0] = theta_s);
+    beta[u][q] likewise towards the end node (beta[N-1] = theta_f); log Z =
+    LSE_q(alpha[N-1][q] + theta_f[q]); the posterior of arc k is the sum over
+    the edges reading its symbol of exp(alpha[u][src_k] + w_e + theta_k +
+    beta[v][dst_k] - log Z), and that of edge e the sum over its arcs.
+    Returns dict(status, logz, counts[A], edge_post[E])."""
+    Q, N = o.Q, lat.N
+    th = o.theta.astype(np.float64)
+    al = np.full((N, Q), -np.inf)
+    al[0] = o.theta_s.astype(np.float64)
+    be = np.full((N, Q), -np.inf)
+    be[N - 1] = o.theta_f.astype(np.float64)
+    arcs_of = {a: np.flatnonzero(o.ilabel == a) for a in set(lat.label.tolist())}
+    into = [[e for e in range(lat.E) if lat.to[e] == v] for v in range(N)]
+    outof = [[e for e in range(lat.E) if lat.frm[e] == v] for v in range(N)]
+    for v in range(1, N):
+        terms = [[] for _ in range(Q)]
+        for e in into[v]:
+            u, w = int(lat.frm[e]), float(lat.weight[e])
+            for k in arcs_of[int(lat.label[e])]:
+                terms[int(o.dst[k])].append(al[u][o.src[k]] + w + th[k])
+        al[v] = [_lse(t) for t in terms]
+    for v in range(N - 2, -1, -1):
+        terms = [[] for _ in range(Q)]
+        for e in outof[v]:
+            t, w = int(lat.to[e]), float(lat.weight[e])
+            for k in arcs_of[int(lat.label[e])]:
+                terms[int(o.src[k])].append(w + th[k] + be[t][o.dst[k]])
+        be[v] = [_lse(x) for x in terms]
+    logz = _lse(al[N - 1] + o.theta_f.astype(np.float64))
+    counts = np.zeros(o.A)
+    epost = np.zeros(lat.E)
+    if logz > -np.inf:
+        for e in range(lat.E):
+            u, v, w = int(lat.frm[e]), int(lat.to[e]), float(lat.weight[e])
+            for k in arcs_of[int(lat.label[e])]:
+                g = np.exp(al[u][o.src[k]] + w + th[k] + be[v][o.dst[k]] - logz)
+                counts[k] += g
+                epost[e] += g
+    return dict(status=OK if logz > -np.inf else NO_PATH, logz=logz, counts=counts, edge_post=epost)

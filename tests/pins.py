@@ -559,6 +559,106 @@ def _enum64(fst, theta64, x):
     return out
 
 
+# --------------------------------------------------------------------------
+# Acyclic input lattices (Sec. 6.1: an FST composed with an input lattice)
+# --------------------------------------------------------------------------
+def random_dag(rng, num_isyms, max_nodes=5, max_edges=7):
+    n = int(rng.integers(1, max_nodes + 1))
+    frm, to = [], []
+    if n > 1:
+        for _ in range(int(rng.integers(1, max_edges + 1))):
+            u = int(rng.integers(0, n - 1))
+            frm.append(u)
+            to.append(int(rng.integers(u + 1, n)))
+    e = len(frm)
+    return oracle.Lattice(n, frm, to, rng.integers(0, num_isyms, size=e),
+                          (-rng.random(e) * 2.0).astype(np.float32))
+
+
+def lattice_paths(lat, v=0):
+    """Edge sequences from node v to the end node."""
+    if v == lat.N - 1:
+        return [()]
+    out = []
+    for e in range(lat.E):
+        if lat.frm[e] == v:
+            out += [(e,) + rest for rest in lattice_paths(lat, int(lat.to[e]))]
+    return out
+
+
+def pin_lattice_chain(lib, cases=60, seed=31):
+    """A string written as a linear lattice (edge weights 0) decodes exactly
+    as the string: the same Viterbi score and arcs, log Z and counts."""
+    rng = np.random.default_rng(seed)
+    for _ in range(cases):
+        fst = synth.tiny_fst(rng)
+        x = rng.integers(0, fst.num_isyms, size=int(rng.integers(0, 6))).astype(np.int32)
+        o = oracle.Fst(fst, lib)
+        lat = oracle.Lattice.from_string(x)
+        v, lv = o.viterbi(x), oracle.lattice_viterbi(o, lat)
+        assert lv["status"] == v["status"] and lv["best"] == v["best"]
+        if v["status"] == oracle.OK:
+            assert np.array_equal(lv["arcs"], v["path"]) and np.array_equal(lv["edges"], np.arange(len(x)))
+        fb, lfb = o.forward_backward(x), oracle.lattice_forward_backward(o, lat)
+        assert lfb["status"] == fb["status"]
+        if fb["logz"] == -math.inf:
+            assert lfb["logz"] == -math.inf
+        else:
+            assert abs(lfb["logz"] - fb["logz"]) <= 1e-12 * max(1.0, abs(fb["logz"]))
+            assert np.allclose(lfb["counts"], fb["counts"], atol=1e-12, rtol=1e-12)
+            assert np.allclose(lfb["edge_post"], 1.0, atol=1e-12)
+
+
+def pin_lattice_bruteforce(lib, cases=150, seed=37):
+    """Random small DAGs against every (lattice path, FST path) pair: the
+    best float32 joint score (each step fl(fl(V + theta) + w)) and a path
+    reaching it; log Z, arc and edge posteriors from the float64 weights."""
+    rng = np.random.default_rng(seed)
+    seen = 0
+    for _ in range(cases):
+        fst = synth.tiny_fst(rng, max_states=4, max_arcs=10)
+        lat = random_dag(rng, fst.num_isyms)
+        o = oracle.Fst(fst, lib)
+        th = o.theta
+        ts, tf = o.theta_s, o.theta_f
+        joint = []
+        for ep in lattice_paths(lat):
+            x = np.array([lat.label[e] for e in ep], np.int32)
+            for seq, _, w64, qn in enumerate_paths(fst, x):
+                if seq:
+                    v = _f32(ts[fst.src[seq[0]]])
+                    for e, k in zip(ep, seq):
+                        v = _f32(_f32(v + th[k]) + lat.weight[e])
+                    v = _f32(v + tf[qn])
+                else:
+                    v = _f32(ts[qn] + tf[qn])
+                joint.append((ep, seq, v, w64 + sum(float(lat.weight[e]) for e in ep)))
+        lv = oracle.lattice_viterbi(o, lat)
+        lfb = oracle.lattice_forward_backward(o, lat)
+        if not joint:
+            assert lv["status"] == oracle.NO_PATH and lfb["logz"] == -math.inf
+            assert np.all(lfb["counts"] == 0) and np.all(lfb["edge_post"] == 0)
+            continue
+        seen += 1
+        best = max(j[2] for j in joint)
+        assert lv["best"] == best, (lv["best"], best)
+        got = (tuple(int(e) for e in lv["edges"]), tuple(int(k) for k in lv["arcs"]))
+        assert any(j[0] == got[0] and tuple(j[1]) == got[1] and j[2] == best for j in joint), got
+        logz = _lse([j[3] for j in joint])
+        assert abs(lfb["logz"] - logz) <= 1e-12 * max(1.0, abs(logz))
+        cnt, ep_ = np.zeros(fst.num_arcs), np.zeros(lat.E)
+        for ep, seq, _, w in joint:
+            g = math.exp(w - logz)
+            for k in seq:
+                cnt[k] += g
+            for e in ep:
+                ep_[e] += g
+        assert np.allclose(lfb["counts"], cnt, atol=1e-12, rtol=1e-12)
+        assert np.allclose(lfb["edge_post"], ep_, atol=1e-12, rtol=1e-12)
+    assert seen > 30
+
+
 ALL_PINS = [pin_fig1, pin_bruteforce, pin_ties, pin_hmm, pin_single_state,
             pin_unweighted_count, pin_invariants, pin_deterministic, pin_state_posteriors,
-            pin_clamped_bruteforce, pin_clamped_marginal, pin_em_fig1, pin_em_invariants]
+            pin_clamped_bruteforce, pin_clamped_marginal, pin_em_fig1, pin_em_invariants,
+            pin_lattice_chain, pin_lattice_bruteforce]
