@@ -310,6 +310,36 @@ FST_API int fst_create_clamped(const fst_t* fst, fst_t** out, int32_t* num_pairs
 FST_API int fst_clamp_labels(const fst_t* clamped, const int32_t* ids, const int32_t* olabels, int64_t n,
                              int32_t* pair_ids);
 
+/* Acyclic input lattices composed with the FST (the generalisation of an
+ * input string that Sec. 6.1 names).  A lattice has num_nodes >= 1 nodes
+ * numbered in a topological order -- node 0 is the start, node
+ * num_nodes-1 the end -- and num_edges >= 0 edges; edge e goes from from[e]
+ * to to[e] (from[e] < to[e] < num_nodes), reads symbol label[e] in [0, m)
+ * and carries the log-weight weight[e] (not NaN or +inf).  All arrays are
+ * host arrays; the calls are synchronous and allocate their working tables
+ * (num_nodes x num_states per table).  A string is the lattice whose edge t
+ * goes from node t to t+1 with weight 0, and decodes exactly as
+ * fst_viterbi / fst_forward_backward.
+ *
+ * Viterbi: the best pair of a lattice path and an FST path reading its
+ * symbols, each step scored fl(fl(V + theta_arc) + weight_edge) in float32
+ * (ties: the lowest arc id into each (node, state), then the lowest edge
+ * id), plus the start and final weights.  best_score gets its log-weight
+ * (-inf: none); edge_path and arc_path ([num_nodes-1] each, NULL allowed
+ * when num_nodes = 1) its edges and arcs; *path_len their number.
+ * Returns FST_OK, FST_ERR_NO_PATH or an error. */
+FST_API int fst_lattice_viterbi(fst_t* fst, int32_t num_nodes, int32_t num_edges, const int32_t* from,
+                                const int32_t* to, const int32_t* label, const float* weight, float* best_score,
+                                int32_t* edge_path, int32_t* arc_path, int32_t* path_len);
+
+/* Forward-backward over a lattice (float64 values): log Z of all (lattice
+ * path, FST path) pairs, the expected count of each arc (summed over the
+ * edges that read its symbol; [num_arcs] or NULL) and the posterior of each
+ * edge ([num_edges] or NULL).  Returns FST_OK, FST_ERR_NO_PATH or an error. */
+FST_API int fst_lattice_forward_backward(fst_t* fst, int32_t num_nodes, int32_t num_edges, const int32_t* from,
+                                         const int32_t* to, const int32_t* label, const float* weight,
+                                         double* log_z, float* arc_posteriors, float* edge_posteriors);
+
 /* log Z of one string with every value and weight in float64 (the forward
  * recursion of Alg. 2 in the log domain; plain method, one launch per
  * position).  For finite-difference checks of d log Z / d theta, which a

@@ -171,6 +171,39 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
 }
 constexpr uint32_t FKEY_NEG_INF = 0x007fffffu;  // fkey(-inf)
 
+// Order-preserving map float64 -> uint64 (as fkey for float32); no finite
+// value or -inf maps to 0, which therefore means "nothing yet".
+__device__ __forceinline__ unsigned long long dkey(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+  const unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)u);
+}
+
+// exp(v - m), v <= m, as a 2^-40 fixed-point integer: sums of these are exact
+// and so independent of the order in which they are added.  A sum of fewer
+// than 2^24 terms cannot overflow (the store refuses longer segments).  The
+// value and the maximum m are float64: the forward and backward values
+// carried from position to position are float64 (a float32 value rounds by
+// up to 2^-24 of its size at every position, and over a 200-position string
+// those roundings shift alpha + beta - log Z by ~1e-5, the whole posterior
+// tolerance), and so is the term, whose relative error would otherwise add
+// to the same drift.  The maximal term is exactly 2^40 and costs no
+// exponential (most destinations of a sparse frontier have one live arc;
+// float64 arithmetic is scarce on this GPU).
+__device__ __forceinline__ unsigned long long fix_exp64(double v, double m) {
+  if (v == -INFINITY) return 0ull;
+  if (v == m) return 1099511627776ull;  // 2^40
+  return __double2ull_rn(exp(v - m) * 1099511627776.0);
+}
+// m + log(s / 2^40), in float64.
+__device__ __forceinline__ double fix_log_sum64(double m, unsigned long long s) {
+  return (m == -INFINITY || s == 0ull) ? -INFINITY : m + log((double)s * 0x1p-40);
+}
+
+
 // ------------------------------------------------------------ primitives
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the key.
 int radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s);
@@ -214,5 +247,20 @@ int set_layout_weights(fst_s* f, const float* d_theta_by_id, cudaStream_t s);
 int set_layout_weights64(fst_s* f, const double* d_theta_by_id, cudaStream_t s);
 
 int grid_for(int64_t work_warps, int block_threads, int num_sms, int max_blocks_per_sm);
+
+// Every arc of every slice as one record {source, destination, id} (id -1 on
+// padding) with its log-weight, in the order fst_set_slice_order chose;
+// symbol a's records are [h_sym_win[a] * WIN, h_sym_win[a+1] * WIN).  Built
+// on first use (slice.cu).
+struct SliceView {
+  const int4* arcs;
+  const float* theta;
+  const int64_t* h_sym_win;
+};
+int slice_view(fst_s* f, cudaStream_t s, SliceView* out);
+
+// Input label, destination and log-weight of every arc by caller id (any
+// output may be NULL; train.cu).
+int arcs_by_id(fst_s* f, int32_t* il, int32_t* dst, float* th, cudaStream_t s);
 
 }  // namespace fstgpu

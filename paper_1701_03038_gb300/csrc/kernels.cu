@@ -328,37 +328,6 @@ __device__ __forceinline__ void block_visit(BlockScratch<Ctx>& sh, int32_t e0, i
   __syncthreads();
 }
 
-// Order-preserving map float64 -> uint64 (as fkey for float32); no finite
-// value or -inf maps to 0, which therefore means "nothing yet".
-__device__ __forceinline__ unsigned long long dkey(double d) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double dkey_inv(unsigned long long k) {
-  const unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
-  return __longlong_as_double((long long)u);
-}
-
-// exp(v - m), v <= m, as a 2^-40 fixed-point integer: sums of these are exact
-// and so independent of the order in which they are added.  A sum of fewer
-// than 2^24 terms cannot overflow (the store refuses longer segments).  The
-// value and the maximum m are float64: the forward and backward values
-// carried from position to position are float64 (a float32 value rounds by
-// up to 2^-24 of its size at every position, and over a 200-position string
-// those roundings shift alpha + beta - log Z by ~1e-5, the whole posterior
-// tolerance), and so is the term, whose relative error would otherwise add
-// to the same drift.  The maximal term is exactly 2^40 and costs no
-// exponential (most destinations of a sparse frontier have one live arc;
-// float64 arithmetic is scarce on this GPU).
-__device__ __forceinline__ unsigned long long fix_exp64(double v, double m) {
-  if (v == -INFINITY) return 0ull;
-  if (v == m) return 1099511627776ull;  // 2^40
-  return __double2ull_rn(exp(v - m) * 1099511627776.0);
-}
-// m + log(s / 2^40), in float64.
-__device__ __forceinline__ double fix_log_sum64(double m, unsigned long long s) {
-  return (m == -INFINITY || s == 0ull) ? -INFINITY : m + log((double)s * 0x1p-40);
-}
 // Order key of a float64 value rounded to float32 (0 = -inf, nothing).
 __device__ __forceinline__ uint32_t fkey64(double v) { return v == -INFINITY ? 0u : fkey((float)v); }
 

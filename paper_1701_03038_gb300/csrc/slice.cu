@@ -242,6 +242,16 @@ inline unsigned nb(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + TB - 
 
 }  // namespace
 
+namespace fstgpu {
+int slice_view(fst_s* f, cudaStream_t s, SliceView* out) {
+  int rc = slice_records(f, s);
+  if (rc) return rc;
+  const Layout& L = slice_layout(f);
+  *out = SliceView{slice_arcs(f), L.theta, L.h_sym_win};
+  return FST_OK;
+}
+}  // namespace fstgpu
+
 extern "C" int fst_set_slice_order(fst_t* f, int32_t order) {
   if (!f || (order != FST_SLICE_BY_DESTINATION && order != FST_SLICE_BY_SOURCE)) {
     set_error("fst_set_slice_order: bad arguments");

@@ -120,6 +120,9 @@ struct DevGuard {
   }
 };
 
+}  // namespace
+
+namespace fstgpu {
 int arcs_by_id(fst_s* f, int32_t* il, int32_t* dst, float* th, cudaStream_t s) {
   const Layout& L = f->bwd;
   if (L.P > 0)
@@ -127,8 +130,7 @@ int arcs_by_id(fst_s* f, int32_t* il, int32_t* dst, float* th, cudaStream_t s) {
   FST_CUDA(cudaGetLastError());
   return FST_OK;
 }
-
-}  // namespace
+}  // namespace fstgpu
 
 extern "C" int fst_em_update(fst_t* f, const float* counts, float pseudo_count, float* theta_out, int32_t flags) {
   if (!f || (f->A > 0 && (!counts || !theta_out)) || !(pseudo_count >= 0.f) || isinf(pseudo_count) ||

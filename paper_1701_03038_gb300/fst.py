@@ -239,6 +239,43 @@ class Fst:
                                           _hptr(lz)), "fst_log_z_f64")
         return float(lz[0])
 
+    # ------------------------------------------------------------ lattices
+    @staticmethod
+    def _lattice_args(num_nodes, frm, to, label, weight):
+        arrs = [_host(frm, np.int32), _host(to, np.int32), _host(label, np.int32), _host(weight, np.float32)]
+        e = int(arrs[0].shape[0])
+        if any(int(a.shape[0]) != e for a in arrs):
+            raise ValueError("lattice arrays differ in length")
+        return int(num_nodes), e, arrs
+
+    def lattice_viterbi(self, num_nodes, frm, to, label, weight):
+        """Best (lattice path, FST path) of an acyclic input lattice (see
+        fst_lattice_viterbi): (score float32, edges int32[L], arcs int32[L], status)."""
+        n, e, (a, b, c, d) = self._lattice_args(num_nodes, frm, to, label, weight)
+        best = np.zeros(1, np.float32)
+        ep = np.zeros(max(n - 1, 1), np.int32)
+        ap = np.zeros(max(n - 1, 1), np.int32)
+        ln = np.zeros(1, np.int32)
+        with torch.cuda.device(self.device):
+            rc = self._lib.fst_lattice_viterbi(self._h, n, e, _hptr(a), _hptr(b), _hptr(c), _hptr(d), _hptr(best),
+                                               _hptr(ep), _hptr(ap), _hptr(ln))
+        check(rc, "fst_lattice_viterbi", allow=(_lib.OK, _lib.NO_PATH))
+        L = int(ln[0])
+        return best[0], ep[:L], ap[:L], rc
+
+    def lattice_forward_backward(self, num_nodes, frm, to, label, weight):
+        """(log Z, arc counts float32[A], edge posteriors float32[E], status)
+        of an acyclic input lattice (see fst_lattice_forward_backward)."""
+        n, e, (a, b, c, d) = self._lattice_args(num_nodes, frm, to, label, weight)
+        lz = np.zeros(1, np.float64)
+        cnt = np.zeros(max(self.num_arcs, 1), np.float32)
+        ep = np.zeros(max(e, 1), np.float32)
+        with torch.cuda.device(self.device):
+            rc = self._lib.fst_lattice_forward_backward(self._h, n, e, _hptr(a), _hptr(b), _hptr(c), _hptr(d),
+                                                        _hptr(lz), _hptr(cnt), _hptr(ep))
+        check(rc, "fst_lattice_forward_backward", allow=(_lib.OK, _lib.NO_PATH))
+        return float(lz[0]), cnt[:self.num_arcs], ep[:e], rc
+
     # ------------------------------------------------------------ training
     def em_update(self, counts, pseudo_count: float = 0.0, apply: bool = False):
         """EM M-step (fst_em_update): new log-weights, each state's outgoing
