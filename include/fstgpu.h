@@ -340,6 +340,22 @@ FST_API int fst_lattice_forward_backward(fst_t* fst, int32_t num_nodes, int32_t 
                                          const int32_t* to, const int32_t* label, const float* weight,
                                          double* log_z, float* arc_posteriors, float* edge_posteriors);
 
+/* The weight of one string as a parallel product over time (the parallel
+ * prefix approach of Sec. 6.1): the slice of each position becomes a dense
+ * num_states x num_states matrix of log-weights, adjacent matrices are
+ * multiplied pairwise in parallel and the products again until one is
+ * left (log2(n) dependent rounds; Q^3 work per product), then closed with
+ * the start and final weights.  For small dense FSTs (num_states <= 512,
+ * FST_ERR_UNSUPPORTED beyond) and long strings.
+ *   log_z       host double: log Z (log-sum products in float32, the final
+ *               sum in float64).
+ *   best_score  host float: the best path's log-weight from max-plus
+ *               products; its float32 additions are associated in tree
+ *               order, so it can differ from fst_viterbi's in the last bits.
+ * Host pointers; synchronous; allocates its matrices.  Returns FST_OK,
+ * FST_ERR_NO_PATH or an error. */
+FST_API int fst_prefix_log_z(fst_t* fst, const int32_t* ids, int32_t n, double* log_z, float* best_score);
+
 /* log Z of one string with every value and weight in float64 (the forward
  * recursion of Alg. 2 in the log domain; plain method, one launch per
  * position).  For finite-difference checks of d log Z / d theta, which a

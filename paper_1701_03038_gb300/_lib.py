@@ -68,6 +68,7 @@ SIGNATURES = {
     "fst_log_z_f64": [vp, vp, vp, i32, vp],
     "fst_em_update": [vp, vp, C.c_float, vp, i32],
     "fst_lattice_viterbi": [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp],
+    "fst_prefix_log_z": [vp, vp, i32, vp, vp],
     "fst_lattice_forward_backward": [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp],
     "fst_create_clamped": [vp, C.POINTER(vp), vp],
     "fst_clamp_labels": [vp, vp, vp, i64, vp],

@@ -276,6 +276,17 @@ class Fst:
         check(rc, "fst_lattice_forward_backward", allow=(_lib.OK, _lib.NO_PATH))
         return float(lz[0]), cnt[:self.num_arcs], ep[:e], rc
 
+    def prefix_log_z(self, ids):
+        """(log Z, best score, status) of one string by the parallel product of
+        its dense slice matrices (small dense FSTs; see fst_prefix_log_z)."""
+        x = _host(ids, np.int32)
+        lz = np.zeros(1, np.float64)
+        best = np.zeros(1, np.float32)
+        with torch.cuda.device(self.device):
+            rc = self._lib.fst_prefix_log_z(self._h, _hptr(x), int(x.shape[0]), _hptr(lz), _hptr(best))
+        check(rc, "fst_prefix_log_z", allow=(_lib.OK, _lib.NO_PATH))
+        return float(lz[0]), best[0], rc
+
     # ------------------------------------------------------------ training
     def em_update(self, counts, pseudo_count: float = 0.0, apply: bool = False):
         """EM M-step (fst_em_update): new log-weights, each state's outgoing

@@ -130,3 +130,33 @@ def test_lattice_rejects_bad_edges():
             f.lattice_viterbi(3, frm, to, lab, w)
         with pytest.raises(FstError):
             f.lattice_forward_backward(3, frm, to, lab, w)
+
+
+def test_parallel_product_over_time():
+    # dense HMMs (every state reaches every state on every symbol): log Z of
+    # long strings by the pairwise product tree against the oracle's sweep;
+    # the best score equals the oracle's Viterbi score up to the rounding of
+    # float32 additions associated in tree order
+    from paper_1701_03038_gb300._lib import UNSUPPORTED, FstError
+    from paper_1701_03038_gb300.fst import Fst
+    rng = np.random.default_rng(47)
+    for K, V, n in ((4, 3, 1), (8, 5, 37), (32, 8, 200), (63, 6, 1000)):
+        pi = rng.dirichlet(np.ones(K))
+        trans = rng.dirichlet(np.ones(K), size=K)
+        emit = rng.dirichlet(np.ones(V), size=K)
+        fa = synth.hmm_fst(pi, trans, emit)
+        f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+        for x in (rng.integers(0, V, size=n).astype(np.int32), np.zeros(0, np.int32)):
+            lz, best, st = f.prefix_log_z(x)
+            want = o.forward_backward(x)
+            assert st == want["status"]
+            assert_logz_close(lz, want["logz"])
+            vb = float(o.viterbi(x)["best"])
+            if math.isinf(vb):
+                assert best == vb
+            else:
+                assert abs(float(best) - vb) <= 1e-5 * max(1.0, abs(vb)), (best, vb)
+    big, _ = synth.make_config("c1", scale=1.0, strings=1)  # 1,000 states: beyond the dense product
+    with pytest.raises(FstError) as ei:
+        Fst.from_arrays(big).prefix_log_z(np.zeros(3, np.int32))
+    assert ei.value.code == UNSUPPORTED
