@@ -86,6 +86,8 @@ def parse_args(argv=None):
                     help="strings decoded with the paper's slice-wide relaxation for comparison")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
+    ap.add_argument("--split-vit", type=int, default=1, help="Viterbi plans (batch parts) on their own streams")
+    ap.add_argument("--split-fb", type=int, default=1, help="forward-backward plans on their own streams")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -459,43 +461,71 @@ def base_line(args, world, fa, strs, ms, relax_step, clk, launches):
             "gpu_launches": launches}
 
 
+def _split(strs, k):
+    """k contiguous sub-batches of about equal size (strings keep their order)."""
+    from paper_1701_03038_gb300 import synth
+    cuts = [round(i * strs.count / k) for i in range(k + 1)]
+    out = []
+    for b0, b1 in zip(cuts[:-1], cuts[1:]):
+        if b1 > b0:
+            out.append(synth.Strings(strs.ids[strs.offsets[b0]:strs.offsets[b1]].copy(),
+                                     (strs.offsets[b0:b1 + 1] - strs.offsets[b0]).copy()))
+    return out
+
+
 def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     import torch
-    from paper_1701_03038_gb300._lib import PLAN_NO_FB, PLAN_NO_VITERBI
-    ids = torch.from_numpy(strs.ids).to(dev)
-    off = torch.from_numpy(strs.offsets).to(dev)
-    # the Viterbi pass and forward-backward are independent: one plan each,
-    # run on two streams so that their latency-bound launches overlap
-    budget = int(args.budget_gb * (1 << 30))
-    plan_v = f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB)
-    plan_f = f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI)
     from paper_1701_03038_gb300 import _lib
+    from paper_1701_03038_gb300._lib import PLAN_NO_FB, PLAN_NO_VITERBI
+    # the Viterbi pass and forward-backward are independent: plans of each
+    # kind (the batch split into --split-vit / --split-fb contiguous parts)
+    # run on their own streams so that their latency-bound launches overlap
+    budget = int(args.budget_gb * (1 << 30))
+
+    def plans_of(k, flags):
+        out = []
+        for sub in _split(strs, k):
+            out.append(f.plan(torch.from_numpy(sub.ids).to(dev), torch.from_numpy(sub.offsets).to(dev),
+                              mem_budget=budget // k, flags=flags))
+        return out
+
+    plans_v = plans_of(args.split_vit, PLAN_NO_FB)
+    plans_f = plans_of(args.split_fb, PLAN_NO_VITERBI)
     tuned = {}
     if args.driver in ("persistent", "persistent-all"):
-        plan_f.set_driver(_lib.DRIVER_PERSISTENT)
+        for p in plans_f:
+            p.set_driver(_lib.DRIVER_PERSISTENT)
     if args.driver == "persistent-all":
-        plan_v.set_driver(_lib.DRIVER_PERSISTENT)
+        for p in plans_v:
+            p.set_driver(_lib.DRIVER_PERSISTENT)
     if args.driver == "autotune":
-        tuned = {"viterbi": plan_v.autotune(), "forward_backward": plan_f.autotune()}
-    info_v, info_f = plan_v.info(), plan_f.info()
-    relax_pass = info_v["relaxations"]
-    s_v, s_f = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        tuned = {"viterbi": [p.autotune() for p in plans_v], "forward_backward": [p.autotune() for p in plans_f]}
+    infos_v, infos_f = [p.info() for p in plans_v], [p.info() for p in plans_f]
+    relax_pass = sum(i["relaxations"] for i in infos_v)
+    allp = plans_v + plans_f
+    streams = [torch.cuda.Stream(device=dev) for _ in allp]
     # two persistent (cooperative) passes never run at the same time
-    serial = plan_v.driver()[0] == _lib.DRIVER_PERSISTENT and plan_f.driver()[0] == _lib.DRIVER_PERSISTENT
+    serial = sum(1 for p in allp if p.driver()[0] == _lib.DRIVER_PERSISTENT) > 1
+
+    def run(p, st):
+        if p in plans_v:
+            p.viterbi(stream=st)
+        else:
+            p.forward_backward(stream=st)
 
     def step():
         main = torch.cuda.current_stream()
         if serial:
-            plan_v.viterbi(stream=main)
-            plan_f.forward_backward(stream=main)
+            for p in allp:
+                run(p, main)
             return
         fork = torch.cuda.Event()
         fork.record(main)
-        s_v.wait_event(fork)
-        s_f.wait_event(fork)
-        plan_v.viterbi(stream=s_v)
-        plan_f.forward_backward(stream=s_f)
-        for st in (s_v, s_f):
+        for st in streams:
+            st.wait_event(fork)
+        for p, st in zip(allp, streams):
+            run(p, st)
+        for st in streams:
             join = torch.cuda.Event()
             join.record(st)
             main.wait_event(join)
@@ -503,7 +533,7 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    # the step's launches replay as one CUDA graph (both streams)
+    # the step's launches replay as one CUDA graph (every stream)
     graph = None
     if not args.no_graph:
         s_c = torch.cuda.Stream(device=dev)
@@ -519,43 +549,46 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
             torch.cuda.synchronize()
     run_step = graph.replay if graph is not None else step
     ms, clk = timed(run_step, args, world, dev, ClockSampler(int(str(dev).split(":")[-1])))
-    launches = info_v["viterbi_launches"] + info_f["fb_launches"]
+    launches = sum(i["viterbi_launches"] for i in infos_v) + sum(i["fb_launches"] for i in infos_f)
     out = base_line(args, world, fa, strs, ms, 3 * relax_pass, clk, args.steps * launches)
 
     # per-kernel device time of one more step, with events around every
     # launch; the passes run one after the other here so that each kernel's
     # time is its own
-    plan_v.profile(True)
-    plan_f.profile(True)
-    plan_v.viterbi()
-    plan_f.forward_backward()
+    for p in allp:
+        p.profile(True)
+    for p in allp:
+        run(p, torch.cuda.current_stream())
     torch.cuda.synchronize()
-    pv, pf = plan_v.profile_read(), plan_f.profile_read()
-    prof = {k: (pv[k][0] + pf[k][0], pv[k][1] + pf[k][1]) for k in pv}
-    plan_v.profile(False)
-    plan_f.profile(False)
-    live = plan_f.live_work()
+    prof = None
+    for p in allp:
+        r = p.profile_read()
+        prof = r if prof is None else {k: (prof[k][0] + r[k][0], prof[k][1] + r[k][1]) for k in r}
+        p.profile(False)
+    lws = [p.live_work() for p in plans_f]
+    live = {"entries": sum(x["entries"] for x in lws), "arcs": sum(x["arcs"] for x in lws)}
     peak, peak_src = load_peak()
-    persistent = (("vit",) if plan_v.driver()[0] else ()) + (("fwd", "bwd") if plan_f.driver()[0] else ())
+    persistent = (("vit",) if plans_v[0].driver()[0] else ()) + (("fwd", "bwd") if plans_f[0].driver()[0] else ())
     rl, passes = roofline(prof, live, peak, peak_src, load_traffic(), stats, strs.ids, persistent)
     performed = 3 * max(live["arcs"], 0)
+    plan_bytes = sum(i["device_bytes"] for i in infos_v + infos_f)
     out["config"].update({
-        "relaxations_per_pass": relax_pass, "waves": max(info_v["waves"], info_f["waves"]),
-        "plan_gb": round((info_v["device_bytes"] + info_f["device_bytes"]) / 2**30, 2),
+        "relaxations_per_pass": relax_pass, "waves": max(i["waves"] for i in infos_v + infos_f),
+        "plan_gb": round(plan_bytes / 2**30, 2),
         "parallelism": "replicas" if world > 1 else "1 GPU",
-        "streams": "a Viterbi plan and a forward-backward plan on two CUDA streams; per-kernel times from one "
-                   "more step run serially",
+        "streams": f"{len(plans_v)} Viterbi and {len(plans_f)} forward-backward plan(s), each on its own CUDA "
+                   "stream; per-kernel times from one more step run serially",
         "launch": "CUDA graph replay" if graph is not None else "host launches",
-        "driver": {"viterbi": "persistent" if plan_v.driver()[0] else "one launch per position",
-                   "forward_backward": "persistent" if plan_f.driver()[0] else "one launch per position",
-                   "grid": {"viterbi": plan_v.driver()[1], "forward_backward": plan_f.driver()[1]},
+        "driver": {"viterbi": "persistent" if plans_v[0].driver()[0] else "one launch per position",
+                   "forward_backward": "persistent" if plans_f[0].driver()[0] else "one launch per position",
+                   "grid": {"viterbi": plans_v[0].driver()[1], "forward_backward": plans_f[0].driver()[1]},
                    "concurrent": not serial, "autotune": tuned or None},
         "l2": "no flush: inputs larger than L2 (arc store and hash "
-              f"{(fa.num_arcs * 24) / 2**30:.2f} GiB, plan storage "
-              f"{(info_v['device_bytes'] + info_f['device_bytes']) / 2**30:.1f} GiB)"})
+              f"{(fa.num_arcs * 24) / 2**30:.2f} GiB, plan storage {plan_bytes / 2**30:.1f} GiB)"})
     out.update({"relaxations_performed_per_s": job_throughput(performed, world, ms / 1000.0),
                 "live_work": live, "roofline": rl, "passes": passes,
                 "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}})
+    s_v, s_f = streams[0], streams[len(plans_v)]
 
     # plain method (one string at a time, one launch per position) on a sample
     if not args.no_plain and rank == 0:
