@@ -708,7 +708,12 @@ def bench_plain(args, rank, world, dev, fa, strs, f, stats):
     position; a step is every string of the workload.  The host API copies
     each string in and its results out, so the step is end to end."""
     import torch
+    from paper_1701_03038_gb300 import _lib
     relax_step = 3 * int(stats[0][strs.ids].sum())
+    # the single-string Viterbi takes the cheaper of the frontier and the
+    # slice-wide kernels, by a cost model calibrated on the first strings
+    k = min(16, strs.count)
+    coef = f.autotune_plain(strs.ids[:strs.offsets[k]], strs.offsets[:k + 1])
 
     def step():
         for b in range(strs.count):
@@ -730,7 +735,15 @@ def bench_plain(args, rank, world, dev, fa, strs, f, stats):
     out["e2e"] = {"value": out["value"], "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                   "ms_per_step": ms, "api": "fst_viterbi + fst_forward_backward (host buffers; copies inside)"}
     out["us_per_sentence"] = 1000.0 * ms / strs.count
-    # per-kernel times and live work of one more step, with events
+    lens = np.diff(strs.offsets)
+    sl = [bool(coef[2] + coef[3] * n + coef[4] * a < coef[0] + coef[1] * n)
+          for n, a in zip(lens, [int(stats[0][strs.get(b)].sum()) for b in range(strs.count)])]
+    out["plain_viterbi"] = {"method": "automatic (fst_autotune_plain on the first strings)",
+                            "coef_us": [round(float(c), 4) for c in coef],
+                            "strings_on_slice_kernel": int(sum(sl)), "strings": strs.count}
+    # per-kernel times and live work of one more step, with events (frontier
+    # kernels for both passes, so that every relaxation is profiled)
+    f.set_plain_method(_lib.PLAIN_FRONTIER)
     f.profile(True)
     entries = arcs = 0
     for b in range(strs.count):
@@ -742,6 +755,7 @@ def bench_plain(args, rank, world, dev, fa, strs, f, stats):
         arcs += max(lw["arcs"], 0)
     prof = f.profile_read()
     f.profile(False)
+    f.set_plain_method(_lib.PLAIN_AUTO)
     live = {"entries": entries, "arcs": arcs}
     peak, peak_src = load_peak()
     rl, passes = roofline(prof, live, peak, peak_src, None, stats, strs.ids)

@@ -131,6 +131,25 @@ FST_API int fst_set_state_weights(fst_t* fst, const float* start_weight, const f
 FST_API int fst_viterbi(fst_t* fst, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
                 int32_t* olabels);
 
+/* Which kernels fst_viterbi uses for one string: FST_PLAIN_FRONTIER (the
+ * frontier-driven steps, the default), FST_PLAIN_SLICE (the paper's
+ * slice-wide relaxation, Sec. 5.1, as fst_viterbi_slice) or FST_PLAIN_AUTO
+ * (the one a calibrated cost model predicts to be faster for the string;
+ * the frontier kernels until fst_autotune_plain has run).  Results are
+ * identical either way. */
+#define FST_PLAIN_FRONTIER 0
+#define FST_PLAIN_SLICE 1
+#define FST_PLAIN_AUTO 2
+FST_API int fst_set_plain_method(fst_t* fst, int32_t method);
+
+/* Calibrate FST_PLAIN_AUTO on sample strings (host arrays: ids, offsets
+ * [B+1] as in the batch calls, B >= 1): each string is decoded both ways
+ * and timed on the host; the frontier time is fitted as d0 + d1 n and the
+ * slice time as c0 + c1 n + c2 S (S = the arcs of the string's slices), by
+ * least squares; the method is set to FST_PLAIN_AUTO.  coef [5] or NULL
+ * receives d0, d1, c0, c1, c2 (microseconds).  Synchronous. */
+FST_API int fst_autotune_plain(fst_t* fst, const int32_t* ids, const int64_t* offsets, int32_t B, double* coef);
+
 /* The paper's relaxation, kept for comparison (Sec. 5.1): Viterbi of one
  * string where, at every position, each arc of the slice delta[w_t] is
  * relaxed by its own thread whether or not its source is live, and

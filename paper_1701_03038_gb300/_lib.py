@@ -21,6 +21,7 @@ FAULT_NONE, FAULT_BARRIER_STALL = 0, 1
 TUNE_REFRESH = 1
 EM_APPLY = 2
 SLICE_BY_DESTINATION, SLICE_BY_SOURCE = 0, 1
+PLAIN_FRONTIER, PLAIN_SLICE, PLAIN_AUTO = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -38,6 +39,8 @@ SIGNATURES = {
     "fst_set_state_weights": [vp, vp, vp, i32, i32],
     "fst_viterbi": [vp, vp, i32, vp, vp, vp],
     "fst_viterbi_slice": [vp, vp, i32, vp, vp],
+    "fst_set_plain_method": [vp, i32],
+    "fst_autotune_plain": [vp, vp, vp, i32, vp],
     "fst_forward_backward_slice": [vp, vp, i32, vp, vp],
     "fst_set_slice_order": [vp, i32],
     "fst_forward_backward": [vp, vp, i32, vp, vp],

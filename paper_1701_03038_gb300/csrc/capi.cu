@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <chrono>
 #include <vector>
 
 #include "fst_internal.cuh"
@@ -447,6 +449,7 @@ extern "C" int fst_destroy(fst_t* f) {
   dfree(f->slice_arcs_src);
   dfree(f->slice_keys);
   dfree(f->slice_fb);
+  dfree(f->slice_out);
   delete f->plain;
   f->plain = nullptr;
   free_layout(f->fwd);
@@ -574,6 +577,10 @@ extern "C" int fst_set_state_weights(fst_t* f, const float* start_weight, const 
 }
 
 // ============================================================ plain method
+static int fst_viterbi_frontier(fst_t* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
+                                int32_t* olabels);
+static bool plain_uses_slice(const fst_s* f, const int32_t* ids, int32_t n);
+
 extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
                            int32_t* olabels) {
   if (!f || n < 0 || (n > 0 && (!ids || !arc_path)) || !best_score) {
@@ -581,6 +588,27 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
     return FST_ERR_INVALID_ARG;
   }
   DevGuard g(f->device);
+  if (plain_uses_slice(f, ids, n)) return viterbi_slice_run(f, ids, n, best_score, arc_path, olabels);
+  return fst_viterbi_frontier(f, ids, n, best_score, arc_path, olabels);
+}
+// Whether fst_viterbi takes the slice-wide kernel for this string: by the
+// handle's setting, or (FST_PLAIN_AUTO, once calibrated) by the predicted
+// times of the two kernels.
+static bool plain_uses_slice(const fst_s* f, const int32_t* ids, int32_t n) {
+  if (f->plain_method == FST_PLAIN_SLICE) return true;
+  if (f->plain_method != FST_PLAIN_AUTO || !f->plain_tuned) return false;
+  double arcs = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (ids[i] < 0 || ids[i] >= f->m) return false;  // the frontier path reports the error
+    arcs += (double)(f->h_sym_arc[ids[i] + 1] - f->h_sym_arc[ids[i]]);
+  }
+  const double* c = f->plain_coef;
+  return c[2] + c[3] * n + c[4] * arcs < c[0] + c[1] * n;
+}
+
+// The frontier kernels' single-string Viterbi.
+static int fst_viterbi_frontier(fst_t* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
+                                int32_t* olabels) {
   int rc;
   if ((rc = plain_init(f))) return rc;
   cudaStream_t s = 0;
@@ -703,5 +731,99 @@ extern "C" int fst_live_work(fst_t* f, int64_t* entries, int64_t* arcs) {
     FST_CUDA(cudaMemcpy(&h, sum.p, 8, cudaMemcpyDeviceToHost));
     *arcs = (int64_t)h;
   }
+  return FST_OK;
+}
+
+// ------------------------------------------------- plain-method calibration
+extern "C" int fst_set_plain_method(fst_t* f, int32_t method) {
+  if (!f || method < FST_PLAIN_FRONTIER || method > FST_PLAIN_AUTO) {
+    set_error("fst_set_plain_method: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  f->plain_method = method;
+  return FST_OK;
+}
+
+// Least squares y ~ X b with X of k <= 3 columns (normal equations,
+// Gaussian elimination with partial pivoting); false if singular.
+static bool least_squares(const std::vector<std::array<double, 3>>& X, const std::vector<double>& y, int k,
+                          double* b) {
+  double M[3][4] = {{0}};
+  for (size_t r = 0; r < X.size(); ++r)
+    for (int i = 0; i < k; ++i) {
+      for (int j = 0; j < k; ++j) M[i][j] += X[r][i] * X[r][j];
+      M[i][3] += X[r][i] * y[r];
+    }
+  for (int c = 0; c < k; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < k; ++r)
+      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+    if (fabs(M[piv][c]) < 1e-30) return false;
+    for (int j = 0; j < 4; ++j) std::swap(M[c][j], M[piv][j]);
+    for (int r = 0; r < k; ++r) {
+      if (r == c) continue;
+      const double m = M[r][c] / M[c][c];
+      for (int j = c; j < 4; ++j) M[r][j] -= m * M[c][j];
+    }
+  }
+  for (int i = 0; i < k; ++i) b[i] = M[i][3] / M[i][i];
+  return true;
+}
+
+extern "C" int fst_autotune_plain(fst_t* f, const int32_t* ids, const int64_t* offsets, int32_t B, double* coef) {
+  if (!f || B < 1 || !offsets || (offsets[B] > 0 && !ids)) {
+    set_error("fst_autotune_plain: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  for (int32_t b = 0; b < B; ++b)
+    if (offsets[b + 1] < offsets[b] || offsets[b + 1] - offsets[b] >= INT32_MAX) {
+      set_error("fst_autotune_plain: offsets must be non-decreasing");
+      return FST_ERR_INVALID_ARG;
+    }
+  DevGuard g(f->device);
+  std::vector<int32_t> path, olab;
+  std::vector<std::array<double, 3>> Xf, Xs;
+  std::vector<double> yf, ys;
+  for (int32_t b = -1; b < B; ++b) {  // b = -1: the first string again, untimed (first-use costs)
+    const int32_t bb = b < 0 ? 0 : b;
+    const int32_t* x = ids + offsets[bb];
+    const int32_t n = (int32_t)(offsets[bb + 1] - offsets[bb]);
+    path.resize(std::max(n, 1));
+    olab.resize(std::max(n, 1));
+    double arcs = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+      if (x[i] < 0 || x[i] >= f->m) { set_error("fst_autotune_plain: symbol outside [0, %d)", f->m); return FST_ERR_INVALID_ARG; }
+      arcs += (double)(f->h_sym_arc[x[i] + 1] - f->h_sym_arc[x[i]]);
+    }
+    float score = 0.f;
+    double t[2];
+    for (int k = 0; k < 2; ++k) {
+      const auto t0 = std::chrono::steady_clock::now();
+      const int rc = k == 0 ? fst_viterbi_frontier(f, x, n, &score, path.data(), olab.data())
+                            : viterbi_slice_run(f, x, n, &score, path.data(), olab.data());
+      if (rc != FST_OK && rc != FST_ERR_NO_PATH) return rc;
+      t[k] = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (b < 0) continue;
+    Xf.push_back({1.0, (double)n, 0.0});
+    yf.push_back(t[0]);
+    Xs.push_back({1.0, (double)n, arcs});
+    ys.push_back(t[1]);
+  }
+  double cf[2] = {0, 0}, cs[3] = {0, 0, 0};
+  if (!least_squares(Xf, yf, 2, cf) || !least_squares(Xs, ys, 3, cs)) {
+    // too few distinct strings for a fit: compare the mean times alone
+    double mf = 0, ms = 0;
+    for (size_t i = 0; i < yf.size(); ++i) { mf += yf[i]; ms += ys[i]; }
+    cf[0] = mf / yf.size(); cf[1] = 0;
+    cs[0] = ms / ys.size(); cs[1] = cs[2] = 0;
+  }
+  const double c[5] = {cf[0], cf[1], cs[0], cs[1], cs[2]};
+  for (int i = 0; i < 5; ++i) {
+    f->plain_coef[i] = c[i];
+    if (coef) coef[i] = c[i];
+  }
+  f->plain_tuned = true;
+  f->plain_method = FST_PLAIN_AUTO;
   return FST_OK;
 }

@@ -146,6 +146,13 @@ struct fst_s {
   int64_t slice_cap = 0;
   float* slice_fb = nullptr;       // forward and backward tables of fst_forward_backward_slice
   int64_t slice_fb_cap = 0;
+  int32_t* slice_out = nullptr;    // slice Viterbi outputs: score, path and output labels
+  int64_t slice_out_cap = 0;
+  // single-string Viterbi: frontier kernels, the slice-wide kernel, or the
+  // cheaper of the two by a cost model fitted by fst_autotune_plain
+  int32_t plain_method = 0;
+  bool plain_tuned = false;
+  double plain_coef[5] = {0, 0, 0, 0, 0};  // frontier d0 + d1 n; slice c0 + c1 n + c2 (slice arcs)
 };
 
 namespace fstgpu {
@@ -258,6 +265,11 @@ struct SliceView {
   const int64_t* h_sym_win;
 };
 int slice_view(fst_s* f, cudaStream_t s, SliceView* out);
+
+// Viterbi of one string by the paper's slice-wide relaxation (slice.cu);
+// host outputs, olabels may be NULL.
+int viterbi_slice_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
+                      int32_t* olabels);
 
 // Input label, destination and log-weight of every arc by caller id (any
 // output may be NULL; train.cu).

@@ -240,6 +240,12 @@ int slice_records(fst_s* f, cudaStream_t s) {
 
 inline unsigned nb(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + TB - 1) / TB); }
 
+__global__ void k_gather_olabels(const int32_t* __restrict__ path, int32_t n, const int32_t* __restrict__ olabel,
+                                 int32_t* __restrict__ out) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = path[i] >= 0 ? olabel[path[i]] : -1;
+}
+
 }  // namespace
 
 namespace fstgpu {
@@ -338,11 +344,11 @@ extern "C" int fst_forward_backward_slice(fst_t* f, const int32_t* ids, int32_t 
   return FST_OK;
 }
 
-extern "C" int fst_viterbi_slice(fst_t* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path) {
-  if (!f || n < 0 || (n > 0 && (!ids || !arc_path)) || !best_score) {
-    set_error("fst_viterbi_slice: bad arguments");
-    return FST_ERR_INVALID_ARG;
-  }
+namespace fstgpu {
+// Viterbi of one string by the slice-wide relaxation; host outputs (olabels
+// may be NULL).  The score, path and output labels equal fst_viterbi's.
+int viterbi_slice_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
+                      int32_t* olabels) {
   for (int32_t i = 0; i < n; ++i)
     if (ids[i] < 0 || ids[i] >= f->m) {
       set_error("symbol %d at position %d is outside [0, %d)", ids[i], i, f->m);
@@ -360,12 +366,17 @@ extern "C" int fst_viterbi_slice(fst_t* f, const int32_t* ids, int32_t n, float*
     if ((rc = dalloc(&f->slice_keys, need))) return rc;
     f->slice_cap = need;
   }
-  float* d_score = nullptr;
-  int32_t* d_path = nullptr;
-  if ((rc = dalloc(&d_score, 1)) || (rc = dalloc(&d_path, std::max(n, 1)))) {
-    dfree(d_score);
-    return rc;
+  // output buffers kept by the handle: score, path and output labels
+  if (n + 2 > f->slice_out_cap) {
+    dfree(f->slice_out);
+    f->slice_out_cap = 0;
+    const int64_t c = std::max<int64_t>(2 * (int64_t)n + 4, 2 * f->slice_out_cap);
+    if ((rc = dalloc(&f->slice_out, 2 * c + 1))) return rc;
+    f->slice_out_cap = c;
   }
+  float* d_score = (float*)f->slice_out;
+  int32_t* d_path = f->slice_out + 1;
+  int32_t* d_olab = f->slice_out + 1 + f->slice_out_cap;
   FST_CUDA(cudaMemsetAsync(f->slice_keys, 0, (size_t)need * 8, s));
   for (int32_t t = 1; t <= n; ++t) {
     const int32_t a = ids[t - 1];
@@ -376,15 +387,24 @@ extern "C" int fst_viterbi_slice(fst_t* f, const int32_t* ids, int32_t n, float*
         f->slice_keys + (int64_t)t * Q);
   }
   k_slice_final<<<1, TB, 0, s>>>(f->slice_keys, n, f->Q, f->theta_s, f->theta_f, f->src_by_id, d_score, d_path);
+  if (olabels && n > 0) k_gather_olabels<<<nb(n), TB, 0, s>>>(d_path, n, f->olabel, d_olab);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpy(best_score, d_score, 4, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && n > 0) e = cudaMemcpy(arc_path, d_path, (size_t)n * 4, cudaMemcpyDeviceToHost);
-  dfree(d_score);
-  dfree(d_path);
-  if (e != cudaSuccess) return cuda_fail(e, "fst_viterbi_slice");
+  if (e == cudaSuccess && olabels && n > 0) e = cudaMemcpy(olabels, d_olab, (size_t)n * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "slice Viterbi");
   if (*best_score == -INFINITY) {
     set_error("no accepting path");
     return FST_ERR_NO_PATH;
   }
   return FST_OK;
+}
+}  // namespace fstgpu
+
+extern "C" int fst_viterbi_slice(fst_t* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path) {
+  if (!f || n < 0 || (n > 0 && (!ids || !arc_path)) || !best_score) {
+    set_error("fst_viterbi_slice: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  return viterbi_slice_run(f, ids, n, best_score, arc_path, nullptr);
 }

@@ -210,6 +210,23 @@ class Fst:
         check(rc, "fst_forward_backward_slice", allow=(_lib.OK, _lib.NO_PATH))
         return float(lz[0]), (cnt[:self.num_arcs] if posteriors else None), rc
 
+    def set_plain_method(self, method: int):
+        """Kernels of the single-string Viterbi: _lib.PLAIN_FRONTIER, PLAIN_SLICE
+        or PLAIN_AUTO (see fst_set_plain_method)."""
+        check(self._lib.fst_set_plain_method(self._h, int(method)), "fst_set_plain_method")
+
+    def autotune_plain(self, ids, offsets) -> np.ndarray:
+        """Calibrate the automatic choice of the single-string Viterbi kernels on
+        sample strings (see fst_autotune_plain); returns the fitted
+        coefficients (d0, d1, c0, c1, c2) in microseconds."""
+        x = _host(ids, np.int32)
+        off = _host(offsets, np.int64)
+        coef = np.zeros(5, np.float64)
+        with torch.cuda.device(self.device):
+            check(self._lib.fst_autotune_plain(self._h, _hptr(x), _hptr(off), int(off.shape[0] - 1), _hptr(coef)),
+                  "fst_autotune_plain")
+        return coef
+
     def set_slice_order(self, order: int):
         """Arc order within a slice for the paper-design calls:
         _lib.SLICE_BY_DESTINATION (column-major) or _lib.SLICE_BY_SOURCE (row-major)."""

@@ -245,3 +245,25 @@ def test_slice_orders_and_paper_forward_backward():
     print(f"paper forward-backward: largest posterior error {worst:.2e}")
     with pytest.raises(_lib.FstError):
         f.set_slice_order(2)
+
+
+def test_plain_viterbi_methods_agree():
+    # fst_viterbi through the frontier kernels, the slice-wide kernel, and the
+    # calibrated automatic choice: the same score, path and output labels
+    from paper_1701_03038_gb300 import _lib
+    fa, strs = synth.make_config("c2", scale=0.02, strings=12)
+    f, o = _fst(fa), oracle.Fst(fa)
+    iid = synth.make_strings(fa, 4, 5, 20, seed=3, kind="iid")
+    xs = [strs.get(b) for b in range(strs.count)] + [iid.get(b) for b in range(iid.count)] + [np.zeros(0, np.int32)]
+    for method in (_lib.PLAIN_SLICE, _lib.PLAIN_FRONTIER):
+        f.set_plain_method(method)
+        for x in xs:
+            s, p, ol, st = f.viterbi(x)
+            assert_viterbi_equal(s, p, ol, st, o.viterbi(x))
+    coef = f.autotune_plain(strs.ids, strs.offsets)
+    assert coef.shape == (5,) and np.isfinite(coef).all()
+    for x in xs:
+        s, p, ol, st = f.viterbi(x)
+        assert_viterbi_equal(s, p, ol, st, o.viterbi(x))
+    with pytest.raises(_lib.FstError):
+        f.set_plain_method(7)
