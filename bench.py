@@ -86,8 +86,8 @@ def parse_args(argv=None):
                     help="strings decoded with the paper's slice-wide relaxation for comparison")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
-    ap.add_argument("--split-vit", type=int, default=1, help="Viterbi plans (batch parts) on their own streams")
-    ap.add_argument("--split-fb", type=int, default=1, help="forward-backward plans on their own streams")
+    ap.add_argument("--parts-vit", type=int, default=2, help="stream-parallel parts of the Viterbi plan")
+    ap.add_argument("--parts-fb", type=int, default=4, help="stream-parallel parts of the forward-backward plan")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -461,36 +461,18 @@ def base_line(args, world, fa, strs, ms, relax_step, clk, launches):
             "gpu_launches": launches}
 
 
-def _split(strs, k):
-    """k contiguous sub-batches of about equal size (strings keep their order)."""
-    from paper_1701_03038_gb300 import synth
-    cuts = [round(i * strs.count / k) for i in range(k + 1)]
-    out = []
-    for b0, b1 in zip(cuts[:-1], cuts[1:]):
-        if b1 > b0:
-            out.append(synth.Strings(strs.ids[strs.offsets[b0]:strs.offsets[b1]].copy(),
-                                     (strs.offsets[b0:b1 + 1] - strs.offsets[b0]).copy()))
-    return out
-
-
 def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     import torch
     from paper_1701_03038_gb300 import _lib
     from paper_1701_03038_gb300._lib import PLAN_NO_FB, PLAN_NO_VITERBI
-    # the Viterbi pass and forward-backward are independent: plans of each
-    # kind (the batch split into --split-vit / --split-fb contiguous parts)
-    # run on their own streams so that their latency-bound launches overlap
+    # the Viterbi pass and forward-backward are independent: one plan each on
+    # its own stream, each cut into stream-parallel parts (FST_PLAN_PARTS),
+    # so that their latency-bound launches overlap
     budget = int(args.budget_gb * (1 << 30))
-
-    def plans_of(k, flags):
-        out = []
-        for sub in _split(strs, k):
-            out.append(f.plan(torch.from_numpy(sub.ids).to(dev), torch.from_numpy(sub.offsets).to(dev),
-                              mem_budget=budget // k, flags=flags))
-        return out
-
-    plans_v = plans_of(args.split_vit, PLAN_NO_FB)
-    plans_f = plans_of(args.split_fb, PLAN_NO_VITERBI)
+    ids = torch.from_numpy(strs.ids).to(dev)
+    off = torch.from_numpy(strs.offsets).to(dev)
+    plans_v = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB, parts=args.parts_vit)]
+    plans_f = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI, parts=args.parts_fb)]
     tuned = {}
     if args.driver in ("persistent", "persistent-all"):
         for p in plans_f:
@@ -576,8 +558,8 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
         "relaxations_per_pass": relax_pass, "waves": max(i["waves"] for i in infos_v + infos_f),
         "plan_gb": round(plan_bytes / 2**30, 2),
         "parallelism": "replicas" if world > 1 else "1 GPU",
-        "streams": f"{len(plans_v)} Viterbi and {len(plans_f)} forward-backward plan(s), each on its own CUDA "
-                   "stream; per-kernel times from one more step run serially",
+        "streams": f"a Viterbi plan of {args.parts_vit} and a forward-backward plan of {args.parts_fb} "
+                   "stream-parallel parts; per-kernel times from one more step run serially",
         "launch": "CUDA graph replay" if graph is not None else "host launches",
         "driver": {"viterbi": "persistent" if plans_v[0].driver()[0] else "one launch per position",
                    "forward_backward": "persistent" if plans_f[0].driver()[0] else "one launch per position",

@@ -247,6 +247,15 @@ FST_API int fst_set_batch_budget(fst_t* fst, int64_t mem_budget_bytes);
 #define FST_PLAN_SINGLE_WAVE 1
 #define FST_PLAN_NO_VITERBI 2   /* do not allocate Viterbi storage (keys, state maps) */
 #define FST_PLAN_NO_FB 4        /* do not allocate forward-backward storage */
+/* FST_PLAN_PARTS(k), k in 2..255, or-ed into flags: the batch is cut into k
+ * contiguous string ranges of about equal token counts, each a plan of its
+ * own (with its own waves and budget share) run on its own stream; a run
+ * forks from `stream` into the parts' streams and joins back (events, so a
+ * run can still be captured into a CUDA graph).  The positions of the parts
+ * proceed independently, which overlaps their latency-bound launches.  The
+ * parts share the count accumulators.  Not with the persistent driver nor
+ * the autotuner. */
+#define FST_PLAN_PARTS(k) ((((int32_t)(k)) & 0xff) << 8)
 FST_API int fst_plan_create(fst_t* fst, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                     int64_t mem_budget_bytes, int32_t flags, void* stream, fst_plan_t** out);
 FST_API int fst_plan_destroy(fst_plan_t* plan);

@@ -120,7 +120,20 @@ struct fst_plan_s {
   uint64_t barrier_limit_ns = 2000000000ull;
   uint32_t barrier_extra = 0;        // fault injection: blocks a barrier waits for beyond the grid
   uint32_t* gbar = nullptr;          // [2] grid barrier (arrivals, generation)
+  // stream-parallel parts (FST_PLAN_PARTS): sub-plans over contiguous string
+  // ranges, each run on its own stream; the plan itself then holds only the
+  // count accumulators that the parts share
+  std::vector<fst_plan_s*> parts;
+  std::vector<int32_t> part_b0;
+  std::vector<int64_t> part_tok0;
+  std::vector<cudaStream_t> part_stream;
+  std::vector<cudaEvent_t> part_event;  // [0] fork, [1 + i] the end of part i
+  bool borrowed_counts = false;         // a part: cnt64 / start64 / final64 belong to the parent
   ~fst_plan_s() {
+    for (fst_plan_s* q : parts) delete q;
+    for (cudaStream_t st : part_stream) cudaStreamDestroy(st);
+    for (cudaEvent_t e : part_event) cudaEventDestroy(e);
+    if (borrowed_counts) cnt64 = start64 = final64 = nullptr;
     for (Wave& w : waves) w.release();
 #define PLAN_FREE(x) dfree(x);
     PLAN_STORAGE(PLAN_FREE)
@@ -405,6 +418,88 @@ inline cudaStream_t as_stream(void* p) { return (cudaStream_t)p; }
 
 }  // namespace
 
+static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B, int64_t mem_budget_bytes,
+                       int32_t flags, void* stream, fst_plan_s* donor, fst_plan_t** out);
+
+// A plan of nparts stream-parallel parts: contiguous string ranges of about
+// equal token counts, each an ordinary plan with its own stream; the count
+// accumulators (and the expected start and final states) are the parent's,
+// shared by the parts (their float64 atomics add up across parts).
+static int plan_create_parts(fst_t* f, const int32_t* d_ids, const std::vector<int64_t>& h_off, int32_t B,
+                             int64_t budget, int32_t flags, cudaStream_t s, int32_t nparts, fst_plan_t** out) {
+  std::unique_ptr<fst_plan_s> P(new fst_plan_s());
+  P->fst = f;
+  P->B = B;
+  P->N = h_off[B];
+  P->flags = flags;
+  P->want_vit = !(flags & FST_PLAN_NO_VITERBI);
+  P->want_fb = !(flags & FST_PLAN_NO_FB);
+  int rc;
+  int32_t b0 = 0;
+  for (int32_t i = 0; i < nparts; ++i) {
+    // the part ends where the token count reaches its share
+    int32_t b1 = B;
+    if (i < nparts - 1) {
+      const int64_t goal = (P->N * (i + 1)) / nparts;
+      b1 = b0 + 1;
+      while (b1 < B - (nparts - 1 - i) && h_off[b1] < goal) ++b1;
+    }
+    std::vector<int64_t> off(b1 - b0 + 1);
+    for (int32_t b = b0; b <= b1; ++b) off[b - b0] = h_off[b] - h_off[b0];
+    int64_t* d_off = nullptr;
+    if ((rc = dalloc(&d_off, (int64_t)off.size()))) return rc;
+    cudaError_t e = cudaMemcpy(d_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice);
+    fst_plan_t* sub = nullptr;
+    rc = e == cudaSuccess ? plan_create(f, d_ids ? d_ids + h_off[b0] : nullptr, d_off, b1 - b0,
+                                        budget > 0 ? std::max<int64_t>(budget / nparts, 1) : 0, flags & 0xff,
+                                        (void*)s, nullptr, &sub)
+                          : cuda_fail(e, "part offsets");
+    dfree(d_off);
+    if (rc) return rc;
+    P->parts.push_back(sub);
+    P->part_b0.push_back(b0);
+    P->part_tok0.push_back(h_off[b0]);
+    P->relax += sub->relax;
+    P->bytes += sub->bytes;
+    P->max_len = std::max(P->max_len, sub->max_len);
+    b0 = b1;
+  }
+  if (P->want_fb) {
+    if ((rc = alloc_track(P.get(), &P->cnt64, f->A)) || (rc = alloc_track(P.get(), &P->start64, f->Q)) ||
+        (rc = alloc_track(P.get(), &P->final64, f->Q)))
+      return rc;
+    for (fst_plan_s* q : P->parts) {
+      dfree(q->cnt64);
+      dfree(q->start64);
+      dfree(q->final64);
+      q->cnt64 = P->cnt64;
+      q->start64 = P->start64;
+      q->final64 = P->final64;
+      q->borrowed_counts = true;
+    }
+  }
+  P->part_event.resize(nparts + 1, nullptr);
+  for (cudaEvent_t& e : P->part_event) FST_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  P->part_stream.resize(nparts, nullptr);
+  for (cudaStream_t& st : P->part_stream) FST_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  *out = P.release();
+  return FST_OK;
+}
+
+// The parts start after the work queued on s and s waits for all of them.
+static int parts_fork(fst_plan_s* P, cudaStream_t s) {
+  FST_CUDA(cudaEventRecord(P->part_event[0], s));
+  for (cudaStream_t st : P->part_stream) FST_CUDA(cudaStreamWaitEvent(st, P->part_event[0], 0));
+  return FST_OK;
+}
+static int parts_join(fst_plan_s* P, cudaStream_t s) {
+  for (size_t i = 0; i < P->parts.size(); ++i) {
+    FST_CUDA(cudaEventRecord(P->part_event[1 + i], P->part_stream[i]));
+    FST_CUDA(cudaStreamWaitEvent(s, P->part_event[1 + i], 0));
+  }
+  return FST_OK;
+}
+
 // Plan creation.  `donor` (owned: always released here) is an earlier plan
 // of the same handle whose device storage is taken over when it is large
 // enough, so that repeated batch calls neither allocate nor clear it again.
@@ -424,6 +519,8 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
   const int64_t N = h_off[B];
   if (N >= ((int64_t)1 << 31)) { set_error("too many tokens"); return FST_ERR_UNSUPPORTED; }
   if (N > 0 && !d_ids) { set_error("ids is NULL"); return FST_ERR_INVALID_ARG; }
+  const int32_t nparts = std::min<int32_t>((flags >> 8) & 0xff, std::max(B, 1));
+  if (nparts > 1) return plan_create_parts(f, d_ids, h_off, B, mem_budget_bytes, flags, s, nparts, out);
   fst_plan_s* P = new fst_plan_s();
   P->fst = f;
   P->B = B;
@@ -595,6 +692,26 @@ extern "C" int fst_plan_info(const fst_plan_t* P, int32_t* num_strings, int64_t*
                              int64_t* fb_launches, int64_t* device_bytes) {
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
   int64_t vl = 0, fl = 0;
+  if (!P->parts.empty()) {
+    int32_t nw = 0;
+    for (fst_plan_s* q : P->parts) {
+      int32_t w = 0;
+      int64_t v = 0, fb = 0;
+      fst_plan_info(q, nullptr, nullptr, &w, nullptr, nullptr, &v, &fb, nullptr);
+      nw = std::max(nw, w);
+      vl += v;
+      fl += fb - 1;  // the parts share one counts-out launch
+    }
+    if (num_strings) *num_strings = P->B;
+    if (num_tokens) *num_tokens = P->N;
+    if (num_waves) *num_waves = nw;
+    if (max_len) *max_len = P->max_len;
+    if (relaxations) *relaxations = P->relax;
+    if (viterbi_launches) *viterbi_launches = vl;
+    if (fb_launches) *fb_launches = fl + 1;
+    if (device_bytes) *device_bytes = P->bytes;
+    return FST_OK;
+  }
   for (const Wave& w : P->waves) {
     if (P->driver == FST_DRIVER_PERSISTENT) {
       // overflow clear, the persistent pass, final, backtrace
@@ -632,6 +749,17 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
   int rc;
   // the Viterbi run reuses the accumulators and pool a pending backward pass needs
   P->forward_done = false;
+  if (!P->parts.empty()) {
+    if ((rc = parts_fork(P, s))) return rc;
+    for (size_t i = 0; i < P->parts.size(); ++i) {
+      const int32_t b0 = P->part_b0[i];
+      const int64_t k0 = P->part_tok0[i];
+      if ((rc = fst_plan_viterbi(P->parts[i], d_scores + b0, d_paths + k0, d_olabels ? d_olabels + k0 : nullptr,
+                                 d_status ? d_status + b0 : nullptr, P->part_stream[i])))
+        return rc;
+    }
+    return parts_join(P, s);
+  }
   for (const Wave& W : P->waves)
     if ((rc = run_viterbi_wave(P, W, d_scores, d_paths, d_olabels, d_status, s))) return rc;
   return FST_OK;
@@ -640,9 +768,20 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
 extern "C" int fst_plan_forward(fst_plan_t* P, double* d_logz, int32_t* d_status, void* stream) {
   if (!P || !d_logz) { set_error("fst_plan_forward: bad arguments"); return FST_ERR_INVALID_ARG; }
   if (!P->want_fb) { set_error("plan was created without forward-backward storage"); return FST_ERR_STATE; }
-  if (P->waves.size() > 1) { set_error("fst_plan_forward needs a single-wave plan"); return FST_ERR_STATE; }
   cudaStream_t s = as_stream(stream);
   int rc;
+  if (!P->parts.empty()) {
+    if ((rc = parts_fork(P, s))) return rc;
+    for (size_t i = 0; i < P->parts.size(); ++i) {
+      const int32_t b0 = P->part_b0[i];
+      if ((rc = fst_plan_forward(P->parts[i], d_logz + b0, d_status ? d_status + b0 : nullptr, P->part_stream[i])))
+        return rc;
+    }
+    if ((rc = parts_join(P, s))) return rc;
+    P->forward_done = true;
+    return FST_OK;
+  }
+  if (P->waves.size() > 1) { set_error("fst_plan_forward needs a single-wave plan"); return FST_ERR_STATE; }
   for (const Wave& W : P->waves)
     if ((rc = run_forward_wave(P, W, s, d_status))) return rc;
   if (P->B > 0) FST_CUDA(cudaMemcpyAsync(d_logz, P->logz, (size_t)P->B * 8, cudaMemcpyDeviceToDevice, s));
@@ -661,6 +800,17 @@ extern "C" int fst_plan_backward_ex(fst_plan_t* P, const float* d_weights, float
   const bool states = d_start || d_final;
   int rc;
   if ((rc = counts_begin(P, states, s))) return rc;
+  if (!P->parts.empty()) {
+    if ((rc = parts_fork(P, s))) return rc;
+    for (size_t i = 0; i < P->parts.size(); ++i) {
+      fst_plan_s* q = P->parts[i];
+      const float* w = d_weights ? d_weights + P->part_b0[i] : nullptr;
+      for (const Wave& W : q->waves)
+        if ((rc = run_backward_wave(q, W, w, states, P->part_stream[i]))) return rc;
+    }
+    if ((rc = parts_join(P, s))) return rc;
+    return counts_end(P, d_counts, d_start, d_final, s);
+  }
   for (const Wave& W : P->waves)
     if ((rc = run_backward_wave(P, W, d_weights, states, s))) return rc;
   return counts_end(P, d_counts, d_start, d_final, s);
@@ -681,6 +831,26 @@ extern "C" int fst_plan_forward_backward_ex(fst_plan_t* P, const float* d_weight
   const bool bwd = d_counts || states;
   int rc;
   if (bwd && (rc = counts_begin(P, states, s))) return rc;
+  if (!P->parts.empty()) {
+    if ((rc = parts_fork(P, s))) return rc;
+    for (size_t i = 0; i < P->parts.size(); ++i) {
+      fst_plan_s* q = P->parts[i];
+      cudaStream_t st = P->part_stream[i];
+      const int32_t b0 = P->part_b0[i];
+      const float* w = d_weights ? d_weights + b0 : nullptr;
+      for (const Wave& W : q->waves) {
+        if ((rc = run_forward_wave(q, W, st, d_status ? d_status + b0 : nullptr))) return rc;
+        if (bwd && (rc = run_backward_wave(q, W, w, states, st))) return rc;
+      }
+      if (q->B > 0) FST_CUDA(cudaMemcpyAsync(d_logz + b0, q->logz, (size_t)q->B * 8, cudaMemcpyDeviceToDevice, st));
+      q->forward_done = q->waves.size() <= 1;
+    }
+    if ((rc = parts_join(P, s))) return rc;
+    if (bwd && (rc = counts_end(P, d_counts, d_start, d_final, s))) return rc;
+    P->forward_done = true;
+    for (fst_plan_s* q : P->parts) P->forward_done = P->forward_done && q->forward_done;
+    return FST_OK;
+  }
   for (const Wave& W : P->waves) {
     if ((rc = run_forward_wave(P, W, s, d_status))) return rc;
     if (bwd && (rc = run_backward_wave(P, W, d_weights, states, s))) return rc;
@@ -745,6 +915,19 @@ extern "C" int fst_forward_backward_batch(fst_t* f, const int32_t* d_ids, const 
 
 extern "C" int fst_plan_live_work(fst_plan_t* P, int64_t* entries, int64_t* arcs, void* stream) {
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
+  if (!P->parts.empty()) {
+    int64_t e = 0, a = 0;
+    for (fst_plan_s* q : P->parts) {
+      int64_t qe = 0, qa = 0;
+      const int rc = fst_plan_live_work(q, &qe, &qa, stream);
+      if (rc) return rc;
+      e += qe;
+      a = (a < 0 || qa < 0) ? -1 : a + qa;
+    }
+    if (entries) *entries = e;
+    if (arcs) *arcs = a;
+    return FST_OK;
+  }
   cudaStream_t s = as_stream(stream);
   int64_t top = 0;
   FST_CUDA(cudaMemcpyAsync(&top, P->pool_top, 8, cudaMemcpyDeviceToHost, s));
@@ -777,6 +960,7 @@ extern "C" int fst_plan_live_work(fst_plan_t* P, int64_t* entries, int64_t* arcs
 extern "C" int fst_plan_limit_pool(fst_plan_t* P, int64_t entries) {
   if (!P || entries < 0) { set_error("fst_plan_limit_pool: bad arguments"); return FST_ERR_INVALID_ARG; }
   P->pool_limit = entries;
+  for (fst_plan_s* q : P->parts) q->pool_limit = entries;
   return FST_OK;
 }
 
@@ -785,6 +969,10 @@ extern "C" int fst_plan_set_driver(fst_plan_t* P, int32_t driver, int32_t grid_b
       barrier_timeout_us < 0) {
     set_error("fst_plan_set_driver: bad arguments");
     return FST_ERR_INVALID_ARG;
+  }
+  if (driver == FST_DRIVER_PERSISTENT && P->parts.size() > 1) {
+    set_error("the persistent driver runs one pass at a time: a plan of several parts cannot use it");
+    return FST_ERR_UNSUPPORTED;
   }
   if (driver == FST_DRIVER_PERSISTENT) {
     int dev = 0, coop = 0;
@@ -895,6 +1083,7 @@ static int tune_time(fst_plan_s* P, cudaStream_t s, int reps, float* d_scores, i
 extern "C" int fst_plan_autotune(fst_plan_t* P, void* stream, int32_t flags, int32_t* driver, int32_t* grid_blocks,
                                  double* best_ms) {
   if (!P || (flags & ~FST_TUNE_REFRESH)) { set_error("fst_plan_autotune: bad arguments"); return FST_ERR_INVALID_ARG; }
+  if (!P->parts.empty()) { set_error("fst_plan_autotune: a plan of several parts is not tuned"); return FST_ERR_UNSUPPORTED; }
   cudaStream_t s = as_stream(stream);
   const std::string key = tune_key(P);
   TuneConf best;
@@ -991,6 +1180,7 @@ extern "C" int fst_plan_fault_inject(fst_plan_t* P, int32_t kind, int64_t value)
     return FST_ERR_INVALID_ARG;
   }
   P->barrier_extra = kind == FST_FAULT_BARRIER_STALL ? (uint32_t)value : 0u;
+  for (fst_plan_s* q : P->parts) q->barrier_extra = P->barrier_extra;
   return FST_OK;
 }
 
@@ -998,12 +1188,32 @@ extern "C" int fst_plan_profile(fst_plan_t* P, int32_t enable) {
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
   P->prof.on = enable != 0;
   P->prof.used = 0;
+  for (fst_plan_s* q : P->parts) {
+    q->prof.on = P->prof.on;
+    q->prof.used = 0;
+  }
   return FST_OK;
 }
 
 extern "C" int fst_plan_profile_read(fst_plan_t* P, double* ms_by_kind, int64_t* launches_by_kind) {
   if (!P) { set_error("plan is NULL"); return FST_ERR_INVALID_ARG; }
-  return P->prof.read(ms_by_kind, launches_by_kind);
+  double ms[FST_PROF_KINDS];
+  int64_t n[FST_PROF_KINDS];
+  int rc = P->prof.read(ms, n);
+  for (fst_plan_s* q : P->parts) {
+    double qm[FST_PROF_KINDS];
+    int64_t qn[FST_PROF_KINDS];
+    if (rc || (rc = q->prof.read(qm, qn))) return rc;
+    for (int k = 0; k < FST_PROF_KINDS; ++k) {
+      ms[k] += qm[k];
+      n[k] += qn[k];
+    }
+  }
+  for (int k = 0; k < FST_PROF_KINDS; ++k) {
+    if (ms_by_kind) ms_by_kind[k] = ms[k];
+    if (launches_by_kind) launches_by_kind[k] = n[k];
+  }
+  return rc;
 }
 
 extern "C" int fst_set_batch_budget(fst_t* f, int64_t mem_budget_bytes) {

@@ -377,7 +377,11 @@ class Fst:
         check(self._lib.fst_set_batch_budget(self._h, int(nbytes)), "fst_set_batch_budget")
 
     def plan(self, ids: torch.Tensor, offsets: torch.Tensor, mem_budget: int = 0, flags: int = 0,
-             stream=None) -> "Plan":
+             stream=None, parts: int = 1) -> "Plan":
+        """A batch plan (see fst_plan_create); ``parts`` > 1 runs the batch as
+        that many stream-parallel parts (FST_PLAN_PARTS)."""
+        if parts > 1:
+            flags |= (int(parts) & 0xFF) << 8
         return Plan(self, ids, offsets, mem_budget=mem_budget, flags=flags, stream=stream)
 
     def viterbi_batch(self, ids: torch.Tensor, offsets: torch.Tensor, stream=None):

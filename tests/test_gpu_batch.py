@@ -279,3 +279,57 @@ def test_autotune_keeps_results_and_caches(c2s, tmp_path, monkeypatch):
     q = f.plan(ids, off)
     again = q.autotune()
     assert again == choice  # cached: same configuration, same recorded time
+
+
+@pytest.mark.parametrize("parts", [2, 3, 7])
+def test_stream_parallel_parts(c2s, parts):
+    # a plan cut into stream-parallel parts: Viterbi bit-identical to the
+    # one-part plan, forward-backward held to the oracle, the split forward /
+    # backward calls and graph capture work the same, the parts' live work
+    # adds up to the whole
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    ref = f.plan(ids, off)
+    ref.viterbi()
+    ref.forward_backward()
+    torch.cuda.synchronize()
+    p = f.plan(ids, off, parts=parts)
+    info = p.info()
+    assert info["strings"] == strs.count and info["relaxations"] == ref.info()["relaxations"]
+    p.viterbi()
+    p.forward_backward()
+    torch.cuda.synchronize()
+    assert torch.equal(p.scores, ref.scores) and torch.equal(p.paths, ref.paths)
+    assert torch.equal(p.olabels, ref.olabels) and torch.equal(p.status, ref.status)
+    check_batch_fb(o, strs, p.logz[:strs.count], p.counts[:o.A])
+    assert p.live_work() == ref.live_work()
+    # weighted split forward / backward (single-wave parts)
+    q = f.plan(ids, off, flags=_lib.PLAN_SINGLE_WAVE, parts=parts)
+    w = torch.linspace(-1.0, 2.0, strs.count, dtype=torch.float32, device="cuda")
+    q.forward()
+    q.backward(w)
+    torch.cuda.synchronize()
+    check_batch_fb(o, strs, q.logz[:strs.count], q.counts[:o.A], weights=w.double().cpu().numpy())
+    # captured and replayed
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        p.viterbi(stream=s)
+        p.forward_backward(stream=s)
+    p.scores.fill_(0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(p.scores, ref.scores)
+    check_batch_fb(o, strs, p.logz[:strs.count], p.counts[:o.A])
+    # profiles add up over the parts
+    p.profile(True)
+    p.viterbi()
+    torch.cuda.synchronize()
+    prof = p.profile_read()
+    p.profile(False)
+    assert prof["vit_step"][1] > 0
+    with pytest.raises(_lib.FstError):
+        p.set_driver(_lib.DRIVER_PERSISTENT)
