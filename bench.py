@@ -87,7 +87,7 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
     ap.add_argument("--parts-vit", type=int, default=2, help="stream-parallel parts of the Viterbi plan")
-    ap.add_argument("--parts-fb", type=int, default=4, help="stream-parallel parts of the forward-backward plan")
+    ap.add_argument("--parts-fb", type=int, default=8, help="stream-parallel parts of the forward-backward plan")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -721,6 +721,7 @@ def bench_plain(args, rank, world, dev, fa, strs, f, stats):
     sl = [bool(coef[2] + coef[3] * n + coef[4] * a < coef[0] + coef[1] * n)
           for n, a in zip(lens, [int(stats[0][strs.get(b)].sum()) for b in range(strs.count)])]
     out["plain_viterbi"] = {"method": "automatic (fst_autotune_plain on the first strings)",
+                            "forward_backward_driver": "see plain_fb_driver",
                             "coef_us": [round(float(c), 4) for c in coef],
                             "strings_on_slice_kernel": int(sum(sl)), "strings": strs.count}
     # per-kernel times and live work of one more step, with events (frontier

@@ -40,6 +40,7 @@ SIGNATURES = {
     "fst_viterbi": [vp, vp, i32, vp, vp, vp],
     "fst_viterbi_slice": [vp, vp, i32, vp, vp],
     "fst_set_plain_method": [vp, i32],
+    "fst_set_plain_driver": [vp, i32, i32],
     "fst_autotune_plain": [vp, vp, vp, i32, vp],
     "fst_forward_backward_slice": [vp, vp, i32, vp, vp],
     "fst_set_slice_order": [vp, i32],

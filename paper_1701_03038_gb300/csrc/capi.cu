@@ -146,6 +146,8 @@ struct PlainWs {
   int32_t* vmap = nullptr;              // [2][Q]
   int32_t *tok_sym = nullptr, *tok_b = nullptr;
   int32_t* iota = nullptr;              // step list: token t-1 is the only slot of position t
+  int32_t* step0 = nullptr;             // [cap_n + 2] step offsets of the persistent passes: step0[t] = t - 1
+  uint32_t* gbar = nullptr;             // [2] grid barrier of the persistent passes
   int64_t* zero64 = nullptr;            // staging offsets: one token per step
   int64_t *slot_base = nullptr, *step_rng = nullptr;
   uint32_t* scnt = nullptr;
@@ -170,7 +172,7 @@ struct PlainWs {
   bool last_fb = false;                 // the last call was forward-backward (pool_n holds arc counts)
   ~PlainWs() {
     dfree(acc); dfree(beta); dfree(vmap); dfree(tok_sym); dfree(tok_b); dfree(iota); dfree(zero64);
-    dfree(slot_base); dfree(step_rng); dfree(scnt); dfree(pool_base); dfree(pool_cnt); dfree(mkey); dfree(ekey);
+    dfree(step0); dfree(gbar); dfree(slot_base); dfree(step_rng); dfree(scnt); dfree(pool_base); dfree(pool_cnt); dfree(mkey); dfree(ekey);
     dfree(csum); dfree(esum); dfree(paths); dfree(olabels); dfree(stage); dfree(stage_b); dfree(pool_q);
     dfree(pool_x); dfree(pool_n); dfree(pool_v); dfree(cnt); dfree(comp); dfree(counts_out); dfree(jfinal); dfree(status);
     dfree(bw_n); dfree(score); dfree(logz); dfree(bw_off); dfree(pool_top); dfree(flags);
@@ -188,7 +190,7 @@ int plain_init(fst_s* f) {
   if ((rc = dalloc(&w->acc, 4 * Q)) || (rc = dalloc(&w->beta, 2 * Q)) || (rc = dalloc(&w->vmap, 2 * Q)) ||
       (rc = dalloc(&w->jfinal, 1)) || (rc = dalloc(&w->status, 1)) || (rc = dalloc(&w->score, 1)) ||
       (rc = dalloc(&w->logz, 1)) || (rc = dalloc(&w->bw_n, 1)) || (rc = dalloc(&w->bw_off, 1)) ||
-      (rc = dalloc(&w->pool_top, 1)) || (rc = dalloc(&w->flags, 2)))
+      (rc = dalloc(&w->pool_top, 1)) || (rc = dalloc(&w->flags, 2)) || (rc = dalloc(&w->gbar, 2)))
     return rc;
   FST_CUDA(cudaMemset(w->acc, 0, (size_t)4 * Q * sizeof(unsigned long long)));
   FST_CUDA(cudaMemset(w->beta, 0, (size_t)2 * Q * sizeof(double)));
@@ -204,16 +206,19 @@ int plain_reserve(PlainWs* w, int64_t n, int64_t stage, int64_t pool) {
   int rc;
   if (n > w->cap_n) {
     const int64_t c = std::max<int64_t>(n, 2 * w->cap_n);
-    dfree(w->tok_sym); dfree(w->tok_b); dfree(w->iota); dfree(w->zero64); dfree(w->slot_base);
+    dfree(w->tok_sym); dfree(w->tok_b); dfree(w->iota); dfree(w->step0); dfree(w->zero64); dfree(w->slot_base);
     dfree(w->step_rng); dfree(w->scnt); dfree(w->pool_base); dfree(w->pool_cnt); dfree(w->mkey); dfree(w->ekey);
     dfree(w->csum); dfree(w->esum); dfree(w->paths); dfree(w->olabels);
     w->cap_n = 0;
-    if ((rc = dalloc(&w->iota, c)) || (rc = dalloc(&w->slot_base, c)) || (rc = dalloc(&w->step_rng, 2 * (c + 2))))
+    if ((rc = dalloc(&w->iota, c)) || (rc = dalloc(&w->slot_base, c)) || (rc = dalloc(&w->step_rng, 2 * (c + 2))) ||
+        (rc = dalloc(&w->step0, c + 2)))
       return rc;
     {
-      std::vector<int32_t> io(c);
+      std::vector<int32_t> io(c), s0(c + 2);
       for (int64_t i = 0; i < c; ++i) io[i] = (int32_t)i;
+      for (int64_t t = 0; t < c + 2; ++t) s0[t] = (int32_t)std::max<int64_t>(t - 1, 0);
       FST_CUDA(cudaMemcpy(w->iota, io.data(), (size_t)c * 4, cudaMemcpyHostToDevice));
+      FST_CUDA(cudaMemcpy(w->step0, s0.data(), (size_t)(c + 2) * 4, cudaMemcpyHostToDevice));
     }
     if ((rc = dalloc(&w->tok_sym, c)) || (rc = dalloc(&w->tok_b, c)) || (rc = dalloc(&w->zero64, c)) ||
         (rc = dalloc(&w->scnt, c)) || (rc = dalloc(&w->pool_base, c)) || (rc = dalloc(&w->pool_cnt, c)) ||
@@ -656,10 +661,22 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   const LayoutView L = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
   const FrontierState S = plain_state(f);
-  if (n >= 1) PLAIN_PROF(FST_PROF_FWD_FIRST, launch_fwd_first(L, T, plain_step(f, n, 1, 0), S, s));
-  for (int32_t t = 1; t <= n; ++t) {
-    PLAIN_PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, plain_step(f, n, t, t - 1), S, s));
-    PLAIN_PROF(FST_PROF_FWD_STEP, launch_fwd_step(L, T, plain_step(f, n, t, t + 1), S, s));
+  // persistent driver: one cooperative launch per pass, positions separated
+  // by grid barriers (the barrier words are cleared before each pass)
+  const bool persist = f->plain_fb_driver == FST_DRIVER_PERSISTENT && n >= 1;
+  const int32_t pgrid = std::max(1, std::min(f->plain_fb_grid > 0 ? f->plain_fb_grid : f->num_sms,
+                                             std::min(persist_grid_limit(1), persist_grid_limit(2))));
+  const WaveSteps D{w->step0, n};
+  const GridSync G{w->gbar, 0u, 2000000000ull};
+  if (persist) {
+    FST_CUDA(cudaMemsetAsync(w->gbar, 0, 8, s));
+    PLAIN_PROF(FST_PROF_FWD_STEP, launch_fwd_persist(L, T, D, S, pgrid, G, s));
+  } else {
+    if (n >= 1) PLAIN_PROF(FST_PROF_FWD_FIRST, launch_fwd_first(L, T, plain_step(f, n, 1, 0), S, s));
+    for (int32_t t = 1; t <= n; ++t) {
+      PLAIN_PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, plain_step(f, n, t, t - 1), S, s));
+      PLAIN_PROF(FST_PROF_FWD_STEP, launch_fwd_step(L, T, plain_step(f, n, t, t + 1), S, s));
+    }
   }
   PLAIN_PROF(FST_PROF_FB_FINAL, launch_fb_final(S, 1, w->logz, w->status, s));
   w->last_fb = true;
@@ -667,8 +684,13 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
     const CountView C{0, w->cnt, w->comp, nullptr};
     FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
     FST_CUDA(cudaMemsetAsync(w->comp, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
-    for (int32_t t = n; t >= 1; --t)
-      PLAIN_PROF(FST_PROF_BWD_STEP, launch_bwd_step(L, T, plain_step(f, n, t, t - 1), S, C, s));
+    if (persist) {
+      FST_CUDA(cudaMemsetAsync(w->gbar, 0, 8, s));
+      PLAIN_PROF(FST_PROF_BWD_STEP, launch_bwd_persist(L, T, D, S, C, pgrid, G, s));
+    } else {
+      for (int32_t t = n; t >= 1; --t)
+        PLAIN_PROF(FST_PROF_BWD_STEP, launch_bwd_step(L, T, plain_step(f, n, t, t - 1), S, C, s));
+    }
     PLAIN_PROF(FST_PROF_COUNTS, launch_counts_out(f->A, C, w->counts_out, s));
     if (f->A > 0)
       FST_CUDA(cudaMemcpy(arc_posteriors, w->counts_out, (size_t)f->A * 4, cudaMemcpyDeviceToHost));
@@ -676,6 +698,10 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   int32_t st = 0;
   FST_CUDA(cudaMemcpy(log_z, w->logz, 8, cudaMemcpyDeviceToHost));
   FST_CUDA(cudaMemcpy(&st, w->status, 4, cudaMemcpyDeviceToHost));
+  if (st == FST_ERR_TIMEOUT) {
+    set_error("a grid barrier of the persistent pass timed out");
+    return FST_ERR_TIMEOUT;
+  }
   if (st != FST_OK) {
     set_error("no accepting path");
     return FST_ERR_NO_PATH;
@@ -811,7 +837,14 @@ extern "C" int fst_autotune_plain(fst_t* f, const int32_t* ids, const int64_t* o
     ys.push_back(t[1]);
   }
   double cf[2] = {0, 0}, cs[3] = {0, 0, 0};
-  if (!least_squares(Xf, yf, 2, cf) || !least_squares(Xs, ys, 3, cs)) {
+  // a fit needs strings of several lengths and slice sizes; with fewer the
+  // mean times alone decide
+  std::vector<double> ns, ss;
+  for (size_t i = 0; i < Xs.size(); ++i) { ns.push_back(Xs[i][1]); ss.push_back(Xs[i][2]); }
+  std::sort(ns.begin(), ns.end());
+  std::sort(ss.begin(), ss.end());
+  const bool spread = Xs.size() >= 4 && ns.front() < ns.back() && ss.front() < ss.back();
+  if (!spread || !least_squares(Xf, yf, 2, cf) || !least_squares(Xs, ys, 3, cs)) {
     // too few distinct strings for a fit: compare the mean times alone
     double mf = 0, ms = 0;
     for (size_t i = 0; i < yf.size(); ++i) { mf += yf[i]; ms += ys[i]; }
@@ -825,5 +858,48 @@ extern "C" int fst_autotune_plain(fst_t* f, const int32_t* ids, const int64_t* o
   }
   f->plain_tuned = true;
   f->plain_method = FST_PLAIN_AUTO;
+  // forward-backward: per-position launches or persistent passes, whichever
+  // decodes the sample faster
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, f->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    coop = 0;
+  }
+  if (coop && std::min(persist_grid_limit(1), persist_grid_limit(2)) > 0) {
+    double tfb[2] = {0, 0};
+    for (int d = 0; d < 2; ++d) {
+      f->plain_fb_driver = d == 0 ? FST_DRIVER_LAUNCH : FST_DRIVER_PERSISTENT;
+      for (int32_t b = -1; b < B; ++b) {
+        const int32_t bb = b < 0 ? 0 : b;
+        double lz = 0;
+        const auto t0 = std::chrono::steady_clock::now();
+        const int rc = fst_forward_backward(f, ids + offsets[bb], (int32_t)(offsets[bb + 1] - offsets[bb]), &lz,
+                                            nullptr);
+        if (rc != FST_OK && rc != FST_ERR_NO_PATH) return rc;
+        if (b >= 0) tfb[d] += std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+      }
+    }
+    f->plain_fb_driver = tfb[1] < tfb[0] ? FST_DRIVER_PERSISTENT : FST_DRIVER_LAUNCH;
+  }
+  return FST_OK;
+}
+
+extern "C" int fst_set_plain_driver(fst_t* f, int32_t driver, int32_t grid_blocks) {
+  if (!f || (driver != FST_DRIVER_LAUNCH && driver != FST_DRIVER_PERSISTENT) || grid_blocks < 0) {
+    set_error("fst_set_plain_driver: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  DevGuard g(f->device);
+  if (driver == FST_DRIVER_PERSISTENT) {
+    int coop = 0;
+    FST_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, f->device));
+    const int cap = std::min(persist_grid_limit(1), persist_grid_limit(2));
+    if (!coop || cap <= 0 || grid_blocks > cap) {
+      set_error("no co-resident grid of %d blocks for the persistent passes (at most %d)", grid_blocks, cap);
+      return FST_ERR_UNSUPPORTED;
+    }
+  }
+  f->plain_fb_driver = driver;
+  f->plain_fb_grid = grid_blocks;
   return FST_OK;
 }

@@ -151,6 +151,8 @@ struct fst_s {
   // single-string Viterbi: frontier kernels, the slice-wide kernel, or the
   // cheaper of the two by a cost model fitted by fst_autotune_plain
   int32_t plain_method = 0;
+  int32_t plain_fb_driver = 0;   // single-string forward-backward: FST_DRIVER_LAUNCH or _PERSISTENT
+  int32_t plain_fb_grid = 0;     // persistent grid (0 = one block per SM)
   bool plain_tuned = false;
   double plain_coef[5] = {0, 0, 0, 0, 0};  // frontier d0 + d1 n; slice c0 + c1 n + c2 (slice arcs)
 };

@@ -666,8 +666,10 @@ __device__ __forceinline__ void add_count(const CountView& C, int32_t id, float 
   if (C.batched) {
     atomicAdd(C.cnt64 + id, (double)g);
   } else {
-    // compensated float32 summation (one string: one writer per arc and step)
-    const float s0 = C.cnt[id], cmp = C.comp[id];
+    // compensated float32 summation (one string: one writer per arc and
+    // step; read through L2, as a persistent pass meets the same arc at
+    // later positions in other blocks)
+    const float s0 = __ldcg(C.cnt + id), cmp = __ldcg(C.comp + id);
     const float y = __fsub_rn(g, cmp);
     const float s1 = __fadd_rn(s0, y);
     C.comp[id] = __fsub_rn(__fsub_rn(s1, s0), y);

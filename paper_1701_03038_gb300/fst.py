@@ -215,6 +215,12 @@ class Fst:
         or PLAIN_AUTO (see fst_set_plain_method)."""
         check(self._lib.fst_set_plain_method(self._h, int(method)), "fst_set_plain_method")
 
+    def set_plain_driver(self, driver: int, grid_blocks: int = 0):
+        """Driver of the single-string forward-backward: _lib.DRIVER_LAUNCH or
+        _lib.DRIVER_PERSISTENT (see fst_set_plain_driver)."""
+        with torch.cuda.device(self.device):
+            check(self._lib.fst_set_plain_driver(self._h, int(driver), int(grid_blocks)), "fst_set_plain_driver")
+
     def autotune_plain(self, ids, offsets) -> np.ndarray:
         """Calibrate the automatic choice of the single-string Viterbi kernels on
         sample strings (see fst_autotune_plain); returns the fitted

@@ -267,3 +267,28 @@ def test_plain_viterbi_methods_agree():
         assert_viterbi_equal(s, p, ol, st, o.viterbi(x))
     with pytest.raises(_lib.FstError):
         f.set_plain_method(7)
+
+
+@pytest.mark.parametrize("grid", [0, 1, 5])
+def test_plain_forward_backward_persistent_driver(grid):
+    # one cooperative launch per pass for a single string (grid 0 = one block
+    # per SM): log Z and posteriors against the oracle, as the launch driver
+    from paper_1701_03038_gb300 import _lib
+    fa, strs = synth.make_config("c2", scale=0.02, strings=8)
+    f, o = _fst(fa), oracle.Fst(fa)
+    f.set_plain_driver(_lib.DRIVER_PERSISTENT, grid)
+    iid = synth.make_strings(fa, 2, 5, 15, seed=9, kind="iid")
+    for x in [strs.get(b) for b in range(strs.count)] + [iid.get(0), np.zeros(0, np.int32)]:
+        lz, cnt, st = f.forward_backward(x)
+        ofb = o.forward_backward(x)
+        assert st == ofb["status"]
+        assert_logz_close(lz, ofb["logz"])
+        assert_counts_close(cnt, ofb["counts"])
+    f.set_plain_driver(_lib.DRIVER_LAUNCH)
+    coef = f.autotune_plain(strs.ids, strs.offsets)  # also picks the driver
+    for b in range(3):
+        x = strs.get(b)
+        lz, cnt, st = f.forward_backward(x)
+        assert_logz_close(lz, o.forward_backward(x)["logz"])
+    with pytest.raises(_lib.FstError):
+        f.set_plain_driver(_lib.DRIVER_PERSISTENT, 10 ** 7)
