@@ -721,7 +721,6 @@ def bench_plain(args, rank, world, dev, fa, strs, f, stats):
     sl = [bool(coef[2] + coef[3] * n + coef[4] * a < coef[0] + coef[1] * n)
           for n, a in zip(lens, [int(stats[0][strs.get(b)].sum()) for b in range(strs.count)])]
     out["plain_viterbi"] = {"method": "automatic (fst_autotune_plain on the first strings)",
-                            "forward_backward_driver": "see plain_fb_driver",
                             "coef_us": [round(float(c), 4) for c in coef],
                             "strings_on_slice_kernel": int(sum(sl)), "strings": strs.count}
     # per-kernel times and live work of one more step, with events (frontier
