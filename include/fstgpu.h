@@ -147,20 +147,21 @@ FST_API int fst_set_plain_method(fst_t* fst, int32_t method);
  * and timed on the host; the frontier time is fitted as d0 + d1 n and the
  * slice time as c0 + c1 n + c2 S (S = the arcs of the string's slices), by
  * least squares (with fewer than four strings of different sizes the mean
- * times decide); the method is set to FST_PLAIN_AUTO.  The forward-backward
- * driver (fst_set_plain_driver) is then chosen by timing both drivers on
- * the same strings.  coef [5] or NULL receives d0, d1, c0, c1, c2
- * (microseconds).  Synchronous. */
+ * times decide); the method is set to FST_PLAIN_AUTO.  Before that, the
+ * driver of the frontier kernels (fst_set_plain_driver: launches, or
+ * persistent passes of 1, 8, 32 or one-per-SM blocks) is chosen by timing
+ * Viterbi and forward-backward on the same strings.  coef [5] or NULL
+ * receives d0, d1, c0, c1, c2 (microseconds).  Synchronous. */
 FST_API int fst_autotune_plain(fst_t* fst, const int32_t* ids, const int64_t* offsets, int32_t B, double* coef);
 
-/* Driver of the single-string fst_forward_backward: FST_DRIVER_LAUNCH (one
- * launch per position and kernel kind, the default) or
- * FST_DRIVER_PERSISTENT (one cooperative launch for the forward pass and
- * one for the backward pass, grid_blocks blocks, 0 = one per SM, positions
- * separated by bounded grid barriers; a barrier that times out makes the
- * call return FST_ERR_TIMEOUT).  fst_autotune_plain also picks this, by
- * timing both on its sample.  FST_ERR_UNSUPPORTED without cooperative
- * launches or for a grid that cannot be co-resident. */
+/* Driver of the single-string frontier kernels (fst_forward_backward, and
+ * fst_viterbi when it uses them): FST_DRIVER_LAUNCH (one launch per
+ * position and kernel kind, the default) or FST_DRIVER_PERSISTENT (one
+ * cooperative launch per pass, grid_blocks blocks, 0 = one per SM,
+ * positions separated by bounded grid barriers; a barrier that times out
+ * makes the call return FST_ERR_TIMEOUT).  fst_autotune_plain also picks
+ * the driver and grid, by timing them on its sample.  FST_ERR_UNSUPPORTED
+ * without cooperative launches or for a grid that cannot be co-resident. */
 FST_API int fst_set_plain_driver(fst_t* fst, int32_t driver, int32_t grid_blocks);
 
 /* The paper's relaxation, kept for comparison (Sec. 5.1): Viterbi of one

@@ -622,10 +622,19 @@ static int fst_viterbi_frontier(fst_t* f, const int32_t* ids, int32_t n, float* 
   const LayoutView L = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
   const FrontierState S = plain_state(f);
-  // one launch per input position (Sec. 5), after the first position's push
-  if (n >= 1) PLAIN_PROF(FST_PROF_VIT_FIRST, launch_vit_first(L, T, plain_step(f, n, 1, 0), S, s));
-  for (int32_t t = 1; t <= n; ++t)
-    PLAIN_PROF(FST_PROF_VIT_STEP, launch_vit_step(L, T, plain_step(f, n, t, t + 1), S, s));
+  if (f->plain_fb_driver == FST_DRIVER_PERSISTENT && n >= 1) {
+    // one cooperative launch for all positions
+    const int32_t pgrid = std::max(1, std::min(f->plain_fb_grid > 0 ? f->plain_fb_grid : f->num_sms,
+                                               persist_grid_limit(0)));
+    FST_CUDA(cudaMemsetAsync(w->gbar, 0, 8, s));
+    PLAIN_PROF(FST_PROF_VIT_STEP, launch_vit_persist(L, T, WaveSteps{w->step0, n}, S, pgrid,
+                                                     GridSync{w->gbar, 0u, 2000000000ull}, s));
+  } else {
+    // one launch per input position (Sec. 5), after the first position's push
+    if (n >= 1) PLAIN_PROF(FST_PROF_VIT_FIRST, launch_vit_first(L, T, plain_step(f, n, 1, 0), S, s));
+    for (int32_t t = 1; t <= n; ++t)
+      PLAIN_PROF(FST_PROF_VIT_STEP, launch_vit_step(L, T, plain_step(f, n, t, t + 1), S, s));
+  }
   PLAIN_PROF(FST_PROF_VIT_FINAL, launch_vit_final(S, 1, w->score, w->jfinal, w->status, s));
   PLAIN_PROF(FST_PROF_BACKTRACE, launch_backtrace(S, f->olabel, 1, w->jfinal, w->paths, w->olabels, s));
   w->last_fb = false;
@@ -635,6 +644,10 @@ static int fst_viterbi_frontier(fst_t* f, const int32_t* ids, int32_t n, float* 
   if (n > 0) {
     FST_CUDA(cudaMemcpy(arc_path, w->paths, (size_t)n * 4, cudaMemcpyDeviceToHost));
     if (olabels) FST_CUDA(cudaMemcpy(olabels, w->olabels, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  }
+  if (st == FST_ERR_TIMEOUT) {
+    set_error("a grid barrier of the persistent pass timed out");
+    return FST_ERR_TIMEOUT;
   }
   if (st != FST_OK) {
     set_error("no accepting path");
@@ -806,29 +819,73 @@ extern "C" int fst_autotune_plain(fst_t* f, const int32_t* ids, const int64_t* o
       set_error("fst_autotune_plain: offsets must be non-decreasing");
       return FST_ERR_INVALID_ARG;
     }
+  for (int64_t i = 0; i < offsets[B]; ++i)
+    if (ids[i] < 0 || ids[i] >= f->m) { set_error("fst_autotune_plain: symbol outside [0, %d)", f->m); return FST_ERR_INVALID_ARG; }
   DevGuard g(f->device);
   std::vector<int32_t> path, olab;
+  auto now = [] { return std::chrono::steady_clock::now(); };
+  auto us = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+    return std::chrono::duration<double, std::micro>(b - a).count();
+  };
+  // 1. the driver of the frontier kernels (both passes): per-position
+  //    launches, or persistent passes of 1, 8, 32 or one-per-SM blocks,
+  //    whichever decodes the sample (Viterbi + forward-backward) fastest
+  std::vector<std::pair<int32_t, int32_t>> cands = {{FST_DRIVER_LAUNCH, 0}};
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, f->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    coop = 0;
+  }
+  const int cap = std::min(persist_grid_limit(0), std::min(persist_grid_limit(1), persist_grid_limit(2)));
+  if (coop && cap > 0)
+    for (int32_t gsz : {1, 8, 32, f->num_sms})
+      if (gsz <= cap) cands.push_back({FST_DRIVER_PERSISTENT, gsz});
+  double best_t = 1e300;
+  std::pair<int32_t, int32_t> best = cands[0];
+  for (const auto& c : cands) {
+    f->plain_fb_driver = c.first;
+    f->plain_fb_grid = c.second;
+    double tot = 0.0;
+    for (int32_t b = -1; b < B; ++b) {  // b = -1: the first string again, untimed (first-use costs)
+      const int32_t bb = b < 0 ? 0 : b;
+      const int32_t* x = ids + offsets[bb];
+      const int32_t n = (int32_t)(offsets[bb + 1] - offsets[bb]);
+      path.resize(std::max(n, 1));
+      olab.resize(std::max(n, 1));
+      float score = 0.f;
+      double lz = 0.0;
+      const auto t0 = now();
+      int rc = fst_viterbi_frontier(f, x, n, &score, path.data(), olab.data());
+      if (rc == FST_OK || rc == FST_ERR_NO_PATH) rc = fst_forward_backward(f, x, n, &lz, nullptr);
+      if (rc != FST_OK && rc != FST_ERR_NO_PATH) return rc;
+      if (b >= 0) tot += us(t0, now());
+    }
+    if (tot < best_t) {
+      best_t = tot;
+      best = c;
+    }
+  }
+  f->plain_fb_driver = best.first;
+  f->plain_fb_grid = best.second;
+  // 2. Viterbi: frontier (with that driver) or slice-wide, by a cost model
   std::vector<std::array<double, 3>> Xf, Xs;
   std::vector<double> yf, ys;
-  for (int32_t b = -1; b < B; ++b) {  // b = -1: the first string again, untimed (first-use costs)
+  for (int32_t b = -1; b < B; ++b) {
     const int32_t bb = b < 0 ? 0 : b;
     const int32_t* x = ids + offsets[bb];
     const int32_t n = (int32_t)(offsets[bb + 1] - offsets[bb]);
     path.resize(std::max(n, 1));
     olab.resize(std::max(n, 1));
     double arcs = 0.0;
-    for (int32_t i = 0; i < n; ++i) {
-      if (x[i] < 0 || x[i] >= f->m) { set_error("fst_autotune_plain: symbol outside [0, %d)", f->m); return FST_ERR_INVALID_ARG; }
-      arcs += (double)(f->h_sym_arc[x[i] + 1] - f->h_sym_arc[x[i]]);
-    }
+    for (int32_t i = 0; i < n; ++i) arcs += (double)(f->h_sym_arc[x[i] + 1] - f->h_sym_arc[x[i]]);
     float score = 0.f;
     double t[2];
     for (int k = 0; k < 2; ++k) {
-      const auto t0 = std::chrono::steady_clock::now();
+      const auto t0 = now();
       const int rc = k == 0 ? fst_viterbi_frontier(f, x, n, &score, path.data(), olab.data())
                             : viterbi_slice_run(f, x, n, &score, path.data(), olab.data());
       if (rc != FST_OK && rc != FST_ERR_NO_PATH) return rc;
-      t[k] = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+      t[k] = us(t0, now());
     }
     if (b < 0) continue;
     Xf.push_back({1.0, (double)n, 0.0});
@@ -845,7 +902,6 @@ extern "C" int fst_autotune_plain(fst_t* f, const int32_t* ids, const int64_t* o
   std::sort(ss.begin(), ss.end());
   const bool spread = Xs.size() >= 4 && ns.front() < ns.back() && ss.front() < ss.back();
   if (!spread || !least_squares(Xf, yf, 2, cf) || !least_squares(Xs, ys, 3, cs)) {
-    // too few distinct strings for a fit: compare the mean times alone
     double mf = 0, ms = 0;
     for (size_t i = 0; i < yf.size(); ++i) { mf += yf[i]; ms += ys[i]; }
     cf[0] = mf / yf.size(); cf[1] = 0;
@@ -858,29 +914,6 @@ extern "C" int fst_autotune_plain(fst_t* f, const int32_t* ids, const int64_t* o
   }
   f->plain_tuned = true;
   f->plain_method = FST_PLAIN_AUTO;
-  // forward-backward: per-position launches or persistent passes, whichever
-  // decodes the sample faster
-  int coop = 0;
-  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, f->device) != cudaSuccess) {
-    (void)cudaGetLastError();
-    coop = 0;
-  }
-  if (coop && std::min(persist_grid_limit(1), persist_grid_limit(2)) > 0) {
-    double tfb[2] = {0, 0};
-    for (int d = 0; d < 2; ++d) {
-      f->plain_fb_driver = d == 0 ? FST_DRIVER_LAUNCH : FST_DRIVER_PERSISTENT;
-      for (int32_t b = -1; b < B; ++b) {
-        const int32_t bb = b < 0 ? 0 : b;
-        double lz = 0;
-        const auto t0 = std::chrono::steady_clock::now();
-        const int rc = fst_forward_backward(f, ids + offsets[bb], (int32_t)(offsets[bb + 1] - offsets[bb]), &lz,
-                                            nullptr);
-        if (rc != FST_OK && rc != FST_ERR_NO_PATH) return rc;
-        if (b >= 0) tfb[d] += std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
-      }
-    }
-    f->plain_fb_driver = tfb[1] < tfb[0] ? FST_DRIVER_PERSISTENT : FST_DRIVER_LAUNCH;
-  }
   return FST_OK;
 }
 

@@ -277,8 +277,11 @@ def test_plain_forward_backward_persistent_driver(grid):
     fa, strs = synth.make_config("c2", scale=0.02, strings=8)
     f, o = _fst(fa), oracle.Fst(fa)
     f.set_plain_driver(_lib.DRIVER_PERSISTENT, grid)
+    f.set_plain_method(_lib.PLAIN_FRONTIER)
     iid = synth.make_strings(fa, 2, 5, 15, seed=9, kind="iid")
     for x in [strs.get(b) for b in range(strs.count)] + [iid.get(0), np.zeros(0, np.int32)]:
+        s, p, ol, vst = f.viterbi(x)  # the frontier Viterbi under the same driver
+        assert_viterbi_equal(s, p, ol, vst, o.viterbi(x))
         lz, cnt, st = f.forward_backward(x)
         ofb = o.forward_backward(x)
         assert st == ofb["status"]
