@@ -88,6 +88,8 @@ def parse_args(argv=None):
     ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
     ap.add_argument("--parts-vit", type=int, default=2, help="stream-parallel parts of the Viterbi plan")
     ap.add_argument("--parts-fb", type=int, default=8, help="stream-parallel parts of the forward-backward plan")
+    ap.add_argument("--dense-acc", action="store_true",
+                    help="dense per-string accumulators (FST_PLAN_DENSE_ACC) instead of hash tables")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -471,8 +473,9 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     budget = int(args.budget_gb * (1 << 30))
     ids = torch.from_numpy(strs.ids).to(dev)
     off = torch.from_numpy(strs.offsets).to(dev)
-    plans_v = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB, parts=args.parts_vit)]
-    plans_f = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI, parts=args.parts_fb)]
+    acc = _lib.PLAN_DENSE_ACC if args.dense_acc else 0
+    plans_v = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB | acc, parts=args.parts_vit)]
+    plans_f = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI | acc, parts=args.parts_fb)]
     tuned = {}
     if args.driver in ("persistent", "persistent-all"):
         for p in plans_f:
@@ -557,6 +560,9 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     out["config"].update({
         "relaxations_per_pass": relax_pass, "waves": max(i["waves"] for i in infos_v + infos_f),
         "plan_gb": round(plan_bytes / 2**30, 2),
+        "accumulators": ("dense per-string arrays (FST_PLAN_DENSE_ACC)" if args.dense_acc else
+                         "hash tables of %d slots per part (Viterbi) and %d (forward-backward)"
+                         % (plans_v[0].table_slots(), plans_f[0].table_slots())),
         "parallelism": "replicas" if world > 1 else "1 GPU",
         "streams": f"a Viterbi plan of {args.parts_vit} and a forward-backward plan of {args.parts_fb} "
                    "stream-parallel parts; per-kernel times from one more step run serially",

@@ -136,14 +136,26 @@ FST_API int fst_viterbi(fst_t* fst, const int32_t* ids, int32_t n, float* best_s
  * slice-wide relaxation, Sec. 5.1, as fst_viterbi_slice) or FST_PLAIN_AUTO
  * (the one a calibrated cost model predicts to be faster for the string;
  * the frontier kernels until fst_autotune_plain has run).  Results are
- * identical either way. */
+ * identical either way.  FST_PLAIN_BLOCK runs fst_viterbi and
+ * fst_forward_backward as one thread block each, the position loop inside
+ * the kernel (the slice-wide relaxation of Sec. 5 with the per-state values
+ * in shared memory): for FSTs of at most FST_BLOCK_MAX_STATES states, where
+ * launches, not arcs, take the time (FST_ERR_UNSUPPORTED above that).
+ * Viterbi results are identical; forward-backward keeps unshifted float64
+ * values (log Z and posteriors agree to float64 rounding). */
 #define FST_PLAIN_FRONTIER 0
 #define FST_PLAIN_SLICE 1
 #define FST_PLAIN_AUTO 2
+#define FST_PLAIN_BLOCK 3
+#define FST_BLOCK_MAX_STATES 8192
 FST_API int fst_set_plain_method(fst_t* fst, int32_t method);
 
 /* Calibrate FST_PLAIN_AUTO on sample strings (host arrays: ids, offsets
- * [B+1] as in the batch calls, B >= 1): each string is decoded both ways
+ * [B+1] as in the batch calls, B >= 1).  An FST small enough for
+ * FST_PLAIN_BLOCK is first timed with it (Viterbi and forward-backward of
+ * the sample); when that beats the frontier kernels under every driver,
+ * FST_PLAIN_AUTO takes the one-block kernels for both calls and the rest
+ * is skipped (coef then reads 0, 0, 0, 0, 0).  Otherwise each string is decoded both ways
  * and timed on the host; the frontier time is fitted as d0 + d1 n and the
  * slice time as c0 + c1 n + c2 S (S = the arcs of the string's slices), by
  * least squares (with fewer than four strings of different sizes the mean
@@ -243,9 +255,15 @@ FST_API int fst_forward_backward_batch(fst_t* fst, const int32_t* d_ids, const i
 FST_API int fst_set_batch_budget(fst_t* fst, int64_t mem_budget_bytes);
 
 /* A plan holds everything a batch needs on the device: the token lists of
- * every position (strings sorted by length), the per-string accumulators,
- * the live pool of every position (states, values, backpointers or arcs)
- * and the per-token scalars.  Once created, the run calls below allocate
+ * every position (strings sorted by length), the accumulators, the live
+ * pool of every position (states, values, backpointers or arcs) and the
+ * per-token scalars.  The accumulators are hash tables keyed by (string,
+ * state), sized for 128 live states per token of the busiest position (at
+ * most the symbols' destination counts) at half load; a position that
+ * holds more live states than a table fits ends the run with FST_ERR_OOM,
+ * like a full pool, and leaves the plan usable.  FST_PLAN_DENSE_ACC gives
+ * each string a dense accumulator of 2 Q slots instead (no such limit;
+ * 16 to 48 bytes a state a string, which bounds the wave size).  Once created, the run calls below allocate
  * nothing, so a sequence of them can be captured into a CUDA graph and
  * replayed.  A Viterbi-only plan and a forward-backward-only plan of the
  * same batch share nothing and may run concurrently on two streams.
@@ -261,6 +279,7 @@ FST_API int fst_set_batch_budget(fst_t* fst, int64_t mem_budget_bytes);
 #define FST_PLAN_SINGLE_WAVE 1
 #define FST_PLAN_NO_VITERBI 2   /* do not allocate Viterbi storage (keys, state maps) */
 #define FST_PLAN_NO_FB 4        /* do not allocate forward-backward storage */
+#define FST_PLAN_DENSE_ACC 8    /* dense per-string accumulators (see above) */
 /* FST_PLAN_PARTS(k), k in 2..255, or-ed into flags: the batch is cut into k
  * contiguous string ranges of about equal token counts, each a plan of its
  * own (with its own waves and budget share) run on its own stream; a run
@@ -512,6 +531,17 @@ FST_API int fst_plan_fault_inject(fst_plan_t* plan, int32_t kind, int64_t value)
  * overflowing one left behind.  For memory-capped deployments and for
  * exercising that failure path. */
 FST_API int fst_plan_limit_pool(fst_plan_t* plan, int64_t entries);
+
+/* Compact accumulators: cap the hash tables of the plan's following runs at
+ * `slots` slots each (rounded down to a power of two, at least 2; 0 = the capacity
+ * allocated, which larger values cannot exceed).  Allocates nothing.  A run
+ * with more live states at one position than a table holds reports
+ * FST_ERR_OOM for every string of its wave and leaves the plan usable, as
+ * with fst_plan_limit_pool.  No effect on FST_PLAN_DENSE_ACC plans. */
+FST_API int fst_plan_limit_table(fst_plan_t* plan, int64_t slots);
+/* Slots of each compact accumulator table (the largest over the plan's
+ * parts; 0 for FST_PLAN_DENSE_ACC). */
+FST_API int fst_plan_table_slots(const fst_plan_t* plan, int64_t* slots);
 
 /* Plain-method Viterbi of one string that allocates no memory (the paper
  * has no counterpart: this is a deployment variant of fst_viterbi).  For

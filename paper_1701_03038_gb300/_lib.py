@@ -15,13 +15,14 @@ from . import build as _build
 OK, INVALID_ARG, NO_PATH, OOM, CUDA, TIMEOUT, UNSUPPORTED, STATE = range(8)
 WEIGHT_LOG, WEIGHT_COST = 0, 1
 FLAG_DEVICE_PTRS = 1
-PLAN_SINGLE_WAVE, PLAN_NO_VITERBI, PLAN_NO_FB = 1, 2, 4
+PLAN_SINGLE_WAVE, PLAN_NO_VITERBI, PLAN_NO_FB, PLAN_DENSE_ACC = 1, 2, 4, 8
 DRIVER_LAUNCH, DRIVER_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_BARRIER_STALL = 0, 1
 TUNE_REFRESH = 1
 EM_APPLY = 2
 SLICE_BY_DESTINATION, SLICE_BY_SOURCE = 0, 1
-PLAIN_FRONTIER, PLAIN_SLICE, PLAIN_AUTO = 0, 1, 2
+PLAIN_FRONTIER, PLAIN_SLICE, PLAIN_AUTO, PLAIN_BLOCK = 0, 1, 2, 3
+BLOCK_MAX_STATES = 8192
 
 _lock = threading.Lock()
 _lib = None
@@ -58,6 +59,8 @@ SIGNATURES = {
     "fst_plan_live_work": [vp, vp, vp, vp],
     "fst_plan_forward_backward_ex": [vp, vp, vp, vp, vp, vp, vp, vp],
     "fst_plan_limit_pool": [vp, i64],
+    "fst_plan_limit_table": [vp, i64],
+    "fst_plan_table_slots": [vp, vp],
     "fst_set_batch_budget": [vp, i64],
     "fst_plan_set_driver": [vp, i32, i32, i64],
     "fst_plan_get_driver": [vp, vp, vp],

@@ -20,7 +20,7 @@ LIB_NAME = "libfstgpu.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 
 SOURCES = ["sort_scan.cu", "store.cu", "kernels.cu", "capi.cu", "plan.cu", "noalloc.cu", "fd64.cu", "slice.cu",
-           "train.cu", "lattice.cu", "prefix.cu"]
+           "train.cu", "lattice.cu", "prefix.cu", "block.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
               "-I", INCLUDE, "-I", CSRC]

@@ -1,0 +1,365 @@
+// block.cu -- one string on a small FST in one thread block.
+//
+// The paper relaxes the slice delta[w_t] of every input position with one
+// thread per arc and one kernel launch per position (Sec. 5).  On a small
+// FST (a thousand states, a few hundred arcs per slice) the launches, not
+// the arcs, take the time: each position costs a launch and a round trip
+// through global memory for a microsecond of work.  Here the position loop
+// runs inside one block of 1024 threads: the values of every state at t-1
+// and the accumulators of t sit in shared memory, the slice's arcs are
+// read from L2, collisions on a destination go to shared-memory atomics,
+// and __syncthreads() separates the positions.
+//
+//   Viterbi  -- the packed (order-preserving score bits << 32 | ~arc id)
+//               atomicMax of Sec. 5.1 (lowest arc id on ties, as the
+//               frontier kernels), a backpointer {arc, source} per state
+//               and position in global memory, the backtrace by one thread;
+//   forward  -- two sweeps of the slice per position: the exact float64
+//               maximum of the arc values into each destination, then
+//               exp(value - maximum) added in 2^-40 fixed point, both
+//               order-independent; alpha_t in float64 to global memory;
+//   backward -- the same two sweeps into each arc's source, beta_t in
+//               shared memory, and the posterior of each arc (Alg. 2)
+//               added by the thread that owns the arc's slice position:
+//               the same thread meets the same arc whenever its symbol
+//               recurs, so the compensated float32 counts need no atomics
+//               and are bitwise repeatable.
+//
+// Values are kept unshifted in float64 (no per-position rescaling: float64
+// holds the sums of log-probabilities of any string length used here).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "fst_internal.cuh"
+
+using namespace fstgpu;
+
+namespace {
+
+constexpr int BT = 1024;  // threads of the block
+
+__device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
+
+// The padded slice of symbol a: positions [sym_win[a], sym_win[a+1]) x WIN.
+struct Slice {
+  int64_t i0, i1;
+};
+__device__ __forceinline__ Slice slice_of(const int64_t* __restrict__ sym_win, int32_t a) {
+  return Slice{__ldg(sym_win + a) * WIN, __ldg(sym_win + a + 1) * WIN};
+}
+
+// Block-wide maximum of a 64-bit key (all threads get it).
+__device__ __forceinline__ unsigned long long block_max_key(unsigned long long k, unsigned long long* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(FULL, k, d);
+    k = o > k ? o : k;
+  }
+  __syncthreads();
+  if (lane == 0) red[warp] = k;
+  __syncthreads();
+  k = red[0];
+  for (int w = 1; w < BT / 32; ++w) k = red[w] > k ? red[w] : k;
+  return k;
+}
+
+// Block-wide sum of a float64, in a fixed order (all threads get it).
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  v = 0.0;
+  for (int w = 0; w < BT / 32; ++w) v += red[w];
+  return v;
+}
+
+// ======================================================================
+// Viterbi (Alg. 1, Sec. 5.1).  Shared: key[Q] (packed best arc of each
+// state at t), v[Q] (float32 score of each state at t-1).  bp[(t-1) Q + q]
+// = {best arc, its source} of state q at position t.
+// ======================================================================
+__global__ void __launch_bounds__(BT, 1) k_block_viterbi(const int4* __restrict__ arcs, const float* __restrict__ theta,
+                                                      const int64_t* __restrict__ sym_win,
+                                                      const int32_t* __restrict__ ids, int32_t n, int32_t Q,
+                                                      const float* __restrict__ theta_s,
+                                                      const float* __restrict__ theta_f,
+                                                      const int32_t* __restrict__ src_by_id,
+                                                      const int32_t* __restrict__ olabel, int2* __restrict__ bp,
+                                                      float* __restrict__ score, int32_t* __restrict__ path,
+                                                      int32_t* __restrict__ olab, int32_t* __restrict__ status) {
+  extern __shared__ unsigned long long smem[];
+  __shared__ unsigned long long red[BT / 32];
+  unsigned long long* key = smem;
+  float* v = (float*)(smem + Q);
+  for (int32_t q = threadIdx.x; q < Q; q += BT) {
+    key[q] = 0ull;
+    v[q] = __ldg(theta_s + q);
+  }
+  __syncthreads();
+  for (int32_t t = 1; t <= n; ++t) {
+    const Slice sl = slice_of(sym_win, __ldg(ids + t - 1));
+    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
+      const int4 r = __ldg(arcs + i);
+      if (r.z < 0) continue;  // padding
+      const float x = v[r.x];
+      if (x == neg_inf()) continue;
+      const float c = __fadd_rn(x, __ldg(theta + i));
+      if (c == neg_inf()) continue;
+      atomicMax(key + r.y, ((unsigned long long)fkey(c) << 32) | (unsigned long long)(~(uint32_t)r.z));
+    }
+    __syncthreads();
+    int2* row = bp + (int64_t)(t - 1) * Q;
+    for (int32_t q = threadIdx.x; q < Q; q += BT) {
+      const unsigned long long k = key[q];
+      const int32_t id = k ? (int32_t)(~(uint32_t)k) : -1;
+      row[q] = make_int2(id, id >= 0 ? __ldg(src_by_id + id) : -1);
+      v[q] = k ? fkey_inv((uint32_t)(k >> 32)) : neg_inf();
+      key[q] = 0ull;
+    }
+    __syncthreads();
+  }
+  // the best final state (lowest state id on ties)
+  unsigned long long best = 0ull;
+  for (int32_t q = threadIdx.x; q < Q; q += BT) {
+    const float c = __fadd_rn(v[q], __ldg(theta_f + q));
+    if (c == neg_inf()) continue;
+    const unsigned long long k = ((unsigned long long)fkey(c) << 32) | (unsigned long long)(~(uint32_t)q);
+    best = k > best ? k : best;
+  }
+  best = block_max_key(best, red);
+  if (threadIdx.x != 0) return;
+  *score = best ? fkey_inv((uint32_t)(best >> 32)) : neg_inf();
+  *status = best ? FST_OK : FST_ERR_NO_PATH;
+  int32_t q = best ? (int32_t)(~(uint32_t)best) : -1;
+  for (int32_t t = n; t >= 1; --t) {
+    const int2 e = q >= 0 ? bp[(int64_t)(t - 1) * Q + q] : make_int2(-1, -1);
+    path[t - 1] = e.x;
+    if (olab) olab[t - 1] = e.x >= 0 ? __ldg(olabel + e.x) : -1;
+    q = e.y;
+  }
+}
+
+// ======================================================================
+// Forward-backward (Alg. 2, Sec. 5.2).  Shared: mx[Q] (order key of the
+// float64 maximum into each state), sm[Q] (fixed-point sum), a[Q] (float64
+// alpha_{t-1}, then beta_t).  alpha[t Q + q] = alpha_t[q], t = 0..n.
+// ======================================================================
+__device__ __forceinline__ double state_value(unsigned long long m, unsigned long long s) {
+  return m ? fix_log_sum64(dkey_inv(m), s) : -INFINITY;
+}
+
+__global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arcs, const float* __restrict__ theta,
+                                                 const int64_t* __restrict__ sym_win, const int32_t* __restrict__ ids,
+                                                 int32_t n, int32_t Q, const float* __restrict__ theta_s,
+                                                 const float* __restrict__ theta_f, double* __restrict__ alpha,
+                                                 float* __restrict__ cnt, float* __restrict__ comp,
+                                                 double* __restrict__ logz, int32_t* __restrict__ status) {
+  extern __shared__ unsigned long long smem[];
+  __shared__ double redd[BT / 32];
+  __shared__ unsigned long long redk[BT / 32];
+  unsigned long long* mx = smem;
+  unsigned long long* sm = smem + Q;
+  double* a = (double*)(smem + 2 * Q);
+  for (int32_t q = threadIdx.x; q < Q; q += BT) {
+    mx[q] = sm[q] = 0ull;
+    a[q] = (double)__ldg(theta_s + q);
+    alpha[q] = a[q];
+  }
+  __syncthreads();
+  // forward
+  for (int32_t t = 1; t <= n; ++t) {
+    const Slice sl = slice_of(sym_win, __ldg(ids + t - 1));
+    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
+      const int4 r = __ldg(arcs + i);
+      if (r.z < 0) continue;
+      const double x = a[r.x] + (double)__ldg(theta + i);
+      if (x != -INFINITY) atomicMax(mx + r.y, dkey(x));
+    }
+    __syncthreads();
+    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
+      const int4 r = __ldg(arcs + i);
+      if (r.z < 0) continue;
+      const double x = a[r.x] + (double)__ldg(theta + i);
+      if (x != -INFINITY) atomicAdd(sm + r.y, fix_exp64(x, dkey_inv(mx[r.y])));
+    }
+    __syncthreads();
+    double* row = alpha + (int64_t)t * Q;
+    for (int32_t q = threadIdx.x; q < Q; q += BT) {
+      a[q] = state_value(mx[q], sm[q]);
+      row[q] = a[q];
+      mx[q] = sm[q] = 0ull;
+    }
+    __syncthreads();
+  }
+  // log Z = log sum_q exp(alpha_n[q] + theta_f[q]): exact maximum, then a
+  // float64 sum in a fixed order
+  unsigned long long mk = 0ull;
+  for (int32_t q = threadIdx.x; q < Q; q += BT) {
+    const double x = a[q] + (double)__ldg(theta_f + q);
+    if (x != -INFINITY) {
+      const unsigned long long k = dkey(x);
+      mk = k > mk ? k : mk;
+    }
+  }
+  mk = block_max_key(mk, redk);
+  const double m = mk ? dkey_inv(mk) : -INFINITY;
+  double part = 0.0;
+  if (mk)
+    for (int32_t q = threadIdx.x; q < Q; q += BT) {
+      const double x = a[q] + (double)__ldg(theta_f + q);
+      if (x != -INFINITY) part += exp(x - m);
+    }
+  const double lz = mk ? m + log(block_sum(part, redd)) : -INFINITY;
+  if (threadIdx.x == 0) {
+    *logz = lz;
+    *status = mk ? FST_OK : FST_ERR_NO_PATH;
+  }
+  if (!cnt || !mk) return;  // block-uniform
+  // backward: beta_n = theta_f
+  __syncthreads();
+  for (int32_t q = threadIdx.x; q < Q; q += BT) a[q] = (double)__ldg(theta_f + q);
+  __syncthreads();
+  for (int32_t t = n; t >= 1; --t) {
+    const Slice sl = slice_of(sym_win, __ldg(ids + t - 1));
+    const double* al = alpha + (int64_t)(t - 1) * Q;
+    // the maxima into the sources, and each arc's posterior
+    // exp(alpha_{t-1}[src] + theta + beta_t[dst] - log Z)
+    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
+      const int4 r = __ldg(arcs + i);
+      if (r.z < 0) continue;
+      const double u = (double)__ldg(theta + i) + a[r.y];
+      if (u == -INFINITY) continue;
+      atomicMax(mx + r.x, dkey(u));
+      const double x = al[r.x];
+      if (x == -INFINITY) continue;
+      const float g = (float)exp((x + u) - lz);
+      // compensated float32 sum: this thread alone writes arc r.z
+      const float s0 = cnt[r.z], cp = comp[r.z];
+      const float y = __fsub_rn(g, cp);
+      const float s1 = __fadd_rn(s0, y);
+      comp[r.z] = __fsub_rn(__fsub_rn(s1, s0), y);
+      cnt[r.z] = s1;
+    }
+    __syncthreads();
+    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
+      const int4 r = __ldg(arcs + i);
+      if (r.z < 0) continue;
+      const double u = (double)__ldg(theta + i) + a[r.y];
+      if (u != -INFINITY) atomicAdd(sm + r.x, fix_exp64(u, dkey_inv(mx[r.x])));
+    }
+    __syncthreads();
+    for (int32_t q = threadIdx.x; q < Q; q += BT) {
+      a[q] = state_value(mx[q], sm[q]);
+      mx[q] = sm[q] = 0ull;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+namespace fstgpu {
+
+bool block_fits(const fst_s* f) { return f->Q >= 1 && f->Q <= BLOCK_QMAX; }
+
+// Grow a device buffer of T to at least `need` elements (doubling).
+template <class T>
+static int grow(T** p, int64_t* cap, int64_t need) {
+  if (need <= *cap) return FST_OK;
+  const int64_t c = std::max<int64_t>(need, 2 * *cap);
+  dfree(*p);
+  *cap = 0;
+  const int rc = dalloc(p, c);
+  if (rc) return rc;
+  *cap = c;
+  return FST_OK;
+}
+
+// Working memory of the block kernels: the string, its outputs, and n Q
+// backpointers or (n + 1) Q forward values (in 8-byte words).
+static int block_reserve(fst_s* f, int32_t n, int64_t words) {
+  int rc;
+  if ((rc = grow(&f->block_ids, &f->block_ids_cap, 3 * (int64_t)std::max(n, 1) + 4)) ||
+      (rc = grow(&f->block_ws, &f->block_ws_cap, words)))
+    return rc;
+  return FST_OK;
+}
+
+template <class K>
+static int block_launch_setup(K kernel, size_t smem) {
+  FST_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return FST_OK;
+}
+
+int viterbi_block_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
+                      int32_t* olabels, int32_t* status) {
+  if (!block_fits(f)) {
+    set_error("the one-block kernels hold at most %d states (this FST has %d)", BLOCK_QMAX, f->Q);
+    return FST_ERR_UNSUPPORTED;
+  }
+  int rc;
+  cudaStream_t s = 0;
+  SliceView sv;
+  if ((rc = slice_view(f, s, &sv))) return rc;
+  const Layout& L = f->slice_order == FST_SLICE_BY_SOURCE ? f->bwd : f->fwd;
+  // block_ids: the string, the path, the output labels, then score and status
+  if ((rc = block_reserve(f, n, (int64_t)std::max(n, 1) * f->Q))) return rc;
+  const int64_t n1 = std::max(n, 1);
+  int32_t* d_ids = f->block_ids;
+  int32_t* d_path = d_ids + n1;
+  int32_t* d_olab = d_ids + 2 * n1;
+  float* d_score = (float*)(d_ids + 3 * n1);
+  int32_t* d_status = d_ids + 3 * n1 + 1;
+  if (n > 0) FST_CUDA(cudaMemcpyAsync(d_ids, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  const size_t smem = (size_t)f->Q * 12;
+  if ((rc = block_launch_setup(k_block_viterbi, smem))) return rc;
+  k_block_viterbi<<<1, BT, smem, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, f->theta_s, f->theta_f,
+                                      f->src_by_id, f->olabel, (int2*)f->block_ws, d_score, d_path,
+                                      olabels ? d_olab : nullptr, d_status);
+  FST_CUDA(cudaGetLastError());
+  FST_CUDA(cudaMemcpy(best_score, d_score, 4, cudaMemcpyDeviceToHost));
+  FST_CUDA(cudaMemcpy(status, d_status, 4, cudaMemcpyDeviceToHost));
+  if (n > 0) {
+    FST_CUDA(cudaMemcpy(arc_path, d_path, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    if (olabels) FST_CUDA(cudaMemcpy(olabels, d_olab, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  }
+  return FST_OK;
+}
+
+int fb_block_run(fst_s* f, const int32_t* ids, int32_t n, float* d_cnt, float* d_comp, double* log_z,
+                 int32_t* status) {
+  if (!block_fits(f)) {
+    set_error("the one-block kernels hold at most %d states (this FST has %d)", BLOCK_QMAX, f->Q);
+    return FST_ERR_UNSUPPORTED;
+  }
+  int rc;
+  cudaStream_t s = 0;
+  SliceView sv;
+  if ((rc = slice_view(f, s, &sv))) return rc;
+  const Layout& L = f->slice_order == FST_SLICE_BY_SOURCE ? f->bwd : f->fwd;
+  // block_ws: log Z, then the forward values; block_ids: the string, then
+  // the status
+  if ((rc = block_reserve(f, n, ((int64_t)n + 1) * f->Q + 1))) return rc;
+  const int64_t n1 = std::max(n, 1);
+  int32_t* d_ids = f->block_ids;
+  int32_t* d_status = d_ids + 3 * n1 + 1;
+  double* d_logz = (double*)f->block_ws;
+  if (n > 0) FST_CUDA(cudaMemcpyAsync(d_ids, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  const size_t smem = (size_t)f->Q * 24;
+  if ((rc = block_launch_setup(k_block_fb, smem))) return rc;
+  k_block_fb<<<1, BT, smem, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, f->theta_s, f->theta_f,
+                                 (double*)f->block_ws + 1, d_cnt, d_comp, d_logz, d_status);
+  FST_CUDA(cudaGetLastError());
+  FST_CUDA(cudaMemcpy(log_z, d_logz, 8, cudaMemcpyDeviceToHost));
+  FST_CUDA(cudaMemcpy(status, d_status, 4, cudaMemcpyDeviceToHost));
+  return FST_OK;
+}
+
+}  // namespace fstgpu

@@ -455,6 +455,8 @@ extern "C" int fst_destroy(fst_t* f) {
   dfree(f->slice_keys);
   dfree(f->slice_fb);
   dfree(f->slice_out);
+  dfree(f->block_ids);
+  dfree(f->block_ws);
   delete f->plain;
   f->plain = nullptr;
   free_layout(f->fwd);
@@ -585,6 +587,7 @@ extern "C" int fst_set_state_weights(fst_t* f, const float* start_weight, const 
 static int fst_viterbi_frontier(fst_t* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
                                 int32_t* olabels);
 static bool plain_uses_slice(const fst_s* f, const int32_t* ids, int32_t n);
+static bool plain_uses_block(const fst_s* f);
 
 extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
                            int32_t* olabels) {
@@ -593,8 +596,25 @@ extern "C" int fst_viterbi(fst_t* f, const int32_t* ids, int32_t n, float* best_
     return FST_ERR_INVALID_ARG;
   }
   DevGuard g(f->device);
+  if (plain_uses_block(f)) {
+    for (int32_t i = 0; i < n; ++i)
+      if (ids[i] < 0 || ids[i] >= f->m) {
+        set_error("symbol %d at position %d is outside [0, %d)", ids[i], i, f->m);
+        return FST_ERR_INVALID_ARG;
+      }
+    int32_t st = FST_OK;
+    const int rc = viterbi_block_run(f, ids, n, best_score, arc_path, olabels, &st);
+    if (rc) return rc;
+    if (st != FST_OK) set_error("no accepting path");
+    return st;
+  }
   if (plain_uses_slice(f, ids, n)) return viterbi_slice_run(f, ids, n, best_score, arc_path, olabels);
   return fst_viterbi_frontier(f, ids, n, best_score, arc_path, olabels);
+}
+// Whether the single-string calls take the one-block kernels: by the
+// handle's setting, or (FST_PLAIN_AUTO) once calibration chose them.
+static bool plain_uses_block(const fst_s* f) {
+  return f->plain_method == FST_PLAIN_BLOCK || (f->plain_method == FST_PLAIN_AUTO && f->plain_tuned && f->plain_block);
 }
 // Whether fst_viterbi takes the slice-wide kernel for this string: by the
 // handle's setting, or (FST_PLAIN_AUTO, once calibrated) by the predicted
@@ -670,6 +690,24 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   if (arc_posteriors && !w->cnt) {
     if ((rc = dalloc(&w->cnt, f->A)) || (rc = dalloc(&w->comp, f->A)) || (rc = dalloc(&w->counts_out, f->A)))
       return rc;
+  }
+  if (plain_uses_block(f)) {
+    if (arc_posteriors) {
+      FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
+      FST_CUDA(cudaMemsetAsync(w->comp, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
+    }
+    int32_t st = FST_OK;
+    if ((rc = fb_block_run(f, ids, n, arc_posteriors ? w->cnt : nullptr, arc_posteriors ? w->comp : nullptr, log_z,
+                           &st)))
+      return rc;
+    if (arc_posteriors) {
+      const CountView C{0, w->cnt, w->comp, nullptr};
+      if ((rc = launch_counts_out(f->A, C, w->counts_out, s))) return rc;
+      if (f->A > 0)
+        FST_CUDA(cudaMemcpy(arc_posteriors, w->counts_out, (size_t)f->A * 4, cudaMemcpyDeviceToHost));
+    }
+    if (st != FST_OK) set_error("no accepting path");
+    return st;
   }
   const LayoutView L = view_of(f->bwd);
   const TokenView T = plain_tokview(w);
@@ -775,9 +813,13 @@ extern "C" int fst_live_work(fst_t* f, int64_t* entries, int64_t* arcs) {
 
 // ------------------------------------------------- plain-method calibration
 extern "C" int fst_set_plain_method(fst_t* f, int32_t method) {
-  if (!f || method < FST_PLAIN_FRONTIER || method > FST_PLAIN_AUTO) {
+  if (!f || method < FST_PLAIN_FRONTIER || method > FST_PLAIN_BLOCK) {
     set_error("fst_set_plain_method: bad arguments");
     return FST_ERR_INVALID_ARG;
+  }
+  if (method == FST_PLAIN_BLOCK && !block_fits(f)) {
+    set_error("the one-block kernels hold at most %d states (this FST has %d)", BLOCK_QMAX, f->Q);
+    return FST_ERR_UNSUPPORTED;
   }
   f->plain_method = method;
   return FST_OK;
@@ -840,11 +882,20 @@ extern "C" int fst_autotune_plain(fst_t* f, const int32_t* ids, const int64_t* o
   if (coop && cap > 0)
     for (int32_t gsz : {1, 8, 32, f->num_sms})
       if (gsz <= cap) cands.push_back({FST_DRIVER_PERSISTENT, gsz});
+  // the one-block kernels, where the FST fits, compete as one more candidate
+  const bool try_block = block_fits(f);
+  if (try_block) cands.push_back({-1, 0});
+  f->plain_method = FST_PLAIN_FRONTIER;
+  f->plain_block = false;
   double best_t = 1e300;
   std::pair<int32_t, int32_t> best = cands[0];
   for (const auto& c : cands) {
-    f->plain_fb_driver = c.first;
-    f->plain_fb_grid = c.second;
+    const bool blk = c.first < 0;
+    if (!blk) {
+      f->plain_fb_driver = c.first;
+      f->plain_fb_grid = c.second;
+    }
+    f->plain_method = blk ? FST_PLAIN_BLOCK : FST_PLAIN_FRONTIER;
     double tot = 0.0;
     for (int32_t b = -1; b < B; ++b) {  // b = -1: the first string again, untimed (first-use costs)
       const int32_t bb = b < 0 ? 0 : b;
@@ -855,15 +906,30 @@ extern "C" int fst_autotune_plain(fst_t* f, const int32_t* ids, const int64_t* o
       float score = 0.f;
       double lz = 0.0;
       const auto t0 = now();
-      int rc = fst_viterbi_frontier(f, x, n, &score, path.data(), olab.data());
+      int rc = fst_viterbi(f, x, n, &score, path.data(), olab.data());
       if (rc == FST_OK || rc == FST_ERR_NO_PATH) rc = fst_forward_backward(f, x, n, &lz, nullptr);
-      if (rc != FST_OK && rc != FST_ERR_NO_PATH) return rc;
+      if (rc != FST_OK && rc != FST_ERR_NO_PATH) {
+        f->plain_method = FST_PLAIN_FRONTIER;
+        return rc;
+      }
       if (b >= 0) tot += us(t0, now());
     }
     if (tot < best_t) {
       best_t = tot;
       best = c;
     }
+  }
+  f->plain_method = FST_PLAIN_FRONTIER;
+  if (best.first < 0) {
+    // the one-block kernels beat every frontier driver
+    f->plain_block = true;
+    for (int i = 0; i < 5; ++i) {
+      f->plain_coef[i] = 0.0;
+      if (coef) coef[i] = 0.0;
+    }
+    f->plain_tuned = true;
+    f->plain_method = FST_PLAIN_AUTO;
+    return FST_OK;
   }
   f->plain_fb_driver = best.first;
   f->plain_fb_grid = best.second;

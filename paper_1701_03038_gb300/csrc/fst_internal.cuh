@@ -148,12 +148,19 @@ struct fst_s {
   int64_t slice_fb_cap = 0;
   int32_t* slice_out = nullptr;    // slice Viterbi outputs: score, path and output labels
   int64_t slice_out_cap = 0;
+  // one-block kernels (block.cu): the string and its outputs; backpointers
+  // or forward values
+  int32_t* block_ids = nullptr;
+  int64_t block_ids_cap = 0;
+  unsigned long long* block_ws = nullptr;
+  int64_t block_ws_cap = 0;
   // single-string Viterbi: frontier kernels, the slice-wide kernel, or the
   // cheaper of the two by a cost model fitted by fst_autotune_plain
   int32_t plain_method = 0;
   int32_t plain_fb_driver = 0;   // single-string forward-backward: FST_DRIVER_LAUNCH or _PERSISTENT
   int32_t plain_fb_grid = 0;     // persistent grid (0 = one block per SM)
   bool plain_tuned = false;
+  bool plain_block = false;  // FST_PLAIN_AUTO, calibrated: the one-block kernels for both calls
   double plain_coef[5] = {0, 0, 0, 0, 0};  // frontier d0 + d1 n; slice c0 + c1 n + c2 (slice arcs)
 };
 
@@ -272,6 +279,17 @@ int slice_view(fst_s* f, cudaStream_t s, SliceView* out);
 // host outputs, olabels may be NULL.
 int viterbi_slice_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
                       int32_t* olabels);
+
+// One string in one thread block (block.cu), for FSTs of at most
+// BLOCK_QMAX states: Viterbi (host outputs, olabels may be NULL; *status
+// FST_OK or FST_ERR_NO_PATH) and forward-backward (the posteriors added to
+// the compensated float32 pair d_cnt / d_comp when not NULL; host log Z).
+constexpr int32_t BLOCK_QMAX = FST_BLOCK_MAX_STATES;
+bool block_fits(const fst_s* f);
+int viterbi_block_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
+                      int32_t* olabels, int32_t* status);
+int fb_block_run(fst_s* f, const int32_t* ids, int32_t n, float* d_cnt, float* d_comp, double* log_z,
+                 int32_t* status);
 
 // Input label, destination and log-weight of every arc by caller id (any
 // output may be NULL; train.cu).

@@ -55,8 +55,6 @@ __device__ __forceinline__ int32_t run_error(uint32_t err) {
 
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
-__device__ __forceinline__ int32_t warp_id_global() { return (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
-
 __device__ __forceinline__ float decode_max(uint32_t k) { return k ? fkey_inv(k) : neg_inf(); }
 
 // Owner of flat entry j among the n slots whose first entries base[0..n)
@@ -146,6 +144,63 @@ __device__ __forceinline__ unsigned long long* vit_key(const FrontierState& S, i
 __device__ __forceinline__ unsigned long long* fwd_sum(const FrontierState& S, int64_t slot) { return S.acc + 2 * slot; }
 __device__ __forceinline__ unsigned long long* fwd_max(const FrontierState& S, int64_t slot) {
   return S.acc + 2 * slot + 1;
+}
+
+// Compact accumulators: open-addressing hash tables with linear probing.
+// A slot's first word is its key, (string + 1) << 32 | state (0 = empty):
+// a table holds one position of each string, and keying by the string
+// rather than the token puts a state that stays live two positions later
+// in the same slot, whose line is then still in L2;
+// the next word the Viterbi key or the forward maximum, and in forward
+// tables the third the fixed-point sum.
+__device__ __forceinline__ bool compact(const FrontierState& S) { return S.hmask != 0ull; }
+__device__ __forceinline__ int hwords(const FrontierState& S) { return 2 * S.acc_stride; }
+__device__ __forceinline__ unsigned long long* htab(const FrontierState& S, int32_t t) {
+  return (t & 1) ? S.htab1 : S.htab0;
+}
+__device__ __forceinline__ unsigned long long* btab(const FrontierState& S, int32_t t) {
+  const int32_t r = t % 3;
+  return r == 0 ? S.btab0 : (r == 1 ? S.btab1 : S.btab2);
+}
+__device__ __forceinline__ unsigned long long tab_key(int32_t b, int32_t q) {
+  return ((unsigned long long)(uint32_t)(b + 1) << 32) | (unsigned long long)(uint32_t)q;
+}
+// Home slot: multiplicative (Fibonacci) hashing; bits 32 and up of the
+// product depend on both the string and the state.
+__device__ __forceinline__ uint64_t tab_home(unsigned long long k, uint64_t mask) {
+  return ((k * 0x9E3779B97F4A7C15ull) >> 32) & mask;
+}
+// The slot of key k in a table of w words a slot: where it already is, or
+// the first empty slot of its probe sequence, taken with a compare-and-swap
+// (*fresh = true: this call inserted it).  -1: the table is full.
+__device__ __forceinline__ int64_t tab_claim(unsigned long long* tab, int w, uint64_t mask, unsigned long long k,
+                                             bool* fresh) {
+  uint64_t h = tab_home(k, mask);
+  for (uint64_t n = 0; n <= mask; ++n) {
+    const unsigned long long old = atomicCAS(tab + h * (uint64_t)w, 0ull, k);
+    if (old == 0ull || old == k) {
+      *fresh = old == 0ull;
+      return (int64_t)h;
+    }
+    h = (h + 1) & mask;
+  }
+  *fresh = false;
+  return -1;
+}
+// The slot holding key k, its first two words in *e; -1 when absent.
+__device__ __forceinline__ int64_t tab_find(const unsigned long long* tab, int w, uint64_t mask,
+                                            unsigned long long k, ulonglong2* e) {
+  uint64_t h = tab_home(k, mask);
+  for (uint64_t n = 0; n <= mask; ++n) {
+    const ulonglong2 x = __ldcg((const ulonglong2*)(tab + h * (uint64_t)w));
+    if (x.x == k) {
+      *e = x;
+      return (int64_t)h;
+    }
+    if (x.x == 0ull) break;
+    h = (h + 1) & mask;
+  }
+  return -1;
 }
 
 // The last block of a kernel to finish hands out consecutive ranges, in step
@@ -287,25 +342,6 @@ __device__ __forceinline__ int block_owner(const int32_t* excl, int32_t a) {
   return o;
 }
 
-// fn(e, ctx of e's owner, owner, valid) for every arc of every thread's
-// segment.  Every thread runs the same rounds and calls fn VU times per
-// round (valid = false past the end), so fn may use warp collectives.
-template <class Ctx, class F>
-__device__ __forceinline__ void block_walk(BlockScratch<Ctx>& sh, int32_t total, F fn) {
-  for (int32_t a0 = 0; a0 < total; a0 += KT * VU) {
-    int oo[VU];
-    int32_t ee[VU];
-#pragma unroll
-    for (int u = 0; u < VU; ++u) {
-      const int32_t a = a0 + u * KT + (int32_t)threadIdx.x;
-      oo[u] = a < total ? block_owner(sh.excl, a) : 0;
-      ee[u] = a < total ? sh.e0[oo[u]] + (a - sh.excl[oo[u]]) : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < VU; ++u) fn(ee[u], sh.ctx[oo[u]], oo[u], a0 + u * KT + (int32_t)threadIdx.x < total);
-  }
-}
-
 template <class Ctx>
 __device__ __forceinline__ int32_t block_stage(BlockScratch<Ctx>& sh, int32_t e0, int32_t len, const Ctx& mine) {
   int32_t total;
@@ -316,16 +352,6 @@ __device__ __forceinline__ int32_t block_stage(BlockScratch<Ctx>& sh, int32_t e0
   sh.acc[threadIdx.x] = 0ull;
   __syncthreads();
   return total;
-}
-
-// visit(e, ctx, valid) for every arc of every thread's segment, called by
-// all threads in the same rounds (valid = false past the end).
-template <class Ctx, class F>
-__device__ __forceinline__ void block_visit(BlockScratch<Ctx>& sh, int32_t e0, int32_t len, const Ctx& mine,
-                                            F visit) {
-  const int32_t total = block_stage(sh, e0, len, mine);
-  block_walk(sh, total, [&](int32_t e, const Ctx& c, int, bool valid) { visit(e, c, valid); });
-  __syncthreads();
 }
 
 // Order key of a float64 value rounded to float32 (0 = -inf, nothing).
@@ -345,20 +371,6 @@ struct RedSum {  // exact integer sum
   static __device__ __forceinline__ T value(unsigned long long k) { return k; }
   static __device__ __forceinline__ void atomic(unsigned long long* a, unsigned long long k) { if (k) atomicAdd(a, k); }
 };
-
-template <class Op, class Ctx, class F>
-__device__ __forceinline__ typename Op::T block_reduce(BlockScratch<Ctx>& sh, int32_t e0, int32_t len,
-                                                       const Ctx& mine, F value) {
-  const int32_t total = block_stage(sh, e0, len, mine);
-  block_walk(sh, total, [&](int32_t e, const Ctx& c, int o, bool valid) {
-    if (valid) Op::atomic(&sh.acc[o], Op::key(value(e, c)));
-  });
-  __syncthreads();
-  const typename Op::T r = Op::value(sh.acc[threadIdx.x]);
-  __syncthreads();
-  return r;
-}
-
 
 // Atomic max of key into a[p] for the lanes that hold one (p >= 0), with one
 // atomic per run of equal p: the lanes of a warp hold consecutive flat
@@ -400,33 +412,92 @@ struct PushCtx {
   double r;   // value of the source (Viterbi: a float32 score, held exactly)
 };
 
-// Arc e out of a live source, into position t: the atomic max on the
-// destination's accumulator, and the staging of a destination met first.
-// All 32 lanes call it (valid = false: no arc).
+// The arcs of every thread's segment out of a live source, pushed into
+// position t: the atomic max on each destination's accumulator, and the
+// staging of a destination met first.  VU arcs per thread a round, their
+// loads and atomics issued together.  Compact accumulators take one
+// compare-and-swap on the key (the home slot, almost always) and a max that
+// returns nothing; the insert that took the slot stages it.  All threads of
+// the block call it.
 template <bool VIT>
-__device__ __forceinline__ void push_arc(const LayoutView& L, const TokenView& T, const FrontierState& S,
-                                         int32_t t, int32_t e, const PushCtx& c, bool valid) {
-  bool first = false;
-  int32_t d = 0;
-  if (valid) {
-    const int4 a = __ldg(L.arcs + e);
-    d = a.x;
-    if (VIT) {
-      // one rounded float32 addition per candidate
-      const float u = __fadd_rn((float)c.r, __int_as_float(a.y));
-      if (u != neg_inf()) {
-        const uint32_t id = (uint32_t)a.z;
-        first = atomicMax(vit_key(S, acc_slot(S, c.b, t, d)),
-                          ((unsigned long long)fkey(u) << 32) | (unsigned long long)(~id)) == 0ull;
+__device__ __forceinline__ void block_push(const LayoutView& L, const TokenView& T, const FrontierState& S,
+                                           int32_t t, BlockScratch<PushCtx>& sh, int32_t e0, int32_t len,
+                                           const PushCtx& mine) {
+  const int32_t total = block_stage(sh, e0, len, mine);
+  const bool cpt = compact(S);
+  unsigned long long* tab = htab(S, t);
+  const int w = hwords(S);
+  int32_t* stg = fwd_stage(S, t);
+  for (int32_t a0 = 0; a0 < total; a0 += KT * VU) {
+    int oo[VU];
+    int4 arc[VU];
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int32_t a = a0 + u * KT + (int32_t)threadIdx.x;
+      oo[u] = a < total ? block_owner(sh.excl, a) : -1;
+      arc[u] = oo[u] >= 0 ? __ldg(L.arcs + sh.e0[oo[u]] + (a - sh.excl[oo[u]])) : make_int4(0, 0, 0, 0);
+    }
+    unsigned long long cand[VU];
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      cand[u] = 0ull;
+      if (oo[u] < 0) continue;
+      const double r = sh.ctx[oo[u]].r;
+      if (VIT) {
+        // one rounded float32 addition per candidate
+        const float x = __fadd_rn((float)r, __int_as_float(arc[u].y));
+        if (x != neg_inf()) cand[u] = ((unsigned long long)fkey(x) << 32) | (unsigned long long)(~(uint32_t)arc[u].z);
+      } else {
+        // the exact float64 maximum (its term in the sum is then exactly 1)
+        const double v = r + (double)__int_as_float(arc[u].y);
+        if (v != -INFINITY) cand[u] = dkey(v);
+      }
+    }
+    bool first[VU];
+    int32_t sv[VU];  // the staged value: the state, or its slot
+    if (cpt) {
+      unsigned long long key[VU], old[VU];
+      uint64_t h[VU];
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        key[u] = cand[u] ? tab_key(sh.ctx[oo[u]].b, arc[u].x) : 0ull;
+        h[u] = tab_home(key[u], S.hmask);
+        old[u] = cand[u] ? atomicCAS(tab + h[u] * (uint64_t)w, 0ull, key[u]) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        first[u] = cand[u] != 0ull && old[u] == 0ull;
+        int64_t slot = (int64_t)h[u];
+        if (cand[u] != 0ull && old[u] != 0ull && old[u] != key[u])  // the home slot holds another key
+          slot = tab_claim(tab, w, S.hmask, key[u], &first[u]);
+        if (cand[u] != 0ull) {
+          if (slot < 0) {
+            atomicOr(S.flags + 1, ERR_POOL);
+          } else {
+            atomicMax(tab + slot * w + 1, cand[u]);
+          }
+        }
+        sv[u] = (int32_t)slot;
       }
     } else {
-      // the exact float64 maximum (its term in the sum is then exactly 1)
-      const double v = c.r + (double)__int_as_float(a.y);
-      if (v != -INFINITY) first = atomicMax(fwd_max(S, acc_slot(S, c.b, t, d)), dkey(v)) == 0ull;
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        first[u] = false;
+        sv[u] = arc[u].x;
+        if (cand[u] != 0ull) {
+          const int64_t slot = acc_slot(S, sh.ctx[oo[u]].b, t, arc[u].x);
+          first[u] = atomicMax(VIT ? vit_key(S, slot) : fwd_max(S, slot), cand[u]) == 0ull;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int32_t p = oo[u] >= 0 ? sh.ctx[oo[u]].p : 0;
+      const uint32_t i = warp_stage_index(S.scnt, p, first[u]);
+      if (first[u]) stg[__ldg(T.stf + p) + i] = sv[u];
     }
   }
-  const uint32_t i = warp_stage_index(S.scnt, c.p, first);
-  if (first) fwd_stage(S, t)[__ldg(T.stf + c.p) + i] = d;
+  __syncthreads();
 }
 
 // Live source j of position t-1 for the tokens of position t: at t = 1 the
@@ -490,7 +561,7 @@ __device__ __forceinline__ void first_position(const LayoutView& L, const TokenV
       len = r.len;
       me = PushCtx{x.p, __ldg(T.b + x.p), x.r};
     }
-    block_visit(sh, e0, len, me, [&](int32_t e, const PushCtx& c, bool ok) { push_arc<VIT>(L, T, S, 1, e, c, ok); });
+    block_push<VIT>(L, T, S, 1, sh, e0, len, me);
   }
   ranges_last_block(T, V, S, S.scnt, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt, S.step_rng + 2);
 }
@@ -543,22 +614,29 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
     if (j < R1) {
       const Entry x = step_entry(T, V, o, j);
       const int32_t b = __ldg(T.b + x.p);
-      const int32_t d = __ldcg(stg + __ldg(T.stf + x.p) + x.i);
+      const int32_t sv = __ldcg(stg + __ldg(T.stf + x.p) + x.i);  // the state, or its table slot
+      const bool cpt = compact(S);
+      unsigned long long* ce = cpt ? htab(S, t) + (int64_t)sv * hwords(S) : nullptr;
+      ulonglong2 kv = make_ulonglong2(0ull, 0ull);  // compact: {key, Viterbi key or maximum}
+      if (cpt) kv = __ldcg((const ulonglong2*)ce);
+      const int32_t d = cpt ? (int32_t)(uint32_t)kv.x : sv;
       const int64_t slot = acc_slot(S, b, t, d);
       double r;
       if (VIT) {
-        const unsigned long long key = __ldcg(vit_key(S, slot));
+        const unsigned long long key = cpt ? kv.y : __ldcg(vit_key(S, slot));
         const float rv = fkey_inv((uint32_t)(key >> 32));
         r = rv;
         S.pool_v[j] = rv;
         const int32_t id = (int32_t)(~(uint32_t)key);  // the best incoming arc
         S.pool_x[j] = id;
-        // the predecessor entry: the source's entry at t-1, which the step
-        // before this one recorded in the state map of that position
-        S.pool_n[j] = t > 1 ? __ldcg(S.vmap + acc_slot(S, b, t - 1, __ldg(S.src_by_id + id))) : -1;
-        S.vmap[slot] = (int32_t)j;
+        if (!cpt) {
+          // the predecessor entry: the source's entry at t-1, which the step
+          // before this one recorded in the state map of that position
+          S.pool_n[j] = t > 1 ? __ldcg(S.vmap + acc_slot(S, b, t - 1, __ldg(S.src_by_id + id))) : -1;
+          S.vmap[slot] = (int32_t)j;
+        }
       } else {
-        const ulonglong2 a = __ldcg((const ulonglong2*)fwd_sum(S, slot));
+        const ulonglong2 a = cpt ? make_ulonglong2(__ldcg(ce + 2), kv.y) : __ldcg((const ulonglong2*)fwd_sum(S, slot));
         const float sh_prev = t > 1 ? decode_max(__ldcg(S.mkey + x.p - 1)) : 0.f;
         r = fix_log_sum64(dkey_inv(a.y) - (double)sh_prev, a.x);
         S.pool_d[j] = r;
@@ -566,13 +644,17 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
         mk_key = fkey64(r);
       }
       S.pool_q[j] = d;
-      // the accumulator is zeroed only once its value has been used: a store
+      // the accumulator is emptied only once its value has been used: a store
       // issued right behind the load of the same word measured 25% slower
       asm volatile("" ::: "memory");
-      if (VIT)
+      if (cpt) {
+        *(ulonglong2*)ce = make_ulonglong2(0ull, 0ull);
+        if (!VIT) ce[2] = 0ull;
+      } else if (VIT) {
         *vit_key(S, slot) = 0ull;
-      else
+      } else {
         *(ulonglong2*)fwd_sum(S, slot) = make_ulonglong2(0ull, 0ull);
+      }
       Arcs nxt{0, 0};
       if (V.x_n > 0 && S.bw_n[b] > t) {  // the string goes on to t+1
         nxt = find_arcs(L, __ldg(T.sym + x.p + 1), d);
@@ -586,8 +668,7 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
       }
     }
     if (!VIT) warp_max_by_token(S.mkey, mk_p, mk_key);  // the step maximum m_t
-    block_visit(sh, e0, len, nx,
-                [&](int32_t e, const PushCtx& c, bool ok) { push_arc<VIT>(L, T, S, t + 1, e, c, ok); });
+    block_push<VIT>(L, T, S, t + 1, sh, e0, len, nx);
   }
   // pool ranges of position t+1's tokens
   if (V.x_n > 0) {
@@ -608,6 +689,71 @@ __global__ void __launch_bounds__(KT) k_vit_step(LayoutView L, TokenView T, Step
 __global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, StepView V, FrontierState S) {
   __shared__ BlockScratch<PushCtx> sh;
   step_position<false>(L, T, V, S, sh);
+}
+
+// The fixed-point terms of every thread's segment, VU arcs per thread a
+// round: the arcs, then each destination's maximum (compact: the home
+// slot's key and maximum in one load), then integer adds that return
+// nothing.  All threads of the block call it.
+__device__ __forceinline__ void sum_push(const LayoutView& L, const FrontierState& S, int32_t t,
+                                         BlockScratch<PushCtx>& sh, int32_t e0, int32_t len, const PushCtx& mine) {
+  const int32_t total = block_stage(sh, e0, len, mine);
+  const bool cpt = compact(S);
+  unsigned long long* tab = htab(S, t);
+  const int w = hwords(S);
+  for (int32_t a0 = 0; a0 < total; a0 += KT * VU) {
+    int oo[VU];
+    int4 arc[VU];
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int32_t a = a0 + u * KT + (int32_t)threadIdx.x;
+      oo[u] = a < total ? block_owner(sh.excl, a) : -1;
+      arc[u] = oo[u] >= 0 ? __ldg(L.arcs + sh.e0[oo[u]] + (a - sh.excl[oo[u]])) : make_int4(0, 0, 0, 0);
+    }
+    double v[VU];
+    unsigned long long* dst[VU];  // the sum word
+    unsigned long long mk[VU];    // the maximum's order key
+    if (cpt) {
+      unsigned long long key[VU];
+      ulonglong2 kv[VU];
+      uint64_t h[VU];
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        v[u] = oo[u] >= 0 ? sh.ctx[oo[u]].r + (double)__int_as_float(arc[u].y) : -INFINITY;
+        key[u] = v[u] != -INFINITY ? tab_key(sh.ctx[oo[u]].b, arc[u].x) : 0ull;
+        h[u] = tab_home(key[u], S.hmask);
+        kv[u] = key[u] ? __ldcg((const ulonglong2*)(tab + h[u] * w)) : make_ulonglong2(0ull, 0ull);
+      }
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        dst[u] = nullptr;
+        mk[u] = kv[u].y;
+        if (key[u] == 0ull) continue;
+        int64_t slot = (int64_t)h[u];
+        // the step before inserted every destination with a finite value
+        if (kv[u].x != key[u]) slot = tab_find(tab, w, S.hmask, key[u], &kv[u]);
+        if (slot >= 0) {
+          dst[u] = tab + slot * w + 2;
+          mk[u] = kv[u].y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        v[u] = oo[u] >= 0 ? sh.ctx[oo[u]].r + (double)__int_as_float(arc[u].y) : -INFINITY;
+        dst[u] = nullptr;
+        mk[u] = 0ull;
+        if (v[u] == -INFINITY) continue;
+        const int64_t slot = acc_slot(S, sh.ctx[oo[u]].b, t, arc[u].x);
+        dst[u] = fwd_sum(S, slot);
+        mk[u] = __ldcg(fwd_max(S, slot));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < VU; ++u)
+      if (dst[u]) atomicAdd(dst[u], fix_exp64(v[u], dkey_inv(mk[u])));
+  }
+  __syncthreads();
 }
 
 // Forward sum of position t: with every maximum M_d final, each live arc
@@ -634,14 +780,7 @@ __device__ __forceinline__ void sum_position(const LayoutView& L, const TokenVie
         me = PushCtx{x.p, __ldg(T.b + x.p), x.r};
       }
     }
-    block_visit(sh, e0, len, me, [&](int32_t e, const PushCtx& c, bool ok) {
-      if (!ok) return;
-      const int4 a = __ldg(L.arcs + e);
-      const double v = c.r + (double)__int_as_float(a.y);
-      if (v == -INFINITY) return;
-      const int64_t slot = acc_slot(S, c.b, t, a.x);
-      atomicAdd(fwd_sum(S, slot), fix_exp64(v, dkey_inv(__ldcg(fwd_max(S, slot)))));
-    });
+    sum_push(L, S, t, sh, e0, len, me);
   }
 }
 
@@ -686,10 +825,91 @@ struct BwdCtx {
   double K;     // C_{t-1} + E_t - log Z - m_{t-1}
 };
 
+// Compact accumulators: empty the backward values of the entries of
+// position y (their slots in bslot), every block a share.
+__device__ __forceinline__ void bwd_clear_position(const FrontierState& S, int32_t y) {
+  const int64_t R0 = __ldcg(S.step_rng + 2 * y), R1 = __ldcg(S.step_rng + 2 * y + 1);
+  unsigned long long* tab = btab(S, y);
+  for (int64_t j = R0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < R1; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t h = __ldcg(S.bslot + j);
+    if (h >= 0) *(ulonglong2*)(tab + 2 * (int64_t)h) = make_ulonglong2(0ull, 0ull);
+  }
+}
+
+// Reduction over each thread's segment of arcs on w_t for the backward
+// step.  VU arcs per thread a round: the arcs, then the backward values of
+// their destinations (the final weight at the string's last position), the
+// loads of a round issued together (compact: the home slot, almost always
+// the key's), then term(arc, beta, ctx) folded into the segment owner's
+// shared accumulator.
+template <class Op, class F>
+__device__ __forceinline__ typename Op::T bwd_reduce(BlockScratch<BwdCtx>& sh, const LayoutView& L,
+                                                     const FrontierState& S, int32_t t, int32_t e0, int32_t len,
+                                                     const BwdCtx& mine, F term) {
+  const int32_t total = block_stage(sh, e0, len, mine);
+  const bool cpt = compact(S);
+  const unsigned long long* tab = cpt ? btab(S, t) : nullptr;
+  for (int32_t a0 = 0; a0 < total; a0 += KT * VU) {
+    int oo[VU];
+    int4 arc[VU];
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int32_t a = a0 + u * KT + (int32_t)threadIdx.x;
+      oo[u] = a < total ? block_owner(sh.excl, a) : -1;
+      arc[u] = oo[u] >= 0 ? __ldg(L.arcs + sh.e0[oo[u]] + (a - sh.excl[oo[u]])) : make_int4(0, 0, 0, 0);
+    }
+    double ub[VU];
+    if (cpt) {
+      unsigned long long key[VU];
+      ulonglong2 kv[VU];
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        ub[u] = -INFINITY;
+        key[u] = 0ull;
+        kv[u] = make_ulonglong2(0ull, 0ull);
+        if (oo[u] < 0) continue;
+        const BwdCtx& c = sh.ctx[oo[u]];
+        if (t == c.n) {
+          ub[u] = (double)__ldg(S.theta_f + arc[u].x);
+        } else {
+          key[u] = tab_key(c.b, arc[u].x);
+          kv[u] = __ldcg((const ulonglong2*)(tab + 2 * tab_home(key[u], S.hmask)));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        if (key[u] == 0ull) continue;
+        // every destination of a live arc is live at t: absent means a
+        // backward value of -inf, which was not stored
+        if (kv[u].x != key[u] && kv[u].x != 0ull) tab_find(tab, 2, S.hmask, key[u], &kv[u]);
+        if (kv[u].x == key[u]) ub[u] = __longlong_as_double((long long)kv[u].y);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        ub[u] = -INFINITY;
+        if (oo[u] < 0) continue;
+        const BwdCtx& c = sh.ctx[oo[u]];
+        ub[u] = (t == c.n) ? (double)__ldg(S.theta_f + arc[u].x) : __ldcg(S.beta + acc_slot(S, c.b, t, arc[u].x));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < VU; ++u)
+      if (oo[u] >= 0) Op::atomic(&sh.acc[oo[u]], Op::key(term(arc[u], ub[u], sh.ctx[oo[u]])));
+  }
+  __syncthreads();
+  const typename Op::T r = Op::value(sh.acc[threadIdx.x]);
+  __syncthreads();
+  return r;
+}
+
 __device__ __forceinline__ void bwd_position(const LayoutView& L, const TokenView& T, const StepView& V,
                                              const FrontierState& S, const CountView& C, BlockScratch<BwdCtx>& sh) {
   const int lane = threadIdx.x & 31;
   const int32_t t = V.t;
+  const bool cpt = compact(S);
+  // the backward values of position t+1 were last read by the step before
+  if (cpt && V.y_t > 0) bwd_clear_position(S, V.y_t);
   int64_t R0, R1;
   source_range(V, S, &R0, &R1);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
@@ -720,23 +940,14 @@ __device__ __forceinline__ void bwd_position(const LayoutView& L, const TokenVie
                     (((t == 1) ? 0.0 : __ldcg(S.csum + p - 1)) + tE - lz) - (double)mprev};
       }
     }
-    // theta_e + beta_t[q'] - e_t; the final weight stands in for beta at the
-    // string's last position
-    auto ub_of = [&](int32_t d, const BwdCtx& c) -> double {
-      return (t == c.n) ? (double)__ldg(S.theta_f + d) : __ldcg(S.beta + acc_slot(S, c.b, t, d));
-    };
-    auto value = [&](int32_t e, const BwdCtx& c) -> double {
-      const int4 a = __ldg(L.arcs + e);
+    // theta_e + beta_t[q'] - e_t
+    me.m = bwd_reduce<RedMaxD>(sh, L, S, t, e0, len, me, [&](const int4& a, double ub, const BwdCtx& c) -> double {
       const float th = __int_as_float(a.y);
-      const double ub = ub_of(a.x, c);
       return (th == neg_inf() || ub == -INFINITY) ? -INFINITY : (double)th + (ub - (double)c.et);
-    };
-    me.m = block_reduce<RedMaxD>(sh, e0, len, me, value);
-    const unsigned long long su =
-        block_reduce<RedSum>(sh, e0, me.m == -INFINITY ? 0 : len, me, [&](int32_t e, const BwdCtx& c) {
-          const int4 a = __ldg(L.arcs + e);
+    });
+    const unsigned long long su = bwd_reduce<RedSum>(
+        sh, L, S, t, e0, me.m == -INFINITY ? 0 : len, me, [&](const int4& a, double ub, const BwdCtx& c) {
           const float th = __int_as_float(a.y);
-          const double ub = ub_of(a.x, c);
           if (th == neg_inf() || ub == -INFINITY) return 0ull;
           const double v = (double)th + (ub - (double)c.et);
           // the exponent adds terms of either sign and tens in size that
@@ -747,7 +958,28 @@ __device__ __forceinline__ void bwd_position(const LayoutView& L, const TokenVie
         });
     int32_t ek_p = -1;
     uint32_t ek_key = 0u;
-    if (q >= 0 && t > 1) {
+    if (cpt && t > 1 && j < R1) {
+      // every entry of position t-1 names its slot (or none), so that the
+      // step of position t-2 can empty the table behind it
+      int32_t h = -1;
+      if (q >= 0) {
+        const double u = fix_log_sum64(me.m, su);
+        if (u != -INFINITY) {
+          unsigned long long* tab = btab(S, t - 1);
+          bool fresh;
+          const int64_t hh = tab_claim(tab, 2, S.hmask, tab_key(me.b, q), &fresh);
+          if (hh < 0) {
+            atomicOr(S.flags + 1, ERR_POOL);
+          } else {
+            tab[2 * hh + 1] = (unsigned long long)__double_as_longlong(u);
+            h = (int32_t)hh;
+          }
+          ek_p = p - 1;
+          ek_key = fkey64(u);
+        }
+      }
+      S.bslot[j] = h;
+    } else if (q >= 0 && t > 1) {
       const double u = fix_log_sum64(me.m, su);
       S.beta[acc_slot(S, me.b, t - 1, q)] = u;
       if (u != -INFINITY) {
@@ -830,6 +1062,7 @@ __device__ __forceinline__ StepView step_at(const WaveSteps& D, int32_t t, int32
   V.x_slot0 = hasx ? D.step0[x_t] : 0;
   V.x_n = hasx ? D.step0[x_t + 1] - V.x_slot0 : 0;
   V.blocks = (int32_t)gridDim.x;
+  V.y_t = 0;
   return V;
 }
 
@@ -865,10 +1098,15 @@ __global__ void __launch_bounds__(KT) k_bwd_persist(LayoutView L, TokenView T, W
   // a forward pass that gave up leaves nothing to walk back over
   if (*(volatile uint32_t*)(S.flags + 1) & ERR_TIMEOUT) return;
   for (int32_t t = D.tmax; t >= 1; --t) {
-    bwd_position(L, T, step_at(D, t, t - 1), S, C, sh);
+    StepView V = step_at(D, t, t - 1);
+    V.y_t = t + 1 < D.tmax ? t + 1 : 0;
+    bwd_position(L, T, V, S, C, sh);
     if (!grid_sync(G, S.flags + 1)) return;
   }
+  if (compact(S) && D.tmax >= 2) bwd_clear_position(S, 1);
 }
+
+__global__ void k_bwd_clear(FrontierState S, int32_t y) { bwd_clear_position(S, y); }
 
 // ======================================================================
 // Epilogues: final reductions (Alg. 1 return line; Alg. 2 Z), backtrace
@@ -927,6 +1165,49 @@ __global__ void __launch_bounds__(FT) k_vit_final(FrontierState S, float* __rest
 // One thread per string, from the last position back: each pool entry
 // names its best incoming arc and the entry of that arc's source, so the
 // path is a chain of loads with no search.
+//
+// With compact accumulators there is no state map to record predecessor
+// entries: a block per string finds each predecessor among the pool entries
+// of the previous token (each state is there once), BB at a time.
+constexpr int BB = 512;
+__global__ void __launch_bounds__(BB) k_backtrace_scan(FrontierState S, const int32_t* __restrict__ olabel_by_id,
+                                                       const int32_t* __restrict__ jfinal,
+                                                       int32_t* __restrict__ paths, int32_t* __restrict__ olabels) {
+  __shared__ int32_t found;
+  const int64_t b = blockIdx.x;
+  const int32_t n = S.bw_n[b];
+  const int64_t off = S.bw_off[b];
+  int32_t j = jfinal[b];
+  int32_t t = n;
+  for (; t >= 1 && j >= 0; --t) {
+    const int32_t id = S.pool_x[j];
+    if (threadIdx.x == 0) {
+      paths[off + t - 1] = id;
+      if (olabels) olabels[off + t - 1] = olabel_by_id[id];
+      found = -1;
+    }
+    __syncthreads();
+    if (t > 1) {
+      const int32_t src = __ldg(S.src_by_id + id);
+      const int64_t p = off + t - 2;  // the token of position t-1
+      const int64_t base = S.pool_base[p];
+      const int32_t cnt = S.pool_cnt[p];
+      for (int32_t i0 = 0; i0 < cnt; i0 += BB) {
+        const int32_t i = i0 + (int32_t)threadIdx.x;
+        const bool hit = i < cnt && S.pool_q[base + i] == src;
+        if (hit) found = (int32_t)(base + i);
+        if (__syncthreads_or(hit)) break;  // the same answer in every thread
+      }
+    }
+    j = found;  // the predecessor entry (none at the first position)
+    __syncthreads();
+  }
+  for (int32_t u = threadIdx.x; u < t; u += BB) {  // no path (or an entry chain cut short): markers
+    paths[off + u] = -1;
+    if (olabels) olabels[off + u] = -1;
+  }
+}
+
 __global__ void k_backtrace(FrontierState S, const int32_t* __restrict__ olabel_by_id, int32_t Bw,
                             const int32_t* __restrict__ jfinal, int32_t* __restrict__ paths,
                             int32_t* __restrict__ olabels) {
@@ -1215,8 +1496,18 @@ int launch_vit_final(const FrontierState& S, int32_t Bw, float* scores, int32_t*
 int launch_backtrace(const FrontierState& S, const int32_t* olabel_by_id, int32_t Bw, const int32_t* jfinal,
                      int32_t* paths, int32_t* olabels, cudaStream_t s) {
   if (Bw <= 0) return FST_OK;
+  if (S.hmask != 0ull) {
+    k_backtrace_scan<<<(unsigned)Bw, BB, 0, s>>>(S, olabel_by_id, jfinal, paths, olabels);
+    return check_launch("k_backtrace_scan");
+  }
   k_backtrace<<<(unsigned)((Bw + 127) / 128), 128, 0, s>>>(S, olabel_by_id, Bw, jfinal, paths, olabels);
   return check_launch("k_backtrace");
+}
+
+int launch_bwd_clear(const FrontierState& S, int32_t pos, int num_sms, cudaStream_t s) {
+  if (S.hmask == 0ull || pos < 1) return FST_OK;
+  k_bwd_clear<<<(unsigned)std::max(num_sms, 1) * 2, 256, 0, s>>>(S, pos);
+  return check_launch("k_bwd_clear");
 }
 
 int launch_fb_final(const FrontierState& S, int32_t Bw, double* logz, int32_t* status, cudaStream_t s) {

@@ -30,6 +30,8 @@ struct StepView {
   int32_t slot0;
   int32_t x_t, x_n, x_slot0;
   int32_t blocks;   // grid of the launch (work is a grid-stride loop)
+  int32_t y_t;      // backward steps with compact accumulators: the position whose
+                    // backward values this step clears (0: none)
 };
 
 struct TokenView {
@@ -41,12 +43,21 @@ struct TokenView {
 
 // State of one wave (or of one plain-method string).
 //
-// Accumulators: dense per string, two parity buffers, all zero between
-// runs.  A forward step pushes every arc out of a live state of position t
-// into the accumulator of its destination at t+1 with an atomic max (the
+// Accumulators, in one of two layouts, all empty between runs:
+//   dense   -- per string, two parity buffers of Q slots each (the plain
+//              method's single string, and plans made with
+//              FST_PLAN_DENSE_ACC);
+//   compact -- open-addressing hash tables keyed by (string, state), one per
+//              position parity, sized for the live states of a position
+//              rather than for every state of every string: a few MB that
+//              stay in L2, where the dense arrays of a large batch take tens
+//              of GB.  The staging lists then hold table slots.
+// In both, a forward step pushes every arc out of a live state of position
+// t into the accumulator of its destination at t+1 with an atomic max (the
 // packed Viterbi key, or the forward maximum); the push that finds the
-// accumulator empty stages the destination.  The next step reads each
-// staged accumulator once, turns it into a live-pool entry and zeroes it.
+// accumulator empty (or inserts its key) stages the destination.  The next
+// step reads each staged accumulator once, turns it into a live-pool entry
+// and empties it.
 //
 // Live pool: for every token, the states with a finite value at its
 // position: the state, its value, and the best incoming arc (Viterbi) or
@@ -56,13 +67,27 @@ struct TokenView {
 // kernels split evenly over blocks, whatever the tokens' frontier sizes.
 struct FrontierState {
   int32_t Q;
-  // [Bw][2][Q] accumulators of acc_stride 64-bit words: Viterbi keys use the
-  // first word; the forward passes need stride 2, {fixed-point sum, maximum
-  // order key in the low half}, so that both sit on one cache line
+  // dense: [Bw][2][Q] accumulators of acc_stride 64-bit words: Viterbi keys
+  // use the first word; the forward passes need stride 2, {fixed-point sum,
+  // maximum order key in the low half}, so that both sit on one cache line
   unsigned long long* acc;
   int32_t acc_stride;
   double* beta;                      // [Bw][2][Q] backward values, float64 (null for Viterbi-only state)
   int32_t* vmap;                     // [Bw][2][Q] Viterbi: pool entry of each live state (null for forward-only state)
+  // compact (hmask > 0): tables of hmask + 1 slots, key (wave-local string
+  // + 1) << 32 | state (0 = empty).  htab0 / htab1 hold the positions of even / odd
+  // parity, 2 acc_stride words a slot: {key, Viterbi key} or {key, maximum
+  // order key, fixed-point sum, 0}.  btab0..2 hold the backward values of
+  // the positions t with t mod 3 = 0, 1, 2, {key, float64 bits}; bslot maps
+  // each pool entry to its slot there (-1: none).  Viterbi needs no state
+  // map: the backtrace finds each predecessor among its token's entries.
+  unsigned long long* htab0;
+  unsigned long long* htab1;
+  unsigned long long* btab0;
+  unsigned long long* btab1;
+  unsigned long long* btab2;
+  int32_t* bslot;
+  uint64_t hmask;
   const int32_t* src_by_id;          // [A] source state of each arc
   int32_t* stage;                    // staged destinations of positions of even parity
   int32_t* stage_b;                  // of odd parity
@@ -170,8 +195,12 @@ int launch_counts_out(int64_t A, const CountView& C, float* out, cudaStream_t s)
 int launch_final_posteriors(const FrontierState& S, int32_t Bw, const CountView& C, cudaStream_t s);
 // out[i] = (float)in[i], i < n.
 int launch_to_float(const double* in, int64_t n, float* out, cudaStream_t s);
-// Zero n 64-bit words of accumulators if error bit 1 is set in *flag: a
-// run whose pool overflowed leaves staged accumulators behind.
+// Zero n 64-bit words of accumulators if an error bit is set in *flag: a
+// run whose pool overflowed (or that gave up at a barrier) leaves staged
+// accumulators behind.
 int launch_clear_if_overflow(const uint32_t* flag, unsigned long long* acc, int64_t n, int num_sms, cudaStream_t s);
+// Compact accumulators: clear the backward values of position y_t (after
+// the pass's last step, which reads those of position 1).
+int launch_bwd_clear(const FrontierState& S, int32_t pos, int num_sms, cudaStream_t s);
 
 }  // namespace fstgpu

@@ -37,6 +37,12 @@ constexpr int64_t POOL_PER_TOKEN = 256;
 // approximate device bytes per token of a wave (token tables, staging
 // counts, pool ranges, step maxima and running sums)
 constexpr int64_t TOKEN_BYTES = 80;
+// compact accumulators: the live states of one position that the tables
+// are sized for, 128 per token of the busiest position and at least 2^18
+// (one string's frontier can span most of a 200,000-state FST), never more
+// than the position's destination bound
+constexpr int64_t LIVE_PER_TOKEN = 128;
+constexpr int64_t LIVE_FLOOR = (int64_t)1 << 18;
 
 // *sum += the non-negative values of v[0..n).
 __global__ void k_sum_i32(const int32_t* __restrict__ v, int64_t n, unsigned long long* __restrict__ sum) {
@@ -76,7 +82,7 @@ struct Wave {
 #define PLAN_STORAGE(X)                                                                                          \
   X(acc) X(beta) X(vmap) X(stage) X(stage_b) X(scnt) X(pool_q) X(pool_x) X(pool_n) X(pool_v) X(pool_base)          \
   X(pool_cnt) X(slot_base) X(step_rng) X(pool_top) X(flags_d) X(mkey) X(ekey) X(csum) X(esum) X(jfinal) X(logz) \
-  X(cnt64) X(start64) X(final64) X(gbar)
+  X(cnt64) X(start64) X(final64) X(gbar) X(htab) X(bslot)
 
 struct fst_plan_s {
   fst_t* fst = nullptr;
@@ -89,6 +95,14 @@ struct fst_plan_s {
   int32_t acc_stride = 1;
   double* beta = nullptr;
   int32_t* vmap = nullptr;
+  // compact accumulators (the default; FST_PLAN_DENSE_ACC: the dense arrays
+  // above): the two parity tables, then (forward-backward) the three
+  // backward-value tables, cap_hslots slots each, in one allocation
+  bool compact = true;
+  int64_t hslots = 0;                  // slots this plan's busiest position needs
+  int64_t table_limit = 0;             // fst_plan_limit_table: slots a run may use (0 = cap_hslots)
+  unsigned long long* htab = nullptr;
+  int32_t* bslot = nullptr;            // [pool_cap]
   int32_t *stage = nullptr, *stage_b = nullptr;
   uint32_t* scnt = nullptr;
   int32_t *pool_q = nullptr, *pool_x = nullptr, *pool_n = nullptr;
@@ -109,7 +123,7 @@ struct fst_plan_s {
   int64_t max_bw = 0, max_ntok = 0, max_stage = 0;
   // capacities of the device storage below: this plan's needs, or more when
   // the storage was taken over from an earlier plan of the same handle
-  int64_t cap_bw = 0, cap_nt = 0, cap_stage = 0, cap_len = 0, cap_B = 0, store_bytes = 0;
+  int64_t cap_bw = 0, cap_nt = 0, cap_stage = 0, cap_len = 0, cap_B = 0, store_bytes = 0, cap_hslots = 0;
   bool forward_done = false;
   // optional per-launch CUDA events (fst_plan_profile)
   LaunchProfile prof;
@@ -247,6 +261,22 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.acc_stride = P->acc_stride;
   S.beta = P->beta;
   S.vmap = P->vmap;
+  if (P->compact) {
+    const int64_t n = P->cap_hslots, hw = 2 * (int64_t)P->acc_stride;
+    S.htab0 = P->htab;
+    S.htab1 = P->htab + n * hw;
+    if (P->want_fb) {
+      S.btab0 = P->htab + 2 * n * hw;
+      S.btab1 = S.btab0 + 2 * n;
+      S.btab2 = S.btab0 + 4 * n;
+    }
+    S.bslot = P->bslot;
+    // a limit uses the first slots of each table (a power of two)
+    int64_t use = n;
+    if (P->table_limit > 0)
+      while (use > 2 && use / 2 >= P->table_limit) use /= 2;  // at least 2: a mask of 0 means dense
+    S.hmask = (uint64_t)(use - 1);
+  }
   S.src_by_id = f->src_by_id;
   S.stage = P->stage;
   S.stage_b = P->stage_b;
@@ -295,15 +325,25 @@ StepView wave_step(const fst_plan_s* P, const Wave& W, int32_t t, int32_t x_t) {
   V.x_n = hasx ? W.step0[x_t + 1] - W.step0[x_t] : 0;
   const int64_t est = (int64_t)std::max(V.n, V.x_n) * P->density;
   V.blocks = (int32_t)std::min<int64_t>((int64_t)P->fst->num_sms * 8, std::max<int64_t>(1, (est + 255) / 256));
+  V.y_t = 0;
   return V;
 }
 
 // State that starts every pass of a wave at zero.  A pass whose pool
 // overflowed left staged accumulators behind: they are cleared first.
+int64_t htab_words(const fst_plan_s* P, int64_t slots) {
+  return slots * (2 * 2 * (int64_t)P->acc_stride + (P->want_fb ? 3 * 2 : 0));
+}
+
 int wave_begin(fst_plan_s* P, const Wave& W, cudaStream_t s, bool fb) {
   int rc;
-  const int64_t na = P->cap_bw * 2 * (int64_t)P->fst->Q * P->acc_stride;
-  if ((rc = launch_clear_if_overflow(P->flags_d + 1, P->acc, na, P->fst->num_sms, s))) return rc;
+  if (P->compact) {
+    rc = launch_clear_if_overflow(P->flags_d + 1, P->htab, htab_words(P, P->cap_hslots), P->fst->num_sms, s);
+  } else {
+    const int64_t na = P->cap_bw * 2 * (int64_t)P->fst->Q * P->acc_stride;
+    rc = launch_clear_if_overflow(P->flags_d + 1, P->acc, na, P->fst->num_sms, s);
+  }
+  if (rc) return rc;
   const size_t n4 = (size_t)std::max<int64_t>(1, W.ntok) * 4;
   FST_CUDA(cudaMemsetAsync(P->scnt, 0, n4, s));
   FST_CUDA(cudaMemsetAsync(P->pool_top, 0, 8, s));
@@ -382,8 +422,15 @@ int run_backward_wave(fst_plan_s* P, const Wave& W, const float* d_weights, bool
       PROF(FST_PROF_BWD_STEP,
            launch_bwd_persist(L, T, wave_steps(W), S, C, persist_grid(P, W, 2), grid_sync_of(P), s));
   } else {
-    for (int32_t t = W.tmax; t >= 1; --t)
-      PROF(FST_PROF_BWD_STEP, launch_bwd_step(L, T, wave_step(P, W, t, t - 1), S, C, s));
+    for (int32_t t = W.tmax; t >= 1; --t) {
+      StepView V = wave_step(P, W, t, t - 1);
+      // compact accumulators: the step empties the backward values of t+1
+      // (none are stored for the last position) and one more launch those
+      // of position 1
+      V.y_t = t + 1 < W.tmax ? t + 1 : 0;
+      PROF(FST_PROF_BWD_STEP, launch_bwd_step(L, T, V, S, C, s));
+    }
+    if (W.tmax >= 2 && P->compact) PROF(FST_PROF_BWD_STEP, launch_bwd_clear(S, 1, f->num_sms, s));
   }
   if (states) PROF(FST_PROF_COUNTS, launch_final_posteriors(S, W.Bw, C, s));
   return FST_OK;
@@ -567,10 +614,13 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
       }
       budget = std::max<int64_t>((int64_t)256 << 20, std::min<int64_t>((int64_t)32 << 30, (int64_t)(free_b / 4)));
     }
-    // accumulators: 2 x 8 bytes per state (Viterbi), or 2 x 16 for the
-    // forward sums and maxima plus 2 x 8 for the backward values; Viterbi
-    // also maps states to pool entries, 2 x 4 bytes
-    const int64_t per_string = (int64_t)f->Q * ((P->want_fb ? 48 : 16) + (P->want_vit ? 8 : 0)) + 64;
+    // dense accumulators: 2 x 8 bytes per state (Viterbi), or 2 x 16 for
+    // the forward sums and maxima plus 2 x 8 for the backward values;
+    // Viterbi also maps states to pool entries, 2 x 4 bytes.  Compact ones
+    // do not grow with the strings.
+    P->compact = !(flags & FST_PLAN_DENSE_ACC);
+    const int64_t per_string =
+        (P->compact ? 0 : (int64_t)f->Q * ((P->want_fb ? 48 : 16) + (P->want_vit ? 8 : 0))) + 64;
     const int64_t per_token = TOKEN_BYTES + POOL_PER_TOKEN * 20;
     int32_t b0 = 0;
     int64_t acc = 0;
@@ -607,11 +657,20 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
                                     std::min(std::max(budget / 4, (int64_t)256 << 20), (int64_t)4 << 30) / ebytes);
       // pool entries are named by int32 indices
       P->pool_cap = std::max(P->pool_cap, std::min(std::min(w.pool_bound, want), (int64_t)INT32_MAX));
+      // compact accumulators at half load (a power of two; slots are named
+      // by int32 indices)
+      int64_t busiest = 0;
+      for (int32_t t = 1; t <= w.tmax; ++t) busiest = std::max<int64_t>(busiest, w.step0[t + 1] - w.step0[t]);
+      const int64_t live = std::min(w.stage, std::max(busiest * LIVE_PER_TOKEN, LIVE_FLOOR));
+      int64_t slots = 1024;
+      while (slots < 2 * live && slots < ((int64_t)1 << 30)) slots <<= 1;
+      P->hslots = std::max(P->hslots, slots);
     }
     if (rc) break;
     P->acc_stride = P->want_fb ? 2 : 1;
     fst_plan_s* d = donor_owner.get();
-    if (d && d->fst == f && d->want_fb == P->want_fb && d->want_vit == P->want_vit && d->cap_bw >= P->max_bw &&
+    if (d && d->fst == f && d->want_fb == P->want_fb && d->want_vit == P->want_vit && d->compact == P->compact &&
+        (!P->compact || d->cap_hslots >= P->hslots) && (P->compact || d->cap_bw >= P->max_bw) &&
         d->cap_nt >= P->max_ntok && d->cap_stage >= P->max_stage && d->pool_cap >= P->pool_cap &&
         d->cap_len >= P->max_len && d->cap_B >= B) {
       // take the donor's storage: its accumulators are zero (or, after an
@@ -624,6 +683,7 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
       P->cap_stage = d->cap_stage;
       P->cap_len = d->cap_len;
       P->cap_B = d->cap_B;
+      P->cap_hslots = d->cap_hslots;
       P->pool_cap = d->pool_cap;
       P->store_bytes = d->store_bytes;
       P->bytes += d->store_bytes;
@@ -635,12 +695,21 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
     P->cap_stage = P->max_stage;
     P->cap_len = P->max_len;
     P->cap_B = B;
-    const int64_t na = P->max_bw * 2 * (int64_t)f->Q;
+    P->cap_hslots = P->compact ? P->hslots : 0;
+    const int64_t na = P->compact ? 0 : P->max_bw * 2 * (int64_t)f->Q;
     const int64_t nt = P->max_ntok;
-    if ((rc = alloc_store(P, &P->acc, na * P->acc_stride))) break;
-    if (P->want_fb && (rc = alloc_store(P, &P->beta, na))) break;
-    if (P->want_vit && (rc = alloc_store(P, &P->vmap, na))) break;
-    if ((rc = alloc_store(P, &P->pool_n, P->pool_cap))) break;
+    const int64_t nh = P->compact ? htab_words(P, P->cap_hslots) : 0;
+    if (P->compact) {
+      if ((rc = alloc_store(P, &P->htab, nh))) break;
+      if (P->want_fb && (rc = alloc_store(P, &P->bslot, P->pool_cap))) break;
+    } else {
+      if ((rc = alloc_store(P, &P->acc, na * P->acc_stride))) break;
+      if (P->want_fb && (rc = alloc_store(P, &P->beta, na))) break;
+      if (P->want_vit && (rc = alloc_store(P, &P->vmap, na))) break;
+    }
+    // forward: arcs on the next symbol; Viterbi with dense accumulators:
+    // the predecessor entry
+    if ((P->want_fb || !P->compact) && (rc = alloc_store(P, &P->pool_n, P->pool_cap))) break;
     if ((rc = alloc_store(P, &P->stage, P->max_stage)) || (rc = alloc_store(P, &P->stage_b, P->max_stage)) ||
         (rc = alloc_store(P, &P->scnt, nt)) || (rc = alloc_store(P, &P->pool_q, P->pool_cap)) ||
         (rc = alloc_store(P, &P->pool_x, P->pool_cap)) || (rc = alloc_store(P, &P->pool_v, P->pool_cap)) ||
@@ -656,8 +725,14 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
                        (rc = alloc_store(P, &P->final64, f->Q))))
       break;
     // the accumulators start at zero and every run leaves them so
-    cudaError_t ce = cudaMemsetAsync(P->acc, 0, (size_t)std::max<int64_t>(na * P->acc_stride, 1) * 8, s);
+    cudaError_t ce = cudaSuccess;
+    if (P->acc) ce = cudaMemsetAsync(P->acc, 0, (size_t)std::max<int64_t>(na * P->acc_stride, 1) * 8, s);
     if (ce == cudaSuccess && P->beta) ce = cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s);
+    if (ce == cudaSuccess && P->htab) ce = cudaMemsetAsync(P->htab, 0, (size_t)std::max<int64_t>(nh, 1) * 8, s);
+    // position ranges start empty (a backward step reads those of a later
+    // position to empty its tables)
+    if (ce == cudaSuccess)
+      ce = cudaMemsetAsync(P->step_rng, 0, (size_t)(2 * ((int64_t)P->max_len + 2)) * 8, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(P->flags_d, 0, 8, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(P->gbar, 0, 8, s);
     // per-token pool ranges start empty: a run that stops early leaves the
@@ -723,8 +798,8 @@ extern "C" int fst_plan_info(const fst_plan_t* P, int32_t* num_strings, int64_t*
     // overflow clear, first push, one step per position, final, backtrace
     vl += (int64_t)w.tmax + 4;
     // overflow clear, first push, sum and step per position, final; one
-    // backward step per position
-    fl += 3 * (int64_t)w.tmax + 3;
+    // backward step per position (and, compact, the clear of position 1)
+    fl += 3 * (int64_t)w.tmax + 3 + ((P->compact && w.tmax >= 2) ? 1 : 0);
   }
   fl += 1;  // counts out
   if (num_strings) *num_strings = P->B;
@@ -961,6 +1036,21 @@ extern "C" int fst_plan_limit_pool(fst_plan_t* P, int64_t entries) {
   if (!P || entries < 0) { set_error("fst_plan_limit_pool: bad arguments"); return FST_ERR_INVALID_ARG; }
   P->pool_limit = entries;
   for (fst_plan_s* q : P->parts) q->pool_limit = entries;
+  return FST_OK;
+}
+
+extern "C" int fst_plan_limit_table(fst_plan_t* P, int64_t slots) {
+  if (!P || slots < 0) { set_error("fst_plan_limit_table: bad arguments"); return FST_ERR_INVALID_ARG; }
+  P->table_limit = slots;
+  for (fst_plan_s* q : P->parts) q->table_limit = slots;
+  return FST_OK;
+}
+
+extern "C" int fst_plan_table_slots(const fst_plan_t* P, int64_t* slots) {
+  if (!P || !slots) { set_error("fst_plan_table_slots: bad arguments"); return FST_ERR_INVALID_ARG; }
+  int64_t n = P->compact ? P->cap_hslots : 0;
+  for (const fst_plan_s* q : P->parts) n = std::max(n, q->compact ? q->cap_hslots : 0);
+  *slots = n;
   return FST_OK;
 }
 

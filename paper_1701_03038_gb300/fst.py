@@ -211,8 +211,8 @@ class Fst:
         return float(lz[0]), (cnt[:self.num_arcs] if posteriors else None), rc
 
     def set_plain_method(self, method: int):
-        """Kernels of the single-string Viterbi: _lib.PLAIN_FRONTIER, PLAIN_SLICE
-        or PLAIN_AUTO (see fst_set_plain_method)."""
+        """Kernels of the single-string calls: _lib.PLAIN_FRONTIER, PLAIN_SLICE,
+        PLAIN_AUTO or PLAIN_BLOCK (see fst_set_plain_method)."""
         check(self._lib.fst_set_plain_method(self._h, int(method)), "fst_set_plain_method")
 
     def set_plain_driver(self, driver: int, grid_blocks: int = 0):
@@ -506,6 +506,16 @@ class Plan:
     def limit_pool(self, entries: int = 0):
         """Cap the live pool of the following runs (0 = the full capacity)."""
         check(self._lib.fst_plan_limit_pool(self._h, int(entries)), "fst_plan_limit_pool")
+
+    def limit_table(self, slots: int = 0):
+        """Cap the compact accumulator tables of the following runs (0 = the full capacity)."""
+        check(self._lib.fst_plan_limit_table(self._h, int(slots)), "fst_plan_limit_table")
+
+    def table_slots(self) -> int:
+        """Slots of each compact accumulator table (0: dense accumulators)."""
+        n = C.c_int64()
+        check(self._lib.fst_plan_table_slots(self._h, C.byref(n)), "fst_plan_table_slots")
+        return n.value
 
     def profile(self, enable: bool = True):
         """Bracket every kernel of the following runs with CUDA events."""

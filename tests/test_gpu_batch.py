@@ -333,3 +333,78 @@ def test_stream_parallel_parts(c2s, parts):
     assert prof["vit_step"][1] > 0
     with pytest.raises(_lib.FstError):
         p.set_driver(_lib.DRIVER_PERSISTENT)
+
+
+@pytest.mark.parametrize("driver", ["launch", "persistent"])
+def test_dense_and_compact_accumulators_agree(c2s, driver):
+    # the hash-table accumulators (default) and the dense per-string arrays
+    # (FST_PLAN_DENSE_ACC) compute the same quantities: Viterbi bit for bit,
+    # log Z bit for bit (exact maxima and fixed-point sums do not depend on
+    # the order of the atomics), counts within float64 rounding
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    pc = f.plan(ids, off)
+    pd = f.plan(ids, off, flags=_lib.PLAN_DENSE_ACC)
+    assert pc.table_slots() >= 1024 and pd.table_slots() == 0
+    if driver == "persistent":
+        for p in (pc, pd):
+            p.set_driver(_lib.DRIVER_PERSISTENT, 0)
+    for p in (pc, pd):
+        p.viterbi()
+        p.forward_backward(states=True)
+    torch.cuda.synchronize()
+    for k in ("scores", "paths", "olabels", "status", "logz"):
+        assert torch.equal(getattr(pc, k), getattr(pd, k)), k
+    assert np.allclose(pc.counts.cpu().numpy(), pd.counts.cpu().numpy(), rtol=1e-9, atol=1e-12)
+    B, N = strs.count, len(strs.ids)
+    check_batch_viterbi(o, strs, dict(scores=pc.scores[:B], paths=pc.paths[:N], olabels=pc.olabels[:N],
+                                      status=pc.status[:B]))
+    check_batch_fb(o, strs, pc.logz[:B], pc.counts[:o.A])
+
+
+def test_compact_tables_near_full(c2s):
+    # shrinking the tables drives the probe sequences through collisions:
+    # each run is exact or, once a position's live states no longer fit,
+    # reports FST_ERR_OOM for every string; the exact runs include tables at
+    # more than half load
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    B, N = strs.count, len(strs.ids)
+    pv = f.plan(ids, off, flags=_lib.PLAN_NO_FB)
+    pf = f.plan(ids, off, flags=_lib.PLAN_NO_VITERBI)
+    pv.viterbi()
+    pf.forward_backward()
+    torch.cuda.synchronize()
+    ref = {k: getattr(pv, k).clone() for k in ("scores", "paths", "olabels")}
+    ref_lz, ref_cnt = pf.logz.clone(), pf.counts.clone()
+    cap = pv.table_slots()
+    exact, full = [], []
+    slots = cap
+    while slots >= 2:
+        pv.limit_table(slots)
+        pf.limit_table(slots)
+        pv.viterbi()
+        pf.forward_backward()
+        torch.cuda.synchronize()
+        sv, sf = pv.status[:B].cpu().numpy(), pf.status[:B].cpu().numpy()
+        if (sv == _lib.OOM).all():
+            assert (sf == _lib.OOM).all() and np.isneginf(pf.logz[:B].cpu().numpy()).all()
+            assert (pv.paths[:N].cpu().numpy() == -1).all()
+            full.append(slots)
+        else:
+            for k, v in ref.items():
+                assert torch.equal(getattr(pv, k), v), (k, slots)
+            assert torch.equal(pf.logz, ref_lz)
+            assert np.allclose(pf.counts.cpu().numpy(), ref_cnt.cpu().numpy(), rtol=1e-9, atol=1e-12)
+            exact.append(slots)
+        slots //= 2
+    assert exact and full
+    # the smallest exact table is within a factor 2 of overflowing: its
+    # busiest position filled more than half of it
+    assert min(exact) == 2 * max(full)
+    pv.limit_table(0)
+    pf.limit_table(0)

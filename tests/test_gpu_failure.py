@@ -75,6 +75,49 @@ def test_pool_overflow_reports_oom_then_recovers():
         check_exact()
 
 
+def test_table_overflow_reports_oom_then_recovers():
+    # the compact accumulator tables capped at 8 slots cannot hold one
+    # position's live states (24 strings, each with at least one): the run
+    # reports FST_ERR_OOM everywhere, and with the cap lifted the same plans
+    # are exact again (the overflowing run's leftovers are cleared)
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    from paper_1701_03038_gb300._lib import PLAN_NO_FB, PLAN_NO_VITERBI
+    from paper_1701_03038_gb300.fst import Fst
+    fa, strs = synth.make_config("c2", scale=0.02, strings=24)
+    f, o = Fst.from_arrays(fa), oracle.Fst(fa)
+    ids = torch.from_numpy(strs.ids).cuda()
+    off = torch.from_numpy(strs.offsets).cuda()
+    pv = f.plan(ids, off, flags=PLAN_NO_FB)
+    pf = f.plan(ids, off, flags=PLAN_NO_VITERBI)
+    B, N = strs.count, len(strs.ids)
+    ofb = o.fb_batch(strs.ids, strs.offsets, nthreads=8)
+    for rnd in range(2):
+        pv.limit_table(8)
+        pf.limit_table(8)
+        pv.viterbi()
+        pf.forward_backward()
+        torch.cuda.synchronize()
+        assert (pv.status[:B].cpu().numpy() == _lib.OOM).all()
+        assert (pf.status[:B].cpu().numpy() == _lib.OOM).all()
+        assert (pv.paths[:N].cpu().numpy() == -1).all()
+        assert (pf.counts.cpu().numpy() == 0).all()
+        pv.limit_table(0)
+        pf.limit_table(0)
+        pv.viterbi()
+        pf.forward_backward()
+        torch.cuda.synchronize()
+        sc, pa, ol, st = (pv.scores.cpu().numpy(), pv.paths.cpu().numpy(), pv.olabels.cpu().numpy(),
+                          pv.status.cpu().numpy())
+        for b in range(B):
+            lo, hi = strs.offsets[b], strs.offsets[b + 1]
+            assert_viterbi_equal(sc[b], pa[lo:hi], ol[lo:hi], st[b], o.viterbi(strs.get(b)))
+            assert_logz_close(pf.logz[b].item(), ofb["logz"][b])
+        assert_counts_close(pf.counts.cpu().numpy(), ofb["counts"], batch=True)
+    with pytest.raises(_lib.FstError):
+        pv.limit_table(-1)
+
+
 def test_pool_limit_rejects_negative():
     import torch
     from paper_1701_03038_gb300._lib import FstError

@@ -295,3 +295,58 @@ def test_plain_forward_backward_persistent_driver(grid):
         assert_logz_close(lz, o.forward_backward(x)["logz"])
     with pytest.raises(_lib.FstError):
         f.set_plain_driver(_lib.DRIVER_PERSISTENT, 10 ** 7)
+
+
+def test_block_method_small_fsts():
+    # the one-block kernels (position loop inside the kernel, per-state values
+    # in shared memory): Viterbi bit-identical to the frontier kernels, log Z
+    # and posteriors against the oracle, on the plain tests' small FSTs
+    from paper_1701_03038_gb300 import _lib
+    rng = np.random.default_rng(321)
+    cases = []
+    fa, x, _, _, _ = pins.fig1_case()
+    cases.append((fa, [x, np.zeros(0, np.int32)]))
+    for _ in range(40):
+        fa = synth.tiny_fst(rng)
+        cases.append((fa, [rng.integers(0, fa.num_isyms, size=int(rng.integers(0, 7))).astype(np.int32)
+                           for _ in range(2)]))
+    fa, strs = synth.make_config("c1", strings=4)
+    cases.append((fa, [strs.get(b) for b in range(strs.count)]))
+    fa, strs = synth.make_config("c2", scale=0.02, strings=10)  # 1,000 states, 100,000 arcs
+    iid = synth.make_strings(fa, 3, 5, 20, seed=5, kind="iid")  # some without a path
+    cases.append((fa, [strs.get(b) for b in range(strs.count)] + [iid.get(b) for b in range(iid.count)]))
+    A, m = 5000, 3  # one state, slices far longer than the block
+    il = rng.integers(0, m, size=A).astype(np.int32)
+    fa = synth.FstArrays(1, m, 4, np.zeros(A, np.int32), np.zeros(A, np.int32), il,
+                         rng.integers(0, 4, size=A).astype(np.int32), (rng.random(A) * 4).astype(np.float32),
+                         np.zeros(1, np.float32), np.zeros(1, np.float32))
+    cases.append((fa, [rng.integers(0, m, size=n).astype(np.int32) for n in (1, 7, 30)]))
+    fa = synth.fig1_fst()
+    fa.num_isyms = 5  # symbols without arcs
+    cases.append((fa, [np.array(v, np.int32) for v in ([0, 1, 2], [3], [0, 4, 2])]))
+    for fa, xs in cases:
+        f, o = _fst(fa), oracle.Fst(fa)
+        f.set_plain_method(_lib.PLAIN_FRONTIER)
+        ref = [f.viterbi(x) for x in xs]
+        f.set_plain_method(_lib.PLAIN_BLOCK)
+        for x, r in zip(xs, ref):
+            s, p, ol, st = f.viterbi(x)
+            assert s == r[0] and np.array_equal(p, r[1]) and np.array_equal(ol, r[2]) and st == r[3]
+            check_string(f, o, x)
+    # repeatable bit for bit, and the calibration picks it on c1
+    fa, strs = synth.make_config("c1", strings=6)
+    f = _fst(fa)
+    f.set_plain_method(_lib.PLAIN_BLOCK)
+    la, ca, _ = f.forward_backward(strs.get(0))
+    lb, cb, _ = f.forward_backward(strs.get(0))
+    assert la == lb and np.array_equal(ca, cb)
+    f.autotune_plain(strs.ids, strs.offsets)
+    o = oracle.Fst(fa)
+    for b in range(strs.count):
+        check_string(f, o, strs.get(b))
+    # beyond the shared-memory limit the method is refused
+    big, _ = synth.make_config("c2", scale=0.2, strings=1)  # 10,000 states
+    assert big.num_states > _lib.BLOCK_MAX_STATES
+    with pytest.raises(_lib.FstError) as ei:
+        _fst(big).set_plain_method(_lib.PLAIN_BLOCK)
+    assert ei.value.code == _lib.UNSUPPORTED
