@@ -217,9 +217,17 @@ def source_hash():
     return h.hexdigest()[:12]
 
 
-def load_traffic():
-    """Per-pass DRAM bytes per algorithmic byte, measured by ncu on a small
-    run of the current kernels; None when the kernel sources changed since."""
+def acc_mode(line_or_args):
+    """'dense' or 'compact': the accumulator layout of a bench line or of the arguments."""
+    if isinstance(line_or_args, dict):
+        return "dense" if str(line_or_args.get("config", {}).get("accumulators", "")).startswith("dense") else "compact"
+    return "dense" if line_or_args.dense_acc else "compact"
+
+
+def load_traffic(mode):
+    """Per-pass DRAM bytes per algorithmic byte for accumulator layout
+    ``mode``, measured by ncu on a small run of the current kernels; None
+    when the kernel sources changed since (or that layout was not measured)."""
     try:
         with open(TRAFFIC_FILE) as fh:
             d = json.load(fh)
@@ -227,7 +235,7 @@ def load_traffic():
         return None
     if d.get("source_hash") != source_hash():
         return None
-    return d
+    return d.get("modes", {}).get(mode)
 
 
 def roofline(prof, live, peak, peak_src, traffic, stats=None, ids=None, persistent=()):
@@ -397,10 +405,20 @@ def ingest_traffic(csv_path, line_path):
         if tot > 0:
             passes[p] = {"dram_bytes": int(tot), "algorithmic_bytes": int(alg[p]),
                          "dram_per_algorithmic_byte": tot / alg[p]}
-    out = {"source_hash": source_hash(), "workload": line["config"]["workload"][:60],
-           "strings": line["config"]["strings"], "live_work": live, "passes": passes,
+    mode = acc_mode(line)
+    out = {"source_hash": source_hash(), "modes": {},
            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over every launch of one step of a small run "
-                   "(--cache-control none), per algorithmic byte of its live work; scaled by the live work"}
+                   "(--cache-control none), per algorithmic byte of its live work, by accumulator layout; "
+                   "scaled by the live work"}
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            old = json.load(fh)
+        if old.get("source_hash") == out["source_hash"]:
+            out["modes"].update(old.get("modes", {}))
+    except (OSError, ValueError):
+        pass
+    out["modes"][mode] = {"workload": line["config"]["workload"][:60], "strings": line["config"]["strings"],
+                          "live_work": live, "passes": passes}
     with open(TRAFFIC_FILE, "w") as fh:
         json.dump(out, fh, indent=1)
     print(json.dumps(out))
@@ -554,7 +572,7 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     live = {"entries": sum(x["entries"] for x in lws), "arcs": sum(x["arcs"] for x in lws)}
     peak, peak_src = load_peak()
     persistent = (("vit",) if plans_v[0].driver()[0] else ()) + (("fwd", "bwd") if plans_f[0].driver()[0] else ())
-    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(), stats, strs.ids, persistent)
+    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(acc_mode(args)), stats, strs.ids, persistent)
     performed = 3 * max(live["arcs"], 0)
     plan_bytes = sum(i["device_bytes"] for i in infos_v + infos_f)
     out["config"].update({
@@ -786,11 +804,13 @@ def bench_train(args, rank, world, dev, fa, strs, f, stats):
     the gradient is minus the expected counts), and an SGD update of the
     arc log-weights (written back to the FST by the next forward)."""
     import torch
+    from paper_1701_03038_gb300 import _lib
     from paper_1701_03038_gb300._lib import PLAN_SINGLE_WAVE
     from paper_1701_03038_gb300.autograd import LogZModule
     ids = torch.from_numpy(strs.ids).to(dev)
     off = torch.from_numpy(strs.offsets).to(dev)
-    plan = f.plan(ids, off, mem_budget=int(args.budget_gb * (1 << 30)), flags=PLAN_SINGLE_WAVE)
+    plan = f.plan(ids, off, mem_budget=int(args.budget_gb * (1 << 30)),
+                  flags=PLAN_SINGLE_WAVE | (_lib.PLAN_DENSE_ACC if args.dense_acc else 0))
     from paper_1701_03038_gb300 import _lib
     tuned = None
     if args.driver in ("persistent", "persistent-all"):
@@ -824,7 +844,7 @@ def bench_train(args, rank, world, dev, fa, strs, f, stats):
     plan.profile(False)
     live = plan.live_work()
     peak, peak_src = load_peak()
-    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(), stats, strs.ids,
+    rl, passes = roofline(prof, live, peak, peak_src, load_traffic(acc_mode(args)), stats, strs.ids,
                           ("fwd", "bwd") if plan.driver()[0] else ())
     out.update({"relaxations_performed_per_s": job_throughput(2 * max(live["arcs"], 0), world, ms / 1000.0),
                 "live_work": live, "roofline": rl, "passes": passes,

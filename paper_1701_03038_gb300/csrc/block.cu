@@ -10,8 +10,9 @@
 // read from L2, collisions on a destination go to shared-memory atomics,
 // and __syncthreads() separates the positions.
 //
-//   Viterbi  -- the packed (order-preserving score bits << 32 | ~arc id)
-//               atomicMax of Sec. 5.1 (lowest arc id on ties, as the
+//   Viterbi  -- the packed (order-preserving score bits << 32 | ~index)
+//               atomicMax of Sec. 5.1, the index that of the arc in its
+//               destination-ordered slice (lowest arc id on ties, as the
 //               frontier kernels), a backpointer {arc, source} per state
 //               and position in global memory, the backtrace by one thread;
 //   forward  -- two sweeps of the slice per position: the exact float64
@@ -80,50 +81,102 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return v;
 }
 
+// The first KR * BT arcs of a slice, KR per thread, are held in registers
+// for every sweep over the slice at a position; they are loaded one
+// position ahead, so the loads of t+1 are in flight while t is relaxed.
+// Arcs past them (slices longer than KR * BT) are read where they are used.
+constexpr int KR = 2;
+struct ArcRegs {
+  int4 r[KR];  // {source, destination, caller id (< 0: none), 0}
+  float th[KR];
+};
+__device__ __forceinline__ void load_arcs(ArcRegs& R, const int4* __restrict__ arcs,
+                                          const float* __restrict__ theta, const Slice& sl) {
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
+    const int64_t i = sl.i0 + k * BT + threadIdx.x;
+    R.r[k] = i < sl.i1 ? __ldg(arcs + i) : make_int4(0, 0, -1, 0);
+    R.th[k] = i < sl.i1 ? __ldg(theta + i) : 0.f;
+  }
+}
+__device__ __forceinline__ Slice slice_at(const int64_t* __restrict__ sym_win, const int32_t* __restrict__ ids,
+                                          int32_t n, int32_t t) {
+  return (t >= 1 && t <= n) ? slice_of(sym_win, __ldg(ids + t - 1)) : Slice{0, 0};
+}
+
 // ======================================================================
-// Viterbi (Alg. 1, Sec. 5.1).  Shared: key[Q] (packed best arc of each
-// state at t), v[Q] (float32 score of each state at t-1).  bp[(t-1) Q + q]
-// = {best arc, its source} of state q at position t.
+// Viterbi (Alg. 1, Sec. 5.1).  The slice records are the destination-
+// ordered ones, where the arcs into a state sit in caller-id order, so the
+// packed key carries the arc's index within the slice: the lowest index
+// into a destination is its lowest arc id.  Shared: key[Q] (packed best
+// arc into each state at t), v[Q] (float32 score of each state at t-1),
+// rec[KR BT] ({caller id, source} of the register arcs, for the readout).
+// bp[(t-1) Q + q] = {best arc, its source} of state q at position t.
 // ======================================================================
-__global__ void __launch_bounds__(BT, 1) k_block_viterbi(const int4* __restrict__ arcs, const float* __restrict__ theta,
-                                                      const int64_t* __restrict__ sym_win,
-                                                      const int32_t* __restrict__ ids, int32_t n, int32_t Q,
-                                                      const float* __restrict__ theta_s,
-                                                      const float* __restrict__ theta_f,
-                                                      const int32_t* __restrict__ src_by_id,
-                                                      const int32_t* __restrict__ olabel, int2* __restrict__ bp,
-                                                      float* __restrict__ score, int32_t* __restrict__ path,
-                                                      int32_t* __restrict__ olab, int32_t* __restrict__ status) {
+__global__ void __launch_bounds__(BT, 1) k_block_viterbi(const int4* __restrict__ arcs,
+                                                         const float* __restrict__ theta,
+                                                         const int64_t* __restrict__ sym_win,
+                                                         const int32_t* __restrict__ ids, int32_t n, int32_t Q,
+                                                         const float* __restrict__ theta_s,
+                                                         const float* __restrict__ theta_f,
+                                                         const int32_t* __restrict__ olabel, int2* __restrict__ bp,
+                                                         float* __restrict__ score, int32_t* __restrict__ path,
+                                                         int32_t* __restrict__ olab, int32_t* __restrict__ status) {
   extern __shared__ unsigned long long smem[];
   __shared__ unsigned long long red[BT / 32];
+  __shared__ int2 rec[KR * BT];
   unsigned long long* key = smem;
   float* v = (float*)(smem + Q);
   for (int32_t q = threadIdx.x; q < Q; q += BT) {
     key[q] = 0ull;
     v[q] = __ldg(theta_s + q);
   }
+  ArcRegs cur, nxt;
+  load_arcs(cur, arcs, theta, slice_at(sym_win, ids, n, 1));
   __syncthreads();
   for (int32_t t = 1; t <= n; ++t) {
-    const Slice sl = slice_of(sym_win, __ldg(ids + t - 1));
-    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
+    const Slice sl = slice_at(sym_win, ids, n, t);
+    load_arcs(nxt, arcs, theta, slice_at(sym_win, ids, n, t + 1));
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const int4 r = cur.r[k];
+      rec[k * BT + threadIdx.x] = make_int2(r.z, r.x);
+      if (r.z < 0) continue;  // padding, or past the slice
+      const float x = v[r.x];
+      if (x == neg_inf()) continue;
+      const float c = __fadd_rn(x, cur.th[k]);
+      if (c == neg_inf()) continue;
+      atomicMax(key + r.y, ((unsigned long long)fkey(c) << 32) | (unsigned long long)(~(uint32_t)(k * BT + threadIdx.x)));
+    }
+    for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
-      if (r.z < 0) continue;  // padding
+      if (r.z < 0) continue;
       const float x = v[r.x];
       if (x == neg_inf()) continue;
       const float c = __fadd_rn(x, __ldg(theta + i));
       if (c == neg_inf()) continue;
-      atomicMax(key + r.y, ((unsigned long long)fkey(c) << 32) | (unsigned long long)(~(uint32_t)r.z));
+      atomicMax(key + r.y, ((unsigned long long)fkey(c) << 32) | (unsigned long long)(~(uint32_t)(i - sl.i0)));
     }
     __syncthreads();
     int2* row = bp + (int64_t)(t - 1) * Q;
     for (int32_t q = threadIdx.x; q < Q; q += BT) {
       const unsigned long long k = key[q];
-      const int32_t id = k ? (int32_t)(~(uint32_t)k) : -1;
-      row[q] = make_int2(id, id >= 0 ? __ldg(src_by_id + id) : -1);
+      int2 e = make_int2(-1, -1);
+      if (k) {
+        const int64_t j = (int64_t)(~(uint32_t)k);
+        if (j < KR * BT) {
+          e = rec[j];
+        } else {
+          const int4 r = __ldg(arcs + sl.i0 + j);
+          e = make_int2(r.z, r.x);
+        }
+      }
+      row[q] = e;
       v[q] = k ? fkey_inv((uint32_t)(k >> 32)) : neg_inf();
       key[q] = 0ull;
     }
     __syncthreads();
+    cur = nxt;
   }
   // the best final state (lowest state id on ties)
   unsigned long long best = 0ull;
@@ -155,12 +208,23 @@ __device__ __forceinline__ double state_value(unsigned long long m, unsigned lon
   return m ? fix_log_sum64(dkey_inv(m), s) : -INFINITY;
 }
 
+// The compensated float32 sum of one arc's posterior: this thread alone
+// writes arc id (the same slice position, whenever its symbol recurs).
+__device__ __forceinline__ void add_post(float* __restrict__ cnt, float* __restrict__ comp, int32_t id, float g,
+                                         float s0, float cp) {
+  const float y = __fsub_rn(g, cp);
+  const float s1 = __fadd_rn(s0, y);
+  comp[id] = __fsub_rn(__fsub_rn(s1, s0), y);
+  cnt[id] = s1;
+}
+
 __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arcs, const float* __restrict__ theta,
-                                                 const int64_t* __restrict__ sym_win, const int32_t* __restrict__ ids,
-                                                 int32_t n, int32_t Q, const float* __restrict__ theta_s,
-                                                 const float* __restrict__ theta_f, double* __restrict__ alpha,
-                                                 float* __restrict__ cnt, float* __restrict__ comp,
-                                                 double* __restrict__ logz, int32_t* __restrict__ status) {
+                                                    const int64_t* __restrict__ sym_win,
+                                                    const int32_t* __restrict__ ids, int32_t n, int32_t Q,
+                                                    const float* __restrict__ theta_s,
+                                                    const float* __restrict__ theta_f, double* __restrict__ alpha,
+                                                    float* __restrict__ cnt, float* __restrict__ comp,
+                                                    double* __restrict__ logz, int32_t* __restrict__ status) {
   extern __shared__ unsigned long long smem[];
   __shared__ double redd[BT / 32];
   __shared__ unsigned long long redk[BT / 32];
@@ -172,18 +236,33 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
     a[q] = (double)__ldg(theta_s + q);
     alpha[q] = a[q];
   }
+  ArcRegs cur, nxt;
+  load_arcs(cur, arcs, theta, slice_at(sym_win, ids, n, 1));
   __syncthreads();
   // forward
   for (int32_t t = 1; t <= n; ++t) {
-    const Slice sl = slice_of(sym_win, __ldg(ids + t - 1));
-    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
+    const Slice sl = slice_at(sym_win, ids, n, t);
+    load_arcs(nxt, arcs, theta, slice_at(sym_win, ids, n, t + 1));
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      if (cur.r[k].z < 0) continue;
+      const double x = a[cur.r[k].x] + (double)cur.th[k];
+      if (x != -INFINITY) atomicMax(mx + cur.r[k].y, dkey(x));
+    }
+    for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
       if (r.z < 0) continue;
       const double x = a[r.x] + (double)__ldg(theta + i);
       if (x != -INFINITY) atomicMax(mx + r.y, dkey(x));
     }
     __syncthreads();
-    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      if (cur.r[k].z < 0) continue;
+      const double x = a[cur.r[k].x] + (double)cur.th[k];
+      if (x != -INFINITY) atomicAdd(sm + cur.r[k].y, fix_exp64(x, dkey_inv(mx[cur.r[k].y])));
+    }
+    for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
       if (r.z < 0) continue;
       const double x = a[r.x] + (double)__ldg(theta + i);
@@ -197,6 +276,7 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
       mx[q] = sm[q] = 0ull;
     }
     __syncthreads();
+    cur = nxt;
   }
   // log Z = log sum_q exp(alpha_n[q] + theta_f[q]): exact maximum, then a
   // float64 sum in a fixed order
@@ -225,34 +305,55 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
   // backward: beta_n = theta_f
   __syncthreads();
   for (int32_t q = threadIdx.x; q < Q; q += BT) a[q] = (double)__ldg(theta_f + q);
+  load_arcs(cur, arcs, theta, slice_at(sym_win, ids, n, n));
   __syncthreads();
   for (int32_t t = n; t >= 1; --t) {
-    const Slice sl = slice_of(sym_win, __ldg(ids + t - 1));
+    const Slice sl = slice_at(sym_win, ids, n, t);
     const double* al = alpha + (int64_t)(t - 1) * Q;
-    // the maxima into the sources, and each arc's posterior
-    // exp(alpha_{t-1}[src] + theta + beta_t[dst] - log Z)
-    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
+    load_arcs(nxt, arcs, theta, slice_at(sym_win, ids, n, t - 1));
+    // alpha_{t-1} of each register arc's source and its running count,
+    // read now and used after the first sweep
+    double alr[KR];
+    float c0[KR], c1[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const bool ok = cur.r[k].z >= 0;
+      alr[k] = ok ? al[cur.r[k].x] : -INFINITY;
+      c0[k] = ok ? cnt[cur.r[k].z] : 0.f;
+      c1[k] = ok ? comp[cur.r[k].z] : 0.f;
+    }
+    // the maxima into the sources
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      if (cur.r[k].z < 0) continue;
+      const double u = (double)cur.th[k] + a[cur.r[k].y];
+      if (u != -INFINITY) atomicMax(mx + cur.r[k].x, dkey(u));
+    }
+    for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
+      const int4 r = __ldg(arcs + i);
+      if (r.z < 0) continue;
+      const double u = (double)__ldg(theta + i) + a[r.y];
+      if (u != -INFINITY) atomicMax(mx + r.x, dkey(u));
+    }
+    __syncthreads();
+    // the sums, and each arc's posterior exp(alpha_{t-1}[src] + theta +
+    // beta_t[dst] - log Z)
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      if (cur.r[k].z < 0) continue;
+      const double u = (double)cur.th[k] + a[cur.r[k].y];
+      if (u == -INFINITY) continue;
+      atomicAdd(sm + cur.r[k].x, fix_exp64(u, dkey_inv(mx[cur.r[k].x])));
+      if (alr[k] != -INFINITY) add_post(cnt, comp, cur.r[k].z, (float)exp((alr[k] + u) - lz), c0[k], c1[k]);
+    }
+    for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
       if (r.z < 0) continue;
       const double u = (double)__ldg(theta + i) + a[r.y];
       if (u == -INFINITY) continue;
-      atomicMax(mx + r.x, dkey(u));
+      atomicAdd(sm + r.x, fix_exp64(u, dkey_inv(mx[r.x])));
       const double x = al[r.x];
-      if (x == -INFINITY) continue;
-      const float g = (float)exp((x + u) - lz);
-      // compensated float32 sum: this thread alone writes arc r.z
-      const float s0 = cnt[r.z], cp = comp[r.z];
-      const float y = __fsub_rn(g, cp);
-      const float s1 = __fadd_rn(s0, y);
-      comp[r.z] = __fsub_rn(__fsub_rn(s1, s0), y);
-      cnt[r.z] = s1;
-    }
-    __syncthreads();
-    for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += BT) {
-      const int4 r = __ldg(arcs + i);
-      if (r.z < 0) continue;
-      const double u = (double)__ldg(theta + i) + a[r.y];
-      if (u != -INFINITY) atomicAdd(sm + r.x, fix_exp64(u, dkey_inv(mx[r.x])));
+      if (x != -INFINITY) add_post(cnt, comp, r.z, (float)exp((x + u) - lz), cnt[r.z], comp[r.z]);
     }
     __syncthreads();
     for (int32_t q = threadIdx.x; q < Q; q += BT) {
@@ -260,6 +361,7 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
       mx[q] = sm[q] = 0ull;
     }
     __syncthreads();
+    cur = nxt;
   }
 }
 
@@ -306,9 +408,14 @@ int viterbi_block_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score
   }
   int rc;
   cudaStream_t s = 0;
+  // the destination-ordered records, whichever order the slice kernels use
   SliceView sv;
-  if ((rc = slice_view(f, s, &sv))) return rc;
-  const Layout& L = f->slice_order == FST_SLICE_BY_SOURCE ? f->bwd : f->fwd;
+  const int32_t order = f->slice_order;
+  f->slice_order = FST_SLICE_BY_DESTINATION;
+  rc = slice_view(f, s, &sv);
+  f->slice_order = order;
+  if (rc) return rc;
+  const Layout& L = f->fwd;
   // block_ids: the string, the path, the output labels, then score and status
   if ((rc = block_reserve(f, n, (int64_t)std::max(n, 1) * f->Q))) return rc;
   const int64_t n1 = std::max(n, 1);
@@ -321,8 +428,8 @@ int viterbi_block_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score
   const size_t smem = (size_t)f->Q * 12;
   if ((rc = block_launch_setup(k_block_viterbi, smem))) return rc;
   k_block_viterbi<<<1, BT, smem, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, f->theta_s, f->theta_f,
-                                      f->src_by_id, f->olabel, (int2*)f->block_ws, d_score, d_path,
-                                      olabels ? d_olab : nullptr, d_status);
+                                      f->olabel, (int2*)f->block_ws, d_score, d_path, olabels ? d_olab : nullptr,
+                                      d_status);
   FST_CUDA(cudaGetLastError());
   FST_CUDA(cudaMemcpy(best_score, d_score, 4, cudaMemcpyDeviceToHost));
   FST_CUDA(cudaMemcpy(status, d_status, 4, cudaMemcpyDeviceToHost));
