@@ -88,8 +88,9 @@ def parse_args(argv=None):
     ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
     ap.add_argument("--parts-vit", type=int, default=2, help="stream-parallel parts of the Viterbi plan")
     ap.add_argument("--parts-fb", type=int, default=8, help="stream-parallel parts of the forward-backward plan")
-    ap.add_argument("--dense-acc", action="store_true",
-                    help="dense per-string accumulators (FST_PLAN_DENSE_ACC) instead of hash tables")
+    ap.add_argument("--acc", default="dense", choices=["dense", "compact"],
+                    help="accumulators of the batched plans: dense per-string arrays (FST_PLAN_DENSE_ACC, the "
+                         "faster) or the library's default hash tables (a third of the memory)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -101,7 +102,9 @@ def parse_args(argv=None):
                          "other; autotune: each plan's driver and grid chosen by fst_plan_autotune")
     ap.add_argument("--ingest-traffic", nargs=2, metavar=("NCU_CSV", "BENCH_JSON"),
                     help="write profiles/traffic.json from an ncu launch list of a small run and that run's line")
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    args.dense_acc = args.acc == "dense"
+    return args
 
 
 # ---------------------------------------------------------------- clocks

@@ -32,7 +32,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <vector>
 
 #include "fst_internal.cuh"
 
@@ -218,13 +221,16 @@ __device__ __forceinline__ void add_post(float* __restrict__ cnt, float* __restr
   cnt[id] = s1;
 }
 
+// cnt / comp [A]: the compensated sum (zeroed here); out [A]: the
+// posteriors cnt - comp (written at the end; nullptr: no posteriors).
 __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arcs, const float* __restrict__ theta,
                                                     const int64_t* __restrict__ sym_win,
                                                     const int32_t* __restrict__ ids, int32_t n, int32_t Q,
-                                                    const float* __restrict__ theta_s,
+                                                    int64_t A, const float* __restrict__ theta_s,
                                                     const float* __restrict__ theta_f, double* __restrict__ alpha,
                                                     float* __restrict__ cnt, float* __restrict__ comp,
-                                                    double* __restrict__ logz, int32_t* __restrict__ status) {
+                                                    float* __restrict__ out, double* __restrict__ logz,
+                                                    int32_t* __restrict__ status) {
   extern __shared__ unsigned long long smem[];
   __shared__ double redd[BT / 32];
   __shared__ unsigned long long redk[BT / 32];
@@ -236,6 +242,8 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
     a[q] = (double)__ldg(theta_s + q);
     alpha[q] = a[q];
   }
+  if (out)
+    for (int64_t i = threadIdx.x; i < A; i += BT) cnt[i] = comp[i] = 0.f;
   ArcRegs cur, nxt;
   load_arcs(cur, arcs, theta, slice_at(sym_win, ids, n, 1));
   __syncthreads();
@@ -301,7 +309,12 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
     *logz = lz;
     *status = mk ? FST_OK : FST_ERR_NO_PATH;
   }
-  if (!cnt || !mk) return;  // block-uniform
+  if (!out) return;  // block-uniform
+  if (!mk) {  // no path: no posteriors
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < A; i += BT) out[i] = 0.f;
+    return;
+  }
   // backward: beta_n = theta_f
   __syncthreads();
   for (int32_t q = threadIdx.x; q < Q; q += BT) a[q] = (double)__ldg(theta_f + q);
@@ -363,6 +376,10 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
     __syncthreads();
     cur = nxt;
   }
+  // every count was last written by the thread that reads it back here or
+  // by another thread before one of the barriers above
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < A; i += BT) out[i] = __fsub_rn(cnt[i], comp[i]);
 }
 
 }  // namespace
@@ -394,9 +411,17 @@ static int block_reserve(fst_s* f, int32_t n, int64_t words) {
   return FST_OK;
 }
 
+// The dynamic shared memory a kernel may take, set once per device.
 template <class K>
-static int block_launch_setup(K kernel, size_t smem) {
-  FST_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+static int block_launch_setup(K kernel, int slot, size_t smem) {
+  static int done[2][64];
+  int dev = 0;
+  FST_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && done[slot][dev]) return FST_OK;
+  FST_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)BLOCK_QMAX * 24)));
+  if (dev >= 0 && dev < 64) done[slot][dev] = 1;
+  (void)smem;
   return FST_OK;
 }
 
@@ -416,7 +441,8 @@ int viterbi_block_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score
   f->slice_order = order;
   if (rc) return rc;
   const Layout& L = f->fwd;
-  // block_ids: the string, the path, the output labels, then score and status
+  // block_ids: the string, then the path, the output labels, the score and
+  // the status, read back with one copy
   if ((rc = block_reserve(f, n, (int64_t)std::max(n, 1) * f->Q))) return rc;
   const int64_t n1 = std::max(n, 1);
   int32_t* d_ids = f->block_ids;
@@ -426,22 +452,23 @@ int viterbi_block_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score
   int32_t* d_status = d_ids + 3 * n1 + 1;
   if (n > 0) FST_CUDA(cudaMemcpyAsync(d_ids, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   const size_t smem = (size_t)f->Q * 12;
-  if ((rc = block_launch_setup(k_block_viterbi, smem))) return rc;
+  if ((rc = block_launch_setup(k_block_viterbi, 0, smem))) return rc;
   k_block_viterbi<<<1, BT, smem, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, f->theta_s, f->theta_f,
                                       f->olabel, (int2*)f->block_ws, d_score, d_path, olabels ? d_olab : nullptr,
                                       d_status);
   FST_CUDA(cudaGetLastError());
-  FST_CUDA(cudaMemcpy(best_score, d_score, 4, cudaMemcpyDeviceToHost));
-  FST_CUDA(cudaMemcpy(status, d_status, 4, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> h((size_t)(2 * n1 + 2));
+  FST_CUDA(cudaMemcpy(h.data(), d_path, h.size() * 4, cudaMemcpyDeviceToHost));
+  memcpy(best_score, &h[2 * n1], 4);
+  *status = h[2 * n1 + 1];
   if (n > 0) {
-    FST_CUDA(cudaMemcpy(arc_path, d_path, (size_t)n * 4, cudaMemcpyDeviceToHost));
-    if (olabels) FST_CUDA(cudaMemcpy(olabels, d_olab, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    memcpy(arc_path, h.data(), (size_t)n * 4);
+    if (olabels) memcpy(olabels, h.data() + n1, (size_t)n * 4);
   }
   return FST_OK;
 }
 
-int fb_block_run(fst_s* f, const int32_t* ids, int32_t n, float* d_cnt, float* d_comp, double* log_z,
-                 int32_t* status) {
+int fb_block_run(fst_s* f, const int32_t* ids, int32_t n, float* arc_posteriors, double* log_z, int32_t* status) {
   if (!block_fits(f)) {
     set_error("the one-block kernels hold at most %d states (this FST has %d)", BLOCK_QMAX, f->Q);
     return FST_ERR_UNSUPPORTED;
@@ -449,23 +476,44 @@ int fb_block_run(fst_s* f, const int32_t* ids, int32_t n, float* d_cnt, float* d
   int rc;
   cudaStream_t s = 0;
   SliceView sv;
-  if ((rc = slice_view(f, s, &sv))) return rc;
-  const Layout& L = f->slice_order == FST_SLICE_BY_SOURCE ? f->bwd : f->fwd;
-  // block_ws: log Z, then the forward values; block_ids: the string, then
-  // the status
-  if ((rc = block_reserve(f, n, ((int64_t)n + 1) * f->Q + 1))) return rc;
-  const int64_t n1 = std::max(n, 1);
+  const int32_t order = f->slice_order;
+  f->slice_order = FST_SLICE_BY_DESTINATION;
+  rc = slice_view(f, s, &sv);
+  f->slice_order = order;
+  if (rc) return rc;
+  const Layout& L = f->fwd;
+  // block_ws: the posteriors [A floats], log Z and the status (read back
+  // with one copy), the compensated pair [2 A floats], then the forward
+  // values [(n + 1) Q]
+  const int64_t A = f->A;
+  const int64_t head = (A + 1) / 2 + 2;  // 8-byte words before the pair
+  const int64_t pair = A;                // 2 A floats
+  if ((rc = block_reserve(f, n, head + pair + ((int64_t)n + 1) * f->Q))) return rc;
   int32_t* d_ids = f->block_ids;
-  int32_t* d_status = d_ids + 3 * n1 + 1;
-  double* d_logz = (double*)f->block_ws;
+  float* d_out = (float*)f->block_ws;
+  double* d_logz = (double*)(f->block_ws + head - 2);
+  int32_t* d_status = (int32_t*)(f->block_ws + head - 1);
+  float* d_cnt = (float*)(f->block_ws + head);
+  float* d_comp = d_cnt + A;
+  double* d_alpha = (double*)(f->block_ws + head + pair);
   if (n > 0) FST_CUDA(cudaMemcpyAsync(d_ids, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   const size_t smem = (size_t)f->Q * 24;
-  if ((rc = block_launch_setup(k_block_fb, smem))) return rc;
-  k_block_fb<<<1, BT, smem, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, f->theta_s, f->theta_f,
-                                 (double*)f->block_ws + 1, d_cnt, d_comp, d_logz, d_status);
+  if ((rc = block_launch_setup(k_block_fb, 1, smem))) return rc;
+  k_block_fb<<<1, BT, smem, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, A, f->theta_s, f->theta_f, d_alpha,
+                                 d_cnt, d_comp, arc_posteriors ? d_out : nullptr, d_logz, d_status);
   FST_CUDA(cudaGetLastError());
-  FST_CUDA(cudaMemcpy(log_z, d_logz, 8, cudaMemcpyDeviceToHost));
-  FST_CUDA(cudaMemcpy(status, d_status, 4, cudaMemcpyDeviceToHost));
+  if (arc_posteriors) {
+    std::vector<unsigned long long> h((size_t)head);
+    FST_CUDA(cudaMemcpy(h.data(), f->block_ws, (size_t)head * 8, cudaMemcpyDeviceToHost));
+    memcpy(arc_posteriors, h.data(), (size_t)A * 4);
+    memcpy(log_z, &h[head - 2], 8);
+    memcpy(status, &h[head - 1], 4);
+  } else {
+    unsigned long long h[2];
+    FST_CUDA(cudaMemcpy(h, f->block_ws + head - 2, 16, cudaMemcpyDeviceToHost));
+    memcpy(log_z, &h[0], 8);
+    memcpy(status, &h[1], 4);
+  }
   return FST_OK;
 }
 

@@ -683,6 +683,17 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   }
   DevGuard g(f->device);
   int rc;
+  if (plain_uses_block(f)) {
+    for (int32_t i = 0; i < n; ++i)
+      if (ids[i] < 0 || ids[i] >= f->m) {
+        set_error("symbol %d at position %d is outside [0, %d)", ids[i], i, f->m);
+        return FST_ERR_INVALID_ARG;
+      }
+    int32_t st = FST_OK;
+    if ((rc = fb_block_run(f, ids, n, arc_posteriors, log_z, &st))) return rc;
+    if (st != FST_OK) set_error("no accepting path");
+    return st;
+  }
   if ((rc = plain_init(f))) return rc;
   cudaStream_t s = 0;
   if ((rc = plain_tokens(f, ids, n, s))) return rc;
@@ -690,24 +701,6 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   if (arc_posteriors && !w->cnt) {
     if ((rc = dalloc(&w->cnt, f->A)) || (rc = dalloc(&w->comp, f->A)) || (rc = dalloc(&w->counts_out, f->A)))
       return rc;
-  }
-  if (plain_uses_block(f)) {
-    if (arc_posteriors) {
-      FST_CUDA(cudaMemsetAsync(w->cnt, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
-      FST_CUDA(cudaMemsetAsync(w->comp, 0, (size_t)std::max<int64_t>(f->A, 1) * 4, s));
-    }
-    int32_t st = FST_OK;
-    if ((rc = fb_block_run(f, ids, n, arc_posteriors ? w->cnt : nullptr, arc_posteriors ? w->comp : nullptr, log_z,
-                           &st)))
-      return rc;
-    if (arc_posteriors) {
-      const CountView C{0, w->cnt, w->comp, nullptr};
-      if ((rc = launch_counts_out(f->A, C, w->counts_out, s))) return rc;
-      if (f->A > 0)
-        FST_CUDA(cudaMemcpy(arc_posteriors, w->counts_out, (size_t)f->A * 4, cudaMemcpyDeviceToHost));
-    }
-    if (st != FST_OK) set_error("no accepting path");
-    return st;
   }
   const LayoutView L = view_of(f->bwd);
   const TokenView T = plain_tokview(w);

@@ -281,15 +281,14 @@ int viterbi_slice_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score
                       int32_t* olabels);
 
 // One string in one thread block (block.cu), for FSTs of at most
-// BLOCK_QMAX states: Viterbi (host outputs, olabels may be NULL; *status
-// FST_OK or FST_ERR_NO_PATH) and forward-backward (the posteriors added to
-// the compensated float32 pair d_cnt / d_comp when not NULL; host log Z).
+// BLOCK_QMAX states, host outputs: Viterbi (olabels may be NULL; *status
+// FST_OK or FST_ERR_NO_PATH) and forward-backward (arc_posteriors [A] or
+// NULL, log Z, *status).
 constexpr int32_t BLOCK_QMAX = FST_BLOCK_MAX_STATES;
 bool block_fits(const fst_s* f);
 int viterbi_block_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score, int32_t* arc_path,
                       int32_t* olabels, int32_t* status);
-int fb_block_run(fst_s* f, const int32_t* ids, int32_t n, float* d_cnt, float* d_comp, double* log_z,
-                 int32_t* status);
+int fb_block_run(fst_s* f, const int32_t* ids, int32_t n, float* arc_posteriors, double* log_z, int32_t* status);
 
 // Input label, destination and log-weight of every arc by caller id (any
 // output may be NULL; train.cu).
