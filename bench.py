@@ -465,10 +465,14 @@ def timed(run_step, args, world, dev, clocks):
     torch.cuda.synchronize()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # an NVTX range around the timed steps: an ncu launch list of exactly
+    # them is `ncu --nvtx --nvtx-include "timed_steps/" ...`
+    torch.cuda.nvtx.range_push("timed_steps")
     ev0.record()
     for _ in range(args.steps):
         run_step()
     ev1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier(world)
