@@ -254,6 +254,16 @@ FST_API int fst_forward_backward_batch(fst_t* fst, const int32_t* d_ids, const i
  * batch whose per-string storage exceeds it runs in several waves. */
 FST_API int fst_set_batch_budget(fst_t* fst, int64_t mem_budget_bytes);
 
+/* Plans of fst_viterbi_batch and fst_forward_backward_batch: parts_viterbi
+ * and parts_fb stream-parallel parts (FST_PLAN_PARTS; 0 = by batch size:
+ * one Viterbi part per 2,048 strings, at most 2, one forward-backward part
+ * per 512 strings, at most 8) and the accumulator layout (-1 = dense when
+ * the dense accumulators and the live pool fit the batch budget in one
+ * wave, else compact; 0 = compact; 1 = FST_PLAN_DENSE_ACC).  The default is
+ * 0, 0, -1.  A batch call keeps its plan's device storage for the next call
+ * of the same kind (part by part). */
+FST_API int fst_set_batch_plan(fst_t* fst, int32_t parts_viterbi, int32_t parts_fb, int32_t layout);
+
 /* A plan holds everything a batch needs on the device: the token lists of
  * every position (strings sorted by length), the accumulators, the live
  * pool of every position (states, values, backpointers or arcs) and the

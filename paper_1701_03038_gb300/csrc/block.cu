@@ -319,54 +319,64 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
   __syncthreads();
   for (int32_t q = threadIdx.x; q < Q; q += BT) a[q] = (double)__ldg(theta_f + q);
   load_arcs(cur, arcs, theta, slice_at(sym_win, ids, n, n));
+  // alpha_{t-1} of each register arc's source, read one position ahead
+  double alr[KR], nalr[KR];
+#pragma unroll
+  for (int k = 0; k < KR; ++k) alr[k] = (n >= 1 && cur.r[k].z >= 0) ? alpha[(int64_t)(n - 1) * Q + cur.r[k].x] : -INFINITY;
   __syncthreads();
   for (int32_t t = n; t >= 1; --t) {
     const Slice sl = slice_at(sym_win, ids, n, t);
     const double* al = alpha + (int64_t)(t - 1) * Q;
     load_arcs(nxt, arcs, theta, slice_at(sym_win, ids, n, t - 1));
-    // alpha_{t-1} of each register arc's source and its running count,
-    // read now and used after the first sweep
-    double alr[KR];
+    // each register arc's running count, read now and used after the first
+    // sweep
     float c0[KR], c1[KR];
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
       const bool ok = cur.r[k].z >= 0;
-      alr[k] = ok ? al[cur.r[k].x] : -INFINITY;
       c0[k] = ok ? cnt[cur.r[k].z] : 0.f;
       c1[k] = ok ? comp[cur.r[k].z] : 0.f;
     }
-    // the maxima into the sources
+    // the maxima into the sources.  Only sources live in the forward pass
+    // (alpha_{t-1} > -inf) are reduced: a dead state's beta takes part in
+    // no posterior (no arc from a live state reaches it), and skipping it
+    // keeps the float64 exponentials and logarithms to the live arcs
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
-      if (cur.r[k].z < 0) continue;
+      if (cur.r[k].z < 0 || alr[k] == -INFINITY) continue;
       const double u = (double)cur.th[k] + a[cur.r[k].y];
       if (u != -INFINITY) atomicMax(mx + cur.r[k].x, dkey(u));
     }
     for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
-      if (r.z < 0) continue;
+      if (r.z < 0 || al[r.x] == -INFINITY) continue;
       const double u = (double)__ldg(theta + i) + a[r.y];
       if (u != -INFINITY) atomicMax(mx + r.x, dkey(u));
     }
     __syncthreads();
+    // the next position's alpha_{t-2} values, its arcs having arrived
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+      nalr[k] = (t >= 2 && nxt.r[k].z >= 0) ? alpha[(int64_t)(t - 2) * Q + nxt.r[k].x] : -INFINITY;
     // the sums, and each arc's posterior exp(alpha_{t-1}[src] + theta +
     // beta_t[dst] - log Z)
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
-      if (cur.r[k].z < 0) continue;
+      if (cur.r[k].z < 0 || alr[k] == -INFINITY) continue;
       const double u = (double)cur.th[k] + a[cur.r[k].y];
       if (u == -INFINITY) continue;
       atomicAdd(sm + cur.r[k].x, fix_exp64(u, dkey_inv(mx[cur.r[k].x])));
-      if (alr[k] != -INFINITY) add_post(cnt, comp, cur.r[k].z, (float)exp((alr[k] + u) - lz), c0[k], c1[k]);
+      add_post(cnt, comp, cur.r[k].z, (float)exp((alr[k] + u) - lz), c0[k], c1[k]);
     }
     for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
       if (r.z < 0) continue;
+      const double x = al[r.x];
+      if (x == -INFINITY) continue;
       const double u = (double)__ldg(theta + i) + a[r.y];
       if (u == -INFINITY) continue;
       atomicAdd(sm + r.x, fix_exp64(u, dkey_inv(mx[r.x])));
-      const double x = al[r.x];
-      if (x != -INFINITY) add_post(cnt, comp, r.z, (float)exp((x + u) - lz), cnt[r.z], comp[r.z]);
+      add_post(cnt, comp, r.z, (float)exp((x + u) - lz), cnt[r.z], comp[r.z]);
     }
     __syncthreads();
     for (int32_t q = threadIdx.x; q < Q; q += BT) {
@@ -375,6 +385,8 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
     }
     __syncthreads();
     cur = nxt;
+#pragma unroll
+    for (int k = 0; k < KR; ++k) alr[k] = nalr[k];
   }
   // every count was last written by the thread that reads it back here or
   // by another thread before one of the barriers above

@@ -78,6 +78,23 @@ struct Wave {
 
 }  // namespace
 
+// The storage budget of a plan created with none: a quarter of the device
+// memory free now, at most 32 GiB and at least 256 MiB.
+int64_t default_budget() {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    (void)cudaGetLastError();
+    free_b = 0;
+  }
+  return std::max<int64_t>((int64_t)256 << 20, std::min<int64_t>((int64_t)32 << 30, (int64_t)(free_b / 4)));
+}
+
+// Dense accumulator bytes per string of a plan (forward-backward and/or
+// Viterbi), and the other per-string and per-token storage.
+int64_t dense_bytes_per_string(const fst_s* f, bool fb, bool vit) {
+  return (int64_t)f->Q * ((fb ? 48 : 16) + (vit ? 8 : 0));
+}
+
 // The device storage of a plan (everything but the per-wave token tables).
 #define PLAN_STORAGE(X)                                                                                          \
   X(acc) X(beta) X(vmap) X(stage) X(stage_b) X(scnt) X(pool_q) X(pool_x) X(pool_n) X(pool_v) X(pool_base)          \
@@ -473,7 +490,13 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
 // accumulators (and the expected start and final states) are the parent's,
 // shared by the parts (their float64 atomics add up across parts).
 static int plan_create_parts(fst_t* f, const int32_t* d_ids, const std::vector<int64_t>& h_off, int32_t B,
-                             int64_t budget, int32_t flags, cudaStream_t s, int32_t nparts, fst_plan_t** out) {
+                             int64_t budget, int32_t flags, cudaStream_t s, int32_t nparts, fst_plan_s* donor,
+                             fst_plan_t** out) {
+  // an earlier plan of as many parts lends each part's storage to the new
+  // part of the same index, and its shared count accumulators
+  std::unique_ptr<fst_plan_s> donor_owner(donor);
+  if (donor && (int32_t)donor->parts.size() != nparts) donor_owner.reset();
+  donor = donor_owner.get();
   std::unique_ptr<fst_plan_s> P(new fst_plan_s());
   P->fst = f;
   P->B = B;
@@ -497,10 +520,12 @@ static int plan_create_parts(fst_t* f, const int32_t* d_ids, const std::vector<i
     if ((rc = dalloc(&d_off, (int64_t)off.size()))) return rc;
     cudaError_t e = cudaMemcpy(d_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice);
     fst_plan_t* sub = nullptr;
+    fst_plan_s* part_donor = nullptr;
+    if (donor) std::swap(part_donor, donor->parts[i]);
     rc = e == cudaSuccess ? plan_create(f, d_ids ? d_ids + h_off[b0] : nullptr, d_off, b1 - b0,
                                         budget > 0 ? std::max<int64_t>(budget / nparts, 1) : 0, flags & 0xff,
-                                        (void*)s, nullptr, &sub)
-                          : cuda_fail(e, "part offsets");
+                                        (void*)s, part_donor, &sub)
+                          : (delete part_donor, cuda_fail(e, "part offsets"));
     dfree(d_off);
     if (rc) return rc;
     P->parts.push_back(sub);
@@ -511,7 +536,22 @@ static int plan_create_parts(fst_t* f, const int32_t* d_ids, const std::vector<i
     P->max_len = std::max(P->max_len, sub->max_len);
     b0 = b1;
   }
-  if (P->want_fb) {
+  if (P->want_fb && donor && donor->want_fb && donor->cnt64 && donor->fst == f) {
+    P->cnt64 = donor->cnt64;
+    P->start64 = donor->start64;
+    P->final64 = donor->final64;
+    donor->cnt64 = donor->start64 = donor->final64 = nullptr;
+    P->bytes += (int64_t)(f->A + 2 * (int64_t)f->Q) * 8;
+    for (fst_plan_s* q : P->parts) {
+      dfree(q->cnt64);
+      dfree(q->start64);
+      dfree(q->final64);
+      q->cnt64 = P->cnt64;
+      q->start64 = P->start64;
+      q->final64 = P->final64;
+      q->borrowed_counts = true;
+    }
+  } else if (P->want_fb) {
     if ((rc = alloc_track(P.get(), &P->cnt64, f->A)) || (rc = alloc_track(P.get(), &P->start64, f->Q)) ||
         (rc = alloc_track(P.get(), &P->final64, f->Q)))
       return rc;
@@ -567,7 +607,8 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
   if (N >= ((int64_t)1 << 31)) { set_error("too many tokens"); return FST_ERR_UNSUPPORTED; }
   if (N > 0 && !d_ids) { set_error("ids is NULL"); return FST_ERR_INVALID_ARG; }
   const int32_t nparts = std::min<int32_t>((flags >> 8) & 0xff, std::max(B, 1));
-  if (nparts > 1) return plan_create_parts(f, d_ids, h_off, B, mem_budget_bytes, flags, s, nparts, out);
+  if (nparts > 1) return plan_create_parts(f, d_ids, h_off, B, mem_budget_bytes, flags, s, nparts, donor_owner.release(), out);
+  if (donor && !donor->parts.empty()) donor_owner.reset();  // a parts plan lends nothing to a single plan
   fst_plan_s* P = new fst_plan_s();
   P->fst = f;
   P->B = B;
@@ -605,22 +646,13 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
     // waves: consecutive strings whose memory fits the budget.  Default: a
     // quarter of the device memory free now, at most 32 GiB and at least
     // 256 MiB (the GPU may be shared; fst_set_batch_budget raises it)
-    int64_t budget = mem_budget_bytes;
-    if (budget <= 0) {
-      size_t free_b = 0, total_b = 0;
-      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-        (void)cudaGetLastError();
-        free_b = 0;
-      }
-      budget = std::max<int64_t>((int64_t)256 << 20, std::min<int64_t>((int64_t)32 << 30, (int64_t)(free_b / 4)));
-    }
+    const int64_t budget = mem_budget_bytes > 0 ? mem_budget_bytes : default_budget();
     // dense accumulators: 2 x 8 bytes per state (Viterbi), or 2 x 16 for
     // the forward sums and maxima plus 2 x 8 for the backward values;
     // Viterbi also maps states to pool entries, 2 x 4 bytes.  Compact ones
     // do not grow with the strings.
     P->compact = !(flags & FST_PLAN_DENSE_ACC);
-    const int64_t per_string =
-        (P->compact ? 0 : (int64_t)f->Q * ((P->want_fb ? 48 : 16) + (P->want_vit ? 8 : 0))) + 64;
+    const int64_t per_string = (P->compact ? 0 : dense_bytes_per_string(f, P->want_fb, P->want_vit)) + 64;
     const int64_t per_token = TOKEN_BYTES + POOL_PER_TOKEN * 20;
     int32_t b0 = 0;
     int64_t acc = 0;
@@ -960,12 +992,54 @@ static void put_cached(fst_t* f, int kind, fst_plan_s* p) {
   delete old;
 }
 
+// Plan flags of a batch call (kind 0: Viterbi, 1: forward-backward): the
+// handle's setting (fst_set_batch_plan) or, by default, stream-parallel
+// parts by batch size (one Viterbi part per 2,048 strings, at most 2; one
+// forward-backward part per 512 strings, at most 8) and dense accumulators
+// when they fit the budget in one wave.
+static int batch_flags(fst_t* f, int kind, const int64_t* d_offsets, int32_t B, cudaStream_t s, int32_t* flags) {
+  int32_t fl = kind == 0 ? FST_PLAN_NO_FB : FST_PLAN_NO_VITERBI;
+  int32_t parts = f->batch_parts[kind];
+  if (parts <= 0) parts = kind == 0 ? std::min(2, std::max(1, B / 2048)) : std::min(8, std::max(1, B / 512));
+  if (parts > 1) fl |= FST_PLAN_PARTS(parts);
+  int32_t layout = f->batch_layout;
+  if (layout < 0) {
+    int64_t N = 0;
+    if (B > 0) {
+      FST_CUDA(cudaMemcpyAsync(&N, d_offsets + B, 8, cudaMemcpyDeviceToHost, s));
+      FST_CUDA(cudaStreamSynchronize(s));
+    }
+    const int64_t budget = f->batch_budget > 0 ? f->batch_budget : default_budget();
+    const int64_t need = (dense_bytes_per_string(f, kind == 1, kind == 0) + 64) * (int64_t)B +
+                         (TOKEN_BYTES + POOL_PER_TOKEN * 20) * N;
+    layout = need <= budget ? 1 : 0;
+  }
+  if (layout == 1) fl |= FST_PLAN_DENSE_ACC;
+  *flags = fl;
+  return FST_OK;
+}
+
+extern "C" int fst_set_batch_plan(fst_t* f, int32_t parts_viterbi, int32_t parts_fb, int32_t layout) {
+  if (!f || parts_viterbi < 0 || parts_viterbi > 255 || parts_fb < 0 || parts_fb > 255 || layout < -1 || layout > 1) {
+    set_error("fst_set_batch_plan: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  f->batch_parts[0] = parts_viterbi;
+  f->batch_parts[1] = parts_fb;
+  f->batch_layout = layout;
+  return FST_OK;
+}
+
 extern "C" int fst_viterbi_batch(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                                  float* d_scores, int32_t* d_paths, int32_t* d_olabels, int32_t* d_status,
                                  void* stream) {
   if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
+  if (B < 0 || !d_offsets) { set_error("fst_viterbi_batch: bad arguments"); return FST_ERR_INVALID_ARG; }
   fst_plan_t* P = nullptr;
-  int rc = plan_create(f, d_ids, d_offsets, B, f->batch_budget, FST_PLAN_NO_FB, stream, take_cached(f, 0), &P);
+  int32_t flags = 0;
+  int rc = batch_flags(f, 0, d_offsets, B, as_stream(stream), &flags);
+  if (rc) return rc;
+  rc = plan_create(f, d_ids, d_offsets, B, f->batch_budget, flags, stream, take_cached(f, 0), &P);
   if (rc) return rc;
   rc = fst_plan_viterbi(P, d_scores, d_paths, d_olabels, d_status, stream);
   cudaError_t e = cudaStreamSynchronize(as_stream(stream));
@@ -978,8 +1052,12 @@ extern "C" int fst_forward_backward_batch(fst_t* f, const int32_t* d_ids, const 
                                           const float* d_weights, double* d_logz, float* d_counts,
                                           int32_t* d_status, void* stream) {
   if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
+  if (B < 0 || !d_offsets) { set_error("fst_forward_backward_batch: bad arguments"); return FST_ERR_INVALID_ARG; }
   fst_plan_t* P = nullptr;
-  int rc = plan_create(f, d_ids, d_offsets, B, f->batch_budget, FST_PLAN_NO_VITERBI, stream, take_cached(f, 1), &P);
+  int32_t flags = 0;
+  int rc = batch_flags(f, 1, d_offsets, B, as_stream(stream), &flags);
+  if (rc) return rc;
+  rc = plan_create(f, d_ids, d_offsets, B, f->batch_budget, flags, stream, take_cached(f, 1), &P);
   if (rc) return rc;
   rc = fst_plan_forward_backward(P, d_weights, d_logz, d_counts, d_status, stream);
   cudaError_t e = cudaStreamSynchronize(as_stream(stream));

@@ -64,12 +64,16 @@ def test_forward_backward_batch(c2s):
     check_batch_fb(o, strs, r["logz"], r["counts"])
 
 
-def test_repeated_batch_calls_reuse_storage(c2s):
-    # each batch call kind keeps its last plan's storage for the next call:
-    # a smaller batch reuses it, a larger one replaces it, and results stay
-    # those of the oracle either way (the accumulators stay zero between runs)
+@pytest.mark.parametrize("plan", [(0, 0, -1), (2, 3, 0), (2, 3, 1), (1, 4, 1), (3, 2, 0)])
+def test_repeated_batch_calls_reuse_storage(c2s, plan):
+    # each batch call kind keeps its last plan's storage for the next call
+    # (part by part for plans of several parts): a smaller batch reuses it, a
+    # larger one replaces it, and results stay those of the oracle either way
+    # (the accumulators stay empty between runs); the plans' parts and
+    # accumulator layout as fst_set_batch_plan sets them
     f, o, strs = c2s
-    subsets = [(0, 60), (10, 30), (0, 60), (25, 60)]
+    f.set_batch_plan(*plan)
+    subsets = [(0, 60), (10, 30), (0, 60), (25, 60), (0, 7)]
     for b0, b1 in subsets:
         sub = synth.Strings(strs.ids[strs.offsets[b0]:strs.offsets[b1]].copy(),
                             (strs.offsets[b0:b1 + 1] - strs.offsets[b0]).copy())
@@ -77,6 +81,7 @@ def test_repeated_batch_calls_reuse_storage(c2s):
         check_batch_viterbi(o, sub, f.viterbi_batch(ids, off))
         r = f.forward_backward_batch(ids, off)
         check_batch_fb(o, sub, r["logz"], r["counts"])
+    f.set_batch_plan(0, 0, -1)
 
 
 def test_waves_match_single_wave(c2s):
