@@ -43,6 +43,9 @@ constexpr int64_t TOKEN_BYTES = 80;
 // than the position's destination bound
 constexpr int64_t LIVE_PER_TOKEN = 128;
 constexpr int64_t LIVE_FLOOR = (int64_t)1 << 18;
+// internal plan flag: a part of a plan of several parts (the parent owns
+// the count accumulators)
+constexpr int32_t PLAN_PART = 1 << 16;
 
 // *sum += the non-negative values of v[0..n).
 __global__ void k_sum_i32(const int32_t* __restrict__ v, int64_t n, unsigned long long* __restrict__ sum) {
@@ -522,9 +525,14 @@ static int plan_create_parts(fst_t* f, const int32_t* d_ids, const std::vector<i
     fst_plan_t* sub = nullptr;
     fst_plan_s* part_donor = nullptr;
     if (donor) std::swap(part_donor, donor->parts[i]);
+    if (part_donor && part_donor->borrowed_counts) {
+      // the count accumulators belong to the donor's parent (taken below)
+      part_donor->cnt64 = part_donor->start64 = part_donor->final64 = nullptr;
+      part_donor->borrowed_counts = false;
+    }
     rc = e == cudaSuccess ? plan_create(f, d_ids ? d_ids + h_off[b0] : nullptr, d_off, b1 - b0,
-                                        budget > 0 ? std::max<int64_t>(budget / nparts, 1) : 0, flags & 0xff,
-                                        (void*)s, part_donor, &sub)
+                                        budget > 0 ? std::max<int64_t>(budget / nparts, 1) : 0,
+                                        (flags & 0xff) | PLAN_PART, (void*)s, part_donor, &sub)
                           : (delete part_donor, cuda_fail(e, "part offsets"));
     dfree(d_off);
     if (rc) return rc;
@@ -753,8 +761,9 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
         (rc = alloc_store(P, &P->esum, nt)) || (rc = alloc_store(P, &P->jfinal, P->max_bw)) ||
         (rc = alloc_store(P, &P->logz, B)) || (rc = alloc_store(P, &P->gbar, 2)))
       break;
-    if (P->want_fb && ((rc = alloc_store(P, &P->cnt64, f->A)) || (rc = alloc_store(P, &P->start64, f->Q)) ||
-                       (rc = alloc_store(P, &P->final64, f->Q))))
+    if (P->want_fb && !(flags & PLAN_PART) &&
+        ((rc = alloc_store(P, &P->cnt64, f->A)) || (rc = alloc_store(P, &P->start64, f->Q)) ||
+         (rc = alloc_store(P, &P->final64, f->Q))))
       break;
     // the accumulators start at zero and every run leaves them so
     cudaError_t ce = cudaSuccess;
@@ -786,7 +795,7 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
 
 extern "C" int fst_plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                                int64_t mem_budget_bytes, int32_t flags, void* stream, fst_plan_t** out) {
-  return plan_create(f, d_ids, d_offsets, B, mem_budget_bytes, flags, stream, nullptr, out);
+  return plan_create(f, d_ids, d_offsets, B, mem_budget_bytes, flags & ~PLAN_PART, stream, nullptr, out);
 }
 
 extern "C" int fst_plan_destroy(fst_plan_t* P) {
