@@ -62,7 +62,7 @@ SIGNATURES = {
     "fst_plan_limit_table": [vp, i64],
     "fst_plan_table_slots": [vp, vp],
     "fst_set_batch_budget": [vp, i64],
-    "fst_set_batch_plan": [vp, i32, i32, i32],
+    "fst_set_batch_plan": [vp, i32, i32, i32, i32],
     "fst_plan_set_driver": [vp, i32, i32, i64],
     "fst_plan_get_driver": [vp, vp, vp],
     "fst_plan_fault_inject": [vp, i32, i64],

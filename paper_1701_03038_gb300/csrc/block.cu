@@ -43,7 +43,11 @@ using namespace fstgpu;
 
 namespace {
 
-constexpr int BT = 1024;  // threads of the block
+// threads of the block (a build-time tuning knob)
+#ifndef FST_BLOCK_THREADS
+#define FST_BLOCK_THREADS 1024
+#endif
+constexpr int BT = FST_BLOCK_THREADS;
 
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
@@ -88,7 +92,10 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // for every sweep over the slice at a position; they are loaded one
 // position ahead, so the loads of t+1 are in flight while t is relaxed.
 // Arcs past them (slices longer than KR * BT) are read where they are used.
-constexpr int KR = 2;
+#ifndef FST_BLOCK_REG_ARCS
+#define FST_BLOCK_REG_ARCS 2
+#endif
+constexpr int KR = FST_BLOCK_REG_ARCS;
 struct ArcRegs {
   int4 r[KR];  // {source, destination, caller id (< 0: none), 0}
   float th[KR];

@@ -19,6 +19,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fst_internal.cuh"
@@ -29,7 +30,6 @@ using namespace fstgpu;
 namespace {
 
 constexpr int TB = 256;
-inline unsigned nblk(int64_t n, int tb = TB) { return (unsigned)std::max<int64_t>(1, (n + tb - 1) / tb); }
 
 // live-pool entries reserved per token (the pool never exceeds the sum of
 // the tokens' destination-segment counts, its exact bound)
@@ -57,11 +57,6 @@ __global__ void k_sum_i32(const int32_t* __restrict__ v, int64_t n, unsigned lon
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sum, acc);
 }
 
-__global__ void k_check_ids(const int32_t* __restrict__ ids, int64_t n, int32_t m, unsigned int* __restrict__ err) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && (ids[i] < 0 || ids[i] >= m)) atomicOr(err, 1u);
-}
-
 struct Wave {
   int32_t b0 = 0, b1 = 0, Bw = 0, tmax = 0;
   int64_t tok0 = 0, ntok = 0;
@@ -74,9 +69,14 @@ struct Wave {
   std::vector<int32_t> step0;  // [tmax + 2]: tokens of position t are step_tok[step0[t] .. step0[t+1])
   int32_t* d_step0 = nullptr;  // the same on the device (persistent passes)
   int32_t grid_est = 1;        // blocks of the busiest position (about 64 live states per token)
-  void release() {
-    dfree(tok_sym); dfree(tok_b); dfree(step_tok); dfree(stf); dfree(bw_n); dfree(bw_off); dfree(d_step0);
-  }
+  // the device arrays above point into the plan's token arena
+  void release() {}
+};
+
+// Host copies of a wave's token tables, uploaded into the token arena.
+struct HostWave {
+  std::vector<int32_t> sym, tb, step_tok, bn;
+  std::vector<int64_t> stf, boff;
 };
 
 }  // namespace
@@ -102,7 +102,7 @@ int64_t dense_bytes_per_string(const fst_s* f, bool fb, bool vit) {
 #define PLAN_STORAGE(X)                                                                                          \
   X(acc) X(beta) X(vmap) X(stage) X(stage_b) X(scnt) X(pool_q) X(pool_x) X(pool_n) X(pool_v) X(pool_base)          \
   X(pool_cnt) X(slot_base) X(step_rng) X(pool_top) X(flags_d) X(mkey) X(ekey) X(csum) X(esum) X(jfinal) X(logz) \
-  X(cnt64) X(start64) X(final64) X(gbar) X(htab) X(bslot)
+  X(cnt64) X(start64) X(final64) X(gbar) X(htab) X(bslot) X(tok_arena)
 
 struct fst_plan_s {
   fst_t* fst = nullptr;
@@ -123,6 +123,9 @@ struct fst_plan_s {
   int64_t table_limit = 0;             // fst_plan_limit_table: slots a run may use (0 = cap_hslots)
   unsigned long long* htab = nullptr;
   int32_t* bslot = nullptr;            // [pool_cap]
+  // every wave's token tables, one allocation (cap_tok bytes)
+  unsigned char* tok_arena = nullptr;
+  int64_t cap_tok = 0;
   int32_t *stage = nullptr, *stage_b = nullptr;
   uint32_t* scnt = nullptr;
   int32_t *pool_q = nullptr, *pool_x = nullptr, *pool_n = nullptr;
@@ -203,20 +206,11 @@ int alloc_store(fst_plan_s* P, T** p, int64_t n) {
   return rc;
 }
 
-template <class T>
-int upload(fst_plan_s* P, T** d, const std::vector<T>& h) {
-  int rc = alloc_track(P, d, (int64_t)h.size());
-  if (rc) return rc;
-  if (!h.empty()) FST_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return FST_OK;
-}
-
 // Token tables of one wave, built on the host from the offsets and symbols.
 // Tokens of a string are consecutive (token p = position t of string b is
 // p = off_b + t - 1); the tokens of position t are listed string by string.
-int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, const std::vector<int32_t>& hid) {
+int build_wave(fst_plan_s* P, Wave& W, const int64_t* h_off, const int32_t* hid, HostWave& H) {
   fst_s* f = P->fst;
-  int rc;
   W.Bw = W.b1 - W.b0;
   W.tok0 = h_off[W.b0];
   W.ntok = h_off[W.b1] - W.tok0;
@@ -265,10 +259,55 @@ int build_wave(fst_plan_s* P, Wave& W, const std::vector<int64_t>& h_off, const 
   int64_t busiest = 1;
   for (int32_t t = 1; t <= W.tmax; ++t) busiest = std::max<int64_t>(busiest, W.step0[t + 1] - W.step0[t]);
   W.grid_est = (int32_t)std::min<int64_t>((int64_t)f->num_sms * 8, (busiest * 64 + 255) / 256);
-  if ((rc = upload(P, &W.bw_off, boff)) || (rc = upload(P, &W.bw_n, bn)) || (rc = upload(P, &W.tok_sym, sym)) ||
-      (rc = upload(P, &W.tok_b, tb)) || (rc = upload(P, &W.step_tok, step_tok)) || (rc = upload(P, &W.stf, stf)) ||
-      (rc = upload(P, &W.d_step0, W.step0)))
-    return rc;
+  H.sym = std::move(sym);
+  H.tb = std::move(tb);
+  H.step_tok = std::move(step_tok);
+  H.bn = std::move(bn);
+  H.stf = std::move(stf);
+  H.boff = std::move(boff);
+  return FST_OK;
+}
+
+// The waves' token tables in the plan's token arena (grown when the one
+// taken over from a donor is too small), uploaded with one copy.
+int upload_tokens(fst_plan_s* P, std::vector<HostWave>& hw, cudaStream_t s) {
+  auto up16 = [](int64_t b) { return (b + 15) & ~(int64_t)15; };
+  int64_t total = 0;
+  for (size_t i = 0; i < P->waves.size(); ++i) {
+    const Wave& W = P->waves[i];
+    total += up16(8 * (int64_t)W.Bw) + up16(4 * (int64_t)W.Bw) + up16(4 * W.ntok) * 3 + up16(8 * W.ntok) +
+             up16(4 * ((int64_t)W.tmax + 2));
+  }
+  total = std::max<int64_t>(total, 16);
+  if (total > P->cap_tok) {
+    dfree(P->tok_arena);
+    P->cap_tok = 0;
+    int rc = dalloc(&P->tok_arena, total);
+    if (rc) return rc;
+    P->cap_tok = total;
+    P->store_bytes += total;
+    P->bytes += total;
+  }
+  std::vector<unsigned char> h((size_t)total);
+  int64_t at = 0;
+  auto put = [&](auto** dptr, const void* src, int64_t bytes) {
+    *dptr = (std::remove_pointer_t<decltype(dptr)>)(P->tok_arena + at);
+    if (bytes > 0) memcpy(h.data() + at, src, (size_t)bytes);
+    at += up16(bytes);
+  };
+  for (size_t i = 0; i < P->waves.size(); ++i) {
+    Wave& W = P->waves[i];
+    HostWave& H = hw[i];
+    put(&W.bw_off, H.boff.data(), 8 * (int64_t)W.Bw);
+    put(&W.bw_n, H.bn.data(), 4 * (int64_t)W.Bw);
+    put(&W.tok_sym, H.sym.data(), 4 * W.ntok);
+    put(&W.tok_b, H.tb.data(), 4 * W.ntok);
+    put(&W.step_tok, H.step_tok.data(), 4 * W.ntok);
+    put(&W.stf, H.stf.data(), 8 * W.ntok);
+    put(&W.d_step0, W.step0.data(), 4 * ((int64_t)W.tmax + 2));
+  }
+  FST_CUDA(cudaMemcpyAsync(P->tok_arena, h.data(), (size_t)at, cudaMemcpyHostToDevice, s));
+  FST_CUDA(cudaStreamSynchronize(s));
   return FST_OK;
 }
 
@@ -485,16 +524,15 @@ inline cudaStream_t as_stream(void* p) { return (cudaStream_t)p; }
 
 }  // namespace
 
-static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B, int64_t mem_budget_bytes,
-                       int32_t flags, void* stream, fst_plan_s* donor, fst_plan_t** out);
+static int plan_build(fst_t* f, const int32_t* hid, const int64_t* h_off, int32_t B, int64_t mem_budget_bytes,
+                      int32_t flags, cudaStream_t s, fst_plan_s* donor, fst_plan_t** out);
 
 // A plan of nparts stream-parallel parts: contiguous string ranges of about
 // equal token counts, each an ordinary plan with its own stream; the count
 // accumulators (and the expected start and final states) are the parent's,
 // shared by the parts (their float64 atomics add up across parts).
-static int plan_create_parts(fst_t* f, const int32_t* d_ids, const std::vector<int64_t>& h_off, int32_t B,
-                             int64_t budget, int32_t flags, cudaStream_t s, int32_t nparts, fst_plan_s* donor,
-                             fst_plan_t** out) {
+static int plan_create_parts(fst_t* f, const int32_t* hid, const int64_t* h_off, int32_t B, int64_t budget,
+                             int32_t flags, cudaStream_t s, int32_t nparts, fst_plan_s* donor, fst_plan_t** out) {
   // an earlier plan of as many parts lends each part's storage to the new
   // part of the same index, and its shared count accumulators
   std::unique_ptr<fst_plan_s> donor_owner(donor);
@@ -519,9 +557,6 @@ static int plan_create_parts(fst_t* f, const int32_t* d_ids, const std::vector<i
     }
     std::vector<int64_t> off(b1 - b0 + 1);
     for (int32_t b = b0; b <= b1; ++b) off[b - b0] = h_off[b] - h_off[b0];
-    int64_t* d_off = nullptr;
-    if ((rc = dalloc(&d_off, (int64_t)off.size()))) return rc;
-    cudaError_t e = cudaMemcpy(d_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice);
     fst_plan_t* sub = nullptr;
     fst_plan_s* part_donor = nullptr;
     if (donor) std::swap(part_donor, donor->parts[i]);
@@ -530,11 +565,8 @@ static int plan_create_parts(fst_t* f, const int32_t* d_ids, const std::vector<i
       part_donor->cnt64 = part_donor->start64 = part_donor->final64 = nullptr;
       part_donor->borrowed_counts = false;
     }
-    rc = e == cudaSuccess ? plan_create(f, d_ids ? d_ids + h_off[b0] : nullptr, d_off, b1 - b0,
-                                        budget > 0 ? std::max<int64_t>(budget / nparts, 1) : 0,
-                                        (flags & 0xff) | PLAN_PART, (void*)s, part_donor, &sub)
-                          : (delete part_donor, cuda_fail(e, "part offsets"));
-    dfree(d_off);
+    rc = plan_build(f, hid + h_off[b0], off.data(), b1 - b0, budget > 0 ? std::max<int64_t>(budget / nparts, 1) : 0,
+                    (flags & 0xff) | PLAN_PART, s, part_donor, &sub);
     if (rc) return rc;
     P->parts.push_back(sub);
     P->part_b0.push_back(b0);
@@ -595,9 +627,9 @@ static int parts_join(fst_plan_s* P, cudaStream_t s) {
   return FST_OK;
 }
 
-// Plan creation.  `donor` (owned: always released here) is an earlier plan
-// of the same handle whose device storage is taken over when it is large
-// enough, so that repeated batch calls neither allocate nor clear it again.
+// Plan creation from device inputs: the offsets and symbols are read back
+// once and checked on the host, then the plan is built from those host
+// arrays (plan_build).  Synchronises the stream.
 static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets, int32_t B, int64_t mem_budget_bytes,
                        int32_t flags, void* stream, fst_plan_s* donor, fst_plan_t** out) {
   std::unique_ptr<fst_plan_s> donor_owner(donor);
@@ -614,8 +646,30 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
   const int64_t N = h_off[B];
   if (N >= ((int64_t)1 << 31)) { set_error("too many tokens"); return FST_ERR_UNSUPPORTED; }
   if (N > 0 && !d_ids) { set_error("ids is NULL"); return FST_ERR_INVALID_ARG; }
+  std::vector<int32_t> hid((size_t)std::max<int64_t>(N, 1));
+  if (N > 0) {
+    FST_CUDA(cudaMemcpyAsync(hid.data(), d_ids, (size_t)N * 4, cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaStreamSynchronize(s));
+  }
+  for (int64_t i = 0; i < N; ++i)
+    if (hid[i] < 0 || hid[i] >= f->m) {
+      set_error("a symbol id is outside [0, %d)", f->m);
+      return FST_ERR_INVALID_ARG;
+    }
+  return plan_build(f, hid.data(), h_off.data(), B, mem_budget_bytes, flags, s, donor_owner.release(), out);
+}
+
+// Plan building from host arrays (symbols checked; h_off[0] = 0).
+// `donor` (owned: always released here) is an earlier plan of the same
+// handle whose device storage is taken over when it is large enough, so
+// that repeated batch calls neither allocate nor clear it again.
+static int plan_build(fst_t* f, const int32_t* hid, const int64_t* h_off, int32_t B, int64_t mem_budget_bytes,
+                      int32_t flags, cudaStream_t s, fst_plan_s* donor, fst_plan_t** out) {
+  std::unique_ptr<fst_plan_s> donor_owner(donor);
+  *out = nullptr;
+  const int64_t N = h_off[B];
   const int32_t nparts = std::min<int32_t>((flags >> 8) & 0xff, std::max(B, 1));
-  if (nparts > 1) return plan_create_parts(f, d_ids, h_off, B, mem_budget_bytes, flags, s, nparts, donor_owner.release(), out);
+  if (nparts > 1) return plan_create_parts(f, hid, h_off, B, mem_budget_bytes, flags, s, nparts, donor_owner.release(), out);
   if (donor && !donor->parts.empty()) donor_owner.reset();  // a parts plan lends nothing to a single plan
   fst_plan_s* P = new fst_plan_s();
   P->fst = f;
@@ -625,29 +679,8 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
   P->want_vit = !(flags & FST_PLAN_NO_VITERBI);
   P->want_fb = !(flags & FST_PLAN_NO_FB);
   int rc = FST_OK;
-  unsigned int* d_err = nullptr;
-  int32_t* d_ids_copy = nullptr;
+  std::vector<HostWave> hw;
   do {
-    // symbols: checked on the device, then read back for the host tables
-    if ((rc = dalloc(&d_ids_copy, N)) || (rc = dalloc(&d_err, 1))) break;
-    if (N > 0 && cudaMemcpyAsync(d_ids_copy, d_ids, (size_t)N * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
-      rc = cuda_fail(cudaGetLastError(), "ids copy");
-      break;
-    }
-    if (cudaMemsetAsync(d_err, 0, 4, s) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset"); break; }
-    if (N > 0) k_check_ids<<<nblk(N), TB, 0, s>>>(d_ids_copy, N, f->m, d_err);
-    unsigned int e = 0;
-    if (cudaMemcpyAsync(&e, d_err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-      rc = cuda_fail(cudaGetLastError(), "id check");
-      break;
-    }
-    if (e) { set_error("a symbol id is outside [0, %d)", f->m); rc = FST_ERR_INVALID_ARG; break; }
-    std::vector<int32_t> hid(N);
-    if (N > 0 && cudaMemcpy(hid.data(), d_ids_copy, (size_t)N * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
-      rc = cuda_fail(cudaGetLastError(), "ids read-back");
-      break;
-    }
     // relaxations of one pass (the paper's definition: every arc of every slice)
     P->relax = 0;
     for (int64_t i = 0; i < N; ++i) P->relax += f->h_sym_arc[hid[i] + 1] - f->h_sym_arc[hid[i]];
@@ -684,7 +717,8 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
       break;
     }
     for (Wave& w : P->waves) {
-      if ((rc = build_wave(P, w, h_off, hid))) break;
+      hw.emplace_back();
+      if ((rc = build_wave(P, w, h_off, hid, hw.back()))) break;
       P->max_bw = std::max<int64_t>(P->max_bw, w.Bw);
       P->max_ntok = std::max<int64_t>(P->max_ntok, w.ntok);
       P->max_stage = std::max(P->max_stage, w.stage);
@@ -724,6 +758,7 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
       P->cap_len = d->cap_len;
       P->cap_B = d->cap_B;
       P->cap_hslots = d->cap_hslots;
+      P->cap_tok = d->cap_tok;
       P->pool_cap = d->pool_cap;
       P->store_bytes = d->store_bytes;
       P->bytes += d->store_bytes;
@@ -783,8 +818,7 @@ static int plan_create(fst_t* f, const int32_t* d_ids, const int64_t* d_offsets,
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) rc = cuda_fail(ce, "plan storage");
   } while (0);
-  dfree(d_ids_copy);
-  dfree(d_err);
+  if (!rc) rc = upload_tokens(P, hw, s);
   if (rc) {
     delete P;
     return rc;
@@ -1028,14 +1062,52 @@ static int batch_flags(fst_t* f, int kind, const int64_t* d_offsets, int32_t B, 
   return FST_OK;
 }
 
-extern "C" int fst_set_batch_plan(fst_t* f, int32_t parts_viterbi, int32_t parts_fb, int32_t layout) {
-  if (!f || parts_viterbi < 0 || parts_viterbi > 255 || parts_fb < 0 || parts_fb > 255 || layout < -1 || layout > 1) {
+extern "C" int fst_set_batch_plan(fst_t* f, int32_t parts_viterbi, int32_t parts_fb, int32_t layout, int32_t graph) {
+  if (!f || parts_viterbi < 0 || parts_viterbi > 255 || parts_fb < 0 || parts_fb > 255 || layout < -1 || layout > 1 ||
+      graph < -1 || graph > 1) {
     set_error("fst_set_batch_plan: bad arguments");
     return FST_ERR_INVALID_ARG;
   }
   f->batch_parts[0] = parts_viterbi;
   f->batch_parts[1] = parts_fb;
   f->batch_layout = layout;
+  f->batch_graph = graph;
+  return FST_OK;
+}
+
+// Run a batch call's plan: its launches recorded into a CUDA graph and the
+// graph launched (the handle's setting; by default when the run has more
+// than 256 launches), or launched one by one.  Recording a launch costs the
+// host less than issuing it, and the graph goes to the GPU in one
+// submission.  The legacy default stream cannot be recorded: launches one
+// by one there, as inside a capture the caller has begun.
+template <class Run>
+static int batch_run(fst_t* f, fst_plan_t* P, int64_t launches, cudaStream_t s, Run run) {
+  bool graph = f->batch_graph == 1 || (f->batch_graph < 0 && launches > 256);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (graph && (s == 0 || s == cudaStreamLegacy || cudaStreamIsCapturing(s, &cs) != cudaSuccess ||
+                cs != cudaStreamCaptureStatusNone)) {
+    (void)cudaGetLastError();
+    graph = false;
+  }
+  if (!graph) return run(s);
+  FST_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const int rc = run(s);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (rc) return rc;
+    return cuda_fail(e, "batch graph capture");
+  }
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 == cudaSuccess) e2 = cudaGraphLaunch(ge, s);
+  if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+  if (ge) cudaGraphExecDestroy(ge);
+  if (e2 != cudaSuccess) return cuda_fail(e2, "batch graph launch");
+  (void)P;
   return FST_OK;
 }
 
@@ -1050,7 +1122,11 @@ extern "C" int fst_viterbi_batch(fst_t* f, const int32_t* d_ids, const int64_t* 
   if (rc) return rc;
   rc = plan_create(f, d_ids, d_offsets, B, f->batch_budget, flags, stream, take_cached(f, 0), &P);
   if (rc) return rc;
-  rc = fst_plan_viterbi(P, d_scores, d_paths, d_olabels, d_status, stream);
+  int64_t vl = 0;
+  fst_plan_info(P, nullptr, nullptr, nullptr, nullptr, nullptr, &vl, nullptr, nullptr);
+  rc = batch_run(f, P, vl, as_stream(stream), [&](cudaStream_t st) {
+    return fst_plan_viterbi(P, d_scores, d_paths, d_olabels, d_status, (void*)st);
+  });
   cudaError_t e = cudaStreamSynchronize(as_stream(stream));
   if (!rc && e != cudaSuccess) rc = cuda_fail(e, "fst_viterbi_batch");
   if (rc) fst_plan_destroy(P); else put_cached(f, 0, P);
@@ -1068,7 +1144,11 @@ extern "C" int fst_forward_backward_batch(fst_t* f, const int32_t* d_ids, const 
   if (rc) return rc;
   rc = plan_create(f, d_ids, d_offsets, B, f->batch_budget, flags, stream, take_cached(f, 1), &P);
   if (rc) return rc;
-  rc = fst_plan_forward_backward(P, d_weights, d_logz, d_counts, d_status, stream);
+  int64_t fl = 0;
+  fst_plan_info(P, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &fl, nullptr);
+  rc = batch_run(f, P, fl, as_stream(stream), [&](cudaStream_t st) {
+    return fst_plan_forward_backward(P, d_weights, d_logz, d_counts, d_status, (void*)st);
+  });
   cudaError_t e = cudaStreamSynchronize(as_stream(stream));
   if (!rc && e != cudaSuccess) rc = cuda_fail(e, "fst_forward_backward_batch");
   if (rc) fst_plan_destroy(P); else put_cached(f, 1, P);

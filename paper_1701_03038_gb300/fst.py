@@ -382,11 +382,12 @@ class Fst:
         forward_backward_batch (0 = the library default)."""
         check(self._lib.fst_set_batch_budget(self._h, int(nbytes)), "fst_set_batch_budget")
 
-    def set_batch_plan(self, parts_viterbi: int = 0, parts_fb: int = 0, layout: int = -1):
+    def set_batch_plan(self, parts_viterbi: int = 0, parts_fb: int = 0, layout: int = -1, graph: int = -1):
         """Plans of viterbi_batch and forward_backward_batch: stream-parallel
-        parts (0 = by batch size) and accumulators (-1 = dense when they fit
-        the budget, 0 = compact, 1 = dense); see fst_set_batch_plan."""
-        check(self._lib.fst_set_batch_plan(self._h, int(parts_viterbi), int(parts_fb), int(layout)),
+        parts (0 = by batch size), accumulators (-1 = dense when they fit
+        the budget, 0 = compact, 1 = dense) and CUDA-graph launch (-1 = above
+        256 launches, 0 = never, 1 = always); see fst_set_batch_plan."""
+        check(self._lib.fst_set_batch_plan(self._h, int(parts_viterbi), int(parts_fb), int(layout), int(graph)),
               "fst_set_batch_plan")
 
     def plan(self, ids: torch.Tensor, offsets: torch.Tensor, mem_budget: int = 0, flags: int = 0,

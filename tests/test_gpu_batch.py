@@ -64,24 +64,31 @@ def test_forward_backward_batch(c2s):
     check_batch_fb(o, strs, r["logz"], r["counts"])
 
 
-@pytest.mark.parametrize("plan", [(0, 0, -1), (2, 3, 0), (2, 3, 1), (1, 4, 1), (3, 2, 0)])
+@pytest.mark.parametrize("plan", [(0, 0, -1, -1), (2, 3, 0, 0), (2, 3, 1, 1), (1, 4, 1, 0), (3, 2, 0, 1)])
 def test_repeated_batch_calls_reuse_storage(c2s, plan):
     # each batch call kind keeps its last plan's storage for the next call
     # (part by part for plans of several parts): a smaller batch reuses it, a
     # larger one replaces it, and results stay those of the oracle either way
     # (the accumulators stay empty between runs); the plans' parts and
     # accumulator layout as fst_set_batch_plan sets them
+    import torch
     f, o, strs = c2s
     f.set_batch_plan(*plan)
+    # on a side stream (a graph cannot record the legacy default stream)
+    side = torch.cuda.Stream()
     subsets = [(0, 60), (10, 30), (0, 60), (25, 60), (0, 7)]
     for b0, b1 in subsets:
         sub = synth.Strings(strs.ids[strs.offsets[b0]:strs.offsets[b1]].copy(),
                             (strs.offsets[b0:b1 + 1] - strs.offsets[b0]).copy())
         ids, off = _dev(sub)
-        check_batch_viterbi(o, sub, f.viterbi_batch(ids, off))
-        r = f.forward_backward_batch(ids, off)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            v = f.viterbi_batch(ids, off, stream=side)
+            r = f.forward_backward_batch(ids, off, stream=side)
+        side.synchronize()
+        check_batch_viterbi(o, sub, v)
         check_batch_fb(o, sub, r["logz"], r["counts"])
-    f.set_batch_plan(0, 0, -1)
+    f.set_batch_plan(0, 0, -1, -1)
 
 
 def test_waves_match_single_wave(c2s):
