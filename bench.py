@@ -86,8 +86,11 @@ def parse_args(argv=None):
                     help="strings decoded with the paper's slice-wide relaxation for comparison")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
-    ap.add_argument("--parts-vit", type=int, default=2, help="stream-parallel parts of the Viterbi plan")
-    ap.add_argument("--parts-fb", type=int, default=8, help="stream-parallel parts of the forward-backward plan")
+    ap.add_argument("--parts-vit", type=int, default=0,
+                    help="stream-parallel parts of the Viterbi plan (0 = the batch calls' rule: one per 2,048 "
+                         "strings, at most 2)")
+    ap.add_argument("--parts-fb", type=int, default=0,
+                    help="stream-parallel parts of the forward-backward plan (0 = one per 512 strings, at most 8)")
     ap.add_argument("--acc", default="dense", choices=["dense", "compact"],
                     help="accumulators of the batched plans: dense per-string arrays (FST_PLAN_DENSE_ACC, the "
                          "faster) or the library's default hash tables (a third of the memory)")
@@ -105,6 +108,13 @@ def parse_args(argv=None):
     args = ap.parse_args(argv)
     args.dense_acc = args.acc == "dense"
     return args
+
+
+def auto_parts(args, B):
+    """The plan parts bench.py uses: the arguments, or the batch calls' rule."""
+    pv = args.parts_vit if args.parts_vit > 0 else min(2, max(1, B // 2048))
+    pf = args.parts_fb if args.parts_fb > 0 else min(8, max(1, B // 512))
+    return pv, pf
 
 
 # ---------------------------------------------------------------- clocks
@@ -499,6 +509,7 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     ids = torch.from_numpy(strs.ids).to(dev)
     off = torch.from_numpy(strs.offsets).to(dev)
     acc = _lib.PLAN_DENSE_ACC if args.dense_acc else 0
+    args.parts_vit, args.parts_fb = auto_parts(args, strs.count)
     plans_v = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB | acc, parts=args.parts_vit)]
     plans_f = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI | acc, parts=args.parts_fb)]
     tuned = {}

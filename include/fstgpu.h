@@ -261,11 +261,13 @@ FST_API int fst_set_batch_budget(fst_t* fst, int64_t mem_budget_bytes);
  * the dense accumulators and the live pool fit the batch budget in one
  * wave, else compact; 0 = compact; 1 = FST_PLAN_DENSE_ACC), and whether
  * the run's launches are recorded into a CUDA graph that is then launched
- * (graph: -1 = when the run has more than 256 launches, 0 = never,
- * 1 = always; never on the legacy default stream or inside a capture the
- * caller began).  The default is 0, 0, -1, -1.  A batch call keeps its
- * plan's device storage for the next call of the same kind (part by
- * part). */
+ * (graph: 0 = no, 1 = yes, never on the legacy default stream or inside a
+ * capture the caller began; -1 = the default, no: recording and
+ * instantiating a run of thousands of launches measured slower than
+ * issuing them).  The default is 0, 0, -1, -1.  A batch call keeps its
+ * plan's device storage for the next call of the same kind (part by part).
+ * Outside a graph capture, the parts of a plan issue their launches from
+ * one host thread each. */
 FST_API int fst_set_batch_plan(fst_t* fst, int32_t parts_viterbi, int32_t parts_fb, int32_t layout, int32_t graph);
 
 /* A plan holds everything a batch needs on the device: the token lists of

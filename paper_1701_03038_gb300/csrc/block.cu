@@ -51,6 +51,12 @@ constexpr int BT = FST_BLOCK_THREADS;
 
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
+// -inf tests on the bit patterns: integer compares, where a float64
+// compare would take the float64 pipe, slow on this part, for every arc of
+// a slice, most of which leave dead states.
+__device__ __forceinline__ bool dead64(double v) { return __double_as_longlong(v) == (long long)0xfff0000000000000ull; }
+__device__ __forceinline__ bool dead32(float v) { return __float_as_uint(v) == 0xff800000u; }
+
 // The padded slice of symbol a: positions [sym_win[a], sym_win[a+1]) x WIN.
 struct Slice {
   int64_t i0, i1;
@@ -258,30 +264,38 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
   for (int32_t t = 1; t <= n; ++t) {
     const Slice sl = slice_at(sym_win, ids, n, t);
     load_arcs(nxt, arcs, theta, slice_at(sym_win, ids, n, t + 1));
+    // an arc counts when its source is live and its weight finite (then
+    // the sum is finite too)
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
-      if (cur.r[k].z < 0) continue;
-      const double x = a[cur.r[k].x] + (double)cur.th[k];
-      if (x != -INFINITY) atomicMax(mx + cur.r[k].y, dkey(x));
+      if (cur.r[k].z < 0 || dead32(cur.th[k])) continue;
+      const double as = a[cur.r[k].x];
+      if (dead64(as)) continue;
+      atomicMax(mx + cur.r[k].y, dkey(as + (double)cur.th[k]));
     }
     for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
-      if (r.z < 0) continue;
-      const double x = a[r.x] + (double)__ldg(theta + i);
-      if (x != -INFINITY) atomicMax(mx + r.y, dkey(x));
+      const float th = __ldg(theta + i);
+      if (r.z < 0 || dead32(th)) continue;
+      const double as = a[r.x];
+      if (dead64(as)) continue;
+      atomicMax(mx + r.y, dkey(as + (double)th));
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
-      if (cur.r[k].z < 0) continue;
-      const double x = a[cur.r[k].x] + (double)cur.th[k];
-      if (x != -INFINITY) atomicAdd(sm + cur.r[k].y, fix_exp64(x, dkey_inv(mx[cur.r[k].y])));
+      if (cur.r[k].z < 0 || dead32(cur.th[k])) continue;
+      const double as = a[cur.r[k].x];
+      if (dead64(as)) continue;
+      atomicAdd(sm + cur.r[k].y, fix_exp64(as + (double)cur.th[k], dkey_inv(mx[cur.r[k].y])));
     }
     for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
-      if (r.z < 0) continue;
-      const double x = a[r.x] + (double)__ldg(theta + i);
-      if (x != -INFINITY) atomicAdd(sm + r.y, fix_exp64(x, dkey_inv(mx[r.y])));
+      const float th = __ldg(theta + i);
+      if (r.z < 0 || dead32(th)) continue;
+      const double as = a[r.x];
+      if (dead64(as)) continue;
+      atomicAdd(sm + r.y, fix_exp64(as + (double)th, dkey_inv(mx[r.y])));
     }
     __syncthreads();
     double* row = alpha + (int64_t)t * Q;
@@ -297,19 +311,19 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
   // float64 sum in a fixed order
   unsigned long long mk = 0ull;
   for (int32_t q = threadIdx.x; q < Q; q += BT) {
-    const double x = a[q] + (double)__ldg(theta_f + q);
-    if (x != -INFINITY) {
-      const unsigned long long k = dkey(x);
-      mk = k > mk ? k : mk;
-    }
+    const float tf = __ldg(theta_f + q);
+    if (dead64(a[q]) || dead32(tf)) continue;
+    const unsigned long long k = dkey(a[q] + (double)tf);
+    mk = k > mk ? k : mk;
   }
   mk = block_max_key(mk, redk);
   const double m = mk ? dkey_inv(mk) : -INFINITY;
   double part = 0.0;
   if (mk)
     for (int32_t q = threadIdx.x; q < Q; q += BT) {
-      const double x = a[q] + (double)__ldg(theta_f + q);
-      if (x != -INFINITY) part += exp(x - m);
+      const float tf = __ldg(theta_f + q);
+      if (dead64(a[q]) || dead32(tf)) continue;
+      part += exp((a[q] + (double)tf) - m);
     }
   const double lz = mk ? m + log(block_sum(part, redd)) : -INFINITY;
   if (threadIdx.x == 0) {
@@ -350,15 +364,18 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
     // keeps the float64 exponentials and logarithms to the live arcs
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
-      if (cur.r[k].z < 0 || alr[k] == -INFINITY) continue;
-      const double u = (double)cur.th[k] + a[cur.r[k].y];
-      if (u != -INFINITY) atomicMax(mx + cur.r[k].x, dkey(u));
+      if (cur.r[k].z < 0 || dead64(alr[k]) || dead32(cur.th[k])) continue;
+      const double b = a[cur.r[k].y];
+      if (dead64(b)) continue;
+      atomicMax(mx + cur.r[k].x, dkey((double)cur.th[k] + b));
     }
     for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
-      if (r.z < 0 || al[r.x] == -INFINITY) continue;
-      const double u = (double)__ldg(theta + i) + a[r.y];
-      if (u != -INFINITY) atomicMax(mx + r.x, dkey(u));
+      const float th = __ldg(theta + i);
+      if (r.z < 0 || dead32(th) || dead64(al[r.x])) continue;
+      const double b = a[r.y];
+      if (dead64(b)) continue;
+      atomicMax(mx + r.x, dkey((double)th + b));
     }
     __syncthreads();
     // the next position's alpha_{t-2} values, its arcs having arrived
@@ -369,19 +386,22 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
     // beta_t[dst] - log Z)
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
-      if (cur.r[k].z < 0 || alr[k] == -INFINITY) continue;
-      const double u = (double)cur.th[k] + a[cur.r[k].y];
-      if (u == -INFINITY) continue;
+      if (cur.r[k].z < 0 || dead64(alr[k]) || dead32(cur.th[k])) continue;
+      const double b = a[cur.r[k].y];
+      if (dead64(b)) continue;
+      const double u = (double)cur.th[k] + b;
       atomicAdd(sm + cur.r[k].x, fix_exp64(u, dkey_inv(mx[cur.r[k].x])));
       add_post(cnt, comp, cur.r[k].z, (float)exp((alr[k] + u) - lz), c0[k], c1[k]);
     }
     for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
-      if (r.z < 0) continue;
+      const float th = __ldg(theta + i);
+      if (r.z < 0 || dead32(th)) continue;
       const double x = al[r.x];
-      if (x == -INFINITY) continue;
-      const double u = (double)__ldg(theta + i) + a[r.y];
-      if (u == -INFINITY) continue;
+      if (dead64(x)) continue;
+      const double b = a[r.y];
+      if (dead64(b)) continue;
+      const double u = (double)th + b;
       atomicAdd(sm + r.x, fix_exp64(u, dkey_inv(mx[r.x])));
       add_post(cnt, comp, r.z, (float)exp((x + u) - lz), cnt[r.z], comp[r.z]);
     }

@@ -134,7 +134,7 @@ struct fst_s {
   int64_t batch_budget = 0;  // plan storage budget of the batch calls (0 = the plan default)
   int32_t batch_parts[2] = {0, 0};  // fst_set_batch_plan: parts of the Viterbi / FB batch plans (0 = by size)
   int32_t batch_layout = -1;        // accumulators of the batch plans: -1 by budget, 0 compact, 1 dense
-  int32_t batch_graph = -1;         // batch runs as a CUDA graph: -1 above 256 launches, 0 never, 1 always
+  int32_t batch_graph = 0;          // batch runs recorded into a CUDA graph and launched: 0 never, 1 always
   // an output-clamped FST (fst_create_clamped): the (input, output) label
   // pair of each of its input symbols, ((uint64)ilabel << 32 | olabel), sorted
   std::vector<uint64_t>* pair_keys = nullptr;

@@ -19,6 +19,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -613,6 +614,40 @@ static int plan_create_parts(fst_t* f, const int32_t* hid, const int64_t* h_off,
   return FST_OK;
 }
 
+// fn(i) for every part i: from one host thread per part (the caller's
+// taking part 0), so that the parts' launches are issued in parallel, or
+// one after the other while the stream is being recorded into a graph.
+template <class Fn>
+static int parts_each(fst_plan_s* P, cudaStream_t s, Fn fn) {
+  const size_t n = P->parts.size();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  bool threads = n > 1;
+  if (threads && (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)) {
+    (void)cudaGetLastError();
+    threads = false;
+  }
+  if (!threads) {
+    for (size_t i = 0; i < n; ++i) {
+      const int rc = fn(i);
+      if (rc) return rc;
+    }
+    return FST_OK;
+  }
+  std::vector<int> rcs(n, FST_OK);
+  const int dev = P->fst->device;
+  std::vector<std::thread> th;
+  th.reserve(n - 1);
+  for (size_t i = 1; i < n; ++i)
+    th.emplace_back([&rcs, &fn, dev, i] {
+      rcs[i] = cudaSetDevice(dev) == cudaSuccess ? fn(i) : cuda_fail(cudaGetLastError(), "part thread");
+    });
+  rcs[0] = fn(0);
+  for (std::thread& t : th) t.join();
+  for (int rc : rcs)
+    if (rc) return rc;
+  return FST_OK;
+}
+
 // The parts start after the work queued on s and s waits for all of them.
 static int parts_fork(fst_plan_s* P, cudaStream_t s) {
   FST_CUDA(cudaEventRecord(P->part_event[0], s));
@@ -901,13 +936,13 @@ extern "C" int fst_plan_viterbi(fst_plan_t* P, float* d_scores, int32_t* d_paths
   P->forward_done = false;
   if (!P->parts.empty()) {
     if ((rc = parts_fork(P, s))) return rc;
-    for (size_t i = 0; i < P->parts.size(); ++i) {
+    rc = parts_each(P, s, [&](size_t i) {
       const int32_t b0 = P->part_b0[i];
       const int64_t k0 = P->part_tok0[i];
-      if ((rc = fst_plan_viterbi(P->parts[i], d_scores + b0, d_paths + k0, d_olabels ? d_olabels + k0 : nullptr,
-                                 d_status ? d_status + b0 : nullptr, P->part_stream[i])))
-        return rc;
-    }
+      return fst_plan_viterbi(P->parts[i], d_scores + b0, d_paths + k0, d_olabels ? d_olabels + k0 : nullptr,
+                              d_status ? d_status + b0 : nullptr, P->part_stream[i]);
+    });
+    if (rc) return rc;
     return parts_join(P, s);
   }
   for (const Wave& W : P->waves)
@@ -922,11 +957,11 @@ extern "C" int fst_plan_forward(fst_plan_t* P, double* d_logz, int32_t* d_status
   int rc;
   if (!P->parts.empty()) {
     if ((rc = parts_fork(P, s))) return rc;
-    for (size_t i = 0; i < P->parts.size(); ++i) {
+    rc = parts_each(P, s, [&](size_t i) {
       const int32_t b0 = P->part_b0[i];
-      if ((rc = fst_plan_forward(P->parts[i], d_logz + b0, d_status ? d_status + b0 : nullptr, P->part_stream[i])))
-        return rc;
-    }
+      return fst_plan_forward(P->parts[i], d_logz + b0, d_status ? d_status + b0 : nullptr, P->part_stream[i]);
+    });
+    if (rc) return rc;
     if ((rc = parts_join(P, s))) return rc;
     P->forward_done = true;
     return FST_OK;
@@ -952,12 +987,16 @@ extern "C" int fst_plan_backward_ex(fst_plan_t* P, const float* d_weights, float
   if ((rc = counts_begin(P, states, s))) return rc;
   if (!P->parts.empty()) {
     if ((rc = parts_fork(P, s))) return rc;
-    for (size_t i = 0; i < P->parts.size(); ++i) {
+    rc = parts_each(P, s, [&](size_t i) {
       fst_plan_s* q = P->parts[i];
       const float* w = d_weights ? d_weights + P->part_b0[i] : nullptr;
-      for (const Wave& W : q->waves)
-        if ((rc = run_backward_wave(q, W, w, states, P->part_stream[i]))) return rc;
-    }
+      for (const Wave& W : q->waves) {
+        const int r = run_backward_wave(q, W, w, states, P->part_stream[i]);
+        if (r) return r;
+      }
+      return (int)FST_OK;
+    });
+    if (rc) return rc;
     if ((rc = parts_join(P, s))) return rc;
     return counts_end(P, d_counts, d_start, d_final, s);
   }
@@ -983,18 +1022,21 @@ extern "C" int fst_plan_forward_backward_ex(fst_plan_t* P, const float* d_weight
   if (bwd && (rc = counts_begin(P, states, s))) return rc;
   if (!P->parts.empty()) {
     if ((rc = parts_fork(P, s))) return rc;
-    for (size_t i = 0; i < P->parts.size(); ++i) {
+    rc = parts_each(P, s, [&](size_t i) {
       fst_plan_s* q = P->parts[i];
       cudaStream_t st = P->part_stream[i];
       const int32_t b0 = P->part_b0[i];
       const float* w = d_weights ? d_weights + b0 : nullptr;
       for (const Wave& W : q->waves) {
-        if ((rc = run_forward_wave(q, W, st, d_status ? d_status + b0 : nullptr))) return rc;
-        if (bwd && (rc = run_backward_wave(q, W, w, states, st))) return rc;
+        int r = run_forward_wave(q, W, st, d_status ? d_status + b0 : nullptr);
+        if (!r && bwd) r = run_backward_wave(q, W, w, states, st);
+        if (r) return r;
       }
       if (q->B > 0) FST_CUDA(cudaMemcpyAsync(d_logz + b0, q->logz, (size_t)q->B * 8, cudaMemcpyDeviceToDevice, st));
       q->forward_done = q->waves.size() <= 1;
-    }
+      return (int)FST_OK;
+    });
+    if (rc) return rc;
     if ((rc = parts_join(P, s))) return rc;
     if (bwd && (rc = counts_end(P, d_counts, d_start, d_final, s))) return rc;
     P->forward_done = true;
@@ -1076,14 +1118,14 @@ extern "C" int fst_set_batch_plan(fst_t* f, int32_t parts_viterbi, int32_t parts
 }
 
 // Run a batch call's plan: its launches recorded into a CUDA graph and the
-// graph launched (the handle's setting; by default when the run has more
-// than 256 launches), or launched one by one.  Recording a launch costs the
-// host less than issuing it, and the graph goes to the GPU in one
-// submission.  The legacy default stream cannot be recorded: launches one
-// by one there, as inside a capture the caller has begun.
+// graph launched (fst_set_batch_plan), or launched one by one (the
+// default: recording a plan of several thousand launches and instantiating
+// the graph measured slower than launching it once).  The legacy default
+// stream cannot be recorded: launches one by one there, as inside a capture
+// the caller has begun.
 template <class Run>
 static int batch_run(fst_t* f, fst_plan_t* P, int64_t launches, cudaStream_t s, Run run) {
-  bool graph = f->batch_graph == 1 || (f->batch_graph < 0 && launches > 256);
+  bool graph = f->batch_graph == 1;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (graph && (s == 0 || s == cudaStreamLegacy || cudaStreamIsCapturing(s, &cs) != cudaSuccess ||
                 cs != cudaStreamCaptureStatusNone)) {
