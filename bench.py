@@ -87,10 +87,10 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
     ap.add_argument("--parts-vit", type=int, default=0,
-                    help="stream-parallel parts of the Viterbi plan (0 = the batch calls' rule: one per 2,048 "
+                    help="stream-parallel parts of the Viterbi plan (0 = the batch calls' rule: one per 32 "
                          "strings, at most 2)")
     ap.add_argument("--parts-fb", type=int, default=0,
-                    help="stream-parallel parts of the forward-backward plan (0 = one per 512 strings, at most 8)")
+                    help="stream-parallel parts of the forward-backward plan (0 = one per 8 strings, at most 8)")
     ap.add_argument("--acc", default="dense", choices=["dense", "compact"],
                     help="accumulators of the batched plans: dense per-string arrays (FST_PLAN_DENSE_ACC, the "
                          "faster) or the library's default hash tables (a third of the memory)")
@@ -112,8 +112,8 @@ def parse_args(argv=None):
 
 def auto_parts(args, B):
     """The plan parts bench.py uses: the arguments, or the batch calls' rule."""
-    pv = args.parts_vit if args.parts_vit > 0 else min(2, max(1, B // 2048))
-    pf = args.parts_fb if args.parts_fb > 0 else min(8, max(1, B // 512))
+    pv = args.parts_vit if args.parts_vit > 0 else min(2, max(1, B // 32))
+    pf = args.parts_fb if args.parts_fb > 0 else min(8, max(1, B // 8))
     return pv, pf
 
 

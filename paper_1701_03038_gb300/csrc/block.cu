@@ -28,6 +28,12 @@
 //
 // Values are kept unshifted in float64 (no per-position rescaling: float64
 // holds the sums of log-probabilities of any string length used here).
+// The float64 pipe of this part is narrow: a float64 exponential or
+// logarithm costs the warp that holds a position's live arcs on the order of
+// a microsecond, which the other warps wait out at the barrier.  The terms
+// and logarithms of the log-sums stay float64 (their accuracy carries over
+// hundreds of positions); a posterior, a float32 count, is exponentiated in
+// float32 from a float64 argument, as in the batched kernels.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
       if (dead64(b)) continue;
       const double u = (double)cur.th[k] + b;
       atomicAdd(sm + cur.r[k].x, fix_exp64(u, dkey_inv(mx[cur.r[k].x])));
-      add_post(cnt, comp, cur.r[k].z, (float)exp((alr[k] + u) - lz), c0[k], c1[k]);
+      add_post(cnt, comp, cur.r[k].z, __expf((float)((alr[k] + u) - lz)), c0[k], c1[k]);
     }
     for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
@@ -403,7 +409,7 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
       if (dead64(b)) continue;
       const double u = (double)th + b;
       atomicAdd(sm + r.x, fix_exp64(u, dkey_inv(mx[r.x])));
-      add_post(cnt, comp, r.z, (float)exp((x + u) - lz), cnt[r.z], comp[r.z]);
+      add_post(cnt, comp, r.z, __expf((float)((x + u) - lz)), cnt[r.z], comp[r.z]);
     }
     __syncthreads();
     for (int32_t q = threadIdx.x; q < Q; q += BT) {

@@ -1079,13 +1079,13 @@ static void put_cached(fst_t* f, int kind, fst_plan_s* p) {
 
 // Plan flags of a batch call (kind 0: Viterbi, 1: forward-backward): the
 // handle's setting (fst_set_batch_plan) or, by default, stream-parallel
-// parts by batch size (one Viterbi part per 2,048 strings, at most 2; one
-// forward-backward part per 512 strings, at most 8) and dense accumulators
+// parts by batch size (one Viterbi part per 32 strings, at most 2; one
+// forward-backward part per 8 strings, at most 8) and dense accumulators
 // when they fit the budget in one wave.
 static int batch_flags(fst_t* f, int kind, const int64_t* d_offsets, int32_t B, cudaStream_t s, int32_t* flags) {
   int32_t fl = kind == 0 ? FST_PLAN_NO_FB : FST_PLAN_NO_VITERBI;
   int32_t parts = f->batch_parts[kind];
-  if (parts <= 0) parts = kind == 0 ? std::min(2, std::max(1, B / 2048)) : std::min(8, std::max(1, B / 512));
+  if (parts <= 0) parts = kind == 0 ? std::min(2, std::max(1, B / 32)) : std::min(8, std::max(1, B / 8));
   if (parts > 1) fl |= FST_PLAN_PARTS(parts);
   int32_t layout = f->batch_layout;
   if (layout < 0) {
