@@ -88,9 +88,10 @@ def parse_args(argv=None):
     ap.add_argument("--strings", type=int, default=0, help="use only the first N strings (profiling captures)")
     ap.add_argument("--parts-vit", type=int, default=0,
                     help="stream-parallel parts of the Viterbi plan (0 = the batch calls' rule: one per 32 "
-                         "strings, at most 2)")
+                         "strings, at most 2 and 400 / the longest string)")
     ap.add_argument("--parts-fb", type=int, default=0,
-                    help="stream-parallel parts of the forward-backward plan (0 = one per 8 strings, at most 8)")
+                    help="stream-parallel parts of the forward-backward plan (0 = one per 8 strings, at most 8 "
+                         "and 1,600 / the longest string)")
     ap.add_argument("--acc", default="dense", choices=["dense", "compact"],
                     help="accumulators of the batched plans: dense per-string arrays (FST_PLAN_DENSE_ACC, the "
                          "faster) or the library's default hash tables (a third of the memory)")
@@ -110,10 +111,13 @@ def parse_args(argv=None):
     return args
 
 
-def auto_parts(args, B):
-    """The plan parts bench.py uses: the arguments, or the batch calls' rule."""
-    pv = args.parts_vit if args.parts_vit > 0 else min(2, max(1, B // 32))
-    pf = args.parts_fb if args.parts_fb > 0 else min(8, max(1, B // 8))
+def auto_parts(args, B, tmax):
+    """The plan parts bench.py uses: the arguments, or the batch calls' rule
+    (by batch size, and at most 400 / tmax and 1,600 / tmax position
+    launches' worth, tmax the longest string)."""
+    tmax = max(int(tmax), 1)
+    pv = args.parts_vit if args.parts_vit > 0 else max(1, min(2, B // 32, 400 // tmax))
+    pf = args.parts_fb if args.parts_fb > 0 else max(1, min(8, B // 8, 1600 // tmax))
     return pv, pf
 
 
@@ -509,7 +513,7 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     ids = torch.from_numpy(strs.ids).to(dev)
     off = torch.from_numpy(strs.offsets).to(dev)
     acc = _lib.PLAN_DENSE_ACC if args.dense_acc else 0
-    args.parts_vit, args.parts_fb = auto_parts(args, strs.count)
+    args.parts_vit, args.parts_fb = auto_parts(args, strs.count, int(np.diff(strs.offsets).max(initial=1)))
     plans_v = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB | acc, parts=args.parts_vit)]
     plans_f = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI | acc, parts=args.parts_fb)]
     tuned = {}

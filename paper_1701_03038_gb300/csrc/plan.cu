@@ -1079,21 +1079,32 @@ static void put_cached(fst_t* f, int kind, fst_plan_s* p) {
 
 // Plan flags of a batch call (kind 0: Viterbi, 1: forward-backward): the
 // handle's setting (fst_set_batch_plan) or, by default, stream-parallel
-// parts by batch size (one Viterbi part per 32 strings, at most 2; one
-// forward-backward part per 8 strings, at most 8) and dense accumulators
+// parts by batch size (one Viterbi part per 32 strings, at most 2 and at
+// most 400 / the longest string; one forward-backward part per 8 strings,
+// at most 8 and at most 1,600 / the longest string) and dense accumulators
 // when they fit the budget in one wave.
 static int batch_flags(fst_t* f, int kind, const int64_t* d_offsets, int32_t B, cudaStream_t s, int32_t* flags) {
   int32_t fl = kind == 0 ? FST_PLAN_NO_FB : FST_PLAN_NO_VITERBI;
+  std::vector<int64_t> h_off((size_t)B + 1, 0);
+  if (B > 0) {
+    FST_CUDA(cudaMemcpyAsync(h_off.data(), d_offsets, (size_t)(B + 1) * 8, cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaStreamSynchronize(s));
+  }
+  int64_t tmax = 1;
+  for (int32_t b = 0; b < B; ++b) tmax = std::max(tmax, h_off[b + 1] - h_off[b]);
+  const int64_t N = h_off[B];
   int32_t parts = f->batch_parts[kind];
-  if (parts <= 0) parts = kind == 0 ? std::min(2, std::max(1, B / 32)) : std::min(8, std::max(1, B / 8));
+  if (parts <= 0) {
+    // by batch size, and few enough that a run stays near 400 (Viterbi) or
+    // 1,600 (forward-backward) position launches: the parts of a long
+    // string's batch multiply launches that the host issues one by one
+    const int64_t by_len = (kind == 0 ? 400 : 1600) / tmax;
+    parts = (int32_t)std::max<int64_t>(
+        1, std::min<int64_t>(kind == 0 ? std::min(2, B / 32) : std::min(8, B / 8), by_len));
+  }
   if (parts > 1) fl |= FST_PLAN_PARTS(parts);
   int32_t layout = f->batch_layout;
   if (layout < 0) {
-    int64_t N = 0;
-    if (B > 0) {
-      FST_CUDA(cudaMemcpyAsync(&N, d_offsets + B, 8, cudaMemcpyDeviceToHost, s));
-      FST_CUDA(cudaStreamSynchronize(s));
-    }
     const int64_t budget = f->batch_budget > 0 ? f->batch_budget : default_budget();
     const int64_t need = (dense_bytes_per_string(f, kind == 1, kind == 0) + 64) * (int64_t)B +
                          (TOKEN_BYTES + POOL_PER_TOKEN * 20) * N;
