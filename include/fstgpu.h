@@ -549,6 +549,18 @@ FST_API int fst_plan_fault_inject(fst_plan_t* plan, int32_t kind, int64_t value)
  * exercising that failure path. */
 FST_API int fst_plan_limit_pool(fst_plan_t* plan, int64_t entries);
 
+/* Direction switch of the forward pass (plans with FST_PLAN_DENSE_ACC and
+ * the launch driver; Sec. 4 remarks that the slice can be read by
+ * destination): a token with at least min_live live states, whose string
+ * goes on, scatters its forward values into a dense vector, and the next
+ * position pulls over the destination-ordered slice -- coalesced records,
+ * a warp-segmented exact maximum and fixed-point sum per destination, one
+ * atomic per destination and row of 32 arcs -- instead of pushing each arc
+ * with an atomic.  Up to 16 tokens per position; the rest push.  The
+ * results are the pushes' (the same exact terms).  min_live: -1 = the
+ * default, max(2048, num_states / 16); 0 = off; else the threshold. */
+FST_API int fst_plan_set_pull(fst_plan_t* plan, int64_t min_live);
+
 /* Compact accumulators: cap the hash tables of the plan's following runs at
  * `slots` slots each (rounded down to a power of two, at least 2; 0 = the capacity
  * allocated, which larger values cannot exceed).  Allocates nothing.  A run

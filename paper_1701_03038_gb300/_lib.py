@@ -60,6 +60,7 @@ SIGNATURES = {
     "fst_plan_forward_backward_ex": [vp, vp, vp, vp, vp, vp, vp, vp],
     "fst_plan_limit_pool": [vp, i64],
     "fst_plan_limit_table": [vp, i64],
+    "fst_plan_set_pull": [vp, i64],
     "fst_plan_table_slots": [vp, vp],
     "fst_set_batch_budget": [vp, i64],
     "fst_set_batch_plan": [vp, i32, i32, i32, i32],

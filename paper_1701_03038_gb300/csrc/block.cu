@@ -57,12 +57,6 @@ constexpr int BT = FST_BLOCK_THREADS;
 
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
-// -inf tests on the bit patterns: integer compares, where a float64
-// compare would take the float64 pipe, slow on this part, for every arc of
-// a slice, most of which leave dead states.
-__device__ __forceinline__ bool dead64(double v) { return __double_as_longlong(v) == (long long)0xfff0000000000000ull; }
-__device__ __forceinline__ bool dead32(float v) { return __float_as_uint(v) == 0xff800000u; }
-
 // The padded slice of symbol a: positions [sym_win[a], sym_win[a+1]) x WIN.
 struct Slice {
   int64_t i0, i1;

@@ -718,7 +718,7 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
   } else {
     if (n >= 1) PLAIN_PROF(FST_PROF_FWD_FIRST, launch_fwd_first(L, T, plain_step(f, n, 1, 0), S, s));
     for (int32_t t = 1; t <= n; ++t) {
-      PLAIN_PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, plain_step(f, n, t, t - 1), S, s));
+      PLAIN_PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, plain_step(f, n, t, t - 1), S, PullView{}, s));
       PLAIN_PROF(FST_PROF_FWD_STEP, launch_fwd_step(L, T, plain_step(f, n, t, t + 1), S, s));
     }
   }

@@ -217,6 +217,11 @@ __device__ __forceinline__ unsigned long long fix_exp64(double v, double m) {
   if (v == m) return 1099511627776ull;  // 2^40
   return __double2ull_rn(exp(v - m) * 1099511627776.0);
 }
+// -inf tests on the bit patterns: integer compares (a float64 compare takes
+// the float64 pipe, narrow on this part).
+__device__ __forceinline__ bool dead64(double v) { return __double_as_longlong(v) == (long long)0xfff0000000000000ull; }
+__device__ __forceinline__ bool dead32(float v) { return __float_as_uint(v) == 0xff800000u; }
+
 // m + log(s / 2^40), in float64.
 __device__ __forceinline__ double fix_log_sum64(double m, unsigned long long s) {
   return (m == -INFINITY || s == 0ull) ? -INFINITY : m + log((double)s * 0x1p-40);
@@ -277,6 +282,9 @@ struct SliceView {
   const int64_t* h_sym_win;
 };
 int slice_view(fst_s* f, cudaStream_t s, SliceView* out);
+// The destination-ordered slice records (fst_s::slice_arcs), built on first
+// use whatever order the slice kernels are set to.
+int slice_records_dst(fst_s* f, cudaStream_t s);
 
 // Viterbi of one string by the paper's slice-wide relaxation (slice.cu);
 // host outputs, olabels may be NULL.

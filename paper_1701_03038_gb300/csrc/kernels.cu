@@ -222,6 +222,7 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
   __shared__ int last;
   __shared__ long long wsum[KT / 32];
   __shared__ long long first_bad, carry;
+  __shared__ int dsel;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   __threadfence();
@@ -233,6 +234,7 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
   if (threadIdx.x == 0) {
     first_bad = (long long)INT64_MAX;
     carry = begin;
+    dsel = 0;
   }
   __syncthreads();
   for (int32_t c = 0; c < V.n; c += KT * RPT) {
@@ -274,6 +276,19 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
       slot_out[V.slot0 + k0 + i] = fit ? base : INT64_MAX;
       if (base_out) base_out[p] = fit ? base : 0;
       if (cnt_out) cnt_out[p] = fit ? (int32_t)m : 0;
+      if (S.dense_min > 0) {
+        // direction switch: a token with many live states whose string goes
+        // on takes a dense value vector (while slots last)
+        int32_t slot = -1;
+        if (fit && m >= S.dense_min && S.bw_n[__ldg(T.b + p)] > V.t) {
+          const int k = atomicAdd(&dsel, 1);
+          if (k < DENSE_SLOTS) {
+            slot = k;
+            S.dlist[(int64_t)V.t * DENSE_SLOTS + k] = p;
+          }
+        }
+        S.dslot[p] = slot;
+      }
       base += m;
     }
     __syncthreads();
@@ -286,6 +301,7 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
     rng_out[0] = begin;
     rng_out[1] = end;
     if (top) *top = end;
+    if (S.dense_min > 0) S.dcnt[V.t] = dsel < DENSE_SLOTS ? dsel : DENSE_SLOTS;
     S.flags[0] = 0u;
   }
 }
@@ -601,6 +617,20 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
                                               const FrontierState& S, BlockScratch<PushCtx>& sh) {
   const int lane = threadIdx.x & 31;
   const int32_t t = V.t;
+  const bool pull = !VIT && S.dense_min > 0;
+  if (pull && t >= 2) {
+    // the dense vectors of position t-1 were last read by the pull and the
+    // sum of position t: back to -inf
+    const int32_t nd = __ldcg(S.dcnt + t - 1);
+    for (int32_t k = 0; k < nd; ++k) {
+      const int32_t p = __ldcg(S.dlist + (int64_t)(t - 1) * DENSE_SLOTS + k);
+      const int64_t base = __ldcg(S.pool_base + p);
+      const int32_t cnt = __ldcg(S.pool_cnt + p);
+      double* D = S.dvec + ((int64_t)k * 2 + ((t - 1) & 1)) * S.Q;
+      for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x)
+        D[__ldcg(S.pool_q + base + j)] = -INFINITY;
+    }
+  }
   const int64_t R0 = __ldcg(S.step_rng + 2 * t), R1 = __ldcg(S.step_rng + 2 * t + 1);
   const int32_t* stg = fwd_stage(S, t);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
@@ -658,9 +688,16 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
       Arcs nxt{0, 0};
       if (V.x_n > 0 && S.bw_n[b] > t) {  // the string goes on to t+1
         nxt = find_arcs(L, __ldg(T.sym + x.p + 1), d);
-        e0 = nxt.pos;
-        len = nxt.len;
-        nx = PushCtx{x.p + 1, b, r};
+        const int32_t ds = pull ? __ldcg(S.dslot + x.p) : -1;
+        if (ds >= 0) {
+          // a dense token: its value goes to the dense vector and the next
+          // position pulls instead
+          S.dvec[((int64_t)ds * 2 + (t & 1)) * S.Q + d] = r;
+        } else {
+          e0 = nxt.pos;
+          len = nxt.len;
+          nx = PushCtx{x.p + 1, b, r};
+        }
       }
       if (!VIT) {
         S.pool_x[j] = nxt.pos;
@@ -670,8 +707,9 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
     if (!VIT) warp_max_by_token(S.mkey, mk_p, mk_key);  // the step maximum m_t
     block_push<VIT>(L, T, S, t + 1, sh, e0, len, nx);
   }
-  // pool ranges of position t+1's tokens
-  if (V.x_n > 0) {
+  // pool ranges of position t+1's tokens (with the direction switch, the
+  // pull of t+1 hands them out once it has staged its destinations)
+  if (V.x_n > 0 && !pull) {
     StepView Vn = V;
     Vn.t = V.x_t;
     Vn.n = V.x_n;
@@ -689,6 +727,88 @@ __global__ void __launch_bounds__(KT) k_vit_step(LayoutView L, TokenView T, Step
 __global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, StepView V, FrontierState S) {
   __shared__ BlockScratch<PushCtx> sh;
   step_position<false>(L, T, V, S, sh);
+}
+
+// ======================================================================
+// Direction switch (forward pass, dense accumulators).  The dense tokens of
+// position s (DENSE_SLOTS at most, each with its values scattered into a
+// dense vector by the forward step) pull over the destination-ordered
+// slice of w_{s+1}: a warp per 128-arc window, 32 consecutive arcs a row
+// (coalesced 16-byte records), the source values gathered from the dense
+// vector, and a segmented reduction over each row's runs of equal
+// destination, so that one atomic per destination per row replaces one per
+// arc.  MAX: the exact maximum (order keys) into each destination, the
+// insert that finds it empty staging it; SUM: the fixed-point terms.  The
+// same terms as the pushes, so the same exact results.
+// ======================================================================
+template <bool SUM>
+__device__ __forceinline__ void pull_windows(const TokenView& T, const FrontierState& S, const PullView& R,
+                                             int32_t s) {
+  const int32_t nd = __ldcg(S.dcnt + s);
+  if (nd <= 0) return;
+  const int lane = threadIdx.x & 31;
+  const int32_t t = s + 1;  // the destination position
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;; gw += warps) {
+    // the dense token whose windows hold window gw (warp-uniform)
+    int32_t k = -1, p = 0;
+    int64_t w = 0, acc = 0;
+    for (int32_t kk = 0; kk < nd; ++kk) {
+      const int32_t pk = __ldcg(S.dlist + (int64_t)s * DENSE_SLOTS + kk);
+      const int32_t a = __ldg(T.sym + pk + 1);
+      const int64_t w0 = __ldg(R.win + a), nw = __ldg(R.win + a + 1) - w0;
+      if (gw < acc + nw) {
+        k = kk;
+        p = pk;
+        w = w0 + (gw - acc);
+        break;
+      }
+      acc += nw;
+    }
+    if (k < 0) break;
+    const int32_t b = __ldg(T.b + p);
+    const double* D = S.dvec + ((int64_t)k * 2 + (s & 1)) * S.Q;
+    int4 r[4];
+    float th[4];
+    double x[4];
+#pragma unroll
+    for (int row = 0; row < 4; ++row) {
+      const int64_t i = w * WIN + row * 32 + lane;
+      r[row] = __ldg(R.rec + i);
+      th[row] = __ldg(R.theta + i);
+    }
+#pragma unroll
+    for (int row = 0; row < 4; ++row) x[row] = (r[row].z >= 0 && !dead32(th[row])) ? __ldcg(D + r[row].x) : -INFINITY;
+#pragma unroll
+    for (int row = 0; row < 4; ++row) {
+      const int32_t d = r[row].y;
+      const bool live = r[row].z >= 0 && !dead32(th[row]) && !dead64(x[row]);
+      const int64_t slot = acc_slot(S, b, t, d);
+      unsigned long long v = 0ull;
+      if (live) {
+        const double u = x[row] + (double)th[row];
+        v = SUM ? fix_exp64(u, dkey_inv(__ldcg(fwd_max(S, slot)))) : dkey(u);
+      }
+      // segmented reduction over the row's runs of equal destination: the
+      // run's last lane ends with its total
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const unsigned long long o = __shfl_up_sync(FULL, v, dd);
+        const int32_t od = __shfl_up_sync(FULL, d, dd);
+        if (lane >= dd && od == d) v = SUM ? v + o : (o > v ? o : v);
+      }
+      const int32_t nd_next = __shfl_down_sync(FULL, d, 1);
+      const bool leader = (lane == 31 || nd_next != d) && v != 0ull;
+      bool first = false;
+      if (SUM) {
+        if (leader) atomicAdd(fwd_sum(S, slot), v);
+      } else {
+        if (leader) first = atomicMax(fwd_max(S, slot), v) == 0ull;
+        const uint32_t i = warp_stage_index(S.scnt, p + 1, first);
+        if (first) fwd_stage(S, t)[__ldg(T.stf + p + 1) + i] = d;
+      }
+    }
+  }
 }
 
 // The fixed-point terms of every thread's segment, VU arcs per thread a
@@ -759,9 +879,13 @@ __device__ __forceinline__ void sum_push(const LayoutView& L, const FrontierStat
 // Forward sum of position t: with every maximum M_d final, each live arc
 // adds exp(r_{t-1}[src] + theta - M_d) to its destination in fixed point.
 __device__ __forceinline__ void sum_position(const LayoutView& L, const TokenView& T, const StepView& V,
-                                             const FrontierState& S, BlockScratch<PushCtx>& sh) {
+                                             const FrontierState& S, const PullView& R,
+                                             BlockScratch<PushCtx>& sh) {
   const int lane = threadIdx.x & 31;
   const int32_t t = V.t;
+  const bool pull = S.dense_min > 0 && t >= 2;
+  // the dense tokens of t-1 by the pull; their entries push nothing here
+  if (pull) pull_windows<true>(T, S, R, t - 1);
   int64_t R0, R1;
   source_range(V, S, &R0, &R1);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
@@ -773,7 +897,7 @@ __device__ __forceinline__ void sum_position(const LayoutView& L, const TokenVie
     PushCtx me{0, 0, 0.0};
     if (j < R1) {
       const Source x = source_at(T, V, S, o, j);
-      if (x.p >= 0) {
+      if (x.p >= 0 && !(pull && __ldcg(S.dslot + x.p - 1) >= 0)) {
         const Arcs r = source_arcs(L, T, V, S, x, j);
         e0 = r.pos;
         len = r.len;
@@ -784,9 +908,17 @@ __device__ __forceinline__ void sum_position(const LayoutView& L, const TokenVie
   }
 }
 
-__global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepView V, FrontierState S) {
+__global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepView V, FrontierState S,
+                                                PullView R) {
   __shared__ BlockScratch<PushCtx> sh;
-  sum_position(L, T, V, S, sh);
+  sum_position(L, T, V, S, R, sh);
+}
+
+// The pull of position V.t (direction switch), then its pool ranges.
+__global__ void __launch_bounds__(KT) k_fwd_pull(TokenView T, StepView V, FrontierState S, PullView R) {
+  pull_windows<false>(T, S, R, V.t - 1);
+  ranges_last_block(T, V, S, S.scnt, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
+                    S.step_rng + 2 * V.t);
 }
 
 // ======================================================================
@@ -1085,7 +1217,7 @@ __global__ void __launch_bounds__(KT) k_fwd_persist(LayoutView L, TokenView T, W
   first_position<false>(L, T, step_at(D, 1, 0), S, sh);
   if (!grid_sync(G, S.flags + 1)) return;
   for (int32_t t = 1; t <= D.tmax; ++t) {
-    sum_position(L, T, step_at(D, t, t - 1), S, sh);
+    sum_position(L, T, step_at(D, t, t - 1), S, PullView{nullptr, nullptr, nullptr}, sh);
     if (!grid_sync(G, S.flags + 1)) return;
     step_position<false>(L, T, step_at(D, t, t + 1), S, sh);
     if (!grid_sync(G, S.flags + 1)) return;
@@ -1346,6 +1478,11 @@ __global__ void __launch_bounds__(FT) k_final_post(FrontierState S, CountView C)
   }
 }
 
+__global__ void k_fill_neg_inf(double* __restrict__ p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = -INFINITY;
+}
+
 __global__ void k_to_float(const double* __restrict__ in, int64_t n, float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -1417,9 +1554,17 @@ int launch_fwd_step(const LayoutView& L, const TokenView& T, const StepView& V, 
 }
 
 int launch_fwd_sum(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
-                   cudaStream_t s) {
-  k_fwd_sum<<<step_grid(k_fwd_sum, &g_grid[4], V), KT, 0, s>>>(L, T, V, S);
+                   const PullView& R, cudaStream_t s) {
+  unsigned g = step_grid(k_fwd_sum, &g_grid[4], V);
+  if (S.dense_min > 0) g = std::max(g, (unsigned)std::min(V.blocks * 4, 2048));  // room for the pull's windows
+  k_fwd_sum<<<g, KT, 0, s>>>(L, T, V, S, R);
   return check_launch("k_fwd_sum");
+}
+
+int launch_fwd_pull(const TokenView& T, const StepView& V, const FrontierState& S, const PullView& R, int num_sms,
+                    cudaStream_t s) {
+  k_fwd_pull<<<(unsigned)std::max(1, num_sms * 4), KT, 0, s>>>(T, V, S, R);
+  return check_launch("k_fwd_pull");
 }
 
 int launch_bwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
@@ -1526,6 +1671,12 @@ int launch_final_posteriors(const FrontierState& S, int32_t Bw, const CountView&
   if (Bw <= 0 || (!C.final64 && !C.start64)) return FST_OK;
   k_final_post<<<(unsigned)Bw, FT, 0, s>>>(S, C);
   return check_launch("k_final_post");
+}
+
+int launch_fill_neg_inf(double* p, int64_t n, cudaStream_t s) {
+  if (n <= 0) return FST_OK;
+  k_fill_neg_inf<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(p, n);
+  return check_launch("k_fill_neg_inf");
 }
 
 int launch_to_float(const double* in, int64_t n, float* out, cudaStream_t s) {

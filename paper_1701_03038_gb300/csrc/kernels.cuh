@@ -88,6 +88,20 @@ struct FrontierState {
   unsigned long long* btab2;
   int32_t* bslot;
   uint64_t hmask;
+  // Direction switch of the forward pass (dense accumulators, launch
+  // driver; dense_min = 0: off).  A token with at least dense_min live
+  // states, whose string goes on, gets one of DENSE_SLOTS dense value
+  // vectors for its position: the forward step scatters its values there
+  // instead of pushing its arcs, and the next position pulls over the
+  // destination-ordered slice.  dvec [DENSE_SLOTS][2][Q] float64 (-inf
+  // between uses), dslot [N] the slot of each token (-1: none), dlist
+  // [T+2][DENSE_SLOTS] the dense tokens of each position, dcnt [T+2] their
+  // number.
+  double* dvec;
+  int32_t* dslot;
+  int32_t* dlist;
+  int32_t* dcnt;
+  int32_t dense_min;
   const int32_t* src_by_id;          // [A] source state of each arc
   int32_t* stage;                    // staged destinations of positions of even parity
   int32_t* stage_b;                  // of odd parity
@@ -117,6 +131,17 @@ struct FrontierState {
   const float* gweight;              // [Bw] or null
   const int32_t* bw_n;               // [Bw] string lengths
   const int64_t* bw_off;             // [Bw] first token of each string
+};
+
+constexpr int DENSE_SLOTS = 16;
+
+// The destination-ordered slices the pull reads: records {source,
+// destination, caller id (< 0: padding), 0}, weights, and each symbol's
+// 128-arc windows [win[a], win[a+1]).
+struct PullView {
+  const int4* rec;
+  const float* theta;
+  const int64_t* win;
 };
 
 // Step offsets of a wave on the device, for the persistent passes: the
@@ -162,9 +187,15 @@ int launch_vit_step(const LayoutView& L, const TokenView& T, const StepView& V, 
 int launch_fwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                     cudaStream_t s);
 // Forward sum of position t: the live states of t-1 (V.x_*) add
-// exp(value - maximum) of each arc to its destination's accumulator.
+// exp(value - maximum) of each arc to its destination's accumulator (the
+// dense tokens of t-1 by the pull over R).
 int launch_fwd_sum(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
-                   cudaStream_t s);
+                   const PullView& R, cudaStream_t s);
+// The pull of position V.t (direction switch): the dense tokens of V.t - 1
+// take the maximum into every destination of their slice on w_t and stage
+// the live ones; the last block hands out the pool ranges of V.t.
+int launch_fwd_pull(const TokenView& T, const StepView& V, const FrontierState& S, const PullView& R,
+                    int num_sms, cudaStream_t s);
 // Backward step of position t: for each live state q of position t-1
 // (V.x_*), beta_{t-1}[q] over its arcs on w_t, and the posterior of each of
 // those arcs.
@@ -193,6 +224,8 @@ int launch_counts_out(int64_t A, const CountView& C, float* out, cudaStream_t s)
 // empty strings, whose paths start where they end), added to C.final64 and
 // C.start64 with the strings' weights.  Needs the forward pass and log Z.
 int launch_final_posteriors(const FrontierState& S, int32_t Bw, const CountView& C, cudaStream_t s);
+// p[i] = -inf, i < n.
+int launch_fill_neg_inf(double* p, int64_t n, cudaStream_t s);
 // out[i] = (float)in[i], i < n.
 int launch_to_float(const double* in, int64_t n, float* out, cudaStream_t s);
 // Zero n 64-bit words of accumulators if an error bit is set in *flag: a

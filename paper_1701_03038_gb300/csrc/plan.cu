@@ -103,7 +103,7 @@ int64_t dense_bytes_per_string(const fst_s* f, bool fb, bool vit) {
 #define PLAN_STORAGE(X)                                                                                          \
   X(acc) X(beta) X(vmap) X(stage) X(stage_b) X(scnt) X(pool_q) X(pool_x) X(pool_n) X(pool_v) X(pool_base)          \
   X(pool_cnt) X(slot_base) X(step_rng) X(pool_top) X(flags_d) X(mkey) X(ekey) X(csum) X(esum) X(jfinal) X(logz) \
-  X(cnt64) X(start64) X(final64) X(gbar) X(htab) X(bslot) X(tok_arena)
+  X(cnt64) X(start64) X(final64) X(gbar) X(htab) X(bslot) X(tok_arena) X(dvec) X(dslot) X(dlist) X(dcnt)
 
 struct fst_plan_s {
   fst_t* fst = nullptr;
@@ -127,6 +127,13 @@ struct fst_plan_s {
   // every wave's token tables, one allocation (cap_tok bytes)
   unsigned char* tok_arena = nullptr;
   int64_t cap_tok = 0;
+  // direction switch of the forward pass (dense accumulators, launch
+  // driver): dense value vectors and the dense tokens of each position
+  double* dvec = nullptr;      // [DENSE_SLOTS][2][Q], -inf between uses
+  int32_t* dslot = nullptr;    // [cap_nt]
+  int32_t* dlist = nullptr;    // [cap_len + 2][DENSE_SLOTS]
+  int32_t* dcnt = nullptr;     // [cap_len + 2]
+  int64_t pull_min = -1;       // fst_plan_set_pull: -1 the default threshold, 0 off
   int32_t *stage = nullptr, *stage_b = nullptr;
   uint32_t* scnt = nullptr;
   int32_t *pool_q = nullptr, *pool_x = nullptr, *pool_n = nullptr;
@@ -269,6 +276,12 @@ int build_wave(fst_plan_s* P, Wave& W, const int64_t* h_off, const int32_t* hid,
   return FST_OK;
 }
 
+// The live states from which a token of the forward pass pulls rather than
+// pushes: a sixteenth of the states, at least 2,048 (where a token's pushes
+// approach a tenth of its slice, a coalesced pass over the slice costs less
+// than the random atomics).
+int32_t pull_default(const fst_s* f) { return std::max<int32_t>(2048, f->Q / 16); }
+
 // The waves' token tables in the plan's token arena (grown when the one
 // taken over from a donor is too small), uploaded with one copy.
 int upload_tokens(fst_plan_s* P, std::vector<HostWave>& hw, cudaStream_t s) {
@@ -321,6 +334,13 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.acc_stride = P->acc_stride;
   S.beta = P->beta;
   S.vmap = P->vmap;
+  if (P->dvec && P->driver == FST_DRIVER_LAUNCH && P->pull_min != 0) {
+    S.dvec = P->dvec;
+    S.dslot = P->dslot;
+    S.dlist = P->dlist;
+    S.dcnt = P->dcnt;
+    S.dense_min = (int32_t)(P->pull_min > 0 ? std::min<int64_t>(P->pull_min, INT32_MAX) : pull_default(P->fst));
+  }
   if (P->compact) {
     const int64_t n = P->cap_hslots, hw = 2 * (int64_t)P->acc_stride;
     S.htab0 = P->htab;
@@ -448,6 +468,12 @@ int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_p
   return FST_OK;
 }
 
+// The destination-ordered slices of the direction switch.
+PullView pull_view(const fst_plan_s* P) {
+  const fst_s* f = P->fst;
+  return PullView{f->slice_arcs, f->fwd.theta, f->fwd.sym_win};
+}
+
 int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_status) {
   fst_s* f = P->fst;
   int rc;
@@ -458,10 +484,15 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
   if (P->driver == FST_DRIVER_PERSISTENT) {
     PROF(FST_PROF_FWD_STEP, launch_fwd_persist(L, T, wave_steps(W), S, persist_grid(P, W, 1), grid_sync_of(P), s));
   } else {
+    const PullView R = pull_view(P);
     if (W.tmax >= 1) PROF(FST_PROF_FWD_FIRST, launch_fwd_first(L, T, wave_step(P, W, 1, 0), S, s));
     for (int32_t t = 1; t <= W.tmax; ++t) {
-      PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, wave_step(P, W, t, t - 1), S, s));
+      PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, wave_step(P, W, t, t - 1), S, R, s));
       PROF(FST_PROF_FWD_STEP, launch_fwd_step(L, T, wave_step(P, W, t, t + 1), S, s));
+      // direction switch: the dense tokens of t pull into t+1, whose pool
+      // ranges this launch then hands out
+      if (S.dense_min > 0 && t < W.tmax)
+        PROF(FST_PROF_FWD_STEP, launch_fwd_pull(T, wave_step(P, W, t + 1, 0), S, R, f->num_sms, s));
     }
   }
   PROF(FST_PROF_FB_FINAL, launch_fb_final(S, W.Bw, P->logz + W.b0, d_status ? d_status + W.b0 : nullptr, s));
@@ -816,6 +847,17 @@ static int plan_build(fst_t* f, const int32_t* hid, const int64_t* h_off, int32_
       if ((rc = alloc_store(P, &P->acc, na * P->acc_stride))) break;
       if (P->want_fb && (rc = alloc_store(P, &P->beta, na))) break;
       if (P->want_vit && (rc = alloc_store(P, &P->vmap, na))) break;
+      if (P->want_fb) {
+        // the direction switch's dense vectors, and the destination-ordered
+        // slice records it reads
+        if ((rc = alloc_store(P, &P->dvec, (int64_t)DENSE_SLOTS * 2 * f->Q)) ||
+            (rc = alloc_store(P, &P->dslot, nt)) ||
+            (rc = alloc_store(P, &P->dlist, ((int64_t)P->max_len + 2) * DENSE_SLOTS)) ||
+            (rc = alloc_store(P, &P->dcnt, (int64_t)P->max_len + 2)))
+          break;
+        if ((rc = launch_fill_neg_inf(P->dvec, (int64_t)DENSE_SLOTS * 2 * f->Q, s))) break;
+        if ((rc = slice_records_dst(f, s))) break;
+      }
     }
     // forward: arcs on the next symbol; Viterbi with dense accumulators:
     // the predecessor entry
@@ -840,6 +882,8 @@ static int plan_build(fst_t* f, const int32_t* hid, const int64_t* h_off, int32_
     if (P->acc) ce = cudaMemsetAsync(P->acc, 0, (size_t)std::max<int64_t>(na * P->acc_stride, 1) * 8, s);
     if (ce == cudaSuccess && P->beta) ce = cudaMemsetAsync(P->beta, 0, (size_t)std::max<int64_t>(na, 1) * 8, s);
     if (ce == cudaSuccess && P->htab) ce = cudaMemsetAsync(P->htab, 0, (size_t)std::max<int64_t>(nh, 1) * 8, s);
+    if (ce == cudaSuccess && P->dcnt)
+      ce = cudaMemsetAsync(P->dcnt, 0, (size_t)((int64_t)P->max_len + 2) * 4, s);
     // position ranges start empty (a backward step reads those of a later
     // position to empty its tables)
     if (ce == cudaSuccess)
@@ -908,8 +952,10 @@ extern "C" int fst_plan_info(const fst_plan_t* P, int32_t* num_strings, int64_t*
     // overflow clear, first push, one step per position, final, backtrace
     vl += (int64_t)w.tmax + 4;
     // overflow clear, first push, sum and step per position, final; one
-    // backward step per position (and, compact, the clear of position 1)
+    // backward step per position (and, compact, the clear of position 1;
+    // with the direction switch, a pull per position but the first)
     fl += 3 * (int64_t)w.tmax + 3 + ((P->compact && w.tmax >= 2) ? 1 : 0);
+    if (P->dvec && P->pull_min != 0 && w.tmax >= 2) fl += w.tmax - 1;
   }
   fl += 1;  // counts out
   if (num_strings) *num_strings = P->B;
@@ -1256,6 +1302,13 @@ extern "C" int fst_plan_limit_pool(fst_plan_t* P, int64_t entries) {
   if (!P || entries < 0) { set_error("fst_plan_limit_pool: bad arguments"); return FST_ERR_INVALID_ARG; }
   P->pool_limit = entries;
   for (fst_plan_s* q : P->parts) q->pool_limit = entries;
+  return FST_OK;
+}
+
+extern "C" int fst_plan_set_pull(fst_plan_t* P, int64_t min_live) {
+  if (!P || min_live < -1) { set_error("fst_plan_set_pull: bad arguments"); return FST_ERR_INVALID_ARG; }
+  P->pull_min = min_live;
+  for (fst_plan_s* q : P->parts) q->pull_min = min_live;
   return FST_OK;
 }
 

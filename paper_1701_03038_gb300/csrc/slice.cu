@@ -249,6 +249,14 @@ __global__ void k_gather_olabels(const int32_t* __restrict__ path, int32_t n, co
 }  // namespace
 
 namespace fstgpu {
+int slice_records_dst(fst_s* f, cudaStream_t s) {
+  const int32_t order = f->slice_order;
+  f->slice_order = FST_SLICE_BY_DESTINATION;
+  const int rc = slice_records(f, s);
+  f->slice_order = order;
+  return rc;
+}
+
 int slice_view(fst_s* f, cudaStream_t s, SliceView* out) {
   int rc = slice_records(f, s);
   if (rc) return rc;

@@ -515,6 +515,12 @@ class Plan:
         """Cap the live pool of the following runs (0 = the full capacity)."""
         check(self._lib.fst_plan_limit_pool(self._h, int(entries)), "fst_plan_limit_pool")
 
+    def set_pull(self, min_live: int = -1):
+        """Direction switch of the forward pass (dense accumulators, launch
+        driver): tokens with at least min_live live states pull (-1 = the
+        default threshold, 0 = off); see fst_plan_set_pull."""
+        check(self._lib.fst_plan_set_pull(self._h, int(min_live)), "fst_plan_set_pull")
+
     def limit_table(self, slots: int = 0):
         """Cap the compact accumulator tables of the following runs (0 = the full capacity)."""
         check(self._lib.fst_plan_limit_table(self._h, int(slots)), "fst_plan_limit_table")

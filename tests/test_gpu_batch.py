@@ -420,3 +420,40 @@ def test_compact_tables_near_full(c2s):
     assert min(exact) == 2 * max(full)
     pv.limit_table(0)
     pf.limit_table(0)
+
+
+@pytest.mark.parametrize("parts", [1, 3])
+def test_forward_pull_matches_push(c2s, parts):
+    # the direction switch of the forward pass (dense accumulators): with a
+    # threshold of 1 every token of a position that has a slot (16) pulls
+    # over the destination-ordered slice and the rest push; log Z bit for
+    # bit as with every arc pushed, counts and state posteriors within
+    # float64 rounding; run twice (the dense vectors must come back to
+    # -inf), and in several waves
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    f, o, strs = c2s
+    ids, off = _dev(strs)
+    B = strs.count
+    res = {}
+    for name, pull, budget in (("push", 0, 0), ("pull", 1, 0), ("pull_waves", 1, 1 << 21)):
+        p = f.plan(ids, off, mem_budget=budget, flags=_lib.PLAN_NO_VITERBI | _lib.PLAN_DENSE_ACC, parts=parts)
+        p.set_pull(pull)
+        for _ in range(2):
+            p.forward_backward(states=True)
+            torch.cuda.synchronize()
+            res.setdefault(name, []).append((p.logz[:B].clone(), p.counts.clone(), p.start_counts.clone(),
+                                             p.final_counts.clone(), p.status[:B].clone()))
+        if name == "pull_waves" and parts == 1:
+            assert p.info()["waves"] > 1
+    ref = res["push"][0]
+    for name, runs in res.items():
+        for lz, cnt, st, fi, status in runs:
+            if name != "pull_waves":
+                assert torch.equal(lz, ref[0]), name
+            else:
+                assert np.allclose(lz.cpu().numpy(), ref[0].cpu().numpy(), rtol=1e-12, atol=1e-9)
+            assert torch.equal(status, ref[4])
+            for a, b in ((cnt, ref[1]), (st, ref[2]), (fi, ref[3])):
+                assert np.allclose(a.cpu().numpy(), b.cpu().numpy(), rtol=1e-9, atol=1e-12), name
+    check_batch_fb(o, strs, res["pull"][1][0], res["pull"][1][1][:o.A])

@@ -36,7 +36,8 @@ def test_pool_overflow_reports_oom_then_recovers():
     ids = torch.from_numpy(strs.ids).cuda()
     off = torch.from_numpy(strs.offsets).cuda()
     pv = f.plan(ids, off, flags=PLAN_NO_FB)
-    pf = f.plan(ids, off, flags=PLAN_NO_VITERBI)
+    pf = f.plan(ids, off, flags=PLAN_NO_VITERBI | _lib.PLAN_DENSE_ACC)
+    pf.set_pull(1)  # the forward pass's dense vectors must survive an overflowed run
     B, N = strs.count, len(strs.ids)
     ov = [o.viterbi(strs.get(b)) for b in range(B)]
     ofb = o.fb_batch(strs.ids, strs.offsets, nthreads=8)
