@@ -92,6 +92,9 @@ def parse_args(argv=None):
     ap.add_argument("--parts-fb", type=int, default=0,
                     help="stream-parallel parts of the forward-backward plan (0 = one per 8 strings, at most 8 "
                          "and 1,600 / the longest string)")
+    ap.add_argument("--pull", type=int, default=-1,
+                    help="direction switch of the forward pass: live states from which a token pulls "
+                         "(-1 = the library default, 0 = off)")
     ap.add_argument("--acc", default="dense", choices=["dense", "compact"],
                     help="accumulators of the batched plans: dense per-string arrays (FST_PLAN_DENSE_ACC, the "
                          "faster) or the library's default hash tables (a third of the memory)")
@@ -516,6 +519,8 @@ def bench_batch(args, rank, world, dev, fa, strs, f, stats):
     args.parts_vit, args.parts_fb = auto_parts(args, strs.count, int(np.diff(strs.offsets).max(initial=1)))
     plans_v = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB | acc, parts=args.parts_vit)]
     plans_f = [f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI | acc, parts=args.parts_fb)]
+    for p in plans_f:
+        p.set_pull(args.pull)
     tuned = {}
     if args.driver in ("persistent", "persistent-all"):
         for p in plans_f:

@@ -558,7 +558,7 @@ FST_API int fst_plan_limit_pool(fst_plan_t* plan, int64_t entries);
  * atomic per destination and row of 32 arcs -- instead of pushing each arc
  * with an atomic.  Up to 16 tokens per position; the rest push.  The
  * results are the pushes' (the same exact terms).  min_live: -1 = the
- * default, max(2048, num_states / 16); 0 = off; else the threshold. */
+ * default, max(2048, num_states / 2); 0 = off; else the threshold. */
 FST_API int fst_plan_set_pull(fst_plan_t* plan, int64_t min_live);
 
 /* Compact accumulators: cap the hash tables of the plan's following runs at

@@ -707,9 +707,10 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
     if (!VIT) warp_max_by_token(S.mkey, mk_p, mk_key);  // the step maximum m_t
     block_push<VIT>(L, T, S, t + 1, sh, e0, len, nx);
   }
-  // pool ranges of position t+1's tokens (with the direction switch, the
-  // pull of t+1 hands them out once it has staged its destinations)
-  if (V.x_n > 0 && !pull) {
+  // pool ranges of position t+1's tokens (when position t has dense
+  // tokens, the pull of t+1 hands them out once it has staged their
+  // destinations)
+  if (V.x_n > 0 && !(pull && __ldcg(S.dcnt + t) > 0)) {
     StepView Vn = V;
     Vn.t = V.x_t;
     Vn.n = V.x_n;
@@ -914,8 +915,11 @@ __global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepV
   sum_position(L, T, V, S, R, sh);
 }
 
-// The pull of position V.t (direction switch), then its pool ranges.
+// The pull of position V.t (direction switch), then its pool ranges; a
+// position whose predecessor has no dense token was handed out by the
+// forward step (block-uniform exit).
 __global__ void __launch_bounds__(KT) k_fwd_pull(TokenView T, StepView V, FrontierState S, PullView R) {
+  if (__ldcg(S.dcnt + V.t - 1) <= 0) return;
   pull_windows<false>(T, S, R, V.t - 1);
   ranges_last_block(T, V, S, S.scnt, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
                     S.step_rng + 2 * V.t);

@@ -277,10 +277,10 @@ int build_wave(fst_plan_s* P, Wave& W, const int64_t* h_off, const int32_t* hid,
 }
 
 // The live states from which a token of the forward pass pulls rather than
-// pushes: a sixteenth of the states, at least 2,048 (where a token's pushes
-// approach a tenth of its slice, a coalesced pass over the slice costs less
-// than the random atomics).
-int32_t pull_default(const fst_s* f) { return std::max<int32_t>(2048, f->Q / 16); }
+// pushes: half the states, at least 2,048.  A pull reads the whole slice;
+// below about half the states live, the pushes touch so much less of it
+// that they win (a sixteenth measured 28% slower on the 20M-arc batch).
+int32_t pull_default(const fst_s* f) { return std::max<int32_t>(2048, f->Q / 2); }
 
 // The waves' token tables in the plan's token arena (grown when the one
 // taken over from a donor is too small), uploaded with one copy.
