@@ -92,9 +92,9 @@ def parse_args(argv=None):
     ap.add_argument("--parts-fb", type=int, default=0,
                     help="stream-parallel parts of the forward-backward plan (0 = one per 8 strings, at most 8 "
                          "and 1,600 / the longest string)")
-    ap.add_argument("--pull", type=int, default=-1,
+    ap.add_argument("--pull", type=int, default=0,
                     help="direction switch of the forward pass: live states from which a token pulls "
-                         "(-1 = the library default, 0 = off)")
+                         "(0 = off, the library default; -1 = half the states)")
     ap.add_argument("--acc", default="dense", choices=["dense", "compact"],
                     help="accumulators of the batched plans: dense per-string arrays (FST_PLAN_DENSE_ACC, the "
                          "faster) or the library's default hash tables (a third of the memory)")

@@ -557,8 +557,10 @@ FST_API int fst_plan_limit_pool(fst_plan_t* plan, int64_t entries);
  * a warp-segmented exact maximum and fixed-point sum per destination, one
  * atomic per destination and row of 32 arcs -- instead of pushing each arc
  * with an atomic.  Up to 16 tokens per position; the rest push.  The
- * results are the pushes' (the same exact terms).  min_live: -1 = the
- * default, max(2048, num_states / 2); 0 = off; else the threshold. */
+ * results are the pushes' (the same exact terms).  min_live: 0 = off (the
+ * default: on the 20M-arc batch every threshold measured slower than none,
+ * the pull's launch per position costing more than it saves); -1 =
+ * max(2048, num_states / 2); else the threshold. */
 FST_API int fst_plan_set_pull(fst_plan_t* plan, int64_t min_live);
 
 /* Compact accumulators: cap the hash tables of the plan's following runs at

@@ -133,7 +133,7 @@ struct fst_plan_s {
   int32_t* dslot = nullptr;    // [cap_nt]
   int32_t* dlist = nullptr;    // [cap_len + 2][DENSE_SLOTS]
   int32_t* dcnt = nullptr;     // [cap_len + 2]
-  int64_t pull_min = -1;       // fst_plan_set_pull: -1 the default threshold, 0 off
+  int64_t pull_min = 0;        // fst_plan_set_pull: 0 off (the default), -1 pull_default, else the threshold
   int32_t *stage = nullptr, *stage_b = nullptr;
   uint32_t* scnt = nullptr;
   int32_t *pool_q = nullptr, *pool_x = nullptr, *pool_n = nullptr;
@@ -276,10 +276,12 @@ int build_wave(fst_plan_s* P, Wave& W, const int64_t* h_off, const int32_t* hid,
   return FST_OK;
 }
 
-// The live states from which a token of the forward pass pulls rather than
-// pushes: half the states, at least 2,048.  A pull reads the whole slice;
-// below about half the states live, the pushes touch so much less of it
-// that they win (a sixteenth measured 28% slower on the 20M-arc batch).
+// The suggested threshold of the direction switch (fst_plan_set_pull(-1)):
+// half the states, at least 2,048.  A pull reads the whole slice; below
+// about half the states live the pushes touch so much less of it that they
+// win.  On the 20M-arc batch even this threshold measured slower than no
+// switch (19.0 against 17.7 ms a step: the pull's launch per position costs
+// more than it saves on the few hub positions), so plans start with it off.
 int32_t pull_default(const fst_s* f) { return std::max<int32_t>(2048, f->Q / 2); }
 
 // The waves' token tables in the plan's token arena (grown when the one

@@ -517,8 +517,8 @@ class Plan:
 
     def set_pull(self, min_live: int = -1):
         """Direction switch of the forward pass (dense accumulators, launch
-        driver): tokens with at least min_live live states pull (-1 = the
-        default threshold, 0 = off); see fst_plan_set_pull."""
+        driver): tokens with at least min_live live states pull (0 = off,
+        the default; -1 = half the states); see fst_plan_set_pull."""
         check(self._lib.fst_plan_set_pull(self._h, int(min_live)), "fst_plan_set_pull")
 
     def limit_table(self, slots: int = 0):

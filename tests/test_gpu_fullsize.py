@@ -53,13 +53,14 @@ def _sub(strs, sel):
     return synth.Strings(np.concatenate(parts).astype(np.int32), off)
 
 
-def _run_two_streams(f, strs, budget=0, flags=0, parts=(1, 1)):
+def _run_two_streams(f, strs, budget=0, flags=0, parts=(1, 1), pull=0):
     import torch
     from paper_1701_03038_gb300._lib import PLAN_NO_FB, PLAN_NO_VITERBI
     ids = torch.from_numpy(strs.ids).cuda()
     off = torch.from_numpy(strs.offsets).cuda()
     pv = f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_FB | flags, parts=parts[0])
     pf = f.plan(ids, off, mem_budget=budget, flags=PLAN_NO_VITERBI | flags, parts=parts[1])
+    pf.set_pull(pull)
     s_v, s_f = torch.cuda.Stream(), torch.cuda.Stream()
     torch.cuda.synchronize()
     pv.viterbi(stream=s_v)
@@ -94,10 +95,10 @@ def test_c3_full_size_hard_strings_elementwise():
     from paper_1701_03038_gb300._lib import PLAN_DENSE_ACC
     sel, biggest = _hard_subbatch(fa, strs, 24, 22, seed=7)
     assert biggest >= 100_000  # the sample reaches the hub regime
-    # the whole batch, as the benchmark runs it: dense accumulators, 2 + 8
-    # stream-parallel parts, the forward pass's direction switch at its
-    # default threshold (the hub tokens pull)
-    full = _run_two_streams(f, strs, budget=48 << 30, flags=PLAN_DENSE_ACC, parts=(2, 8))
+    # the whole batch, as the benchmark runs it (dense accumulators, 2 + 8
+    # stream-parallel parts), with the forward pass's direction switch at
+    # half the states: the hub tokens pull
+    full = _run_two_streams(f, strs, budget=48 << 30, flags=PLAN_DENSE_ACC, parts=(2, 8), pull=-1)
     assert (full["vstatus"] == 0).all() and (full["fstatus"] == 0).all()
     # and with compact accumulators, every arc pushed: the same exact maxima
     # and fixed-point sums, so Viterbi and log Z agree bit for bit on all
