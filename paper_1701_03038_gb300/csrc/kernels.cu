@@ -280,7 +280,9 @@ __device__ void ranges_last_block(const TokenView& T, const StepView& V, const F
         // direction switch: a token with many live states whose string goes
         // on takes a dense value vector (while slots last)
         int32_t slot = -1;
-        if (fit && m >= S.dense_min && S.bw_n[__ldg(T.b + p)] > V.t) {
+        int32_t a = 0;
+        if (fit && m >= S.dense_min && S.bw_n[__ldg(T.b + p)] > V.t &&
+            (a = __ldg(T.sym + p + 1), __ldg(S.pull_lseg + a + 1) == __ldg(S.pull_lseg + a))) {
           const int k = atomicAdd(&dsel, 1);
           if (k < DENSE_SLOTS) {
             slot = k;
@@ -707,10 +709,9 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
     if (!VIT) warp_max_by_token(S.mkey, mk_p, mk_key);  // the step maximum m_t
     block_push<VIT>(L, T, S, t + 1, sh, e0, len, nx);
   }
-  // pool ranges of position t+1's tokens (when position t has dense
-  // tokens, the pull of t+1 hands them out once it has staged their
-  // destinations)
-  if (V.x_n > 0 && !(pull && __ldcg(S.dcnt + t) > 0)) {
+  // pool ranges of position t+1's tokens (with the direction switch, the
+  // sum launch of t+1 hands them out, after its pull has staged)
+  if (V.x_n > 0 && !pull) {
     StepView Vn = V;
     Vn.t = V.x_t;
     Vn.n = V.x_n;
@@ -733,18 +734,75 @@ __global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, Step
 // ======================================================================
 // Direction switch (forward pass, dense accumulators).  The dense tokens of
 // position s (DENSE_SLOTS at most, each with its values scattered into a
-// dense vector by the forward step) pull over the destination-ordered
-// slice of w_{s+1}: a warp per 128-arc window, 32 consecutive arcs a row
-// (coalesced 16-byte records), the source values gathered from the dense
-// vector, and a segmented reduction over each row's runs of equal
-// destination, so that one atomic per destination per row replaces one per
-// arc.  MAX: the exact maximum (order keys) into each destination, the
-// insert that finds it empty staging it; SUM: the fixed-point terms.  The
-// same terms as the pushes, so the same exact results.
+// dense vector by the forward step of s) pull over the destination-ordered
+// slice of w_{s+1} inside the sum launch of s+1: a warp per 128-arc window,
+// four consecutive 16-byte records per lane, the source values gathered
+// from the dense vector.  The tokens were chosen on symbols whose slice has
+// no segment longer than a window, so every destination's arcs lie in one
+// window: the warp takes each destination's exact maximum (a forward and a
+// backward segmented scan over the window's runs of equal destination),
+// its fixed-point terms and their sum (a segmented scan), and writes the
+// accumulator and stages the destination itself -- no atomics on the
+// accumulators, and the same exact terms as the pushes.
 // ======================================================================
-template <bool SUM>
-__device__ __forceinline__ void pull_windows(const TokenView& T, const FrontierState& S, const PullView& R,
-                                             int32_t s) {
+// Segmented inclusive scans over a warp's 128 elements, 4 consecutive ones
+// per lane: forward (runs start where head is set) and backward (runs end
+// where tail is set).  op is associative and commutative (max, sum).
+template <class V, class Op>
+__device__ __forceinline__ void seg_scan_fwd(V (&a)[4], const bool (&head)[4], Op op) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 1; i < 4; ++i)
+    if (!head[i]) a[i] = op(a[i - 1], a[i]);
+  V carry = a[3];
+  bool flag = head[0] || head[1] || head[2] || head[3];
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const V o = __shfl_up_sync(FULL, carry, dd);
+    const bool of = __shfl_up_sync(FULL, flag, dd);
+    if (lane >= dd) {
+      if (!flag) carry = op(o, carry);
+      flag = flag || of;
+    }
+  }
+  const V in = __shfl_up_sync(FULL, carry, 1);
+  if (lane > 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (head[i]) break;
+      a[i] = op(in, a[i]);
+    }
+  }
+}
+template <class V, class Op>
+__device__ __forceinline__ void seg_scan_bwd(V (&a)[4], const bool (&tail)[4], Op op) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 2; i >= 0; --i)
+    if (!tail[i]) a[i] = op(a[i], a[i + 1]);
+  V carry = a[0];
+  bool flag = tail[0] || tail[1] || tail[2] || tail[3];
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const V o = __shfl_down_sync(FULL, carry, dd);
+    const bool of = __shfl_down_sync(FULL, flag, dd);
+    if (lane + dd < 32) {
+      if (!flag) carry = op(carry, o);
+      flag = flag || of;
+    }
+  }
+  const V in = __shfl_down_sync(FULL, carry, 1);
+  if (lane < 31) {
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+      if (tail[i]) break;
+      a[i] = op(a[i], in);
+    }
+  }
+}
+
+__device__ __forceinline__ void pull_fused(const TokenView& T, const FrontierState& S, const PullView& R,
+                                           int32_t s) {
   const int32_t nd = __ldcg(S.dcnt + s);
   if (nd <= 0) return;
   const int lane = threadIdx.x & 31;
@@ -769,45 +827,55 @@ __device__ __forceinline__ void pull_windows(const TokenView& T, const FrontierS
     if (k < 0) break;
     const int32_t b = __ldg(T.b + p);
     const double* D = S.dvec + ((int64_t)k * 2 + (s & 1)) * S.Q;
+    const int64_t i0 = w * WIN + lane * 4;
     int4 r[4];
     float th[4];
-    double x[4];
 #pragma unroll
-    for (int row = 0; row < 4; ++row) {
-      const int64_t i = w * WIN + row * 32 + lane;
-      r[row] = __ldg(R.rec + i);
-      th[row] = __ldg(R.theta + i);
+    for (int i = 0; i < 4; ++i) {
+      r[i] = __ldg(R.rec + i0 + i);
+      th[i] = __ldg(R.theta + i0 + i);
     }
+    double v[4];
+    bool live[4];
 #pragma unroll
-    for (int row = 0; row < 4; ++row) x[row] = (r[row].z >= 0 && !dead32(th[row])) ? __ldcg(D + r[row].x) : -INFINITY;
+    for (int i = 0; i < 4; ++i) v[i] = (r[i].z >= 0 && !dead32(th[i])) ? __ldcg(D + r[i].x) : -INFINITY;
+    unsigned long long fm[4], bm[4];
 #pragma unroll
-    for (int row = 0; row < 4; ++row) {
-      const int32_t d = r[row].y;
-      const bool live = r[row].z >= 0 && !dead32(th[row]) && !dead64(x[row]);
-      const int64_t slot = acc_slot(S, b, t, d);
-      unsigned long long v = 0ull;
-      if (live) {
-        const double u = x[row] + (double)th[row];
-        v = SUM ? fix_exp64(u, dkey_inv(__ldcg(fwd_max(S, slot)))) : dkey(u);
-      }
-      // segmented reduction over the row's runs of equal destination: the
-      // run's last lane ends with its total
+    for (int i = 0; i < 4; ++i) {
+      live[i] = !dead64(v[i]);
+      if (live[i]) v[i] += (double)th[i];
+      fm[i] = bm[i] = live[i] ? dkey(v[i]) : 0ull;
+    }
+    // runs of equal destination
+    const int32_t prev = __shfl_up_sync(FULL, r[3].y, 1), next = __shfl_down_sync(FULL, r[0].y, 1);
+    bool head[4], tail[4];
 #pragma unroll
-      for (int dd = 1; dd < 32; dd <<= 1) {
-        const unsigned long long o = __shfl_up_sync(FULL, v, dd);
-        const int32_t od = __shfl_up_sync(FULL, d, dd);
-        if (lane >= dd && od == d) v = SUM ? v + o : (o > v ? o : v);
+    for (int i = 0; i < 4; ++i) {
+      head[i] = i == 0 ? (lane == 0 || prev != r[0].y) : r[i].y != r[i - 1].y;
+      tail[i] = i == 3 ? (lane == 31 || next != r[3].y) : r[i].y != r[i + 1].y;
+    }
+    auto mx = [](unsigned long long x, unsigned long long y) { return x > y ? x : y; };
+    auto add = [](unsigned long long x, unsigned long long y) { return x + y; };
+    seg_scan_fwd(fm, head, mx);
+    seg_scan_bwd(bm, tail, mx);
+    unsigned long long e[4], M[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      M[i] = mx(fm[i], bm[i]);  // the run's maximum, at every element of the run
+      e[i] = live[i] ? fix_exp64(v[i], dkey_inv(M[i])) : 0ull;
+    }
+    seg_scan_fwd(e, head, add);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      // the run's last element writes its destination's accumulator
+      const bool want = tail[i] && M[i] != 0ull;
+      if (want) {
+        const int64_t slot = acc_slot(S, b, t, r[i].y);
+        *fwd_max(S, slot) = M[i];
+        *fwd_sum(S, slot) = e[i];
       }
-      const int32_t nd_next = __shfl_down_sync(FULL, d, 1);
-      const bool leader = (lane == 31 || nd_next != d) && v != 0ull;
-      bool first = false;
-      if (SUM) {
-        if (leader) atomicAdd(fwd_sum(S, slot), v);
-      } else {
-        if (leader) first = atomicMax(fwd_max(S, slot), v) == 0ull;
-        const uint32_t i = warp_stage_index(S.scnt, p + 1, first);
-        if (first) fwd_stage(S, t)[__ldg(T.stf + p + 1) + i] = d;
-      }
+      const uint32_t j = warp_stage_index(S.scnt, p + 1, want);
+      if (want) fwd_stage(S, t)[__ldg(T.stf + p + 1) + j] = r[i].y;
     }
   }
 }
@@ -879,14 +947,15 @@ __device__ __forceinline__ void sum_push(const LayoutView& L, const FrontierStat
 
 // Forward sum of position t: with every maximum M_d final, each live arc
 // adds exp(r_{t-1}[src] + theta - M_d) to its destination in fixed point.
+template <bool PULL>
 __device__ __forceinline__ void sum_position(const LayoutView& L, const TokenView& T, const StepView& V,
                                              const FrontierState& S, const PullView& R,
                                              BlockScratch<PushCtx>& sh) {
   const int lane = threadIdx.x & 31;
   const int32_t t = V.t;
-  const bool pull = S.dense_min > 0 && t >= 2;
+  const bool pull = PULL && S.dense_min > 0 && t >= 2;
   // the dense tokens of t-1 by the pull; their entries push nothing here
-  if (pull) pull_windows<true>(T, S, R, t - 1);
+  if (pull) pull_fused(T, S, R, t - 1);
   int64_t R0, R1;
   source_range(V, S, &R0, &R1);
   for (int64_t cb = R0 + (int64_t)blockIdx.x * KT; cb < R1; cb += (int64_t)gridDim.x * KT) {
@@ -907,22 +976,16 @@ __device__ __forceinline__ void sum_position(const LayoutView& L, const TokenVie
     }
     sum_push(L, S, t, sh, e0, len, me);
   }
+  // with the direction switch, this launch hands out the pool ranges of t
+  // (the pull staged destinations of t above)
+  if (pull) ranges_last_block(T, V, S, S.scnt, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
+                              S.step_rng + 2 * t);
 }
 
 __global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepView V, FrontierState S,
                                                 PullView R) {
   __shared__ BlockScratch<PushCtx> sh;
-  sum_position(L, T, V, S, R, sh);
-}
-
-// The pull of position V.t (direction switch), then its pool ranges; a
-// position whose predecessor has no dense token was handed out by the
-// forward step (block-uniform exit).
-__global__ void __launch_bounds__(KT) k_fwd_pull(TokenView T, StepView V, FrontierState S, PullView R) {
-  if (__ldcg(S.dcnt + V.t - 1) <= 0) return;
-  pull_windows<false>(T, S, R, V.t - 1);
-  ranges_last_block(T, V, S, S.scnt, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt,
-                    S.step_rng + 2 * V.t);
+  sum_position<true>(L, T, V, S, R, sh);
 }
 
 // ======================================================================
@@ -1221,7 +1284,7 @@ __global__ void __launch_bounds__(KT) k_fwd_persist(LayoutView L, TokenView T, W
   first_position<false>(L, T, step_at(D, 1, 0), S, sh);
   if (!grid_sync(G, S.flags + 1)) return;
   for (int32_t t = 1; t <= D.tmax; ++t) {
-    sum_position(L, T, step_at(D, t, t - 1), S, PullView{nullptr, nullptr, nullptr}, sh);
+    sum_position<false>(L, T, step_at(D, t, t - 1), S, PullView{nullptr, nullptr, nullptr}, sh);
     if (!grid_sync(G, S.flags + 1)) return;
     step_position<false>(L, T, step_at(D, t, t + 1), S, sh);
     if (!grid_sync(G, S.flags + 1)) return;
@@ -1563,12 +1626,6 @@ int launch_fwd_sum(const LayoutView& L, const TokenView& T, const StepView& V, c
   if (S.dense_min > 0) g = std::max(g, (unsigned)std::min(V.blocks * 4, 2048));  // room for the pull's windows
   k_fwd_sum<<<g, KT, 0, s>>>(L, T, V, S, R);
   return check_launch("k_fwd_sum");
-}
-
-int launch_fwd_pull(const TokenView& T, const StepView& V, const FrontierState& S, const PullView& R, int num_sms,
-                    cudaStream_t s) {
-  k_fwd_pull<<<(unsigned)std::max(1, num_sms * 4), KT, 0, s>>>(T, V, S, R);
-  return check_launch("k_fwd_pull");
 }
 
 int launch_bwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,

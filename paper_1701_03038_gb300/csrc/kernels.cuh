@@ -90,10 +90,11 @@ struct FrontierState {
   uint64_t hmask;
   // Direction switch of the forward pass (dense accumulators, launch
   // driver; dense_min = 0: off).  A token with at least dense_min live
-  // states, whose string goes on, gets one of DENSE_SLOTS dense value
-  // vectors for its position: the forward step scatters its values there
-  // instead of pushing its arcs, and the next position pulls over the
-  // destination-ordered slice.  dvec [DENSE_SLOTS][2][Q] float64 (-inf
+  // states, whose string goes on and whose next symbol's slice has no
+  // segment longer than a window (pull_lseg), gets one of DENSE_SLOTS dense
+  // value vectors for its position: the forward step scatters its values
+  // there instead of pushing its arcs, and the next position pulls over
+  // the destination-ordered slice.  dvec [DENSE_SLOTS][2][Q] float64 (-inf
   // between uses), dslot [N] the slot of each token (-1: none), dlist
   // [T+2][DENSE_SLOTS] the dense tokens of each position, dcnt [T+2] their
   // number.
@@ -101,6 +102,7 @@ struct FrontierState {
   int32_t* dslot;
   int32_t* dlist;
   int32_t* dcnt;
+  const int64_t* pull_lseg;  // [m+1] long segments of the destination-ordered slices before each symbol
   int32_t dense_min;
   const int32_t* src_by_id;          // [A] source state of each arc
   int32_t* stage;                    // staged destinations of positions of even parity
@@ -187,15 +189,13 @@ int launch_vit_step(const LayoutView& L, const TokenView& T, const StepView& V, 
 int launch_fwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                     cudaStream_t s);
 // Forward sum of position t: the live states of t-1 (V.x_*) add
-// exp(value - maximum) of each arc to its destination's accumulator (the
-// dense tokens of t-1 by the pull over R).
+// exp(value - maximum) of each arc to its destination's accumulator.  With
+// the direction switch, the dense tokens of t-1 pull over R (maxima, terms
+// and sums of their destinations at once), and the last block hands out
+// the pool ranges of t.
 int launch_fwd_sum(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                    const PullView& R, cudaStream_t s);
-// The pull of position V.t (direction switch): the dense tokens of V.t - 1
-// take the maximum into every destination of their slice on w_t and stage
-// the live ones; the last block hands out the pool ranges of V.t.
-int launch_fwd_pull(const TokenView& T, const StepView& V, const FrontierState& S, const PullView& R,
-                    int num_sms, cudaStream_t s);
+
 // Backward step of position t: for each live state q of position t-1
 // (V.x_*), beta_{t-1}[q] over its arcs on w_t, and the posterior of each of
 // those arcs.

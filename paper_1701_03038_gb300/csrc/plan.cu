@@ -279,9 +279,7 @@ int build_wave(fst_plan_s* P, Wave& W, const int64_t* h_off, const int32_t* hid,
 // The suggested threshold of the direction switch (fst_plan_set_pull(-1)):
 // half the states, at least 2,048.  A pull reads the whole slice; below
 // about half the states live the pushes touch so much less of it that they
-// win.  On the 20M-arc batch even this threshold measured slower than no
-// switch (19.0 against 17.7 ms a step: the pull's launch per position costs
-// more than it saves on the few hub positions), so plans start with it off.
+// win.
 int32_t pull_default(const fst_s* f) { return std::max<int32_t>(2048, f->Q / 2); }
 
 // The waves' token tables in the plan's token arena (grown when the one
@@ -341,6 +339,7 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
     S.dslot = P->dslot;
     S.dlist = P->dlist;
     S.dcnt = P->dcnt;
+    S.pull_lseg = P->fst->fwd.sym_lseg;
     S.dense_min = (int32_t)(P->pull_min > 0 ? std::min<int64_t>(P->pull_min, INT32_MAX) : pull_default(P->fst));
   }
   if (P->compact) {
@@ -491,10 +490,7 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
     for (int32_t t = 1; t <= W.tmax; ++t) {
       PROF(FST_PROF_FWD_SUM, launch_fwd_sum(L, T, wave_step(P, W, t, t - 1), S, R, s));
       PROF(FST_PROF_FWD_STEP, launch_fwd_step(L, T, wave_step(P, W, t, t + 1), S, s));
-      // direction switch: the dense tokens of t pull into t+1, whose pool
-      // ranges this launch then hands out
-      if (S.dense_min > 0 && t < W.tmax)
-        PROF(FST_PROF_FWD_STEP, launch_fwd_pull(T, wave_step(P, W, t + 1, 0), S, R, f->num_sms, s));
+
     }
   }
   PROF(FST_PROF_FB_FINAL, launch_fb_final(S, W.Bw, P->logz + W.b0, d_status ? d_status + W.b0 : nullptr, s));
@@ -954,10 +950,9 @@ extern "C" int fst_plan_info(const fst_plan_t* P, int32_t* num_strings, int64_t*
     // overflow clear, first push, one step per position, final, backtrace
     vl += (int64_t)w.tmax + 4;
     // overflow clear, first push, sum and step per position, final; one
-    // backward step per position (and, compact, the clear of position 1;
-    // with the direction switch, a pull per position but the first)
+    // backward step per position (and, compact, the clear of position 1)
     fl += 3 * (int64_t)w.tmax + 3 + ((P->compact && w.tmax >= 2) ? 1 : 0);
-    if (P->dvec && P->pull_min != 0 && w.tmax >= 2) fl += w.tmax - 1;
+
   }
   fl += 1;  // counts out
   if (num_strings) *num_strings = P->B;
