@@ -63,7 +63,7 @@ WORKLOADS = {
 PERSIST_NAMES = {"vit": "k_vit_persist", "fwd": "k_fwd_persist", "bwd": "k_bwd_persist"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 # the files that decide what the step kernels read and write
-KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "store.cu", "plan.cu")
+KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "store.cu")  # the device code of the batched passes
 PASS_KERNELS = {"vit": ("vit_first", "vit_step"), "fwd": ("fwd_first", "fwd_sum", "fwd_step"),
                 "bwd": ("bwd_step",)}
 KERNEL_NAMES = {"vit_first": "k_vit_first", "vit_step": "k_vit_step", "fwd_first": "k_fwd_first",

@@ -645,12 +645,21 @@ static int plan_create_parts(fst_t* f, const int32_t* hid, const int64_t* h_off,
 
 // fn(i) for every part i: from one host thread per part (the caller's
 // taking part 0), so that the parts' launches are issued in parallel, or
-// one after the other while the stream is being recorded into a graph.
+// one after the other while the stream is being recorded into a graph, or
+// when FSTGPU_PART_THREADS=0 (a profiler that selects launches by a range
+// of the calling thread then sees them all).
+static bool part_threads_on() {
+  static const bool on = [] {
+    const char* e = std::getenv("FSTGPU_PART_THREADS");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 template <class Fn>
 static int parts_each(fst_plan_s* P, cudaStream_t s, Fn fn) {
   const size_t n = P->parts.size();
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  bool threads = n > 1;
+  bool threads = n > 1 && part_threads_on();
   if (threads && (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)) {
     (void)cudaGetLastError();
     threads = false;
