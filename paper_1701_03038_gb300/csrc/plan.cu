@@ -162,6 +162,12 @@ struct fst_plan_s {
   int32_t driver = FST_DRIVER_LAUNCH;
   int32_t persist_grid = 0;          // 0: the plan's estimate, capped at what is co-resident
   int32_t density = 64;              // launch driver: live states per token assumed when sizing a grid
+  // launch driver, single-wave plans: the live states of every position
+  // read back after a completed run (pool ranges), which size the grids of
+  // the later runs' launches instead of the density estimate
+  std::vector<int64_t> live;
+  bool learned = false, ran = false;
+  cudaEvent_t run_event = nullptr;   // recorded at the end of each run outside a graph capture
   uint64_t barrier_limit_ns = 2000000000ull;
   uint32_t barrier_extra = 0;        // fault injection: blocks a barrier waits for beyond the grid
   uint32_t* gbar = nullptr;          // [2] grid barrier (arrivals, generation)
@@ -178,6 +184,7 @@ struct fst_plan_s {
     for (fst_plan_s* q : parts) delete q;
     for (cudaStream_t st : part_stream) cudaStreamDestroy(st);
     for (cudaEvent_t e : part_event) cudaEventDestroy(e);
+    if (run_event) cudaEventDestroy(run_event);
     if (borrowed_counts) cnt64 = start64 = final64 = nullptr;
     for (Wave& w : waves) w.release();
 #define PLAN_FREE(x) dfree(x);
@@ -404,10 +411,53 @@ StepView wave_step(const fst_plan_s* P, const Wave& W, int32_t t, int32_t x_t) {
   V.x_t = hasx ? x_t : 0;
   V.x_slot0 = hasx ? W.step0[x_t] : 0;
   V.x_n = hasx ? W.step0[x_t + 1] - W.step0[x_t] : 0;
-  const int64_t est = (int64_t)std::max(V.n, V.x_n) * P->density;
+  int64_t est = (int64_t)std::max(V.n, V.x_n) * P->density;
+  if (P->learned) {
+    // the live states the launch walks: those of t-1 for the sums and the
+    // backward steps, those of t for the forward steps
+    const int32_t u = (x_t == t - 1) ? t - 1 : t;
+    est = (u >= 1 && u < (int32_t)P->live.size()) ? P->live[u] : est;
+  }
   V.blocks = (int32_t)std::min<int64_t>((int64_t)P->fst->num_sms * 8, std::max<int64_t>(1, (est + 255) / 256));
   V.y_t = 0;
   return V;
+}
+
+// Learn the live states of every position from the last completed run (a
+// single-wave plan, outside a graph capture); no waiting: a run still in
+// flight leaves the estimate in place until a later call.
+void plan_learn(fst_plan_s* P, cudaStream_t s) {
+  if (P->learned || !P->ran || P->waves.size() != 1 || !P->run_event) return;
+  if (cudaEventQuery(P->run_event) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return;
+  }
+  const Wave& W = P->waves[0];
+  std::vector<int64_t> rng(2 * ((size_t)W.tmax + 2));
+  if (cudaMemcpy(rng.data(), P->step_rng, rng.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return;
+  }
+  P->live.assign((size_t)W.tmax + 2, 0);
+  for (int32_t t = 1; t <= W.tmax; ++t) P->live[t] = std::max<int64_t>(0, rng[2 * t + 1] - rng[2 * t]);
+  P->learned = true;
+  (void)s;
+}
+
+// A run ended: mark it, outside a graph capture, for plan_learn.
+void plan_ran(fst_plan_s* P, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    return;
+  }
+  if (!P->run_event && cudaEventCreateWithFlags(&P->run_event, cudaEventDisableTiming) != cudaSuccess) {
+    (void)cudaGetLastError();
+    P->run_event = nullptr;
+    return;
+  }
+  if (cudaEventRecord(P->run_event, s) == cudaSuccess) P->ran = true;
+  else (void)cudaGetLastError();
 }
 
 // State that starts every pass of a wave at zero.  A pass whose pool
@@ -451,6 +501,7 @@ int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_p
                      int32_t* d_status, cudaStream_t s) {
   fst_s* f = P->fst;
   int rc;
+  plan_learn(P, s);
   const LayoutView L = view_of(f->bwd);
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, nullptr);
@@ -466,6 +517,7 @@ int run_viterbi_wave(fst_plan_s* P, const Wave& W, float* d_scores, int32_t* d_p
        launch_vit_final(S, W.Bw, d_scores + W.b0, P->jfinal, d_status ? d_status + W.b0 : nullptr, s));
   PROF(FST_PROF_BACKTRACE, launch_backtrace(S, f->olabel, W.Bw, P->jfinal, d_paths + W.tok0,
                                             d_olabels ? d_olabels + W.tok0 : nullptr, s));
+  plan_ran(P, s);
   return FST_OK;
 }
 
@@ -478,6 +530,7 @@ PullView pull_view(const fst_plan_s* P) {
 int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_status) {
   fst_s* f = P->fst;
   int rc;
+  plan_learn(P, s);
   const LayoutView L = view_of(f->bwd);
   const TokenView T = wave_tokens(W);
   const FrontierState S = wave_state(P, W, nullptr);
@@ -494,6 +547,7 @@ int run_forward_wave(fst_plan_s* P, const Wave& W, cudaStream_t s, int32_t* d_st
     }
   }
   PROF(FST_PROF_FB_FINAL, launch_fb_final(S, W.Bw, P->logz + W.b0, d_status ? d_status + W.b0 : nullptr, s));
+  plan_ran(P, s);
   return FST_OK;
 }
 
