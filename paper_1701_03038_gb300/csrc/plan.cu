@@ -428,20 +428,26 @@ StepView wave_step(const fst_plan_s* P, const Wave& W, int32_t t, int32_t x_t) {
 // flight leaves the estimate in place until a later call.
 void plan_learn(fst_plan_s* P, cudaStream_t s) {
   if (P->learned || !P->ran || P->waves.size() != 1 || !P->run_event) return;
+  // nothing that would break a graph capture of this run
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    return;
+  }
   if (cudaEventQuery(P->run_event) != cudaSuccess) {
     (void)cudaGetLastError();
     return;
   }
   const Wave& W = P->waves[0];
   std::vector<int64_t> rng(2 * ((size_t)W.tmax + 2));
-  if (cudaMemcpy(rng.data(), P->step_rng, rng.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+  if (cudaMemcpyAsync(rng.data(), P->step_rng, rng.size() * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
     (void)cudaGetLastError();
     return;
   }
   P->live.assign((size_t)W.tmax + 2, 0);
   for (int32_t t = 1; t <= W.tmax; ++t) P->live[t] = std::max<int64_t>(0, rng[2 * t + 1] - rng[2 * t]);
   P->learned = true;
-  (void)s;
 }
 
 // A run ended: mark it, outside a graph capture, for plan_learn.
