@@ -735,6 +735,34 @@ def e2e_batch(args, world, dev, fa, strs, f, s_v, s_f, relax_step):
                    "built per call; device storage kept from the previous call of the same kind)"}
 
 
+def plain_launches(f, strs, stats, coef) -> int:
+    """Kernel launches of one plain step, from the method and driver the
+    handle takes (fst_get_plain_method) and the launch sites of each: the
+    one-block kernels one launch per call; the slice-wide Viterbi one per
+    non-empty slice + final + output labels; the frontier Viterbi first +
+    n steps + final + backtrace (one persistent pass + 2 with that
+    driver); the frontier forward-backward first + n (sum + step) + final
+    + n backward steps + counts (persistent: 2 passes + 2)."""
+    from paper_1701_03038_gb300 import _lib
+    pm = f.plain_method()
+    if pm["method"] == _lib.PLAIN_BLOCK:
+        return 2 * strs.count
+    persist = pm["driver"] == _lib.DRIVER_PERSISTENT
+    total = 0
+    for b in range(strs.count):
+        x = strs.get(b)
+        n = len(x)
+        arcs = int(stats[0][x].sum())
+        slice_vit = pm["method"] == _lib.PLAIN_SLICE or (
+            pm["method"] == _lib.PLAIN_AUTO and coef[2] + coef[3] * n + coef[4] * arcs < coef[0] + coef[1] * n)
+        if slice_vit:
+            total += int((stats[0][x] > 0).sum()) + 1 + (n > 0)
+        else:
+            total += (3 if n >= 1 else 2) if persist else n + 3 - (n == 0)
+        total += (4 if n >= 1 else 2) if persist else 3 * n + 3 - (n == 0)
+    return total
+
+
 def bench_plain(args, rank, world, dev, fa, strs, f, stats):
     """The plain method: one string at a time through the host API
     (fst_viterbi + fst_forward_backward with posteriors), one launch per
@@ -755,9 +783,7 @@ def bench_plain(args, rank, world, dev, fa, strs, f, stats):
             f.forward_backward(x)
 
     ms, clk = timed(step, args, world, dev, ClockSampler(int(str(dev).split(":")[-1])))
-    # launches per string: Viterbi n+3, forward-backward 3n+3
-    lens = np.diff(strs.offsets)
-    launches = int((lens + 3).sum() + (3 * lens + 3).sum())
+    launches = plain_launches(f, strs, stats, coef)
     out = base_line(args, world, fa, strs, ms, relax_step, clk, args.steps * launches)
     out["config"].update({"parallelism": "replicas" if world > 1 else "1 GPU",
                           "launch": "host launches, one string at a time (fst_viterbi, fst_forward_backward)",

@@ -176,6 +176,17 @@ FST_API int fst_autotune_plain(fst_t* fst, const int32_t* ids, const int64_t* of
  * without cooperative launches or for a grid that cannot be co-resident. */
 FST_API int fst_set_plain_driver(fst_t* fst, int32_t driver, int32_t grid_blocks);
 
+/* What the single-string calls take now, for accounting (host only, no
+ * device work): *method = FST_PLAIN_BLOCK when fst_viterbi and
+ * fst_forward_backward run the one-block kernels (set, or chosen by
+ * fst_autotune_plain); FST_PLAIN_SLICE or FST_PLAIN_FRONTIER when set;
+ * FST_PLAIN_AUTO when each fst_viterbi call chooses between those two by
+ * the calibrated cost model (fst_autotune_plain's coefficients); an
+ * uncalibrated FST_PLAIN_AUTO reads FST_PLAIN_FRONTIER.  *driver and
+ * *grid_blocks are the frontier kernels' driver (fst_set_plain_driver).
+ * Any output pointer may be NULL.  FST_ERR_INVALID_ARG for a NULL handle. */
+FST_API int fst_get_plain_method(const fst_t* fst, int32_t* method, int32_t* driver, int32_t* grid_blocks);
+
 /* The paper's relaxation, kept for comparison (Sec. 5.1): Viterbi of one
  * string where, at every position, each arc of the slice delta[w_t] is
  * relaxed by its own thread whether or not its source is live, and
@@ -562,6 +573,16 @@ FST_API int fst_plan_limit_pool(fst_plan_t* plan, int64_t entries);
  * the pull's launch per position costing more than it saves); -1 =
  * max(2048, num_states / 2); else the threshold. */
 FST_API int fst_plan_set_pull(fst_plan_t* plan, int64_t min_live);
+
+/* Bounds-checked build.  A library compiled with -DFST_DEBUG (build.py's
+ * build_debug) checks, in the frontier kernels, every computed index into
+ * the staging buffers, the live pool, the dense accumulators and the arc
+ * records against its buffer's size; a violation is counted, the first is
+ * recorded (code: 1 staging, 2 pool write, 3 pool read, 4 dense
+ * accumulator, 5 arc record; its index and the bound) and the access is
+ * skipped.  This call reads the record (host outputs, any may be NULL) and
+ * clears it.  FST_ERR_UNSUPPORTED in a normal build. */
+FST_API int fst_debug_checks(int64_t* violations, int32_t* code, int64_t* index, int64_t* bound);
 
 /* Compact accumulators: cap the hash tables of the plan's following runs at
  * `slots` slots each (rounded down to a power of two, at least 2; 0 = the capacity

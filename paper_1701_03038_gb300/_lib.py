@@ -42,6 +42,7 @@ SIGNATURES = {
     "fst_viterbi_slice": [vp, vp, i32, vp, vp],
     "fst_set_plain_method": [vp, i32],
     "fst_set_plain_driver": [vp, i32, i32],
+    "fst_get_plain_method": [vp, vp, vp, vp],
     "fst_autotune_plain": [vp, vp, vp, i32, vp],
     "fst_forward_backward_slice": [vp, vp, i32, vp, vp],
     "fst_set_slice_order": [vp, i32],
@@ -61,6 +62,7 @@ SIGNATURES = {
     "fst_plan_limit_pool": [vp, i64],
     "fst_plan_limit_table": [vp, i64],
     "fst_plan_set_pull": [vp, i64],
+    "fst_debug_checks": [vp, vp, vp, vp],
     "fst_plan_table_slots": [vp, vp],
     "fst_set_batch_budget": [vp, i64],
     "fst_set_batch_plan": [vp, i32, i32, i32, i32],

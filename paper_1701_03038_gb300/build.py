@@ -83,3 +83,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), out_path: 
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+
+
+def build_debug(out_path: str | None = None) -> str:
+    """The bounds-checked variant (-DFST_DEBUG): the frontier kernels check
+    their computed indices against their buffers and record violations
+    (fst_debug_checks).  Built beside the in-tree library, or at out_path;
+    load it with FSTGPU_LIB."""
+    return build(extra_flags=["-DFST_DEBUG"], out_path=out_path or os.path.join(OUT_DIR, "libfstgpu_debug.so"))

@@ -289,6 +289,8 @@ FrontierState plain_state(fst_s* f) {
   S.src_by_id = f->src_by_id;
   S.stage = w->stage;
   S.stage_b = w->stage_b;
+  S.stage_cap = w->cap_stage;
+  S.Bw = 1;
   S.scnt = w->scnt;
   S.pool_q = w->pool_q;
   S.pool_x = w->pool_x;
@@ -754,6 +756,10 @@ extern "C" int fst_forward_backward(fst_t* f, const int32_t* ids, int32_t n, dou
 }
 
 // ============================================================ measurement
+extern "C" int fst_debug_checks(int64_t* violations, int32_t* code, int64_t* index, int64_t* bound) {
+  return debug_read(violations, code, index, bound);
+}
+
 extern "C" int fst_profile(fst_t* f, int32_t enable) {
   if (!f) { set_error("fst is NULL"); return FST_ERR_INVALID_ARG; }
   f->prof.on = enable != 0;
@@ -973,6 +979,20 @@ extern "C" int fst_autotune_plain(fst_t* f, const int32_t* ids, const int64_t* o
   }
   f->plain_tuned = true;
   f->plain_method = FST_PLAIN_AUTO;
+  return FST_OK;
+}
+
+extern "C" int fst_get_plain_method(const fst_t* f, int32_t* method, int32_t* driver, int32_t* grid_blocks) {
+  if (!f) {
+    set_error("fst_get_plain_method: bad arguments");
+    return FST_ERR_INVALID_ARG;
+  }
+  int32_t m = f->plain_method;
+  if (plain_uses_block(f)) m = FST_PLAIN_BLOCK;
+  else if (m == FST_PLAIN_AUTO && !f->plain_tuned) m = FST_PLAIN_FRONTIER;
+  if (method) *method = m;
+  if (driver) *driver = f->plain_fb_driver;
+  if (grid_blocks) *grid_blocks = f->plain_fb_grid;
   return FST_OK;
 }
 

@@ -55,6 +55,28 @@ __device__ __forceinline__ int32_t run_error(uint32_t err) {
 
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
+// Bounds-checked build (FST_DEBUG): in_bounds(code, i, n) checks 0 <= i < n,
+// and on a violation counts it, records the first (code, index, bound) and
+// returns false so that the caller skips the access.  A normal build
+// compiles every check away.
+enum : int { CHK_STAGE = 1, CHK_POOL_WRITE = 2, CHK_POOL_READ = 3, CHK_ACC = 4, CHK_ARC = 5, CHK_TOKEN = 6 };
+#ifdef FST_DEBUG
+__device__ unsigned long long g_dbg[4];  // violations, code, index, bound
+__device__ __noinline__ bool in_bounds_slow(int code, long long i, long long n) {
+  if (atomicAdd(&g_dbg[0], 1ull) == 0ull) {
+    g_dbg[1] = (unsigned long long)code;
+    g_dbg[2] = (unsigned long long)i;
+    g_dbg[3] = (unsigned long long)n;
+  }
+  return false;
+}
+__device__ __forceinline__ bool in_bounds(int code, long long i, long long n) {
+  return (i >= 0 && i < n) ? true : in_bounds_slow(code, i, n);
+}
+#else
+__device__ __forceinline__ bool in_bounds(int, long long, long long) { return true; }
+#endif
+
 __device__ __forceinline__ float decode_max(uint32_t k) { return k ? fkey_inv(k) : neg_inf(); }
 
 // Owner of flat entry j among the n slots whose first entries base[0..n)
@@ -121,7 +143,11 @@ __device__ __forceinline__ Arcs find_arcs(const LayoutView& L, int32_t a, int32_
   uint64_t h = seg_hash_slot(k, L.hash_mask);
   for (int64_t probe = 0; probe <= L.hash_mask; ++probe) {
     const ulonglong2 e = __ldg(L.seg_hash + h);
-    if (e.x == k) return Arcs{(int32_t)(uint32_t)e.y, (int32_t)(e.y >> 32)};
+    if (e.x == k) {
+      const Arcs r{(int32_t)(uint32_t)e.y, (int32_t)(e.y >> 32)};
+      if (r.len > 0 && !in_bounds(CHK_ARC, (long long)r.pos + r.len - 1, L.P)) return Arcs{0, 0};
+      return r;
+    }
     if (e.x == ~0ull) break;
     h = (h + 1) & (uint64_t)L.hash_mask;
   }
@@ -453,6 +479,7 @@ __device__ __forceinline__ void block_push(const LayoutView& L, const TokenView&
     for (int u = 0; u < VU; ++u) {
       const int32_t a = a0 + u * KT + (int32_t)threadIdx.x;
       oo[u] = a < total ? block_owner(sh.excl, a) : -1;
+      if (oo[u] >= 0 && !in_bounds(CHK_ARC, (long long)sh.e0[oo[u]] + (a - sh.excl[oo[u]]), L.P)) oo[u] = -1;
       arc[u] = oo[u] >= 0 ? __ldg(L.arcs + sh.e0[oo[u]] + (a - sh.excl[oo[u]])) : make_int4(0, 0, 0, 0);
     }
     unsigned long long cand[VU];
@@ -504,7 +531,8 @@ __device__ __forceinline__ void block_push(const LayoutView& L, const TokenView&
         sv[u] = arc[u].x;
         if (cand[u] != 0ull) {
           const int64_t slot = acc_slot(S, sh.ctx[oo[u]].b, t, arc[u].x);
-          first[u] = atomicMax(VIT ? vit_key(S, slot) : fwd_max(S, slot), cand[u]) == 0ull;
+          if (in_bounds(CHK_ACC, slot, (long long)S.Bw * 2 * S.Q))
+            first[u] = atomicMax(VIT ? vit_key(S, slot) : fwd_max(S, slot), cand[u]) == 0ull;
         }
       }
     }
@@ -512,7 +540,7 @@ __device__ __forceinline__ void block_push(const LayoutView& L, const TokenView&
     for (int u = 0; u < VU; ++u) {
       const int32_t p = oo[u] >= 0 ? sh.ctx[oo[u]].p : 0;
       const uint32_t i = warp_stage_index(S.scnt, p, first[u]);
-      if (first[u]) stg[__ldg(T.stf + p) + i] = sv[u];
+      if (first[u] && in_bounds(CHK_STAGE, __ldg(T.stf + p) + i, S.stage_cap)) stg[__ldg(T.stf + p) + i] = sv[u];
     }
   }
   __syncthreads();
@@ -535,7 +563,7 @@ __device__ __forceinline__ Source source_at(const TokenView& T, const StepView& 
     x.q = __ldg(S.start_q + (int32_t)(j % S.nstart));
     x.r = (double)__ldg(S.theta_s + x.q);
     x.head = j % S.nstart == 0;
-  } else {
+  } else if (in_bounds(CHK_POOL_READ, j, S.pool_cap)) {
     const int32_t pp = __ldg(T.step_tok + V.x_slot0 + o.k);
     if (S.bw_n[__ldg(T.b + pp)] >= V.t) {
       x.p = pp + 1;
@@ -643,7 +671,8 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
     PushCtx nx{0, 0, 0.0};
     int32_t mk_p = -1;  // forward: the token and order key of this lane's value
     uint32_t mk_key = 0u;
-    if (j < R1) {
+    if (j < R1 && in_bounds(CHK_POOL_WRITE, j, S.pool_cap) &&
+        in_bounds(CHK_STAGE, __ldg(T.stf + step_entry(T, V, o, j).p) + step_entry(T, V, o, j).i, S.stage_cap)) {
       const Entry x = step_entry(T, V, o, j);
       const int32_t b = __ldg(T.b + x.p);
       const int32_t sv = __ldcg(stg + __ldg(T.stf + x.p) + x.i);  // the state, or its table slot
@@ -1667,6 +1696,24 @@ int launch_persist(K kernel, int* cap_cache, int32_t grid, GridSync G, cudaStrea
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)kernel, dim3((unsigned)grid), dim3(KT), argv, 0, s);
   if (e != cudaSuccess) return cuda_fail(e, what);
   return FST_OK;
+}
+
+int debug_read(int64_t* violations, int32_t* code, int64_t* index, int64_t* bound) {
+#ifdef FST_DEBUG
+  unsigned long long h[4] = {0, 0, 0, 0};
+  FST_CUDA(cudaMemcpyFromSymbol(h, g_dbg, sizeof(h)));
+  const unsigned long long z[4] = {0, 0, 0, 0};
+  FST_CUDA(cudaMemcpyToSymbol(g_dbg, z, sizeof(z)));
+  if (violations) *violations = (int64_t)h[0];
+  if (code) *code = (int32_t)h[1];
+  if (index) *index = (int64_t)h[2];
+  if (bound) *bound = (int64_t)h[3];
+  return FST_OK;
+#else
+  (void)violations; (void)code; (void)index; (void)bound;
+  set_error("this library was built without FST_DEBUG (no bounds checks)");
+  return FST_ERR_UNSUPPORTED;
+#endif
 }
 
 int persist_grid_limit(int which) {

@@ -13,9 +13,10 @@ struct LayoutView {
   const int4* arcs;            // [P] {destination, theta bits, caller id, 0}
   const ulonglong2* seg_hash;  // (symbol, state) -> len << 32 | first position
   int64_t hash_mask;
+  int64_t P;                   // arc records (the bounds-checked build checks against it)
 };
 
-inline LayoutView view_of(const Layout& L) { return LayoutView{L.arcs, L.seg_hash, L.hash_mask}; }
+inline LayoutView view_of(const Layout& L) { return LayoutView{L.arcs, L.seg_hash, L.hash_mask, L.P}; }
 
 // The tokens of one input position t: slots slot0 .. slot0+n-1 of the
 // step list T.step_tok (tokens of a wave in step order).  Token p is
@@ -107,6 +108,8 @@ struct FrontierState {
   const int32_t* src_by_id;          // [A] source state of each arc
   int32_t* stage;                    // staged destinations of positions of even parity
   int32_t* stage_b;                  // of odd parity
+  int64_t stage_cap;                 // entries of each staging buffer
+  int32_t Bw;                        // strings of the wave (dense accumulators: [Bw][2][Q])
   uint32_t* scnt;                    // [N] destinations staged per token
   int32_t* pool_q;                   // [cap] state
   int32_t* pool_x;                   // [cap] Viterbi: best incoming arc id; forward: first arc on the next symbol
@@ -228,6 +231,14 @@ int launch_final_posteriors(const FrontierState& S, int32_t Bw, const CountView&
 int launch_fill_neg_inf(double* p, int64_t n, cudaStream_t s);
 // out[i] = (float)in[i], i < n.
 int launch_to_float(const double* in, int64_t n, float* out, cudaStream_t s);
+// Bounds-checked build (compiled with FST_DEBUG): the kernels check every
+// computed index into the staging buffers, the live pool, the dense
+// accumulators and the arc records against its buffer's size, count the
+// violations, record the first (check code, index, bound) and skip the
+// access.  Reads and clears that record; FST_ERR_UNSUPPORTED in a normal
+// build.
+int debug_read(int64_t* violations, int32_t* code, int64_t* index, int64_t* bound);
+
 // Zero n 64-bit words of accumulators if an error bit is set in *flag: a
 // run whose pool overflowed (or that gave up at a barrier) leaves staged
 // accumulators behind.

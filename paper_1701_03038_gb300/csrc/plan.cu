@@ -368,6 +368,8 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.src_by_id = f->src_by_id;
   S.stage = P->stage;
   S.stage_b = P->stage_b;
+  S.stage_cap = P->cap_stage;
+  S.Bw = (int32_t)P->cap_bw;
   S.scnt = P->scnt;
   S.pool_q = P->pool_q;
   S.pool_x = P->pool_x;

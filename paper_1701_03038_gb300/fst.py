@@ -221,6 +221,13 @@ class Fst:
         with torch.cuda.device(self.device):
             check(self._lib.fst_set_plain_driver(self._h, int(driver), int(grid_blocks)), "fst_set_plain_driver")
 
+    def plain_method(self) -> dict:
+        """What the single-string calls take now (fst_get_plain_method):
+        {"method", "driver", "grid_blocks"}."""
+        m, d, g = C.c_int32(), C.c_int32(), C.c_int32()
+        check(self._lib.fst_get_plain_method(self._h, C.byref(m), C.byref(d), C.byref(g)), "fst_get_plain_method")
+        return {"method": m.value, "driver": d.value, "grid_blocks": g.value}
+
     def autotune_plain(self, ids, offsets) -> np.ndarray:
         """Calibrate the automatic choice of the single-string Viterbi kernels on
         sample strings (see fst_autotune_plain); returns the fitted
@@ -579,3 +586,13 @@ class Plan:
             check(self._lib.fst_plan_forward_backward(self._h, _dptr(weights), _dptr(self.logz),
                                                       _dptr(self.counts) if counts else None, _dptr(self.status),
                                                       _stream(stream)), "fst_plan_forward_backward")
+
+
+def debug_checks() -> dict:
+    """The bounds-checked build's violation record (fst_debug_checks), read
+    and cleared: {"violations", "code", "index", "bound"}.  Raises FstError
+    (UNSUPPORTED) on a normal build."""
+    lib = _lib.load()
+    v, c, i, b = C.c_int64(), C.c_int32(), C.c_int64(), C.c_int64()
+    check(lib.fst_debug_checks(C.byref(v), C.byref(c), C.byref(i), C.byref(b)), "fst_debug_checks")
+    return {"violations": v.value, "code": c.value, "index": i.value, "bound": b.value}

@@ -63,3 +63,13 @@ def test_invalid_args_rejected_without_gpu(libpath):
     rc = lib.fst_create(0, 0, None, None, None, None, None, 0, None, None, 1, 0, ctypes.byref(out))
     assert rc == _lib.INVALID_ARG and not out.value
     assert b"bad sizes" in lib.fst_last_error()
+
+
+def test_debug_checks_unsupported_in_a_normal_build(libpath):
+    # the bounds-checked record exists only in a -DFST_DEBUG build; a normal
+    # build says so (no device call is made)
+    lib = _lib.load()
+    v = ctypes.c_int64(-1)
+    rc = lib.fst_debug_checks(ctypes.byref(v), None, None, None)
+    assert rc == _lib.UNSUPPORTED and v.value == -1
+    assert b"FST_DEBUG" in lib.fst_last_error()

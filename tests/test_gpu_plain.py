@@ -340,10 +340,19 @@ def test_block_method_small_fsts():
     la, ca, _ = f.forward_backward(strs.get(0))
     lb, cb, _ = f.forward_backward(strs.get(0))
     assert la == lb and np.array_equal(ca, cb)
-    f.autotune_plain(strs.ids, strs.offsets)
+    f.set_plain_method(_lib.PLAIN_AUTO)
+    assert f.plain_method()["method"] == _lib.PLAIN_FRONTIER  # not calibrated yet
+    coef = f.autotune_plain(strs.ids, strs.offsets)
+    # coefficients all zero exactly when the calibration took the block kernels
+    assert (f.plain_method()["method"] == _lib.PLAIN_BLOCK) == (not np.any(coef))
     o = oracle.Fst(fa)
     for b in range(strs.count):
         check_string(f, o, strs.get(b))
+    for m in (_lib.PLAIN_FRONTIER, _lib.PLAIN_SLICE, _lib.PLAIN_BLOCK):
+        f.set_plain_method(m)
+        assert f.plain_method()["method"] == m
+    f.set_plain_driver(_lib.DRIVER_PERSISTENT, 4)
+    assert f.plain_method() == {"method": _lib.PLAIN_BLOCK, "driver": _lib.DRIVER_PERSISTENT, "grid_blocks": 4}
     # beyond the shared-memory limit the method is refused
     big, _ = synth.make_config("c2", scale=0.2, strings=1)  # 10,000 states
     assert big.num_states > _lib.BLOCK_MAX_STATES
