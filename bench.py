@@ -63,7 +63,7 @@ WORKLOADS = {
 PERSIST_NAMES = {"vit": "k_vit_persist", "fwd": "k_fwd_persist", "bwd": "k_bwd_persist"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 # the files that decide what the step kernels read and write
-KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "store.cu")  # the device code of the batched passes
+KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "store.cu", "fst_internal.cuh")  # the device code of the batched passes
 PASS_KERNELS = {"vit": ("vit_first", "vit_step"), "fwd": ("fwd_first", "fwd_sum", "fwd_step"),
                 "bwd": ("bwd_step",)}
 KERNEL_NAMES = {"vit_first": "k_vit_first", "vit_step": "k_vit_step", "fwd_first": "k_fwd_first",
@@ -738,7 +738,9 @@ def e2e_batch(args, world, dev, fa, strs, f, s_v, s_f, relax_step):
 def plain_launches(f, strs, stats, coef) -> int:
     """Kernel launches of one plain step, from the method and driver the
     handle takes (fst_get_plain_method) and the launch sites of each: the
-    one-block kernels one launch per call; the slice-wide Viterbi one per
+    one-block kernels one launch for Viterbi and, for forward-backward, the
+    forward and backward blocks, the posteriors (non-empty strings) and
+    their conversion (arcs > 0); the slice-wide Viterbi one per
     non-empty slice + final + output labels; the frontier Viterbi first +
     n steps + final + backtrace (one persistent pass + 2 with that
     driver); the frontier forward-backward first + n (sum + step) + final
@@ -746,7 +748,8 @@ def plain_launches(f, strs, stats, coef) -> int:
     from paper_1701_03038_gb300 import _lib
     pm = f.plain_method()
     if pm["method"] == _lib.PLAIN_BLOCK:
-        return 2 * strs.count
+        lens = np.diff(strs.offsets)
+        return int(strs.count * (3 if f.num_arcs > 0 else 2) + (lens > 0).sum())
     persist = pm["driver"] == _lib.DRIVER_PERSISTENT
     total = 0
     for b in range(strs.count):
@@ -931,9 +934,16 @@ def main():
     if not args.no_cpu and rank == 0 and world == 1:
         sel = cpu_sample(fa, strs, kind, args.cpu_seconds)
         dt, rx, th = cpu_oracle_run(fa, strs, sel, kind)
+        # a whole workload that takes under 2 s (c1: one string) is timed
+        # over repeated passes until 2 s have gone by
+        reps = 1
+        while len(sel) == strs.count and dt < 2.0:
+            d2, r2, _ = cpu_oracle_run(fa, strs, sel, kind)
+            dt, rx, reps = dt + d2, rx + r2, reps + 1
         out["cpu_baseline"] = {"value": rx / dt, "unit": UNIT, "cores": th, "kind": "oracle",
-                               "sentences_per_s": len(sel) / dt,
-                               "sample": f"first {len(sel)} strings of the workload, "
+                               "sentences_per_s": reps * len(sel) / dt,
+                               "sample": f"first {len(sel)} strings of the workload"
+                                         f"{f' ({reps} passes)' if reps > 1 else ''}, "
                                          f"{'forward-backward with counts' if kind == 'train' else 'Viterbi + forward-backward with counts'}, "
                                          f"{th} threads, {dt:.1f} s"}
     if rank == 0:

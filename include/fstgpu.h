@@ -268,7 +268,7 @@ FST_API int fst_set_batch_budget(fst_t* fst, int64_t mem_budget_bytes);
 /* Plans of fst_viterbi_batch and fst_forward_backward_batch: parts_viterbi
  * and parts_fb stream-parallel parts (FST_PLAN_PARTS; 0 = by batch size:
  * one Viterbi part per 32 strings, at most 2 and at most 400 / n, one
- * forward-backward part per 8 strings, at most 8 and at most 1,600 / n,
+ * forward-backward part per 8 strings, at most 4 and at most 1,600 / n,
  * n the longest string) and the accumulator layout (-1 = dense when
  * the dense accumulators and the live pool fit the batch budget in one
  * wave, else compact; 0 = compact; 1 = FST_PLAN_DENSE_ACC), and whether

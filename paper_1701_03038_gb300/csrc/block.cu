@@ -14,17 +14,20 @@
 //               atomicMax of Sec. 5.1, the index that of the arc in its
 //               destination-ordered slice (lowest arc id on ties, as the
 //               frontier kernels), a backpointer {arc, source} per state
-//               and position in global memory, the backtrace by one thread;
+//               and position in global memory (the sources also in shared
+//               memory when the string's rows fit), the backtrace by one
+//               thread, the path gathered by all;
 //   forward  -- two sweeps of the slice per position: the exact float64
 //               maximum of the arc values into each destination, then
 //               exp(value - maximum) added in 2^-40 fixed point, both
 //               order-independent; alpha_t in float64 to global memory;
 //   backward -- the same two sweeps into each arc's source, beta_t in
-//               shared memory, and the posterior of each arc (Alg. 2)
-//               added by the thread that owns the arc's slice position:
-//               the same thread meets the same arc whenever its symbol
-//               recurs, so the compensated float32 counts need no atomics
-//               and are bitwise repeatable.
+//               shared memory and global memory.  The backward recursion
+//               does not depend on alpha, so it runs in a second block at
+//               the same time as the forward one;
+//   posteriors -- once both have finished, a kernel over (position, slice
+//               arc) pairs adds each arc's posterior (Alg. 2) in 2^-40 fixed
+//               point (exact integer sums, bitwise repeatable).
 //
 // Values are kept unshifted in float64 (no per-position rescaling: float64
 // holds the sums of log-probabilities of any string length used here).
@@ -32,8 +35,8 @@
 // logarithm costs the warp that holds a position's live arcs on the order of
 // a microsecond, which the other warps wait out at the barrier.  The terms
 // and logarithms of the log-sums stay float64 (their accuracy carries over
-// hundreds of positions); a posterior, a float32 count, is exponentiated in
-// float32 from a float64 argument, as in the batched kernels.
+// hundreds of positions); a posterior term is exponentiated in float32 from
+// a float64 argument, as in the batched kernels.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -137,12 +140,18 @@ __global__ void __launch_bounds__(BT, 1) k_block_viterbi(const int4* __restrict_
                                                          const float* __restrict__ theta_f,
                                                          const int32_t* __restrict__ olabel, int2* __restrict__ bp,
                                                          float* __restrict__ score, int32_t* __restrict__ path,
-                                                         int32_t* __restrict__ olab, int32_t* __restrict__ status) {
+                                                         int32_t* __restrict__ olab, int32_t* __restrict__ status,
+                                                         int32_t keep) {
   extern __shared__ unsigned long long smem[];
   __shared__ unsigned long long red[BT / 32];
   __shared__ int2 rec[KR * BT];
   unsigned long long* key = smem;
   float* v = (float*)(smem + Q);
+  // keep: the state path qs[n + 1] and each position's best sources
+  // src[(t - 1) Q + q] (0xffff: none; Q <= 8192) also in shared memory, so
+  // that the backtrace walks shared rather than global memory
+  int32_t* qs = (int32_t*)(v + Q);
+  uint16_t* src = (uint16_t*)(qs + n + 1);
   for (int32_t q = threadIdx.x; q < Q; q += BT) {
     key[q] = 0ull;
     v[q] = __ldg(theta_s + q);
@@ -188,6 +197,7 @@ __global__ void __launch_bounds__(BT, 1) k_block_viterbi(const int4* __restrict_
         }
       }
       row[q] = e;
+      if (keep) src[(int64_t)(t - 1) * Q + q] = e.y < 0 ? (uint16_t)0xffff : (uint16_t)e.y;
       v[q] = k ? fkey_inv((uint32_t)(k >> 32)) : neg_inf();
       key[q] = 0ull;
     }
@@ -203,9 +213,29 @@ __global__ void __launch_bounds__(BT, 1) k_block_viterbi(const int4* __restrict_
     best = k > best ? k : best;
   }
   best = block_max_key(best, red);
+  if (threadIdx.x == 0) {
+    *score = best ? fkey_inv((uint32_t)(best >> 32)) : neg_inf();
+    *status = best ? FST_OK : FST_ERR_NO_PATH;
+  }
+  if (keep) {
+    if (threadIdx.x == 0) {
+      int32_t q = best ? (int32_t)(~(uint32_t)best) : -1;
+      for (int32_t t = n; t >= 1; --t) {
+        qs[t] = q;
+        const uint16_t p = q >= 0 ? src[(int64_t)(t - 1) * Q + q] : (uint16_t)0xffff;
+        q = p == 0xffff ? -1 : (int32_t)p;
+      }
+    }
+    __syncthreads();
+    for (int32_t t = 1 + (int32_t)threadIdx.x; t <= n; t += BT) {
+      const int32_t q = qs[t];
+      const int2 e = q >= 0 ? bp[(int64_t)(t - 1) * Q + q] : make_int2(-1, -1);
+      path[t - 1] = e.x;
+      if (olab) olab[t - 1] = e.x >= 0 ? __ldg(olabel + e.x) : -1;
+    }
+    return;
+  }
   if (threadIdx.x != 0) return;
-  *score = best ? fkey_inv((uint32_t)(best >> 32)) : neg_inf();
-  *status = best ? FST_OK : FST_ERR_NO_PATH;
   int32_t q = best ? (int32_t)(~(uint32_t)best) : -1;
   for (int32_t t = n; t >= 1; --t) {
     const int2 e = q >= 0 ? bp[(int64_t)(t - 1) * Q + q] : make_int2(-1, -1);
@@ -216,51 +246,32 @@ __global__ void __launch_bounds__(BT, 1) k_block_viterbi(const int4* __restrict_
 }
 
 // ======================================================================
-// Forward-backward (Alg. 2, Sec. 5.2).  Shared: mx[Q] (order key of the
-// float64 maximum into each state), sm[Q] (fixed-point sum), a[Q] (float64
-// alpha_{t-1}, then beta_t).  alpha[t Q + q] = alpha_t[q], t = 0..n.
+// Forward-backward (Alg. 2, Sec. 5.2).  Block 0 runs the forward pass and
+// block 1 (when posteriors are wanted) the backward pass, each with its own
+// shared mx[Q] (order key of the float64 maximum into each state), sm[Q]
+// (fixed-point sum) and a[Q] (float64 values of the previous position).
+// alpha[t Q + q] = alpha_t[q] and beta[t Q + q] = beta_t[q], t = 0..n.
 // ======================================================================
 __device__ __forceinline__ double state_value(unsigned long long m, unsigned long long s) {
   return m ? fix_log_sum64(dkey_inv(m), s) : -INFINITY;
 }
 
-// The compensated float32 sum of one arc's posterior: this thread alone
-// writes arc id (the same slice position, whenever its symbol recurs).
-__device__ __forceinline__ void add_post(float* __restrict__ cnt, float* __restrict__ comp, int32_t id, float g,
-                                         float s0, float cp) {
-  const float y = __fsub_rn(g, cp);
-  const float s1 = __fadd_rn(s0, y);
-  comp[id] = __fsub_rn(__fsub_rn(s1, s0), y);
-  cnt[id] = s1;
-}
-
-// cnt / comp [A]: the compensated sum (zeroed here); out [A]: the
-// posteriors cnt - comp (written at the end; nullptr: no posteriors).
-__global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arcs, const float* __restrict__ theta,
-                                                    const int64_t* __restrict__ sym_win,
-                                                    const int32_t* __restrict__ ids, int32_t n, int32_t Q,
-                                                    int64_t A, const float* __restrict__ theta_s,
-                                                    const float* __restrict__ theta_f, double* __restrict__ alpha,
-                                                    float* __restrict__ cnt, float* __restrict__ comp,
-                                                    float* __restrict__ out, double* __restrict__ logz,
-                                                    int32_t* __restrict__ status) {
-  extern __shared__ unsigned long long smem[];
-  __shared__ double redd[BT / 32];
-  __shared__ unsigned long long redk[BT / 32];
-  unsigned long long* mx = smem;
-  unsigned long long* sm = smem + Q;
-  double* a = (double*)(smem + 2 * Q);
+// The forward pass (block 0): alpha_0 = theta_s, then alpha_t of every
+// position; log Z and the status at the end.
+__device__ void block_forward(const int4* __restrict__ arcs, const float* __restrict__ theta,
+                              const int64_t* __restrict__ sym_win, const int32_t* __restrict__ ids, int32_t n,
+                              int32_t Q, const float* __restrict__ theta_s, const float* __restrict__ theta_f,
+                              double* __restrict__ alpha, double* __restrict__ logz, int32_t* __restrict__ status,
+                              unsigned long long* mx, unsigned long long* sm, double* a, double* redd,
+                              unsigned long long* redk) {
   for (int32_t q = threadIdx.x; q < Q; q += BT) {
     mx[q] = sm[q] = 0ull;
     a[q] = (double)__ldg(theta_s + q);
     alpha[q] = a[q];
   }
-  if (out)
-    for (int64_t i = threadIdx.x; i < A; i += BT) cnt[i] = comp[i] = 0.f;
   ArcRegs cur, nxt;
   load_arcs(cur, arcs, theta, slice_at(sym_win, ids, n, 1));
   __syncthreads();
-  // forward
   for (int32_t t = 1; t <= n; ++t) {
     const Slice sl = slice_at(sym_win, ids, n, t);
     load_arcs(nxt, arcs, theta, slice_at(sym_win, ids, n, t + 1));
@@ -330,41 +341,28 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
     *logz = lz;
     *status = mk ? FST_OK : FST_ERR_NO_PATH;
   }
-  if (!out) return;  // block-uniform
-  if (!mk) {  // no path: no posteriors
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < A; i += BT) out[i] = 0.f;
-    return;
+}
+
+// The backward pass (block 1): beta_n = theta_f, then beta_{t-1} of every
+// position from the slice of w_t, the log-sum taken into each arc's source.
+__device__ void block_backward(const int4* __restrict__ arcs, const float* __restrict__ theta,
+                               const int64_t* __restrict__ sym_win, const int32_t* __restrict__ ids, int32_t n,
+                               int32_t Q, const float* __restrict__ theta_f, double* __restrict__ beta,
+                               unsigned long long* mx, unsigned long long* sm, double* a) {
+  for (int32_t q = threadIdx.x; q < Q; q += BT) {
+    mx[q] = sm[q] = 0ull;
+    a[q] = (double)__ldg(theta_f + q);
+    beta[(int64_t)n * Q + q] = a[q];
   }
-  // backward: beta_n = theta_f
-  __syncthreads();
-  for (int32_t q = threadIdx.x; q < Q; q += BT) a[q] = (double)__ldg(theta_f + q);
+  ArcRegs cur, nxt;
   load_arcs(cur, arcs, theta, slice_at(sym_win, ids, n, n));
-  // alpha_{t-1} of each register arc's source, read one position ahead
-  double alr[KR], nalr[KR];
-#pragma unroll
-  for (int k = 0; k < KR; ++k) alr[k] = (n >= 1 && cur.r[k].z >= 0) ? alpha[(int64_t)(n - 1) * Q + cur.r[k].x] : -INFINITY;
   __syncthreads();
   for (int32_t t = n; t >= 1; --t) {
     const Slice sl = slice_at(sym_win, ids, n, t);
-    const double* al = alpha + (int64_t)(t - 1) * Q;
     load_arcs(nxt, arcs, theta, slice_at(sym_win, ids, n, t - 1));
-    // each register arc's running count, read now and used after the first
-    // sweep
-    float c0[KR], c1[KR];
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
-      const bool ok = cur.r[k].z >= 0;
-      c0[k] = ok ? cnt[cur.r[k].z] : 0.f;
-      c1[k] = ok ? comp[cur.r[k].z] : 0.f;
-    }
-    // the maxima into the sources.  Only sources live in the forward pass
-    // (alpha_{t-1} > -inf) are reduced: a dead state's beta takes part in
-    // no posterior (no arc from a live state reaches it), and skipping it
-    // keeps the float64 exponentials and logarithms to the live arcs
-#pragma unroll
-    for (int k = 0; k < KR; ++k) {
-      if (cur.r[k].z < 0 || dead64(alr[k]) || dead32(cur.th[k])) continue;
+      if (cur.r[k].z < 0 || dead32(cur.th[k])) continue;
       const double b = a[cur.r[k].y];
       if (dead64(b)) continue;
       atomicMax(mx + cur.r[k].x, dkey((double)cur.th[k] + b));
@@ -372,53 +370,98 @@ __global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arc
     for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
       const float th = __ldg(theta + i);
-      if (r.z < 0 || dead32(th) || dead64(al[r.x])) continue;
+      if (r.z < 0 || dead32(th)) continue;
       const double b = a[r.y];
       if (dead64(b)) continue;
       atomicMax(mx + r.x, dkey((double)th + b));
     }
     __syncthreads();
-    // the next position's alpha_{t-2} values, its arcs having arrived
-#pragma unroll
-    for (int k = 0; k < KR; ++k)
-      nalr[k] = (t >= 2 && nxt.r[k].z >= 0) ? alpha[(int64_t)(t - 2) * Q + nxt.r[k].x] : -INFINITY;
-    // the sums, and each arc's posterior exp(alpha_{t-1}[src] + theta +
-    // beta_t[dst] - log Z)
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
-      if (cur.r[k].z < 0 || dead64(alr[k]) || dead32(cur.th[k])) continue;
+      if (cur.r[k].z < 0 || dead32(cur.th[k])) continue;
       const double b = a[cur.r[k].y];
       if (dead64(b)) continue;
-      const double u = (double)cur.th[k] + b;
-      atomicAdd(sm + cur.r[k].x, fix_exp64(u, dkey_inv(mx[cur.r[k].x])));
-      add_post(cnt, comp, cur.r[k].z, __expf((float)((alr[k] + u) - lz)), c0[k], c1[k]);
+      atomicAdd(sm + cur.r[k].x, fix_exp64((double)cur.th[k] + b, dkey_inv(mx[cur.r[k].x])));
     }
     for (int64_t i = sl.i0 + KR * BT + threadIdx.x; i < sl.i1; i += BT) {
       const int4 r = __ldg(arcs + i);
       const float th = __ldg(theta + i);
       if (r.z < 0 || dead32(th)) continue;
-      const double x = al[r.x];
-      if (dead64(x)) continue;
       const double b = a[r.y];
       if (dead64(b)) continue;
-      const double u = (double)th + b;
-      atomicAdd(sm + r.x, fix_exp64(u, dkey_inv(mx[r.x])));
-      add_post(cnt, comp, r.z, __expf((float)((x + u) - lz)), cnt[r.z], comp[r.z]);
+      atomicAdd(sm + r.x, fix_exp64((double)th + b, dkey_inv(mx[r.x])));
     }
     __syncthreads();
+    double* row = beta + (int64_t)(t - 1) * Q;
     for (int32_t q = threadIdx.x; q < Q; q += BT) {
       a[q] = state_value(mx[q], sm[q]);
+      row[q] = a[q];
       mx[q] = sm[q] = 0ull;
     }
     __syncthreads();
     cur = nxt;
-#pragma unroll
-    for (int k = 0; k < KR; ++k) alr[k] = nalr[k];
   }
-  // every count was last written by the thread that reads it back here or
-  // by another thread before one of the barriers above
-  __syncthreads();
-  for (int64_t i = threadIdx.x; i < A; i += BT) out[i] = __fsub_rn(cnt[i], comp[i]);
+}
+
+// Block 0: the forward pass; block 1 (launched when posteriors are wanted):
+// the backward pass, which also zeroes the fixed-point counts cnt [A].
+__global__ void __launch_bounds__(BT, 1) k_block_fb(const int4* __restrict__ arcs, const float* __restrict__ theta,
+                                                    const int64_t* __restrict__ sym_win,
+                                                    const int32_t* __restrict__ ids, int32_t n, int32_t Q,
+                                                    int64_t A, const float* __restrict__ theta_s,
+                                                    const float* __restrict__ theta_f, double* __restrict__ alpha,
+                                                    double* __restrict__ beta, unsigned long long* __restrict__ cnt,
+                                                    double* __restrict__ logz, int32_t* __restrict__ status) {
+  extern __shared__ unsigned long long smem[];
+  __shared__ double redd[BT / 32];
+  __shared__ unsigned long long redk[BT / 32];
+  unsigned long long* mx = smem;
+  unsigned long long* sm = smem + Q;
+  double* a = (double*)(smem + 2 * Q);
+  if (blockIdx.x == 0) {
+    block_forward(arcs, theta, sym_win, ids, n, Q, theta_s, theta_f, alpha, logz, status, mx, sm, a, redd, redk);
+  } else {
+    for (int64_t i = threadIdx.x; i < A; i += BT) cnt[i] = 0ull;
+    block_backward(arcs, theta, sym_win, ids, n, Q, theta_f, beta, mx, sm, a);
+  }
+}
+
+// The posteriors of position t (block t - 1): for each arc of the slice of
+// w_t, gamma = exp(alpha_{t-1}[src] + theta + beta_t[dst] - log Z) added to
+// its arc's count in 2^-40 fixed point (gamma <= 1, fewer than 2^24
+// positions: no overflow).  Nothing for a string without a path.
+__global__ void __launch_bounds__(256) k_block_post(const int4* __restrict__ arcs, const float* __restrict__ theta,
+                                                    const int64_t* __restrict__ sym_win,
+                                                    const int32_t* __restrict__ ids, int32_t n, int32_t Q,
+                                                    const double* __restrict__ alpha,
+                                                    const double* __restrict__ beta,
+                                                    const double* __restrict__ logz,
+                                                    const int32_t* __restrict__ status,
+                                                    unsigned long long* __restrict__ cnt) {
+  if (*status != FST_OK) return;
+  const int32_t t = (int32_t)blockIdx.x + 1;
+  const Slice sl = slice_at(sym_win, ids, n, t);
+  const double lz = *logz;
+  const double* al = alpha + (int64_t)(t - 1) * Q;
+  const double* be = beta + (int64_t)t * Q;
+  for (int64_t i = sl.i0 + threadIdx.x; i < sl.i1; i += blockDim.x) {
+    const int4 r = __ldg(arcs + i);
+    const float th = __ldg(theta + i);
+    if (r.z < 0 || dead32(th)) continue;
+    const double x = al[r.x];
+    if (dead64(x)) continue;
+    const double b = be[r.y];
+    if (dead64(b)) continue;
+    const double u = (double)th + b;
+    const float g = __expf((float)((x + u) - lz));
+    atomicAdd(cnt + r.z, (unsigned long long)__float2ull_rn(g * 1099511627776.0f));  // 2^40
+  }
+}
+
+// out[i] = cnt[i] / 2^40 as float32.
+__global__ void k_block_post_out(const unsigned long long* __restrict__ cnt, int64_t A, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)((double)cnt[i] * 0x1p-40);
 }
 
 }  // namespace
@@ -490,11 +533,15 @@ int viterbi_block_run(fst_s* f, const int32_t* ids, int32_t n, float* best_score
   float* d_score = (float*)(d_ids + 3 * n1);
   int32_t* d_status = d_ids + 3 * n1 + 1;
   if (n > 0) FST_CUDA(cudaMemcpyAsync(d_ids, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
-  const size_t smem = (size_t)f->Q * 12;
+  // the backtrace rows in shared memory when they fit the block's limit
+  const size_t base = (size_t)f->Q * 12;
+  const size_t kept = base + 4 * ((size_t)n + 1) + 2 * (size_t)n * (size_t)f->Q;
+  const int32_t keep = kept <= (size_t)BLOCK_QMAX * 24 ? 1 : 0;
+  const size_t smem = keep ? kept : base;
   if ((rc = block_launch_setup(k_block_viterbi, 0, smem))) return rc;
   k_block_viterbi<<<1, BT, smem, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, f->theta_s, f->theta_f,
                                       f->olabel, (int2*)f->block_ws, d_score, d_path, olabels ? d_olab : nullptr,
-                                      d_status);
+                                      d_status, keep);
   FST_CUDA(cudaGetLastError());
   std::vector<int32_t> h((size_t)(2 * n1 + 2));
   FST_CUDA(cudaMemcpy(h.data(), d_path, h.size() * 4, cudaMemcpyDeviceToHost));
@@ -522,26 +569,34 @@ int fb_block_run(fst_s* f, const int32_t* ids, int32_t n, float* arc_posteriors,
   if (rc) return rc;
   const Layout& L = f->fwd;
   // block_ws: the posteriors [A floats], log Z and the status (read back
-  // with one copy), the compensated pair [2 A floats], then the forward
-  // values [(n + 1) Q]
+  // with one copy), the fixed-point counts [A], then the forward and the
+  // backward values [(n + 1) Q] each
   const int64_t A = f->A;
-  const int64_t head = (A + 1) / 2 + 2;  // 8-byte words before the pair
-  const int64_t pair = A;                // 2 A floats
-  if ((rc = block_reserve(f, n, head + pair + ((int64_t)n + 1) * f->Q))) return rc;
+  const int64_t Q = f->Q;
+  const int64_t head = (A + 1) / 2 + 2;  // 8-byte words before the counts
+  const int64_t rows = ((int64_t)n + 1) * Q;
+  if ((rc = block_reserve(f, n, head + A + 2 * rows))) return rc;
   int32_t* d_ids = f->block_ids;
   float* d_out = (float*)f->block_ws;
   double* d_logz = (double*)(f->block_ws + head - 2);
   int32_t* d_status = (int32_t*)(f->block_ws + head - 1);
-  float* d_cnt = (float*)(f->block_ws + head);
-  float* d_comp = d_cnt + A;
-  double* d_alpha = (double*)(f->block_ws + head + pair);
+  unsigned long long* d_cnt = f->block_ws + head;
+  double* d_alpha = (double*)(f->block_ws + head + A);
+  double* d_beta = d_alpha + rows;
   if (n > 0) FST_CUDA(cudaMemcpyAsync(d_ids, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
-  const size_t smem = (size_t)f->Q * 24;
+  const size_t smem = (size_t)Q * 24;
   if ((rc = block_launch_setup(k_block_fb, 1, smem))) return rc;
-  k_block_fb<<<1, BT, smem, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, A, f->theta_s, f->theta_f, d_alpha,
-                                 d_cnt, d_comp, arc_posteriors ? d_out : nullptr, d_logz, d_status);
+  // block 0 the forward pass, block 1 the backward pass (posteriors only)
+  k_block_fb<<<arc_posteriors ? 2 : 1, BT, smem, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, A, f->theta_s,
+                                                      f->theta_f, d_alpha, d_beta, d_cnt, d_logz, d_status);
   FST_CUDA(cudaGetLastError());
   if (arc_posteriors) {
+    if (n > 0)
+      k_block_post<<<(unsigned)n, 256, 0, s>>>(sv.arcs, L.theta, L.sym_win, d_ids, n, f->Q, d_alpha, d_beta, d_logz,
+                                               d_status, d_cnt);
+    if (A > 0)
+      k_block_post_out<<<(unsigned)std::min<int64_t>((A + 255) / 256, 4096), 256, 0, s>>>(d_cnt, A, d_out);
+    FST_CUDA(cudaGetLastError());
     std::vector<unsigned long long> h((size_t)head);
     FST_CUDA(cudaMemcpy(h.data(), f->block_ws, (size_t)head * 8, cudaMemcpyDeviceToHost));
     memcpy(arc_posteriors, h.data(), (size_t)A * 4);

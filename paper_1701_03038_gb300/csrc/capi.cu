@@ -291,6 +291,7 @@ FrontierState plain_state(fst_s* f) {
   S.stage_b = w->stage_b;
   S.stage_cap = w->cap_stage;
   S.Bw = 1;
+  S.chain = 1;
   S.scnt = w->scnt;
   S.pool_q = w->pool_q;
   S.pool_x = w->pool_x;

@@ -222,9 +222,12 @@ __device__ __forceinline__ unsigned long long fix_exp64(double v, double m) {
 __device__ __forceinline__ bool dead64(double v) { return __double_as_longlong(v) == (long long)0xfff0000000000000ull; }
 __device__ __forceinline__ bool dead32(float v) { return __float_as_uint(v) == 0xff800000u; }
 
-// m + log(s / 2^40), in float64.
+// m + log(s / 2^40), in float64.  A sum that is the maximal term alone
+// (s = 2^40, the usual case on a sparse frontier: one live arc into the
+// state) is m itself and takes no logarithm.
 __device__ __forceinline__ double fix_log_sum64(double m, unsigned long long s) {
-  return (m == -INFINITY || s == 0ull) ? -INFINITY : m + log((double)s * 0x1p-40);
+  if (__double_as_longlong(m) == (long long)0xfff0000000000000ull || s == 0ull) return -INFINITY;
+  return s == 1099511627776ull ? m : m + log((double)s * 0x1p-40);
 }
 
 

@@ -36,6 +36,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "kernels.cuh"
 
@@ -612,12 +613,27 @@ __device__ __forceinline__ void first_position(const LayoutView& L, const TokenV
   ranges_last_block(T, V, S, S.scnt, S.pool_top, S.pool_cap, S.slot_base, S.pool_base, S.pool_cnt, S.step_rng + 2);
 }
 
+// Chained launches of the per-position kernels (programmatic dependent
+// launch).  A step kernel launched with programmatic stream serialization
+// may be scheduled while the previous kernel of its stream still runs.  Its
+// first instruction waits until that kernel has completed and its writes
+// are visible (griddepcontrol.wait), so no access of the step precedes it;
+// then it lets the next position's kernel be scheduled in turn.  What
+// overlaps is the launch and block scheduling of position t+1 with the work
+// of position t.  Launched without the attribute, both do nothing.
+__device__ __forceinline__ void chain_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(KT) k_vit_first(LayoutView L, TokenView T, StepView V, FrontierState S) {
   __shared__ BlockScratch<PushCtx> sh;
+  chain_enter();
   first_position<true>(L, T, V, S, sh);
 }
 __global__ void __launch_bounds__(KT) k_fwd_first(LayoutView L, TokenView T, StepView V, FrontierState S) {
   __shared__ BlockScratch<PushCtx> sh;
+  chain_enter();
   first_position<false>(L, T, V, S, sh);
 }
 
@@ -752,11 +768,13 @@ __device__ __forceinline__ void step_position(const LayoutView& L, const TokenVi
 
 __global__ void __launch_bounds__(KT) k_vit_step(LayoutView L, TokenView T, StepView V, FrontierState S) {
   __shared__ BlockScratch<PushCtx> sh;
+  chain_enter();
   step_position<true>(L, T, V, S, sh);
 }
 
 __global__ void __launch_bounds__(KT) k_fwd_step(LayoutView L, TokenView T, StepView V, FrontierState S) {
   __shared__ BlockScratch<PushCtx> sh;
+  chain_enter();
   step_position<false>(L, T, V, S, sh);
 }
 
@@ -1014,6 +1032,7 @@ __device__ __forceinline__ void sum_position(const LayoutView& L, const TokenVie
 __global__ void __launch_bounds__(KT) k_fwd_sum(LayoutView L, TokenView T, StepView V, FrontierState S,
                                                 PullView R) {
   __shared__ BlockScratch<PushCtx> sh;
+  chain_enter();
   sum_position<true>(L, T, V, S, R, sh);
 }
 
@@ -1227,6 +1246,7 @@ __device__ __forceinline__ void bwd_position(const LayoutView& L, const TokenVie
 __global__ void __launch_bounds__(KT) k_bwd_step(LayoutView L, TokenView T, StepView V, FrontierState S,
                                                  CountView C) {
   __shared__ BlockScratch<BwdCtx> sh;
+  chain_enter();
   bwd_position(L, T, V, S, C, sh);
 }
 
@@ -1623,44 +1643,73 @@ inline unsigned step_grid(K kernel, int* cache, const StepView& V) {
 
 int g_grid[6] = {0, 0, 0, 0, 0, 0};
 
+// Chained launches are on unless FSTGPU_CHAIN=0.
+bool chain_on() {
+  static const bool on = [] {
+    const char* e = std::getenv("FSTGPU_CHAIN");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// Launch a step kernel (KT threads, static shared memory only), chained to
+// the previous kernel of its stream when the state asks for it: a chain of
+// one stream's positions gains the launch latency; stream-parallel parts
+// run unchained, where the early-scheduled blocks of one part would hold
+// SM slots that the other parts' running positions need.
+template <class... KArgs, class... Args>
+int launch_step(void (*kernel)(KArgs...), unsigned grid, cudaStream_t s, const char* what, bool chain,
+                Args... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(KT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = chain && chain_on() ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_fail(e, what);
+  }
+  return check_launch(what);
+}
+
 }  // namespace
 
 int launch_vit_first(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                      cudaStream_t s) {
-  k_vit_first<<<step_grid(k_vit_first, &g_grid[0], V), KT, 0, s>>>(L, T, V, S);
-  return check_launch("k_vit_first");
+  return launch_step(k_vit_first, step_grid(k_vit_first, &g_grid[0], V), s, "k_vit_first", S.chain != 0, L, T, V, S);
 }
 
 int launch_fwd_first(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                      cudaStream_t s) {
-  k_fwd_first<<<step_grid(k_fwd_first, &g_grid[1], V), KT, 0, s>>>(L, T, V, S);
-  return check_launch("k_fwd_first");
+  return launch_step(k_fwd_first, step_grid(k_fwd_first, &g_grid[1], V), s, "k_fwd_first", S.chain != 0, L, T, V, S);
 }
 
 int launch_vit_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                     cudaStream_t s) {
-  k_vit_step<<<step_grid(k_vit_step, &g_grid[2], V), KT, 0, s>>>(L, T, V, S);
-  return check_launch("k_vit_step");
+  return launch_step(k_vit_step, step_grid(k_vit_step, &g_grid[2], V), s, "k_vit_step", S.chain != 0, L, T, V, S);
 }
 
 int launch_fwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                     cudaStream_t s) {
-  k_fwd_step<<<step_grid(k_fwd_step, &g_grid[3], V), KT, 0, s>>>(L, T, V, S);
-  return check_launch("k_fwd_step");
+  return launch_step(k_fwd_step, step_grid(k_fwd_step, &g_grid[3], V), s, "k_fwd_step", S.chain != 0, L, T, V, S);
 }
 
 int launch_fwd_sum(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                    const PullView& R, cudaStream_t s) {
   unsigned g = step_grid(k_fwd_sum, &g_grid[4], V);
   if (S.dense_min > 0) g = std::max(g, (unsigned)std::min(V.blocks * 4, 2048));  // room for the pull's windows
-  k_fwd_sum<<<g, KT, 0, s>>>(L, T, V, S, R);
-  return check_launch("k_fwd_sum");
+  return launch_step(k_fwd_sum, g, s, "k_fwd_sum", S.chain != 0, L, T, V, S, R);
 }
 
 int launch_bwd_step(const LayoutView& L, const TokenView& T, const StepView& V, const FrontierState& S,
                     const CountView& C, cudaStream_t s) {
-  k_bwd_step<<<step_grid(k_bwd_step, &g_grid[5], V), KT, 0, s>>>(L, T, V, S, C);
-  return check_launch("k_bwd_step");
+  return launch_step(k_bwd_step, step_grid(k_bwd_step, &g_grid[5], V), s, "k_bwd_step", S.chain != 0, L, T, V, S, C);
 }
 
 // Largest co-resident grid of a persistent kernel on this device.

@@ -110,6 +110,7 @@ struct FrontierState {
   int32_t* stage_b;                  // of odd parity
   int64_t stage_cap;                 // entries of each staging buffer
   int32_t Bw;                        // strings of the wave (dense accumulators: [Bw][2][Q])
+  int32_t chain;                     // host only: launch the step kernels chained to their predecessor
   uint32_t* scnt;                    // [N] destinations staged per token
   int32_t* pool_q;                   // [cap] state
   int32_t* pool_x;                   // [cap] Viterbi: best incoming arc id; forward: first arc on the next symbol

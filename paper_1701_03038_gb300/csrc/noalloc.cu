@@ -172,6 +172,7 @@ extern "C" int fst_viterbi_noalloc(fst_t* f, const int32_t* ids, int32_t n, floa
   S.stage_b = stage_b;
   S.stage_cap = dmax;
   S.Bw = 1;
+  S.chain = 1;
   S.scnt = scnt;
   S.pool_q = pool_q;
   S.pool_x = pool_x;

@@ -370,6 +370,7 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.stage_b = P->stage_b;
   S.stage_cap = P->cap_stage;
   S.Bw = (int32_t)P->cap_bw;
+  S.chain = !(P->flags & PLAN_PART);  // the parts of a plan run unchained
   S.scnt = P->scnt;
   S.pool_q = P->pool_q;
   S.pool_x = P->pool_x;
@@ -619,6 +620,8 @@ inline cudaStream_t as_stream(void* p) { return (cudaStream_t)p; }
 static int plan_build(fst_t* f, const int32_t* hid, const int64_t* h_off, int32_t B, int64_t mem_budget_bytes,
                       int32_t flags, cudaStream_t s, fst_plan_s* donor, fst_plan_t** out);
 
+static bool part_threads_on();
+
 // A plan of nparts stream-parallel parts: contiguous string ranges of about
 // equal token counts, each an ordinary plan with its own stream; the count
 // accumulators (and the expected start and final states) are the parent's,
@@ -638,35 +641,82 @@ static int plan_create_parts(fst_t* f, const int32_t* hid, const int64_t* h_off,
   P->want_vit = !(flags & FST_PLAN_NO_VITERBI);
   P->want_fb = !(flags & FST_PLAN_NO_FB);
   int rc;
-  int32_t b0 = 0;
+  // the parts' string ranges: each ends where the token count reaches its
+  // share
+  std::vector<int32_t> bs((size_t)nparts + 1, 0);
   for (int32_t i = 0; i < nparts; ++i) {
-    // the part ends where the token count reaches its share
     int32_t b1 = B;
     if (i < nparts - 1) {
       const int64_t goal = (P->N * (i + 1)) / nparts;
-      b1 = b0 + 1;
+      b1 = bs[i] + 1;
       while (b1 < B - (nparts - 1 - i) && h_off[b1] < goal) ++b1;
     }
-    std::vector<int64_t> off(b1 - b0 + 1);
-    for (int32_t b = b0; b <= b1; ++b) off[b - b0] = h_off[b] - h_off[b0];
-    fst_plan_t* sub = nullptr;
-    fst_plan_s* part_donor = nullptr;
-    if (donor) std::swap(part_donor, donor->parts[i]);
-    if (part_donor && part_donor->borrowed_counts) {
+    bs[i + 1] = b1;
+  }
+  // each part's donor: the earlier plan's part of the same index
+  std::vector<fst_plan_s*> pd((size_t)nparts, nullptr);
+  for (int32_t i = 0; i < nparts; ++i) {
+    if (donor) std::swap(pd[i], donor->parts[i]);
+    if (pd[i] && pd[i]->borrowed_counts) {
       // the count accumulators belong to the donor's parent (taken below)
-      part_donor->cnt64 = part_donor->start64 = part_donor->final64 = nullptr;
-      part_donor->borrowed_counts = false;
+      pd[i]->cnt64 = pd[i]->start64 = pd[i]->final64 = nullptr;
+      pd[i]->borrowed_counts = false;
     }
-    rc = plan_build(f, hid + h_off[b0], off.data(), b1 - b0, budget > 0 ? std::max<int64_t>(budget / nparts, 1) : 0,
-                    (flags & 0xff) | PLAN_PART, s, part_donor, &sub);
-    if (rc) return rc;
-    P->parts.push_back(sub);
-    P->part_b0.push_back(b0);
-    P->part_tok0.push_back(h_off[b0]);
-    P->relax += sub->relax;
-    P->bytes += sub->bytes;
-    P->max_len = std::max(P->max_len, sub->max_len);
-    b0 = b1;
+  }
+  // what the parts would otherwise each set up on the handle or read from
+  // the device: the destination-ordered slice records (dense accumulators
+  // with forward-backward) and the budget, taken once before they are built
+  if (P->want_fb && (flags & FST_PLAN_DENSE_ACC) && (rc = slice_records_dst(f, s))) {
+    for (fst_plan_s* q : pd) delete q;
+    return rc;
+  }
+  const int64_t part_budget = budget > 0 ? std::max<int64_t>(budget / nparts, 1) : default_budget();
+  // the parts are built in parallel, one host thread each (the caller's
+  // building part 0; one after the other when FSTGPU_PART_THREADS=0):
+  // their host tables and uploads are independent
+  std::vector<fst_plan_t*> sub((size_t)nparts, nullptr);
+  std::vector<int> prc((size_t)nparts, FST_OK);
+  std::vector<std::string> perr((size_t)nparts);
+  const int dev = f->device;
+  auto build_part = [&](int32_t i) {
+    if (i > 0 && cudaSetDevice(dev) != cudaSuccess) {
+      prc[i] = cuda_fail(cudaGetLastError(), "part thread");
+      perr[i] = fst_last_error();
+      delete pd[i];
+      return;
+    }
+    std::vector<int64_t> off((size_t)(bs[i + 1] - bs[i]) + 1);
+    for (int32_t b = bs[i]; b <= bs[i + 1]; ++b) off[b - bs[i]] = h_off[b] - h_off[bs[i]];
+    prc[i] = plan_build(f, hid + h_off[bs[i]], off.data(), bs[i + 1] - bs[i], part_budget,
+                        (flags & 0xff) | PLAN_PART, s, pd[i], &sub[i]);
+    if (prc[i]) perr[i] = fst_last_error();
+  };
+  {
+    std::vector<std::thread> th;
+    const bool threads = part_threads_on();
+    for (int32_t i = 1; i < nparts && threads; ++i) th.emplace_back(build_part, i);
+    build_part(0);
+    for (int32_t i = 1; i < nparts && !threads; ++i) build_part(i);
+    for (std::thread& t : th) t.join();
+  }
+  rc = FST_OK;
+  for (int32_t i = 0; i < nparts; ++i) {
+    if (prc[i] && !rc) {
+      rc = prc[i];
+      set_error("%s", perr[i].c_str());
+    }
+  }
+  if (rc) {
+    for (fst_plan_t* q : sub) delete q;
+    return rc;
+  }
+  for (int32_t i = 0; i < nparts; ++i) {
+    P->parts.push_back(sub[i]);
+    P->part_b0.push_back(bs[i]);
+    P->part_tok0.push_back(h_off[bs[i]]);
+    P->relax += sub[i]->relax;
+    P->bytes += sub[i]->bytes;
+    P->max_len = std::max(P->max_len, sub[i]->max_len);
   }
   if (P->want_fb && donor && donor->want_fb && donor->cnt64 && donor->fst == f) {
     P->cnt64 = donor->cnt64;
@@ -925,7 +975,8 @@ static int plan_build(fst_t* f, const int32_t* hid, const int64_t* h_off, int32_
             (rc = alloc_store(P, &P->dcnt, (int64_t)P->max_len + 2)))
           break;
         if ((rc = launch_fill_neg_inf(P->dvec, (int64_t)DENSE_SLOTS * 2 * f->Q, s))) break;
-        if ((rc = slice_records_dst(f, s))) break;
+        // (a part's parent has set them up before building its parts)
+        if (!(flags & PLAN_PART) && (rc = slice_records_dst(f, s))) break;
       }
     }
     // forward: arcs on the next symbol; Viterbi with dense accumulators:
@@ -1195,7 +1246,7 @@ static void put_cached(fst_t* f, int kind, fst_plan_s* p) {
 // handle's setting (fst_set_batch_plan) or, by default, stream-parallel
 // parts by batch size (one Viterbi part per 32 strings, at most 2 and at
 // most 400 / the longest string; one forward-backward part per 8 strings,
-// at most 8 and at most 1,600 / the longest string) and dense accumulators
+// at most 4 and at most 1,600 / the longest string) and dense accumulators
 // when they fit the budget in one wave.
 static int batch_flags(fst_t* f, int kind, const int64_t* d_offsets, int32_t B, cudaStream_t s, int32_t* flags) {
   int32_t fl = kind == 0 ? FST_PLAN_NO_FB : FST_PLAN_NO_VITERBI;
@@ -1214,7 +1265,7 @@ static int batch_flags(fst_t* f, int kind, const int64_t* d_offsets, int32_t B, 
     // string's batch multiply launches that the host issues one by one
     const int64_t by_len = (kind == 0 ? 400 : 1600) / tmax;
     parts = (int32_t)std::max<int64_t>(
-        1, std::min<int64_t>(kind == 0 ? std::min(2, B / 32) : std::min(8, B / 8), by_len));
+        1, std::min<int64_t>(kind == 0 ? std::min(2, B / 32) : std::min(4, B / 8), by_len));
   }
   if (parts > 1) fl |= FST_PLAN_PARTS(parts);
   int32_t layout = f->batch_layout;

@@ -324,6 +324,12 @@ def test_block_method_small_fsts():
     fa = synth.fig1_fst()
     fa.num_isyms = 5  # symbols without arcs
     cases.append((fa, [np.array(v, np.int32) for v in ([0, 1, 2], [3], [0, 4, 2])]))
+    # 5,000 states: the Viterbi backtrace rows of a 6-position string fit in
+    # shared memory, those of a 40-position one do not
+    fa, _ = synth.make_config("c2", scale=0.1, strings=1)
+    walks = synth.make_strings(fa, 2, 6, 6, seed=11, kind="walk")
+    longw = synth.make_strings(fa, 2, 40, 40, seed=12, kind="walk")
+    cases.append((fa, [walks.get(0), walks.get(1), longw.get(0), longw.get(1)]))
     for fa, xs in cases:
         f, o = _fst(fa), oracle.Fst(fa)
         f.set_plain_method(_lib.PLAIN_FRONTIER)
