@@ -1,0 +1,109 @@
+"""Host logic of the bench's launch accounting for the plain method: the
+kernels one fst_viterbi + fst_forward_backward (with posteriors) call pair
+launches, by the method and driver the handle reports.  The expected
+sequences are written out launch by launch, in the order the single-string
+entry points issue them."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1701_03038_gb300 import _lib, synth  # noqa: E402
+
+
+class FakeFst:
+    def __init__(self, method, driver, num_arcs=10):
+        self.m = {"method": method, "driver": driver, "grid_blocks": 0}
+        self.num_arcs = num_arcs
+
+    def plain_method(self):
+        return dict(self.m)
+
+
+def frontier_viterbi(n, persistent):
+    seq = []
+    if persistent and n >= 1:
+        seq.append("k_vit_persist")
+    else:
+        if n >= 1:
+            seq.append("k_vit_first")
+        seq += ["k_vit_step"] * n
+    return seq + ["k_vit_final", "k_backtrace"]
+
+
+def frontier_fb(n, persistent):
+    seq = []
+    if persistent and n >= 1:
+        seq.append("k_fwd_persist")
+    else:
+        if n >= 1:
+            seq.append("k_fwd_first")
+        seq += ["k_fwd_sum", "k_fwd_step"] * n
+    seq.append("k_fb_final")
+    seq += ["k_bwd_persist"] if persistent and n >= 1 else ["k_bwd_step"] * n
+    return seq + ["k_counts_out"]
+
+
+def slice_viterbi(x, arcs_per_symbol):
+    seq = ["k_slice_relax" for a in x if arcs_per_symbol[a] > 0]
+    seq.append("k_slice_final")
+    if len(x) > 0:
+        seq.append("k_gather_olabels")
+    return seq
+
+
+def block_pair(n, num_arcs):
+    seq = ["k_block_viterbi", "k_block_fb"]
+    if n > 0:
+        seq.append("k_block_post")
+    if num_arcs > 0:
+        seq.append("k_block_post_out")
+    return seq
+
+
+def _case():
+    arcs_per_symbol = np.array([3, 0, 5, 1], np.int64)  # symbol 1 has no arcs
+    xs = [np.zeros(0, np.int32), np.array([0, 1, 2], np.int32), np.array([1, 1], np.int32),
+          np.array([2, 3, 0, 2, 1], np.int32)]
+    off = np.zeros(len(xs) + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in xs])
+    strs = synth.Strings(np.concatenate(xs).astype(np.int32), off)
+    return xs, strs, (arcs_per_symbol,)
+
+
+def test_block_method_counts():
+    xs, strs, stats = _case()
+    for num_arcs in (10, 0):
+        f = FakeFst(_lib.PLAIN_BLOCK, _lib.DRIVER_LAUNCH, num_arcs)
+        want = sum(len(block_pair(len(x), num_arcs)) for x in xs)
+        assert bench.plain_launches(f, strs, stats, np.zeros(5)) == want
+
+
+def test_frontier_counts_both_drivers():
+    xs, strs, stats = _case()
+    for driver in (_lib.DRIVER_LAUNCH, _lib.DRIVER_PERSISTENT):
+        p = driver == _lib.DRIVER_PERSISTENT
+        f = FakeFst(_lib.PLAIN_FRONTIER, driver)
+        want = sum(len(frontier_viterbi(len(x), p)) + len(frontier_fb(len(x), p)) for x in xs)
+        assert bench.plain_launches(f, strs, stats, np.zeros(5)) == want
+
+
+def test_slice_and_auto_counts():
+    xs, strs, stats = _case()
+    f = FakeFst(_lib.PLAIN_SLICE, _lib.DRIVER_LAUNCH)
+    want = sum(len(slice_viterbi(x, stats[0])) + len(frontier_fb(len(x), False)) for x in xs)
+    assert bench.plain_launches(f, strs, stats, np.zeros(5)) == want
+    # the calibrated choice: slice when c0 + c1 n + c2 S < d0 + d1 n
+    coef = np.array([0.0, 10.0, 5.0, 0.0, 1.0])  # frontier 10 n, slice 5 + S
+    f = FakeFst(_lib.PLAIN_AUTO, _lib.DRIVER_LAUNCH)
+    want = 0
+    for x in xs:
+        n, S = len(x), int(stats[0][x].sum())
+        v = slice_viterbi(x, stats[0]) if 5.0 + S < 10.0 * n else frontier_viterbi(n, False)
+        want += len(v) + len(frontier_fb(n, False))
+    assert bench.plain_launches(f, strs, stats, coef) == want
