@@ -115,9 +115,13 @@ def parse_args(argv=None):
 
 
 def auto_parts(args, B, tmax):
-    """The plan parts bench.py uses: the arguments, or the batch calls' rule
-    (by batch size, and at most 400 / tmax and 1,600 / tmax position
-    launches' worth, tmax the longest string)."""
+    """The plan parts of the graph-replayed device step: the arguments, or
+    by batch size (one Viterbi part per 32 strings, at most 2; one
+    forward-backward part per 8, at most 8) and at most 400 / tmax and
+    1,600 / tmax position launches' worth, tmax the longest string.  A
+    graph replays the parts' launches without host threads, so it keeps up
+    to 8 forward-backward parts where the batch calls, which issue them
+    from host threads, stop at 4."""
     tmax = max(int(tmax), 1)
     pv = args.parts_vit if args.parts_vit > 0 else max(1, min(2, B // 32, 400 // tmax))
     pf = args.parts_fb if args.parts_fb > 0 else max(1, min(8, B // 8, 1600 // tmax))
@@ -770,7 +774,8 @@ def bench_plain(args, rank, world, dev, fa, strs, f, stats):
     """The plain method: one string at a time through the host API
     (fst_viterbi + fst_forward_backward with posteriors), one launch per
     position; a step is every string of the workload.  The host API copies
-    each string in and its results out, so the step is end to end."""
+    each string in and its results out, so the step is end to end; each
+    string's posteriors go to one pinned host buffer reused by every call."""
     import torch
     from paper_1701_03038_gb300 import _lib
     relax_step = 3 * int(stats[0][strs.ids].sum())
@@ -778,24 +783,27 @@ def bench_plain(args, rank, world, dev, fa, strs, f, stats):
     # slice-wide kernels, by a cost model calibrated on the first strings
     k = min(16, strs.count)
     coef = f.autotune_plain(strs.ids[:strs.offsets[k]], strs.offsets[:k + 1])
+    # the posteriors of each string are read into one pinned host buffer
+    # (the batched e2e leg reads its results into pinned buffers too)
+    h_post = torch.empty(max(fa.num_arcs, 1), dtype=torch.float32).pin_memory().numpy()
 
     def step():
         for b in range(strs.count):
             x = strs.get(b)
             f.viterbi(x)
-            f.forward_backward(x)
+            f.forward_backward(x, out=h_post)
 
     ms, clk = timed(step, args, world, dev, ClockSampler(int(str(dev).split(":")[-1])))
     launches = plain_launches(f, strs, stats, coef)
     out = base_line(args, world, fa, strs, ms, relax_step, clk, args.steps * launches)
     out["config"].update({"parallelism": "replicas" if world > 1 else "1 GPU",
-                          "launch": "host launches, one string at a time (fst_viterbi, fst_forward_backward)",
+                          "launch": "host launches, one string at a time (fst_viterbi, fst_forward_backward; posteriors into a pinned host buffer)",
                           "l2": "no flush: the step streams every string's slices; consecutive strings share "
                                 "L2-resident arcs, as a decoding loop would"})
     h2d = strs.ids.nbytes
     d2h = 4 * strs.count + 4 * len(strs.ids) * 2 + 8 * strs.count + 4 * fa.num_arcs * strs.count
     out["e2e"] = {"value": out["value"], "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                  "ms_per_step": ms, "api": "fst_viterbi + fst_forward_backward (host buffers; copies inside)"}
+                  "ms_per_step": ms, "api": "fst_viterbi + fst_forward_backward (host buffers, the posteriors pinned; copies inside)"}
     out["us_per_sentence"] = 1000.0 * ms / strs.count
     lens = np.diff(strs.offsets)
     sl = [bool(coef[2] + coef[3] * n + coef[4] * a < coef[0] + coef[1] * n)

@@ -25,13 +25,22 @@
  *     the lowest so that results are reproducible and checkable).
  *   - Viterbi runs in float32 with one rounded addition per candidate, so
  *     its score and path are bit-identical to a sequential float32 Viterbi.
- *     Forward-backward relaxes in float32 in the log domain with a float64
- *     running per-step normaliser folded into log Z.
+ *     Forward-backward forms each arc's term from its float32 weight and
+ *     the float64 value of its source (forward) or destination (backward),
+ *     shifted by a float64 per-step normaliser folded into log Z; each
+ *     state's log-sum takes the exact maximum and adds exp(term - maximum)
+ *     in 2^-40 fixed point, so the sums do not depend on their order.
  *   - Status codes: 0 = FST_OK; every failure returns a nonzero code and
  *     sets a thread-local message readable with fst_last_error().
  *   - All entry points are host functions.  "Host" pointers are ordinary
  *     CPU memory; "device" pointers are CUDA device memory of the device
  *     that was current when the FST was created.
+ *   - Environment: FSTGPU_CHAIN=0 launches the per-position kernels
+ *     without programmatic dependent launch (by default a single-part plan
+ *     and the single-string kernels chain each position's launch to the
+ *     previous one); FSTGPU_PART_THREADS=0 builds and issues the parts of a
+ *     plan from the calling thread (by default one host thread per part);
+ *     FSTGPU_TUNE_CACHE names the autotuner's cache file.
  */
 #ifndef FSTGPU_H_
 #define FSTGPU_H_

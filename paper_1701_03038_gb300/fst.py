@@ -245,12 +245,21 @@ class Fst:
         _lib.SLICE_BY_DESTINATION (column-major) or _lib.SLICE_BY_SOURCE (row-major)."""
         check(self._lib.fst_set_slice_order(self._h, int(order)), "fst_set_slice_order")
 
-    def forward_backward(self, ids, posteriors: bool = True):
-        """(log Z float64, expected arc counts float32[A] or None, status)."""
+    def forward_backward(self, ids, posteriors: bool = True, out: np.ndarray | None = None):
+        """(log Z float64, expected arc counts float32[A] or None, status).
+        ``out``, a C-contiguous float32 host array of at least A elements
+        (for instance the numpy view of a pinned torch tensor, reused from
+        call to call), receives the counts instead of a new array; the
+        counts returned are its first A elements."""
         x = _host(ids, np.int32)
         n = int(x.shape[0])
         lz = np.zeros(1, np.float64)
-        cnt = np.zeros(max(self.num_arcs, 1), np.float32) if posteriors else None
+        if out is not None:
+            if (not isinstance(out, np.ndarray) or out.dtype != np.float32 or not out.flags.c_contiguous
+                    or out.ndim != 1 or out.shape[0] < max(self.num_arcs, 1)):
+                raise ValueError(f"out must be a contiguous float32 array of at least {max(self.num_arcs, 1)} elements")
+            posteriors = True
+        cnt = (out if out is not None else np.zeros(max(self.num_arcs, 1), np.float32)) if posteriors else None
         with torch.cuda.device(self.device):
             rc = self._lib.fst_forward_backward(self._h, _hptr(x), n, _hptr(lz),
                                                 _hptr(cnt) if posteriors else None)

@@ -136,6 +136,29 @@ def test_repeatable_bitwise():
     assert la == lb and np.array_equal(ca, cb)
 
 
+def test_posteriors_into_caller_buffer():
+    # forward_backward(out=...) writes the counts into the caller's array
+    # (here the numpy view of a pinned tensor, reused): the same values as a
+    # fresh array, for the frontier kernels and the one-block kernels
+    import torch
+    from paper_1701_03038_gb300 import _lib
+    fa, strs = synth.make_config("c2", scale=0.01, strings=3)
+    f = _fst(fa)
+    buf = torch.full((fa.num_arcs + 5,), 7.0, dtype=torch.float32).pin_memory().numpy()
+    for method in (_lib.PLAIN_FRONTIER, _lib.PLAIN_BLOCK):
+        f.set_plain_method(method)
+        for b in range(strs.count):
+            x = strs.get(b)
+            la, ca, ra = f.forward_backward(x)
+            lb, cb, rb = f.forward_backward(x, out=buf)
+            assert la == lb and ra == rb and np.array_equal(ca, cb)
+            assert np.shares_memory(cb, buf) and np.array_equal(buf[:fa.num_arcs], ca)
+    for bad in (np.zeros(fa.num_arcs - 1, np.float32), np.zeros(fa.num_arcs, np.float64),
+                np.zeros((2, fa.num_arcs), np.float32)[:, 0]):
+        with pytest.raises(ValueError):
+            f.forward_backward(strs.get(0), out=bad)
+
+
 def test_invalid_inputs():
     from paper_1701_03038_gb300._lib import FstError
     from paper_1701_03038_gb300.fst import Fst
