@@ -38,8 +38,10 @@
  *   - Environment: FSTGPU_CHAIN=0 launches the per-position kernels
  *     without programmatic dependent launch (by default a single-part plan
  *     and the single-string kernels chain each position's launch to the
- *     previous one); FSTGPU_PART_THREADS=0 builds and issues the parts of a
- *     plan from the calling thread (by default one host thread per part);
+ *     previous one; FSTGPU_CHAIN_PARTS=k chains the parts of plans of at
+ *     most k parts, default 1: parts run unchained); FSTGPU_PART_THREADS=0
+ *     builds and issues the parts of a plan from the calling thread (by
+ *     default one host thread per part);
  *     FSTGPU_TUNE_CACHE names the autotuner's cache file.
  */
 #ifndef FSTGPU_H_

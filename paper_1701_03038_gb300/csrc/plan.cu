@@ -120,6 +120,7 @@ struct fst_plan_s {
   // above): the two parity tables, then (forward-backward) the three
   // backward-value tables, cap_hslots slots each, in one allocation
   bool compact = true;
+  bool chain = true;  // launch the step kernels chained (set per part by its parent)
   int64_t hslots = 0;                  // slots this plan's busiest position needs
   int64_t table_limit = 0;             // fst_plan_limit_table: slots a run may use (0 = cap_hslots)
   unsigned long long* htab = nullptr;
@@ -370,7 +371,7 @@ FrontierState wave_state(fst_plan_s* P, const Wave& W, const float* gweight) {
   S.stage_b = P->stage_b;
   S.stage_cap = P->cap_stage;
   S.Bw = (int32_t)P->cap_bw;
-  S.chain = !(P->flags & PLAN_PART);  // the parts of a plan run unchained
+  S.chain = P->chain;
   S.scnt = P->scnt;
   S.pool_q = P->pool_q;
   S.pool_x = P->pool_x;
@@ -622,6 +623,18 @@ static int plan_build(fst_t* f, const int32_t* hid, const int64_t* h_off, int32_
 
 static bool part_threads_on();
 
+// The most parts a plan may have for its parts' step kernels to run chained
+// (FSTGPU_CHAIN_PARTS, default 1: parts run unchained, where one part's
+// early-scheduled blocks would hold SM slots that the other parts' running
+// positions need).
+static int32_t chain_parts_max() {
+  static const int32_t v = [] {
+    const char* e = std::getenv("FSTGPU_CHAIN_PARTS");
+    return e && *e ? std::max(1, atoi(e)) : 1;
+  }();
+  return v;
+}
+
 // A plan of nparts stream-parallel parts: contiguous string ranges of about
 // equal token counts, each an ordinary plan with its own stream; the count
 // accumulators (and the expected start and final states) are the parent's,
@@ -711,6 +724,7 @@ static int plan_create_parts(fst_t* f, const int32_t* hid, const int64_t* h_off,
     return rc;
   }
   for (int32_t i = 0; i < nparts; ++i) {
+    sub[i]->chain = nparts <= chain_parts_max();
     P->parts.push_back(sub[i]);
     P->part_b0.push_back(bs[i]);
     P->part_tok0.push_back(h_off[bs[i]]);
