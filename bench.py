@@ -913,11 +913,51 @@ def bench_train(args, rank, world, dev, fa, strs, f, stats):
     out.update({"relaxations_performed_per_s": job_throughput(2 * max(live["arcs"], 0), world, ms / 1000.0),
                 "live_work": live, "roofline": rl, "passes": passes,
                 "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}})
-    h2d = 0
-    d2h = 8  # the loss
-    out["e2e"] = {"value": out["value"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                  "ms_per_step": ms, "api": "LogZModule forward, loss.backward(), SGD step (weights resident)"}
+    if not args.no_e2e:
+        out["e2e"] = e2e_train(args, world, dev, fa, strs, f, 2 * relax_pass)
     return out
+
+
+def e2e_train(args, world, dev, fa, strs, f, relax_step):
+    """The training step end to end through the public API, its batch
+    copied in every step: ids and offsets from pinned host memory,
+    fst_set_weights of the current log-weights, fst_forward_backward_batch
+    with per-string weights 1/B (its counts are then minus the gradient of
+    the mean -log Z, the loss), the SGD update of the log-weights on the
+    device, and the loss read back into pinned memory.  The same step as the
+    device-timed one, which keeps its batch in a plan."""
+    import torch
+    h_ids = torch.from_numpy(strs.ids).pin_memory()
+    h_off = torch.from_numpy(strs.offsets).pin_memory()
+    h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+    B = strs.count
+    theta = torch.from_numpy(-fa.weight.astype(np.float32)).to(dev)
+    w = torch.full((B,), 1.0 / B, dtype=torch.float32, device=dev)
+    st = torch.cuda.Stream(device=dev)
+
+    def step():
+        with torch.cuda.stream(st):
+            d_ids = h_ids.to(dev, non_blocking=True)
+            d_off = h_off.to(dev, non_blocking=True)
+            f.set_weights(theta, "log")
+            r = f.forward_backward_batch(d_ids, d_off, weights=w, stream=st)
+            h_loss.copy_(-(r["logz"].sum() / B).reshape(1), non_blocking=True)
+            theta.add_(r["counts"], alpha=1e-3)  # SGD, learning rate 1e-3: theta -= lr * (-counts)
+            st.synchronize()
+
+    step()  # the batch call's storage, kept for the next call
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step()
+    dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dev)
+    barrier(world)
+    return {"value": job_throughput(relax_step, world, dt), "unit": UNIT,
+            "h2d_bytes_per_step": int(strs.ids.nbytes + strs.offsets.nbytes), "d2h_bytes_per_step": 8,
+            "ms_per_step": 1000 * dt,
+            "api": "fst_set_weights, Fst.forward_backward_batch with per-string weights 1/B (counts = minus the "
+                   "gradient of the mean -log Z), SGD on the device, the loss read back; ids and offsets from "
+                   "pinned memory every step"}
 
 
 def main():
