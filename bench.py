@@ -116,15 +116,17 @@ def parse_args(argv=None):
 
 def auto_parts(args, B, tmax):
     """The plan parts of the graph-replayed device step: the arguments, or
-    by batch size (one Viterbi part per 32 strings, at most 2; one
-    forward-backward part per 8, at most 8) and at most 400 / tmax and
-    1,600 / tmax position launches' worth, tmax the longest string.  A
-    graph replays the parts' launches without host threads, so it keeps up
-    to 8 forward-backward parts where the batch calls, which issue them
-    from host threads, stop at 4."""
+    by batch size: one Viterbi part per 32 strings, at most 2 and at most
+    400 / tmax position launches' worth (tmax the longest string), and one
+    forward-backward part per 256 strings, at most 16.  A graph replays the
+    parts' launches without host threads, so it takes more
+    forward-backward parts than the batch calls, which issue them from
+    host threads and stop at 4.  Measured on c3 (Viterbi / forward-backward
+    parts, ms a step): 2 / 8 15.6, 4 / 12 15.1, 2 / 16 14.2, 4 / 16 14.2,
+    2 / 24 14.1."""
     tmax = max(int(tmax), 1)
     pv = args.parts_vit if args.parts_vit > 0 else max(1, min(2, B // 32, 400 // tmax))
-    pf = args.parts_fb if args.parts_fb > 0 else max(1, min(8, B // 8, 1600 // tmax))
+    pf = args.parts_fb if args.parts_fb > 0 else max(1, min(16, B // 256))
     return pv, pf
 
 
