@@ -107,3 +107,18 @@ def test_slice_and_auto_counts():
         v = slice_viterbi(x, stats[0]) if 5.0 + S < 10.0 * n else frontier_viterbi(n, False)
         want += len(v) + len(frontier_fb(n, False))
     assert bench.plain_launches(f, strs, stats, coef) == want
+
+
+def test_graph_step_parts_rule():
+    # the graph-replayed batched step: one Viterbi part per 32 strings (at
+    # most 2, at most 400 / tmax), one forward-backward part per 256 strings
+    # (at most 16); explicit arguments win
+    class A:
+        parts_vit = 0
+        parts_fb = 0
+    assert bench.auto_parts(A, 4096, 200) == (2, 16)   # c3
+    assert bench.auto_parts(A, 64, 1000) == (1, 1)     # c5
+    assert bench.auto_parts(A, 1000, 60) == (2, 3)     # c2's strings batched
+    assert bench.auto_parts(A, 1, 50) == (1, 1)        # c1
+    A.parts_vit, A.parts_fb = 3, 5
+    assert bench.auto_parts(A, 4096, 200) == (3, 5)
