@@ -122,3 +122,54 @@ def test_graph_step_parts_rule():
     assert bench.auto_parts(A, 1, 50) == (1, 1)        # c1
     A.parts_vit, A.parts_fb = 3, 5
     assert bench.auto_parts(A, 4096, 200) == (3, 5)
+
+
+def _ncu_csv(path, rows):
+    import csv
+    with open(path, "w", newline="") as fh:
+        w = csv.writer(fh)
+        w.writerow(["ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value"])
+        for i, (k, m, u, v) in enumerate(rows):
+            w.writerow([str(i), k, m, u, v])
+
+
+def test_traffic_ingest_and_staleness(tmp_path, monkeypatch):
+    # per-pass DRAM bytes from an ncu launch list (units scaled, write and
+    # read summed over every launch of the pass's kernels, other kernels
+    # ignored), divided by the live-work byte model of the run's bench line;
+    # read back only for the layout measured and only while the device code
+    # is the one it was measured on
+    import json
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "traffic.json"))
+    rows = [("fstgpu::(anonymous namespace)::k_vit_step(LayoutView)", "dram__bytes_read.sum", "Mbyte", "1.5"),
+            ("fstgpu::(anonymous namespace)::k_vit_step(LayoutView)", "dram__bytes_write.sum", "Kbyte", "500"),
+            ("k_vit_first", "dram__bytes_read.sum", "byte", "1,000"),
+            ("k_fwd_sum", "dram__bytes_read.sum", "byte", "3000"),
+            ("k_fwd_step", "dram__bytes_write.sum", "byte", "7000"),
+            ("k_fwd_step", "gpu__time_duration.sum", "nsecond", "12345"),
+            ("k_bwd_step", "dram__bytes_read.sum", "Gbyte", "0.000004"),
+            ("k_counts_out", "dram__bytes_read.sum", "byte", "999999")]
+    _ncu_csv(tmp_path / "l.csv", rows)
+    E, P = 100, 250
+    line = {"live_work": {"entries": E, "arcs": P},
+            "config": {"workload": "tiny", "strings": 3, "accumulators": "dense per-string arrays"}}
+    (tmp_path / "b.json").write_text("noise\n" + json.dumps(line) + "\n")
+    bench.ingest_traffic(str(tmp_path / "l.csv"), str(tmp_path / "b.json"))
+    d = json.load(open(tmp_path / "traffic.json"))
+    assert d["source_hash"] == bench.source_hash()
+    p = d["modes"]["dense"]["passes"]
+    alg = {"vit": 12 * P + 12 * E, "fwd": 12 * P + 8 * E, "bwd": 20 * P + 12 * E}
+    assert p["vit"]["dram_bytes"] == 1_500_000 + 500_000 + 1_000
+    assert p["fwd"]["dram_bytes"] == 10_000 and p["bwd"]["dram_bytes"] == 4_000
+    for k in alg:
+        assert p[k]["algorithmic_bytes"] == alg[k]
+        assert abs(p[k]["dram_per_algorithmic_byte"] - p[k]["dram_bytes"] / alg[k]) < 1e-12
+    assert bench.load_traffic("dense")["passes"]["vit"]["dram_bytes"] == 2_001_000
+    assert bench.load_traffic("compact") is None
+    # a second layout joins the first while the hash holds
+    line["config"]["accumulators"] = "hash tables"
+    (tmp_path / "b.json").write_text(json.dumps(line) + "\n")
+    bench.ingest_traffic(str(tmp_path / "l.csv"), str(tmp_path / "b.json"))
+    assert bench.load_traffic("dense") is not None and bench.load_traffic("compact") is not None
+    monkeypatch.setattr(bench, "source_hash", lambda: "another")
+    assert bench.load_traffic("dense") is None
