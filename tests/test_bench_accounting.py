@@ -173,3 +173,32 @@ def test_traffic_ingest_and_staleness(tmp_path, monkeypatch):
     assert bench.load_traffic("dense") is not None and bench.load_traffic("compact") is not None
     monkeypatch.setattr(bench, "source_hash", lambda: "another")
     assert bench.load_traffic("dense") is None
+
+
+def test_roofline_of_the_dominant_pass():
+    # the pass with the most summed kernel time; achieved = its live-work
+    # algorithmic bytes over that time, frac against the peak, traffic the
+    # measured DRAM-per-algorithmic-byte ratio times those bytes
+    kinds = ["vit_first", "vit_step", "vit_final", "backtrace", "fwd_first", "fwd_sum", "fwd_step", "fb_final",
+             "bwd_step", "counts"]
+    prof = {k: (0.0, 0) for k in kinds}
+    prof.update({"vit_step": (2.0, 10), "vit_first": (0.5, 1), "fwd_sum": (3.0, 10), "fwd_step": (4.0, 10),
+                 "fwd_first": (0.25, 1), "bwd_step": (1.0, 10)})
+    E, P = 1_000_000, 2_000_000
+    traffic = {"passes": {"fwd": {"dram_per_algorithmic_byte": 10.0}}, "note": "n"}
+    r, passes = bench.roofline(prof, {"entries": E, "arcs": P}, 1000.0, "src", traffic)
+    fwd_bytes = 12 * P + 8 * E
+    sec = (3.0 + 4.0 + 0.25) / 1000.0
+    assert r["per"].startswith("fwd") and r["launches"] == 21 and r["pass_ms"] == 7.25
+    assert r["kernel"] == "k_fwd_first + k_fwd_sum + k_fwd_step"
+    assert r["algorithmic_bytes"] == fwd_bytes
+    assert abs(r["achieved"] - round(fwd_bytes / sec / 1e9, 2)) < 1e-9
+    assert abs(r["frac"] - round(fwd_bytes / sec / 1e9 / 1000.0, 5)) < 1e-12
+    assert r["traffic"] == int(10.0 * fwd_bytes) and r["wasted_traffic_ratio"] == 10.0
+    assert set(passes) == {"vit", "fwd", "bwd"} and passes["vit"]["ms"] == 2.5
+    # without a capture for the pass there is no traffic figure
+    r2, _ = bench.roofline(prof, {"entries": E, "arcs": P}, 1000.0, "src", None)
+    assert r2["traffic"] is None and "wasted_traffic_ratio" not in r2
+    # a persistent pass is named by its one kernel
+    r3, _ = bench.roofline(prof, {"entries": E, "arcs": P}, 1000.0, "src", None, persistent=("fwd",))
+    assert r3["kernel"] == "k_fwd_persist"
