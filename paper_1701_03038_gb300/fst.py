@@ -250,7 +250,8 @@ class Fst:
         ``out``, a C-contiguous float32 host array of at least A elements
         (for instance the numpy view of a pinned torch tensor, reused from
         call to call), receives the counts instead of a new array; the
-        counts returned are its first A elements."""
+        counts returned are its first A elements.  Passing ``out`` asks for
+        the counts whatever ``posteriors`` says."""
         x = _host(ids, np.int32)
         n = int(x.shape[0])
         lz = np.zeros(1, np.float64)
