@@ -341,6 +341,23 @@ def cpu_oracle_run(fa, strs, sel, kind):
     return dt, passes * int(A[ids].sum()), th
 
 
+def cpu_baseline(fa, strs, kind, target_s, min_s=2.0):
+    """The oracle timed on a bounded sample of the workload (about target_s
+    seconds of one pass); a whole workload that takes under min_s (c1: one
+    string) is timed over repeated passes until min_s have gone by."""
+    sel = cpu_sample(fa, strs, kind, target_s)
+    dt, rx, th = cpu_oracle_run(fa, strs, sel, kind)
+    reps = 1
+    while len(sel) == strs.count and dt < min_s:
+        d2, r2, _ = cpu_oracle_run(fa, strs, sel, kind)
+        dt, rx, reps = dt + d2, rx + r2, reps + 1
+    what = "forward-backward with counts" if kind == "train" else "Viterbi + forward-backward with counts"
+    return {"value": rx / dt, "unit": UNIT, "cores": th, "kind": "oracle",
+            "sentences_per_s": reps * len(sel) / dt,
+            "sample": f"first {len(sel)} strings of the workload{f' ({reps} passes)' if reps > 1 else ''}, "
+                      f"{what}, {th} threads, {dt:.1f} s"}
+
+
 def cpu_sample(fa, strs, kind, target_s):
     """Strings of a bounded oracle sample: grow it until one pass takes about
     target_s seconds (at least one string)."""
@@ -982,20 +999,7 @@ def main():
 
     # CPU oracle on the host cores, bounded sample (rank 0, N = 1 only)
     if not args.no_cpu and rank == 0 and world == 1:
-        sel = cpu_sample(fa, strs, kind, args.cpu_seconds)
-        dt, rx, th = cpu_oracle_run(fa, strs, sel, kind)
-        # a whole workload that takes under 2 s (c1: one string) is timed
-        # over repeated passes until 2 s have gone by
-        reps = 1
-        while len(sel) == strs.count and dt < 2.0:
-            d2, r2, _ = cpu_oracle_run(fa, strs, sel, kind)
-            dt, rx, reps = dt + d2, rx + r2, reps + 1
-        out["cpu_baseline"] = {"value": rx / dt, "unit": UNIT, "cores": th, "kind": "oracle",
-                               "sentences_per_s": reps * len(sel) / dt,
-                               "sample": f"first {len(sel)} strings of the workload"
-                                         f"{f' ({reps} passes)' if reps > 1 else ''}, "
-                                         f"{'forward-backward with counts' if kind == 'train' else 'Viterbi + forward-backward with counts'}, "
-                                         f"{th} threads, {dt:.1f} s"}
+        out["cpu_baseline"] = cpu_baseline(fa, strs, kind, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

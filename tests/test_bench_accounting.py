@@ -202,3 +202,22 @@ def test_roofline_of_the_dominant_pass():
     # a persistent pass is named by its one kernel
     r3, _ = bench.roofline(prof, {"entries": E, "arcs": P}, 1000.0, "src", None, persistent=("fwd",))
     assert r3["kernel"] == "k_fwd_persist"
+
+
+def test_cpu_baseline_sample_and_repeats():
+    # the oracle leg: a bounded sample of the workload's first strings; a
+    # whole workload shorter than the minimum is repeated until it has run
+    # that long, and the rates count every pass
+    rng = np.random.default_rng(5)
+    fa = synth.tiny_fst(rng, max_states=5, max_syms=3)
+    xs = [rng.integers(0, fa.num_isyms, size=4).astype(np.int32) for _ in range(3)]
+    off = np.zeros(4, np.int64)
+    off[1:] = np.cumsum([4, 4, 4])
+    strs = synth.Strings(np.concatenate(xs), off)
+    r = bench.cpu_baseline(fa, strs, "batch", target_s=0.01, min_s=0.05)
+    assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0
+    assert "passes)" in r["sample"] and r["sentences_per_s"] > 0
+    # relaxations of one pass: every arc of every slice, three passes
+    per_pass = 3 * int(np.bincount(fa.ilabel, minlength=fa.num_isyms)[strs.ids].sum())
+    dt, rx, _ = bench.cpu_oracle_run(fa, strs, list(range(strs.count)), "batch")
+    assert rx == per_pass and dt > 0
