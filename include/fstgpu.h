@@ -98,13 +98,13 @@ FST_API int fst_create(int32_t num_states, int64_t num_arcs, const int32_t* src,
                int32_t num_isyms, int32_t flags, fst_t** out);
 
 /* Free an FST and everything it owns.  NULL is accepted.  Plans created on
- * it must be destroyed first. */
+ * it must be destroyed first. (Resource management: no counterpart in the paper.) */
 FST_API int fst_destroy(fst_t* fst);
 
 /* Sizes of a built FST (host outputs, any may be NULL): states, arcs, input
  * symbols, padded arcs of the forward layout, windows of the forward
  * layout, destination segments (sum over symbols of distinct destinations)
- * and source segments. */
+ * and source segments. (The structures of Sec. 4 and Fig. 2, for measurement.) */
 FST_API int fst_info(const fst_t* fst, int32_t* num_states, int64_t* num_arcs, int32_t* num_isyms,
              int64_t* padded_arcs, int64_t* num_windows, int64_t* dst_segments,
              int64_t* src_segments);
@@ -118,7 +118,7 @@ FST_API int fst_symbol_stats(const fst_t* fst, int64_t* arcs, int64_t* dsts, int
  * host or device per flags).  Same validation as fst_create; on error the
  * FST keeps its old weights.  Used between training steps.  Synchronous
  * with respect to the host; call it only when no plan on this FST is
- * running. */
+ * running. The weights are the theta of Sec. 3. */
 FST_API int fst_set_weights(fst_t* fst, const float* weight, int32_t weight_kind, int32_t flags);
 
 /* Replace the start and final weights of every state ([num_states] each,
@@ -174,7 +174,8 @@ FST_API int fst_set_plain_method(fst_t* fst, int32_t method);
  * driver of the frontier kernels (fst_set_plain_driver: launches, or
  * persistent passes of 1, 8, 32 or one-per-SM blocks) is chosen by timing
  * Viterbi and forward-backward on the same strings.  coef [5] or NULL
- * receives d0, d1, c0, c1, c2 (microseconds).  Synchronous. */
+ * receives d0, d1, c0, c1, c2 (microseconds).  Synchronous. (The choice between
+ * two kernels for Sec. 5's plain method.) */
 FST_API int fst_autotune_plain(fst_t* fst, const int32_t* ids, const int64_t* offsets, int32_t B, double* coef);
 
 /* Driver of the single-string frontier kernels (fst_forward_backward, and
@@ -184,7 +185,8 @@ FST_API int fst_autotune_plain(fst_t* fst, const int32_t* ids, const int64_t* of
  * positions separated by bounded grid barriers; a barrier that times out
  * makes the call return FST_ERR_TIMEOUT).  fst_autotune_plain also picks
  * the driver and grid, by timing them on its sample.  FST_ERR_UNSUPPORTED
- * without cooperative launches or for a grid that cannot be co-resident. */
+ * without cooperative launches or for a grid that cannot be co-resident.
+ * (Sec. 5 launches one kernel per position.) */
 FST_API int fst_set_plain_driver(fst_t* fst, int32_t driver, int32_t grid_blocks);
 
 /* What the single-string calls take now, for accounting (host only, no
@@ -195,7 +197,8 @@ FST_API int fst_set_plain_driver(fst_t* fst, int32_t driver, int32_t grid_blocks
  * the calibrated cost model (fst_autotune_plain's coefficients); an
  * uncalibrated FST_PLAIN_AUTO reads FST_PLAIN_FRONTIER.  *driver and
  * *grid_blocks are the frontier kernels' driver (fst_set_plain_driver).
- * Any output pointer may be NULL.  FST_ERR_INVALID_ARG for a NULL handle. */
+ * Any output pointer may be NULL.  FST_ERR_INVALID_ARG for a NULL handle.
+ * (Accounting: no counterpart in the paper.) */
 FST_API int fst_get_plain_method(const fst_t* fst, int32_t* method, int32_t* driver, int32_t* grid_blocks);
 
 /* The paper's relaxation, kept for comparison (Sec. 5.1): Viterbi of one
@@ -240,7 +243,8 @@ FST_API int fst_set_slice_order(fst_t* fst, int32_t order);
 FST_API int fst_forward_backward(fst_t* fst, const int32_t* ids, int32_t n, double* log_z,
                          float* arc_posteriors);
 
-/* Batched method: B strings decoded together, all on the device.
+/* Batched method: Alg. 1 (Sec. 5.1) for B strings decoded together, all on
+ * the device.
  *   d_ids       device int32 [N], concatenated strings.
  *   d_offsets   device int64 [B+1], d_offsets[0] = 0, non-decreasing;
  *               string b is d_ids[d_offsets[b] .. d_offsets[b+1]).
@@ -262,7 +266,8 @@ FST_API int fst_viterbi_batch(fst_t* fst, const int32_t* d_ids, const int64_t* d
                       float* d_scores, int32_t* d_paths, int32_t* d_olabels, int32_t* d_status,
                       void* stream);
 
-/* Batched forward-backward.  Arguments as fst_viterbi_batch, plus
+/* Batched forward-backward: Alg. 2 (Sec. 5.2) for every string.  Arguments
+ * as fst_viterbi_batch, plus
  *   d_weights   device float [B] or NULL (all 1): per-string factor g_b;
  *   d_logz      device double [B];
  *   d_counts    device float [num_arcs] or NULL: sum_b g_b * count_b(k),
@@ -273,7 +278,8 @@ FST_API int fst_forward_backward_batch(fst_t* fst, const int32_t* d_ids, const i
 
 /* Storage budget of the plans that fst_viterbi_batch and
  * fst_forward_backward_batch build (0 = the fst_plan_create default).  A
- * batch whose per-string storage exceeds it runs in several waves. */
+ * batch whose per-string storage exceeds it runs in several waves. (Memory
+ * policy: no counterpart in the paper.) */
 FST_API int fst_set_batch_budget(fst_t* fst, int64_t mem_budget_bytes);
 
 /* Plans of fst_viterbi_batch and fst_forward_backward_batch: parts_viterbi
@@ -290,10 +296,11 @@ FST_API int fst_set_batch_budget(fst_t* fst, int64_t mem_budget_bytes);
  * issuing them).  The default is 0, 0, -1, -1.  A batch call keeps its
  * plan's device storage for the next call of the same kind (part by part).
  * Outside a graph capture, the parts of a plan issue their launches from
- * one host thread each. */
+ * one host thread each. (Execution policy: no counterpart in the paper.) */
 FST_API int fst_set_batch_plan(fst_t* fst, int32_t parts_viterbi, int32_t parts_fb, int32_t layout, int32_t graph);
 
-/* A plan holds everything a batch needs on the device: the token lists of
+/* A plan holds everything a batch needs on the device for the per-position
+ * loops of Alg. 1 and Alg. 2 (Sec. 5): the token lists of
  * every position (strings sorted by length), the accumulators, the live
  * pool of every position (states, values, backpointers or arcs) and the
  * per-token scalars.  The accumulators are hash tables keyed by (string,
@@ -302,7 +309,8 @@ FST_API int fst_set_batch_plan(fst_t* fst, int32_t parts_viterbi, int32_t parts_
  * holds more live states than a table fits ends the run with FST_ERR_OOM,
  * like a full pool, and leaves the plan usable.  FST_PLAN_DENSE_ACC gives
  * each string a dense accumulator of 2 Q slots instead (no such limit;
- * 16 to 48 bytes a state a string, which bounds the wave size).  Once created, the run calls below allocate
+ * 16 to 48 bytes a state a string, which bounds the wave size).  Once created,
+ * the run calls below allocate
  * nothing, so a sequence of them can be captured into a CUDA graph and
  * replayed.  A Viterbi-only plan and a forward-backward-only plan of the
  * same batch share nothing and may run concurrently on two streams.
@@ -330,31 +338,34 @@ FST_API int fst_set_batch_plan(fst_t* fst, int32_t parts_viterbi, int32_t parts_
 #define FST_PLAN_PARTS(k) ((((int32_t)(k)) & 0xff) << 8)
 FST_API int fst_plan_create(fst_t* fst, const int32_t* d_ids, const int64_t* d_offsets, int32_t B,
                     int64_t mem_budget_bytes, int32_t flags, void* stream, fst_plan_t** out);
+/* Free a plan (NULL accepted).  (No counterpart in the paper.) */
 FST_API int fst_plan_destroy(fst_plan_t* plan);
 
 /* Plan statistics (host outputs, any may be NULL): strings, tokens (sum of
  * lengths), waves, longest string, arc relaxations of one pass (sum over
  * tokens of |delta[w_t]|), kernel launches of one Viterbi run and of one
- * forward-backward run, and device bytes held by the plan. */
+ * forward-backward run, and device bytes held by the plan. The relaxations are
+ * the paper's count (Sec. 5). */
 FST_API int fst_plan_info(const fst_plan_t* plan, int32_t* num_strings, int64_t* num_tokens,
                   int32_t* num_waves, int32_t* max_len, int64_t* relaxations,
                   int64_t* viterbi_launches, int64_t* fb_launches, int64_t* device_bytes);
 
-/* Run Viterbi for every string of the plan (outputs as fst_viterbi_batch).
- * Asynchronous on `stream`; allocates nothing. */
+/* Run Viterbi (Alg. 1) for every string of the plan (outputs as
+ * fst_viterbi_batch).  Asynchronous on `stream`; allocates nothing. */
 FST_API int fst_plan_viterbi(fst_plan_t* plan, float* d_scores, int32_t* d_paths, int32_t* d_olabels,
                      int32_t* d_status, void* stream);
 
-/* Forward pass only (log Z per string); keeps the forward values in the
- * plan for fst_plan_backward.  Requires a single-wave plan. */
+/* Forward pass only (Alg. 2's forward loop; log Z per string); keeps the
+ * forward values in the plan for fst_plan_backward.  Requires a single-wave
+ * plan. */
 FST_API int fst_plan_forward(fst_plan_t* plan, double* d_logz, int32_t* d_status, void* stream);
 
 /* Backward pass and expected counts after fst_plan_forward on the same plan:
  * d_counts[k] = sum_b d_weights[b] * count_b(k) (d_weights NULL = all 1).
- * Returns FST_ERR_STATE if no forward pass preceded it. */
+ * Returns FST_ERR_STATE if no forward pass preceded it. Alg. 2's backward and count loops. */
 FST_API int fst_plan_backward(fst_plan_t* plan, const float* d_weights, float* d_counts, void* stream);
 
-/* Forward and backward for every wave of the plan (any number of waves). */
+/* Forward and backward for every wave of the plan (any number of waves). Alg. 2. */
 FST_API int fst_plan_forward_backward(fst_plan_t* plan, const float* d_weights, double* d_logz,
                               float* d_counts, int32_t* d_status, void* stream);
 
@@ -369,6 +380,7 @@ FST_API int fst_plan_forward_backward(fst_plan_t* plan, const float* d_weights, 
  * fst_plan_backward_ex.  Strings without a path add nothing. */
 FST_API int fst_plan_backward_ex(fst_plan_t* plan, const float* d_weights, float* d_counts, float* d_start,
                                  float* d_final, void* stream);
+/* Alg. 2 with the expected start and final states, every wave. */
 FST_API int fst_plan_forward_backward_ex(fst_plan_t* plan, const float* d_weights, double* d_logz,
                                          float* d_counts, float* d_start, float* d_final, int32_t* d_status,
                                          void* stream);
@@ -406,7 +418,7 @@ FST_API int fst_create_clamped(const fst_t* fst, fst_t** out, int32_t* num_pairs
 /* Pair string of (ids, olabels) for an FST made by fst_create_clamped: host
  * arrays of length n; pair_ids[t] is the symbol of (ids[t], olabels[t]), or
  * num_pairs (no arcs) when no arc carries that pair.  FST_ERR_STATE for a
- * handle that is not a clamped FST. */
+ * handle that is not a clamped FST. (The CRF numerator: not in the paper.) */
 FST_API int fst_clamp_labels(const fst_t* clamped, const int32_t* ids, const int32_t* olabels, int64_t n,
                              int32_t* pair_ids);
 
@@ -435,7 +447,8 @@ FST_API int fst_lattice_viterbi(fst_t* fst, int32_t num_nodes, int32_t num_edges
 /* Forward-backward over a lattice (float64 values): log Z of all (lattice
  * path, FST path) pairs, the expected count of each arc (summed over the
  * edges that read its symbol; [num_arcs] or NULL) and the posterior of each
- * edge ([num_edges] or NULL).  Returns FST_OK, FST_ERR_NO_PATH or an error. */
+ * edge ([num_edges] or NULL).  Returns FST_OK, FST_ERR_NO_PATH or an error.
+ * Alg. 2 over the lattice (Sec. 6.1). */
 FST_API int fst_lattice_forward_backward(fst_t* fst, int32_t num_nodes, int32_t num_edges, const int32_t* from,
                                          const int32_t* to, const int32_t* label, const float* weight,
                                          double* log_z, float* arc_posteriors, float* edge_posteriors);
@@ -474,7 +487,8 @@ FST_API int fst_log_z_f64(fst_t* fst, const double* theta, const int32_t* ids, i
  * waits for the last of them and returns, per kernel kind, the summed
  * device time in milliseconds and the number of launches since the last
  * read (host arrays of FST_PROF_KINDS entries, either may be NULL), then
- * starts a new accumulation.  Do not enable it while capturing a graph. */
+ * starts a new accumulation.  Do not enable it while capturing a graph.
+ * (Tracing: no counterpart in the paper.) */
 #define FST_PROF_VIT_FIRST 0   /* Viterbi: start states push their arcs into the first position */
 #define FST_PROF_VIT_STEP 1    /* Viterbi: one position's live states read out, their arcs pushed into the next */
 #define FST_PROF_VIT_FINAL 2   /* Viterbi final reduction */
@@ -487,25 +501,29 @@ FST_API int fst_log_z_f64(fst_t* fst, const double* theta, const int32_t* ids, i
 #define FST_PROF_COUNTS 9      /* expected counts to float */
 #define FST_PROF_KINDS 10
 FST_API int fst_plan_profile(fst_plan_t* plan, int32_t enable);
+/* Read and restart the accumulation (no counterpart in the paper). */
 FST_API int fst_plan_profile_read(fst_plan_t* plan, double* ms_by_kind, int64_t* launches_by_kind);
 
 /* The same per-launch timing for the single-string calls of a handle
  * (fst_viterbi, fst_forward_backward): kinds and semantics as
- * fst_plan_profile / fst_plan_profile_read. */
+ * fst_plan_profile / fst_plan_profile_read. (Tracing: no counterpart in the paper.) */
 FST_API int fst_profile(fst_t* fst, int32_t enable);
+/* Read and restart the accumulation (no counterpart in the paper). */
 FST_API int fst_profile_read(fst_t* fst, double* ms_by_kind, int64_t* launches_by_kind);
 
 /* The live work of the handle's last single-string call, for measurement:
  * *entries = live states over all positions, *arcs = arcs out of them on
  * their next symbol (-1 unless the last call was fst_forward_backward).
- * Synchronous.  Either output may be NULL. */
+ * Synchronous.  Either output may be NULL. (The relaxations Sec. 5 counts,
+ * restricted to live states.) */
 FST_API int fst_live_work(fst_t* fst, int64_t* entries, int64_t* arcs);
 
 /* The live work of the plan's last pass (its last wave), for measurement:
  * *entries = live states over all positions (the pool entries handed out),
  * *arcs = arcs out of those states on their next symbol (the pushes of the
  * forward pass; -1 for a plan without forward-backward storage).  Waits for
- * the plan's work on `stream`.  Either output may be NULL. */
+ * the plan's work on `stream`.  Either output may be NULL. (The relaxations
+ * Sec. 5 counts, restricted to live states.) */
 FST_API int fst_plan_live_work(fst_plan_t* plan, int64_t* entries, int64_t* arcs, void* stream);
 
 /* How a plan advances its positions (the batched driver).
@@ -525,12 +543,13 @@ FST_API int fst_plan_live_work(fst_plan_t* plan, int64_t* entries, int64_t* arcs
  * Results are identical under both drivers.  FST_ERR_UNSUPPORTED when the
  * device cannot launch cooperative kernels or grid_blocks cannot be
  * co-resident.  Do not run a persistent plan concurrently with another
- * persistent plan on the same device. */
+ * persistent plan on the same device. (Sec. 5 launches one kernel per position;
+ * the persistent driver has no counterpart in the paper.) */
 #define FST_DRIVER_LAUNCH 0
 #define FST_DRIVER_PERSISTENT 1
 FST_API int fst_plan_set_driver(fst_plan_t* plan, int32_t driver, int32_t grid_blocks, int64_t barrier_timeout_us);
 /* The plan's driver and, for the persistent one, the grid of its forward
- * pass (host outputs, either may be NULL). */
+ * pass (host outputs, either may be NULL). (No counterpart in the paper.) */
 FST_API int fst_plan_get_driver(const fst_plan_t* plan, int32_t* driver, int32_t* grid_blocks);
 
 /* Autotuner of the batched driver: runs the plan's own passes (Viterbi and
@@ -547,7 +566,7 @@ FST_API int fst_plan_get_driver(const fst_plan_t* plan, int32_t* driver, int32_t
  * from and appended to it.  Allocates scratch outputs for the timing runs
  * and synchronises `stream`; do not call it during graph capture.  Host
  * outputs (any may be NULL): the chosen driver, its persistent grid (0 for
- * the launch driver) and its time in milliseconds. */
+ * the launch driver) and its time in milliseconds. (No counterpart in the paper.) */
 #define FST_TUNE_REFRESH 1
 FST_API int fst_plan_autotune(fst_plan_t* plan, void* stream, int32_t flags, int32_t* driver, int32_t* grid_blocks,
                               double* best_ms);
@@ -556,7 +575,7 @@ FST_API int fst_plan_autotune(fst_plan_t* plan, void* stream, int32_t flags, int
  * faults).  FST_FAULT_BARRIER_STALL: the grid barriers of the plan's
  * persistent passes wait for `value` blocks (1..1024) beyond the grid, so
  * that no wait can complete and every wait runs out (the FST_ERR_TIMEOUT
- * path).  FST_FAULT_NONE (value ignored) turns injection off. */
+ * path).  FST_FAULT_NONE (value ignored) turns injection off. (No counterpart in the paper.) */
 #define FST_FAULT_NONE 0
 #define FST_FAULT_BARRIER_STALL 1
 FST_API int fst_plan_fault_inject(fst_plan_t* plan, int32_t kind, int64_t value);
@@ -568,7 +587,7 @@ FST_API int fst_plan_fault_inject(fst_plan_t* plan, int32_t kind, int64_t value)
  * status of every string of its wave (scores -inf, paths -1, log Z -inf,
  * no counts) and leaves the plan usable: the next run clears what the
  * overflowing one left behind.  For memory-capped deployments and for
- * exercising that failure path. */
+ * exercising that failure path. (No counterpart in the paper.) */
 FST_API int fst_plan_limit_pool(fst_plan_t* plan, int64_t entries);
 
 /* Direction switch of the forward pass (plans with FST_PLAN_DENSE_ACC and
@@ -592,7 +611,7 @@ FST_API int fst_plan_set_pull(fst_plan_t* plan, int64_t min_live);
  * recorded (code: 1 staging, 2 pool write, 3 pool read, 4 dense
  * accumulator, 5 arc record; its index and the bound) and the access is
  * skipped.  This call reads the record (host outputs, any may be NULL) and
- * clears it.  FST_ERR_UNSUPPORTED in a normal build. */
+ * clears it.  FST_ERR_UNSUPPORTED in a normal build. (No counterpart in the paper.) */
 FST_API int fst_debug_checks(int64_t* violations, int32_t* code, int64_t* index, int64_t* bound);
 
 /* Compact accumulators: cap the hash tables of the plan's following runs at
@@ -600,10 +619,11 @@ FST_API int fst_debug_checks(int64_t* violations, int32_t* code, int64_t* index,
  * allocated, which larger values cannot exceed).  Allocates nothing.  A run
  * with more live states at one position than a table holds reports
  * FST_ERR_OOM for every string of its wave and leaves the plan usable, as
- * with fst_plan_limit_pool.  No effect on FST_PLAN_DENSE_ACC plans. */
+ * with fst_plan_limit_pool.  No effect on FST_PLAN_DENSE_ACC plans.
+ * (No counterpart in the paper.) */
 FST_API int fst_plan_limit_table(fst_plan_t* plan, int64_t slots);
 /* Slots of each compact accumulator table (the largest over the plan's
- * parts; 0 for FST_PLAN_DENSE_ACC). */
+ * parts; 0 for FST_PLAN_DENSE_ACC). (No counterpart in the paper.) */
 FST_API int fst_plan_table_slots(const fst_plan_t* plan, int64_t* slots);
 
 /* Plain-method Viterbi of one string that allocates no memory (the paper
@@ -630,13 +650,15 @@ FST_API int fst_plan_table_slots(const fst_plan_t* plan, int64_t* slots);
  * about 24*Q + 16*(sum over positions of the distinct destinations of the
  * position's symbol) + 8*(the largest such count) + 60*n bytes.  The
  * first call on a device looks up the array's device address with that
- * device current: make it before any stream capture.  All calls share the array and see the previous call's
+ * device current: make it before any stream capture.  All calls share the array
+ * and see the previous call's
  * contents, which each call clears where needed; calls that overlap on the
  * GPU race on it and must be serialised by the caller. */
 FST_API int fst_viterbi_noalloc(fst_t* fst, const int32_t* ids, int32_t n, float* d_score, int32_t* d_path,
                                 int32_t* d_olabels, void* stream);
 
-/* Message of the last failing call on this host thread ("" if none). */
+/* Message of the last failing call on this host thread ("" if none).
+ * (No counterpart in the paper.) */
 FST_API const char* fst_last_error(void);
 
 #ifdef __cplusplus
