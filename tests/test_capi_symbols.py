@@ -73,3 +73,18 @@ def test_debug_checks_unsupported_in_a_normal_build(libpath):
     rc = lib.fst_debug_checks(ctypes.byref(v), None, None, None)
     assert rc == _lib.UNSUPPORTED and v.value == -1
     assert b"FST_DEBUG" in lib.fst_last_error()
+
+
+def test_every_declaration_cites_its_passage():
+    # each entry point's comment cites the paper passage it follows (a
+    # section, algorithm, equation, figure or table) or says the paper has
+    # no counterpart
+    h = open(os.path.join(ROOT, "include", "fstgpu.h")).read()
+    decls = list(re.finditer(r"FST_API[^;]*?\b(fst_[a-z0-9_]+)\s*\(", h))
+    assert len(decls) > 40
+    prev, missing = 0, []
+    for m in decls:
+        if not re.search(r"Sec\.|Alg\.|Eq\.|Fig\.|Table|paper", h[prev:m.start()]):
+            missing.append(m.group(1))
+        prev = m.end()
+    assert not missing, missing
