@@ -87,7 +87,7 @@ def _ptr(a):
 
 
 def theta_of_cost(w) -> np.ndarray:
-    """theta = -w in float32, +inf cost -> -inf, and -0.0 -> +0.0."""
+    """theta = -w in float32, +inf cost -> -inf, and -0.0 -> +0.0 (reading R1)."""
     t = -np.asarray(w, dtype=np.float32)
     t = t + np.float32(0.0)  # -0.0 + 0.0 == +0.0 under round-to-nearest
     return np.ascontiguousarray(t, dtype=np.float32)
@@ -114,8 +114,9 @@ class Fst:
                 self.theta_f, self.m)
 
     def viterbi(self, x, tables: bool = False):
-        """Returns dict(status, best (float32), final_state, path[n] arc ids,
-        olabels[n]) and, with tables=True, V[(n+1),Q] and bp[n,Q]."""
+        """Alg. 1 (Sec. 5.1) on one string.  Returns dict(status, best
+        (float32), final_state, path[n] arc ids, olabels[n]) and, with
+        tables=True, V[(n+1),Q] and bp[n,Q]."""
         x = np.ascontiguousarray(x, np.int32)
         n = int(x.shape[0])
         best = np.zeros(1, np.float32)
@@ -135,7 +136,7 @@ class Fst:
         return out
 
     def forward_backward(self, x, tables: bool = False):
-        """Returns dict(status, logz (float64), counts[A] float64) and, with
+        """Alg. 2 (Sec. 5.2) on one string.  Returns dict(status, logz (float64), counts[A] float64) and, with
         tables=True, alpha and beta [(n+1), Q] float64."""
         x = np.ascontiguousarray(x, np.int32)
         n = int(x.shape[0])
@@ -172,7 +173,7 @@ class Fst:
         return dict(status=fb["status"], logz=lz, start=np.nan_to_num(start), final=np.nan_to_num(final))
 
     def state_posteriors_batch(self, ids, offsets, weights=None):
-        """Weighted sums over a batch of state_posteriors (weight 1 by
+        """Weighted sums over a batch of state_posteriors (reading R14; weight 1 by
         default): the gradients of sum_b g_b log Z_b."""
         off = np.asarray(offsets, np.int64)
         start = np.zeros(self.Q, np.float64)
@@ -185,6 +186,7 @@ class Fst:
         return dict(start=start, final=final)
 
     def viterbi_batch(self, ids, offsets, nthreads: int = 1):
+        """Alg. 1 on every string of a batch (threads over strings)."""
         ids = np.ascontiguousarray(ids, np.int32)
         off = np.ascontiguousarray(offsets, np.int64)
         B = int(off.shape[0] - 1)
@@ -197,6 +199,8 @@ class Fst:
         return dict(best=best[:B], paths=paths[:int(off[-1])], status=status[:B])
 
     def fb_batch(self, ids, offsets, nthreads: int = 1, weights=None, counts: bool = True):
+        """Alg. 2 on every string of a batch (threads over strings): log Z per
+        string and sum_b weights[b] count_b (reading R10)."""
         ids = np.ascontiguousarray(ids, np.int32)
         off = np.ascontiguousarray(offsets, np.int64)
         B = int(off.shape[0] - 1)
@@ -212,7 +216,7 @@ class Fst:
 
     # ------------------------------------------------------------ training
     def em_update(self, counts, alpha: float = 0.0) -> np.ndarray:
-        """EM re-estimation (see oracle_em_update in oracle.c): float64 log-weights
+        """EM re-estimation (Sec. 4; oracle_em_update in oracle.c): float64 log-weights
         theta'_k = log((count_k + alpha) / sum over the arcs of src_k of
         (count + alpha)); states with a zero total keep their old weights."""
         c = np.ascontiguousarray(counts, np.float64)
@@ -223,7 +227,7 @@ class Fst:
         return out[:self.A]
 
     def clamped(self, x, y):
-        """The output-clamped problem of (x, y): the paths that read x and
+        """The output-clamped problem of (x, y) (reading R18): the paths that read x and
         write y are the paths of the FST whose arc k reads the pair
         (ilabel_k, olabel_k), run on the string of pairs (x_t, y_t).  Returns
         (an Fst view of that FST, the pair string); a pair no arc carries maps
@@ -278,8 +282,9 @@ class Lattice:
 
 
 def lattice_viterbi(o: Fst, lat: Lattice):
-    """Viterbi over an input lattice composed with the FST, node by node in
-    id order (a topological order), float32 as the string case: a candidate
+    """Viterbi (Alg. 1) over an input lattice (Sec. 6.1) composed with the
+    FST, node by node in id order (a topological order), float32 as the
+    string case: a candidate
     through edge e = (u -> v) and arc k is fl(fl(V[u][src_k] + theta_k) +
     w_e); the best wins, ties to the lowest arc id, then the lowest edge id.
     At the end node the best state adds its final weight (lowest state on

@@ -63,6 +63,8 @@ typedef struct {
     int64_t *arcs;  /* [A]   */
 } sym_index;
 
+/* The slices delta[a] of Sec. 4 / Fig. 2: the R offsets and the arcs of each
+ * input symbol, by a counting sort over the arcs. */
 static int build_index(int64_t A, const int32_t *ilabel, int32_t m, sym_index *ix)
 {
     ix->m = m;
@@ -79,6 +81,7 @@ static int build_index(int64_t A, const int32_t *ilabel, int32_t m, sym_index *i
     return OR_OK;
 }
 
+/* Release a slice index (no counterpart in the paper). */
 static void free_index(sym_index *ix)
 {
     free(ix->off);
@@ -158,8 +161,9 @@ static int viterbi_one(const fst_view *f, const sym_index *ix, const int32_t *x,
 /* two-pass log-sum-exp).                                                   */
 /* ---------------------------------------------------------------------- */
 
-/* One forward step: out[q'] = LSE_{k in slice, dst_k = q'} (in[src_k] + theta_k).
- * With `reverse`, the roles of src and dst swap (backward step). */
+/* One forward step of Alg. 2: out[q'] = LSE_{k in slice, dst_k = q'}
+ * (in[src_k] + theta_k).  With `reverse`, the roles of src and dst swap
+ * (backward step). */
 static void lse_step(const fst_view *f, const sym_index *ix, int32_t a, const double *in,
                      double *out, double *mx, int reverse)
 {
@@ -181,6 +185,8 @@ static void lse_step(const fst_view *f, const sym_index *ix, int32_t a, const do
         out[q] = (mx[q] > -INFINITY) ? mx[q] + log(out[q]) : -INFINITY;
 }
 
+/* Alg. 2 for one string: the forward and backward loops, log Z, and the
+ * expected count of each arc (per arc, reading R6). */
 static int fb_one(const fst_view *f, const sym_index *ix, const int32_t *x, int32_t n,
                   double scale, double *logz_out, double *counts /* += scale*gamma */,
                   double *alpha_out, double *beta_out)
@@ -238,6 +244,8 @@ static int fb_one(const fst_view *f, const sym_index *ix, const int32_t *x, int3
     return logz > -INFINITY ? OR_OK : OR_NO_PATH;
 }
 
+/* The FST of Sec. 3 is well formed: states and labels in range, no NaN and
+ * no +inf log-weight (reading R1). */
 static int check_fst(const fst_view *f)
 {
     if (f->Q <= 0 || f->A < 0 || f->m <= 0) return OR_INVALID;
@@ -257,7 +265,8 @@ static int check_fst(const fst_view *f)
     const int32_t *ilabel, const float *theta, const float *theta_s, const float *theta_f, int32_t m
 #define FST_VIEW fst_view f = {Q, A, src, dst, ilabel, theta, theta_s, theta_f, m}
 
-/* Single string, Viterbi.  V_out [(n+1)*Q] and bp_out [n*Q] are optional. */
+/* Single string, Viterbi (Alg. 1, Sec. 5.1).  V_out [(n+1)*Q] and bp_out
+ * [n*Q] are optional. */
 int oracle_viterbi(FST_ARGS, const int32_t *x, int32_t n, float *best, int32_t *final_state,
                    int32_t *path, float *V_out, int32_t *bp_out)
 {
@@ -270,8 +279,9 @@ int oracle_viterbi(FST_ARGS, const int32_t *x, int32_t n, float *best, int32_t *
     return rc;
 }
 
-/* Single string, forward-backward.  counts [A] receives sum_t gamma_t(k)
- * (it is overwritten); alpha_out / beta_out [(n+1)*Q] are optional. */
+/* Single string, forward-backward (Alg. 2, Sec. 5.2).  counts [A] receives
+ * sum_t gamma_t(k) (it is overwritten); alpha_out / beta_out [(n+1)*Q] are
+ * optional. */
 int oracle_forward_backward(FST_ARGS, const int32_t *x, int32_t n, double *logz,
                             double *counts, double *alpha_out, double *beta_out)
 {
@@ -310,6 +320,8 @@ typedef struct {
 
 typedef struct { batch_job *job; int tid; } batch_arg;
 
+/* One thread of a batch: Alg. 1 or Alg. 2 string by string, unchanged (the
+ * strings are independent; threads only split the batch). */
 static void *batch_worker(void *p)
 {
     batch_arg *arg = (batch_arg *)p;
@@ -333,6 +345,7 @@ static void *batch_worker(void *p)
     return NULL;
 }
 
+/* Start the batch's threads and wait for them (no counterpart in the paper). */
 static int run_batch(batch_job *job, int nthreads)
 {
     if (nthreads < 1) nthreads = 1;
@@ -354,6 +367,7 @@ static int run_batch(batch_job *job, int nthreads)
     return atomic_load(&job->fail);
 }
 
+/* Alg. 1 for every string of a batch (ids, off as the batched calls). */
 int oracle_viterbi_batch(FST_ARGS, const int32_t *ids, const int64_t *off, int32_t B,
                          int32_t nthreads, float *best, int32_t *paths, int32_t *status)
 {
@@ -370,7 +384,8 @@ int oracle_viterbi_batch(FST_ARGS, const int32_t *ids, const int64_t *off, int32
     return rc;
 }
 
-/* counts_sum [A] (optional) receives sum_b weights[b] * count_b (weights NULL = all 1). */
+/* Alg. 2 for every string of a batch.  counts_sum [A] (optional) receives
+ * sum_b weights[b] * count_b (weights NULL = all 1). */
 int oracle_fb_batch(FST_ARGS, const int32_t *ids, const int64_t *off, int32_t B,
                     int32_t nthreads, const double *weights, double *logz,
                     double *counts_sum, int32_t *status)
