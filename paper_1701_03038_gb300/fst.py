@@ -172,7 +172,7 @@ class Fst:
 
     # ------------------------------------------------- plain method (one string)
     def viterbi(self, ids):
-        """Best path of one string: (score float32, arc ids int32[n], output
+        """Alg. 1 (Sec. 5.1): best path of one string: (score float32, arc ids int32[n], output
         labels int32[n], status).  Status NO_PATH means no accepting path."""
         x = _host(ids, np.int32)
         n = int(x.shape[0])
@@ -185,7 +185,7 @@ class Fst:
         return best[0], path[:n], olab[:n], rc
 
     def viterbi_slice(self, ids):
-        """The paper's relaxation (every arc of every slice, one thread per
+        """The paper's relaxation of Sec. 5.1 (every arc of every slice, one thread per
         arc), for comparison: (score float32, arc ids int32[n], status),
         bit-identical to viterbi()."""
         x = _host(ids, np.int32)
@@ -198,7 +198,7 @@ class Fst:
         return best[0], path[:n], rc
 
     def forward_backward_slice(self, ids, posteriors: bool = True):
-        """The paper's forward-backward (every arc of every slice, atomic
+        """The paper's forward-backward of Sec. 5.2 (every arc of every slice, atomic
         log-add-exp in float32), for comparison: (log Z, counts, status)."""
         x = _host(ids, np.int32)
         n = int(x.shape[0])
@@ -246,7 +246,7 @@ class Fst:
         check(self._lib.fst_set_slice_order(self._h, int(order)), "fst_set_slice_order")
 
     def forward_backward(self, ids, posteriors: bool = True, out: np.ndarray | None = None):
-        """(log Z float64, expected arc counts float32[A] or None, status).
+        """Alg. 2 (Sec. 5.2) on one string: (log Z float64, expected arc counts float32[A] or None, status).
         ``out``, a C-contiguous float32 host array of at least A elements
         (for instance the numpy view of a pinned torch tensor, reused from
         call to call), receives the counts instead of a new array; the
@@ -289,7 +289,7 @@ class Fst:
         return int(num_nodes), e, arrs
 
     def lattice_viterbi(self, num_nodes, frm, to, label, weight):
-        """Best (lattice path, FST path) of an acyclic input lattice (see
+        """Best (lattice path, FST path) of an acyclic input lattice (Sec. 6.1; see
         fst_lattice_viterbi): (score float32, edges int32[L], arcs int32[L], status)."""
         n, e, (a, b, c, d) = self._lattice_args(num_nodes, frm, to, label, weight)
         best = np.zeros(1, np.float32)
@@ -304,7 +304,7 @@ class Fst:
         return best[0], ep[:L], ap[:L], rc
 
     def lattice_forward_backward(self, num_nodes, frm, to, label, weight):
-        """(log Z, arc counts float32[A], edge posteriors float32[E], status)
+        """Alg. 2 over an input lattice (Sec. 6.1): (log Z, arc counts float32[A], edge posteriors float32[E], status)
         of an acyclic input lattice (see fst_lattice_forward_backward)."""
         n, e, (a, b, c, d) = self._lattice_args(num_nodes, frm, to, label, weight)
         lz = np.zeros(1, np.float64)
@@ -317,7 +317,7 @@ class Fst:
         return float(lz[0]), cnt[:self.num_arcs], ep[:e], rc
 
     def prefix_log_z(self, ids):
-        """(log Z, best score, status) of one string by the parallel product of
+        """(log Z, best score, status) of one string by the parallel product (Sec. 6.1) of
         its dense slice matrices (small dense FSTs; see fst_prefix_log_z)."""
         x = _host(ids, np.int32)
         lz = np.zeros(1, np.float64)
@@ -329,7 +329,7 @@ class Fst:
 
     # ------------------------------------------------------------ training
     def em_update(self, counts, pseudo_count: float = 0.0, apply: bool = False):
-        """EM M-step (fst_em_update): new log-weights, each state's outgoing
+        """EM M-step (Sec. 4; fst_em_update): new log-weights, each state's outgoing
         arcs renormalised from their expected counts.  ``counts``: a CUDA
         float32 tensor (returns a CUDA tensor) or a host array (returns
         numpy).  ``apply`` also installs them as the FST's weights."""
@@ -416,6 +416,8 @@ class Fst:
         return Plan(self, ids, offsets, mem_budget=mem_budget, flags=flags, stream=stream)
 
     def viterbi_batch(self, ids: torch.Tensor, offsets: torch.Tensor, stream=None):
+        """Alg. 1 for every string of a batch (fst_viterbi_batch): dict of
+        scores [B], paths [N], olabels [N], status [B] on the device."""
         _require_cuda(ids, torch.int32, "ids")
         _require_cuda(offsets, torch.int64, "offsets")
         B = int(offsets.numel()) - 1
@@ -432,6 +434,9 @@ class Fst:
 
     def forward_backward_batch(self, ids: torch.Tensor, offsets: torch.Tensor, weights=None,
                                counts: bool = True, stream=None):
+        """Alg. 2 for every string of a batch (fst_forward_backward_batch):
+        dict of logz [B], counts [A] (sum_b weights[b] count_b, or None) and
+        status [B] on the device."""
         _require_cuda(ids, torch.int32, "ids")
         _require_cuda(offsets, torch.int64, "offsets")
         B = int(offsets.numel()) - 1
@@ -448,7 +453,8 @@ class Fst:
 
 
 class Plan:
-    """Device work lists and storage for one batch (see fst_plan_create).
+    """Device work lists and storage for one batch (see fst_plan_create): the
+    per-position loops of Alg. 1 and Alg. 2 (Sec. 5) for every string.
     Run calls allocate nothing and are safe to capture in a CUDA graph."""
 
     def __init__(self, fst: Fst, ids: torch.Tensor, offsets: torch.Tensor, mem_budget: int = 0,
@@ -560,17 +566,19 @@ class Plan:
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(_lib.PROF_KINDS)}
 
     def viterbi(self, stream=None):
-        """Queue Viterbi for every string; results land in self.scores /
+        """Queue Viterbi (Alg. 1) for every string; results land in self.scores /
         self.paths / self.olabels / self.status."""
         check(self._lib.fst_plan_viterbi(self._h, _dptr(self.scores), _dptr(self.paths), _dptr(self.olabels),
                                          _dptr(self.status), _stream(stream)), "fst_plan_viterbi")
 
     def forward(self, stream=None):
+        """Forward pass only (Alg. 2's forward loop): log Z into self.logz;
+        the forward values stay in the plan for backward()."""
         check(self._lib.fst_plan_forward(self._h, _dptr(self.logz), _dptr(self.status), _stream(stream)),
               "fst_plan_forward")
 
     def backward(self, weights: torch.Tensor | None = None, stream=None, states: bool = False):
-        """Backward pass after forward(): arc counts into self.counts and,
+        """Backward pass (Alg. 2's backward and count loops) after forward(): arc counts into self.counts and,
         with states=True, expected start and final states into
         self.start_counts / self.final_counts."""
         if weights is not None:
