@@ -1,6 +1,8 @@
 // noalloc.cu -- fst_viterbi_noalloc: the plain Viterbi decode of one string
-// with every piece of per-call working memory taken from one fixed,
-// file-scope device array instead of cudaMalloc.
+// (Alg. 1, Sec. 5.1, with the frontier-driven steps of the other
+// single-string calls) with every piece of per-call working memory taken
+// from one fixed, file-scope device array instead of cudaMalloc.  The paper
+// has no counterpart: this is a deployment variant.
 //
 // Some callers cannot allocate device memory at decode time: a host
 // application whose memory manager owns every allocation, code that must not

@@ -1,6 +1,8 @@
 // sort_scan.cu -- device primitives used when an FST or a plan is built:
 // exclusive prefix sums and a stable LSD radix sort of (u64 key, u32 value)
-// pairs.  Written for this library; no external sort or scan library.
+// pairs.  They sort the arcs into the symbol-major slices of Sec. 4 / Fig. 2
+// (the R offsets are a prefix sum of the per-symbol arc counts).  Written
+// for this library; no external sort or scan library.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
