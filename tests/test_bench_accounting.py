@@ -221,3 +221,24 @@ def test_cpu_baseline_sample_and_repeats():
     per_pass = 3 * int(np.bincount(fa.ilabel, minlength=fa.num_isyms)[strs.ids].sum())
     dt, rx, _ = bench.cpu_oracle_run(fa, strs, list(range(strs.count)), "batch")
     assert rx == per_pass and dt > 0
+
+
+def test_reference_arm_line(capsys):
+    # bench.py --impl reference: the oracle on the host cores, one JSON line
+    # with the contract's keys, its own cpu_baseline and an e2e that moves no
+    # bytes; ranks other than 0 print nothing
+    import json
+    args = bench.parse_args(["--impl", "reference", "--workload", "c1", "--steps", "2", "--warmup", "3"])
+    bench.run_reference(args, 1)
+    assert capsys.readouterr().out == ""
+    bench.run_reference(args, 0)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 3
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["unit"] == line["unit"]
+    assert line["config"]["workload"].startswith("c1")
